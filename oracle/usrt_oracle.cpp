@@ -1,0 +1,1375 @@
+// usrt oracle: a plain, slow, FP64 CPU implementation of the differentiable full-path
+// Monte Carlo ultrasound ray-tracing hot path (arXiv 2604.15017).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or calls this
+// file; it shares no code, header, table or constant generator with the CUDA path.  Only the
+// tests, the package's smoke check and the benchmark's CPU-baseline leg load it.
+//
+// Every function names the passage of the paper it follows.  Where the paper is silent the
+// reading taken is stated beside the code (the same readings are listed in the design notes).
+//
+// Units: SI throughout (metres, seconds, hertz, kg/m^3); attenuation in dB/cm/MHz.
+// Parameter vector theta = [c_0, rho_0, alpha_0, ..., c_{M-1}, rho_{M-1}, alpha_{M-1}, A_s, f0].
+//
+// Pieces:
+//   * Philox4x32-10 counter-based generator (Salmon et al., SC'11): 10 rounds, multipliers
+//     0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
+//   * scene: triangles with (m_front, m_back) media, point scatterers, brute force or a simple
+//     median-split BVH for closest-hit and all-crossings queries (textbook Moller-Trumbore).
+//   * forward transport (Sec. 2.3.1-2.3.3): emission, traversal, Fresnel/Snell interface,
+//     receiver-guided secondary rays at scatterers, receive directivity (Eq. cutoff).
+//   * replay of frozen decisions, templated on the scalar so that the same code runs in double
+//     (finite differences, Sec. 3.2 / Sec. 4.2.1) and in forward-mode dual numbers (gradient).
+//   * splat with the axial pulse (Eq. axial_sig), delay-and-sum (Eq. das), Hilbert envelope,
+//     log compression and dynamic-range clip (Sec. 2.3.4), the l1+l2 loss (Eq.
+//     weighted_l1_l2_loss) and the vector-Jacobian products of the image chain (Eq.
+//     das_adjoint and the envelope/log derivative).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+// amplitude attenuation exponent per (dB/cm/MHz) * Hz * m: ln(10)/20 [Np/dB] * 1e-6 [MHz/Hz] * 100 [cm/m]
+const double KAPPA = std::log(10.0) / 20.0 * 1e-4;
+// minimum hit distance [m] of every ray query (reading: a ray leaving a surface must not re-hit
+// that surface or its neighbour at the shared edge; 0.1 um is far below a wavelength)
+const double T_MIN = 1e-7;
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11).  One round maps (c0,c1,c2,c3) with key (k0,k1) to
+//   (hi(B*c2) ^ c1 ^ k0, lo(B*c2), hi(A*c0) ^ c3 ^ k1, lo(A*c0)),  A=0xD2511F53, B=0xCD9E8D57,
+// and the key is bumped by the Weyl constants between rounds.
+// ------------------------------------------------------------------------------------------
+struct U4 {
+  uint32_t v[4];
+};
+
+U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+  for (int round = 0; round < 10; ++round) {
+    uint64_t pa = (uint64_t)0xD2511F53u * (uint64_t)c0;
+    uint64_t pb = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+    uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)pb;
+    uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)pa;
+    c0 = n0;
+    c1 = n1;
+    c2 = n2;
+    c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  U4 r = {{c0, c1, c2, c3}};
+  return r;
+}
+
+// top 24 bits as a uniform in [0, 1): exactly representable in float and double
+double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+
+// ------------------------------------------------------------------------------------------
+// Forward-mode dual numbers: value + gradient w.r.t. up to NP parameters.
+// ------------------------------------------------------------------------------------------
+const int NP = 48;
+
+struct Dual {
+  double v;
+  double d[NP];
+  Dual() : v(0) { std::memset(d, 0, sizeof d); }
+  Dual(double x) : v(x) { std::memset(d, 0, sizeof d); }
+};
+
+Dual operator+(const Dual& a, const Dual& b) {
+  Dual r(a.v + b.v);
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+Dual operator-(const Dual& a, const Dual& b) {
+  Dual r(a.v - b.v);
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+Dual operator-(const Dual& a) {
+  Dual r(-a.v);
+  for (int i = 0; i < NP; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+Dual operator*(const Dual& a, const Dual& b) {
+  Dual r(a.v * b.v);
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+Dual operator/(const Dual& a, const Dual& b) {
+  Dual r(a.v / b.v);
+  for (int i = 0; i < NP; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+  return r;
+}
+Dual operator+(const Dual& a, double b) { Dual r = a; r.v += b; return r; }
+Dual operator-(double b, const Dual& a) { return -a + b; }
+Dual operator*(const Dual& a, double b) {
+  Dual r(a.v * b);
+  for (int i = 0; i < NP; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+Dual operator*(double b, const Dual& a) { return a * b; }
+Dual operator/(const Dual& a, double b) { return a * (1.0 / b); }
+Dual operator/(double a, const Dual& b) {
+  Dual r(a / b.v);
+  for (int i = 0; i < NP; ++i) r.d[i] = -a * b.d[i] / (b.v * b.v);
+  return r;
+}
+// chain rule helper: f(a) with derivative df
+Dual chain(const Dual& a, double f, double df) {
+  Dual r(f);
+  for (int i = 0; i < NP; ++i) r.d[i] = df * a.d[i];
+  return r;
+}
+Dual sqrt(const Dual& a) { double s = std::sqrt(a.v); return chain(a, s, s > 0 ? 0.5 / s : 0.0); }
+Dual exp(const Dual& a) { double e = std::exp(a.v); return chain(a, e, e); }
+Dual sin(const Dual& a) { return chain(a, std::sin(a.v), std::cos(a.v)); }
+Dual acos(const Dual& a) {
+  double q = 1.0 - a.v * a.v;
+  return chain(a, std::acos(a.v), q > 0 ? -1.0 / std::sqrt(q) : 0.0);
+}
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+using std::acos;
+using std::exp;
+using std::fabs;
+using std::log;
+using std::sin;
+using std::cos;
+using std::sqrt;
+
+template <class S>
+struct V3 {
+  S x, y, z;
+};
+template <class S> V3<S> mk3(S x, S y, S z) { V3<S> r; r.x = x; r.y = y; r.z = z; return r; }
+template <class S, class T> V3<S> add(const V3<S>& a, const V3<T>& b) { return mk3<S>(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class S, class T> V3<S> sub(const V3<S>& a, const V3<T>& b) { return mk3<S>(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class S, class K> V3<S> scale(const V3<S>& a, const K& k) { return mk3<S>(a.x * k, a.y * k, a.z * k); }
+template <class S, class T> S dot(const V3<S>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+typedef V3<double> D3;
+D3 d3(double x, double y, double z) { return mk3<double>(x, y, z); }
+D3 cross(const D3& a, const D3& b) { return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+double dotd(const D3& a, const D3& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+D3 subd(const D3& a, const D3& b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
+
+// ------------------------------------------------------------------------------------------
+// Acquisition and image descriptors (flat double arrays; layout mirrored in oracle.py)
+// ------------------------------------------------------------------------------------------
+enum {
+  A_NE = 0, A_PITCH, A_HEL, A_NTX, A_FS, A_NS, A_KMAX, A_NR, A_BW, A_ALPHA_M, A_ALPHA_C, A_CBF,
+  A_SPLIT_MODE, A_SPLIT_Q, A_STREAM, A_TX_ELEM, A_COUNT
+};
+enum { I_NL = 0, I_ND, I_X0, I_X1, I_Z0, I_Z1, I_DR, I_L1, I_L2, I_COUNT };
+
+struct Acq {
+  int ne, ntx, ns, kmax, nr, split_mode, tx_elem;
+  double pitch, hel, fs, bw, alpha_m, alpha_c, cbf, split_q;
+  uint32_t stream;
+  std::vector<double> angles;
+  int n_emit() const { return tx_elem < 0 ? ne : 1; }
+  long long rays_per_tx() const { return (long long)n_emit() * nr; }
+  long long n_paths() const { return rays_per_tx() * ntx; }
+  double elem_x(int e) const { return (e - 0.5 * (ne - 1)) * pitch; }
+  double aperture() const { return (ne - 1) * pitch; }
+};
+
+Acq make_acq(const double* a, const double* angles) {
+  Acq q;
+  q.ne = (int)a[A_NE];
+  q.pitch = a[A_PITCH];
+  q.hel = a[A_HEL];
+  q.ntx = (int)a[A_NTX];
+  q.fs = a[A_FS];
+  q.ns = (int)a[A_NS];
+  q.kmax = (int)a[A_KMAX];
+  q.nr = (int)a[A_NR];
+  q.bw = a[A_BW];
+  q.alpha_m = a[A_ALPHA_M];
+  q.alpha_c = a[A_ALPHA_C];
+  q.cbf = a[A_CBF];
+  q.split_mode = (int)a[A_SPLIT_MODE];
+  q.split_q = a[A_SPLIT_Q];
+  q.stream = (uint32_t)a[A_STREAM];
+  q.tx_elem = (int)a[A_TX_ELEM];
+  q.angles.assign(angles, angles + q.ntx);
+  return q;
+}
+
+struct Img {
+  int nl, nd;
+  double x0, x1, z0, z1, dr, l1, l2;
+};
+Img make_img(const double* p) {
+  Img m;
+  m.nl = (int)p[I_NL];
+  m.nd = (int)p[I_ND];
+  m.x0 = p[I_X0];
+  m.x1 = p[I_X1];
+  m.z0 = p[I_Z0];
+  m.z1 = p[I_Z1];
+  m.dr = p[I_DR];
+  m.l1 = p[I_L1];
+  m.l2 = p[I_L2];
+  return m;
+}
+double line_x(const Img& m, int l) { return m.nl > 1 ? m.x0 + (m.x1 - m.x0) * l / (m.nl - 1) : m.x0; }
+double depth_z(const Img& m, int d) { return m.nd > 1 ? m.z0 + (m.z1 - m.z0) * d / (m.nd - 1) : m.z0; }
+
+// ------------------------------------------------------------------------------------------
+// Scene: triangles (v0,v1,v2; front medium = side the normal (v1-v0)x(v2-v0) points to),
+// point scatterers (centre, amplitude s_j, common radius r_s), optional median-split BVH.
+// ------------------------------------------------------------------------------------------
+enum { CLS_NONE = 0, CLS_XDCR = 1, CLS_TRI = 2, CLS_SCAT = 3 };
+
+struct Hit {
+  double t;
+  int cls, id;
+};
+bool hit_before(const Hit& a, const Hit& b) {  // (t, class, id) lexicographic
+  if (a.t != b.t) return a.t < b.t;
+  if (a.cls != b.cls) return a.cls < b.cls;
+  return a.id < b.id;
+}
+
+struct BNode {
+  double lo[3], hi[3];
+  int left, right;  // children (inner) or -1
+  int first, count; // primitive range in order[] for leaves
+};
+
+struct Scene {
+  int nt = 0, nsct = 0;
+  std::vector<D3> v0, v1, v2;
+  std::vector<int> mfront, mback;
+  std::vector<D3> sp;
+  std::vector<double> samp;
+  double rs = 0;
+  bool use_bvh = false;
+  std::vector<BNode> nodes;
+  std::vector<int> order;  // primitive ids: 0..nt-1 triangles, nt.. scatterers
+
+  void prim_box(int p, double lo[3], double hi[3]) const {
+    if (p < nt) {
+      const D3* v[3] = {&v0[p], &v1[p], &v2[p]};
+      for (int a = 0; a < 3; ++a) {
+        double mn = 1e300, mx = -1e300;
+        for (int k = 0; k < 3; ++k) {
+          double c = a == 0 ? v[k]->x : a == 1 ? v[k]->y : v[k]->z;
+          mn = std::min(mn, c);
+          mx = std::max(mx, c);
+        }
+        lo[a] = mn;
+        hi[a] = mx;
+      }
+    } else {
+      const D3& c = sp[p - nt];
+      lo[0] = c.x - rs; hi[0] = c.x + rs;
+      lo[1] = c.y - rs; hi[1] = c.y + rs;
+      lo[2] = c.z - rs; hi[2] = c.z + rs;
+    }
+  }
+
+  // simple recursive median split on the longest centroid axis, leaves of <= 4 primitives
+  int build(int first, int count, std::vector<double>& cen) {
+    BNode n;
+    for (int a = 0; a < 3; ++a) { n.lo[a] = 1e300; n.hi[a] = -1e300; }
+    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    for (int i = first; i < first + count; ++i) {
+      double lo[3], hi[3];
+      prim_box(order[i], lo, hi);
+      for (int a = 0; a < 3; ++a) {
+        n.lo[a] = std::min(n.lo[a], lo[a]);
+        n.hi[a] = std::max(n.hi[a], hi[a]);
+        double c = cen[3 * order[i] + a];
+        clo[a] = std::min(clo[a], c);
+        chi[a] = std::max(chi[a], c);
+      }
+    }
+    int idx = (int)nodes.size();
+    nodes.push_back(n);
+    if (count <= 4) {
+      nodes[idx].left = nodes[idx].right = -1;
+      nodes[idx].first = first;
+      nodes[idx].count = count;
+      return idx;
+    }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+      if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+    int mid = first + count / 2;
+    std::nth_element(order.begin() + first, order.begin() + mid, order.begin() + first + count,
+                     [&](int p, int q) { return cen[3 * p + axis] < cen[3 * q + axis]; });
+    int l = build(first, mid - first, cen);
+    int r = build(mid, first + count - mid, cen);
+    nodes[idx].left = l;
+    nodes[idx].right = r;
+    nodes[idx].first = nodes[idx].count = 0;
+    return idx;
+  }
+
+  void build_bvh() {
+    int n = nt + nsct;
+    order.resize(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::vector<double> cen(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+      double lo[3], hi[3];
+      prim_box(i, lo, hi);
+      for (int a = 0; a < 3; ++a) cen[3 * i + a] = 0.5 * (lo[a] + hi[a]);
+    }
+    nodes.clear();
+    if (n) build(0, n, cen);
+    use_bvh = true;
+  }
+};
+
+// Moller-Trumbore ray/triangle test (Moller & Trumbore 1997); returns t > 0 or -1
+double tri_hit(const Scene& s, int i, const D3& o, const D3& w) {
+  D3 e1 = subd(s.v1[i], s.v0[i]), e2 = subd(s.v2[i], s.v0[i]);
+  D3 p = cross(w, e2);
+  double det = dotd(e1, p);
+  if (det == 0.0) return -1;
+  double inv = 1.0 / det;
+  D3 tv = subd(o, s.v0[i]);
+  double u = dotd(tv, p) * inv;
+  if (u < 0.0 || u > 1.0) return -1;
+  D3 q = cross(tv, e1);
+  double v = dotd(w, q) * inv;
+  if (v < 0.0 || u + v > 1.0) return -1;
+  double t = dotd(e2, q) * inv;
+  return t > T_MIN ? t : -1;
+}
+
+// point scatterer: event at the closest approach t = (p - o).w, if within r_s of the centre
+double scat_hit(const Scene& s, int j, const D3& o, const D3& w) {
+  D3 d = subd(s.sp[j], o);
+  double t = dotd(d, w);
+  if (!(t > T_MIN)) return -1;
+  D3 q = d3(o.x + t * w.x - s.sp[j].x, o.y + t * w.y - s.sp[j].y, o.z + t * w.z - s.sp[j].z);
+  return dotd(q, q) <= s.rs * s.rs ? t : -1;
+}
+
+// slab test of a ray against a box, interval [t0, t1] clipped to [0, tmax]
+bool box_hit(const BNode& n, const D3& o, const D3& w, double tmax) {
+  double t0 = 0.0, t1 = tmax;
+  double oo[3] = {o.x, o.y, o.z}, ww[3] = {w.x, w.y, w.z};
+  for (int a = 0; a < 3; ++a) {
+    if (ww[a] == 0.0) {
+      if (oo[a] < n.lo[a] || oo[a] > n.hi[a]) return false;
+      continue;
+    }
+    double ta = (n.lo[a] - oo[a]) / ww[a], tb = (n.hi[a] - oo[a]) / ww[a];
+    if (ta > tb) std::swap(ta, tb);
+    t0 = std::max(t0, ta);
+    t1 = std::min(t1, tb);
+    if (t0 > t1) return false;
+  }
+  return true;
+}
+
+void test_prim(const Scene& s, int p, const D3& o, const D3& w, int xcls, int xid, Hit& best) {
+  Hit h;
+  if (p < s.nt) {
+    if (xcls == CLS_TRI && xid == p) return;
+    h.t = tri_hit(s, p, o, w);
+    h.cls = CLS_TRI;
+    h.id = p;
+  } else {
+    int j = p - s.nt;
+    if (xcls == CLS_SCAT && xid == j) return;
+    h.t = scat_hit(s, j, o, w);
+    h.cls = CLS_SCAT;
+    h.id = j;
+  }
+  if (h.t > 0 && hit_before(h, best)) best = h;
+}
+
+// closest hit over triangles and scatterers (transducer handled by the caller), excluding
+// the primitive (xcls, xid) the ray leaves from.  [Sec. 2.3.2]
+void closest_scene(const Scene& s, const D3& o, const D3& w, int xcls, int xid, Hit& best) {
+  if (!s.use_bvh) {
+    for (int p = 0; p < s.nt + s.nsct; ++p) test_prim(s, p, o, w, xcls, xid, best);
+    return;
+  }
+  if (s.nodes.empty()) return;
+  int stack[128];
+  int sp = 0;
+  stack[sp++] = 0;
+  while (sp) {
+    const BNode& n = s.nodes[stack[--sp]];
+    if (!box_hit(n, o, w, best.t)) continue;
+    if (n.left < 0) {
+      for (int i = n.first; i < n.first + n.count; ++i) test_prim(s, s.order[i], o, w, xcls, xid, best);
+    } else {
+      stack[sp++] = n.left;
+      stack[sp++] = n.right;
+    }
+  }
+}
+
+// all triangle crossings of the segment o + t w, 0 < t < tmax (secondary rays) [Sec. 2.3.3]
+void all_crossings(const Scene& s, const D3& o, const D3& w, double tmax, std::vector<std::pair<double, int>>& out) {
+  out.clear();
+  if (!s.use_bvh) {
+    for (int i = 0; i < s.nt; ++i) {
+      double t = tri_hit(s, i, o, w);
+      if (t > 0 && t < tmax) out.push_back(std::make_pair(t, i));  // tri_hit already has t > T_MIN
+    }
+  } else if (!s.nodes.empty()) {
+    int stack[128];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+      const BNode& n = s.nodes[stack[--sp]];
+      if (!box_hit(n, o, w, tmax)) continue;
+      if (n.left < 0) {
+        for (int i = n.first; i < n.first + n.count; ++i) {
+          int p = s.order[i];
+          if (p >= s.nt) continue;
+          double t = tri_hit(s, p, o, w);
+          if (t > 0 && t < tmax) out.push_back(std::make_pair(t, p));
+        }
+      } else {
+        stack[sp++] = n.left;
+        stack[sp++] = n.right;
+      }
+    }
+  }
+  std::sort(out.begin(), out.end());
+}
+
+// ------------------------------------------------------------------------------------------
+// Physics parameters in scalar type S
+// ------------------------------------------------------------------------------------------
+template <class S>
+struct Phys {
+  int M;
+  std::vector<S> c, rho, al;
+  S As, f0;
+};
+
+Phys<double> phys_double(const double* th, int M) {
+  Phys<double> p;
+  p.M = M;
+  for (int m = 0; m < M; ++m) {
+    p.c.push_back(th[3 * m]);
+    p.rho.push_back(th[3 * m + 1]);
+    p.al.push_back(th[3 * m + 2]);
+  }
+  p.As = th[3 * M];
+  p.f0 = th[3 * M + 1];
+  return p;
+}
+
+Phys<Dual> phys_dual(const double* th, int M) {
+  Phys<Dual> p;
+  p.M = M;
+  for (int m = 0; m < M; ++m) {
+    Dual c(th[3 * m]), r(th[3 * m + 1]), a(th[3 * m + 2]);
+    c.d[3 * m] = 1;
+    r.d[3 * m + 1] = 1;
+    a.d[3 * m + 2] = 1;
+    p.c.push_back(c);
+    p.rho.push_back(r);
+    p.al.push_back(a);
+  }
+  Dual as(th[3 * M]), f(th[3 * M + 1]);
+  as.d[3 * M] = 1;
+  f.d[3 * M + 1] = 1;
+  p.As = as;
+  p.f0 = f;
+  return p;
+}
+
+// receive directivity, Eq. cutoff (trapezoid in the angle to the element normal)
+template <class S>
+S f_rx(const S& theta, double am, double ac) {
+  double th = val(theta);
+  if (th <= am) return S(1.0);
+  if (th > ac) return S(0.0);
+  return (ac - theta) / (ac - am);
+}
+
+// ------------------------------------------------------------------------------------------
+// Per-path record of discrete decisions (frozen for replay / differentiation)
+// ------------------------------------------------------------------------------------------
+enum { CH_NONE = 0, CH_REFLECT = 1, CH_TRANSMIT = 2, CH_TIR = 3 };
+
+struct Rec {  // one per segment
+  int cls, id;   // primitive hit (CLS_NONE = escape)
+  int choice;    // interface decision, or CH_NONE
+  int aux;       // NEE element (scatterer events) / receiving element (transducer)
+};
+
+template <class S>
+struct Arrival {
+  int tx, e, kind, ev;  // kind 0 = transducer hit, 1 = secondary (NEE) ray; ev = segment index
+  long long path;
+  S tau, a;
+};
+
+struct Counters {
+  long long segments = 0, nee = 0;
+};
+
+// ------------------------------------------------------------------------------------------
+// Interface event [Sec. 2.3.2]: incident unit direction w, unit normal nin pointing back into
+// the incident medium 1.  Specular reflection w_r = w + 2 cos(theta_i) nin; Snell's law with
+// sound speeds sin(theta_t) / c2 = sin(theta_i) / c1 (the impedance ratio Z1/Z2 the paper
+// defines is not a refractive index); total internal reflection when sin(theta_t) >= 1.
+// Pressure coefficients (reading of the printed Fresnel form, which at normal incidence gives
+// the opposite sign to (Z2 - Z1)/(Z2 + Z1)):
+//   R = (Z2 cos_i - Z1 cos_t) / (Z2 cos_i + Z1 cos_t),   T = 2 Z2 cos_i / (Z2 cos_i + Z1 cos_t).
+// clamp_ct forces cos_t = 0 (a frozen transmit/reflect branch replayed past the critical angle).
+// ------------------------------------------------------------------------------------------
+template <class S>
+struct Iface {
+  bool tir;
+  S ci, ct, r, R, T;
+  V3<S> wr, wt;
+};
+
+template <class S>
+Iface<S> interface_event(const V3<S>& w, const V3<S>& nin, const S& c1, const S& c2, const S& rho1,
+                         const S& rho2, bool clamp_ct = false) {
+  Iface<S> f;
+  f.ci = -dot(w, nin);
+  f.r = c2 / c1;
+  S si2 = 1.0 - f.ci * f.ci;
+  if (val(si2) < 0) si2 = S(0.0);
+  S st2 = f.r * f.r * si2;
+  f.tir = val(st2) >= 1.0;
+  f.wr = add(w, scale(nin, 2.0 * f.ci));
+  if (f.tir && !clamp_ct) {
+    f.ct = S(0.0);
+    f.R = S(1.0);
+    f.T = S(0.0);
+    f.wt = f.wr;
+    return f;
+  }
+  f.ct = clamp_ct ? S(0.0) : sqrt(1.0 - st2);
+  S A = rho2 * c2 * f.ci, B = rho1 * c1 * f.ct;
+  f.R = (A - B) / (A + B);
+  f.T = 2.0 * A / (A + B);
+  f.wt = add(scale(w, f.r), scale(nin, f.r * f.ci - f.ct));
+  return f;
+}
+
+// ------------------------------------------------------------------------------------------
+// Secondary (receiver-directed) ray from a scatterer centre to the chosen element centre
+// [Sec. 2.3.3]: straight segment, transmission coefficient at every crossed interface (zero
+// under total internal reflection), attenuation and travel time per sub-segment in the medium
+// tracked across the crossings, receive directivity at the element.
+// ------------------------------------------------------------------------------------------
+template <class S>
+bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, int m_start, S& gain, S& dt,
+                std::vector<std::pair<double, int>>& xs, double* frx_out) {
+  D3 p = sc.sp[j];
+  D3 tgt = d3(q.elem_x(e2), 0.0, 0.0);
+  D3 dv = subd(tgt, p);
+  double D = std::sqrt(dotd(dv, dv));
+  D3 d = d3(dv.x / D, dv.y / D, dv.z / D);
+  double frx = val(f_rx<double>(std::acos(std::max(-1.0, std::min(1.0, -d.z))), q.alpha_m, q.alpha_c));
+  *frx_out = frx;
+  if (frx == 0.0) return false;
+  all_crossings(sc, p, d, D, xs);
+  S prodT(1.0), path_alpha(0.0);
+  S time(0.0);
+  int m = m_start;
+  double tprev = 0.0;
+  for (size_t i = 0; i < xs.size(); ++i) {
+    double t = xs[i].first;
+    int tri = xs[i].second;
+    double l = t - tprev;
+    path_alpha = path_alpha + P.al[m] * l;
+    time = time + l / P.c[m];
+    D3 n = cross(subd(sc.v1[tri], sc.v0[tri]), subd(sc.v2[tri], sc.v0[tri]));
+    double nl = std::sqrt(dotd(n, n));
+    n = d3(n.x / nl, n.y / nl, n.z / nl);
+    double dn = dotd(d, n);
+    int m1 = dn < 0 ? sc.mfront[tri] : sc.mback[tri];
+    int m2 = dn < 0 ? sc.mback[tri] : sc.mfront[tri];
+    V3<S> ws = mk3<S>(S(d.x), S(d.y), S(d.z));
+    V3<S> nin = dn < 0 ? mk3<S>(S(n.x), S(n.y), S(n.z)) : mk3<S>(S(-n.x), S(-n.y), S(-n.z));
+    Iface<S> f = interface_event<S>(ws, nin, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
+    if (f.tir) return false;  // total internal reflection: no transmitted pressure
+    prodT = prodT * f.T;
+    m = m2;
+    tprev = t;
+  }
+  double l = D - tprev;
+  path_alpha = path_alpha + P.al[m] * l;
+  time = time + l / P.c[m];
+  gain = prodT * exp(-KAPPA * P.f0 * path_alpha) * frx * (double)q.ne;
+  dt = time;
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------
+// One path.  FORWARD (S = double, rec_in == nullptr): closest-hit search, decisions drawn from
+// Philox and written to rec_out.  REPLAY (rec_in != nullptr): the primitive sequence and
+// decisions are read from rec_in; hit distances are re-solved on the frozen primitive (its
+// plane, the closest approach to the scatterer centre, or the transducer plane), so the result
+// is the smooth function of theta that fixed-sample differentiation differentiates
+// [Sec. 3.2, Eq. chain_rule].
+// Emission [Sec. 2.3.1, Eq. directivity, Eq. pressure_mc]: origin uniform on the element face,
+// direction cosine-weighted, so f_d / p = pi; weight pi / N_r; transmit delay as a time stamp.
+// Interface [Sec. 2.3.2]: specular reflection, Snell refraction with sound speeds, Fresnel
+// pressure coefficients R, T = 1 + R; split probability P_r = R^2 (or a fixed q), weight
+// amplitude / selection probability.  Attenuation per segment (exp(-kappa alpha f0 L)).
+// ------------------------------------------------------------------------------------------
+struct PathIO {
+  // injected emission (tests); when inject is false the emission is sampled from Philox
+  bool inject = false;
+  D3 o0, w0;
+  double a0 = 0, tau0 = 0;
+  int tx = 0;
+  long long ray = 0;
+  // forced interface choices (tests); nullptr = from Philox
+  const int* forced = nullptr;
+  int n_forced = 0;
+  bool physical = false;  // weight interface by R or T instead of amplitude / probability
+  double* last_state = nullptr;  // tests: position and direction at the last hit (6 doubles)
+};
+
+template <class S>
+void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, uint32_t k1, const PathIO& io,
+                long long path, const Rec* rec_in, Rec* rec_out, std::vector<Arrival<S>>& arr, Counters& cnt) {
+  const bool replay = rec_in != nullptr;
+  const uint32_t ray32 = (uint32_t)io.ray;
+  D3 o0, w0;
+  double a0, tau0;
+  if (io.inject) {
+    o0 = io.o0;
+    w0 = io.w0;
+    a0 = io.a0;
+    tau0 = io.tau0;
+  } else {
+    U4 u = philox(ray32, (uint32_t)io.tx, q.stream, 0u, k0, k1);
+    int e = (int)(io.ray / q.nr);
+    double xe = q.elem_x(e);
+    double u0 = u01(u.v[0]), u1 = u01(u.v[1]), u2 = u01(u.v[2]), u3 = u01(u.v[3]);
+    o0 = d3(xe + (u0 - 0.5) * q.pitch, (u1 - 0.5) * q.hel, 0.0);
+    double r = std::sqrt(u2), ph = 2.0 * PI * u3;
+    w0 = d3(r * std::cos(ph), r * std::sin(ph), std::sqrt(1.0 - u2));
+    a0 = PI / q.nr;
+    double st = std::sin(q.angles[io.tx]);
+    tau0 = (xe * st + 0.5 * q.aperture() * std::fabs(st)) / q.cbf;
+  }
+  V3<S> o = mk3<S>(S(o0.x), S(o0.y), S(o0.z));
+  V3<S> w = mk3<S>(S(w0.x), S(w0.y), S(w0.z));
+  S a(a0), tau(tau0);
+  int m = 0;
+  int xcls = CLS_NONE, xid = -1;
+  std::vector<std::pair<double, int>> xs;
+  for (int k = 0; k <= q.kmax; ++k) {
+    Hit h;
+    if (!replay) {
+      cnt.segments++;
+      D3 od = d3(val(o.x), val(o.y), val(o.z)), wd = d3(val(w.x), val(w.y), val(w.z));
+      h.t = 1e300;
+      h.cls = CLS_NONE;
+      h.id = -1;
+      if (wd.z < 0.0) {  // transducer face z = 0, |x| <= N_e p / 2, |y| <= h_el / 2
+        double t = -od.z / wd.z;
+        double x = od.x + t * wd.x, y = od.y + t * wd.y;
+        if (t > T_MIN && std::fabs(x) <= 0.5 * q.ne * q.pitch && std::fabs(y) <= 0.5 * q.hel) {
+          h.t = t;
+          h.cls = CLS_XDCR;
+          h.id = std::min(q.ne - 1, std::max(0, (int)std::floor((x + 0.5 * q.ne * q.pitch) / q.pitch)));
+        }
+      }
+      closest_scene(sc, od, wd, xcls, xid, h);
+      if (rec_out) {
+        rec_out[k].cls = h.cls;
+        rec_out[k].id = h.id;
+        rec_out[k].choice = CH_NONE;
+        rec_out[k].aux = h.cls == CLS_XDCR ? h.id : -1;
+      }
+    } else {
+      h.cls = rec_in[k].cls;
+      h.id = rec_in[k].id;
+      h.t = 0;
+    }
+    if (h.cls == CLS_NONE) break;  // escape
+    // hit distance on the frozen primitive
+    S t;
+    if (!replay) {
+      t = S(h.t);
+    } else if (h.cls == CLS_XDCR) {
+      t = -o.z / w.z;
+    } else if (h.cls == CLS_TRI) {
+      D3 N = cross(subd(sc.v1[h.id], sc.v0[h.id]), subd(sc.v2[h.id], sc.v0[h.id]));
+      t = dot(sub(mk3<S>(S(sc.v0[h.id].x), S(sc.v0[h.id].y), S(sc.v0[h.id].z)), o), N) / dot(w, N);
+    } else {
+      V3<S> d = sub(mk3<S>(S(sc.sp[h.id].x), S(sc.sp[h.id].y), S(sc.sp[h.id].z)), o);
+      t = dot(d, w);
+    }
+    a = a * exp(-KAPPA * P.al[m] * P.f0 * t);
+    tau = tau + t / P.c[m];
+    V3<S> x = add(o, scale(w, t));
+    if (io.last_state) {
+      double st[6] = {val(x.x), val(x.y), val(x.z), val(w.x), val(w.y), val(w.z)};
+      std::memcpy(io.last_state, st, sizeof st);
+    }
+    if (h.cls == CLS_XDCR) {  // arrival at the receiving element [Sec. 2.3.4]
+      S cosd = -w.z;
+      double cv = std::max(-1.0, std::min(1.0, val(cosd)));
+      S th = (cv == val(cosd)) ? acos(cosd) : S(std::acos(cv));
+      S f = f_rx<S>(th, q.alpha_m, q.alpha_c);
+      int e = replay ? rec_in[k].aux : h.id;
+      if (val(f) != 0.0) {
+        Arrival<S> A;
+        A.tx = io.tx;
+        A.e = e;
+        A.kind = 0;
+        A.ev = k;
+        A.path = path;
+        A.tau = tau;
+        A.a = a * f;
+        arr.push_back(A);
+      }
+      break;
+    }
+    if (k == q.kmax) {  // interaction budget spent
+      break;
+    }
+    U4 u = philox(ray32, (uint32_t)io.tx, q.stream, (uint32_t)(k + 1), k0, k1);
+    if (h.cls == CLS_TRI) {
+      D3 N = cross(subd(sc.v1[h.id], sc.v0[h.id]), subd(sc.v2[h.id], sc.v0[h.id]));
+      double nl = std::sqrt(dotd(N, N));
+      D3 n = d3(N.x / nl, N.y / nl, N.z / nl);
+      double wn = val(w.x) * n.x + val(w.y) * n.y + val(w.z) * n.z;
+      bool front = wn < 0;  // arriving from the side the normal points to
+      D3 nin = front ? n : d3(-n.x, -n.y, -n.z);  // unit normal pointing back into medium 1
+      int m1 = front ? sc.mfront[h.id] : sc.mback[h.id];
+      int m2 = front ? sc.mback[h.id] : sc.mfront[h.id];
+      V3<S> nn = mk3<S>(S(nin.x), S(nin.y), S(nin.z));
+      Iface<S> f = interface_event<S>(w, nn, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
+      int choice;
+      if (replay) {
+        choice = rec_in[k].choice;
+        if (choice != CH_TIR && f.tir) f = interface_event<S>(w, nn, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2], true);
+      } else if (f.tir) {
+        choice = CH_TIR;
+      } else {
+        double pr = q.split_mode == 0 ? val(f.R) * val(f.R) : q.split_q;
+        double u0 = u01(u.v[0]);
+        if (io.forced && k < io.n_forced) choice = io.forced[k];
+        else choice = u0 < pr ? CH_REFLECT : CH_TRANSMIT;
+      }
+      if (rec_out) rec_out[k].choice = choice;
+      S pr = q.split_mode == 0 ? f.R * f.R : S(q.split_q);
+      if (choice == CH_TIR) {
+        w = f.wr;
+        m = m1;
+      } else if (choice == CH_REFLECT) {
+        a = io.physical ? a * f.R : a * f.R / pr;
+        w = f.wr;
+        m = m1;
+      } else {
+        a = io.physical ? a * f.T : a * f.T / (1.0 - pr);
+        w = f.wt;
+        m = m2;
+      }
+      o = x;
+      xcls = CLS_TRI;
+      xid = h.id;
+    } else {  // scatterer: secondary ray to a uniformly chosen element, Born pass-through
+      int e2 = replay ? rec_in[k].aux : std::min(q.ne - 1, (int)std::floor(u01(u.v[1]) * q.ne));
+      if (rec_out) rec_out[k].aux = e2;
+      if (!replay) cnt.nee++;
+      S gain, dt;
+      double frx;
+      if (nee_weight<S>(sc, P, q, h.id, e2, m, gain, dt, xs, &frx)) {
+        Arrival<S> A;
+        A.tx = io.tx;
+        A.e = e2;
+        A.kind = 1;
+        A.ev = k;
+        A.path = path;
+        A.tau = tau + dt;
+        A.a = a * P.As * sc.samp[h.id] * gain;
+        arr.push_back(A);
+      }
+      o = x;
+      xcls = CLS_SCAT;
+      xid = h.id;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Axial pulse, Eq. axial_sig: s(t) = sin(2 pi f0 t) exp(-t^2 / sigma).  Reading of the
+// bandwidth: -6 dB fractional bandwidth bw, i.e. the Gaussian envelope's spectrum falls to one
+// half at f0 +- bw f0 / 2, which gives sigma = 4 ln 2 / (pi^2 (bw f0)^2).  Support |t| <= 4 sqrt(sigma).
+// ------------------------------------------------------------------------------------------
+template <class S>
+S pulse_sigma(const S& f0, double bw) {
+  return 4.0 * std::log(2.0) / (PI * PI * bw * bw) / (f0 * f0);
+}
+template <class S>
+S pulse(const S& t, const S& f0, const S& sigma) {
+  return sin(2.0 * PI * f0 * t) * exp(-(t * t) / sigma);
+}
+// sample window [n0, n1] of an arrival at tau
+void pulse_window(double tau, double sigma, const Acq& q, int& n0, int& n1) {
+  double half = 4.0 * std::sqrt(sigma);
+  n0 = std::max(0, (int)std::ceil((tau - half) * q.fs));
+  n1 = std::min(q.ns - 1, (int)std::floor((tau + half) * q.fs));
+}
+
+// ------------------------------------------------------------------------------------------
+// Runs over all paths of an acquisition (std::thread over contiguous blocks of paths; every
+// block writes its own arrival list, concatenated in path order: deterministic).
+// ------------------------------------------------------------------------------------------
+struct Run {
+  Acq q;
+  int M = 0;
+  long long path_lo = 0;  // first path index of the run
+  long long n_paths = 0;
+  int K1 = 0;
+  std::vector<Rec> rec;  // n_paths * K1
+  std::vector<Arrival<double>> arr;
+  Counters cnt;
+};
+
+template <class F>
+void parallel_blocks(long long n, int nthreads, F f) {
+  if (nthreads <= 1 || n < 2) {
+    f(0, 0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int b = 0; b < nthreads; ++b) {
+    long long lo = n * b / nthreads, hi = n * (b + 1) / nthreads;
+    th.emplace_back([=]() { f(b, lo, hi); });
+  }
+  for (auto& t : th) t.join();
+}
+
+PathIO path_io(const Acq& q, long long path) {
+  PathIO io;
+  long long rpt = q.rays_per_tx();
+  io.tx = (int)(path / rpt);
+  long long local = path % rpt;
+  io.ray = q.tx_elem < 0 ? local : (long long)q.tx_elem * q.nr + local;
+  return io;
+}
+
+void forward_run(const Scene& sc, const double* th, Run& run, uint64_t seed, int nthreads,
+                 long long path_lo, long long path_hi) {
+  const Acq& q = run.q;
+  Phys<double> P = phys_double(th, run.M);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  long long n = path_hi - path_lo;
+  std::vector<std::vector<Arrival<double>>> parts(std::max(1, nthreads));
+  std::vector<Counters> cnts(std::max(1, nthreads));
+  parallel_blocks(n, nthreads, [&](int b, long long lo, long long hi) {
+    for (long long i = lo; i < hi; ++i) {
+      long long p = path_lo + i;
+      PathIO io = path_io(q, p);
+      Rec* ro = &run.rec[(size_t)i * run.K1];
+      for (int k = 0; k < run.K1; ++k) ro[k].cls = CLS_NONE, ro[k].id = -1, ro[k].choice = CH_NONE, ro[k].aux = -1;
+      trace_path<double>(sc, P, q, k0, k1, io, p, nullptr, ro, parts[b], cnts[b]);
+    }
+  });
+  for (size_t b = 0; b < parts.size(); ++b) {
+    run.arr.insert(run.arr.end(), parts[b].begin(), parts[b].end());
+    run.cnt.segments += cnts[b].segments;
+    run.cnt.nee += cnts[b].nee;
+  }
+}
+
+// Splat [Sec. 2.3.4]: RF[tx][e][n] += a s(n / fs - tau), summed in arrival (path) order.
+void splat_direct(const Acq& q, double f0, const Arrival<double>* arr, long long n, double* rf) {
+  double sig = pulse_sigma<double>(f0, q.bw);
+  for (long long i = 0; i < n; ++i) {
+    const Arrival<double>& A = arr[i];
+    int n0, n1;
+    pulse_window(A.tau, sig, q, n0, n1);
+    double* row = rf + ((size_t)A.tx * q.ne + A.e) * q.ns;
+    for (int s = n0; s <= n1; ++s) row[s] += A.a * pulse<double>(s / q.fs - A.tau, f0, sig);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Image formation
+// ------------------------------------------------------------------------------------------
+double hann(int e, int ne) { return 0.5 * (1.0 - std::cos(2.0 * PI * (e + 1) / (ne + 1))); }
+
+// two-way plane-wave delay in samples for pixel (x, z), element e, steering angle th  [Eq. das]
+double das_delay_samples(const Acq& q, double x, double z, int e, double th) {
+  double st = std::sin(th), ct = std::cos(th);
+  double ttx = (x * st + z * ct + 0.5 * q.aperture() * std::fabs(st)) / q.cbf;
+  double dx = x - q.elem_x(e);
+  double trx = std::sqrt(dx * dx + z * z) / q.cbf;
+  return (ttx + trx) * q.fs;
+}
+
+// Eq. das: I_rf(x,z) = sum_tx sum_e w_e P(e, tau_e(x,z)), P read by linear interpolation,
+// samples outside [0, N_s - 1] count as zero; transmits compounded coherently.
+void das(const Acq& q, const Img& im, const double* rf, double* irf) {
+  for (int l = 0; l < im.nl; ++l)
+    for (int d = 0; d < im.nd; ++d) {
+      double x = line_x(im, l), z = depth_z(im, d), acc = 0;
+      for (int tx = 0; tx < q.ntx; ++tx)
+        for (int e = 0; e < q.ne; ++e) {
+          double u = das_delay_samples(q, x, z, e, q.angles[tx]);
+          double fl = std::floor(u);
+          long long i = (long long)fl;
+          double f = u - fl;
+          const double* row = rf + ((size_t)tx * q.ne + e) * q.ns;
+          double a = (i >= 0 && i < q.ns) ? row[i] : 0.0;
+          double b = (i + 1 >= 0 && i + 1 < q.ns) ? row[i + 1] : 0.0;
+          acc += hann(e, q.ne) * ((1.0 - f) * a + f * b);
+        }
+      irf[(size_t)l * im.nd + d] = acc;
+    }
+}
+
+// Eq. das_adjoint: scatter the image gradient back to the two interpolation samples.
+void das_adjoint(const Acq& q, const Img& im, const double* gi, double* grf) {
+  for (int l = 0; l < im.nl; ++l)
+    for (int d = 0; d < im.nd; ++d) {
+      double x = line_x(im, l), z = depth_z(im, d), g = gi[(size_t)l * im.nd + d];
+      for (int tx = 0; tx < q.ntx; ++tx)
+        for (int e = 0; e < q.ne; ++e) {
+          double u = das_delay_samples(q, x, z, e, q.angles[tx]);
+          double fl = std::floor(u);
+          long long i = (long long)fl;
+          double f = u - fl;
+          double* row = grf + ((size_t)tx * q.ne + e) * q.ns;
+          double w = hann(e, q.ne);
+          if (i >= 0 && i < q.ns) row[i] += w * (1.0 - f) * g;
+          if (i + 1 >= 0 && i + 1 < q.ns) row[i + 1] += w * f * g;
+        }
+    }
+}
+
+// discrete Fourier transform, sign -1 forward / +1 inverse (unnormalised).  Radix-2
+// Cooley-Tukey for powers of two, the O(N^2) definition otherwise.
+void dft(std::vector<double>& re, std::vector<double>& im, int sign) {
+  size_t n = re.size();
+  if (n && (n & (n - 1)) == 0) {
+    for (size_t i = 1, j = 0; i < n; ++i) {  // bit reversal
+      size_t bit = n >> 1;
+      for (; j & bit; bit >>= 1) j ^= bit;
+      j ^= bit;
+      if (i < j) {
+        std::swap(re[i], re[j]);
+        std::swap(im[i], im[j]);
+      }
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+      for (size_t i = 0; i < n; i += len)
+        for (size_t k = 0; k < len / 2; ++k) {
+          double ang = sign * 2.0 * PI * (double)k / (double)len;
+          double wr = std::cos(ang), wi = std::sin(ang);
+          size_t a = i + k, b = i + k + len / 2;
+          double xr = re[b] * wr - im[b] * wi, xi = re[b] * wi + im[b] * wr;
+          re[b] = re[a] - xr;
+          im[b] = im[a] - xi;
+          re[a] += xr;
+          im[a] += xi;
+        }
+    }
+    return;
+  }
+  std::vector<double> r2(n), i2(n);
+  for (size_t k = 0; k < n; ++k) {
+    double sr = 0, si = 0;
+    for (size_t j = 0; j < n; ++j) {
+      double ang = sign * 2.0 * PI * (double)((k * j) % n) / (double)n;
+      sr += re[j] * std::cos(ang) - im[j] * std::sin(ang);
+      si += re[j] * std::sin(ang) + im[j] * std::cos(ang);
+    }
+    r2[k] = sr;
+    i2[k] = si;
+  }
+  re = r2;
+  im = i2;
+}
+
+// Hilbert transform of a real line via the analytic signal: X = DFT(x), multiply by
+// h = [1, 2 ... 2, (1 at N/2 for even N), 0 ...], inverse DFT; returns Im(analytic) in y.
+void hilbert(const double* x, int n, double* y) {
+  std::vector<double> re(x, x + n), im(n, 0.0);
+  dft(re, im, -1);
+  for (int k = 0; k < n; ++k) {
+    double h;
+    if (k == 0) h = 1;
+    else if (2 * k < n) h = 2;
+    else if (2 * k == n) h = 1;
+    else h = 0;
+    re[k] *= h;
+    im[k] *= h;
+  }
+  dft(re, im, +1);
+  for (int k = 0; k < n; ++k) y[k] = im[k] / n;
+}
+
+// envelope |x + i H(x)| per line along depth ("demodulation to baseband", Sec. 2.3.4)
+void envelope(const Img& im, const double* irf, double* env) {
+  std::vector<double> y(im.nd);
+  for (int l = 0; l < im.nl; ++l) {
+    const double* x = irf + (size_t)l * im.nd;
+    hilbert(x, im.nd, y.data());
+    for (int d = 0; d < im.nd; ++d) env[(size_t)l * im.nd + d] = std::sqrt(x[d] * x[d] + y[d] * y[d]);
+  }
+}
+
+// log compression with dynamic-range limit: B = max(20 log10(E / E_max), -DR)
+long long log_compress(const Img& im, const double* env, double* b) {
+  size_t n = (size_t)im.nl * im.nd;
+  long long am = 0;
+  for (size_t i = 1; i < n; ++i)
+    if (env[i] > env[am]) am = (long long)i;
+  double emax = n ? env[am] : 0.0;
+  for (size_t i = 0; i < n; ++i) {
+    double v = -im.dr;
+    if (emax > 0 && env[i] > 0) v = std::max(20.0 * std::log10(env[i] / emax), -im.dr);
+    b[i] = v;
+  }
+  return am;
+}
+
+// Eq. weighted_l1_l2_loss and its exact gradient (sign(0) = 0)
+double loss_grad(const Img& im, const double* b, const double* bref, double* gb) {
+  size_t n = (size_t)im.nl * im.nd;
+  double s1 = 0, s2 = 0;
+  for (size_t i = 0; i < n; ++i) {
+    double r = b[i] - bref[i];
+    s1 += std::fabs(r);
+    s2 += r * r;
+    if (gb) gb[i] = (im.l1 * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) + 2.0 * im.l2 * r) / (double)n;
+  }
+  return (im.l1 * s1 + im.l2 * s2) / (double)n;
+}
+
+// VJP of B(irf): log (20/ln10 / E on unclipped pixels, E_max's share to the first argmax),
+// then the envelope E = |x + i H x|: g_x = (x/E) g_E + H^T((y/E) g_E), with H^T = -H.
+void envlog_vjp(const Img& im, const double* irf, const double* gb, double* gi) {
+  size_t n = (size_t)im.nl * im.nd;
+  std::vector<double> env(n), b(n), y(n), ge(n, 0.0);
+  for (int l = 0; l < im.nl; ++l) hilbert(irf + (size_t)l * im.nd, im.nd, &y[(size_t)l * im.nd]);
+  for (size_t i = 0; i < n; ++i) env[i] = std::sqrt(irf[i] * irf[i] + y[i] * y[i]);
+  long long am = log_compress(im, env.data(), b.data());
+  double emax = env[am];
+  const double c = 20.0 / std::log(10.0);
+  double smax = 0;
+  for (size_t i = 0; i < n; ++i) {
+    bool live = emax > 0 && env[i] > 0 && 20.0 * std::log10(env[i] / emax) > -im.dr;
+    if (!live) continue;
+    ge[i] += gb[i] * c / env[i];
+    smax += gb[i] * c / emax;
+  }
+  ge[am] -= smax;
+  std::vector<double> v(im.nd), hv(im.nd);
+  for (int l = 0; l < im.nl; ++l) {
+    size_t o = (size_t)l * im.nd;
+    for (int d = 0; d < im.nd; ++d) {
+      double e = env[o + d];
+      v[d] = e > 0 ? y[o + d] / e * ge[o + d] : 0.0;
+    }
+    hilbert(v.data(), im.nd, hv.data());
+    for (int d = 0; d < im.nd; ++d) {
+      double e = env[o + d];
+      gi[o + d] = (e > 0 ? irf[o + d] / e * ge[o + d] : 0.0) - hv[d];
+    }
+  }
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI used by oracle/oracle.py (ctypes)
+// ==========================================================================================
+extern "C" {
+
+void ora_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, uint32_t* out) {
+  U4 r = philox(c0, c1, c2, c3, k0, k1);
+  for (int i = 0; i < 4; ++i) out[i] = r.v[i];
+}
+
+// n blocks with counters (c0_base + i, c1, c2, c3); out[4 i + j]
+void ora_philox_fill(uint32_t c0_base, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, long long n,
+                     uint32_t* out) {
+  for (long long i = 0; i < n; ++i) {
+    U4 r = philox(c0_base + (uint32_t)i, c1, c2, c3, k0, k1);
+    for (int j = 0; j < 4; ++j) out[4 * i + j] = r.v[j];
+  }
+}
+
+void* ora_scene_create(int nt, const double* tri, const int* media, int ns, const double* sp, const double* samp,
+                       double rs, int use_bvh) {
+  Scene* s = new Scene();
+  s->nt = nt;
+  for (int i = 0; i < nt; ++i) {
+    const double* t = tri + 9 * (size_t)i;
+    s->v0.push_back(d3(t[0], t[1], t[2]));
+    s->v1.push_back(d3(t[3], t[4], t[5]));
+    s->v2.push_back(d3(t[6], t[7], t[8]));
+    s->mfront.push_back(media[2 * i]);
+    s->mback.push_back(media[2 * i + 1]);
+  }
+  s->nsct = ns;
+  for (int j = 0; j < ns; ++j) {
+    s->sp.push_back(d3(sp[3 * j], sp[3 * j + 1], sp[3 * j + 2]));
+    s->samp.push_back(samp[j]);
+  }
+  s->rs = rs;
+  if (use_bvh) s->build_bvh();
+  return s;
+}
+
+void ora_scene_free(void* s) { delete (Scene*)s; }
+
+// interface event (tests): out = {tir, cos_i, cos_t, R, T, wr[3], wt[3]}
+void ora_interface(const double* w, const double* nin, double c1, double c2, double rho1, double rho2, double* out) {
+  Iface<double> f = interface_event<double>(d3(w[0], w[1], w[2]), d3(nin[0], nin[1], nin[2]), c1, c2, rho1, rho2);
+  out[0] = f.tir;
+  out[1] = f.ci;
+  out[2] = f.ct;
+  out[3] = f.R;
+  out[4] = f.T;
+  out[5] = f.wr.x; out[6] = f.wr.y; out[7] = f.wr.z;
+  out[8] = f.wt.x; out[9] = f.wt.y; out[10] = f.wt.z;
+}
+
+// closest hit (tests): out = {t, cls, id}
+void ora_closest(void* sp, const double* o, const double* w, int xcls, int xid, double* out) {
+  const Scene& s = *(Scene*)sp;
+  Hit h;
+  h.t = 1e300;
+  h.cls = CLS_NONE;
+  h.id = -1;
+  closest_scene(s, d3(o[0], o[1], o[2]), d3(w[0], w[1], w[2]), xcls, xid, h);
+  out[0] = h.cls == CLS_NONE ? -1 : h.t;
+  out[1] = h.cls;
+  out[2] = h.id;
+}
+
+// forward transport over paths [path_lo, path_hi) of the acquisition
+void* ora_trace(void* scene, const double* theta, int M, const double* acq, const double* angles, uint64_t seed,
+                int nthreads, long long path_lo, long long path_hi) {
+  Run* r = new Run();
+  r->q = make_acq(acq, angles);
+  r->M = M;
+  if (path_hi < 0) path_hi = r->q.n_paths();
+  r->path_lo = path_lo;
+  r->n_paths = path_hi - path_lo;
+  r->K1 = r->q.kmax + 1;
+  r->rec.resize((size_t)r->n_paths * r->K1);
+  forward_run(*(Scene*)scene, theta, *r, seed, nthreads, path_lo, path_hi);
+  return r;
+}
+
+void ora_run_free(void* r) { delete (Run*)r; }
+long long ora_run_n_arrivals(void* r) { return (long long)((Run*)r)->arr.size(); }
+void ora_run_counters(void* r, long long* out) {
+  out[0] = ((Run*)r)->cnt.segments;
+  out[1] = ((Run*)r)->cnt.nee;
+}
+void ora_run_arrivals(void* rp, int* tx, int* e, double* tau, double* a, long long* path, int* kind, int* ev) {
+  Run* r = (Run*)rp;
+  for (size_t i = 0; i < r->arr.size(); ++i) {
+    const Arrival<double>& A = r->arr[i];
+    tx[i] = A.tx;
+    e[i] = A.e;
+    tau[i] = A.tau;
+    a[i] = A.a;
+    path[i] = A.path;
+    kind[i] = A.kind;
+    ev[i] = A.ev;
+  }
+}
+// per-path records: cls, id, choice, aux arrays of n_paths * (kmax + 1)
+void ora_run_records(void* rp, int* cls, int* id, int* choice, int* aux) {
+  Run* r = (Run*)rp;
+  for (size_t i = 0; i < r->rec.size(); ++i) {
+    cls[i] = r->rec[i].cls;
+    id[i] = r->rec[i].id;
+    choice[i] = r->rec[i].choice;
+    aux[i] = r->rec[i].aux;
+  }
+}
+
+// splat of the run's arrivals into rf[ntx][ne][ns] (zeroed by the caller)
+void ora_splat_run(void* rp, const double* theta, double* rf) {
+  Run* r = (Run*)rp;
+  splat_direct(r->q, theta[3 * r->M + 1], r->arr.data(), (long long)r->arr.size(), rf);
+}
+
+// splat of an explicit arrival list (stage tests)
+void ora_splat(const double* acq, const double* angles, double f0, long long n, const int* tx, const int* e,
+               const double* tau, const double* a, double* rf) {
+  Acq q = make_acq(acq, angles);
+  std::vector<Arrival<double>> arr(n);
+  for (long long i = 0; i < n; ++i) {
+    arr[i].tx = tx[i];
+    arr[i].e = e[i];
+    arr[i].tau = tau[i];
+    arr[i].a = a[i];
+  }
+  splat_direct(q, f0, arr.data(), n, rf);
+}
+
+// splat adjoint per arrival: ga = sum_n g s(t_n - tau), gt = -a sum_n g s'(t_n - tau),
+// gf = a sum_n g ds/df0 (sigma follows f0), by forward-mode duals of the pulse.
+void ora_splat_adjoint(const double* acq, const double* angles, double f0, long long n, const int* tx, const int* e,
+                       const double* tau, const double* a, const double* grf, double* ga, double* gt, double* gf) {
+  Acq q = make_acq(acq, angles);
+  double sig = pulse_sigma<double>(f0, q.bw);
+  for (long long i = 0; i < n; ++i) {
+    int n0, n1;
+    pulse_window(tau[i], sig, q, n0, n1);
+    Dual T(tau[i]), F(f0);
+    T.d[0] = 1;
+    F.d[1] = 1;
+    Dual S = pulse_sigma<Dual>(F, q.bw);
+    double sa = 0, st = 0, sf = 0;
+    const double* row = grf + ((size_t)tx[i] * q.ne + e[i]) * q.ns;
+    for (int s = n0; s <= n1; ++s) {
+      Dual p = pulse<Dual>(Dual(s / q.fs) - T, F, S);
+      sa += row[s] * p.v;
+      st += row[s] * p.d[0];
+      sf += row[s] * p.d[1];
+    }
+    ga[i] = sa;
+    gt[i] = a[i] * st;
+    gf[i] = a[i] * sf;
+  }
+}
+
+void ora_das(const double* acq, const double* angles, const double* img, const double* rf, double* irf) {
+  das(make_acq(acq, angles), make_img(img), rf, irf);
+}
+void ora_das_adjoint(const double* acq, const double* angles, const double* img, const double* gi, double* grf) {
+  das_adjoint(make_acq(acq, angles), make_img(img), gi, grf);
+}
+void ora_hilbert(const double* x, int n, double* y) { hilbert(x, n, y); }
+void ora_envelope(const double* img, const double* irf, double* env) { envelope(make_img(img), irf, env); }
+long long ora_log_compress(const double* img, const double* env, double* b) { return log_compress(make_img(img), env, b); }
+double ora_loss(const double* img, const double* b, const double* bref, double* gb) {
+  return loss_grad(make_img(img), b, bref, gb);
+}
+void ora_envlog_vjp(const double* img, const double* irf, const double* gb, double* gi) {
+  envlog_vjp(make_img(img), irf, gb, gi);
+}
+
+// replay of a run's frozen decisions at (possibly perturbed) theta -> rf (double), for
+// finite differences on the same frozen realisation
+void ora_replay_rf(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, double* rf) {
+  Run* r = (Run*)rp;
+  const Scene& sc = *(Scene*)scene;
+  const Acq& q = r->q;
+  Phys<double> P = phys_double(theta, r->M);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  std::vector<std::vector<Arrival<double>>> parts(std::max(1, nthreads));
+  std::vector<Counters> cnts(std::max(1, nthreads));
+  parallel_blocks(r->n_paths, nthreads, [&](int b, long long lo, long long hi) {
+    for (long long i = lo; i < hi; ++i) {
+      PathIO io = path_io(q, r->path_lo + i);
+      trace_path<double>(sc, P, q, k0, k1, io, r->path_lo + i, &r->rec[(size_t)i * r->K1], nullptr, parts[b],
+                         cnts[b]);
+    }
+  });
+  for (auto& p : parts) splat_direct(q, P.f0, p.data(), (long long)p.size(), rf);
+}
+
+// gradient of sum_{tx,e,n} grf[tx][e][n] * RF[tx][e][n] w.r.t. theta on the run's frozen
+// realisation (forward-mode duals through replay and the pulse; Eq. chain_rule)
+void ora_gradient(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
+                  double* gtheta) {
+  Run* r = (Run*)rp;
+  const Scene& sc = *(Scene*)scene;
+  const Acq& q = r->q;
+  Phys<Dual> P = phys_dual(theta, r->M);
+  int np = 3 * r->M + 2;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  int nb = std::max(1, nthreads);
+  std::vector<std::vector<double>> acc(nb, std::vector<double>(np, 0.0));
+  parallel_blocks(r->n_paths, nthreads, [&](int b, long long lo, long long hi) {
+    std::vector<Arrival<Dual>> arr;
+    Counters c;
+    for (long long i = lo; i < hi; ++i) {
+      arr.clear();
+      PathIO io = path_io(q, r->path_lo + i);
+      trace_path<Dual>(sc, P, q, k0, k1, io, r->path_lo + i, &r->rec[(size_t)i * r->K1], nullptr, arr, c);
+      for (const Arrival<Dual>& A : arr) {
+        Dual sig = pulse_sigma<Dual>(P.f0, q.bw);
+        int n0, n1;
+        pulse_window(A.tau.v, sig.v, q, n0, n1);
+        const double* row = grf + ((size_t)A.tx * q.ne + A.e) * q.ns;
+        Dual s(0.0);
+        for (int n = n0; n <= n1; ++n) {
+          if (row[n] == 0.0) continue;
+          s = s + row[n] * pulse<Dual>(Dual(n / q.fs) - A.tau, P.f0, sig);
+        }
+        Dual contrib = A.a * s;
+        for (int k = 0; k < np; ++k) acc[b][k] += contrib.d[k];
+      }
+    }
+  });
+  for (int k = 0; k < np; ++k) {
+    double s = 0;
+    for (int b = 0; b < nb; ++b) s += acc[b][k];
+    gtheta[k] = s;
+  }
+}
+
+// single injected path (tests): emission state given, optional forced interface choices,
+// optional physical (R / T) weights.  Returns the number of arrivals written (<= cap).
+int ora_trace_injected(void* scene, const double* theta, int M, const double* acq, const double* angles, uint64_t seed,
+                       const double* o, const double* w, double a0, double tau0, int tx, long long ray,
+                       const int* forced, int n_forced, int physical, int cap, int* e_out, double* tau_out,
+                       double* a_out, int* kind_out, int* rec_out, double* last_state) {
+  Acq q = make_acq(acq, angles);
+  Phys<double> P = phys_double(theta, M);
+  PathIO io;
+  io.inject = true;
+  io.o0 = d3(o[0], o[1], o[2]);
+  io.w0 = d3(w[0], w[1], w[2]);
+  io.a0 = a0;
+  io.tau0 = tau0;
+  io.tx = tx;
+  io.ray = ray;
+  io.forced = forced;
+  io.n_forced = n_forced;
+  io.physical = physical != 0;
+  io.last_state = last_state;
+  std::vector<Rec> rec(q.kmax + 1);
+  for (auto& x : rec) x.cls = CLS_NONE, x.id = -1, x.choice = CH_NONE, x.aux = -1;
+  std::vector<Arrival<double>> arr;
+  Counters c;
+  trace_path<double>(*(Scene*)scene, P, q, (uint32_t)seed, (uint32_t)(seed >> 32), io, 0, nullptr, rec.data(), arr, c);
+  int n = std::min(cap, (int)arr.size());
+  for (int i = 0; i < n; ++i) {
+    e_out[i] = arr[i].e;
+    tau_out[i] = arr[i].tau;
+    a_out[i] = arr[i].a;
+    kind_out[i] = arr[i].kind;
+  }
+  if (rec_out)
+    for (int k = 0; k <= q.kmax; ++k) {
+      rec_out[4 * k] = rec[k].cls;
+      rec_out[4 * k + 1] = rec[k].id;
+      rec_out[4 * k + 2] = rec[k].choice;
+      rec_out[4 * k + 3] = rec[k].aux;
+    }
+  return n;
+}
+
+}  // extern "C"

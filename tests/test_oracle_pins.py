@@ -1,0 +1,553 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix (CPU only).
+
+Each test ties one part of the oracle to something other than itself: a closed form, an
+invariant, an independent library routine, brute force, or finite differences.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2604_15017_gb300 import phantoms as P
+
+MM = 1e-3
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "planar_interface.json")))
+
+
+# ------------------------------------------------------------------------------------------
+# P1  Philox4x32-10 sample streams
+# ------------------------------------------------------------------------------------------
+TRITON_SCRIPT = r"""
+import sys, json
+import numpy as np
+import torch
+import triton
+import triton.language as tl
+
+@triton.jit
+def k(c0p, c1p, c2p, c3p, k0p, k1p, out, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(c0p + i); c1 = tl.load(c1p + i); c2 = tl.load(c2p + i); c3 = tl.load(c3p + i)
+    k0 = tl.load(k0p + i); k1 = tl.load(k1p + i)
+    a, b, c, d = tl.philox_impl(c0, c1, c2, c3, k0, k1, 10)
+    tl.store(out + 4 * i, a); tl.store(out + 4 * i + 1, b)
+    tl.store(out + 4 * i + 2, c); tl.store(out + 4 * i + 3, d)
+
+inp = np.array(json.loads(sys.stdin.read()), dtype=np.uint32)
+n = inp.shape[1]
+t = [torch.from_numpy(inp[j].copy()) for j in range(6)]
+out = torch.zeros(4 * n, dtype=torch.uint32)
+k[(1,)](*t, out, N=n)
+print(json.dumps(out.numpy().astype(np.int64).tolist()))
+"""
+
+
+def test_philox_matches_independent_triton_implementation():
+    """Triton ships its own Philox4x32-10 (run here by its CPU interpreter): bit-exact."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(11)
+    n = 64
+    inp = rng.integers(0, 2**32, size=(6, n), dtype=np.uint64)
+    inp[:, 0] = 0  # all-zero counter and key
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", TRITON_SCRIPT], input=json.dumps(inp.tolist()), env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    ref = np.array(json.loads(r.stdout.strip().splitlines()[-1]), dtype=np.uint64).reshape(n, 4)
+    got = np.stack([O.philox(inp[:4, i], inp[4:, i]) for i in range(n)]).astype(np.uint64)
+    assert np.array_equal(got, ref)
+
+
+def test_philox_statistics_and_avalanche():
+    x = O.philox_fill(0, 7, 0, 0, 1234, 5678, 200000).reshape(-1)
+    u = (x >> 8).astype(np.float64) / 2**24
+    assert abs(u.mean() - 0.5) < 0.002
+    hist = np.bincount((x >> 24).astype(np.int64), minlength=256)
+    chi2 = (((hist - len(x) / 256) ** 2) / (len(x) / 256)).sum()
+    assert chi2 < 400  # 255 dof: mean 255, sd ~22.6
+    base = O.philox([1, 2, 3, 4], [5, 6])
+    flips = []
+    for w in range(4):
+        for bit in range(0, 32, 5):
+            c = [1, 2, 3, 4]
+            c[w] ^= 1 << bit
+            d = O.philox(c, [5, 6]) ^ base
+            flips.append(sum(bin(int(v)).count("1") for v in d))
+    assert 50 < np.mean(flips) < 78  # ~64 of 128 output bits flip
+
+
+# ------------------------------------------------------------------------------------------
+# P3  interface: Snell, reflection law, Fresnel energy balance
+# ------------------------------------------------------------------------------------------
+def test_interface_normal_incidence_matches_closed_form():
+    g = GOLD
+    f = O.interface([0, 0, 1.0], [0, 0, -1.0], g["c1"], g["c2"], g["rho1"], g["rho2"])
+    assert not f["tir"]
+    assert abs(f["R"] - g["R"]) < g["tolerance_abs_printed"]
+    assert abs(f["T"] - g["T"]) < g["tolerance_abs_printed"]
+    z1, z2 = g["Z1"], g["Z2"]
+    assert abs(f["R"] - (z2 - z1) / (z2 + z1)) < 1e-15
+    assert abs(f["R"] ** 2 - g["R2"]) < 1e-7
+    assert abs(z1 / z2 * f["T"] ** 2 - g["Z1_over_Z2_T2"]) < 1e-7
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_interface_oblique_invariants(seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        c1, c2 = rng.uniform(1400, 1700, 2)
+        r1, r2 = rng.uniform(900, 1200, 2)
+        n = rng.normal(size=3)
+        n /= np.linalg.norm(n)
+        w = rng.normal(size=3)
+        w /= np.linalg.norm(w)
+        if w @ n > 0:
+            w = -w  # arriving against nin (nin points back into medium 1)
+        f = O.interface(w, n, c1, c2, r1, r2)
+        ci = -w @ n
+        si = math.sqrt(max(0.0, 1 - ci * ci))
+        assert abs(f["cos_i"] - ci) < 1e-12
+        wr = f["wr"]
+        # reflection law: unit, mirrored normal component, same tangential component
+        assert abs(np.linalg.norm(wr) - 1) < 1e-12
+        assert abs(wr @ n - ci) < 1e-12
+        assert np.allclose(wr - (wr @ n) * n, w - (w @ n) * n, atol=1e-12)
+        if c2 / c1 * si >= 1:
+            assert f["tir"] and f["R"] == 1.0
+            continue
+        assert not f["tir"]
+        wt = f["wt"]
+        assert abs(np.linalg.norm(wt) - 1) < 1e-12
+        st = np.linalg.norm(wt - (wt @ n) * n)
+        assert abs(st / c2 - si / c1) < 1e-12  # Snell with sound speeds
+        assert wt @ n < 0  # continues into medium 2
+        tang_w = w - (w @ n) * n
+        if np.linalg.norm(tang_w) > 1e-9:  # plane of incidence
+            assert np.linalg.norm(np.cross(tang_w, wt - (wt @ n) * n)) < 1e-9
+        ct = f["cos_t"]
+        z1, z2 = r1 * c1, r2 * c2
+        assert abs(f["R"] ** 2 + (z1 * ct) / (z2 * ci) * f["T"] ** 2 - 1) < 1e-12  # energy balance
+        assert abs(f["T"] - 1 - f["R"]) < 1e-12  # pressure continuity
+
+
+def test_critical_angle_water_to_tissue():
+    g = GOLD
+    crit = math.degrees(math.asin(g["c1"] / g["c2"]))
+    assert abs(crit - g["critical_angle_deg"]) < 0.01
+    n = np.array([0, 0, -1.0])
+    for ang, tir in [(crit - 0.05, False), (crit + 0.05, True)]:
+        a = math.radians(ang)
+        f = O.interface([math.sin(a), 0, math.cos(a)], n, g["c1"], g["c2"], g["rho1"], g["rho2"])
+        assert f["tir"] == tir
+
+
+# ------------------------------------------------------------------------------------------
+# P2  single planar interface: echo time 2d/c, amplitude R times attenuation
+# ------------------------------------------------------------------------------------------
+def two_layer_scene():
+    w = P.two_layer()
+    return w, O.Scene.from_workload(w)
+
+
+def test_planar_echo_time_and_amplitude():
+    g = GOLD
+    w, sc = two_layer_scene()
+    acq = w["acq"]
+    for e in [0, 10, 32, 63]:
+        xe = (e - 0.5 * (acq["n_elem"] - 1)) * acq["pitch"]
+        arr, rec, _ = O.trace_injected(sc, w["theta"], 2, acq, [xe, 0, 0], [0, 0, 1], forced=[O.CH_REFLECT],
+                                       physical=True)
+        assert len(arr) == 1
+        ee, tau, amp, kind = arr[0]
+        assert ee == e and kind == 0
+        assert abs(tau - g["echo_time_s"]) < 1e-15
+        assert abs(tau * 40e6 - g["echo_sample_at_40MHz"]) < 0.005
+        att = 10 ** (-g["alpha1"] * g["f0"] / 1e6 * 2 * g["d"] * 100 / 20)
+        assert abs(att - g["attenuation_two_way"]) < 5e-6
+        assert abs(amp - g["R"] * att) < 1e-6
+        assert abs(amp - g["echo_amplitude"]) < g["tolerance_abs_printed"]
+
+
+def test_planar_echo_monte_carlo_mean():
+    """E[weight] over the reflect/transmit split equals R * attenuation (weight = amplitude / P_r)."""
+    g = GOLD
+    w, sc = two_layer_scene()
+    acq = dict(w["acq"], k_max=1)
+    n = 40000
+    vals = np.zeros(n)
+    for i in range(n):
+        arr, _, _ = O.trace_injected(sc, w["theta"], 2, acq, [0.1 * MM, 0.37 * MM, 0], [0, 0, 1], ray=i, seed=3)
+        vals[i] = sum(a for (_, tau, a, _) in arr if abs(tau - g["echo_time_s"]) < 1e-9)
+    target = g["echo_amplitude"]
+    sigma = vals.std() / math.sqrt(n)
+    assert abs(vals.mean() - target) < 3 * sigma
+    assert 0.3 < (vals != 0).mean() / g["R2"] < 3
+
+
+def test_two_way_path_through_slab_and_attenuation_products():
+    """Transmit, reflect at the slab bottom, transmit: T12 R23 T21 and per-segment attenuation."""
+    w, sc = two_layer_scene()
+    th = w["theta"].copy()
+    g = GOLD
+    R = g["R"]
+    o = [0.1 * MM, 0.37 * MM, 0]
+    arr, rec, _ = O.trace_injected(sc, th, 2, w["acq"], o, [0, 0, 1],
+                                   forced=[O.CH_TRANSMIT, O.CH_REFLECT, O.CH_TRANSMIT], physical=True)
+    (_, tau, amp, _), = arr
+    assert abs(tau - (0.04 / 1480 + 0.04 / 1540)) < 1e-15
+    att_w = 10 ** (-0.002 * 5 * 4 / 20)
+    att_s = 10 ** (-0.5 * 5 * 4 / 20)
+    R_exact = (g["Z2"] - g["Z1"]) / (g["Z2"] + g["Z1"])
+    assert abs(amp - (1 + R_exact) * (-R_exact) * (1 - R_exact) * att_w * att_s) < 1e-12
+    assert abs(R_exact - R) < 5e-7
+    # attenuation factors multiply over segments: doubling alpha in the slab squares its factor
+    th2 = th.copy()
+    th2[5] *= 2
+    (_, _, amp2, _), = O.trace_injected(sc, th2, 2, w["acq"], o, [0, 0, 1],
+                                        forced=[O.CH_TRANSMIT, O.CH_REFLECT, O.CH_TRANSMIT], physical=True)[0]
+    assert abs(amp2 / amp - att_s) < 1e-12
+
+
+# ------------------------------------------------------------------------------------------
+# P5  reciprocity of specular two-way paths
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("deg", [2.0, 7.0, -11.0])
+def test_reciprocity_specular_paths(deg):
+    w, sc = two_layer_scene()
+    acq = dict(w["acq"], n_elem=128)
+    a = math.radians(deg)
+    o = np.array([-3 * MM * np.sign(deg), 0.4 * MM, 0.0])
+    d = np.array([math.sin(a), 0.02, math.cos(a)])
+    d /= np.linalg.norm(d)
+    forced = [O.CH_TRANSMIT, O.CH_REFLECT, O.CH_TRANSMIT]
+    arr, _, last = O.trace_injected(sc, w["theta"], 2, acq, o, d, forced=forced, physical=True)
+    assert len(arr) == 1
+    (e_ij, tau_ij, amp_ij, _), = arr
+    back, _, last_b = O.trace_injected(sc, w["theta"], 2, acq, last[:3], -last[3:], forced=forced, physical=True)
+    (e_ji, tau_ji, amp_ji, _), = back
+    assert np.allclose(last_b[:3], o, atol=1e-12)
+    assert np.allclose(last_b[3:], -d, atol=1e-12)
+    assert abs(tau_ij - tau_ji) < 1e-18
+    assert abs(amp_ij - amp_ji) < 1e-14
+
+
+def test_reciprocity_scatterer_paths_statistical():
+    """Single-element transmits: RF_{i<-j} and RF_{j<-i} agree within Monte Carlo noise."""
+    sp = np.array([[0.5 * MM, 0.0, 10 * MM], [-1.5 * MM, 0.3 * MM, 12 * MM]])
+    sc = O.Scene(np.zeros((0, 9)), np.zeros((0, 2), np.int32), sp, [1.0, -0.7], 0.2 * MM)
+    th = P.theta_vector([(1500.0, 1000.0, 0.3)])
+    i, j = 1, 6
+    e_ij = []
+    for tx_e, rx_e in [(i, j), (j, i)]:
+        acq = P.acquisition(8, 0.3 * MM, 1024, [0.0], 3000000, 2, 1500.0, tx_elem=tx_e)
+        run = O.Run(sc, th, 1, acq, 9)
+        rf = run.rf()[0, rx_e]
+        e_ij.append(rf)
+    a, b = e_ij
+    assert np.abs(a).max() > 0 and np.abs(b).max() > 0
+    # correlation of the two received traces and energy ratio
+    corr = (a @ b) / math.sqrt((a @ a) * (b @ b))
+    assert corr > 0.8
+    assert 0.5 < (a @ a) / (b @ b) < 2.0
+
+
+# ------------------------------------------------------------------------------------------
+# P4  point-scatterer image location (transport times + DAS delays, plane-wave steering)
+# ------------------------------------------------------------------------------------------
+def point_scatterer_bmode(xs, zs, angle_deg, das_angle_deg=None, n_rays=200000):
+    acq = P.acquisition(64, 0.3 * MM, 1024, [angle_deg], n_rays, 2, 1480.0)
+    img = P.image(128, 512, -9.45 * MM, 9.45 * MM, 5 * MM, 25 * MM)
+    th = P.theta_vector([(1480.0, 1000.0, 0.0)])
+    sc = O.Scene(np.zeros((0, 9)), np.zeros((0, 2), np.int32), [[xs, 0, zs]], [1.0], 0.1 * MM, bvh=False)
+    run = O.Run(sc, th, 1, acq, 1)
+    rf = run.rf()
+    acq_das = acq if das_angle_deg is None else dict(acq, angles=[math.radians(das_angle_deg)])
+    irf, env, b = O.bmode(acq_das, img, rf)
+    l, d = np.unravel_index(env.argmax(), env.shape)
+    x = img["x0"] + (img["x1"] - img["x0"]) * l / (img["n_lines"] - 1)
+    z = img["z0"] + (img["z1"] - img["z0"]) * d / (img["n_depth"] - 1)
+    return x, z, (img["x1"] - img["x0"]) / (img["n_lines"] - 1)
+
+
+@pytest.mark.parametrize("angle,xs,zs,n_rays", [(0.0, 2 * MM, 15 * MM, 200000), (10.0, 2 * MM, 15 * MM, 200000),
+                                                (-10.0, 2 * MM, 15 * MM, 200000), (0.0, -3 * MM, 12 * MM, 800000)])
+def test_point_scatterer_image_location(angle, xs, zs, n_rays):
+    """Enough rays that Monte Carlo noise in the ~1e-5 hit probability no longer moves the peak."""
+    x, z, dline = point_scatterer_bmode(xs, zs, angle, n_rays=n_rays)
+    lam = 1480.0 / 5e6
+    assert abs(x - xs) <= dline
+    assert abs(z - zs) <= lam / 4
+
+
+def test_point_scatterer_steering_sign_matters():
+    xs, zs = 2 * MM, 15 * MM
+    x, z, dline = point_scatterer_bmode(xs, zs, 12.0, das_angle_deg=-12.0)
+    assert abs(x - xs) > dline or abs(z - zs) > 1480.0 / 5e6 / 4
+
+
+# ------------------------------------------------------------------------------------------
+# P6  pulse: bandwidth reading, envelope peak, splat linearity
+# ------------------------------------------------------------------------------------------
+def test_pulse_minus6db_bandwidth_is_60_percent():
+    f0 = 5e6
+    fs = 400e6
+    ns = 8192
+    acq = P.acquisition(1, 0.3 * MM, ns, [0.0], 1, 1, 1500.0, fs=fs)
+    tau = ns / 2 / fs
+    rf = O.splat(acq, f0, [0], [0], [tau], [1.0])[0, 0]
+    spec = np.abs(np.fft.rfft(rf, 16 * ns))
+    f = np.fft.rfftfreq(16 * ns, 1 / fs)
+    pk = spec.argmax()
+    assert abs(f[pk] - f0) / f0 < 0.02
+    half = spec >= 0.5 * spec[pk]
+    lo = f[np.argmax(half)]
+    hi = f[len(half) - 1 - np.argmax(half[::-1])]
+    assert abs((hi - lo) / f0 - 0.6) < 0.01
+
+
+def test_splat_envelope_peaks_at_arrival_time_and_is_linear():
+    acq = P.acquisition(4, 0.3 * MM, 2048, [0.0, 5.0], 1, 1, 1500.0)
+    rng = np.random.default_rng(1)
+    n = 50
+    tx = rng.integers(0, 2, n)
+    e = rng.integers(0, 4, n)
+    tau = rng.uniform(5e-6, 45e-6, n)
+    a = rng.normal(size=n)
+    full = O.splat(acq, 5e6, tx, e, tau, a)
+    parts = O.splat(acq, 5e6, tx[:20], e[:20], tau[:20], a[:20]) + O.splat(acq, 5e6, tx[20:], e[20:], tau[20:],
+                                                                            a[20:])
+    assert np.allclose(full, parts, atol=1e-13)
+    # single arrival: Hilbert envelope peaks at tau (to within one sample)
+    one = O.splat(acq, 5e6, [0], [1], [20.3e-6], [2.0])[0, 1]
+    env = np.abs(one + 1j * O.hilbert(one))
+    assert abs(env.argmax() - 20.3e-6 * acq["fs"]) <= 1.0
+    assert abs(env.max() - 2.0) < 0.02
+
+
+# ------------------------------------------------------------------------------------------
+# P7  image chain: Hilbert, DAS adjoint, log compression, loss
+# ------------------------------------------------------------------------------------------
+def test_hilbert_matches_scipy_and_is_skew():
+    sig = pytest.importorskip("scipy.signal")
+    rng = np.random.default_rng(2)
+    for n in [1024, 1000, 63, 8]:
+        x = rng.normal(size=n)
+        assert np.allclose(O.hilbert(x), np.imag(sig.hilbert(x)), atol=1e-10)
+    n = 64
+    H = np.stack([O.hilbert(np.eye(n)[k]) for k in range(n)], axis=1)
+    assert np.allclose(H, -H.T, atol=1e-12)
+    # bin-centred cosine has a constant envelope
+    k = 7
+    x = np.cos(2 * np.pi * k * np.arange(n) / n + 0.3)
+    env = np.abs(x + 1j * O.hilbert(x))
+    assert np.allclose(env, 1.0, atol=1e-12)
+
+
+def test_das_adjoint_dot_product():
+    acq = P.acquisition(8, 0.3 * MM, 300, [-7.0, 0.0, 11.0], 1, 1, 1540.0)
+    img = P.image(9, 40, -1.5 * MM, 1.2 * MM, 0.5 * MM, 9 * MM)
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(3, 8, 300))
+    y = rng.normal(size=(9, 40))
+    lhs = (O.das(acq, img, x) * y).sum()
+    rhs = (x * O.das_adjoint(acq, img, y)).sum()
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_das_is_linear_interpolation_with_zero_outside():
+    """A constant RF row gives, at each pixel, the Hann-weighted count of in-range taps."""
+    acq = P.acquisition(4, 0.3 * MM, 100, [0.0], 1, 1, 1540.0)
+    img = P.image(3, 50, -0.5 * MM, 0.5 * MM, 0.0, 10 * MM)
+    rf = np.ones((1, 4, 100))
+    out = O.das(acq, img, rf)
+    hann = 0.5 * (1 - np.cos(2 * np.pi * (np.arange(4) + 1) / 5))
+    assert np.allclose(out[:, 0], hann.sum())
+    assert np.all(out[:, -1] == 0.0)  # 2 * 10 mm / 1540 m/s * 40 MHz > 100 samples
+
+
+def test_log_compression_and_clip():
+    img = P.image(1, 5, 0, 0, 0, 1, dr_db=60.0)
+    env = np.array([[1.0, 0.1, 1e-3, 1e-4, 0.0]])
+    b, am = O.log_compress(img, env)
+    assert am == 0
+    assert np.allclose(b[0], [0.0, -20.0, -60.0, -60.0, -60.0])
+
+
+def test_loss_normalisation_and_gradient():
+    img = P.image(4, 8, 0, 0, 0, 1, lambda1=0.3, lambda2=0.7)
+    rng = np.random.default_rng(4)
+    b = rng.normal(size=(4, 8))
+    ref = b - 1.0
+    val, g = O.loss(img, b, ref)
+    assert abs(val - (0.3 + 0.7)) < 1e-12
+    # gradient vs central differences
+    for idx in [(0, 0), (2, 5), (3, 7)]:
+        h = 1e-6
+        bp, bm = b.copy(), b.copy()
+        bp[idx] += h
+        bm[idx] -= h
+        fd = (O.loss(img, bp, ref)[0] - O.loss(img, bm, ref)[0]) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-8
+
+
+def test_envlog_vjp_matches_finite_differences():
+    img = P.image(3, 64, 0, 0, 0, 1, dr_db=40.0)
+    rng = np.random.default_rng(5)
+    t = np.arange(64)
+    irf = np.stack([np.sin(0.6 * t + p) * np.exp(-((t - c) / 12.0) ** 2) for p, c in [(0.1, 20), (1.0, 33), (2, 45)]])
+    irf += 0.01 * rng.normal(size=irf.shape)
+    gb = rng.normal(size=irf.shape)
+
+    def f(x):
+        env = O.envelope(img, x)
+        b, _ = O.log_compress(img, env)
+        return (b * gb).sum()
+
+    gi = O.envlog_vjp(img, irf, gb)
+    for idx in [(0, 20), (1, 33), (2, 50), (0, 3), (1, 60)]:
+        h = 1e-7
+        p, m = irf.copy(), irf.copy()
+        p[idx] += h
+        m[idx] -= h
+        fd = (f(p) - f(m)) / (2 * h)
+        assert abs(fd - gi[idx]) < 1e-4 * max(1.0, abs(fd))
+
+
+def test_splat_adjoint_matches_finite_differences():
+    acq = P.acquisition(3, 0.3 * MM, 1024, [0.0], 1, 1, 1500.0)
+    rng = np.random.default_rng(6)
+    grf = rng.normal(size=(1, 3, 1024))
+    tx, e = np.array([0, 0]), np.array([1, 2])
+    tau = np.array([10.1e-6, 17.77e-6])
+    a = np.array([0.7, -1.3])
+    f0 = 5e6
+    ga, gt, gf = O.splat_adjoint(acq, f0, tx, e, tau, a, grf)
+
+    def L(tau_, a_, f0_):
+        return (O.splat(acq, f0_, tx, e, tau_, a_) * grf).sum()
+
+    for k in range(2):
+        da = np.zeros(2)
+        da[k] = 1e-6
+        assert abs((L(tau, a + da, f0) - L(tau, a - da, f0)) / 2e-6 - ga[k]) < 1e-6 * max(1, abs(ga[k]))
+        dt = np.zeros(2)
+        dt[k] = 1e-12
+        fd = (L(tau + dt, a, f0) - L(tau - dt, a, f0)) / 2e-12
+        assert abs(fd - gt[k]) < 1e-4 * max(abs(fd), 1e3)
+    fd = (L(tau, a, f0 + 1.0) - L(tau, a, f0 - 1.0)) / 2.0
+    assert abs(fd - gf.sum()) < 1e-4 * max(abs(fd), 1e-9)
+
+
+# ------------------------------------------------------------------------------------------
+# P8  BVH vs brute force
+# ------------------------------------------------------------------------------------------
+def small_inclusions(n_rays=300, k_max=6):
+    return P.inclusions(n_regions=3, n_scat=3000, n_rays=n_rays, k_max=k_max, n_samples=2048, angles_deg=[0.0, 9.0],
+                        n_lines=32, n_depth=256, n_elem=16, n_lat=12, n_lon=20)
+
+
+def test_bvh_matches_brute_force():
+    w = small_inclusions()
+    runs = []
+    for bvh in (False, True):
+        sc = O.Scene.from_workload(w, bvh=bvh)
+        runs.append(O.Run(sc, w["theta"], w["M"], w["acq"], 5))
+    r0, r1 = [r.records() for r in runs]
+    for k in r0:
+        assert np.array_equal(r0[k], r1[k])
+    a0, a1 = runs[0].arrivals(), runs[1].arrivals()
+    for k in a0:
+        assert np.array_equal(a0[k], a1[k])
+    assert runs[0].counters()["nee"] > 100
+    assert (r0["cls"] == O.CLS_TRI).sum() > 100
+
+
+def test_flat_face_diagonal_does_not_self_hit():
+    """A normal ray reflected exactly on the shared diagonal of a flat face returns to the probe."""
+    w, sc = two_layer_scene()
+    arr, rec, _ = O.trace_injected(sc, w["theta"], 2, w["acq"], [0, 0, 0], [0, 0, 1], forced=[O.CH_REFLECT])
+    assert rec[1, 0] == O.CLS_XDCR and len(arr) == 1
+
+
+def test_closest_hit_excludes_previous_and_breaks_ties():
+    tri = np.array([[0, -1, 1, 1, -1, 1, 0, 1, 1.0], [0, -1, 1, 1, -1, 1, 0, 1, 1.0]])  # two identical triangles
+    sc = O.Scene(tri, np.zeros((2, 2), np.int32), np.zeros((0, 3)), np.zeros(0), 0.1, bvh=False)
+    t, cls, i = sc.closest([0.2, 0, 0], [0, 0, 1.0])
+    assert (t, cls, i) == (1.0, O.CLS_TRI, 0)
+    t, cls, i = sc.closest([0.2, 0, 0], [0, 0, 1.0], O.CLS_TRI, 0)
+    assert (cls, i) == (O.CLS_TRI, 1)
+
+
+# ------------------------------------------------------------------------------------------
+# P9  linearity in the scatterer amplitude scale
+# ------------------------------------------------------------------------------------------
+def test_rf_linear_in_scatterer_amplitude_scale():
+    w = P.slab_scatterers(n_rays=200)
+    sc = O.Scene.from_workload(w)
+    th = w["theta"].copy()
+    run = O.Run(sc, th, 2, w["acq"], 0)
+    arr = run.arrivals()
+    nee = arr["kind"] == 1
+    assert nee.sum() > 10
+    th2 = th.copy()
+    th2[6] *= 2.5
+    run2 = O.Run(sc, th2, 2, w["acq"], 0)
+    arr2 = run2.arrivals()
+    assert np.allclose(arr2["a"][nee], 2.5 * arr["a"][nee], rtol=1e-14)
+    assert np.array_equal(arr2["a"][~nee], arr["a"][~nee])
+
+
+# ------------------------------------------------------------------------------------------
+# P10 fixed-sample gradient vs central finite differences on the frozen realisation
+# ------------------------------------------------------------------------------------------
+def test_gradient_matches_replay_finite_differences():
+    w = P.slab_scatterers(n_rays=1500, n_scat=1000)
+    w["img"] = P.image(64, 512, w["img"]["x0"], w["img"]["x1"], 0.0, w["img"]["z1"])
+    sc = O.Scene.from_workload(w)
+    th = w["theta"]
+    acq, img = w["acq"], w["img"]
+    run = O.Run(sc, th, 2, acq, 0)
+    ref_run = O.Run(sc, w["theta_target"], 2, acq, 0)
+    _, _, bref = O.bmode(acq, img, ref_run.rf())
+    rf = run.rf()
+    _, _, b = O.bmode(acq, img, rf)
+    _, gb = O.loss(img, b, bref)
+    grf = O.bmode_vjp(acq, img, rf, gb)
+    g = run.gradient(grf)
+
+    def L(t):
+        _, _, bb = O.bmode(acq, img, run.replay_rf(t))
+        return O.loss(img, bb, bref)[0]
+
+    def lin(t):
+        return (grf * run.replay_rf(t)).sum()
+
+    # replay at theta reproduces the forward RF
+    assert np.allclose(run.replay_rf(th), rf, atol=1e-12 * np.abs(rf).max())
+    sens = np.abs(g * th)
+    assert sens.max() > 0
+    for k in range(len(th)):
+        # (1) the transport + splat derivative: d/dtheta of the linear functional <grf, RF>
+        tp, tm = th.copy(), th.copy()
+        tp[k] *= 1 + 1e-6
+        tm[k] *= 1 - 1e-6
+        fd = (lin(tp) - lin(tm)) / (2e-6 * th[k])
+        assert abs(fd - g[k]) * abs(th[k]) <= 1e-4 * abs(g[k] * th[k]) + 1e-7 * sens.max(), (k, g[k], fd)
+        # (2) the whole loss, with the step swept as in the paper's FD-vs-AD study (Sec. 4.2.1):
+        # a relative step of 1e-3 moves every echo of a sound-speed parameter by ~27 ns
+        # (0.85 rad of pulse phase), so agreement is asked for at the best step of the sweep.
+        errs = []
+        for h in (1e-4, 1e-5, 1e-6, 1e-7):
+            tp, tm = th.copy(), th.copy()
+            tp[k] *= 1 + h
+            tm[k] *= 1 - h
+            fd = (L(tp) - L(tm)) / (2 * h * th[k])
+            errs.append(abs(fd - g[k]) * abs(th[k]))
+        assert min(errs) <= 1e-2 * abs(g[k] * th[k]) + 1e-4 * sens.max(), (k, g[k], errs)
