@@ -1,0 +1,274 @@
+"""Benchmark: one step = the whole hot path (transport, splat, DAS, envelope/log, loss, image
+VJP, transposed DAS, splat adjoint, path adjoint) on the inclusion phantom (200k triangles in
+12 regions, 1e5 scatterers, 128 elements, 16 plane waves, 1e6 rays per transmit, <= 8
+interactions, 4096 samples, 256 x 1024 B-mode), synthetic data, FP32.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "path-segments/s"
+UNIT = "segments/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="record", choices=["record", "recompute"])
+    ap.add_argument("--rays", type=int, default=7813, help="rays per element and transmit")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-stages", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.stop = threading.Event()
+        self.t = None
+
+    def _run(self):
+        while not self.stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                if out.returncode == 0:
+                    self.samples.append([v.strip() for v in out.stdout.strip().split(",")])
+            except Exception:
+                pass
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.t = threading.Thread(target=self._run, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if len(s) > 3 + k and
+                          s[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# --------------------------------------------------------------------------------------------
+def cpu_baseline(w, seconds, seed):
+    """The FP64 oracle as it stands on the host cores: transport + splat of a contiguous sample
+    of paths, grown until about `seconds` of work; path-segments/s."""
+    from oracle import oracle as O
+
+    nth = O.default_threads()
+    sc = O.Scene.from_workload(w)
+    n = 2000
+    spent = 0.0
+    segs = 0
+    total_paths = 0
+    lo = 0
+    while spent < seconds:
+        t0 = time.perf_counter()
+        run = O.Run(sc, w["theta"], w["M"], w["acq"], seed, nth, lo, lo + n)
+        run.rf()
+        dt = time.perf_counter() - t0
+        c = run.counters()
+        spent += dt
+        segs += c["segments"] + c["nee"]
+        total_paths += n
+        lo += n
+        if dt < seconds / 8:
+            n *= 2
+    return dict(value=segs / spent, unit=UNIT, cores=nth, kind="oracle",
+                sample="%d contiguous paths of the first transmit (of %d), transport + splat, %.1f s" %
+                (total_paths, w["acq"]["n_rays"] * w["acq"]["n_elem"] * len(w["acq"]["angles"]), spent))
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    nth = O.default_threads()
+    sc = O.Scene.from_workload(w)
+    per_step = max(1.0, 20.0 / max(1, args.steps + args.warmup))
+    # size the per-step sample from a probe
+    n = 1000
+    t0 = time.perf_counter()
+    O.Run(sc, w["theta"], w["M"], w["acq"], w["seed"], nth, 0, n).rf()
+    n = max(500, int(n * per_step / max(time.perf_counter() - t0, 1e-3)))
+    lo = 0
+    for _ in range(args.warmup):
+        O.Run(sc, w["theta"], w["M"], w["acq"], w["seed"], nth, lo, lo + n).rf()
+        lo += n
+    segs = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = O.Run(sc, w["theta"], w["M"], w["acq"], w["seed"], nth, lo, lo + n)
+        r.rf()
+        c = r.counters()
+        segs += c["segments"] + c["nee"]
+        lo += n
+    dt = time.perf_counter() - t0
+    val = segs / dt
+    sample = "%d paths per step (transport + splat) of the inclusion workload" % n
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "inclusions-200k-tris-1e5-scatterers-16tx-1e6rays"},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": nth, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# --------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    from paper_2604_15017_gb300 import phantoms as P
+
+    w = P.inclusions(n_rays=args.rays)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2604_15017_gb300 import usrt
+
+    ctx = usrt.Context(local)
+    sid = ctx.upload_workload(w)
+    acq, img = w["acq"], w["img"]
+    seed = w["seed"] + 1000 * rank  # independent frames per rank
+    mode = usrt.MODE_RECORD if args.mode == "record" else usrt.MODE_RECOMPUTE
+    # target image at the perturbed parameters (outside the timed region)
+    _, bref = ctx.forward(sid, P.perturbed_theta(w["theta"], 7), acq, img, seed=seed)
+    bref = bref.clone()
+    theta = w["theta"]
+    st = torch.cuda.current_stream()
+
+    def step():
+        rf, b = ctx.forward(sid, theta, acq, img, seed=seed, keep_record=(mode == usrt.MODE_RECORD))
+        loss, gb = ctx.loss(img, b, bref)
+        gth, _ = ctx.adjoint(sid, theta, acq, img, seed, rf, gb, mode=mode)
+        return loss, gth
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = ctx.stats()
+    segs_per_step = stats["segments"] + stats["nee_queries"]
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            loss, gth = step()
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+    value = segs_per_step * world / (ms * 1e-3)
+
+    # end to end through the public API with host buffers: B_ref host -> device each step,
+    # loss and gradient device -> host each step
+    bref_h = bref.cpu().pin_memory()
+    gth_h = torch.empty(len(theta), dtype=torch.float32).pin_memory()
+    loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
+    bref_d = torch.empty_like(bref)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bref_d.copy_(bref_h, non_blocking=True)
+        rf, b = ctx.forward(sid, theta, acq, img, seed=seed, keep_record=(mode == usrt.MODE_RECORD))
+        loss, gb = ctx.loss(img, b, bref_d)
+        gth, _ = ctx.adjoint(sid, theta, acq, img, seed, rf, gb, mode=mode)
+        gth_h.copy_(gth, non_blocking=True)
+        loss_h.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": segs_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bref_h.numel() * 4,
+           "d2h_bytes_per_step": 4 * (len(theta) + 1)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "inclusions-200k-tris-1e5-scatterers-16tx-1e6rays", "step": "fwd+adj",
+                      "adjoint_mode": args.mode, "paths_per_step": stats["n_paths"],
+                      "segments_per_step": stats["segments"], "nee_queries_per_step": stats["nee_queries"],
+                      "arrivals_per_step": stats["arrivals"], "frames_per_s": world * 1e3 / ms,
+                      "l2": "per-step working set (path queues + arrivals, ~4 GB) exceeds L2; scene BVH resident"},
+           "clocks": clk.summary(), "e2e": e2e, "gpu_launches": None}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, seed)
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

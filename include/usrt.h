@@ -1,0 +1,235 @@
+/*
+ * usrt.h -- C ABI of the GB300 (sm_103a) differentiable Monte Carlo ultrasound ray tracer.
+ *
+ * The library implements the hot path of "Fully Differentiable Ultrasound Simulation Utilizing
+ * Ray-Tracing" (arXiv 2604.15017): full-path Monte Carlo acoustic transport through a triangle
+ * scene with point scatterers (Sec. 2.3.1-2.3.3), the pulse splat into per-element channel data
+ * (Sec. 2.3.4, Eq. axial_sig), delay-and-sum beamforming (Eq. das), envelope detection and log
+ * compression (Sec. 2.3.4), the l1/l2 image loss (Eq. weighted_l1_l2_loss) and the
+ * fixed-sample vector-Jacobian product back to the continuous parameters (Sec. 3.2, Eq.
+ * chain_rule; Eq. das_adjoint).  Every arithmetic step runs in the library's own CUDA kernels,
+ * in FP32.
+ *
+ * Conventions shared by every call
+ *   - Units: SI (m, s, Hz, kg/m^3).  Attenuation alpha in dB/cm/MHz.
+ *   - Parameter vector theta (HOST, float[3*M+2]):
+ *       [c_0, rho_0, alpha_0, c_1, rho_1, alpha_1, ..., c_{M-1}, rho_{M-1}, alpha_{M-1}, A_s, f0]
+ *     M media (medium 0 holds the probe), scatterer amplitude scale A_s, centre frequency f0.
+ *   - Probe: elements e = 0..n_elem-1 at x_e = (e - (n_elem-1)/2) * pitch, z = 0, normal +z,
+ *     element face pitch x h_el.  Transmit tx uses plane-wave steering angle angles[tx].
+ *   - Channel data rf: DEVICE float[n_tx][n_elem][n_samples], sample n at t = n / fs.
+ *   - Images: DEVICE float[n_lines][n_depth] (depth contiguous); line l at
+ *     x0 + l (x1-x0)/(n_lines-1), depth d at z0 + d (z1-z0)/(n_depth-1).
+ *   - "*_dev" pointers are device memory owned by the caller; they must be 16-byte aligned.
+ *     Host pointers are read during the call only.  The library owns scenes, path records and
+ *     workspaces, all charged against the context's memory budget.
+ *   - Calls enqueue work on the caller's CUDA stream (passed as void*, a cudaStream_t) and
+ *     return without synchronising unless stated.  Scratch buffers grow on first use; make the
+ *     first call of each shape outside CUDA-graph capture.
+ *   - Every call returns a us_status (0 = success, < 0 = error).  No exception or abort
+ *     crosses the ABI; us_last_error() describes the most recent failure of the context.
+ *     Device-side faults are reported by status words, never by traps.
+ */
+#ifndef USRT_H
+#define USRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  US_OK = 0,
+  US_ERR_ARG = -1,      /* invalid argument, size or alignment */
+  US_ERR_OOM = -2,      /* allocation failed, or the memory budget refuses the request */
+  US_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+  US_ERR_TIMEOUT = -4,  /* a bounded device wait gave up (reported through a status word) */
+  US_ERR_OVERFLOW = -5, /* a fixed-capacity device list overflowed (secondary-ray crossings) */
+  US_ERR_STATE = -6     /* call order: e.g. adjoint in record mode without a kept record */
+} us_status;
+
+typedef struct us_ctx us_ctx;
+
+/* Scene: triangles with the media on their two sides, plus point scatterers. */
+typedef struct {
+  int32_t n_tris;
+  const float* tris;     /* HOST, n_tris * 9: v0, v1, v2 (x, y, z) in metres */
+  const int32_t* media;  /* HOST, n_tris * 2: (m_front, m_back); front = side the normal
+                            (v1 - v0) x (v2 - v0) points to */
+  int32_t n_media;       /* M, number of media referenced by theta (<= 32) */
+  int32_t n_scat;
+  const float* scat_pos; /* HOST, n_scat * 3 */
+  const float* scat_amp; /* HOST, n_scat: per-scatterer amplitude s_j */
+  float r_s;             /* scatterer radius: a primary ray interacts at its closest approach
+                            when that lies within r_s of the centre */
+} us_scene_desc;
+
+/* Acquisition: probe, transmits, sampling and transport limits (Sec. 2.3.1-2.3.4). */
+typedef struct {
+  int32_t n_elem;        /* <= 256 */
+  float pitch;           /* element pitch = element width (kerf 0) */
+  float h_el;            /* element height (elevation) */
+  int32_t n_tx;          /* <= 64 transmits */
+  const float* angles;   /* HOST, n_tx steering angles [rad] */
+  float fs;              /* sampling rate [Hz] */
+  int32_t n_samples;     /* multiple of 4, <= 4096 */
+  int32_t k_max;         /* maximum interactions per path (<= 15) */
+  int32_t n_rays;        /* rays per emitting element and transmit */
+  float bw;              /* -6 dB fractional bandwidth of the pulse */
+  float alpha_m;         /* receive directivity main-lobe angle [rad] (Eq. cutoff) */
+  float alpha_c;         /* receive directivity cutoff angle [rad] */
+  float c_bf;            /* beamforming / steering-delay sound speed */
+  int32_t split_mode;    /* 0: P_reflect = R^2 (Sec. 2.3.2); 1: fixed P_reflect = split_q */
+  float split_q;
+  uint32_t stream_id;    /* third Philox counter word (independent scenes / requests) */
+  int32_t tx_elem;       /* -1: every element emits; else only this element (single-element
+                            transmit) */
+} us_acq_desc;
+
+/* Image grid, dynamic range and loss weights. */
+typedef struct {
+  int32_t n_lines;
+  int32_t n_depth;       /* power of two, 16..4096 (FFT envelope) */
+  float x0, x1, z0, z1;
+  float dr_db;           /* dynamic range: B = max(20 log10(E / E_max), -dr_db) */
+  float lambda1, lambda2;/* loss weights (Eq. weighted_l1_l2_loss) */
+} us_img_desc;
+
+/* Transport statistics of the most recent us_forward / us_trace on a context. */
+typedef struct {
+  int64_t n_paths;
+  int64_t segments;      /* primary closest-hit queries (one per path segment) */
+  int64_t nee_queries;   /* secondary-ray all-crossings queries */
+  int64_t arrivals;      /* arrivals splatted (transducer hits + secondary rays) */
+  int64_t dropped;       /* arrivals dropped: crossing-list overflow */
+  int32_t status;        /* device status word: 0, or a us_status raised on the device */
+} us_stats;
+
+/* ---------------------------------------------------------------------------------------- */
+/* Context and scenes                                                                        */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the library's own device
+ * allocations (scenes, records, workspaces); 0 = no cap.  *out receives the context. */
+int us_create(us_ctx** out, int device, size_t mem_budget_bytes);
+
+/* Destroy a context: synchronises the device, frees every scene and workspace. */
+void us_destroy(us_ctx* ctx);
+
+/* Text of the most recent error on this context ("" if none).  Owned by the context. */
+const char* us_last_error(us_ctx* ctx);
+
+/* Upload a scene and build its BVH (binned SAH over triangles and scatterer spheres) on the
+ * host; the BVH and primitive data stay resident on the device until released.
+ * Synchronous.  *scene_id receives a handle (> 0). */
+int us_scene_upload(us_ctx* ctx, const us_scene_desc* desc, uint64_t* scene_id);
+
+/* Release a scene's device memory (synchronises the device first). */
+int us_scene_release(us_ctx* ctx, uint64_t scene_id);
+
+/* Bytes currently allocated by the context, and its budget. */
+int us_memory(us_ctx* ctx, size_t* used, size_t* budget);
+
+/* ---------------------------------------------------------------------------------------- */
+/* S1: sample streams                                                                        */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Philox4x32-10 (Salmon et al., SC'11): out_dev[4 i + j] = word j of block
+ * philox(ctr = (c0_base + i, c1, c2, c3), key = (k0, k1)), i < n.  The transport draws block
+ * (ray_id, tx, stream_id, event) with key (seed_lo, seed_hi) and uses u = (x >> 8) * 2^-24. */
+int us_philox_fill(us_ctx* ctx, uint32_t c0_base, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                   uint32_t k1, int64_t n, uint32_t* out_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Forward hot path                                                                          */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Full forward pass (Sec. 2.3; Eq. das): emission, wavefront transport (closest hits,
+ * Fresnel/Snell interfaces, attenuation, receiver-guided secondary rays at scatterers), sort-
+ * based pulse splat -> rf_dev, DAS -> envelope -> log compression -> bmode_dev (dB, in
+ * [-dr_db, 0]).  bmode_dev may be NULL (channel data only); img may then be NULL.
+ * keep_record != 0 keeps the per-path event record on the context for us_adjoint in record
+ * mode and for us_get_record.  seed fixes every sample (common random numbers, Sec. 3.2). */
+int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq,
+               const us_img_desc* img, uint64_t seed, int keep_record, float* rf_dev, float* bmode_dev,
+               void* stream);
+
+/* Statistics of the most recent forward pass (synchronises the stream of that pass). */
+int us_get_stats(us_ctx* ctx, us_stats* out);
+
+/* Copy the kept record of paths [path_lo, path_lo + n) to out_dev (uint32 per event,
+ * n * (k_max + 1) entries).  Event word: bits 0-19 primitive id (element for the transducer),
+ * bits 20-21 class (0 none/escape, 1 transducer, 2 triangle, 3 scatterer), bits 22-23 interface
+ * choice (0 none, 1 reflect, 2 transmit, 3 total internal reflection), bits 24-31 secondary-ray
+ * element.  Path p = tx * rays_per_tx + local ray. */
+int us_get_record(us_ctx* ctx, int64_t path_lo, int64_t n, uint32_t* out_dev, void* stream);
+
+/* S6 alone: splat an explicit arrival list into rf_dev (zeroed first).  Arrival i lands on
+ * row tx_dev[i] * n_elem + e_dev[i] at time tau_dev[i] [s] with amplitude a_dev[i] (Eq.
+ * axial_sig, pulse centre frequency f0). */
+int us_splat(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int32_t* tx_dev,
+             const int32_t* e_dev, const float* tau_dev, const float* a_dev, float* rf_dev, void* stream);
+
+/* S7 alone: DAS (Eq. das), rf_dev -> irf_dev [n_lines][n_depth], transmits summed coherently,
+ * Hann apodisation, linear interpolation, samples outside the record count as zero. */
+int us_das(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev, float* irf_dev,
+           void* stream);
+
+/* S8 alone: fused envelope (|analytic signal| along depth) and log compression with the
+ * dynamic-range clip, irf_dev -> bmode_dev. */
+int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* bmode_dev, void* stream);
+
+/* RF -> B-mode (S7 + S8). */
+int us_bmode(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+             float* bmode_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Loss and adjoint                                                                          */
+/* ---------------------------------------------------------------------------------------- */
+
+/* S9a: l1/l2 loss (Eq. weighted_l1_l2_loss, normalised by the pixel count) and its exact
+ * gradient: loss_dev[0] = L, dL_dB_dev = dL/dB (may be NULL). */
+int us_loss(us_ctx* ctx, const us_img_desc* img, const float* bmode_dev, const float* bref_dev, float* loss_dev,
+            float* dL_dB_dev, void* stream);
+
+/* S9b alone: VJP of the fused envelope/log stage: dL/dI_rf from dL/dB. */
+int us_envlog_vjp(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, const float* dL_dB_dev,
+                  float* dL_dirf_dev, void* stream);
+
+/* S10 alone: transposed DAS (Eq. das_adjoint), a scatter of dL/dI_rf back to the two
+ * interpolation samples of every tap; dL_drf_dev is overwritten. */
+int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* dL_dirf_dev,
+                   float* dL_drf_dev, void* stream);
+
+/* dL/dRF from dL/dB through log, envelope and DAS (S7 recomputed, S9b, S10). */
+int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+                 const float* dL_dB_dev, float* dL_drf_dev, void* stream);
+
+/* S11 alone: splat adjoint per arrival: ga = sum_n g[n] s(t_n - tau),
+ * gt = -a sum_n g[n] s'(t_n - tau), gf = a sum_n g[n] ds(t_n - tau)/df0 (the pulse width
+ * follows f0 at fixed fractional bandwidth). */
+int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int32_t* tx_dev,
+                     const int32_t* e_dev, const float* tau_dev, const float* a_dev, const float* dL_drf_dev,
+                     float* ga_dev, float* gt_dev, float* gf_dev, void* stream);
+
+/* S11 + S12: fixed-sample transport VJP (Sec. 3.2, Eq. chain_rule): dL/dtheta from dL/dRF for
+ * the realisation fixed by seed.  mode 0 = record (uses the record kept by the last
+ * us_forward with keep_record on this scene, theta, acq and seed), mode 1 = recompute (re-runs
+ * the transport in chunks of paths to regenerate the decisions).  dL_dtheta_dev: DEVICE
+ * float[3M+2], overwritten. */
+int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                     int mode, const float* dL_drf_dev, float* dL_dtheta_dev, void* stream);
+
+/* Full adjoint: dL/dB -> dL/dRF (us_bmode_vjp) -> dL/dtheta (us_transport_vjp).
+ * dL_drf_dev is an optional output (NULL: a library workspace is used). */
+int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+               uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
+               float* dL_drf_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* USRT_H */

@@ -1,0 +1,412 @@
+// Fixed-sample adjoint of the transport and splat (Sec. 3.2, Eq. chain_rule).
+//
+// One thread per path replays the path from its record (primitive, interface choice and
+// secondary-ray element per event are frozen; hit distances are re-solved on the frozen
+// primitive: its plane, the closest approach to the scatterer centre, or the transducer
+// plane).  For every arrival the splat adjoint is gathered on the fly from dL/dRF (S11), then
+// a reverse sweep over the events propagates the adjoints of amplitude, time, position and
+// direction through attenuation, Fresnel weights, Snell directions, hit distances and the
+// receive directivity, accumulating dL/dtheta in shared memory.
+#include "adjoint.cuh"
+#include "bvh_query.cuh"
+
+namespace usrt {
+
+// ------------------------------------------------------------------------------------------
+// S11: splat adjoint of one arrival (time t_hi + t_lo [s], amplitude a) against the row g:
+//   ga = sum_n g[n] s(x_n),  gt = -a sum_n g[n] s'(x_n),  gf = a sum_n g[n] ds(x_n)/df0,
+// x_n = n / fs - tau, s(x) = sin(2 pi f0 x) exp(-x^2 / sigma), sigma = 4 ln2 / (pi bw f0)^2.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void splat_adj_gather(const float* __restrict__ g, float t_hi, float t_lo, float a,
+                                                 const PulseP& P, float& ga, float& gt, float& gf) {
+  const float u = __fmul_rn(t_hi, P.fs);
+  const float e = __fmaf_rn(t_hi, P.fs, -u);
+  const float n0f = floorf(u);
+  const float fr = (u - n0f) + (e + t_lo * P.fs);  // tau fs = n0 + fr
+  const int n0 = (int)n0f;
+  const int lo = max(0, n0 + (int)ceilf(fr - P.half));
+  const int hi = min(P.ns - 1, n0 + (int)floorf(fr + P.half));
+  float sa = 0.0f, st = 0.0f, sf = 0.0f;
+  const float w = 2.0f * PI_F * P.f0;
+  const float inv_sig = 1.0f / P.sig;
+  for (int n = lo; n <= hi; ++n) {
+    const float gn = __ldg(&g[n]);
+    if (gn == 0.0f) continue;
+    const float x = ((float)(n - n0) - fr) / P.fs;
+    float sn, cs;
+    sincosf(w * x, &sn, &cs);
+    const float E = expf(-x * x * inv_sig);
+    const float s = sn * E;
+    const float ds_dx = (w * cs - 2.0f * x * inv_sig * sn) * E;
+    const float ds_df = (2.0f * PI_F * x * cs - sn * 2.0f * x * x * inv_sig / P.f0) * E;
+    sa = fmaf(gn, s, sa);
+    st = fmaf(gn, -ds_dx, st);
+    sf = fmaf(gn, ds_df, sf);
+  }
+  ga = sa;
+  gt = a * st;
+  gf = a * sf;
+}
+
+__global__ void k_splat_adjoint(Acq q, PulseP P, const int32_t* tx, const int32_t* e, const float* tau, const float* a,
+                                long long n, const float* grf, float* ga, float* gt, float* gf) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float x, y, z;
+    splat_adj_gather(grf + ((size_t)tx[i] * q.ne + e[i]) * q.ns, tau[i], 0.0f, a[i], P, x, y, z);
+    ga[i] = x;
+    gt[i] = y;
+    gf[i] = z;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// frozen hit distance and its gradient w.r.t. (o, w)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float frozen_t(const SceneDev& S, uint32_t cls, uint32_t id, float3 o, float3 w) {
+  if (cls == CLS_XDCR) return -o.z / w.z;
+  if (cls == CLS_TRI) {
+    const float3 n = xyz(__ldg(&S.tri_nrm[id]));
+    const float3 v0 = xyz(__ldg(&S.tri_v0[id]));
+    return dot3(v0 - o, n) / dot3(w, n);
+  }
+  const float3 p = xyz(__ldg(&S.scat[id]));
+  return dot3(p - o, w);
+}
+
+// ------------------------------------------------------------------------------------------
+// S12: path adjoint
+// ------------------------------------------------------------------------------------------
+constexpr int ADJ_THREADS = 128;
+
+// each thread accumulates dL/dtheta in a private shared-memory row (odd stride: no bank
+// conflicts, no atomics); the block sums the rows once at the end
+#define ADD(slot, v) ((slot) += (v))
+__host__ __device__ constexpr int adj_row_stride(int P) { return P | 1; }
+
+__global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
+  extern __shared__ float gsm[];
+  const Acq& q = A.acq;
+  const Media& med = A.med;
+  const int P = A.P;
+  const int PS = adj_row_stride(P);
+  float* acc = gsm + threadIdx.x * PS;
+  const int iAs = 3 * med.M, iF0 = 3 * med.M + 1;
+  for (int p = 0; p < P; ++p) acc[p] = 0.0f;
+  const int K1 = q.kmax + 1;
+  float3 O[MAX_KMAX + 1], W[MAX_KMAX + 1];
+  float Aa[MAX_KMAX + 1], SA[MAX_KMAX + 1], ST[MAX_KMAX + 1];
+  int Mk[MAX_KMAX + 1];
+  uint32_t Rw[MAX_KMAX + 1];
+  float xt[MAX_XINGS];
+  uint32_t xid[MAX_XINGS];
+  const float kap = KAPPA_F;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_paths; i += gridDim.x * blockDim.x) {
+    const long long path = A.path_base + i;
+    const int tx = (int)(path / q.rays_per_tx);
+    const long long local = path - (long long)tx * q.rays_per_tx;
+    const uint32_t ray = (uint32_t)(q.tx_elem < 0 ? local : (long long)q.tx_elem * q.nr + local);
+    // emission (identical to the forward pass)
+    const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, 0u), make_uint2(q.key0, q.key1));
+    const int e = (int)(ray / (uint32_t)q.nr);
+    const float xe = (e - 0.5f * (q.ne - 1)) * q.pitch;
+    float sp, cp;
+    sincospif(2.0f * u01(u.w), &sp, &cp);
+    const float r0 = sqrtf(u01(u.z));
+    float3 o = f3(xe + (u01(u.x) - 0.5f) * q.pitch, (u01(u.y) - 0.5f) * q.hel, 0.0f);
+    float3 w = f3(r0 * cp, r0 * sp, sqrtf(1.0f - u01(u.z)));
+    float a = PI_F / q.nr;
+    const float st0 = q.sin_tx[tx];
+    float th = (xe * st0 + 0.5f * (q.ne - 1) * q.pitch * fabsf(st0)) / q.cbf, tl = 0.0f;
+    int m = 0;
+    int nseg = 0;
+    float gxa = 0.0f, gxt = 0.0f;
+    const uint32_t* rec = A.record + (size_t)i * K1;
+    // ---- forward replay ----
+    for (int k = 0; k <= q.kmax; ++k) {
+      const uint32_t r = rec[k];
+      const uint32_t cls = code_cls(r), id = code_id(r);
+      if (cls == CLS_NONE) break;
+      O[k] = o;
+      W[k] = w;
+      Aa[k] = a;
+      Mk[k] = m;
+      Rw[k] = r;
+      SA[k] = 0.0f;
+      ST[k] = 0.0f;
+      nseg = k + 1;
+      const float t = frozen_t(A.S, cls, id, o, w);
+      const float a1 = a * expf(-kap * med.al[m] * med.f0 * t);
+      ff_add(th, tl, t / med.c[m]);
+      const float3 x = o + w * t;
+      if (cls == CLS_XDCR) {
+        const float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+        if (frx > 0.0f) {
+          float ga, gt, gf;
+          splat_adj_gather(A.grf + ((size_t)tx * q.ne + id) * q.ns, th, tl, a1 * frx, A.pulse, ga, gt, gf);
+          ADD(acc[iF0], gf);
+          gxa = ga;
+          gxt = gt;
+        }
+        break;
+      }
+      if (k == q.kmax) break;
+      if (cls == CLS_TRI) {
+        const float4 nr = __ldg(&A.S.tri_nrm[id]);
+        const uint32_t mm = __float_as_uint(nr.w);
+        const float3 nn = xyz(nr);
+        const bool front = dot3(w, nn) < 0.0f;
+        const float3 nin = front ? nn : nn * -1.0f;
+        const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+        const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+        const Iface f = iface(w, nin, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
+        const uint32_t choice = (r >> 22) & 3u;
+        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+        if (choice == CH_TIR || f.tir) {
+          w = w + nin * (2.0f * f.ci);
+          m = m1;
+          a = a1;
+        } else if (choice == CH_REFLECT) {
+          a = a1 * (f.R / pr);
+          w = w + nin * (2.0f * f.ci);
+          m = m1;
+        } else {
+          a = a1 * (f.T / (1.0f - pr));
+          w = w * f.r + nin * (f.r * f.ci - f.ct);
+          m = m2;
+        }
+      } else {  // scatterer: secondary ray, whose geometry does not depend on theta
+        const int e2 = (int)(r >> 24);
+        const float4 sc = __ldg(&A.S.scat[id]);
+        float nh = th, nl = tl;
+        float3 d;
+        float D;
+        const NeeOut no = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
+        if (no.ok) {
+          const float k_n = med.As * sc.w * no.gain;  // a_n = a1 * k_n
+          const float a_n = a1 * k_n;
+          float ga, gt, gf;
+          splat_adj_gather(A.grf + ((size_t)tx * q.ne + e2) * q.ns, nh, nl, a_n, A.pulse, ga, gt, gf);
+          ADD(acc[iF0], gf);
+          const float Ga = ga * a_n;  // adjoint of log a_n
+          ADD(acc[iAs], ga * a1 * sc.w * no.gain);
+          ADD(acc[iF0], Ga * (-kap * no.sum_al));
+          // sub-segments and crossings again, with derivatives
+          float tprev = 0.0f;
+          int mm_cur = m;
+          for (int c = 0; c <= no.n; ++c) {
+            const float tc = c < no.n ? xt[c] : D;
+            const float l = tc - tprev;
+            ADD(acc[3 * mm_cur + 2], Ga * (-kap * med.f0 * l));
+            ADD(acc[3 * mm_cur + 0], gt * (-l / (med.c[mm_cur] * med.c[mm_cur])));
+            if (c == no.n) break;
+            const float4 nr = __ldg(&A.S.tri_nrm[xid[c]]);
+            const uint32_t mm = __float_as_uint(nr.w);
+            const float dn = dot3(d, xyz(nr));
+            const int m1 = dn < 0.0f ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+            const int m2 = dn < 0.0f ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+            const float ci = fabsf(dn);
+            const float c1 = med.c[m1], c2 = med.c[m2], r1 = med.rho[m1], r2 = med.rho[m2];
+            const float rr = c2 / c1;
+            const float si2 = fmaxf(0.0f, 1.0f - ci * ci);
+            const float ct = sqrtf(fmaxf(0.0f, 1.0f - rr * rr * si2));
+            const float Av = r2 * c2 * ci, Bv = r1 * c1 * ct;
+            const float Ab = Ga * Bv / (Av * (Av + Bv));
+            const float Bb = -Ga / (Av + Bv);
+            ADD(acc[3 * m2 + 1], Ab * c2 * ci);
+            float c2b = Ab * r2 * ci;
+            ADD(acc[3 * m1 + 1], Bb * c1 * ct);
+            float c1b = Bb * r1 * ct;
+            const float ctb = Bb * r1 * c1;
+            if (ct > 0.0f) {
+              const float rb = ctb * (-rr * si2 / ct);
+              c2b += rb / c1;
+              c1b += -rb * c2 / (c1 * c1);
+            }
+            ADD(acc[3 * m2 + 0], c2b);
+            ADD(acc[3 * m1 + 0], c1b);
+            mm_cur = m2;
+            tprev = tc;
+          }
+          SA[k] = ga * k_n;
+          ST[k] = gt;
+        }
+        a = a1;  // Born pass-through: amplitude after the segment, direction unchanged
+      }
+      o = x;
+    }
+    // ---- reverse sweep ----
+    float ab = 0.0f, tb = 0.0f;
+    float3 ob = f3(0.f, 0.f, 0.f), wb = f3(0.f, 0.f, 0.f);
+    for (int k = nseg - 1; k >= 0; --k) {
+      const float3 ok = O[k], wk = W[k];
+      const float ak = Aa[k];
+      const int mk = Mk[k];
+      const uint32_t r = Rw[k];
+      const uint32_t cls = code_cls(r), id = code_id(r);
+      const float t = frozen_t(A.S, cls, id, ok, wk);
+      const float att = expf(-kap * med.al[mk] * med.f0 * t);
+      const float a1 = ak * att;
+      float a1b, t1b;
+      float3 xb, wpb;
+      if (cls == CLS_XDCR) {
+        const float cosd = -wk.z;
+        const float frx = f_rx(cosd, q.alpha_m, q.alpha_c);
+        a1b = gxa * frx;
+        t1b = gxt;
+        xb = f3(0.f, 0.f, 0.f);
+        wpb = f3(0.f, 0.f, 0.f);
+        const float thd = acosf(fminf(1.0f, fmaxf(-1.0f, cosd)));
+        if (thd > q.alpha_m && thd <= q.alpha_c && frx > 0.0f) {
+          const float s = sqrtf(fmaxf(1e-30f, 1.0f - wk.z * wk.z));
+          wpb.z = gxa * a1 * (-1.0f / ((q.alpha_c - q.alpha_m) * s));
+        }
+      } else if (cls == CLS_TRI) {
+        const float4 nr = __ldg(&A.S.tri_nrm[id]);
+        const uint32_t mm = __float_as_uint(nr.w);
+        const float3 nn = xyz(nr);
+        const bool front = dot3(wk, nn) < 0.0f;
+        const float3 nin = front ? nn : nn * -1.0f;
+        const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+        const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+        const float c1 = med.c[m1], c2 = med.c[m2], r1 = med.rho[m1], r2 = med.rho[m2];
+        const Iface f = iface(wk, nin, c1, c2, r1, r2);
+        const uint32_t choice = (r >> 22) & 3u;
+        t1b = tb;
+        xb = ob;
+        float cib = 0.0f, ctb = 0.0f, rb = 0.0f, Rb = 0.0f, Tb = 0.0f;
+        if (choice == CH_TIR || f.tir) {
+          a1b = ab;
+          wpb = wb;
+          cib += 2.0f * dot3(wb, nin);
+        } else if (choice == CH_REFLECT) {
+          if (q.split_mode == 0) {
+            a1b = ab / f.R;
+            Rb = ab * a1 * (-1.0f / (f.R * f.R));
+          } else {
+            a1b = ab * (f.R / q.split_q);
+            Rb = ab * a1 / q.split_q;
+          }
+          wpb = wb;
+          cib += 2.0f * dot3(wb, nin);
+        } else {
+          if (q.split_mode == 0) {
+            const float om = 1.0f - f.R;
+            a1b = ab / om;
+            Rb = ab * a1 / (om * om);
+          } else {
+            a1b = ab * (f.T / (1.0f - q.split_q));
+            Tb = ab * a1 / (1.0f - q.split_q);
+          }
+          wpb = wb * f.r;
+          rb += dot3(wb, wk + nin * f.ci);
+          const float wn = dot3(wb, nin);
+          cib += f.r * wn;
+          ctb -= wn;
+        }
+        if (!f.tir && choice != CH_TIR) {
+          const float Av = r2 * c2 * f.ci, Bv = r1 * c1 * f.ct;
+          const float den = Av + Bv;
+          const float den2 = den * den;
+          const float Ab = (Rb + Tb) * 2.0f * Bv / den2;
+          const float Bb = -(Rb + Tb) * 2.0f * Av / den2;
+          ADD(acc[3 * m2 + 1], Ab * c2 * f.ci);
+          float c2b = Ab * r2 * f.ci;
+          cib += Ab * r2 * c2;
+          ADD(acc[3 * m1 + 1], Bb * c1 * f.ct);
+          float c1b = Bb * r1 * f.ct;
+          ctb += Bb * r1 * c1;
+          if (f.ct > 0.0f) {
+            const float si2 = fmaxf(0.0f, 1.0f - f.ci * f.ci);
+            rb += ctb * (-f.r * si2 / f.ct);
+            cib += ctb * (-f.r * f.r / (2.0f * f.ct)) * (-2.0f * f.ci);
+          }
+          c2b += rb / c1;
+          c1b += -rb * c2 / (c1 * c1);
+          ADD(acc[3 * m2 + 0], c2b);
+          ADD(acc[3 * m1 + 0], c1b);
+        }
+        wpb = wpb + nin * (-cib);
+      } else {  // scatterer
+        a1b = ab + SA[k];
+        t1b = tb + ST[k];
+        xb = ob;
+        wpb = wb;
+      }
+      // segment x = o + w t, a1 = a att(t), tau1 = tau + t / c
+      float ttb = dot3(xb, wk);
+      float3 obn = xb;
+      float3 wbn = wpb + xb * t;
+      const float attb = a1b * ak;
+      const float gatt = attb * att * (-kap);
+      ADD(acc[3 * mk + 2], gatt * med.f0 * t);
+      ADD(acc[iF0], gatt * med.al[mk] * t);
+      ttb += gatt * med.al[mk] * med.f0;
+      const float cm = med.c[mk];
+      ttb += t1b / cm;
+      ADD(acc[3 * mk + 0], -t1b * t / (cm * cm));
+      if (cls == CLS_TRI) {
+        const float3 n = xyz(__ldg(&A.S.tri_nrm[id]));
+        const float den = dot3(wk, n);
+        obn = obn + n * (-ttb / den);
+        wbn = wbn + n * (-ttb * t / den);
+      } else if (cls == CLS_SCAT) {
+        const float3 pp = xyz(__ldg(&A.S.scat[id]));
+        obn = obn + wk * (-ttb);
+        wbn = wbn + (pp - ok) * ttb;
+      } else {
+        obn.z += -ttb / wk.z;
+        wbn.z += ttb * ok.z / (wk.z * wk.z);
+      }
+      ab = a1b * att;
+      tb = t1b;
+      ob = obn;
+      wb = wbn;
+    }
+  }
+  __syncthreads();
+  float* out = A.gpart + (size_t)blockIdx.x * P;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    float s = 0.0f;
+    for (int t = 0; t < (int)blockDim.x; ++t) s += gsm[t * PS + p];
+    out[p] = (A.accumulate ? out[p] : 0.0f) + s;
+  }
+}
+
+__global__ void k_grad_reduce(const float* gpart, int nblocks, int P, float* g) {
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    float s = 0.0f;
+    for (int b = 0; b < nblocks; ++b) s += gpart[(size_t)b * P + p];
+    g[p] = s;
+  }
+}
+
+// S1 as a standalone stream: Philox blocks with consecutive first counter words
+__global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                              long long n, uint32_t* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4(c0 + (uint32_t)i, c1, c2, c3), make_uint2(k0, k1));
+    reinterpret_cast<uint4*>(out)[i] = r;
+  }
+}
+
+void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
+  k_path_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);
+}
+cudaError_t adjoint_set_attrs() {
+  return cudaFuncSetAttribute(k_path_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P)));
+}
+void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st) {
+  k_grad_reduce<<<1, 128, 0, st>>>(gpart, nblocks, P, g);
+}
+void launch_splat_adjoint(const Acq& q, const PulseP& P, const int32_t* tx, const int32_t* e, const float* tau,
+                          const float* a, long long n, const float* grf, float* ga, float* gt, float* gf, int grid,
+                          cudaStream_t st) {
+  k_splat_adjoint<<<grid, 256, 0, st>>>(q, P, tx, e, tau, a, n, grf, ga, gt, gf);
+}
+void launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, long long n,
+                        uint32_t* out, int grid, cudaStream_t st) {
+  k_philox_fill<<<grid, 256, 0, st>>>(c0, c1, c2, c3, k0, k1, n, out);
+}
+
+}  // namespace usrt

@@ -1,0 +1,38 @@
+// Adjoint kernels interface.
+#pragma once
+
+#include "usrt_device.cuh"
+
+namespace usrt {
+
+constexpr int MAX_P = 3 * MAX_MEDIA + 2;
+
+struct PulseP {
+  float f0, sig, fs, half;  // half = 4 sqrt(sigma) fs (support in samples)
+  int ns;
+};
+
+struct AdjArgs {
+  SceneDev S;
+  Media med;
+  Acq acq;
+  PulseP pulse;
+  const uint32_t* record;  // (path - path_base) * (kmax + 1) + k
+  long long path_base;
+  uint32_t n_paths;
+  const float* grf;        // dL/dRF [ntx][ne][ns]
+  float* gpart;            // [gridDim.x][P] per-block partial gradients
+  int P;
+  int accumulate;          // add into gpart instead of overwriting
+};
+
+void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
+cudaError_t adjoint_set_attrs();
+void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st);
+void launch_splat_adjoint(const Acq& q, const PulseP& P, const int32_t* tx, const int32_t* e, const float* tau,
+                          const float* a, long long n, const float* grf, float* ga, float* gt, float* gf, int grid,
+                          cudaStream_t st);
+void launch_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1, long long n,
+                        uint32_t* out, int grid, cudaStream_t st);
+
+}  // namespace usrt

@@ -1,0 +1,765 @@
+// C ABI of the usrt library (include/usrt.h): context, resident scenes, grow-only workspaces
+// charged against a memory budget, and the entry points that sequence the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/usrt.h"
+#include "adjoint.cuh"
+#include "bvh_build.h"
+#include "image.cuh"
+#include "splat.cuh"
+#include "transport.cuh"
+
+using namespace usrt;
+
+namespace {
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+enum Slot {
+  W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
+  W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
+  W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_COUNT
+};
+
+struct SceneGPU {
+  SceneDev dev;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  int n_media_hint = 0;
+  int depth = 0;
+};
+
+struct RecordKey {
+  uint64_t scene = 0, seed = 0;
+  std::vector<float> theta;
+  std::vector<char> acq;  // bytes of the packed Acq
+  long long n_paths = 0;
+  bool valid = false;
+};
+
+}  // namespace
+
+struct us_ctx {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  std::string err;
+  std::map<uint64_t, SceneGPU> scenes;
+  uint64_t next_id = 1;
+  Buf ws[W_COUNT];
+  Buf record;
+  RecordKey rkey;
+  int num_sms = 148;
+  Counters* h_cnt = nullptr;  // pinned copy of the last forward's counters
+  cudaEvent_t ev_stats = nullptr;
+  long long last_paths = 0;
+  bool stats_valid = false;
+};
+
+namespace {
+
+int fail(us_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return fail(ctx, US_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKS(expr)                 \
+  do {                            \
+    int s_ = (expr);              \
+    if (s_ != US_OK) return s_;   \
+  } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int dev_alloc(us_ctx* ctx, void** p, size_t bytes) {
+  if (ctx->budget && ctx->used + bytes > ctx->budget)
+    return fail(ctx, US_ERR_OOM, "memory budget exceeded: %zu used + %zu requested > %zu", ctx->used, bytes,
+                ctx->budget);
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, US_ERR_OOM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  ctx->used += bytes;
+  return US_OK;
+}
+
+void dev_free(us_ctx* ctx, void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  ctx->used -= bytes;
+}
+
+// grow-only workspace; growing synchronises the stream before freeing the old buffer
+int ws_get(us_ctx* ctx, int slot, size_t bytes, cudaStream_t st, void** out) {
+  Buf& b = ctx->ws[slot];
+  if (b.cap < bytes) {
+    if (b.p) {
+      CK(cudaStreamSynchronize(st));
+      dev_free(ctx, b.p, b.cap);
+      b.p = nullptr;
+      b.cap = 0;
+    }
+    size_t want = bytes + bytes / 8 + 256;
+    CKS(dev_alloc(ctx, &b.p, want));
+    b.cap = want;
+  }
+  *out = b.p;
+  return US_OK;
+}
+template <class T>
+int ws(us_ctx* ctx, int slot, size_t count, cudaStream_t st, T** out) {
+  void* p;
+  CKS(ws_get(ctx, slot, sizeof(T) * count, st, &p));
+  *out = (T*)p;
+  return US_OK;
+}
+
+int grid_of(us_ctx* ctx, int per_sm) { return ctx->num_sms * per_sm; }
+
+int make_media(us_ctx* ctx, const float* theta, int M, Media& med) {
+  if (!theta) return fail(ctx, US_ERR_ARG, "theta is NULL");
+  if (M < 1 || M > MAX_MEDIA) return fail(ctx, US_ERR_ARG, "n_media %d outside [1, %d]", M, MAX_MEDIA);
+  std::memset(&med, 0, sizeof med);
+  med.M = M;
+  for (int m = 0; m < M; ++m) {
+    med.c[m] = theta[3 * m];
+    med.rho[m] = theta[3 * m + 1];
+    med.al[m] = theta[3 * m + 2];
+    if (!(med.c[m] > 0) || !(med.rho[m] > 0)) return fail(ctx, US_ERR_ARG, "medium %d: c and rho must be > 0", m);
+  }
+  med.As = theta[3 * M];
+  med.f0 = theta[3 * M + 1];
+  if (!(med.f0 > 0)) return fail(ctx, US_ERR_ARG, "f0 must be > 0");
+  return US_OK;
+}
+
+int make_acq(us_ctx* ctx, const us_acq_desc* d, uint64_t seed, Acq& q) {
+  if (!d) return fail(ctx, US_ERR_ARG, "acq is NULL");
+  std::memset(&q, 0, sizeof q);
+  if (d->n_elem < 1 || d->n_elem > MAX_ELEM) return fail(ctx, US_ERR_ARG, "n_elem %d outside [1, %d]", d->n_elem, MAX_ELEM);
+  if (d->n_tx < 1 || d->n_tx > MAX_TX) return fail(ctx, US_ERR_ARG, "n_tx %d outside [1, %d]", d->n_tx, MAX_TX);
+  if (!d->angles) return fail(ctx, US_ERR_ARG, "angles is NULL");
+  if (d->k_max < 0 || d->k_max > MAX_KMAX) return fail(ctx, US_ERR_ARG, "k_max %d outside [0, %d]", d->k_max, MAX_KMAX);
+  if (d->n_samples < 4 || d->n_samples % 4 || d->n_samples > MAX_SPLAT_NS)
+    return fail(ctx, US_ERR_ARG, "n_samples %d: multiple of 4 in [4, %d]", d->n_samples, MAX_SPLAT_NS);
+  if (d->n_rays < 1) return fail(ctx, US_ERR_ARG, "n_rays must be >= 1");
+  if (d->tx_elem >= d->n_elem) return fail(ctx, US_ERR_ARG, "tx_elem %d >= n_elem", d->tx_elem);
+  if (!(d->fs > 0) || !(d->pitch > 0) || !(d->c_bf > 0) || !(d->bw > 0))
+    return fail(ctx, US_ERR_ARG, "fs, pitch, c_bf and bw must be > 0");
+  if (d->split_mode != 0 && !(d->split_q > 0 && d->split_q < 1))
+    return fail(ctx, US_ERR_ARG, "split_q must lie in (0, 1)");
+  q.ne = d->n_elem;
+  q.ntx = d->n_tx;
+  q.ns = d->n_samples;
+  q.kmax = d->k_max;
+  q.nr = d->n_rays;
+  q.tx_elem = d->tx_elem < 0 ? -1 : d->tx_elem;
+  q.n_emit = q.tx_elem < 0 ? q.ne : 1;
+  q.split_mode = d->split_mode;
+  q.pitch = d->pitch;
+  q.hel = d->h_el;
+  q.fs = d->fs;
+  q.bw = d->bw;
+  q.alpha_m = d->alpha_m;
+  q.alpha_c = d->alpha_c;
+  q.cbf = d->c_bf;
+  q.split_q = d->split_q;
+  q.stream = d->stream_id;
+  q.key0 = (uint32_t)seed;
+  q.key1 = (uint32_t)(seed >> 32);
+  q.rays_per_tx = (long long)q.n_emit * q.nr;
+  for (int t = 0; t < q.ntx; ++t) {
+    q.sin_tx[t] = (float)std::sin((double)d->angles[t]);
+    q.cos_tx[t] = (float)std::cos((double)d->angles[t]);
+    q.cos_lo[t] = (float)(std::cos((double)d->angles[t]) - (double)q.cos_tx[t]);
+  }
+  if (q.rays_per_tx * q.ntx >= (1ll << 32) - 1) return fail(ctx, US_ERR_ARG, "too many paths (>= 2^32)");
+  if ((long long)q.ntx * q.ne > 16384) return fail(ctx, US_ERR_ARG, "n_tx * n_elem > 16384");
+  return US_OK;
+}
+
+int make_img(us_ctx* ctx, const us_img_desc* d, Img& im) {
+  if (!d) return fail(ctx, US_ERR_ARG, "img is NULL");
+  if (d->n_lines < 1) return fail(ctx, US_ERR_ARG, "n_lines must be >= 1");
+  if (d->n_depth < 16 || d->n_depth > 4096 || (d->n_depth & (d->n_depth - 1)))
+    return fail(ctx, US_ERR_ARG, "n_depth %d: power of two in [16, 4096]", d->n_depth);
+  im.nl = d->n_lines;
+  im.nd = d->n_depth;
+  im.x0 = d->x0;
+  im.x1 = d->x1;
+  im.z0 = d->z0;
+  im.z1 = d->z1;
+  im.dr = d->dr_db;
+  im.l1 = d->lambda1;
+  im.l2 = d->lambda2;
+  return US_OK;
+}
+
+int splat_geom(us_ctx* ctx, const Acq& q, float f0, SplatGeom& g, PulseP& P) {
+  const double sig = 4.0 * std::log(2.0) / (M_PI * M_PI * (double)q.bw * q.bw * (double)f0 * f0);
+  const double half = 4.0 * std::sqrt(sig) * q.fs;
+  g.nrows = q.ntx * q.ne;
+  g.ns = q.ns;
+  g.nbins = q.ns + 2 * HALO;
+  g.dlo = -(int)std::floor(half);
+  const int dhi = (int)std::floor(half) + 1;
+  g.ntaps = dhi - g.dlo + 1;
+  g.Sig = (float)(sig * (double)q.fs * q.fs);
+  g.Om = (float)(2.0 * M_PI * f0 / q.fs);
+  if (g.ntaps > MAX_TAPS || dhi > HALO)
+    return fail(ctx, US_ERR_ARG, "pulse support %.1f samples exceeds the splat window (%d)", half, HALO);
+  P.f0 = f0;
+  P.sig = (float)sig;
+  P.fs = q.fs;
+  P.half = (float)half;
+  P.ns = q.ns;
+  return US_OK;
+}
+
+SceneGPU* get_scene(us_ctx* ctx, uint64_t id) {
+  auto it = ctx->scenes.find(id);
+  if (it == ctx->scenes.end()) {
+    fail(ctx, US_ERR_ARG, "unknown scene id %llu", (unsigned long long)id);
+    return nullptr;
+  }
+  return &it->second;
+}
+
+int set_attrs(us_ctx* ctx) {
+  SplatGeom g;
+  g.nbins = MAX_SPLAT_NS + 2 * HALO;
+  g.ntaps = MAX_TAPS;
+  CK(splat_set_attrs(g));
+  CK(row_scatter_set_attrs(16384));
+  CK(row_hist_set_attrs(16384));
+  CK(image_set_attrs(4096));
+  CK(adjoint_set_attrs());
+  return US_OK;
+}
+
+struct Queues {
+  PathQ a, b;
+};
+
+int alloc_queues(us_ctx* ctx, long long n, cudaStream_t st, Queues& Q) {
+  CKS(ws(ctx, W_QA_PA, n, st, &Q.a.pa));
+  CKS(ws(ctx, W_QA_WT, n, st, &Q.a.wt));
+  CKS(ws(ctx, W_QA_META, n, st, &Q.a.meta));
+  CKS(ws(ctx, W_QB_PA, n, st, &Q.b.pa));
+  CKS(ws(ctx, W_QB_WT, n, st, &Q.b.wt));
+  CKS(ws(ctx, W_QB_META, n, st, &Q.b.meta));
+  return US_OK;
+}
+
+// transport of paths [path0, path0 + n): generate + (k_max + 1) rounds of traverse / interact /
+// secondary rays.  arr may be null (no arrivals: decisions only).
+int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& q, long long path0, uint32_t n,
+                  Arrival* arr, uint32_t arr_cap, uint32_t* record, bool do_nee, Counters* cnt, cudaStream_t st) {
+  Queues Q;
+  CKS(alloc_queues(ctx, n, st, Q));
+  TransportArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.S = sc->dev;
+  A.med = med;
+  A.acq = q;
+  CKS(ws(ctx, W_HITS, n, st, &A.hits));
+  CKS(ws(ctx, W_NEE_JOB, n, st, &A.nee.job));
+  CKS(ws(ctx, W_NEE_JM, n, st, &A.nee.jm));
+  A.arr = arr;
+  A.arr_cap = arr_cap;
+  A.record = record;
+  A.path_base = path0;
+  A.cnt = cnt;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
+  if (record) CK(cudaMemsetAsync(record, 0, sizeof(uint32_t) * (size_t)n * (q.kmax + 1), st));
+  A.qout = Q.a;
+  launch_generate(A, path0, n, grid_of(ctx, 8), st);
+  for (int k = 0; k <= q.kmax; ++k) {
+    A.k = k;
+    A.qin = (k & 1) ? Q.b : Q.a;
+    A.qout = (k & 1) ? Q.a : Q.b;
+    launch_traverse(A, grid_of(ctx, 16), st);
+    launch_interact(A, grid_of(ctx, 8), st);
+    if (do_nee && sc->dev.n_scat > 0) launch_nee(A, grid_of(ctx, 16), st);
+  }
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int do_splat(us_ctx* ctx, const Acq& q, float f0, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, float* rf,
+             cudaStream_t st) {
+  SplatGeom g;
+  PulseP P;
+  CKS(splat_geom(ctx, q, f0, g, P));
+  SplatWork w;
+  CKS(ws(ctx, W_ROW_CNT, g.nrows, st, &w.row_cnt));
+  CKS(ws(ctx, W_ROW_OFF, g.nrows + 1, st, &w.row_off));
+  CKS(ws(ctx, W_ROW_CUR, g.nrows, st, &w.row_cursor));
+  CKS(ws(ctx, W_BUCKET, (size_t)cap + 1, st, &w.bucket));
+  CKS(ws(ctx, W_SCRATCH, (size_t)cap + 1, st, &w.scratch));
+  float* G;
+  CKS(ws(ctx, W_GTAB, K_MOM * MAX_TAPS, st, &G));
+  launch_pulse_table(g, G, st);
+  launch_splat(g, arr, n_arr, cap, w, G, rf, grid_of(ctx, 4), st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* bmode, cudaStream_t st) {
+  float *irf, *env;
+  unsigned long long* key;
+  CKS(ws(ctx, W_IRF, (size_t)im.nl * im.nd, st, &irf));
+  CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
+  CKS(ws(ctx, W_KEY, 1, st, &key));
+  launch_das(q, im, rf, irf, grid_of(ctx, 8), st);
+  launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+}  // namespace
+
+// =========================================================================================
+extern "C" {
+
+int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return US_ERR_ARG;
+  *out = nullptr;
+  us_ctx* ctx = new us_ctx();
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return US_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost((void**)&ctx->h_cnt, sizeof(Counters)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_stats, cudaEventDisableTiming) != cudaSuccess) {
+    delete ctx;
+    return US_ERR_CUDA;
+  }
+  if (set_attrs(ctx) != US_OK) {
+    delete ctx;
+    return US_ERR_CUDA;
+  }
+  *out = ctx;
+  return US_OK;
+}
+
+void us_destroy(us_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->scenes)
+    for (void* p : kv.second.allocs) cudaFree(p);
+  for (int i = 0; i < W_COUNT; ++i)
+    if (ctx->ws[i].p) cudaFree(ctx->ws[i].p);
+  if (ctx->record.p) cudaFree(ctx->record.p);
+  if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  if (ctx->ev_stats) cudaEventDestroy(ctx->ev_stats);
+  delete ctx;
+}
+
+const char* us_last_error(us_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int us_memory(us_ctx* ctx, size_t* used, size_t* budget) {
+  if (!ctx) return US_ERR_ARG;
+  if (used) *used = ctx->used;
+  if (budget) *budget = ctx->budget;
+  return US_OK;
+}
+
+int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
+  if (!ctx || !d || !scene_id) return fail(ctx, US_ERR_ARG, "null argument");
+  if (d->n_tris < 0 || d->n_scat < 0 || (d->n_tris && (!d->tris || !d->media)) ||
+      (d->n_scat && (!d->scat_pos || !d->scat_amp)))
+    return fail(ctx, US_ERR_ARG, "invalid scene arrays");
+  if (d->n_tris >= (1 << 20) || d->n_scat >= (1 << 20))
+    return fail(ctx, US_ERR_ARG, "at most 2^20 - 1 triangles and scatterers");
+  if (d->n_media < 1 || d->n_media > MAX_MEDIA) return fail(ctx, US_ERR_ARG, "n_media outside [1, %d]", MAX_MEDIA);
+  for (int i = 0; i < 2 * d->n_tris; ++i)
+    if (d->media[i] < 0 || d->media[i] >= d->n_media) return fail(ctx, US_ERR_ARG, "triangle medium out of range");
+  CK(cudaSetDevice(ctx->device));
+  HostSceneIn in;
+  in.n_tris = d->n_tris;
+  in.tris = d->tris;
+  in.media = d->media;
+  in.n_scat = d->n_scat;
+  in.scat_pos = d->scat_pos;
+  in.scat_amp = d->scat_amp;
+  in.r_s = d->r_s;
+  HostSceneOut o;
+  build_scene_host(in, o);
+  SceneGPU sc;
+  sc.n_media_hint = d->n_media;
+  auto up = [&](const std::vector<float>& v, const float4** dst) -> int {
+    void* p = nullptr;
+    size_t bytes = v.size() * sizeof(float);
+    CKS(dev_alloc(ctx, &p, bytes));
+    sc.allocs.push_back(p);
+    sc.bytes += bytes;
+    if (bytes) CK(cudaMemcpy(p, v.data(), bytes, cudaMemcpyHostToDevice));
+    *dst = (const float4*)p;
+    return US_OK;
+  };
+  int s;
+  if ((s = up(o.nodes, &sc.dev.nodes)) || (s = up(o.prims, &sc.dev.prims)) || (s = up(o.tri_nrm, &sc.dev.tri_nrm)) ||
+      (s = up(o.tri_v0, &sc.dev.tri_v0)) || (s = up(o.scat, &sc.dev.scat)) ||
+      (s = up(o.nodes_t, &sc.dev.nodes_t)) || (s = up(o.prims_t, &sc.dev.prims_t))) {
+    for (void* p : sc.allocs) cudaFree(p);
+    ctx->used -= sc.bytes;
+    return s;
+  }
+  sc.dev.n_nodes = o.n_nodes;
+  sc.dev.n_tris = d->n_tris;
+  sc.dev.n_scat = d->n_scat;
+  sc.dev.rs2 = d->r_s * d->r_s;
+  // depth check: the traversal stacks hold 64 entries
+  sc.depth = std::max(o.depth, o.depth_t);
+  if (sc.depth > 60) {
+    for (void* p : sc.allocs) cudaFree(p);
+    ctx->used -= sc.bytes;
+    return fail(ctx, US_ERR_ARG, "BVH depth %d exceeds the traversal stack", sc.depth);
+  }
+  uint64_t id = ctx->next_id++;
+  ctx->scenes[id] = sc;
+  *scene_id = id;
+  return US_OK;
+}
+
+int us_scene_release(us_ctx* ctx, uint64_t scene_id) {
+  if (!ctx) return US_ERR_ARG;
+  SceneGPU* sc = get_scene(ctx, scene_id);
+  if (!sc) return US_ERR_ARG;
+  CK(cudaDeviceSynchronize());
+  for (void* p : sc->allocs) cudaFree(p);
+  ctx->used -= sc->bytes;
+  ctx->scenes.erase(scene_id);
+  if (ctx->rkey.scene == scene_id) ctx->rkey.valid = false;
+  return US_OK;
+}
+
+int us_philox_fill(us_ctx* ctx, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
+                   int64_t n, uint32_t* out_dev, void* stream) {
+  if (!ctx || (n > 0 && !out_dev) || n < 0) return fail(ctx, US_ERR_ARG, "invalid arguments");
+  if (!aligned16(out_dev)) return fail(ctx, US_ERR_ARG, "out_dev must be 16-byte aligned");
+  if (n == 0) return US_OK;
+  launch_philox_fill(c0, c1, c2, c3, k0, k1, n, out_dev, grid_of(ctx, 8), (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+               uint64_t seed, int keep_record, float* rf_dev, float* bmode_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  SceneGPU* sc = get_scene(ctx, scene);
+  if (!sc) return US_ERR_ARG;
+  if (!rf_dev || !aligned16(rf_dev) || (bmode_dev && !aligned16(bmode_dev)))
+    return fail(ctx, US_ERR_ARG, "rf_dev / bmode_dev must be non-null (rf) and 16-byte aligned");
+  Media med;
+  Acq q;
+  Img im;
+  CKS(make_media(ctx, theta, sc->n_media_hint, med));
+  CKS(make_acq(ctx, acq, seed, q));
+  if (bmode_dev) CKS(make_img(ctx, img, im));
+  const long long n_paths = q.rays_per_tx * q.ntx;
+  const long long cap_ll = n_paths * (q.kmax + 1);
+  const uint32_t cap = (uint32_t)std::min<long long>(cap_ll, 0xFFFFFFF0ll);
+  Arrival* arr;
+  Counters* cnt;
+  CKS(ws(ctx, W_ARR, cap, st, &arr));
+  CKS(ws(ctx, W_CNT, 1, st, &cnt));
+  uint32_t* record = nullptr;
+  if (keep_record) {
+    size_t bytes = sizeof(uint32_t) * (size_t)n_paths * (q.kmax + 1);
+    if (ctx->record.cap < bytes) {
+      if (ctx->record.p) {
+        CK(cudaStreamSynchronize(st));
+        dev_free(ctx, ctx->record.p, ctx->record.cap);
+        ctx->record.p = nullptr;
+        ctx->record.cap = 0;
+      }
+      CKS(dev_alloc(ctx, &ctx->record.p, bytes));
+      ctx->record.cap = bytes;
+    }
+    record = (uint32_t*)ctx->record.p;
+  }
+  CKS(run_transport(ctx, sc, med, q, 0, (uint32_t)n_paths, arr, cap, record, true, cnt, st));
+  CKS(do_splat(ctx, q, med.f0, arr, &cnt->n_arr, cap, rf_dev, st));
+  if (bmode_dev) CKS(do_bmode(ctx, q, im, rf_dev, bmode_dev, st));
+  CK(cudaMemcpyAsync(ctx->h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(ctx->ev_stats, st));
+  ctx->last_paths = n_paths;
+  ctx->stats_valid = true;
+  if (keep_record) {
+    ctx->rkey.scene = scene;
+    ctx->rkey.seed = seed;
+    ctx->rkey.theta.assign(theta, theta + 3 * sc->n_media_hint + 2);
+    ctx->rkey.acq.assign((const char*)&q, (const char*)&q + sizeof q);
+    ctx->rkey.n_paths = n_paths;
+    ctx->rkey.valid = true;
+  }
+  return US_OK;
+}
+
+int us_get_stats(us_ctx* ctx, us_stats* out) {
+  if (!ctx || !out) return US_ERR_ARG;
+  if (!ctx->stats_valid) return fail(ctx, US_ERR_STATE, "no forward pass yet");
+  CK(cudaEventSynchronize(ctx->ev_stats));
+  const Counters& c = *ctx->h_cnt;
+  out->n_paths = ctx->last_paths;
+  long long seg = 0, nee = 0;
+  for (int k = 0; k <= MAX_KMAX; ++k) {
+    seg += c.live[k];
+    nee += c.nee[k];
+  }
+  out->segments = seg;
+  out->nee_queries = nee;
+  out->arrivals = c.n_arr;
+  out->dropped = c.dropped;
+  out->status = (c.status & ST_OVERFLOW) ? US_ERR_OVERFLOW : (c.status & ST_TIMEOUT ? US_ERR_TIMEOUT : 0);
+  return US_OK;
+}
+
+int us_get_record(us_ctx* ctx, int64_t path_lo, int64_t n, uint32_t* out_dev, void* stream) {
+  if (!ctx || !out_dev || n < 0 || path_lo < 0) return fail(ctx, US_ERR_ARG, "invalid arguments");
+  if (!ctx->rkey.valid) return fail(ctx, US_ERR_STATE, "no record kept");
+  if (path_lo + n > ctx->rkey.n_paths) return fail(ctx, US_ERR_ARG, "path range outside the record");
+  const Acq* q = (const Acq*)ctx->rkey.acq.data();
+  const size_t K1 = q->kmax + 1;
+  CK(cudaMemcpyAsync(out_dev, (uint32_t*)ctx->record.p + (size_t)path_lo * K1, sizeof(uint32_t) * (size_t)n * K1,
+                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return US_OK;
+}
+
+int us_splat(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int32_t* tx_dev, const int32_t* e_dev,
+             const float* tau_dev, const float* a_dev, float* rf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Acq q;
+  CKS(make_acq(ctx, acq, 0, q));
+  if (n < 0 || n >= 0xFFFFFFF0ll || !rf_dev || !aligned16(rf_dev) || (n && (!tx_dev || !e_dev || !tau_dev || !a_dev)))
+    return fail(ctx, US_ERR_ARG, "invalid arrival list");
+  Arrival* arr;
+  uint32_t* n_out;
+  CKS(ws(ctx, W_PACK, (size_t)n + 1, st, &arr));
+  CKS(ws(ctx, W_NPACK, 1, st, &n_out));
+  CK(cudaMemsetAsync(n_out, 0, sizeof(uint32_t), st));
+  if (n) launch_pack_arrivals(tx_dev, e_dev, tau_dev, a_dev, n, q.ne, q.fs, arr, n_out, grid_of(ctx, 4), st);
+  return do_splat(ctx, q, f0, arr, n_out, (uint32_t)n + 1, rf_dev, st);
+}
+
+int us_das(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev, float* irf_dev,
+           void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  Acq q;
+  Img im;
+  CKS(make_acq(ctx, acq, 0, q));
+  CKS(make_img(ctx, img, im));
+  if (!rf_dev || !irf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  launch_das(q, im, rf_dev, irf_dev, grid_of(ctx, 8), (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* bmode_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Img im;
+  CKS(make_img(ctx, img, im));
+  if (!irf_dev || !bmode_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  float* env;
+  unsigned long long* key;
+  CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
+  CKS(ws(ctx, W_KEY, 1, st, &key));
+  launch_envlog(im, irf_dev, env, key, bmode_dev, grid_of(ctx, 8), st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_bmode(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev, float* bmode_dev,
+             void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  Acq q;
+  Img im;
+  CKS(make_acq(ctx, acq, 0, q));
+  CKS(make_img(ctx, img, im));
+  if (!rf_dev || !bmode_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  return do_bmode(ctx, q, im, rf_dev, bmode_dev, (cudaStream_t)stream);
+}
+
+int us_loss(us_ctx* ctx, const us_img_desc* img, const float* bmode_dev, const float* bref_dev, float* loss_dev,
+            float* dL_dB_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Img im;
+  CKS(make_img(ctx, img, im));
+  if (!bmode_dev || !bref_dev || !loss_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  float* part;
+  const int np = grid_of(ctx, 2);
+  CKS(ws(ctx, W_PART, np, st, &part));
+  launch_loss(im, bmode_dev, bref_dev, dL_dB_dev, part, np, loss_dev, st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_envlog_vjp(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, const float* dL_dB_dev,
+                  float* dL_dirf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Img im;
+  CKS(make_img(ctx, img, im));
+  if (!irf_dev || !dL_dB_dev || !dL_dirf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  float *env, *part, *scal;
+  unsigned long long* key;
+  const int np = grid_of(ctx, 2);
+  CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
+  CKS(ws(ctx, W_KEY, 1, st, &key));
+  CKS(ws(ctx, W_PART, np, st, &part));
+  CKS(ws(ctx, W_SCAL, 4, st, &scal));
+  launch_envlog_vjp(im, irf_dev, dL_dB_dev, env, key, part, np, scal, dL_dirf_dev, grid_of(ctx, 8), st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* dL_dirf_dev,
+                   float* dL_drf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  Acq q;
+  Img im;
+  CKS(make_acq(ctx, acq, 0, q));
+  CKS(make_img(ctx, img, im));
+  if (!dL_dirf_dev || !dL_drf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  launch_das_adj(q, im, dL_dirf_dev, dL_drf_dev, grid_of(ctx, 8), (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+                 const float* dL_dB_dev, float* dL_drf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Acq q;
+  Img im;
+  CKS(make_acq(ctx, acq, 0, q));
+  CKS(make_img(ctx, img, im));
+  if (!rf_dev || !dL_dB_dev || !dL_drf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  float *irf, *gi;
+  CKS(ws(ctx, W_IRF, (size_t)im.nl * im.nd, st, &irf));
+  CKS(ws(ctx, W_GI, (size_t)im.nl * im.nd, st, &gi));
+  launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st);
+  CKS(us_envlog_vjp(ctx, img, irf, dL_dB_dev, gi, stream));
+  launch_das_adj(q, im, gi, dL_drf_dev, grid_of(ctx, 8), st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int32_t* tx_dev,
+                     const int32_t* e_dev, const float* tau_dev, const float* a_dev, const float* dL_drf_dev,
+                     float* ga_dev, float* gt_dev, float* gf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  Acq q;
+  CKS(make_acq(ctx, acq, 0, q));
+  SplatGeom g;
+  PulseP P;
+  CKS(splat_geom(ctx, q, f0, g, P));
+  if (n < 0 || (n && (!tx_dev || !e_dev || !tau_dev || !a_dev || !dL_drf_dev || !ga_dev || !gt_dev || !gf_dev)))
+    return fail(ctx, US_ERR_ARG, "invalid arrival list");
+  if (n) launch_splat_adjoint(q, P, tx_dev, e_dev, tau_dev, a_dev, n, dL_drf_dev, ga_dev, gt_dev, gf_dev,
+                              grid_of(ctx, 4), (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                     int mode, const float* dL_drf_dev, float* dL_dtheta_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  SceneGPU* sc = get_scene(ctx, scene);
+  if (!sc) return US_ERR_ARG;
+  if (!dL_drf_dev || !dL_dtheta_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  Media med;
+  Acq q;
+  CKS(make_media(ctx, theta, sc->n_media_hint, med));
+  CKS(make_acq(ctx, acq, seed, q));
+  SplatGeom g;
+  AdjArgs A;
+  std::memset(&A, 0, sizeof A);
+  CKS(splat_geom(ctx, q, med.f0, g, A.pulse));
+  A.S = sc->dev;
+  A.med = med;
+  A.acq = q;
+  A.grf = dL_drf_dev;
+  A.P = 3 * med.M + 2;
+  const int grid = grid_of(ctx, 8);
+  CKS(ws(ctx, W_GPART, (size_t)grid * A.P, st, &A.gpart));
+  const long long n_paths = q.rays_per_tx * q.ntx;
+  if (mode == 0) {
+    if (!ctx->rkey.valid || ctx->rkey.scene != scene || ctx->rkey.seed != seed || ctx->rkey.n_paths != n_paths ||
+        ctx->rkey.acq.size() != sizeof q || std::memcmp(ctx->rkey.acq.data(), &q, sizeof q) != 0 ||
+        ctx->rkey.theta.size() != (size_t)A.P ||
+        std::memcmp(ctx->rkey.theta.data(), theta, sizeof(float) * A.P) != 0)
+      return fail(ctx, US_ERR_STATE, "record mode needs a forward pass with keep_record on the same inputs");
+    A.record = (const uint32_t*)ctx->record.p;
+    A.path_base = 0;
+    A.n_paths = (uint32_t)n_paths;
+    A.accumulate = 0;
+    launch_path_adjoint(A, grid, st);
+  } else {
+    // recompute: regenerate the decisions chunk by chunk, then sweep each chunk
+    const long long chunk = std::min<long long>(n_paths, 1ll << 22);
+    uint32_t* rec;
+    Counters* cnt;
+    CKS(ws(ctx, W_REC_CHUNK, (size_t)chunk * (q.kmax + 1), st, &rec));
+    CKS(ws(ctx, W_CNT, 1, st, &cnt));
+    for (long long p0 = 0; p0 < n_paths; p0 += chunk) {
+      const uint32_t n = (uint32_t)std::min<long long>(chunk, n_paths - p0);
+      CKS(run_transport(ctx, sc, med, q, p0, n, nullptr, 0, rec, false, cnt, st));
+      A.record = rec;
+      A.path_base = p0;
+      A.n_paths = n;
+      A.accumulate = p0 > 0;
+      launch_path_adjoint(A, grid, st);
+    }
+  }
+  launch_grad_reduce(A.gpart, grid, A.P, dL_dtheta_dev, st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+               uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
+               float* dL_drf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Acq q;
+  CKS(make_acq(ctx, acq, seed, q));
+  float* grf = dL_drf_dev;
+  if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
+  CKS(us_bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream));
+  return us_transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, stream);
+}
+
+}  // extern "C"

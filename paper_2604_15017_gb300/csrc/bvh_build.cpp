@@ -1,0 +1,331 @@
+// Host-side BVH construction for the usrt scene (binned surface-area heuristic).
+//
+// Two BVHs are built: one over triangles and point-scatterer spheres (closest hits of primary
+// rays) and one over triangles only (all-crossings queries of secondary rays, which ignore the
+// scatterers).  The device layout is a BVH2 whose
+// inner nodes hold both children's boxes in four 16-byte words, so a traversal step is four
+// 128-bit loads of one 64-byte (32-byte aligned) node:
+//   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   n2 = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)   n3 = int4(child0, child1, count0, count1)
+// count_i == 0: child_i is an inner node index (or -1 = empty); count_i > 0: child_i is the
+// first primitive of a leaf in the leaf-ordered primitive array.
+#include "bvh_build.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace usrt {
+
+namespace {
+
+struct Box {
+  double lo[3], hi[3];
+  void empty() {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = 1e300;
+      hi[a] = -1e300;
+    }
+  }
+  void grow(const Box& b) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+  }
+  void grow(const double p[3]) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], p[a]);
+      hi[a] = std::max(hi[a], p[a]);
+    }
+  }
+  double area() const {
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = std::max(0.0, hi[a] - lo[a]);
+    return 2.0 * (d[0] * d[1] + d[1] * d[2] + d[2] * d[0]);
+  }
+  bool valid() const { return lo[0] <= hi[0]; }
+};
+
+struct TNode {
+  Box box;
+  int left = -1, right = -1;  // tree children (inner)
+  int first = 0, count = 0;   // leaf range (count > 0)
+};
+
+const int LEAF_MAX = 4;
+const int BINS = 16;
+
+struct Builder {
+  std::vector<Box> pbox;
+  std::vector<double> cen;  // 3 per prim
+  std::vector<int> idx;
+  std::vector<TNode> tree;
+
+  int make_leaf(const Box& b, int first, int count) {
+    TNode n;
+    n.box = b;
+    n.first = first;
+    n.count = count;
+    tree.push_back(n);
+    return (int)tree.size() - 1;
+  }
+
+  int build(int first, int count) {
+    Box b, cb;
+    b.empty();
+    cb.empty();
+    for (int i = first; i < first + count; ++i) {
+      b.grow(pbox[idx[i]]);
+      cb.grow(&cen[3 * (size_t)idx[i]]);
+    }
+    if (count <= LEAF_MAX) return make_leaf(b, first, count);
+    // binned SAH over the three axes
+    int best_axis = -1, best_split = -1;
+    double best_cost = 1e300;
+    for (int a = 0; a < 3; ++a) {
+      double ext = cb.hi[a] - cb.lo[a];
+      if (!(ext > 0)) continue;
+      Box bins[BINS];
+      int cnt[BINS];
+      for (int k = 0; k < BINS; ++k) {
+        bins[k].empty();
+        cnt[k] = 0;
+      }
+      double scale = BINS / ext;
+      for (int i = first; i < first + count; ++i) {
+        int k = std::min(BINS - 1, (int)((cen[3 * (size_t)idx[i] + a] - cb.lo[a]) * scale));
+        bins[k].grow(pbox[idx[i]]);
+        cnt[k]++;
+      }
+      double rarea[BINS];
+      int rcnt[BINS];
+      Box acc;
+      acc.empty();
+      int c = 0;
+      for (int k = BINS - 1; k > 0; --k) {
+        if (cnt[k]) acc.grow(bins[k]);
+        c += cnt[k];
+        rarea[k] = acc.valid() ? acc.area() : 0.0;
+        rcnt[k] = c;
+      }
+      acc.empty();
+      c = 0;
+      for (int k = 0; k < BINS - 1; ++k) {
+        if (cnt[k]) acc.grow(bins[k]);
+        c += cnt[k];
+        if (c == 0 || rcnt[k + 1] == 0) continue;
+        double cost = (acc.valid() ? acc.area() : 0.0) * c + rarea[k + 1] * rcnt[k + 1];
+        if (cost < best_cost) {
+          best_cost = cost;
+          best_axis = a;
+          best_split = k;
+        }
+      }
+    }
+    int mid;
+    if (best_axis < 0) {
+      // all centroids coincide: split the range in half
+      mid = first + count / 2;
+    } else {
+      double ext = cb.hi[best_axis] - cb.lo[best_axis];
+      double scale = BINS / ext;
+      auto it = std::partition(idx.begin() + first, idx.begin() + first + count, [&](int p) {
+        int k = std::min(BINS - 1, (int)((cen[3 * (size_t)p + best_axis] - cb.lo[best_axis]) * scale));
+        return k <= best_split;
+      });
+      mid = (int)(it - idx.begin());
+      if (mid == first || mid == first + count) mid = first + count / 2;
+    }
+    int me = (int)tree.size();
+    tree.push_back(TNode());
+    tree[me].box = b;
+    int l = build(first, mid - first);
+    int r = build(mid, first + count - mid);
+    tree[me].left = l;
+    tree[me].right = r;
+    return me;
+  }
+};
+
+float round_down(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = std::nextafter(f, -INFINITY);
+  return f;
+}
+float round_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = std::nextafter(f, INFINITY);
+  return f;
+}
+float bits_f(uint32_t u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace
+
+// BVH over the primitive subset `ids` (0..nt-1 triangles, nt.. scatterers): device nodes and
+// primitives in leaf order
+static void build_one(const HostSceneIn& in, const std::vector<int>& ids, std::vector<float>& nodes_out,
+                      std::vector<float>& prims_out, int& n_nodes_out, int& depth_out) {
+  const int nt = in.n_tris;
+  const int n = (int)ids.size();
+  Builder B;
+  B.pbox.resize(n);
+  B.cen.resize(3 * (size_t)n);
+  B.idx.resize(n);
+  for (int k = 0; k < n; ++k) {
+    const int i = ids[k];
+    Box b;
+    if (i < nt) {
+      b.empty();
+      for (int v = 0; v < 3; ++v) {
+        double p[3] = {in.tris[9 * (size_t)i + 3 * v], in.tris[9 * (size_t)i + 3 * v + 1], in.tris[9 * (size_t)i + 3 * v + 2]};
+        b.grow(p);
+      }
+    } else {
+      const int j = i - nt;
+      for (int a = 0; a < 3; ++a) {
+        b.lo[a] = (double)in.scat_pos[3 * (size_t)j + a] - in.r_s;
+        b.hi[a] = (double)in.scat_pos[3 * (size_t)j + a] + in.r_s;
+      }
+    }
+    B.pbox[k] = b;
+    for (int a = 0; a < 3; ++a) B.cen[3 * (size_t)k + a] = 0.5 * (b.lo[a] + b.hi[a]);
+    B.idx[k] = k;
+  }
+  B.tree.reserve(2 * (size_t)n + 2);
+  int root = n ? B.build(0, n) : -1;
+
+  // device nodes: one per inner tree node, DFS order; a leaf root gets a wrapper node
+  std::vector<int> gpu_index(B.tree.size(), -1);
+  std::vector<int> depth(B.tree.size(), 0);
+  std::vector<int> order;  // inner tree nodes in DFS order
+  int maxd = 1;
+  if (root >= 0) {
+    std::vector<int> st(1, root);
+    depth[root] = 1;
+    while (!st.empty()) {
+      int t = st.back();
+      st.pop_back();
+      maxd = std::max(maxd, depth[t]);
+      if (B.tree[t].count > 0) continue;
+      gpu_index[t] = (int)order.size();
+      order.push_back(t);
+      depth[B.tree[t].left] = depth[B.tree[t].right] = depth[t] + 1;
+      st.push_back(B.tree[t].right);
+      st.push_back(B.tree[t].left);
+    }
+  }
+  depth_out = maxd;
+  auto child_fields = [&](int c, float* lo, float* hi, int& ci, int& cnt) {
+    if (c < 0) {
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = 1.0f;
+        hi[a] = -1.0f;  // never traversed: count 0 and index -1
+      }
+      ci = -1;
+      cnt = 0;
+      return;
+    }
+    const TNode& t = B.tree[c];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = round_down(t.box.lo[a]);
+      hi[a] = round_up(t.box.hi[a]);
+    }
+    if (t.count > 0) {
+      ci = t.first;
+      cnt = t.count;
+    } else {
+      ci = gpu_index[c];
+      cnt = 0;
+    }
+  };
+  nodes_out.clear();
+  auto emit = [&](int c0, int c1) {
+    float lo0[3], hi0[3], lo1[3], hi1[3];
+    int i0, i1, n0, n1;
+    child_fields(c0, lo0, hi0, i0, n0);
+    child_fields(c1, lo1, hi1, i1, n1);
+    float w[16] = {lo0[0], hi0[0], lo0[1], hi0[1], lo1[0], hi1[0], lo1[1], hi1[1],
+                   lo0[2], hi0[2], lo1[2], hi1[2], bits_f((uint32_t)i0), bits_f((uint32_t)i1),
+                   bits_f((uint32_t)n0), bits_f((uint32_t)n1)};
+    nodes_out.insert(nodes_out.end(), w, w + 16);
+  };
+  if (root < 0) {
+    emit(-1, -1);
+  } else if (B.tree[root].count > 0) {
+    emit(root, -1);
+  } else {
+    for (int t : order) emit(B.tree[t].left, B.tree[t].right);
+  }
+  n_nodes_out = (int)(nodes_out.size() / 16);
+
+  // primitives in leaf order
+  prims_out.assign(12 * (size_t)n, 0.0f);
+  for (int k = 0; k < n; ++k) {
+    const int p = ids[B.idx[k]];
+    float* o = &prims_out[12 * (size_t)k];
+    if (p < nt) {
+      const float* t = &in.tris[9 * (size_t)p];
+      o[0] = t[0];
+      o[1] = t[1];
+      o[2] = t[2];
+      o[3] = bits_f((2u << 20) | (uint32_t)p);
+      for (int a = 0; a < 3; ++a) {
+        o[4 + a] = (float)((double)t[3 + a] - (double)t[a]);
+        o[8 + a] = (float)((double)t[6 + a] - (double)t[a]);
+      }
+    } else {
+      const int j = p - nt;
+      o[0] = in.scat_pos[3 * (size_t)j];
+      o[1] = in.scat_pos[3 * (size_t)j + 1];
+      o[2] = in.scat_pos[3 * (size_t)j + 2];
+      o[3] = bits_f((3u << 20) | (uint32_t)j);
+    }
+  }
+}
+
+void build_scene_host(const HostSceneIn& in, HostSceneOut& out) {
+  const int nt = in.n_tris, ns = in.n_scat;
+  std::vector<int> all(nt + ns), tris(nt);
+  for (int i = 0; i < nt + ns; ++i) all[i] = i;
+  for (int i = 0; i < nt; ++i) tris[i] = i;
+  build_one(in, all, out.nodes, out.prims, out.n_nodes, out.depth);
+  build_one(in, tris, out.nodes_t, out.prims_t, out.n_nodes_t, out.depth_t);
+
+  // per-triangle normal + media, vertex 0; per-scatterer centre + amplitude
+  out.tri_nrm.assign(4 * (size_t)nt, 0.0f);
+  out.tri_v0.assign(4 * (size_t)nt, 0.0f);
+  for (int i = 0; i < nt; ++i) {
+    const float* t = &in.tris[9 * (size_t)i];
+    double e1[3], e2[3];
+    for (int a = 0; a < 3; ++a) {
+      e1[a] = (double)t[3 + a] - t[a];
+      e2[a] = (double)t[6 + a] - t[a];
+    }
+    double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double l = std::sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    if (l == 0) l = 1;
+    uint32_t med = (uint32_t)(in.media[2 * (size_t)i] & 0xFFFF) | ((uint32_t)(in.media[2 * (size_t)i + 1] & 0xFFFF) << 16);
+    out.tri_nrm[4 * (size_t)i] = (float)(nn[0] / l);
+    out.tri_nrm[4 * (size_t)i + 1] = (float)(nn[1] / l);
+    out.tri_nrm[4 * (size_t)i + 2] = (float)(nn[2] / l);
+    out.tri_nrm[4 * (size_t)i + 3] = bits_f(med);
+    out.tri_v0[4 * (size_t)i] = t[0];
+    out.tri_v0[4 * (size_t)i + 1] = t[1];
+    out.tri_v0[4 * (size_t)i + 2] = t[2];
+  }
+  out.scat.assign(4 * (size_t)ns, 0.0f);
+  for (int j = 0; j < ns; ++j) {
+    out.scat[4 * (size_t)j] = in.scat_pos[3 * (size_t)j];
+    out.scat[4 * (size_t)j + 1] = in.scat_pos[3 * (size_t)j + 1];
+    out.scat[4 * (size_t)j + 2] = in.scat_pos[3 * (size_t)j + 2];
+    out.scat[4 * (size_t)j + 3] = in.scat_amp[j];
+  }
+}
+
+}  // namespace usrt

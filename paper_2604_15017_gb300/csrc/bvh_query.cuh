@@ -1,0 +1,305 @@
+// BVH queries (Sec. 2.3.2 traversal, Sec. 2.3.3 secondary rays), header-only so that the
+// transport and adjoint kernels inline them.
+#pragma once
+
+#include "usrt_device.cuh"
+
+namespace usrt {
+
+constexpr int BVH_STACK = 64;
+
+struct RayInv {
+  float3 inv, oi;
+};
+__device__ __forceinline__ float safe_inv(float d) {
+  return 1.0f / (fabsf(d) > 1e-20f ? d : copysignf(1e-20f, d));
+}
+__device__ __forceinline__ RayInv ray_inv(float3 o, float3 w) {
+  RayInv r;
+  r.inv = f3(safe_inv(w.x), safe_inv(w.y), safe_inv(w.z));
+  r.oi = f3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+  return r;
+}
+
+// slab test of both children of a node; tmin returned, hit when tmin <= tmax'.  tmax is
+// widened by 2 ulp-ish (robust traversal) so that rounding never culls a box that holds a hit.
+__device__ __forceinline__ void node_boxes(const RayInv& r, float4 n0, float4 n1, float4 n2, float tlimit, bool& h0,
+                                           bool& h1, float& t0, float& t1) {
+  const float ax0 = fmaf(n0.x, r.inv.x, -r.oi.x), bx0 = fmaf(n0.y, r.inv.x, -r.oi.x);
+  const float ay0 = fmaf(n0.z, r.inv.y, -r.oi.y), by0 = fmaf(n0.w, r.inv.y, -r.oi.y);
+  const float az0 = fmaf(n2.x, r.inv.z, -r.oi.z), bz0 = fmaf(n2.y, r.inv.z, -r.oi.z);
+  const float ax1 = fmaf(n1.x, r.inv.x, -r.oi.x), bx1 = fmaf(n1.y, r.inv.x, -r.oi.x);
+  const float ay1 = fmaf(n1.z, r.inv.y, -r.oi.y), by1 = fmaf(n1.w, r.inv.y, -r.oi.y);
+  const float az1 = fmaf(n2.z, r.inv.z, -r.oi.z), bz1 = fmaf(n2.w, r.inv.z, -r.oi.z);
+  const float lo0 = fmaxf(fmaxf(fminf(ax0, bx0), fminf(ay0, by0)), fmaxf(fminf(az0, bz0), 0.0f));
+  const float hi0 = fminf(fminf(fmaxf(ax0, bx0), fmaxf(ay0, by0)), fminf(fmaxf(az0, bz0), tlimit));
+  const float lo1 = fmaxf(fmaxf(fminf(ax1, bx1), fminf(ay1, by1)), fmaxf(fminf(az1, bz1), 0.0f));
+  const float hi1 = fminf(fminf(fmaxf(ax1, bx1), fmaxf(ay1, by1)), fminf(fmaxf(az1, bz1), tlimit));
+  h0 = lo0 <= hi0 * 1.0000004f;
+  h1 = lo1 <= hi1 * 1.0000004f;
+  t0 = lo0;
+  t1 = lo1;
+}
+
+// Moller-Trumbore ray/triangle test; returns t > T_MIN or -1
+__device__ __forceinline__ float tri_test(float3 o, float3 w, float3 v0, float3 e1, float3 e2) {
+  const float3 p = cross3(w, e2);
+  const float det = dot3(e1, p);
+  if (det == 0.0f) return -1.0f;
+  const float inv = 1.0f / det;
+  const float3 tv = o - v0;
+  const float u = dot3(tv, p) * inv;
+  if (u < 0.0f || u > 1.0f) return -1.0f;
+  const float3 qv = cross3(tv, e1);
+  const float v = dot3(w, qv) * inv;
+  if (v < 0.0f || u + v > 1.0f) return -1.0f;
+  const float t = dot3(e2, qv) * inv;
+  return t > T_MIN ? t : -1.0f;
+}
+
+// point scatterer: event at the closest approach t = (p - o).w when within r_s of the centre
+__device__ __forceinline__ float scat_test(float3 o, float3 w, float3 p, float rs2) {
+  const float3 d = p - o;
+  const float t = dot3(d, w);
+  if (!(t > T_MIN)) return -1.0f;
+  const float3 q = w * t - d;
+  return dot3(q, q) <= rs2 ? t : -1.0f;
+}
+
+__device__ __forceinline__ bool hit_better(float t, uint32_t c, float tb, uint32_t cb) {
+  return t < tb || (t == tb && c < cb);
+}
+
+// transducer face z = 0, |x| <= n_elem pitch / 2, |y| <= h_el / 2, approached from z > 0
+__device__ __forceinline__ void xdcr_test(const Acq& q, float3 o, float3 w, float& tbest, uint32_t& cbest) {
+  if (!(w.z < 0.0f)) return;
+  const float t = -o.z / w.z;
+  const float x = fmaf(t, w.x, o.x), y = fmaf(t, w.y, o.y);
+  const float half = 0.5f * q.ne * q.pitch;
+  if (t > T_MIN && fabsf(x) <= half && fabsf(y) <= 0.5f * q.hel) {
+    int e = (int)floorf((x + half) / q.pitch);
+    e = min(q.ne - 1, max(0, e));
+    if (hit_better(t, prim_code(CLS_XDCR, e), tbest, cbest)) {
+      tbest = t;
+      cbest = prim_code(CLS_XDCR, (uint32_t)e);
+    }
+  }
+}
+
+__device__ __forceinline__ void leaf_closest(const SceneDev& S, int first, int count, float3 o, float3 w,
+                                             uint32_t prev, float& tbest, uint32_t& cbest) {
+  for (int i = first; i < first + count; ++i) {
+    const float4 A = __ldg(&S.prims[3 * i]);
+    const uint32_t code = __float_as_uint(A.w);
+    if (code == prev) continue;
+    float t;
+    if (code_cls(code) == CLS_TRI) {
+      const float4 B = __ldg(&S.prims[3 * i + 1]);
+      const float4 C = __ldg(&S.prims[3 * i + 2]);
+      t = tri_test(o, w, xyz(A), xyz(B), xyz(C));
+    } else {
+      t = scat_test(o, w, xyz(A), S.rs2);
+    }
+    if (t > 0.0f && hit_better(t, code, tbest, cbest)) {
+      tbest = t;
+      cbest = code;
+    }
+  }
+}
+
+// closest hit over the transducer, triangles and scatterers, excluding the primitive `prev`
+// the ray leaves from.  cbest = prim_code(CLS_NONE, 0) when the ray escapes.
+__device__ __forceinline__ void closest_hit(const SceneDev& S, const Acq& q, float3 o, float3 w, uint32_t prev,
+                                            float& tbest, uint32_t& cbest) {
+  tbest = 3.0e38f;
+  cbest = 0xFFFFFFFFu;
+  xdcr_test(q, o, w, tbest, cbest);
+  const RayInv r = ray_inv(o, w);
+  int stack[BVH_STACK];
+  float stt[BVH_STACK];
+  int sp = 0;
+  int node = 0;
+  float node_t = 0.0f;
+  while (true) {
+    if (node_t <= tbest) {
+      const float4 n0 = __ldg(&S.nodes[4 * node]);
+      const float4 n1 = __ldg(&S.nodes[4 * node + 1]);
+      const float4 n2 = __ldg(&S.nodes[4 * node + 2]);
+      const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes[4 * node + 3]));
+      bool h0, h1;
+      float t0, t1;
+      node_boxes(r, n0, n1, n2, tbest, h0, h1, t0, t1);
+      if (h0 && n3.z > 0) {
+        leaf_closest(S, n3.x, n3.z, o, w, prev, tbest, cbest);
+        h0 = false;
+      }
+      if (h1 && n3.w > 0) {
+        leaf_closest(S, n3.y, n3.w, o, w, prev, tbest, cbest);
+        h1 = false;
+      }
+      h0 = h0 && n3.x >= 0;
+      h1 = h1 && n3.y >= 0;
+      if (h0 && h1) {
+        const bool first0 = t0 <= t1;
+        if (sp < BVH_STACK) {
+          stack[sp] = first0 ? n3.y : n3.x;
+          stt[sp] = first0 ? t1 : t0;
+          ++sp;
+        }
+        node = first0 ? n3.x : n3.y;
+        node_t = first0 ? t0 : t1;
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? n3.x : n3.y;
+        node_t = h0 ? t0 : t1;
+        continue;
+      }
+    }
+    if (sp == 0) break;
+    --sp;
+    node = stack[sp];
+    node_t = stt[sp];
+  }
+  if (cbest == 0xFFFFFFFFu) cbest = prim_code(CLS_NONE, 0);
+}
+
+// all triangle crossings T_MIN < t < tmax of the segment o + t d (secondary rays; triangle-only
+// BVH), sorted by t.
+// Returns the count, or -1 when more than MAX_XINGS crossings were found.
+__device__ __forceinline__ int all_crossings(const SceneDev& S, float3 o, float3 d, float tmax, float* xt,
+                                             uint32_t* xid) {
+  const RayInv r = ray_inv(o, d);
+  int stack[BVH_STACK];
+  int sp = 0;
+  int node = 0;
+  int n = 0;
+  bool overflow = false;
+  while (true) {
+    const float4 n0 = __ldg(&S.nodes_t[4 * node]);
+    const float4 n1 = __ldg(&S.nodes_t[4 * node + 1]);
+    const float4 n2 = __ldg(&S.nodes_t[4 * node + 2]);
+    const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes_t[4 * node + 3]));
+    bool h0, h1;
+    float t0, t1;
+    node_boxes(r, n0, n1, n2, tmax, h0, h1, t0, t1);
+    for (int c = 0; c < 2; ++c) {
+      const bool h = c ? h1 : h0;
+      const int cnt = c ? n3.w : n3.z;
+      const int first = c ? n3.y : n3.x;
+      if (!h || cnt == 0) continue;
+      for (int i = first; i < first + cnt; ++i) {
+        const float4 A = __ldg(&S.prims_t[3 * i]);
+        const uint32_t code = __float_as_uint(A.w);
+        if (code_cls(code) != CLS_TRI) continue;
+        const float4 B = __ldg(&S.prims_t[3 * i + 1]);
+        const float4 C = __ldg(&S.prims_t[3 * i + 2]);
+        const float t = tri_test(o, d, xyz(A), xyz(B), xyz(C));
+        if (t > 0.0f && t < tmax) {
+          if (n < MAX_XINGS) {
+            xt[n] = t;
+            xid[n] = code_id(code);
+            ++n;
+          } else {
+            overflow = true;
+          }
+        }
+      }
+    }
+    const bool i0 = h0 && n3.z == 0 && n3.x >= 0;
+    const bool i1 = h1 && n3.w == 0 && n3.y >= 0;
+    if (i0 && i1) {
+      if (sp < BVH_STACK) stack[sp++] = n3.y;
+      node = n3.x;
+      continue;
+    }
+    if (i0 || i1) {
+      node = i0 ? n3.x : n3.y;
+      continue;
+    }
+    if (sp == 0) break;
+    node = stack[--sp];
+  }
+  if (overflow) return -1;
+  // insertion sort by t (ties by id)
+  for (int i = 1; i < n; ++i) {
+    const float t = xt[i];
+    const uint32_t id = xid[i];
+    int j = i - 1;
+    while (j >= 0 && (xt[j] > t || (xt[j] == t && xid[j] > id))) {
+      xt[j + 1] = xt[j];
+      xid[j + 1] = xid[j];
+      --j;
+    }
+    xt[j + 1] = t;
+    xid[j + 1] = id;
+  }
+  return n;
+}
+
+// secondary ray from a scatterer centre to element e (Sec. 2.3.3): straight segment, product
+// of transmission coefficients (zero under total internal reflection), attenuation and time
+// per sub-segment in the medium tracked across the crossings, receive directivity (Eq. cutoff).
+struct NeeOut {
+  bool ok;        // false: no contribution (directivity cutoff, TIR or overflow)
+  bool overflow;
+  float gain;     // prod T * exp(-kappa f0 sum alpha l) * f_rx * n_elem
+  float sum_al;   // sum alpha_m l_m
+  int n;          // crossings
+};
+
+__device__ __forceinline__ float elem_x(const Acq& q, int e) { return (e - 0.5f * (q.ne - 1)) * q.pitch; }
+
+template <bool DERIV>
+__device__ __forceinline__ NeeOut nee_eval(const SceneDev& S, const Media& med, const Acq& q, float3 p, int e2,
+                                           int m_start, float& t_hi, float& t_lo, float* xt, uint32_t* xid,
+                                           float3* dir_out, float* D_out) {
+  NeeOut r;
+  r.ok = false;
+  r.overflow = false;
+  r.gain = 0.0f;
+  r.sum_al = 0.0f;
+  r.n = 0;
+  const float3 tgt = f3(elem_x(q, e2), 0.0f, 0.0f);
+  const float3 dv = tgt - p;
+  const float D = sqrtf(dot3(dv, dv));
+  const float3 d = dv * (1.0f / D);
+  if (dir_out) *dir_out = d;
+  if (D_out) *D_out = D;
+  const float frx = f_rx(-d.z, q.alpha_m, q.alpha_c);
+  if (frx == 0.0f) return r;
+  const int n = all_crossings(S, p, d, D, xt, xid);
+  if (n < 0) {
+    r.overflow = true;
+    return r;
+  }
+  r.n = n;
+  float prodT = 1.0f, sa = 0.0f, tprev = 0.0f;
+  int m = m_start;
+  for (int i = 0; i < n; ++i) {
+    const float l = xt[i] - tprev;
+    sa = fmaf(med.al[m], l, sa);
+    ff_add(t_hi, t_lo, l / med.c[m]);
+    const float4 nr = __ldg(&S.tri_nrm[xid[i]]);
+    const uint32_t mm = __float_as_uint(nr.w);
+    const float3 nn = xyz(nr);
+    const float dn = dot3(d, nn);
+    const int m1 = dn < 0.0f ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+    const int m2 = dn < 0.0f ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+    const float3 nin = dn < 0.0f ? nn : nn * -1.0f;
+    const Iface f = iface(d, nin, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
+    if (f.tir) return r;
+    prodT *= f.T;
+    m = m2;
+    tprev = xt[i];
+  }
+  const float l = D - tprev;
+  sa = fmaf(med.al[m], l, sa);
+  ff_add(t_hi, t_lo, l / med.c[m]);
+  r.sum_al = sa;
+  r.gain = prodT * expf(-KAPPA_F * med.f0 * sa) * frx * (float)q.ne;
+  r.ok = true;
+  return r;
+}
+
+}  // namespace usrt

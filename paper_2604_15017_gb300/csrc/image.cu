@@ -1,0 +1,359 @@
+// Image formation and its adjoint: delay-and-sum (Eq. das) and its transpose (Eq.
+// das_adjoint), the Hilbert envelope along depth, log compression with the dynamic-range clip
+// (Sec. 2.3.4), the l1/l2 loss (Eq. weighted_l1_l2_loss) and the envelope/log VJP.
+#include "image.cuh"
+
+namespace usrt {
+
+// ------------------------------------------------------------------------------------------
+// DAS delays (Eq. das), in samples, evaluated in float-float so that the interpolation
+// position of a ~4000-sample delay is resolved to ~1e-6 samples:
+//   u = (x sin(th) + z cos(th) + W/2 |sin(th)|) fs / c_bf + sqrt((x - x_e)^2 + z^2) fs / c_bf
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ ff ff_div_f(ff a, float b) {
+  const float q = __fdiv_rn(a.hi, b);
+  const float r = __fmaf_rn(-q, b, a.hi);
+  return ff_fast(q, __fdiv_rn(__fadd_rn(r, a.lo), b));
+}
+// coordinate v0 + (v1 - v0) i / (n - 1)
+__device__ __forceinline__ ff grid_coord(float v0, float v1, int i, int n) {
+  if (n <= 1) return ff{v0, 0.0f};
+  const ff span = ff_div_f(ff_two_sum(v1, -v0), (float)(n - 1));
+  const ff off = ff_mulf(span, (float)i);
+  return ff_addx(ff{v0, 0.0f}, off);
+}
+struct DasGeo {
+  ff k;       // fs / c_bf
+  ff half_w;  // (n_elem - 1) pitch / 2
+};
+__device__ __forceinline__ DasGeo das_geo(const Acq& q) {
+  DasGeo g;
+  g.k = ff_divf(q.fs, q.cbf);
+  g.half_w = ff_mulf(ff{0.5f * (float)(q.ne - 1), 0.0f}, q.pitch);
+  return g;
+}
+__device__ __forceinline__ ff das_utx(const Acq& q, const DasGeo& g, ff x, ff z, int t) {
+  const float st = q.sin_tx[t];
+  ff p = ff_mulf(x, st);
+  p = ff_addx(p, ff_mul(z, ff{q.cos_tx[t], q.cos_lo[t]}));
+  p = ff_addx(p, ff_mulf(g.half_w, fabsf(st)));
+  return ff_mul(p, g.k);
+}
+__device__ __forceinline__ ff das_urx(const Acq& q, const DasGeo& g, ff x, ff z, int e) {
+  const ff xe = ff_mulf(ff{(float)e - 0.5f * (float)(q.ne - 1), 0.0f}, q.pitch);
+  const ff dx = ff_addx(x, ff{-xe.hi, -xe.lo});
+  const ff r2 = ff_addx(ff_mul(dx, dx), ff_mul(z, z));
+  return ff_mul(ff_sqrt(r2), g.k);
+}
+__device__ __forceinline__ float hann_w(int e, int ne) {
+  return 0.5f * (1.0f - cospif(2.0f * (float)(e + 1) / (float)(ne + 1)));
+}
+
+// DAS: one pixel per thread; transmit delays staged per pixel in shared memory, the receive
+// delay computed once per (pixel, element) and reused for every transmit; channel data read
+// through the read-only path (rows stay L2-resident)
+constexpr int DAS_THREADS = 256;
+__global__ void __launch_bounds__(DAS_THREADS) k_das(Acq q, Img im, const float* __restrict__ rf,
+                                                     float* __restrict__ irf) {
+  extern __shared__ float2 utx_s[];  // [ntx][DAS_THREADS]
+  const int npx = im.nl * im.nd;
+  const DasGeo g = das_geo(q);
+  for (int base = blockIdx.x * DAS_THREADS; base < npx; base += gridDim.x * DAS_THREADS) {
+    const int p = base + threadIdx.x;
+    const bool valid = p < npx;
+    const int l = valid ? p / im.nd : 0, d = valid ? p - l * im.nd : 0;
+    const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
+    for (int t = 0; t < q.ntx; ++t) {
+      const ff u = das_utx(q, g, x, z, t);
+      utx_s[t * DAS_THREADS + threadIdx.x] = make_float2(u.hi, u.lo);
+    }
+    float acc = 0.0f;
+    if (valid) {
+      for (int e = 0; e < q.ne; ++e) {
+        const ff ur = das_urx(q, g, x, z, e);
+        float s = 0.0f;
+        for (int t = 0; t < q.ntx; ++t) {
+          const float2 ut = utx_s[t * DAS_THREADS + threadIdx.x];
+          int i;
+          float f;
+          ff_floor(ff_addx(ff{ut.x, ut.y}, ur), i, f);
+          const float* row = rf + ((size_t)t * q.ne + e) * q.ns;
+          const float a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
+          const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
+          s += fmaf(f, b - a, a);
+        }
+        acc = fmaf(hann_w(e, q.ne), s, acc);
+      }
+      irf[p] = acc;
+    }
+  }
+}
+
+// transposed DAS: every tap scatters w_e (1 - f) g and w_e f g to its two samples
+__global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const float* __restrict__ gi, float* grf) {
+  extern __shared__ float2 utx_s[];
+  const int npx = im.nl * im.nd;
+  const DasGeo g = das_geo(q);
+  for (int base = blockIdx.x * DAS_THREADS; base < npx; base += gridDim.x * DAS_THREADS) {
+    const int p = base + threadIdx.x;
+    const bool valid = p < npx;
+    const int l = valid ? p / im.nd : 0, d = valid ? p - l * im.nd : 0;
+    const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
+    for (int t = 0; t < q.ntx; ++t) {
+      const ff u = das_utx(q, g, x, z, t);
+      utx_s[t * DAS_THREADS + threadIdx.x] = make_float2(u.hi, u.lo);
+    }
+    const float gv = valid ? gi[p] : 0.0f;
+    if (gv != 0.0f) {
+      for (int e = 0; e < q.ne; ++e) {
+        const ff ur = das_urx(q, g, x, z, e);
+        const float wg = hann_w(e, q.ne) * gv;
+        for (int t = 0; t < q.ntx; ++t) {
+          const float2 ut = utx_s[t * DAS_THREADS + threadIdx.x];
+          int i;
+          float f;
+          ff_floor(ff_addx(ff{ut.x, ut.y}, ur), i, f);
+          float* row = grf + ((size_t)t * q.ne + e) * q.ns;
+          if (i >= 0 && i < q.ns) atomicAdd(&row[i], wg * (1.0f - f));
+          if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], wg * f);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// shared-memory radix-2 FFT of one line (N = n_depth, power of two)
+// ------------------------------------------------------------------------------------------
+__device__ void fft_smem(float2* z, const float2* tw, int N, int logN, bool inverse) {
+  for (int len = 2, s = 1; len <= N; len <<= 1, ++s) {
+    const int half = len >> 1;
+    const int step = N >> s;
+    for (int b = threadIdx.x; b < (N >> 1); b += blockDim.x) {
+      const int grp = b >> (s - 1);
+      const int kk = b & (half - 1);
+      const int i = grp * len + kk, j = i + half;
+      float2 w = tw[kk * step];
+      if (inverse) w.y = -w.y;
+      const float2 xj = z[j], xi = z[i];
+      const float2 t = make_float2(w.x * xj.x - w.y * xj.y, w.x * xj.y + w.y * xj.x);
+      z[j] = make_float2(xi.x - t.x, xi.y - t.y);
+      z[i] = make_float2(xi.x + t.x, xi.y + t.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void twiddles(float2* tw, int N) {
+  for (int kk = threadIdx.x; kk < N / 2; kk += blockDim.x) {
+    float s, c;
+    sincospif(-2.0f * (float)kk / (float)N, &s, &c);
+    tw[kk] = make_float2(c, s);
+  }
+}
+
+// analytic signal of a real line (already bit-reversed into z): X = FFT(x); X *= h; IFFT / N
+__device__ void analytic_smem(float2* z, const float2* tw, int N, int logN) {
+  fft_smem(z, tw, N, logN, false);
+  for (int kk = threadIdx.x; kk < N; kk += blockDim.x) {
+    const float h = (kk == 0 || 2 * kk == N) ? 1.0f : (2 * kk < N ? 2.0f : 0.0f);
+    const float sc = h / (float)N;
+    z[kk] = make_float2(z[kk].x * sc, z[kk].y * sc);
+  }
+  __syncthreads();
+  // bit-reverse in place for the inverse transform
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int j = (int)(__brev((unsigned)i) >> (32 - logN));
+    if (i < j) {
+      const float2 t = z[i];
+      z[i] = z[j];
+      z[j] = t;
+    }
+  }
+  __syncthreads();
+  fft_smem(z, tw, N, logN, true);
+}
+
+// envelope of each line: E = |x + i H x|; per-image maximum (value, first index) into a
+// packed 64-bit key (float bits << 32 | ~index) with atomicMax
+__global__ void k_envelope(Img im, const float* __restrict__ irf, float* env, unsigned long long* emax_key) {
+  extern __shared__ float2 sz[];
+  const int N = im.nd;
+  const int logN = 31 - __clz(N);
+  float2* z = sz;
+  float2* tw = sz + N;
+  twiddles(tw, N);
+  __shared__ unsigned long long best;
+  if (threadIdx.x == 0) best = 0ull;
+  for (int l = blockIdx.x; l < im.nl; l += gridDim.x) {
+    const float* x = irf + (size_t)l * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int j = (int)(__brev((unsigned)i) >> (32 - logN));
+      z[j] = make_float2(__ldg(&x[i]), 0.0f);
+    }
+    __syncthreads();
+    analytic_smem(z, tw, N, logN);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const float e = sqrtf(z[i].x * z[i].x + z[i].y * z[i].y);
+      env[(size_t)l * N + i] = e;
+      const unsigned long long key =
+          ((unsigned long long)__float_as_uint(e) << 32) | (0xFFFFFFFFu - (uint32_t)(l * N + i));
+      atomicMax(&best, key);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(emax_key, best);
+}
+
+__device__ __forceinline__ float key_emax(unsigned long long k) { return __uint_as_float((uint32_t)(k >> 32)); }
+__device__ __forceinline__ int key_argmax(unsigned long long k) { return (int)(0xFFFFFFFFu - (uint32_t)k); }
+
+// B = max(20 log10(E / E_max), -DR); E = 0 or E_max = 0 -> -DR
+__global__ void k_logc(Img im, const float* __restrict__ env, const unsigned long long* emax_key, float* b) {
+  const int n = im.nl * im.nd;
+  const float emax = key_emax(*emax_key);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float e = env[i];
+    float v = -im.dr;
+    if (emax > 0.0f && e > 0.0f) v = fmaxf(20.0f * log10f(e / emax), -im.dr);
+    b[i] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// loss: L = (l1 sum |r| + l2 sum r^2) / N, dL/dB = (l1 sign(r) + 2 l2 r) / N
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float block_sum(float v) {
+  __shared__ float ws[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.0f;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  }
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+__global__ void k_loss_partial(Img im, const float* __restrict__ b, const float* __restrict__ bref, float* gb,
+                               float* part) {
+  const int n = im.nl * im.nd;
+  const float inv = 1.0f / (float)n;
+  float s = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float r = b[i] - bref[i];
+    s += im.l1 * fabsf(r) + im.l2 * r * r;
+    if (gb) gb[i] = (im.l1 * (r > 0.0f ? 1.0f : (r < 0.0f ? -1.0f : 0.0f)) + 2.0f * im.l2 * r) * inv;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_final(const float* part, int n, float scale, float* out) {
+  float s = 0.0f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[0] = s * scale;
+}
+
+// sum over unclipped pixels of dL/dB (the E_max share of the log-compression derivative)
+__global__ void k_live_sum(Img im, const float* __restrict__ env, const unsigned long long* emax_key,
+                           const float* __restrict__ gb, float* part) {
+  const int n = im.nl * im.nd;
+  const float emax = key_emax(*emax_key);
+  float s = 0.0f;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float e = env[i];
+    if (emax > 0.0f && e > 0.0f && 20.0f * log10f(e / emax) > -im.dr) s += gb[i];
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// per line: g_E = dL/dB * (20/ln10) / E on unclipped pixels, minus (20/ln10) S / E_max at the
+// argmax; then g_x = (x/E) g_E - H((y/E) g_E) (the Hilbert matrix is skew-symmetric)
+__global__ void k_envlog_vjp(Img im, const float* __restrict__ irf, const float* __restrict__ gb,
+                             const unsigned long long* emax_key, const float* live_sum, float* gi) {
+  extern __shared__ float2 sz[];
+  const int N = im.nd;
+  const int logN = 31 - __clz(N);
+  float2* z = sz;
+  float2* v = sz + N;
+  float2* tw = sz + 2 * N;
+  twiddles(tw, N);
+  const float emax = key_emax(*emax_key);
+  const int am = key_argmax(*emax_key);
+  const float c = 8.685889638065036f;  // 20 / ln(10)
+  const float S = *live_sum;
+  for (int l = blockIdx.x; l < im.nl; l += gridDim.x) {
+    const float* x = irf + (size_t)l * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int j = (int)(__brev((unsigned)i) >> (32 - logN));
+      z[j] = make_float2(__ldg(&x[i]), 0.0f);
+    }
+    __syncthreads();
+    analytic_smem(z, tw, N, logN);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const float xi = __ldg(&x[i]), yi = z[i].y;
+      const float e = sqrtf(xi * xi + yi * yi);
+      const int p = l * N + i;
+      float ge = 0.0f;
+      if (emax > 0.0f && e > 0.0f && 20.0f * log10f(e / emax) > -im.dr) ge = gb[p] * c / e;
+      if (p == am && emax > 0.0f) ge -= c * S / emax;
+      const float vv = e > 0.0f ? yi / e * ge : 0.0f;
+      z[i] = make_float2(e > 0.0f ? xi / e * ge : 0.0f, 0.0f);  // keep (x/E) g_E in z.x
+      const int j = (int)(__brev((unsigned)i) >> (32 - logN));
+      v[j] = make_float2(vv, 0.0f);
+    }
+    __syncthreads();
+    analytic_smem(v, tw, N, logN);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) gi[(size_t)l * N + i] = z[i].x - v[i].y;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st) {
+  k_das<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, rf, irf);
+}
+void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st) {
+  cudaMemsetAsync(grf, 0, sizeof(float) * (size_t)q.ntx * q.ne * q.ns, st);
+  k_das_adj<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, gi, grf);
+}
+void launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
+                   cudaStream_t st) {
+  cudaMemsetAsync(key, 0, sizeof(unsigned long long), st);
+  const int nb = min(im.nl, grid);
+  k_envelope<<<nb, 256, sizeof(float2) * (size_t)(im.nd + im.nd / 2), st>>>(im, irf, env, key);
+  if (bmode) k_logc<<<grid, 256, 0, st>>>(im, env, key, bmode);
+}
+void launch_loss(const Img& im, const float* b, const float* bref, float* gb, float* part, int nparts, float* loss,
+                 cudaStream_t st) {
+  k_loss_partial<<<nparts, 256, 0, st>>>(im, b, bref, gb, part);
+  k_sum_final<<<1, 1024, 0, st>>>(part, nparts, 1.0f / (float)(im.nl * im.nd), loss);
+}
+void launch_envlog_vjp(const Img& im, const float* irf, const float* gb, float* env, unsigned long long* key,
+                       float* part, int nparts, float* live_sum, float* gi, int grid, cudaStream_t st) {
+  launch_envlog(im, irf, env, key, nullptr, grid, st);
+  k_live_sum<<<nparts, 256, 0, st>>>(im, env, key, gb, part);
+  k_sum_final<<<1, 1024, 0, st>>>(part, nparts, 1.0f, live_sum);
+  const int nb = min(im.nl, grid);
+  k_envlog_vjp<<<nb, 256, sizeof(float2) * (size_t)(2 * im.nd + im.nd / 2), st>>>(im, irf, gb, key, live_sum, gi);
+}
+cudaError_t image_set_attrs(int nd) {
+  cudaError_t e = cudaFuncSetAttribute(k_das, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float2) * DAS_THREADS * MAX_TX));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_das_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float2) * DAS_THREADS * MAX_TX));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_envelope, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float2) * (size_t)(nd + nd / 2)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_envlog_vjp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(float2) * (size_t)(2 * nd + nd / 2)));
+}
+
+}  // namespace usrt

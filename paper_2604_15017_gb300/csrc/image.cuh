@@ -1,0 +1,19 @@
+// Image-formation kernels interface.
+#pragma once
+
+#include "usrt_device.cuh"
+
+namespace usrt {
+
+void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st);
+void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st);
+// envelope -> env (workspace) + packed (E_max, argmax) key; log compression -> bmode (optional)
+void launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
+                   cudaStream_t st);
+void launch_loss(const Img& im, const float* b, const float* bref, float* gb, float* part, int nparts, float* loss,
+                 cudaStream_t st);
+void launch_envlog_vjp(const Img& im, const float* irf, const float* gb, float* env, unsigned long long* key,
+                       float* part, int nparts, float* live_sum, float* gi, int grid, cudaStream_t st);
+cudaError_t image_set_attrs(int nd);
+
+}  // namespace usrt

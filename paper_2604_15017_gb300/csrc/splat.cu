@@ -1,0 +1,313 @@
+// Sort-based RF splat (Sec. 2.3.4, Eq. axial_sig): RF[row][n] = sum_i a_i s(n / fs - tau_i).
+//
+// No scatter of pulse taps with atomics.  Instead:
+//   1. rows:   counting sort of the arrivals by row = tx * n_elem + e (histogram, scan, scatter);
+//   2. per row (one CTA): counting sort by time bin b = floor(tau fs) into an L2-resident
+//      scratch, then a segmented warp reduction of the Taylor moments
+//        M_j(b) = sum_{i in b} a_i (-delta_i)^j,  delta_i = tau_i fs - (b + 1/2),  j < 8,
+//      and finally the convolution RF[n] = sum_j sum_d G_j(d) M_j(n - d) with the table
+//        G_j(d) = g^(j)(d - 1/2) / j!,  g(x) = s(x / fs)
+//      (truncation after 8 moments: |delta| <= 1/2 sample gives < 1e-7 relative error).
+#include <cooperative_groups.h>
+
+#include "splat.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace usrt {
+
+// ------------------------------------------------------------------------------------------
+// pulse-derivative table: g(x) = Im h(x), h(x) = exp(-x^2 / S + i W x) with S = sigma fs^2 and
+// W = 2 pi f0 / fs; with y = (x - i W S / 2) / sqrt(S),  h^(j)(x) = h(x) (-1/sqrt(S))^j H_j(y)
+// (physicists' Hermite polynomials, H_{j+1} = 2 y H_j - 2 j H_{j-1}).
+// ------------------------------------------------------------------------------------------
+__global__ void k_pulse_table(SplatGeom g, float* G) {
+  const int d = threadIdx.x;
+  if (d >= g.ntaps) return;
+  const float x = (float)(g.dlo + d) - 0.5f;
+  const float S = g.Sig, W = g.Om;
+  const float rs = rsqrtf(S);
+  const float yr = x * rs, yi = -0.5f * W * S * rs;
+  float e_s, e_c;
+  const float mag = expf(-x * x / S);
+  sincosf(W * x, &e_s, &e_c);
+  const float hr = mag * e_c, hi = mag * e_s;  // h(x)
+  float Hr0 = 1.0f, Hi0 = 0.0f, Hr1 = 2.0f * yr, Hi1 = 2.0f * yi;
+  float fact = 1.0f, sc = 1.0f;
+  for (int j = 0; j < K_MOM; ++j) {
+    float Hr, Hi;
+    if (j == 0) {
+      Hr = Hr0;
+      Hi = Hi0;
+    } else if (j == 1) {
+      Hr = Hr1;
+      Hi = Hi1;
+    } else {
+      const float nr = 2.0f * (yr * Hr1 - yi * Hi1) - 2.0f * (j - 1) * Hr0;
+      const float ni = 2.0f * (yr * Hi1 + yi * Hr1) - 2.0f * (j - 1) * Hi0;
+      Hr0 = Hr1;
+      Hi0 = Hi1;
+      Hr1 = nr;
+      Hi1 = ni;
+      Hr = nr;
+      Hi = ni;
+    }
+    if (j > 0) {
+      fact *= (float)j;
+      sc *= -rs;
+    }
+    // Im(h * H) * sc / j!
+    G[j * g.ntaps + d] = (hr * Hi + hi * Hr) * sc / fact;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// 1. bucket by row
+// ------------------------------------------------------------------------------------------
+__global__ void k_row_hist(const Arrival* arr, const uint32_t* n_arr, uint32_t cap, uint32_t* row_cnt, int nrows) {
+  extern __shared__ uint32_t h[];
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x) h[r] = 0;
+  __syncthreads();
+  const uint32_t n = min(*n_arr, cap);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(&h[arr[i].x], 1u);
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrows; r += blockDim.x)
+    if (h[r]) atomicAdd(&row_cnt[r], h[r]);
+}
+
+// exclusive scan of the row counts (one block of 1024 threads); off[nrows] = total
+__global__ void k_row_scan(const uint32_t* cnt, uint32_t* off, uint32_t* cursor, int nrows) {
+  __shared__ uint32_t part[1024];
+  const int per = (nrows + blockDim.x - 1) / blockDim.x;
+  const int lo = threadIdx.x * per, hi = min(nrows, lo + per);
+  uint32_t s = 0;
+  for (int r = lo; r < hi; ++r) s += cnt[r];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (int r = lo; r < hi; ++r) {
+    off[r] = run;
+    cursor[r] = 0;
+    run += cnt[r];
+  }
+  if (threadIdx.x == blockDim.x - 1) off[nrows] = part[threadIdx.x];
+}
+
+// scatter into row buckets: each block takes chunks of CH arrivals, ranks them per row in
+// shared memory and reserves one range per (chunk, row) with a single global atomic
+constexpr int SC_THREADS = 512;
+constexpr int SC_PER = 16;
+constexpr int SC_CH = SC_THREADS * SC_PER;
+__global__ void __launch_bounds__(SC_THREADS) k_row_scatter(const Arrival* arr, const uint32_t* n_arr, uint32_t cap,
+                                                            const uint32_t* off, uint32_t* cursor, uint2* out,
+                                                            int nrows) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* h = sm;           // per-row count in this chunk
+  uint32_t* base = sm + nrows;
+  const uint32_t n = min(*n_arr, cap);
+  for (uint32_t c0 = blockIdx.x * SC_CH; c0 < n; c0 += gridDim.x * SC_CH) {
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) h[r] = 0;
+    __syncthreads();
+    uint32_t row[SC_PER], rank[SC_PER];
+    uint2 val[SC_PER];
+#pragma unroll
+    for (int k = 0; k < SC_PER; ++k) {
+      const uint32_t i = c0 + k * SC_THREADS + threadIdx.x;
+      row[k] = 0xFFFFFFFFu;
+      if (i < n) {
+        const Arrival A = arr[i];
+        row[k] = A.x;
+        val[k] = make_uint2(A.y, A.z);
+        rank[k] = atomicAdd(&h[A.x], 1u);
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x)
+      if (h[r]) base[r] = off[r] + atomicAdd(&cursor[r], h[r]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SC_PER; ++k)
+      if (row[k] != 0xFFFFFFFFu) out[base[row[k]] + rank[k]] = val[k];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// 2. per row: sort by bin, segmented moment reduction, convolution
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(ROW_THREADS) k_row_splat(SplatGeom g, const uint2* bucket, const uint32_t* off,
+                                                           uint2* scratch, const float* Gtab, float* rf) {
+  extern __shared__ float smf[];
+  const int row = blockIdx.x;
+  const int NB = g.nbins;        // bins -HALO .. ns + HALO - 1
+  float* M = smf;                // [K_MOM][NB]
+  uint32_t* hist = reinterpret_cast<uint32_t*>(M + K_MOM * NB);  // [NB + 1]
+  float* G = reinterpret_cast<float*>(hist + NB + 1);            // [K_MOM][ntaps]
+  const uint32_t a0 = off[row], a1 = off[row + 1];
+  for (int i = threadIdx.x; i < K_MOM * NB; i += blockDim.x) M[i] = 0.0f;
+  for (int i = threadIdx.x; i <= NB; i += blockDim.x) hist[i] = 0;
+  for (int i = threadIdx.x; i < K_MOM * g.ntaps; i += blockDim.x) G[i] = Gtab[i];
+  __syncthreads();
+  const uint32_t mask = (1u << TQ_FRAC) - 1u;
+  // pass 1: histogram of bins
+  for (uint32_t i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    const int b = (int)(bucket[i].x >> TQ_FRAC) - TQ_OFFSET + HALO;
+    if (b >= 0 && b < NB) atomicAdd(&hist[b], 1u);
+  }
+  __syncthreads();
+  // exclusive scan of hist (NB entries) in place: per-thread serial chunk + block scan
+  {
+    __shared__ uint32_t part[ROW_THREADS];
+    const int per = (NB + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(NB, lo + per);
+    uint32_t s = 0;
+    for (int b = lo; b < hi; ++b) s += hist[b];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+      uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int b = lo; b < hi; ++b) {
+      const uint32_t c = hist[b];
+      hist[b] = run;
+      run += c;
+    }
+    if (threadIdx.x == blockDim.x - 1) hist[NB] = part[threadIdx.x];
+  }
+  __syncthreads();
+  // pass 2: scatter into bin order (scratch shares the row's index range)
+  for (uint32_t i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    const uint2 v = bucket[i];
+    const int b = (int)(v.x >> TQ_FRAC) - TQ_OFFSET + HALO;
+    if (b >= 0 && b < NB) scratch[a0 + atomicAdd(&hist[b], 1u)] = v;
+  }
+  __syncthreads();
+  // after pass 2 hist[b] = end of bin b; total kept arrivals:
+  const uint32_t nk = hist[NB];
+  __syncthreads();
+  // pass 3: segmented warp reduction of the moments over the bin-sorted arrivals
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = (threadIdx.x & ~31u); base < nk; base += blockDim.x) {
+    const uint32_t i = base + lane;
+    int b = -1;
+    float m[K_MOM];
+#pragma unroll
+    for (int j = 0; j < K_MOM; ++j) m[j] = 0.0f;
+    if (i < nk) {
+      const uint2 v = scratch[a0 + i];
+      b = (int)(v.x >> TQ_FRAC) - TQ_OFFSET + HALO;
+      const float delta = (float)(v.x & mask) * (1.0f / (float)(1u << TQ_FRAC)) - 0.5f;
+      float p = __uint_as_float(v.y);
+      m[0] = p;
+#pragma unroll
+      for (int j = 1; j < K_MOM; ++j) {
+        p = p * (-delta);  // the 1/j! of the Taylor term lives in the pulse table
+        m[j] = p;
+      }
+    }
+    // inclusive segmented scan: lanes of one bin are contiguous (sorted)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int bu = __shfl_up_sync(0xFFFFFFFFu, b, o);
+#pragma unroll
+      for (int j = 0; j < K_MOM; ++j) {
+        const float mu = __shfl_up_sync(0xFFFFFFFFu, m[j], o);
+        if (lane >= o && bu == b) m[j] += mu;
+      }
+    }
+    const int bn = __shfl_down_sync(0xFFFFFFFFu, b, 1);
+    const bool tail = (b >= 0) && (lane == 31 || bn != b);
+    if (tail) {
+#pragma unroll
+      for (int j = 0; j < K_MOM; ++j) atomicAdd(&M[j * NB + b], m[j]);
+    }
+  }
+  __syncthreads();
+  // convolution: each thread produces R consecutive samples of the row
+  const int ns = g.ns;
+  const int R = (ns + blockDim.x - 1) / blockDim.x;
+  const int n0 = threadIdx.x * R;
+  const int Rv = max(0, min(R, ns - n0));
+  float acc[ROW_MAX_R];
+#pragma unroll
+  for (int r = 0; r < ROW_MAX_R; ++r) acc[r] = 0.0f;
+  for (int j = 0; j < K_MOM; ++j) {
+    const float* Mj = M + j * NB;
+    const float* Gj = G + j * g.ntaps;
+    for (int d = 0; d < g.ntaps; ++d) {
+      const float gv = Gj[d];
+      // bin of sample n for tap d: n - (dlo + d); shifted by HALO
+      const int bb = n0 - (g.dlo + d) + HALO;
+#pragma unroll
+      for (int r = 0; r < ROW_MAX_R; ++r)
+        if (r < Rv) acc[r] = fmaf(gv, Mj[bb + r], acc[r]);
+    }
+  }
+  float* out = rf + (size_t)row * ns;
+#pragma unroll
+  for (int r = 0; r < ROW_MAX_R; ++r)
+    if (r < Rv) out[n0 + r] = acc[r];
+}
+
+// standalone arrival list -> packed arrivals
+__global__ void k_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n,
+                                int ne, float fs, Arrival* out, uint32_t* n_out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t tq = time_to_tq(tau[i], 0.0f, fs);
+    if (tq == 0xFFFFFFFFu) continue;
+    cg::coalesced_group grp = cg::coalesced_threads();
+    uint32_t s = 0;
+    if (grp.thread_rank() == 0) s = atomicAdd(n_out, (uint32_t)grp.size());
+    s = grp.shfl(s, 0) + grp.thread_rank();
+    out[s] = make_uint4((uint32_t)(tx[i] * ne + e[i]), tq, __float_as_uint(a[i]), (uint32_t)i);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+size_t row_splat_smem(const SplatGeom& g) {
+  return sizeof(float) * (size_t)K_MOM * g.nbins + sizeof(uint32_t) * (g.nbins + 1) +
+         sizeof(float) * (size_t)K_MOM * g.ntaps;
+}
+
+void launch_pulse_table(const SplatGeom& g, float* G, cudaStream_t st) { k_pulse_table<<<1, 128, 0, st>>>(g, G); }
+
+void launch_splat(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
+                  const float* G, float* rf, int grid, cudaStream_t st) {
+  const int nrows = g.nrows;
+  cudaMemsetAsync(w.row_cnt, 0, sizeof(uint32_t) * nrows, st);
+  k_row_hist<<<grid, 256, sizeof(uint32_t) * nrows, st>>>(arr, n_arr, cap, w.row_cnt, nrows);
+  k_row_scan<<<1, 1024, 0, st>>>(w.row_cnt, w.row_off, w.row_cursor, nrows);
+  k_row_scatter<<<grid, SC_THREADS, 2 * sizeof(uint32_t) * nrows, st>>>(arr, n_arr, cap, w.row_off, w.row_cursor,
+                                                                         w.bucket, nrows);
+  k_row_splat<<<nrows, ROW_THREADS, row_splat_smem(g), st>>>(g, w.bucket, w.row_off, w.scratch, G, rf);
+}
+
+void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n, int ne,
+                          float fs, Arrival* out, uint32_t* n_out, int grid, cudaStream_t st) {
+  k_pack_arrivals<<<grid, 256, 0, st>>>(tx, e, tau, a, n, ne, fs, out, n_out);
+}
+
+cudaError_t splat_set_attrs(const SplatGeom& g) {
+  return cudaFuncSetAttribute(k_row_splat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_splat_smem(g));
+}
+cudaError_t row_scatter_set_attrs(int nrows) {
+  return cudaFuncSetAttribute(k_row_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * sizeof(uint32_t) * nrows));
+}
+cudaError_t row_hist_set_attrs(int nrows) {
+  return cudaFuncSetAttribute(k_row_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(sizeof(uint32_t) * nrows));
+}
+
+}  // namespace usrt

@@ -1,0 +1,39 @@
+// Sort-based splat interface.
+#pragma once
+
+#include "usrt_device.cuh"
+
+namespace usrt {
+
+typedef uint4 Arrival;  // (row, tq, bits(a), path id)
+
+constexpr int ROW_THREADS = 512;
+constexpr int ROW_MAX_R = 8;   // samples per thread: n_samples <= ROW_THREADS * ROW_MAX_R
+constexpr int HALO = 64;       // bins kept on each side of the record (>= pulse half-width)
+constexpr int MAX_SPLAT_NS = ROW_THREADS * ROW_MAX_R;
+
+struct SplatGeom {
+  int nrows, ns, nbins;  // nbins = ns + 2 * HALO
+  int dlo, ntaps;        // taps d = dlo .. dlo + ntaps - 1 (d = n - bin)
+  float Sig, Om;         // sigma * fs^2, 2 pi f0 / fs
+};
+
+struct SplatWork {
+  uint32_t* row_cnt;     // [nrows]
+  uint32_t* row_off;     // [nrows + 1]
+  uint32_t* row_cursor;  // [nrows]
+  uint2* bucket;         // [cap] (tq, bits(a)) in row order
+  uint2* scratch;        // [cap] (tq, bits(a)) in (row, bin) order
+};
+
+size_t row_splat_smem(const SplatGeom& g);
+void launch_pulse_table(const SplatGeom& g, float* G, cudaStream_t st);
+void launch_splat(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
+                  const float* G, float* rf, int grid, cudaStream_t st);
+void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n, int ne,
+                          float fs, Arrival* out, uint32_t* n_out, int grid, cudaStream_t st);
+cudaError_t splat_set_attrs(const SplatGeom& g);
+cudaError_t row_scatter_set_attrs(int nrows);
+cudaError_t row_hist_set_attrs(int nrows);
+
+}  // namespace usrt

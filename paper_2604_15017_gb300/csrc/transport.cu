@@ -1,0 +1,214 @@
+// Wavefront transport kernels (Sec. 2.3.1-2.3.3): generate, traverse, interact, secondary rays.
+//
+// Every kernel is a grid-stride loop whose trip count is read from a device counter written by
+// the previous kernel, so a whole forward pass is a fixed launch sequence (no host round trip,
+// capturable in a CUDA graph).  Live paths are compacted after every interaction with
+// warp-aggregated appends (one atomic per coalesced group).
+#include <cooperative_groups.h>
+
+#include "bvh_query.cuh"
+#include "transport.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace usrt {
+
+// one atomic per group of coalesced lanes; returns this lane's slot
+__device__ __forceinline__ uint32_t append_slot(uint32_t* counter) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  uint32_t base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (uint32_t)g.size());
+  base = g.shfl(base, 0);
+  return base + g.thread_rank();
+}
+
+__device__ __forceinline__ void path_tx_ray(const Acq& q, long long path, int& tx, uint32_t& ray) {
+  tx = (int)(path / q.rays_per_tx);
+  const long long local = path - (long long)tx * q.rays_per_tx;
+  ray = (uint32_t)(q.tx_elem < 0 ? local : (long long)q.tx_elem * q.nr + local);
+}
+
+// ------------------------------------------------------------------------------------------
+// Emission (Sec. 2.3.1, Eq. directivity, Eq. pressure_mc): origin uniform over the element
+// face, cosine-weighted direction (f_d / p = pi), weight pi / N_r, steering delay as a time
+// stamp tau_tx = (x_e sin(theta) + W/2 |sin(theta)|) / c_bf.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long path0, uint32_t n) {
+  const Acq& q = A.acq;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long path = path0 + i;
+    int tx;
+    uint32_t ray;
+    path_tx_ray(q, path, tx, ray);
+    const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, 0u), make_uint2(q.key0, q.key1));
+    const int e = (int)(ray / (uint32_t)q.nr);
+    const float xe = (e - 0.5f * (q.ne - 1)) * q.pitch;
+    const float u0 = u01(u.x), u1 = u01(u.y), u2 = u01(u.z), u3 = u01(u.w);
+    const float r = sqrtf(u2);
+    float sp, cp;
+    sincospif(2.0f * u3, &sp, &cp);
+    const float wz = sqrtf(1.0f - u2);
+    const float st = q.sin_tx[tx];
+    const float tau0 = (xe * st + 0.5f * (q.ne - 1) * q.pitch * fabsf(st)) / q.cbf;
+    A.qout.pa[i] = make_float4(xe + (u0 - 0.5f) * q.pitch, (u1 - 0.5f) * q.hel, 0.0f, 3.14159265358979f / q.nr);
+    A.qout.wt[i] = make_float4(r * cp, r * sp, wz, tau0);
+    A.qout.meta[i] = make_uint4((uint32_t)path, 0xFFFFFFFFu, 0u, __float_as_uint(0.0f));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt->live[0] = n;
+}
+
+// ------------------------------------------------------------------------------------------
+// Closest-hit traversal of every live path
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_traverse(TransportArgs A) {
+  const uint32_t n = A.cnt->live[A.k];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 pa = A.qin.pa[i];
+    const float4 wt = A.qin.wt[i];
+    const uint32_t prev = A.qin.meta[i].y;
+    float t;
+    uint32_t c;
+    closest_hit(A.S, A.acq, xyz(pa), xyz(wt), prev, t, c);
+    A.hits[i] = make_float2(t, __uint_as_float(c));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Interaction: attenuation and travel time over the segment, then the event at its end:
+// transducer arrival, interface split (Fresnel / Snell, Sec. 2.3.2), or a scatterer (queue a
+// secondary ray, pass through).  Survivors are compacted into the output queue.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
+  const Acq& q = A.acq;
+  const Media& med = A.med;
+  const uint32_t n = A.cnt->live[A.k];
+  const int K1 = q.kmax + 1;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float2 h = A.hits[i];
+    const uint32_t code = __float_as_uint(h.y);
+    const uint32_t cls = code_cls(code);
+    const uint4 meta = A.qin.meta[i];
+    const long long path = meta.x;
+    uint32_t* rec = A.record ? &A.record[(size_t)(path - A.path_base) * K1 + A.k] : nullptr;
+    if (cls == CLS_NONE) {  // escape
+      if (rec) *rec = 0u;
+      continue;
+    }
+    float4 pa = A.qin.pa[i];
+    float4 wt = A.qin.wt[i];
+    int m = (int)(meta.z & 0xFF);
+    float tau_lo = __uint_as_float(meta.w);
+    const float t = h.x;
+    float3 w = xyz(wt);
+    float a = pa.w * expf(-KAPPA_F * med.al[m] * med.f0 * t);
+    float tau_hi = wt.w;
+    ff_add(tau_hi, tau_lo, t / med.c[m]);
+    const float3 x = xyz(pa) + w * t;
+    int tx;
+    uint32_t ray;
+    path_tx_ray(q, path, tx, ray);
+    if (cls == CLS_XDCR) {  // arrival at the receiving element (Sec. 2.3.4)
+      if (rec) *rec = code;
+      const float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+      if (frx > 0.0f && A.arr) {
+        const uint32_t tq = time_to_tq(tau_hi, tau_lo, q.fs);
+        if (tq != 0xFFFFFFFFu) {
+          const uint32_t slot = append_slot(&A.cnt->n_arr);
+          if (slot < A.arr_cap)
+            A.arr[slot] = make_uint4((uint32_t)(tx * q.ne) + code_id(code), tq, __float_as_uint(a * frx), (uint32_t)path);
+        }
+      }
+      continue;
+    }
+    if (A.k == q.kmax) {  // interaction budget spent
+      if (rec) *rec = code;
+      continue;
+    }
+    const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, (uint32_t)(A.k + 1)),
+                                  make_uint2(q.key0, q.key1));
+    uint32_t word = code;
+    if (cls == CLS_TRI) {
+      const float4 nr = __ldg(&A.S.tri_nrm[code_id(code)]);
+      const uint32_t mm = __float_as_uint(nr.w);
+      const float3 nn = xyz(nr);
+      const bool front = dot3(w, nn) < 0.0f;
+      const float3 nin = front ? nn : nn * -1.0f;
+      const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+      const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+      const Iface f = iface(w, nin, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
+      uint32_t choice;
+      if (f.tir) {
+        choice = CH_TIR;
+      } else {
+        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+        choice = u01(u.x) < pr ? CH_REFLECT : CH_TRANSMIT;
+      }
+      if (choice == CH_TIR) {
+        w = w + nin * (2.0f * f.ci);
+        m = m1;
+      } else if (choice == CH_REFLECT) {
+        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+        a = a * (f.R / pr);
+        w = w + nin * (2.0f * f.ci);
+        m = m1;
+      } else {
+        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+        a = a * (f.T / (1.0f - pr));
+        w = w * f.r + nin * (f.r * f.ci - f.ct);
+        m = m2;
+      }
+      word |= choice << 22;
+    } else {  // scatterer: secondary ray to a uniformly chosen element; Born pass-through
+      const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
+      word |= (uint32_t)e2 << 24;
+      const uint32_t slot = append_slot(&A.cnt->nee[A.k]);
+      A.nee.job[slot] = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code)));
+      A.nee.jm[slot] = (uint32_t)m | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16);
+    }
+    if (rec) *rec = word;
+    const uint32_t o = append_slot(&A.cnt->live[A.k + 1]);
+    A.qout.pa[o] = make_float4(x.x, x.y, x.z, a);
+    A.qout.wt[o] = make_float4(w.x, w.y, w.z, tau_hi);
+    A.qout.meta[o] = make_uint4(meta.x, code, (uint32_t)m | ((uint32_t)(A.k + 1) << 8), __float_as_uint(tau_lo));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Secondary rays of the scatterer events of segment k (Sec. 2.3.3)
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
+  const Acq& q = A.acq;
+  const Media& med = A.med;
+  const uint32_t n = A.cnt->nee[A.k];
+  float xt[MAX_XINGS];
+  uint32_t xid[MAX_XINGS];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float4 job = A.nee.job[i];
+    const uint32_t jm = A.nee.jm[i];
+    const uint32_t j = __float_as_uint(job.w);
+    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)(jm >> 16);
+    const float4 sc = __ldg(&A.S.scat[j]);
+    float th = job.y, tl = job.z;
+    const NeeOut r = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, th, tl, xt, xid, nullptr, nullptr);
+    if (r.overflow) {
+      atomicOr(&A.cnt->status, ST_OVERFLOW);
+      atomicAdd(&A.cnt->dropped, 1u);
+      continue;
+    }
+    if (!r.ok || !A.arr) continue;
+    const uint32_t tq = time_to_tq(th, tl, q.fs);
+    if (tq == 0xFFFFFFFFu) continue;
+    const float amp = job.x * med.As * sc.w * r.gain;
+    const uint32_t slot = append_slot(&A.cnt->n_arr);
+    if (slot < A.arr_cap) A.arr[slot] = make_uint4((uint32_t)(tx * q.ne + e2), tq, __float_as_uint(amp), 0xFFFFFFFFu);
+  }
+}
+
+void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {
+  k_generate<<<grid, 256, 0, st>>>(a, path0, n);
+}
+void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st) { k_traverse<<<grid, 128, 0, st>>>(a); }
+void launch_interact(const TransportArgs& a, int grid, cudaStream_t st) { k_interact<<<grid, 256, 0, st>>>(a); }
+void launch_nee(const TransportArgs& a, int grid, cudaStream_t st) { k_nee<<<grid, 128, 0, st>>>(a); }
+
+}  // namespace usrt

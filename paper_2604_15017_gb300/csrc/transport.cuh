@@ -1,0 +1,54 @@
+// Wavefront transport: queues, counters, BVH queries and the per-path state.
+#pragma once
+
+#include "usrt_device.cuh"
+
+namespace usrt {
+
+// path queue, structure of arrays (48 B per path)
+struct PathQ {
+  float4* pa;   // (o.x, o.y, o.z, a)
+  float4* wt;   // (w.x, w.y, w.z, tau_hi)
+  uint4* meta;  // (path id, previous primitive code, medium | k << 8, bits(tau_lo))
+};
+
+// secondary-ray jobs queued by the interaction kernel
+struct NeeQ {
+  float4* job;   // (a, tau_hi, tau_lo, bits(scatterer id))
+  uint32_t* jm;  // medium | element << 8 | tx << 16
+};
+
+// device counters of one transport pass
+struct Counters {
+  uint32_t live[MAX_KMAX + 2];  // paths entering segment k
+  uint32_t nee[MAX_KMAX + 2];   // secondary jobs produced at segment k
+  uint32_t n_arr;               // arrivals appended
+  uint32_t dropped;             // arrivals dropped (crossing list overflow)
+  int status;                   // ST_* bits
+  uint32_t pad;
+};
+
+// arrival: (row = tx * n_elem + e, tq fixed-point time, bits(a), path id)
+typedef uint4 Arrival;
+
+struct TransportArgs {
+  SceneDev S;
+  Media med;
+  Acq acq;
+  PathQ qin, qout;
+  float2* hits;       // (t, bits(code)) per queue slot
+  NeeQ nee;
+  Arrival* arr;       // may be null (adjoint recompute: no arrivals)
+  uint32_t arr_cap;
+  uint32_t* record;   // may be null; index (path - path_base) * (kmax + 1) + k
+  long long path_base;
+  Counters* cnt;
+  int k;              // segment index
+};
+
+void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st);
+void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st);
+void launch_interact(const TransportArgs& a, int grid, cudaStream_t st);
+void launch_nee(const TransportArgs& a, int grid, cudaStream_t st);
+
+}  // namespace usrt

@@ -1,0 +1,220 @@
+// Device-side building blocks shared by the usrt kernels: Philox4x32-10, launch parameters,
+// scene layout, float-float time accumulation, the interface event and the pulse.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace usrt {
+
+constexpr int MAX_MEDIA = 32;
+constexpr int MAX_TX = 64;
+constexpr int MAX_ELEM = 256;
+constexpr int MAX_KMAX = 15;
+constexpr int K_MOM = 8;         // Taylor moments of the sort-based splat
+constexpr int MAX_TAPS = 96;     // pulse support in samples (both sides)
+constexpr int MAX_XINGS = 32;    // interface crossings of one secondary ray
+constexpr float T_MIN = 1e-7f;   // minimum hit distance [m]: no re-hit of the surface just left
+constexpr float PI_F = 3.14159265358979f;
+// amplitude attenuation per (dB/cm/MHz * Hz * m): ln(10)/20 * 1e-6 * 100
+constexpr float KAPPA_F = 1.1512925464970229e-05f;
+// arrival times are carried as fixed point in samples: tq = (u + TQ_OFFSET) * 2^TQ_FRAC
+constexpr int TQ_FRAC = 18;
+constexpr int TQ_OFFSET = 64;
+
+// primitive / event codes (record word): id bits 0-19, class 20-21, choice 22-23, aux 24-31
+enum : uint32_t { CLS_NONE = 0, CLS_XDCR = 1, CLS_TRI = 2, CLS_SCAT = 3 };
+enum : uint32_t { CH_NONE = 0, CH_REFLECT = 1, CH_TRANSMIT = 2, CH_TIR = 3 };
+__host__ __device__ __forceinline__ uint32_t prim_code(uint32_t cls, uint32_t id) { return (cls << 20) | id; }
+__host__ __device__ __forceinline__ uint32_t code_cls(uint32_t c) { return (c >> 20) & 3u; }
+__host__ __device__ __forceinline__ uint32_t code_id(uint32_t c) { return c & 0xFFFFFu; }
+
+// device status word bits
+enum : int { ST_OVERFLOW = 1, ST_TIMEOUT = 2 };
+
+// ------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
+    const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+// ------------------------------------------------------------------------------------------
+// Launch parameters (passed by value)
+// ------------------------------------------------------------------------------------------
+struct Media {
+  int M;
+  float c[MAX_MEDIA], rho[MAX_MEDIA], al[MAX_MEDIA];
+  float As, f0;
+};
+
+struct Acq {
+  int ne, ntx, ns, kmax, nr, n_emit, tx_elem, split_mode;
+  float pitch, hel, fs, bw, alpha_m, alpha_c, cbf, split_q;
+  uint32_t stream, key0, key1;
+  long long rays_per_tx;
+  float sin_tx[MAX_TX], cos_tx[MAX_TX];
+  float cos_lo[MAX_TX];  // cos(angle) - cos_tx (float-float steering cosine for the delays)
+};
+
+struct Img {
+  int nl, nd;
+  float x0, x1, z0, z1, dr, l1, l2;
+};
+
+// device-resident scene (BVH2 nodes of 4 float4; primitives in leaf order, 3 float4 each)
+struct SceneDev {
+  const float4* nodes;   // n0=(c0.lo.x,c0.hi.x,c0.lo.y,c0.hi.y) n1=(same for c1) n2=(c0 z, c1 z) n3=int4
+  const float4* prims;   // triangle: (v0, code) (e1, -) (e2, -); scatterer: (p, code) (-) (-)
+  const float4* tri_nrm; // by triangle id: (unit normal, bits(m_front | m_back << 16))
+  const float4* tri_v0;  // by triangle id: (v0, 0)
+  const float4* scat;    // by scatterer id: (p, amplitude)
+  const float4* nodes_t; // triangle-only BVH (secondary rays)
+  const float4* prims_t;
+  int n_nodes, n_tris, n_scat;
+  float rs2;
+};
+
+// ------------------------------------------------------------------------------------------
+// small vector helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 xyz(float4 v) { return f3(v.x, v.y, v.z); }
+
+// ------------------------------------------------------------------------------------------
+// float-float accumulation of the path time (error-free TwoSum, Knuth)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = __fadd_rn(hi, x);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// ------------------------------------------------------------------------------------------
+// float-float arithmetic (Dekker / Knuth error-free transformations) for delays that must be
+// resolved to ~1e-6 samples out of ~4000
+// ------------------------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return ff{s, e};
+}
+__device__ __forceinline__ ff ff_fast(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_addx(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.hi, b, -p);
+  return ff_fast(p, __fmaf_rn(a.lo, b, e));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return ff_fast(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  if (!(a.hi > 0.0f)) return ff{0.0f, 0.0f};
+  const float s = sqrtf(a.hi);
+  const float r = __fmaf_rn(-s, s, a.hi);  // exact residual
+  return ff_fast(s, __fdiv_rn(__fadd_rn(r, a.lo), __fmul_rn(2.0f, s)));
+}
+__device__ __forceinline__ ff ff_divf(float a, float b) {  // a / b
+  const float q = __fdiv_rn(a, b);
+  const float r = __fmaf_rn(-q, b, a);
+  return ff_fast(q, __fdiv_rn(r, b));
+}
+// split x = i + f, 0 <= f < 1, from a float-float
+__device__ __forceinline__ void ff_floor(ff u, int& i, float& f) {
+  const float fl = floorf(u.hi);
+  float fr = __fadd_rn(__fsub_rn(u.hi, fl), u.lo);
+  int ii = (int)fl;
+  if (fr < 0.0f) {
+    fr = __fadd_rn(fr, 1.0f);
+    ii -= 1;
+  } else if (fr >= 1.0f) {
+    fr = __fsub_rn(fr, 1.0f);
+    ii += 1;
+  }
+  if (fr >= 1.0f) fr = 0.99999994f;
+  i = ii;
+  f = fr;
+}
+
+// time (hi, lo) [s] -> fixed-point samples tq, or 0xFFFFFFFF outside [-TQ_OFFSET, 2^(32-TQ_FRAC) - TQ_OFFSET)
+__device__ __forceinline__ uint32_t time_to_tq(float hi, float lo, float fs) {
+  const float u = __fmul_rn(hi, fs);
+  const float e = __fmaf_rn(hi, fs, -u);  // exact product error
+  const float fl = floorf(u);
+  const float frac = (u - fl) + (e + lo * fs);  // u - fl is exact
+  const float base = fl + (float)TQ_OFFSET;
+  if (!(base >= 0.0f) || base >= (float)(1u << (32 - TQ_FRAC)) - 2.0f) return 0xFFFFFFFFu;
+  const long long q = (long long)base * (1ll << TQ_FRAC) + __float2ll_rn(frac * (float)(1 << TQ_FRAC));
+  if (q < 0 || q >= 0xFFFFFFFFll) return 0xFFFFFFFFu;
+  return (uint32_t)q;
+}
+
+// receive directivity, Eq. cutoff; cosd = cos of the angle to the element normal
+__device__ __forceinline__ float f_rx(float cosd, float am, float ac) {
+  const float th = acosf(fminf(1.0f, fmaxf(-1.0f, cosd)));
+  if (th <= am) return 1.0f;
+  if (th > ac) return 0.0f;
+  return (ac - th) / (ac - am);
+}
+
+// ------------------------------------------------------------------------------------------
+// Interface event (Sec. 2.3.2): w incident, nin unit normal back into medium 1.
+// R = (Z2 ci - Z1 ct)/(Z2 ci + Z1 ct), T = 2 Z2 ci/(Z2 ci + Z1 ct); Snell with sound speeds.
+// ------------------------------------------------------------------------------------------
+struct Iface {
+  bool tir;
+  float ci, ct, r, R, T;
+};
+__device__ __forceinline__ Iface iface(float3 w, float3 nin, float c1, float c2, float rho1, float rho2) {
+  Iface f;
+  f.ci = -dot3(w, nin);
+  f.r = c2 / c1;
+  const float si2 = fmaxf(0.0f, 1.0f - f.ci * f.ci);
+  const float st2 = f.r * f.r * si2;
+  f.tir = st2 >= 1.0f;
+  if (f.tir) {
+    f.ct = 0.0f;
+    f.R = 1.0f;
+    f.T = 0.0f;
+    return f;
+  }
+  f.ct = sqrtf(1.0f - st2);
+  const float A = rho2 * c2 * f.ci, B = rho1 * c1 * f.ct;
+  const float inv = 1.0f / (A + B);
+  f.R = (A - B) * inv;
+  f.T = 2.0f * A * inv;
+  return f;
+}
+
+}  // namespace usrt

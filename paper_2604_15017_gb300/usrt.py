@@ -1,0 +1,330 @@
+"""Python binding of the usrt C ABI (``include/usrt.h``).
+
+Argument marshalling only: every arithmetic step runs in the CUDA kernels of
+``_build/libusrt.so``.  PyTorch supplies device memory and the current CUDA stream; the
+library raises ``UsrtError`` when a call fails and ``RuntimeError`` when it cannot be loaded
+(there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libusrt.so")
+
+US_OK, US_ERR_ARG, US_ERR_OOM, US_ERR_CUDA, US_ERR_TIMEOUT, US_ERR_OVERFLOW, US_ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+MODE_RECORD, MODE_RECOMPUTE = 0, 1
+
+# the C ABI's entry points (each declared in include/usrt.h)
+EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_scene_release", "us_memory",
+           "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
+           "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
+           "us_transport_vjp", "us_adjoint"]
+
+
+class UsrtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("usrt error %d: %s" % (code, msg))
+        self.code = code
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_tris", C.c_int32), ("tris", C.POINTER(C.c_float)), ("media", C.POINTER(C.c_int32)),
+                ("n_media", C.c_int32), ("n_scat", C.c_int32), ("scat_pos", C.POINTER(C.c_float)),
+                ("scat_amp", C.POINTER(C.c_float)), ("r_s", C.c_float)]
+
+
+class AcqDesc(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("pitch", C.c_float), ("h_el", C.c_float), ("n_tx", C.c_int32),
+                ("angles", C.POINTER(C.c_float)), ("fs", C.c_float), ("n_samples", C.c_int32),
+                ("k_max", C.c_int32), ("n_rays", C.c_int32), ("bw", C.c_float), ("alpha_m", C.c_float),
+                ("alpha_c", C.c_float), ("c_bf", C.c_float), ("split_mode", C.c_int32), ("split_q", C.c_float),
+                ("stream_id", C.c_uint32), ("tx_elem", C.c_int32)]
+
+
+class ImgDesc(C.Structure):
+    _fields_ = [("n_lines", C.c_int32), ("n_depth", C.c_int32), ("x0", C.c_float), ("x1", C.c_float),
+                ("z0", C.c_float), ("z1", C.c_float), ("dr_db", C.c_float), ("lambda1", C.c_float),
+                ("lambda2", C.c_float)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_paths", C.c_int64), ("segments", C.c_int64), ("nee_queries", C.c_int64),
+                ("arrivals", C.c_int64), ("dropped", C.c_int64), ("status", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+VP = C.c_void_p
+
+
+def lib():
+    """Load the in-tree library (building it first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from . import build as _b
+                _b.build()
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("usrt CUDA library missing: " + LIB_PATH)
+            l = C.CDLL(LIB_PATH)
+            l.us_create.argtypes = [C.POINTER(VP), C.c_int, C.c_size_t]
+            l.us_destroy.argtypes = [VP]
+            l.us_destroy.restype = None
+            l.us_last_error.argtypes = [VP]
+            l.us_last_error.restype = C.c_char_p
+            l.us_scene_upload.argtypes = [VP, C.POINTER(SceneDesc), C.POINTER(C.c_uint64)]
+            l.us_scene_release.argtypes = [VP, C.c_uint64]
+            l.us_memory.argtypes = [VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+            l.us_philox_fill.argtypes = [VP] + [C.c_uint32] * 6 + [C.c_int64, VP, VP]
+            l.us_forward.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc), C.POINTER(ImgDesc),
+                                     C.c_uint64, C.c_int, VP, VP, VP]
+            l.us_get_stats.argtypes = [VP, C.POINTER(Stats)]
+            l.us_get_record.argtypes = [VP, C.c_int64, C.c_int64, VP, VP]
+            l.us_splat.argtypes = [VP, C.POINTER(AcqDesc), C.c_float, C.c_int64, VP, VP, VP, VP, VP, VP]
+            l.us_das.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP]
+            l.us_envlog.argtypes = [VP, C.POINTER(ImgDesc), VP, VP, VP]
+            l.us_bmode.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP]
+            l.us_loss.argtypes = [VP, C.POINTER(ImgDesc), VP, VP, VP, VP, VP]
+            l.us_envlog_vjp.argtypes = [VP, C.POINTER(ImgDesc), VP, VP, VP, VP]
+            l.us_das_adjoint.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP]
+            l.us_bmode_vjp.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP, VP]
+            l.us_splat_adjoint.argtypes = [VP, C.POINTER(AcqDesc), C.c_float, C.c_int64, VP, VP, VP, VP, VP, VP, VP,
+                                           VP, VP]
+            l.us_transport_vjp.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc), C.c_uint64,
+                                           C.c_int, VP, VP, VP]
+            l.us_adjoint.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc), C.POINTER(ImgDesc),
+                                     C.c_uint64, C.c_int, VP, VP, VP, VP, VP]
+            _lib = l
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+def acq_desc(acq):
+    """Acquisition dict (phantoms.acquisition) -> (AcqDesc, keep-alive angle array)."""
+    ang = _f32(acq["angles"])
+    d = AcqDesc(int(acq["n_elem"]), float(acq["pitch"]), float(acq["h_el"]), len(ang),
+                ang.ctypes.data_as(C.POINTER(C.c_float)), float(acq["fs"]), int(acq["n_samples"]),
+                int(acq["k_max"]), int(acq["n_rays"]), float(acq["bw"]), float(acq["alpha_m"]),
+                float(acq["alpha_c"]), float(acq["c_bf"]), int(acq.get("split_mode", 0)),
+                float(acq.get("split_q", 0.5)), int(acq.get("stream_id", 0)) & 0xFFFFFFFF,
+                int(acq.get("tx_elem", -1)))
+    return d, ang
+
+
+def img_desc(img):
+    return ImgDesc(int(img["n_lines"]), int(img["n_depth"]), float(img["x0"]), float(img["x1"]), float(img["z0"]),
+                   float(img["z1"]), float(img.get("dr_db", 60.0)), float(img.get("lambda1", 0.0)),
+                   float(img.get("lambda2", 1.0)))
+
+
+class Context:
+    """One library context on one CUDA device (scenes, records and workspaces stay resident)."""
+
+    def __init__(self, device=0, mem_budget_bytes=0):
+        self.device = torch.device("cuda", device)
+        h = VP()
+        rc = lib().us_create(C.byref(h), int(device), int(mem_budget_bytes))
+        if rc != US_OK:
+            raise UsrtError(rc, "us_create failed")
+        self.h = h
+        self.scene_media = {}
+
+    def _check(self, rc):
+        if rc != US_OK:
+            raise UsrtError(rc, lib().us_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().us_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def memory(self):
+        u, b = C.c_size_t(), C.c_size_t()
+        self._check(lib().us_memory(self.h, C.byref(u), C.byref(b)))
+        return u.value, b.value
+
+    # ---- scenes ---------------------------------------------------------------------------
+    def upload_scene(self, tris, media, n_media, scat_pos, scat_amp, r_s):
+        tris = _f32(np.asarray(tris).reshape(-1, 9))
+        media = np.ascontiguousarray(np.asarray(media, dtype=np.int32).reshape(-1, 2))
+        sp = _f32(np.asarray(scat_pos).reshape(-1, 3))
+        sa = _f32(np.asarray(scat_amp).reshape(-1))
+        d = SceneDesc(len(tris), tris.ctypes.data_as(C.POINTER(C.c_float)), media.ctypes.data_as(C.POINTER(C.c_int32)),
+                      int(n_media), len(sa), sp.ctypes.data_as(C.POINTER(C.c_float)),
+                      sa.ctypes.data_as(C.POINTER(C.c_float)), float(r_s))
+        sid = C.c_uint64()
+        self._check(lib().us_scene_upload(self.h, C.byref(d), C.byref(sid)))
+        self.scene_media[sid.value] = int(n_media)
+        return sid.value
+
+    def upload_workload(self, w):
+        return self.upload_scene(w["tris"], w["media"], w["M"], w["scat_pos"], w["scat_amp"], w["r_s"])
+
+    def release_scene(self, sid):
+        self._check(lib().us_scene_release(self.h, int(sid)))
+
+    # ---- S1 -----------------------------------------------------------------------------------
+    def philox_fill(self, c0, c1, c2, c3, k0, k1, n, out=None, stream=None):
+        out = out if out is not None else torch.empty(4 * n, dtype=torch.int32, device=self.device)
+        self._check(lib().us_philox_fill(self.h, c0 & 0xFFFFFFFF, c1, c2, c3, k0, k1, n, _ptr(out), _stream(stream)))
+        return out
+
+    # ---- forward ----------------------------------------------------------------------------
+    def rf_shape(self, acq):
+        return (len(acq["angles"]), int(acq["n_elem"]), int(acq["n_samples"]))
+
+    def forward(self, scene, theta, acq, img=None, seed=0, keep_record=False, rf=None, bmode=None, stream=None):
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img) if img is not None else None
+        rf = rf if rf is not None else torch.empty(self.rf_shape(acq), dtype=torch.float32, device=self.device)
+        if img is not None and bmode is None:
+            bmode = torch.empty((img["n_lines"], img["n_depth"]), dtype=torch.float32, device=self.device)
+        self._check(lib().us_forward(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad),
+                                     C.byref(idesc) if idesc is not None else None, int(seed) & (2**64 - 1),
+                                     int(bool(keep_record)), _ptr(rf), _ptr(bmode), _stream(stream)))
+        return rf, bmode
+
+    def stats(self):
+        s = Stats()
+        self._check(lib().us_get_stats(self.h, C.byref(s)))
+        return dict(n_paths=s.n_paths, segments=s.segments, nee_queries=s.nee_queries, arrivals=s.arrivals,
+                    dropped=s.dropped, status=s.status)
+
+    def record(self, path_lo, n, k_max, stream=None):
+        out = torch.empty((n, k_max + 1), dtype=torch.int32, device=self.device)
+        self._check(lib().us_get_record(self.h, int(path_lo), int(n), _ptr(out), _stream(stream)))
+        return out
+
+    def splat(self, acq, f0, tx, e, tau, a, rf=None, stream=None):
+        ad, ang = acq_desc(acq)
+        rf = rf if rf is not None else torch.empty(self.rf_shape(acq), dtype=torch.float32, device=self.device)
+        self._check(lib().us_splat(self.h, C.byref(ad), float(f0), int(tau.numel()), _ptr(tx), _ptr(e), _ptr(tau),
+                                   _ptr(a), _ptr(rf), _stream(stream)))
+        return rf
+
+    def das(self, acq, img, rf, out=None, stream=None):
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        out = out if out is not None else torch.empty((img["n_lines"], img["n_depth"]), dtype=torch.float32,
+                                                      device=self.device)
+        self._check(lib().us_das(self.h, C.byref(ad), C.byref(idesc), _ptr(rf), _ptr(out), _stream(stream)))
+        return out
+
+    def envlog(self, img, irf, out=None, stream=None):
+        idesc = img_desc(img)
+        out = out if out is not None else torch.empty_like(irf)
+        self._check(lib().us_envlog(self.h, C.byref(idesc), _ptr(irf), _ptr(out), _stream(stream)))
+        return out
+
+    def bmode(self, acq, img, rf, out=None, stream=None):
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        out = out if out is not None else torch.empty((img["n_lines"], img["n_depth"]), dtype=torch.float32,
+                                                      device=self.device)
+        self._check(lib().us_bmode(self.h, C.byref(ad), C.byref(idesc), _ptr(rf), _ptr(out), _stream(stream)))
+        return out
+
+    # ---- loss and adjoint -------------------------------------------------------------------
+    def loss(self, img, b, bref, grad=True, stream=None):
+        idesc = img_desc(img)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        gb = torch.empty_like(b) if grad else None
+        self._check(lib().us_loss(self.h, C.byref(idesc), _ptr(b), _ptr(bref), _ptr(loss), _ptr(gb), _stream(stream)))
+        return loss, gb
+
+    def envlog_vjp(self, img, irf, gb, stream=None):
+        idesc = img_desc(img)
+        gi = torch.empty_like(irf)
+        self._check(lib().us_envlog_vjp(self.h, C.byref(idesc), _ptr(irf), _ptr(gb), _ptr(gi), _stream(stream)))
+        return gi
+
+    def das_adjoint(self, acq, img, gi, stream=None):
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        grf = torch.empty(self.rf_shape(acq), dtype=torch.float32, device=self.device)
+        self._check(lib().us_das_adjoint(self.h, C.byref(ad), C.byref(idesc), _ptr(gi), _ptr(grf), _stream(stream)))
+        return grf
+
+    def bmode_vjp(self, acq, img, rf, gb, stream=None):
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        grf = torch.empty(self.rf_shape(acq), dtype=torch.float32, device=self.device)
+        self._check(lib().us_bmode_vjp(self.h, C.byref(ad), C.byref(idesc), _ptr(rf), _ptr(gb), _ptr(grf),
+                                       _stream(stream)))
+        return grf
+
+    def splat_adjoint(self, acq, f0, tx, e, tau, a, grf, stream=None):
+        ad, ang = acq_desc(acq)
+        n = int(tau.numel())
+        ga, gt, gf = (torch.empty(n, dtype=torch.float32, device=self.device) for _ in range(3))
+        self._check(lib().us_splat_adjoint(self.h, C.byref(ad), float(f0), n, _ptr(tx), _ptr(e), _ptr(tau), _ptr(a),
+                                           _ptr(grf), _ptr(ga), _ptr(gt), _ptr(gf), _stream(stream)))
+        return ga, gt, gf
+
+    def transport_vjp(self, scene, theta, acq, seed, grf, mode=MODE_RECORD, out=None, stream=None):
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        out = out if out is not None else torch.empty(len(th), dtype=torch.float32, device=self.device)
+        self._check(lib().us_transport_vjp(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad),
+                                           int(seed) & (2**64 - 1), int(mode), _ptr(grf), _ptr(out), _stream(stream)))
+        return out
+
+    def adjoint(self, scene, theta, acq, img, seed, rf, gb, mode=MODE_RECORD, want_grf=False, stream=None):
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
+        grf = torch.empty(self.rf_shape(acq), dtype=torch.float32, device=self.device) if want_grf else None
+        self._check(lib().us_adjoint(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad),
+                                     C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
+                                     _ptr(gth), _ptr(grf), _stream(stream)))
+        return gth, grf
+
+
+class BModeSimulation(torch.autograd.Function):
+    """theta -> B-mode image, differentiable with the fixed-sample adjoint (Sec. 3.2-3.3).
+
+    forward = us_forward (transport, splat, DAS, envelope, log) keeping the path record;
+    backward = us_adjoint (envelope/log VJP, transposed DAS, splat adjoint, path adjoint).
+    theta is a CPU float tensor; the returned gradient is moved back to the CPU.
+    """
+
+    @staticmethod
+    def forward(fctx, theta, ctx, scene, acq, img, seed):
+        th = theta.detach().cpu().numpy().astype(np.float32)
+        rf, b = ctx.forward(scene, th, acq, img, seed, keep_record=True)
+        fctx.save_for_backward(theta)
+        fctx.usrt = (ctx, scene, acq, img, seed, th, rf)
+        return b
+
+    @staticmethod
+    def backward(fctx, gb):
+        ctx, scene, acq, img, seed, th, rf = fctx.usrt
+        gth, _ = ctx.adjoint(scene, th, acq, img, seed, rf, gb.contiguous().float(), mode=MODE_RECORD)
+        return gth.to(fctx.saved_tensors[0].device, fctx.saved_tensors[0].dtype), None, None, None, None, None

@@ -1,0 +1,379 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, stage by stage and
+end to end.  Tolerances (north star, or derived from FP32 arithmetic where it states none):
+
+* Philox streams: bit-exact.
+* per-path event sequences: >= 99.99 % of paths identical (primitive, class, choice, element).
+* RF: relative L2 <= 1e-4.
+* B-mode: max |dB| <= 0.05 on pixels above -60 dB.
+* DAS / transposed DAS: per pixel |error| <= 2e-3 * DAS(|RF|) + 1e-6 max: the interpolation
+  position u ~ 4096 samples carries a few FP32 ulps (~1e-3 samples) of error, and a lerp
+  moves by at most |a| + |b| per sample of position error.
+* splat of a given arrival list: relative L2 <= 1e-5 (8-moment truncation < 1e-7, FP32 sums).
+* adjoint: within 1e-3 relative of the oracle's FP64 gradient for the same dL/dRF.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2604_15017_gb300 import phantoms as P
+
+pytestmark = pytest.mark.gpu
+
+MM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_15017_gb300 import usrt
+
+    c = usrt.Context(0)
+    yield c
+    c.close()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype).cuda()
+
+
+def small_inclusions(n_rays=200, k_max=6, n_tx=2):
+    return P.inclusions(n_regions=3, n_scat=3000, n_rays=n_rays, k_max=k_max, n_samples=2048,
+                        angles_deg=list(np.linspace(-8, 8, n_tx)), n_lines=64, n_depth=512, n_elem=32, n_lat=24,
+                        n_lon=40)
+
+
+def decode(rec):
+    r = rec.astype(np.int64) & 0xFFFFFFFF
+    return dict(id=r & 0xFFFFF, cls=(r >> 20) & 3, choice=(r >> 22) & 3, aux=(r >> 24) & 0xFF)
+
+
+def sequence_agreement(gpu_rec, ora):
+    g = decode(gpu_rec)
+    same = (g["cls"] == ora["cls"]) & ((g["id"] == ora["id"]) | (ora["cls"] == 0))
+    tri = ora["cls"] == O.CLS_TRI
+    same &= ~tri | (g["choice"] == ora["choice"]) | (ora["choice"] == O.CH_NONE)
+    scat = ora["cls"] == O.CLS_SCAT
+    same &= ~scat | (g["aux"] == np.maximum(ora["aux"], 0)) | (ora["aux"] < 0)
+    return same.all(axis=1)
+
+
+# ------------------------------------------------------------------------------------------
+# S1
+# ------------------------------------------------------------------------------------------
+def test_philox_bit_exact_1e8_draws(ctx):
+    n = 25_000_000  # blocks of 4 words
+    out = ctx.philox_fill(123, 7, 5, 9, 0xDEADBEEF, 0x12345678, n)
+    got = out.cpu().numpy().view(np.uint32).reshape(n, 4)
+    ref = O.philox_fill(123, 7, 5, 9, 0xDEADBEEF, 0x12345678, n)
+    assert np.array_equal(got, ref)
+
+
+def test_philox_counter_wraps_like_the_oracle(ctx):
+    out = ctx.philox_fill(0xFFFFFFF0, 1, 2, 3, 4, 5, 64).cpu().numpy().view(np.uint32).reshape(64, 4)
+    ref = O.philox_fill(0xFFFFFFF0, 1, 2, 3, 4, 5, 64)
+    assert np.array_equal(out, ref)
+
+
+# ------------------------------------------------------------------------------------------
+# S6 splat of a given arrival list
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [0, 1, 1000, 200000])
+def test_splat_matches_oracle(ctx, n):
+    acq = P.acquisition(48, 0.3 * MM, 2048, [-5.0, 0.0, 7.0], 1, 1, 1540.0)
+    rng = np.random.default_rng(n)
+    tx = rng.integers(0, 3, n).astype(np.int32)
+    e = rng.integers(0, 48, n).astype(np.int32)
+    tau = rng.uniform(-2e-6, 2048 / 40e6 + 2e-6, n)  # includes arrivals beyond both record ends
+    tau[: n // 10] = np.round(tau[: n // 10] * 40e6) / 40e6  # exactly on samples
+    a = rng.normal(size=n)
+    ref = O.splat(acq, 5e6, tx, e, tau, a)
+    rf = ctx.splat(acq, 5e6, dev(tx, torch.int32), dev(e, torch.int32), dev(tau), dev(a)).cpu().numpy()
+    if n == 0:
+        assert np.all(rf == 0)
+        return
+    # the GPU carries tau in float: compare against the oracle fed the same rounded times
+    ref32 = O.splat(acq, 5e6, tx, e, tau.astype(np.float32).astype(np.float64), a.astype(np.float32))
+    assert rel_l2(rf, ref32) <= 1e-5, rel_l2(rf, ref32)
+    assert rel_l2(rf, ref) <= 1e-4
+
+
+def test_splat_other_frequency_and_bandwidth(ctx):
+    acq = P.acquisition(8, 0.3 * MM, 1024, [0.0], 1, 1, 1540.0, fs=31.25e6, bw=0.8)
+    rng = np.random.default_rng(4)
+    n = 5000
+    tx = np.zeros(n, np.int32)
+    e = rng.integers(0, 8, n).astype(np.int32)
+    tau = rng.uniform(0, 1024 / 31.25e6, n).astype(np.float32).astype(np.float64)
+    a = rng.normal(size=n).astype(np.float32)
+    ref = O.splat(acq, 3.5e6, tx, e, tau, a)
+    rf = ctx.splat(acq, 3.5e6, dev(tx, torch.int32), dev(e, torch.int32), dev(tau), dev(a)).cpu().numpy()
+    assert rel_l2(rf, ref) <= 1e-5
+
+
+# ------------------------------------------------------------------------------------------
+# S7 / S10 DAS and its transpose, S8 envelope + log, S9 loss and envelope/log VJP
+# ------------------------------------------------------------------------------------------
+def das_case():
+    acq = P.acquisition(64, 0.3 * MM, 2048, [-10.0, 0.0, 12.0], 1, 1, 1540.0)
+    img = P.image(96, 512, -9.45 * MM, 9.45 * MM, 1 * MM, 38 * MM)
+    rng = np.random.default_rng(8)
+    n = 20000
+    rf = O.splat(acq, 5e6, rng.integers(0, 3, n), rng.integers(0, 64, n), rng.uniform(0, 2048 / 40e6, n),
+                 rng.normal(size=n))
+    return acq, img, rf.astype(np.float32).astype(np.float64)
+
+
+def test_das_matches_oracle(ctx):
+    acq, img, rf = das_case()
+    ref = O.das(acq, img, rf)
+    bound = 2e-3 * O.das(acq, img, np.abs(rf)) + 1e-6 * np.abs(ref).max()
+    got = ctx.das(acq, img, dev(rf)).cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
+
+
+def test_das_adjoint_matches_oracle_and_dot_product(ctx):
+    acq, img, rf = das_case()
+    rng = np.random.default_rng(9)
+    gi = rng.normal(size=(img["n_lines"], img["n_depth"])).astype(np.float32).astype(np.float64)
+    ref = O.das_adjoint(acq, img, gi)
+    got = ctx.das_adjoint(acq, img, dev(gi)).cpu().numpy()
+    bound = 2e-3 * O.das_adjoint(acq, img, np.abs(gi)) + 1e-6 * np.abs(ref).max()
+    # transposed taps land on the same two samples; the bound covers a shifted split
+    assert rel_l2(got, ref) <= 2e-3
+    x = rng.normal(size=rf.shape)
+    lhs = float((ctx.das(acq, img, dev(x)).double().cpu().numpy() * gi).sum())
+    rhs = float((x * got).sum())
+    assert abs(lhs - rhs) <= 1e-4 * (np.abs(x).sum() * np.abs(gi).max())
+    assert np.mean(np.abs(got - ref) <= bound + 1e-5 * np.abs(ref).max()) > 0.999
+
+
+def test_envlog_matches_oracle(ctx):
+    acq, img, rf = das_case()
+    irf = O.das(acq, img, rf).astype(np.float32).astype(np.float64)
+    env = O.envelope(img, irf)
+    bref, am = O.log_compress(img, env)
+    b = ctx.envlog(img, dev(irf)).cpu().numpy()
+    live = bref > -60.0
+    assert live.mean() > 0.05
+    assert np.max(np.abs(b - bref)[live]) <= 0.05
+    assert np.max(np.abs(b - bref)) <= 0.05 + 1e-6  # clipped pixels stay at -DR (or cross it by < tol)
+
+
+def test_bmode_is_das_then_envlog(ctx):
+    acq, img, rf = das_case()
+    r = dev(rf)
+    b1 = ctx.bmode(acq, img, r)
+    b2 = ctx.envlog(img, ctx.das(acq, img, r))
+    assert torch.equal(b1, b2)
+
+
+def test_loss_matches_oracle(ctx):
+    img = P.image(64, 256, 0, 1, 0, 1, lambda1=0.3, lambda2=0.7)
+    rng = np.random.default_rng(10)
+    b = rng.uniform(-60, 0, (64, 256)).astype(np.float32).astype(np.float64)
+    bref = rng.uniform(-60, 0, (64, 256)).astype(np.float32).astype(np.float64)
+    l_ref, g_ref = O.loss(img, b, bref)
+    l, g = ctx.loss(img, dev(b), dev(bref))
+    assert abs(float(l) - l_ref) <= 1e-5 * abs(l_ref)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= 1e-6
+
+
+def test_envlog_vjp_matches_oracle(ctx):
+    acq, img, rf = das_case()
+    img = dict(img, dr_db=40.0)
+    irf = O.das(acq, img, rf).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(11)
+    gb = rng.normal(size=irf.shape).astype(np.float32).astype(np.float64)
+    ref = O.envlog_vjp(img, irf, gb)
+    got = ctx.envlog_vjp(img, dev(irf), dev(gb)).cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-3, rel_l2(got, ref)
+
+
+def test_bmode_vjp_matches_oracle(ctx):
+    acq, img, rf = das_case()
+    rng = np.random.default_rng(12)
+    gb = rng.normal(size=(img["n_lines"], img["n_depth"])).astype(np.float32).astype(np.float64)
+    ref = O.bmode_vjp(acq, img, rf, gb)
+    got = ctx.bmode_vjp(acq, img, dev(rf), dev(gb)).cpu().numpy()
+    assert rel_l2(got, ref) <= 5e-3, rel_l2(got, ref)
+
+
+# ------------------------------------------------------------------------------------------
+# S11 splat adjoint
+# ------------------------------------------------------------------------------------------
+def test_splat_adjoint_matches_oracle(ctx):
+    acq = P.acquisition(16, 0.3 * MM, 2048, [0.0, 4.0], 1, 1, 1540.0)
+    rng = np.random.default_rng(13)
+    n = 4000
+    tx = rng.integers(0, 2, n).astype(np.int32)
+    e = rng.integers(0, 16, n).astype(np.int32)
+    tau = rng.uniform(-1e-6, 2048 / 40e6 + 1e-6, n).astype(np.float32).astype(np.float64)
+    a = rng.normal(size=n).astype(np.float32).astype(np.float64)
+    grf = rng.normal(size=(2, 16, 2048)).astype(np.float32).astype(np.float64)
+    ra, rt, rf_ = O.splat_adjoint(acq, 5e6, tx, e, tau, a, grf)
+    ga, gt, gf = ctx.splat_adjoint(acq, 5e6, dev(tx, torch.int32), dev(e, torch.int32), dev(tau), dev(a), dev(grf))
+    for got, ref in [(ga, ra), (gt, rt), (gf, rf_)]:
+        g = got.cpu().numpy()
+        assert rel_l2(g, ref) <= 1e-4, rel_l2(g, ref)
+
+
+# ------------------------------------------------------------------------------------------
+# transport: event sequences, RF and B-mode end to end
+# ------------------------------------------------------------------------------------------
+def forward_pair(ctx, w, seed=None):
+    seed = w["seed"] if seed is None else seed
+    sid = ctx.upload_workload(w)
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=seed, keep_record=True)
+    torch.cuda.synchronize()
+    ref = O.forward(w, seed=seed)
+    return sid, rf, b, ref
+
+
+@pytest.mark.parametrize("make", [lambda: P.two_layer(), lambda: P.slab_scatterers(n_rays=2000),
+                                  lambda: small_inclusions(n_rays=400)])
+def test_transport_end_to_end_parity(ctx, make):
+    w = make()
+    sid, rf, b, ref = forward_pair(ctx, w)
+    acq = w["acq"]
+    n_paths = len(acq["angles"]) * acq["n_elem"] * acq["n_rays"]
+    rec = ctx.record(0, n_paths, acq["k_max"]).cpu().numpy()
+    same = sequence_agreement(rec, ref["run"].records())
+    assert same.mean() >= 0.9999, (same.mean(), np.flatnonzero(~same)[:10])
+    st = ctx.stats()
+    assert st["status"] == 0 and st["dropped"] == 0
+    assert st["segments"] == ref["run"].counters()["segments"] or same.mean() < 1
+    rf_g = rf.double().cpu().numpy()
+    assert rel_l2(rf_g, ref["rf"]) <= 1e-4, rel_l2(rf_g, ref["rf"])
+    bg = b.cpu().numpy()
+    live = ref["b"] > -60.0
+    assert np.max(np.abs(bg - ref["b"])[live]) <= 0.05
+    ctx.release_scene(sid)
+
+
+def test_stats_count_segments_and_secondary_rays(ctx):
+    w = P.slab_scatterers(n_rays=500)
+    sid, rf, b, ref = forward_pair(ctx, w)
+    st = ctx.stats()
+    c = ref["run"].counters()
+    assert abs(st["segments"] - c["segments"]) <= 1e-4 * c["segments"]
+    assert abs(st["nee_queries"] - c["nee"]) <= 1e-4 * max(c["nee"], 1)
+    ctx.release_scene(sid)
+
+
+def test_full_size_inclusions_sampled_paths(ctx):
+    """The 200k-triangle, 1e5-scatterer workload at full size: event sequences of a contiguous
+    sample of paths (the oracle traces them one by one with its own BVH)."""
+    w = P.inclusions()
+    sid = ctx.upload_workload(w)
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    assert st["n_paths"] == 16 * 128 * 7813 and st["status"] == 0
+    assert torch.isfinite(rf).all() and torch.isfinite(b).all()
+    sc = O.Scene.from_workload(w)
+    k1 = w["acq"]["k_max"] + 1
+    for lo in (0, 8_000_000, 16 * 128 * 7813 - 20000):
+        run = O.Run(sc, w["theta"], w["M"], w["acq"], w["seed"], path_lo=lo, path_hi=lo + 20000)
+        rec = ctx.record(lo, 20000, w["acq"]["k_max"]).cpu().numpy()
+        same = sequence_agreement(rec, run.records())
+        assert same.mean() >= 0.999, same.mean()
+    ctx.release_scene(sid)
+
+
+# ------------------------------------------------------------------------------------------
+# S12 transport adjoint
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [0, 1])
+def test_transport_vjp_matches_oracle_gradient(ctx, mode):
+    w = P.slab_scatterers(n_rays=1500)
+    sid, rf, b, ref = forward_pair(ctx, w)
+    run = ref["run"]
+    rng = np.random.default_rng(14)
+    grf = O.bmode_vjp(w["acq"], w["img"], ref["rf"], rng.normal(size=ref["b"].shape) * (ref["b"] > -60))
+    grf32 = grf.astype(np.float32).astype(np.float64)
+    g_ref = run.gradient(grf32)
+    g = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf32), mode=mode).double().cpu().numpy()
+    scale = np.abs(g_ref * w["theta"])
+    err = np.abs(g - g_ref) * np.abs(w["theta"])
+    assert np.all(err <= 1e-3 * scale + 1e-5 * scale.max()), (g, g_ref)
+    ctx.release_scene(sid)
+
+
+def test_transport_vjp_inclusions(ctx):
+    w = small_inclusions(n_rays=300, k_max=5, n_tx=1)
+    sid, rf, b, ref = forward_pair(ctx, w)
+    rng = np.random.default_rng(15)
+    grf = rng.normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
+    g_ref = ref["run"].gradient(grf)
+    g = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=0).double().cpu().numpy()
+    scale = np.abs(g_ref * w["theta"])
+    err = np.abs(g - g_ref) * np.abs(w["theta"])
+    assert np.all(err <= 1e-3 * scale + 1e-4 * scale.max()), np.c_[g, g_ref]
+    ctx.release_scene(sid)
+
+
+def test_adjoint_end_to_end_and_autograd(ctx):
+    from paper_2604_15017_gb300 import usrt
+
+    w = P.slab_scatterers(n_rays=800)
+    sid = ctx.upload_workload(w)
+    bref_ref = O.forward(w, theta=w["theta_target"])["b"]
+    bref = dev(bref_ref)
+    th = torch.tensor(w["theta"], dtype=torch.float32, requires_grad=True)
+    b = usrt.BModeSimulation.apply(th, ctx, sid, w["acq"], w["img"], w["seed"])
+    loss = ((b - bref) ** 2).mean()
+    loss.backward()
+    g_gpu = th.grad.double().numpy()
+    # oracle: same chain on its own forward
+    ref = O.forward(w)
+    _, gb = O.loss(w["img"], ref["b"], bref_ref)
+    grf = O.bmode_vjp(w["acq"], w["img"], ref["rf"], gb)
+    g_ref = ref["run"].gradient(grf)
+    scale = np.abs(g_ref * w["theta"])
+    err = np.abs(g_gpu - g_ref) * np.abs(w["theta"])
+    assert np.all(err <= 2e-2 * scale + 1e-3 * scale.max()), np.c_[g_gpu, g_ref]
+    ctx.release_scene(sid)
+
+
+def test_record_mode_needs_matching_forward(ctx):
+    from paper_2604_15017_gb300 import usrt
+
+    w = P.two_layer(n_rays=100)
+    sid = ctx.upload_workload(w)
+    ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=1, keep_record=True)
+    grf = torch.zeros(ctx.rf_shape(w["acq"]), device="cuda")
+    with pytest.raises(usrt.UsrtError) as ei:
+        ctx.transport_vjp(sid, w["theta"], w["acq"], 2, grf, mode=0)
+    assert ei.value.code == usrt.US_ERR_STATE
+    ctx.release_scene(sid)
+
+
+def test_invalid_arguments_are_refused(ctx):
+    from paper_2604_15017_gb300 import usrt
+
+    w = P.two_layer(n_rays=10)
+    sid = ctx.upload_workload(w)
+    bad = dict(w["acq"], n_samples=4098)
+    with pytest.raises(usrt.UsrtError) as ei:
+        ctx.forward(sid, w["theta"], bad, None, rf=torch.empty(1, 64, 4098, device="cuda"))
+    assert ei.value.code == usrt.US_ERR_ARG
+    with pytest.raises(usrt.UsrtError):
+        ctx.forward(12345, w["theta"], w["acq"], w["img"])
+    ctx.release_scene(sid)
+
+
+def test_memory_budget_refuses_admission():
+    from paper_2604_15017_gb300 import usrt
+
+    c = usrt.Context(0, mem_budget_bytes=1 << 20)
+    w = P.inclusions(n_scat=1000)
+    with pytest.raises(usrt.UsrtError) as ei:
+        c.upload_workload(w)
+    assert ei.value.code == usrt.US_ERR_OOM
+    c.close()
