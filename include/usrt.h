@@ -181,6 +181,25 @@ int us_das(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const fl
  * dynamic-range clip, irf_dev -> bmode_dev. */
 int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* bmode_dev, void* stream);
 
+/* Allocation-free S8: the same fused envelope + log compression as us_envlog, for callers that
+ * cannot allocate device memory at call time (work issued inside another framework's memory
+ * pool or under a hard memory cap, work enqueued while a stream is being captured, or serving
+ * loops that cannot afford a first-call allocation and the synchronisation it implies).  The
+ * paper has no counterpart; this is a deployment variant.
+ *   - Needs no context and calls no allocator: its scratch (the envelope image and the packed
+ *     maximum) lives in a fixed device array of the library, sized for at most
+ *     US_ENVLOG_NOALLOC_MAX_PIXELS = n_lines * n_depth pixels (1 MiB of floats), that every GPU
+ *     which loads the library holds until the process exits.
+ *   - Runs on the current CUDA device.  The first call on each device resolves that array's
+ *     address and the launch shape; make that first call before any stream capture.
+ *   - All calls share the one array and each call overwrites it (the maximum is cleared at the
+ *     start of every call), so calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race and must be serialised by the caller.
+ *   - Returns US_ERR_ARG for a NULL pointer, an invalid image shape or more pixels than the
+ *     limit; US_ERR_CUDA if the set-up or the launch fails.  There is no us_last_error text. */
+#define US_ENVLOG_NOALLOC_MAX_PIXELS (256 * 1024)
+int us_envlog_noalloc(const us_img_desc* img, const float* irf_dev, float* bmode_dev, void* stream);
+
 /* RF -> B-mode (S7 + S8). */
 int us_bmode(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
              float* bmode_dev, void* stream);

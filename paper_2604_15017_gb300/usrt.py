@@ -24,7 +24,7 @@ MODE_RECORD, MODE_RECOMPUTE = 0, 1
 EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_scene_release", "us_memory",
            "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
-           "us_transport_vjp", "us_adjoint"]
+           "us_transport_vjp", "us_adjoint", "us_envlog_noalloc"]
 
 
 class UsrtError(RuntimeError):
