@@ -99,6 +99,69 @@ def peaks():
         return {}
 
 
+# algorithmic work per unit of each stage
+FMA_LANES_PER_SM = 128  # FP32 lanes per SM (sm_100-class)
+
+
+def alu_peak_tflops(pk, n_sms):
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return n_sms * FMA_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def traverse_flops_per_query(n_prims):
+    # 2 log2(N) node visits x 2 box tests x 12 flop + 4 triangle tests x 30 flop
+    return 2 * math.ceil(math.log2(max(2, n_prims))) * 2 * 12 + 4 * 30
+
+
+def stage_work(stage, w, stats, n_prims):
+    """(bound, algorithmic work per step in flop or bytes) of a stage."""
+    acq, img = w["acq"], w["img"]
+    taps = img["n_lines"] * img["n_depth"] * acq["n_elem"] * len(acq["angles"])
+    rows = acq["n_elem"] * len(acq["angles"])
+    if stage == "traverse":
+        return "alu", stats["segments"] * traverse_flops_per_query(n_prims)
+    if stage == "nee":
+        return "alu", stats["nee_queries"] * traverse_flops_per_query(w["tris"].shape[0])
+    if stage in ("path_adj", "nee_adj"):
+        return "alu", 300 * stats["segments"] + 57 * 30 * stats["arrivals"]
+    if stage in ("das", "das_adj"):
+        return "alu", 25 * taps
+    if stage in ("splat_sort", "splat_rows"):
+        return "hbm", 16 * stats["arrivals"] + 4 * rows * acq["n_samples"]
+    if stage == "interact":
+        return "hbm", 96 * stats["segments"]
+    return "hbm", 8 * img["n_lines"] * img["n_depth"]
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, or None when the
+    kernel's sources changed since the capture (the summary records their hash)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", kernel + ".md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    srcs = vals.get("sources", "").split()
+    h = hashlib.sha256()
+    for f in srcs:
+        fp = os.path.join(ROOT, "paper_2604_15017_gb300", "csrc", f)
+        if not os.path.exists(fp):
+            return None
+        h.update(open(fp, "rb").read())
+    if h.hexdigest()[:16] != vals.get("sources_sha256", ""):
+        return None
+    try:
+        return float(vals["dram_bytes_per_step"]) / float(vals["launches_per_step"])
+    except Exception:
+        return None
+
+
 # --------------------------------------------------------------------------------------------
 def cpu_baseline(w, seconds, seed):
     """The FP64 oracle as it stands on the host cores: transport + splat of a contiguous sample
@@ -216,6 +279,8 @@ def main():
             dist.barrier()
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
@@ -226,6 +291,9 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
+    stages = ctx.profile_read()
+    ctx.profile(False)
+    gpu_launches = ctx.launch_count() - launches0
     if world > 1:
         import torch.distributed as dist
 
@@ -254,6 +322,29 @@ def main():
     e2e = {"value": segs_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bref_h.numel() * 4,
            "d2h_bytes_per_step": 4 * (len(theta) + 1)}
 
+    # roofline of the dominant stage, from its live CUDA-event time over the timed region
+    n_prims = int(w["tris"].shape[0] + w["scat_pos"].shape[0])
+    pk = peaks()
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / args.steps
+    dom_launches = max(1, stages[dom][1] // args.steps)
+    bound, work = stage_work(dom, w, stats, n_prims)
+    if bound == "alu":
+        achieved = work / (dom_ms * 1e-3) / 1e12
+        peak = alu_peak_tflops(pk, torch.cuda.get_device_properties(local).multi_processor_count)
+        unit = "TFLOP/s"
+    else:
+        achieved = work / (dom_ms * 1e-3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        unit = "GB/s"
+    kernel_of = {"traverse": "k_traverse", "path_adj": "k_path_adjoint", "nee": "k_nee", "das": "k_das",
+                 "splat_rows": "k_row_splat", "nee_adj": "k_nee_adjoint"}
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": profile_traffic(kernel_of.get(dom, dom)), "kernel": kernel_of.get(dom, dom),
+                "stage_ms_per_step": dom_ms, "launches_per_step": dom_launches,
+                "work_per_step": work, "peak_source": "measured" if bound == "hbm" else
+                "derived: SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"}
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -262,7 +353,8 @@ def main():
                       "segments_per_step": stats["segments"], "nee_queries_per_step": stats["nee_queries"],
                       "arrivals_per_step": stats["arrivals"], "frames_per_s": world * 1e3 / ms,
                       "l2": "per-step working set (path queues + arrivals, ~4 GB) exceeds L2; scene BVH resident"},
-           "clocks": clk.summary(), "e2e": e2e, "gpu_launches": None}
+           "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+           "stages_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in stages.items() if v[1]}}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, seed)
     if rank == 0:

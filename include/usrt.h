@@ -133,6 +133,29 @@ int us_scene_release(us_ctx* ctx, uint64_t scene_id);
 int us_memory(us_ctx* ctx, size_t* used, size_t* budget);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Tracing: per-stage device time and kernel launch counts                                   */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Stages timed by us_profile (CUDA events recorded on the launching stream around each
+ * stage's kernels). */
+enum {
+  US_STAGE_GENERATE = 0, US_STAGE_TRAVERSE, US_STAGE_INTERACT, US_STAGE_NEE, US_STAGE_SPLAT_SORT,
+  US_STAGE_SPLAT_ROWS, US_STAGE_DAS, US_STAGE_ENVLOG, US_STAGE_LOSS, US_STAGE_ENVLOG_VJP, US_STAGE_DAS_ADJ,
+  US_STAGE_NEE_ADJ, US_STAGE_PATH_ADJ, US_STAGE_OTHER, US_N_STAGES
+};
+
+/* enable != 0 starts recording stage events (and clears what was accumulated); 0 stops. */
+int us_profile(us_ctx* ctx, int enable);
+
+/* Synchronise on the recorded events and return, per stage, the summed device time [ms] and
+ * the number of kernels launched since the last us_profile(ctx, 1).  Arrays hold n entries
+ * (at most US_N_STAGES are written). */
+int us_profile_read(us_ctx* ctx, double* ms, int64_t* launches, int n);
+
+/* Total number of kernels this context has launched since it was created. */
+int us_launch_count(us_ctx* ctx, int64_t* n);
+
+/* ---------------------------------------------------------------------------------------- */
 /* S1: sample streams                                                                        */
 /* ---------------------------------------------------------------------------------------- */
 

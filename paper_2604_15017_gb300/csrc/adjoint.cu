@@ -97,10 +97,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
   float Aa[MAX_KMAX + 1], SA[MAX_KMAX + 1], ST[MAX_KMAX + 1];
   int Mk[MAX_KMAX + 1];
   uint32_t Rw[MAX_KMAX + 1];
-  float xt[MAX_XINGS];
-  uint32_t xid[MAX_XINGS];
   const float kap = KAPPA_F;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < A.n_paths; i += gridDim.x * blockDim.x) {
+  const uint32_t n_act = *A.n_active;
+  for (uint32_t ai = blockIdx.x * blockDim.x + threadIdx.x; ai < n_act; ai += gridDim.x * blockDim.x) {
+    const uint32_t i = A.active[ai];
     const long long path = A.path_base + i;
     const int tx = (int)(path / q.rays_per_tx);
     const long long local = path - (long long)tx * q.rays_per_tx;
@@ -174,62 +174,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           w = w * f.r + nin * (f.r * f.ci - f.ct);
           m = m2;
         }
-      } else {  // scatterer: secondary ray, whose geometry does not depend on theta
-        const int e2 = (int)(r >> 24);
-        const float4 sc = __ldg(&A.S.scat[id]);
-        float nh = th, nl = tl;
-        float3 d;
-        float D;
-        const NeeOut no = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
-        if (no.ok) {
-          const float k_n = med.As * sc.w * no.gain;  // a_n = a1 * k_n
-          const float a_n = a1 * k_n;
-          float ga, gt, gf;
-          splat_adj_gather(A.grf + ((size_t)tx * q.ne + e2) * q.ns, nh, nl, a_n, A.pulse, ga, gt, gf);
-          ADD(acc[iF0], gf);
-          const float Ga = ga * a_n;  // adjoint of log a_n
-          ADD(acc[iAs], ga * a1 * sc.w * no.gain);
-          ADD(acc[iF0], Ga * (-kap * no.sum_al));
-          // sub-segments and crossings again, with derivatives
-          float tprev = 0.0f;
-          int mm_cur = m;
-          for (int c = 0; c <= no.n; ++c) {
-            const float tc = c < no.n ? xt[c] : D;
-            const float l = tc - tprev;
-            ADD(acc[3 * mm_cur + 2], Ga * (-kap * med.f0 * l));
-            ADD(acc[3 * mm_cur + 0], gt * (-l / (med.c[mm_cur] * med.c[mm_cur])));
-            if (c == no.n) break;
-            const float4 nr = __ldg(&A.S.tri_nrm[xid[c]]);
-            const uint32_t mm = __float_as_uint(nr.w);
-            const float dn = dot3(d, xyz(nr));
-            const int m1 = dn < 0.0f ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
-            const int m2 = dn < 0.0f ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
-            const float ci = fabsf(dn);
-            const float c1 = med.c[m1], c2 = med.c[m2], r1 = med.rho[m1], r2 = med.rho[m2];
-            const float rr = c2 / c1;
-            const float si2 = fmaxf(0.0f, 1.0f - ci * ci);
-            const float ct = sqrtf(fmaxf(0.0f, 1.0f - rr * rr * si2));
-            const float Av = r2 * c2 * ci, Bv = r1 * c1 * ct;
-            const float Ab = Ga * Bv / (Av * (Av + Bv));
-            const float Bb = -Ga / (Av + Bv);
-            ADD(acc[3 * m2 + 1], Ab * c2 * ci);
-            float c2b = Ab * r2 * ci;
-            ADD(acc[3 * m1 + 1], Bb * c1 * ct);
-            float c1b = Bb * r1 * ct;
-            const float ctb = Bb * r1 * c1;
-            if (ct > 0.0f) {
-              const float rb = ctb * (-rr * si2 / ct);
-              c2b += rb / c1;
-              c1b += -rb * c2 / (c1 * c1);
-            }
-            ADD(acc[3 * m2 + 0], c2b);
-            ADD(acc[3 * m1 + 0], c1b);
-            mm_cur = m2;
-            tprev = tc;
-          }
-          SA[k] = ga * k_n;
-          ST[k] = gt;
-        }
+      } else {  // scatterer: the secondary ray's adjoint seeds come from k_nee_adjoint
+        const float2 sd = A.seeds[(size_t)i * K1 + k];
+        SA[k] = sd.x;
+        ST[k] = sd.y;
         a = a1;  // Born pass-through: amplitude after the segment, direction unchanged
       }
       o = x;
@@ -372,6 +320,153 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Secondary-ray adjoint, one thread per job of the forward pass: the ray's geometry is fixed,
+// so its crossings are recomputed, the splat adjoint is gathered for its arrival, the direct
+// derivatives of a_n = a' A_s s_j prod T exp(-kappa f0 sum alpha l) f_rx N_e and of
+// tau_n = tau' + sum l / c go to theta, and the seeds (dL/da', dL/dtau') are left for the
+// path's reverse sweep.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
+  extern __shared__ float gsm[];
+  const Acq& q = A.acq;
+  const Media& med = A.med;
+  const int P = A.P;
+  const int PS = adj_row_stride(P);
+  float* acc = gsm + threadIdx.x * PS;
+  const int iAs = 3 * med.M, iF0 = 3 * med.M + 1;
+  for (int p = 0; p < P; ++p) acc[p] = 0.0f;
+  const int K1 = q.kmax + 1;
+  const float kap = KAPPA_F;
+  uint32_t total = 0;
+  for (int k = 0; k <= q.kmax; ++k) total += A.cnt->nee[k];
+  float xt[MAX_XINGS];
+  uint32_t xid[MAX_XINGS];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const float4 job = A.nee.job[i];
+    const uint32_t jm = A.nee.jm[i];
+    const uint32_t jid = __float_as_uint(job.w);
+    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
+    const int k = (int)(jm >> 24);
+    const long long path = A.nee.jpath[i];
+    float2* seed = &A.seeds[(size_t)(path - A.path_base) * K1 + k];
+    const float a1 = job.x;
+    float nh = job.y, nl = job.z;
+    const float4 sc = __ldg(&A.S.scat[jid]);
+    float3 d;
+    float D;
+    const NeeOut no = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
+    if (!no.ok) {
+      *seed = make_float2(0.0f, 0.0f);
+      continue;
+    }
+    const float k_n = med.As * sc.w * no.gain;
+    const float a_n = a1 * k_n;
+    float ga, gt, gf;
+    splat_adj_gather(A.grf + ((size_t)tx * q.ne + e2) * q.ns, nh, nl, a_n, A.pulse, ga, gt, gf);
+    const float Ga = ga * a_n;  // adjoint of log a_n
+    ADD(acc[iF0], gf + Ga * (-kap * no.sum_al));
+    ADD(acc[iAs], ga * a1 * sc.w * no.gain);
+    float tprev = 0.0f;
+    int mm_cur = m;
+    for (int c = 0; c <= no.n; ++c) {
+      const float tc = c < no.n ? xt[c] : D;
+      const float l = tc - tprev;
+      ADD(acc[3 * mm_cur + 2], Ga * (-kap * med.f0 * l));
+      ADD(acc[3 * mm_cur + 0], gt * (-l / (med.c[mm_cur] * med.c[mm_cur])));
+      if (c == no.n) break;
+      const float4 nr = __ldg(&A.S.tri_nrm[xid[c]]);
+      const uint32_t mm = __float_as_uint(nr.w);
+      const float dn = dot3(d, xyz(nr));
+      const int m1 = dn < 0.0f ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+      const int m2 = dn < 0.0f ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+      const float ci = fabsf(dn);
+      const float c1 = med.c[m1], c2 = med.c[m2], r1 = med.rho[m1], r2 = med.rho[m2];
+      const float rr = c2 / c1;
+      const float si2 = fmaxf(0.0f, 1.0f - ci * ci);
+      const float ct = sqrtf(fmaxf(0.0f, 1.0f - rr * rr * si2));
+      const float Av = r2 * c2 * ci, Bv = r1 * c1 * ct;
+      const float Ab = Ga * Bv / (Av * (Av + Bv));
+      const float Bb = -Ga / (Av + Bv);
+      ADD(acc[3 * m2 + 1], Ab * c2 * ci);
+      float c2b = Ab * r2 * ci;
+      ADD(acc[3 * m1 + 1], Bb * c1 * ct);
+      float c1b = Bb * r1 * ct;
+      const float ctb = Bb * r1 * c1;
+      if (ct > 0.0f) {
+        const float rb = ctb * (-rr * si2 / ct);
+        c2b += rb / c1;
+        c1b += -rb * c2 / (c1 * c1);
+      }
+      ADD(acc[3 * m2 + 0], c2b);
+      ADD(acc[3 * m1 + 0], c1b);
+      mm_cur = m2;
+      tprev = tc;
+    }
+    *seed = make_float2(ga * k_n, gt);
+  }
+  __syncthreads();
+  float* out = A.gpart + (size_t)blockIdx.x * P;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    float s = 0.0f;
+    for (int t = 0; t < (int)blockDim.x; ++t) s += gsm[t * PS + p];
+    out[p] = (A.accumulate ? out[p] : 0.0f) + s;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Paths that produced an arrival (a transducer hit, or a scatterer event before the
+// interaction budget ran out), grouped by their number of events so that the lanes of a warp
+// sweep paths of equal length.  work: [0, 17) counts, [17, 34) offsets, [34, 51) cursors,
+// [51] total.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int path_class(const uint32_t* rec, int kmax) {
+  int nseg = 0;
+  bool active = false;
+  for (int k = 0; k <= kmax; ++k) {
+    const uint32_t c = code_cls(rec[k]);
+    if (c == CLS_NONE) break;
+    nseg = k + 1;
+    if (c == CLS_XDCR || (c == CLS_SCAT && k < kmax)) active = true;
+  }
+  return active ? nseg : -1;
+}
+
+__global__ void k_active_count(const uint32_t* record, uint32_t n, int kmax, uint32_t* work) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = path_class(record + (size_t)i * (kmax + 1), kmax);
+    if (c < 0) continue;
+    const unsigned same = __match_any_sync(__activemask(), c);  // lanes of this class
+    if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&work[c], (uint32_t)__popc(same));
+  }
+}
+
+__global__ void k_active_scan(uint32_t* work) {
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int c = 16; c >= 0; --c) {  // longest paths first
+      work[17 + c] = run;
+      work[34 + c] = 0;
+      run += work[c];
+    }
+    work[51] = run;
+  }
+}
+
+__global__ void k_active_fill(const uint32_t* record, uint32_t n, int kmax, uint32_t* work, uint32_t* active) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = path_class(record + (size_t)i * (kmax + 1), kmax);
+    if (c < 0) continue;
+    const unsigned same = __match_any_sync(__activemask(), c);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(same) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&work[34 + c], (uint32_t)__popc(same));
+    base = __shfl_sync(same, base, leader);
+    active[work[17 + c] + base + __popc(same & ((1u << lane) - 1u))] = i;
+  }
+}
+
 __global__ void k_grad_reduce(const float* gpart, int nblocks, int P, float* g) {
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     float s = 0.0f;
@@ -389,11 +484,24 @@ __global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
   }
 }
 
+void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
+  k_nee_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);
+}
+void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint32_t* active,
+                         int grid, cudaStream_t st) {
+  cudaMemsetAsync(work, 0, sizeof(uint32_t) * 52, st);
+  k_active_count<<<grid, 256, 0, st>>>(record, n_paths, kmax, work);
+  k_active_scan<<<1, 32, 0, st>>>(work);
+  k_active_fill<<<grid, 256, 0, st>>>(record, n_paths, kmax, work, active);
+}
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   k_path_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);
 }
 cudaError_t adjoint_set_attrs() {
-  return cudaFuncSetAttribute(k_path_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_path_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P)));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_nee_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P)));
 }
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st) {

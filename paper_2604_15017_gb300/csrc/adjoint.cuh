@@ -1,6 +1,7 @@
 // Adjoint kernels interface.
 #pragma once
 
+#include "transport.cuh"
 #include "usrt_device.cuh"
 
 namespace usrt {
@@ -24,8 +25,18 @@ struct AdjArgs {
   float* gpart;            // [gridDim.x][P] per-block partial gradients
   int P;
   int accumulate;          // add into gpart instead of overwriting
+  NeeQ nee;                // the pass's secondary-ray jobs
+  const Counters* cnt;     // job counts per round
+  float2* seeds;           // per (path - path_base, k): (dL/da, dL/dtau) seeded by secondary rays
+  const uint32_t* active;  // paths with an arrival, grouped by event count
+  const uint32_t* n_active;
 };
 
+// secondary-ray adjoint (job-parallel): seeds + direct parameter derivatives
+void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
+// active paths of the record grouped by event count: work = 2 counters + 17 offsets + n entries
+void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint32_t* active,
+                         int grid, cudaStream_t st);
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
 cudaError_t adjoint_set_attrs();
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st);

@@ -27,7 +27,7 @@ struct Buf {
 enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
-  W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_COUNT
+  W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_COUNT
 };
 
 struct SceneGPU {
@@ -36,6 +36,11 @@ struct SceneGPU {
   size_t bytes = 0;
   int n_media_hint = 0;
   int depth = 0;
+};
+
+struct StageRec {
+  int stage;
+  cudaEvent_t a, b;
 };
 
 struct RecordKey {
@@ -58,10 +63,18 @@ struct us_ctx {
   Buf record;
   RecordKey rkey;
   int num_sms = 148;
+  int trav_per_sm = 4;  // resident blocks of the persistent traversal kernel
   Counters* h_cnt = nullptr;  // pinned copy of the last forward's counters
   cudaEvent_t ev_stats = nullptr;
   long long last_paths = 0;
   bool stats_valid = false;
+  // tracing
+  bool prof = false;
+  std::vector<StageRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  long long launches = 0;
+  long long stage_launches[US_N_STAGES] = {};
 };
 
 namespace {
@@ -135,6 +148,38 @@ int ws(us_ctx* ctx, int slot, size_t count, cudaStream_t st, T** out) {
 }
 
 int grid_of(us_ctx* ctx, int per_sm) { return ctx->num_sms * per_sm; }
+
+cudaEvent_t pool_event(us_ctx* ctx) {
+  if (ctx->pool_used < ctx->pool.size()) return ctx->pool[ctx->pool_used++];
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  ctx->pool.push_back(e);
+  ctx->pool_used++;
+  return e;
+}
+
+// counts a stage's kernel launches and, while tracing, brackets them with events on the
+// launching stream
+struct StageScope {
+  us_ctx* c;
+  int stage, nk;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageScope(us_ctx* c_, int stage_, int nk_, cudaStream_t st_) : c(c_), stage(stage_), nk(nk_), st(st_) {
+    if (c->prof && (a = pool_event(c))) cudaEventRecord(a, st);
+  }
+  ~StageScope() {
+    c->launches += nk;
+    c->stage_launches[stage] += nk;
+    if (a) {
+      cudaEvent_t b = pool_event(c);
+      if (b) {
+        cudaEventRecord(b, st);
+        c->recs.push_back(StageRec{stage, a, b});
+      }
+    }
+  }
+};
 
 int make_media(us_ctx* ctx, const float* theta, int M, Media& med) {
   if (!theta) return fail(ctx, US_ERR_ARG, "theta is NULL");
@@ -283,8 +328,10 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   A.med = med;
   A.acq = q;
   CKS(ws(ctx, W_HITS, n, st, &A.hits));
-  CKS(ws(ctx, W_NEE_JOB, n, st, &A.nee.job));
-  CKS(ws(ctx, W_NEE_JM, n, st, &A.nee.jm));
+  const size_t jobs = (size_t)n * std::max(1, q.kmax);  // at most one job per path and round
+  CKS(ws(ctx, W_NEE_JOB, jobs, st, &A.nee.job));
+  CKS(ws(ctx, W_NEE_JM, jobs, st, &A.nee.jm));
+  CKS(ws(ctx, W_NEE_PATH, jobs, st, &A.nee.jpath));
   A.arr = arr;
   A.arr_cap = arr_cap;
   A.record = record;
@@ -293,14 +340,26 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   CK(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
   if (record) CK(cudaMemsetAsync(record, 0, sizeof(uint32_t) * (size_t)n * (q.kmax + 1), st));
   A.qout = Q.a;
-  launch_generate(A, path0, n, grid_of(ctx, 8), st);
+  {
+    StageScope sc_(ctx, US_STAGE_GENERATE, 1, st);
+    launch_generate(A, path0, n, grid_of(ctx, 8), st);
+  }
   for (int k = 0; k <= q.kmax; ++k) {
     A.k = k;
     A.qin = (k & 1) ? Q.b : Q.a;
     A.qout = (k & 1) ? Q.a : Q.b;
-    launch_traverse(A, grid_of(ctx, 16), st);
-    launch_interact(A, grid_of(ctx, 8), st);
-    if (do_nee && sc->dev.n_scat > 0) launch_nee(A, grid_of(ctx, 16), st);
+    {
+      StageScope sc_(ctx, US_STAGE_TRAVERSE, 1, st);
+      launch_traverse(A, grid_of(ctx, ctx->trav_per_sm), st);
+    }
+    {
+      StageScope sc_(ctx, US_STAGE_INTERACT, 1, st);
+      launch_interact(A, grid_of(ctx, 8), st);
+    }
+    if (do_nee && sc->dev.n_scat > 0) {
+      StageScope sc_(ctx, US_STAGE_NEE, 1, st);
+      launch_nee(A, grid_of(ctx, 16), st);
+    }
   }
   CK(cudaGetLastError());
   return US_OK;
@@ -319,8 +378,15 @@ int do_splat(us_ctx* ctx, const Acq& q, float f0, const Arrival* arr, const uint
   CKS(ws(ctx, W_SCRATCH, (size_t)cap + 1, st, &w.scratch));
   float* G;
   CKS(ws(ctx, W_GTAB, K_MOM * MAX_TAPS, st, &G));
-  launch_pulse_table(g, G, st);
-  launch_splat(g, arr, n_arr, cap, w, G, rf, grid_of(ctx, 4), st);
+  {
+    StageScope sc_(ctx, US_STAGE_SPLAT_SORT, 4, st);
+    launch_pulse_table(g, G, st);
+    launch_splat_sort(g, arr, n_arr, cap, w, grid_of(ctx, 4), st);
+  }
+  {
+    StageScope sc_(ctx, US_STAGE_SPLAT_ROWS, 1, st);
+    launch_splat_rows(g, w, G, rf, st);
+  }
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -331,8 +397,14 @@ int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* b
   CKS(ws(ctx, W_IRF, (size_t)im.nl * im.nd, st, &irf));
   CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
   CKS(ws(ctx, W_KEY, 1, st, &key));
-  launch_das(q, im, rf, irf, grid_of(ctx, 8), st);
-  launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
+  {
+    StageScope sc_(ctx, US_STAGE_DAS, 1, st);
+    launch_das(q, im, rf, irf, grid_of(ctx, 8), st);
+  }
+  {
+    StageScope sc_(ctx, US_STAGE_ENVLOG, 2, st);
+    launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
+  }
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -359,6 +431,7 @@ int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
     delete ctx;
     return US_ERR_CUDA;
   }
+  ctx->trav_per_sm = traverse_blocks_per_sm();
   if (set_attrs(ctx) != US_OK) {
     delete ctx;
     return US_ERR_CUDA;
@@ -378,7 +451,42 @@ void us_destroy(us_ctx* ctx) {
   if (ctx->record.p) cudaFree(ctx->record.p);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
   if (ctx->ev_stats) cudaEventDestroy(ctx->ev_stats);
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
+}
+
+int us_profile(us_ctx* ctx, int enable) {
+  if (!ctx) return US_ERR_ARG;
+  ctx->prof = enable != 0;
+  ctx->recs.clear();
+  ctx->pool_used = 0;
+  for (int i = 0; i < US_N_STAGES; ++i) ctx->stage_launches[i] = 0;
+  return US_OK;
+}
+
+int us_profile_read(us_ctx* ctx, double* ms, int64_t* launches, int n) {
+  if (!ctx || n < 0 || (n && (!ms || !launches))) return fail(ctx, US_ERR_ARG, "invalid arguments");
+  std::vector<double> acc(US_N_STAGES, 0.0);
+  for (const StageRec& r : ctx->recs) {
+    CK(cudaEventSynchronize(r.b));
+    float t = 0.0f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    acc[r.stage] += t;
+  }
+  for (int i = 0; i < n && i < US_N_STAGES; ++i) {
+    ms[i] = acc[i];
+    launches[i] = ctx->stage_launches[i];
+  }
+  ctx->recs.clear();
+  ctx->pool_used = 0;
+  for (int i = 0; i < US_N_STAGES; ++i) ctx->stage_launches[i] = 0;
+  return US_OK;
+}
+
+int us_launch_count(us_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return US_ERR_ARG;
+  *n = ctx->launches;
+  return US_OK;
 }
 
 const char* us_last_error(us_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -465,6 +573,7 @@ int us_philox_fill(us_ctx* ctx, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t 
   if (!ctx || (n > 0 && !out_dev) || n < 0) return fail(ctx, US_ERR_ARG, "invalid arguments");
   if (!aligned16(out_dev)) return fail(ctx, US_ERR_ARG, "out_dev must be 16-byte aligned");
   if (n == 0) return US_OK;
+  StageScope sc_(ctx, US_STAGE_OTHER, 1, (cudaStream_t)stream);
   launch_philox_fill(c0, c1, c2, c3, k0, k1, n, out_dev, grid_of(ctx, 8), (cudaStream_t)stream);
   CK(cudaGetLastError());
   return US_OK;
@@ -484,6 +593,7 @@ int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   CKS(make_media(ctx, theta, sc->n_media_hint, med));
   CKS(make_acq(ctx, acq, seed, q));
   if (bmode_dev) CKS(make_img(ctx, img, im));
+  ctx->rkey.valid = false;  // job buffers and counters are about to be overwritten
   const long long n_paths = q.rays_per_tx * q.ntx;
   const long long cap_ll = n_paths * (q.kmax + 1);
   const uint32_t cap = (uint32_t)std::min<long long>(cap_ll, 0xFFFFFFF0ll);
@@ -567,7 +677,10 @@ int us_splat(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int
   CKS(ws(ctx, W_PACK, (size_t)n + 1, st, &arr));
   CKS(ws(ctx, W_NPACK, 1, st, &n_out));
   CK(cudaMemsetAsync(n_out, 0, sizeof(uint32_t), st));
-  if (n) launch_pack_arrivals(tx_dev, e_dev, tau_dev, a_dev, n, q.ne, q.fs, arr, n_out, grid_of(ctx, 4), st);
+  if (n) {
+    StageScope sc_(ctx, US_STAGE_OTHER, 1, st);
+    launch_pack_arrivals(tx_dev, e_dev, tau_dev, a_dev, n, q.ne, q.fs, arr, n_out, grid_of(ctx, 4), st);
+  }
   return do_splat(ctx, q, f0, arr, n_out, (uint32_t)n + 1, rf_dev, st);
 }
 
@@ -579,6 +692,7 @@ int us_das(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const fl
   CKS(make_acq(ctx, acq, 0, q));
   CKS(make_img(ctx, img, im));
   if (!rf_dev || !irf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  StageScope sc_(ctx, US_STAGE_DAS, 1, (cudaStream_t)stream);
   launch_das(q, im, rf_dev, irf_dev, grid_of(ctx, 8), (cudaStream_t)stream);
   CK(cudaGetLastError());
   return US_OK;
@@ -594,6 +708,7 @@ int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* 
   unsigned long long* key;
   CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
   CKS(ws(ctx, W_KEY, 1, st, &key));
+  StageScope sc_(ctx, US_STAGE_ENVLOG, 2, st);
   launch_envlog(im, irf_dev, env, key, bmode_dev, grid_of(ctx, 8), st);
   CK(cudaGetLastError());
   return US_OK;
@@ -620,6 +735,7 @@ int us_loss(us_ctx* ctx, const us_img_desc* img, const float* bmode_dev, const f
   float* part;
   const int np = grid_of(ctx, 2);
   CKS(ws(ctx, W_PART, np, st, &part));
+  StageScope sc_(ctx, US_STAGE_LOSS, 2, st);
   launch_loss(im, bmode_dev, bref_dev, dL_dB_dev, part, np, loss_dev, st);
   CK(cudaGetLastError());
   return US_OK;
@@ -639,6 +755,7 @@ int us_envlog_vjp(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, con
   CKS(ws(ctx, W_KEY, 1, st, &key));
   CKS(ws(ctx, W_PART, np, st, &part));
   CKS(ws(ctx, W_SCAL, 4, st, &scal));
+  StageScope sc_(ctx, US_STAGE_ENVLOG_VJP, 4, st);
   launch_envlog_vjp(im, irf_dev, dL_dB_dev, env, key, part, np, scal, dL_dirf_dev, grid_of(ctx, 8), st);
   CK(cudaGetLastError());
   return US_OK;
@@ -652,6 +769,7 @@ int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, 
   CKS(make_acq(ctx, acq, 0, q));
   CKS(make_img(ctx, img, im));
   if (!dL_dirf_dev || !dL_drf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  StageScope sc_(ctx, US_STAGE_DAS_ADJ, 1, (cudaStream_t)stream);
   launch_das_adj(q, im, dL_dirf_dev, dL_drf_dev, grid_of(ctx, 8), (cudaStream_t)stream);
   CK(cudaGetLastError());
   return US_OK;
@@ -669,9 +787,15 @@ int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, co
   float *irf, *gi;
   CKS(ws(ctx, W_IRF, (size_t)im.nl * im.nd, st, &irf));
   CKS(ws(ctx, W_GI, (size_t)im.nl * im.nd, st, &gi));
-  launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st);
+  {
+    StageScope sc_(ctx, US_STAGE_DAS, 1, st);
+    launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st);
+  }
   CKS(us_envlog_vjp(ctx, img, irf, dL_dB_dev, gi, stream));
-  launch_das_adj(q, im, gi, dL_drf_dev, grid_of(ctx, 8), st);
+  {
+    StageScope sc_(ctx, US_STAGE_DAS_ADJ, 1, st);
+    launch_das_adj(q, im, gi, dL_drf_dev, grid_of(ctx, 8), st);
+  }
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -687,8 +811,11 @@ int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, c
   CKS(splat_geom(ctx, q, f0, g, P));
   if (n < 0 || (n && (!tx_dev || !e_dev || !tau_dev || !a_dev || !dL_drf_dev || !ga_dev || !gt_dev || !gf_dev)))
     return fail(ctx, US_ERR_ARG, "invalid arrival list");
-  if (n) launch_splat_adjoint(q, P, tx_dev, e_dev, tau_dev, a_dev, n, dL_drf_dev, ga_dev, gt_dev, gf_dev,
-                              grid_of(ctx, 4), (cudaStream_t)stream);
+  if (n) {
+    StageScope sc_(ctx, US_STAGE_OTHER, 1, (cudaStream_t)stream);
+    launch_splat_adjoint(q, P, tx_dev, e_dev, tau_dev, a_dev, n, dL_drf_dev, ga_dev, gt_dev, gf_dev, grid_of(ctx, 4),
+                         (cudaStream_t)stream);
+  }
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -714,37 +841,65 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
   A.grf = dL_drf_dev;
   A.P = 3 * med.M + 2;
   const int grid = grid_of(ctx, 8);
-  CKS(ws(ctx, W_GPART, (size_t)grid * A.P, st, &A.gpart));
+  float* gpart;  // [0, grid) rows: path sweep; [grid, 2 grid): secondary rays
+  CKS(ws(ctx, W_GPART, (size_t)2 * grid * A.P, st, &gpart));
   const long long n_paths = q.rays_per_tx * q.ntx;
+  const int K1 = q.kmax + 1;
+  uint32_t *work, *active;
+  const auto sweep = [&](const uint32_t* rec, long long p0, uint32_t n, Counters* cnt, int accumulate) -> int {
+    A.record = rec;
+    A.path_base = p0;
+    A.n_paths = n;
+    A.accumulate = accumulate;
+    A.nee.job = (float4*)ctx->ws[W_NEE_JOB].p;
+    A.nee.jm = (uint32_t*)ctx->ws[W_NEE_JM].p;
+    A.nee.jpath = (uint32_t*)ctx->ws[W_NEE_PATH].p;
+    A.cnt = cnt;
+    CKS(ws(ctx, W_SEEDS, (size_t)n * K1, st, &A.seeds));
+    CKS(ws(ctx, W_ACTIVE, (size_t)n + 1, st, &active));
+    CKS(ws(ctx, W_ACT_CNT, 64, st, &work));
+    A.active = active;
+    A.n_active = work + 51;
+    if (sc->dev.n_scat > 0 && A.nee.job) {
+      A.gpart = gpart + (size_t)grid * A.P;
+      StageScope sc_(ctx, US_STAGE_NEE_ADJ, 1, st);
+      launch_nee_adjoint(A, grid, st);
+    } else if (!accumulate) {
+      CK(cudaMemsetAsync(gpart + (size_t)grid * A.P, 0, sizeof(float) * grid * A.P, st));
+    }
+    {
+      StageScope sc_(ctx, US_STAGE_PATH_ADJ, 4, st);
+      launch_active_paths(rec, n, q.kmax, work, active, grid_of(ctx, 4), st);
+      A.gpart = gpart;
+      launch_path_adjoint(A, grid, st);
+    }
+    return US_OK;
+  };
   if (mode == 0) {
     if (!ctx->rkey.valid || ctx->rkey.scene != scene || ctx->rkey.seed != seed || ctx->rkey.n_paths != n_paths ||
         ctx->rkey.acq.size() != sizeof q || std::memcmp(ctx->rkey.acq.data(), &q, sizeof q) != 0 ||
         ctx->rkey.theta.size() != (size_t)A.P ||
         std::memcmp(ctx->rkey.theta.data(), theta, sizeof(float) * A.P) != 0)
-      return fail(ctx, US_ERR_STATE, "record mode needs a forward pass with keep_record on the same inputs");
-    A.record = (const uint32_t*)ctx->record.p;
-    A.path_base = 0;
-    A.n_paths = (uint32_t)n_paths;
-    A.accumulate = 0;
-    launch_path_adjoint(A, grid, st);
+      return fail(ctx, US_ERR_STATE, "record mode needs the last forward pass, with keep_record, on the same inputs");
+    CKS(sweep((const uint32_t*)ctx->record.p, 0, (uint32_t)n_paths, (Counters*)ctx->ws[W_CNT].p, 0));
   } else {
     // recompute: regenerate the decisions chunk by chunk, then sweep each chunk
     const long long chunk = std::min<long long>(n_paths, 1ll << 22);
     uint32_t* rec;
     Counters* cnt;
-    CKS(ws(ctx, W_REC_CHUNK, (size_t)chunk * (q.kmax + 1), st, &rec));
+    CKS(ws(ctx, W_REC_CHUNK, (size_t)chunk * K1, st, &rec));
     CKS(ws(ctx, W_CNT, 1, st, &cnt));
+    ctx->rkey.valid = false;  // the job buffers and counters now hold the recomputed chunk
     for (long long p0 = 0; p0 < n_paths; p0 += chunk) {
       const uint32_t n = (uint32_t)std::min<long long>(chunk, n_paths - p0);
       CKS(run_transport(ctx, sc, med, q, p0, n, nullptr, 0, rec, false, cnt, st));
-      A.record = rec;
-      A.path_base = p0;
-      A.n_paths = n;
-      A.accumulate = p0 > 0;
-      launch_path_adjoint(A, grid, st);
+      CKS(sweep(rec, p0, n, cnt, p0 > 0));
     }
   }
-  launch_grad_reduce(A.gpart, grid, A.P, dL_dtheta_dev, st);
+  {
+    StageScope sc_(ctx, US_STAGE_PATH_ADJ, 1, st);
+    launch_grad_reduce(gpart, 2 * grid, A.P, dL_dtheta_dev, st);
+  }
   CK(cudaGetLastError());
   return US_OK;
 }

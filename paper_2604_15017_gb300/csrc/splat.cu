@@ -282,15 +282,17 @@ size_t row_splat_smem(const SplatGeom& g) {
 
 void launch_pulse_table(const SplatGeom& g, float* G, cudaStream_t st) { k_pulse_table<<<1, 128, 0, st>>>(g, G); }
 
-void launch_splat(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
-                  const float* G, float* rf, int grid, cudaStream_t st) {
+void launch_splat_sort(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
+                       int grid, cudaStream_t st) {
   const int nrows = g.nrows;
   cudaMemsetAsync(w.row_cnt, 0, sizeof(uint32_t) * nrows, st);
   k_row_hist<<<grid, 256, sizeof(uint32_t) * nrows, st>>>(arr, n_arr, cap, w.row_cnt, nrows);
   k_row_scan<<<1, 1024, 0, st>>>(w.row_cnt, w.row_off, w.row_cursor, nrows);
   k_row_scatter<<<grid, SC_THREADS, 2 * sizeof(uint32_t) * nrows, st>>>(arr, n_arr, cap, w.row_off, w.row_cursor,
                                                                          w.bucket, nrows);
-  k_row_splat<<<nrows, ROW_THREADS, row_splat_smem(g), st>>>(g, w.bucket, w.row_off, w.scratch, G, rf);
+}
+void launch_splat_rows(const SplatGeom& g, SplatWork w, const float* G, float* rf, cudaStream_t st) {
+  k_row_splat<<<g.nrows, ROW_THREADS, row_splat_smem(g), st>>>(g, w.bucket, w.row_off, w.scratch, G, rf);
 }
 
 void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n, int ne,

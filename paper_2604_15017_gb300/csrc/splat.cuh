@@ -28,8 +28,10 @@ struct SplatWork {
 
 size_t row_splat_smem(const SplatGeom& g);
 void launch_pulse_table(const SplatGeom& g, float* G, cudaStream_t st);
-void launch_splat(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
-                  const float* G, float* rf, int grid, cudaStream_t st);
+// row bucketing (3 kernels), then the per-row sort / reduction / convolution (1 kernel)
+void launch_splat_sort(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
+                       int grid, cudaStream_t st);
+void launch_splat_rows(const SplatGeom& g, SplatWork w, const float* G, float* rf, cudaStream_t st);
 void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n, int ne,
                           float fs, Arrival* out, uint32_t* n_out, int grid, cudaStream_t st);
 cudaError_t splat_set_attrs(const SplatGeom& g);

@@ -58,9 +58,14 @@ __global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long pat
 }
 
 // ------------------------------------------------------------------------------------------
-// Closest-hit traversal of every live path
+// Closest-hit traversal of every live path (one ray per thread, grid-stride).  The lanes of a
+// warp start their rays at the root together, so the upper levels of the BVH are fetched once
+// per warp; a variant that refilled each lane as soon as its ray finished was measured slower
+// (lanes at different depths lose that sharing).
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_traverse(TransportArgs A) {
+__global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
+  if (blockIdx.x == 0 && threadIdx.x == 0)  // secondary jobs of this round follow the previous rounds'
+    A.cnt->nee_off[A.k] = A.k ? A.cnt->nee_off[A.k - 1] + A.cnt->nee[A.k - 1] : 0u;
   const uint32_t n = A.cnt->live[A.k];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float4 pa = A.qin.pa[i];
@@ -161,9 +166,10 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
     } else {  // scatterer: secondary ray to a uniformly chosen element; Born pass-through
       const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
       word |= (uint32_t)e2 << 24;
-      const uint32_t slot = append_slot(&A.cnt->nee[A.k]);
+      const uint32_t slot = A.cnt->nee_off[A.k] + append_slot(&A.cnt->nee[A.k]);
       A.nee.job[slot] = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code)));
-      A.nee.jm[slot] = (uint32_t)m | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16);
+      A.nee.jm[slot] = (uint32_t)m | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16) | ((uint32_t)A.k << 24);
+      A.nee.jpath[slot] = (uint32_t)path;
     }
     if (rec) *rec = word;
     const uint32_t o = append_slot(&A.cnt->live[A.k + 1]);
@@ -180,13 +186,15 @@ __global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
   const Acq& q = A.acq;
   const Media& med = A.med;
   const uint32_t n = A.cnt->nee[A.k];
+  const uint32_t off = A.cnt->nee_off[A.k];
   float xt[MAX_XINGS];
   uint32_t xid[MAX_XINGS];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (uint32_t ii = blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += gridDim.x * blockDim.x) {
+    const uint32_t i = off + ii;
     const float4 job = A.nee.job[i];
     const uint32_t jm = A.nee.jm[i];
     const uint32_t j = __float_as_uint(job.w);
-    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)(jm >> 16);
+    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
     const float4 sc = __ldg(&A.S.scat[j]);
     float th = job.y, tl = job.z;
     const NeeOut r = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, th, tl, xt, xid, nullptr, nullptr);
@@ -207,7 +215,12 @@ __global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {
   k_generate<<<grid, 256, 0, st>>>(a, path0, n);
 }
-void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st) { k_traverse<<<grid, 128, 0, st>>>(a); }
+void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st) { k_traverse<<<grid, TRAV_THREADS, 0, st>>>(a); }
+int traverse_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_traverse, TRAV_THREADS, 0) != cudaSuccess || b < 1) b = 4;
+  return 2 * b;  // two waves of resident blocks: a short tail without a long grid-stride loop
+}
 void launch_interact(const TransportArgs& a, int grid, cudaStream_t st) { k_interact<<<grid, 256, 0, st>>>(a); }
 void launch_nee(const TransportArgs& a, int grid, cudaStream_t st) { k_nee<<<grid, 128, 0, st>>>(a); }
 

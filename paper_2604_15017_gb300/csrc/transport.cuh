@@ -12,16 +12,19 @@ struct PathQ {
   uint4* meta;  // (path id, previous primitive code, medium | k << 8, bits(tau_lo))
 };
 
-// secondary-ray jobs queued by the interaction kernel
+// secondary-ray jobs queued by the interaction kernels; round k appends at nee_off[k], so the
+// buffer keeps every job of the pass (the adjoint replays them)
 struct NeeQ {
-  float4* job;   // (a, tau_hi, tau_lo, bits(scatterer id))
-  uint32_t* jm;  // medium | element << 8 | tx << 16
+  float4* job;      // (a, tau_hi, tau_lo, bits(scatterer id)) at the event
+  uint32_t* jm;     // medium | element << 8 | tx << 16 | k << 24
+  uint32_t* jpath;  // path id
 };
 
 // device counters of one transport pass
 struct Counters {
   uint32_t live[MAX_KMAX + 2];  // paths entering segment k
   uint32_t nee[MAX_KMAX + 2];   // secondary jobs produced at segment k
+  uint32_t nee_off[MAX_KMAX + 2]; // first job of round k in the job buffer
   uint32_t n_arr;               // arrivals appended
   uint32_t dropped;             // arrivals dropped (crossing list overflow)
   int status;                   // ST_* bits
@@ -47,7 +50,9 @@ struct TransportArgs {
 };
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st);
+constexpr int TRAV_THREADS = 128;
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st);
+int traverse_blocks_per_sm();  // blocks per SM of the traversal grid
 void launch_interact(const TransportArgs& a, int grid, cudaStream_t st);
 void launch_nee(const TransportArgs& a, int grid, cudaStream_t st);
 

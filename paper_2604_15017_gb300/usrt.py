@@ -24,7 +24,10 @@ MODE_RECORD, MODE_RECOMPUTE = 0, 1
 EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_scene_release", "us_memory",
            "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
-           "us_transport_vjp", "us_adjoint", "us_envlog_noalloc"]
+           "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
+           "us_launch_count"]
+STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
+          "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
 
 
 class UsrtError(RuntimeError):
@@ -101,6 +104,9 @@ def lib():
                                            C.c_int, VP, VP, VP]
             l.us_adjoint.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc), C.POINTER(ImgDesc),
                                      C.c_uint64, C.c_int, VP, VP, VP, VP, VP]
+            l.us_profile.argtypes = [VP, C.c_int]
+            l.us_profile_read.argtypes = [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
+            l.us_launch_count.argtypes = [VP, C.POINTER(C.c_int64)]
             _lib = l
     return _lib
 
@@ -167,6 +173,23 @@ class Context:
         u, b = C.c_size_t(), C.c_size_t()
         self._check(lib().us_memory(self.h, C.byref(u), C.byref(b)))
         return u.value, b.value
+
+    # ---- tracing --------------------------------------------------------------------------
+    def profile(self, enable=True):
+        self._check(lib().us_profile(self.h, int(bool(enable))))
+
+    def profile_read(self):
+        """{stage: (device ms, kernel launches)} since profile(True) (synchronises)."""
+        n = len(STAGES)
+        ms = (C.c_double * n)()
+        ln = (C.c_int64 * n)()
+        self._check(lib().us_profile_read(self.h, ms, ln, n))
+        return {STAGES[i]: (ms[i], ln[i]) for i in range(n)}
+
+    def launch_count(self):
+        v = C.c_int64()
+        self._check(lib().us_launch_count(self.h, C.byref(v)))
+        return v.value
 
     # ---- scenes ---------------------------------------------------------------------------
     def upload_scene(self, tris, media, n_media, scat_pos, scat_amp, r_s):
