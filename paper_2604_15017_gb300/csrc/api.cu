@@ -27,11 +27,13 @@ struct Buf {
 enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
-  W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_COUNT
+  W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
+  W_RAY_OFF, W_RAY_CUR, W_COUNT
 };
 
 struct SceneGPU {
   SceneDev dev;
+  float lo[3], hi[3];  // bounds of all primitives (ray-sort cells)
   std::vector<void*> allocs;
   size_t bytes = 0;
   int n_media_hint = 0;
@@ -299,6 +301,7 @@ int set_attrs(us_ctx* ctx) {
   CK(row_hist_set_attrs(16384));
   CK(image_set_attrs(4096));
   CK(adjoint_set_attrs());
+  CK(ray_sort_set_attrs());
   return US_OK;
 }
 
@@ -339,6 +342,17 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   A.cnt = cnt;
   CK(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
   if (record) CK(cudaMemsetAsync(record, 0, sizeof(uint32_t) * (size_t)n * (q.kmax + 1), st));
+  RaySort rs;
+  for (int a = 0; a < 3; ++a) {
+    const float ext = std::max(sc->hi[a] - sc->lo[a], 1e-6f);
+    (&rs.lo.x)[a] = sc->lo[a];
+    (&rs.inv_ext.x)[a] = 1.0f / ext;
+  }
+  CKS(ws(ctx, W_RAY_KEY, n, st, &rs.key));
+  CKS(ws(ctx, W_RAY_CNT, RAY_BUCKETS, st, &rs.cnt));
+  CKS(ws(ctx, W_RAY_OFF, RAY_BUCKETS + 1, st, &rs.off));
+  CKS(ws(ctx, W_RAY_CUR, RAY_BUCKETS, st, &rs.cursor));
+  // Q.a: rays as generated / as the interaction kernel appends them; Q.b: coherence-sorted
   A.qout = Q.a;
   {
     StageScope sc_(ctx, US_STAGE_GENERATE, 1, st);
@@ -346,8 +360,12 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   }
   for (int k = 0; k <= q.kmax; ++k) {
     A.k = k;
-    A.qin = (k & 1) ? Q.b : Q.a;
-    A.qout = (k & 1) ? Q.a : Q.b;
+    {
+      StageScope sc_(ctx, US_STAGE_GENERATE, 3, st);
+      launch_ray_sort(A, Q.a, Q.b, rs, grid_of(ctx, 2), st);
+    }
+    A.qin = Q.b;
+    A.qout = Q.a;
     {
       StageScope sc_(ctx, US_STAGE_TRAVERSE, 1, st);
       launch_traverse(A, grid_of(ctx, ctx->trav_per_sm), st);
@@ -538,6 +556,17 @@ int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
     for (void* p : sc.allocs) cudaFree(p);
     ctx->used -= sc.bytes;
     return s;
+  }
+  // root box = union of the two children of node 0: x at words (0,1)/(4,5), y at (2,3)/(6,7),
+  // z at (8,9)/(10,11)
+  const int lo_w[3][2] = {{0, 4}, {2, 6}, {8, 10}};
+  for (int a = 0; a < 3; ++a) {
+    sc.lo[a] = std::min(o.nodes[lo_w[a][0]], o.nodes[lo_w[a][1]]);
+    sc.hi[a] = std::max(o.nodes[lo_w[a][0] + 1], o.nodes[lo_w[a][1] + 1]);
+    if (!(sc.lo[a] <= sc.hi[a])) {
+      sc.lo[a] = -1.0f;
+      sc.hi[a] = 1.0f;
+    }
   }
   sc.dev.n_nodes = o.n_nodes;
   sc.dev.n_tris = d->n_tris;

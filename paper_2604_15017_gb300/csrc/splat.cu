@@ -300,6 +300,10 @@ void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau,
   k_pack_arrivals<<<grid, 256, 0, st>>>(tx, e, tau, a, n, ne, fs, out, n_out);
 }
 
+void launch_count_scan(const uint32_t* cnt, uint32_t* off, uint32_t* cursor, int n, cudaStream_t st) {
+  k_row_scan<<<1, 1024, 0, st>>>(cnt, off, cursor, n);
+}
+
 cudaError_t splat_set_attrs(const SplatGeom& g) {
   return cudaFuncSetAttribute(k_row_splat, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)row_splat_smem(g));
 }

@@ -35,6 +35,8 @@ void launch_splat_rows(const SplatGeom& g, SplatWork w, const float* G, float* r
 void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n, int ne,
                           float fs, Arrival* out, uint32_t* n_out, int grid, cudaStream_t st);
 cudaError_t splat_set_attrs(const SplatGeom& g);
+// exclusive scan of n counts (one block): off[n] = total, cursor zeroed
+void launch_count_scan(const uint32_t* cnt, uint32_t* off, uint32_t* cursor, int n, cudaStream_t st);
 cudaError_t row_scatter_set_attrs(int nrows);
 cudaError_t row_hist_set_attrs(int nrows);
 

@@ -7,6 +7,7 @@
 #include <cooperative_groups.h>
 
 #include "bvh_query.cuh"
+#include "splat.cuh"
 #include "transport.cuh"
 
 namespace cg = cooperative_groups;
@@ -210,6 +211,96 @@ __global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
     const uint32_t slot = append_slot(&A.cnt->n_arr);
     if (slot < A.arr_cap) A.arr[slot] = make_uint4((uint32_t)(tx * q.ne + e2), tq, __float_as_uint(amp), 0xFFFFFFFFu);
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// Coherence sort of a ray queue (one counting-sort pass, 14-bit key)
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 w) {
+  // origin: 8 x 8 cells over the scene's x and z extent
+  const int cx = min(7, max(0, (int)((o.x - rs.lo.x) * rs.inv_ext.x * 8.0f)));
+  const int cz = min(7, max(0, (int)((o.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
+  // direction: octahedral map of the unit sphere onto [-1, 1]^2, 16 x 16 bins
+  const float l1 = fabsf(w.x) + fabsf(w.y) + fabsf(w.z);
+  float u = w.x / l1, v = w.y / l1;
+  if (w.z < 0.0f) {
+    const float uu = (1.0f - fabsf(v)) * copysignf(1.0f, u);
+    const float vv = (1.0f - fabsf(u)) * copysignf(1.0f, v);
+    u = uu;
+    v = vv;
+  }
+  const int bu = min(15, max(0, (int)((u + 1.0f) * 8.0f)));
+  const int bv = min(15, max(0, (int)((v + 1.0f) * 8.0f)));
+  return (uint32_t)((((cz << 3) | cx) << 8) | (bu << 4) | bv);
+}
+
+__global__ void __launch_bounds__(256) k_ray_keys(TransportArgs A, PathQ from, RaySort rs) {
+  extern __shared__ uint32_t h[];
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const uint32_t n = A.cnt->live[A.k];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t key = ray_key(rs, xyz(from.pa[i]), xyz(from.wt[i]));
+    rs.key[i] = key;
+    atomicAdd(&h[key], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+    if (h[b]) atomicAdd(&rs.cnt[b], h[b]);
+}
+
+constexpr int RS_THREADS = 512;
+constexpr int RS_PER = 16;
+constexpr int RS_CH = RS_THREADS * RS_PER;
+__global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, PathQ from, PathQ to, RaySort rs) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* h = sm;
+  uint32_t* base = sm + RAY_BUCKETS;
+  const uint32_t n = A.cnt->live[A.k];
+  for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
+    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    uint32_t key[RS_PER], rank[RS_PER];
+#pragma unroll
+    for (int j = 0; j < RS_PER; ++j) {
+      const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
+      key[j] = 0xFFFFFFFFu;
+      if (i < n) {
+        key[j] = rs.key[i];
+        rank[j] = atomicAdd(&h[key[j]], 1u);
+      }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+      if (h[b]) base[b] = rs.off[b] + atomicAdd(&rs.cursor[b], h[b]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_PER; ++j) {
+      if (key[j] == 0xFFFFFFFFu) continue;
+      const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
+      const uint32_t o = base[key[j]] + rank[j];
+      to.pa[o] = from.pa[i];
+      to.wt[o] = from.wt[i];
+      to.meta[o] = from.meta[i];
+    }
+    __syncthreads();
+  }
+}
+
+void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
+                     cudaStream_t st) {
+  cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st);
+  k_ray_keys<<<grid, 256, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, rs);
+  launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
+  k_ray_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
+}
+
+cudaError_t ray_sort_set_attrs() {
+  cudaError_t e = cudaFuncSetAttribute(k_ray_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(uint32_t) * RAY_BUCKETS));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_ray_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * sizeof(uint32_t) * RAY_BUCKETS));
 }
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {

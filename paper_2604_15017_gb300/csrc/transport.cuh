@@ -49,6 +49,23 @@ struct TransportArgs {
   int k;              // segment index
 };
 
+// coherence sort of a ray queue: one counting-sort pass over a 14-bit key (origin cell in x and
+// z, octahedral direction bin), so that the lanes of a warp start near each other and point the
+// same way
+constexpr int RAY_KEY_BITS = 14;
+constexpr int RAY_BUCKETS = 1 << RAY_KEY_BITS;
+struct RaySort {
+  float3 lo, inv_ext;   // scene bounds for the origin cells
+  uint32_t* key;        // per ray
+  uint32_t* cnt;        // [RAY_BUCKETS]
+  uint32_t* off;        // [RAY_BUCKETS + 1]
+  uint32_t* cursor;     // [RAY_BUCKETS]
+};
+// sorts queue `from` (count live[k]) into `to`
+void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
+                     cudaStream_t st);
+cudaError_t ray_sort_set_attrs();
+
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st);
 constexpr int TRAV_THREADS = 128;
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st);
