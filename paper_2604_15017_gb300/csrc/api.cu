@@ -28,7 +28,7 @@ enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
-  W_RAY_OFF, W_RAY_CUR, W_COUNT
+  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_COUNT
 };
 
 struct SceneGPU {
@@ -331,10 +331,19 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   A.med = med;
   A.acq = q;
   CKS(ws(ctx, W_HITS, n, st, &A.hits));
+  // secondary-ray jobs: the interaction kernel appends into `unsorted`, each round's jobs are
+  // sorted into A.nee, which the secondary-ray kernel and the adjoint read
   const size_t jobs = (size_t)n * std::max(1, q.kmax);  // at most one job per path and round
   CKS(ws(ctx, W_NEE_JOB, jobs, st, &A.nee.job));
   CKS(ws(ctx, W_NEE_JM, jobs, st, &A.nee.jm));
   CKS(ws(ctx, W_NEE_PATH, jobs, st, &A.nee.jpath));
+  NeeQ sorted = A.nee, unsorted;
+  const bool sort_jobs = sc->dev.n_scat > 0;
+  if (sort_jobs) {
+    CKS(ws(ctx, W_JOBU_JOB, jobs, st, &unsorted.job));
+    CKS(ws(ctx, W_JOBU_JM, jobs, st, &unsorted.jm));
+    CKS(ws(ctx, W_JOBU_PATH, jobs, st, &unsorted.jpath));
+  }
   A.arr = arr;
   A.arr_cap = arr_cap;
   A.record = record;
@@ -366,6 +375,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     }
     A.qin = Q.b;
     A.qout = Q.a;
+    if (sort_jobs) A.nee = unsorted;
     {
       StageScope sc_(ctx, US_STAGE_TRAVERSE, 1, st);
       launch_traverse(A, grid_of(ctx, ctx->trav_per_sm), st);
@@ -374,6 +384,11 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
       StageScope sc_(ctx, US_STAGE_INTERACT, 1, st);
       launch_interact(A, grid_of(ctx, 8), st);
     }
+    if (sort_jobs && k < q.kmax) {
+      StageScope sc_(ctx, US_STAGE_GENERATE, 3, st);
+      launch_job_sort(A, unsorted, sorted, rs, grid_of(ctx, 2), st);
+    }
+    A.nee = sorted;
     if (do_nee && sc->dev.n_scat > 0) {
       StageScope sc_(ctx, US_STAGE_NEE, 1, st);
       launch_nee(A, grid_of(ctx, 16), st);

@@ -287,6 +287,73 @@ __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, Pat
   }
 }
 
+__device__ __forceinline__ uint32_t job_key(const RaySort& rs, const SceneDev& S, float4 job, uint32_t jm) {
+  const float3 p = xyz(__ldg(&S.scat[__float_as_uint(job.w)]));
+  const int cx = min(3, max(0, (int)((p.x - rs.lo.x) * rs.inv_ext.x * 4.0f)));
+  const int cz = min(7, max(0, (int)((p.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
+  const uint32_t e2 = (jm >> 8) & 0xFF;
+  const uint32_t tx = (jm >> 16) & 0xFF;
+  return (((tx & 1u) << 13) | (e2 << 5) | ((uint32_t)cz << 2) | (uint32_t)cx) & (RAY_BUCKETS - 1);
+}
+
+__global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, RaySort rs) {
+  extern __shared__ uint32_t h[];
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t key = job_key(rs, A.S, from.job[off + i], from.jm[off + i]);
+    rs.key[i] = key;
+    atomicAdd(&h[key], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+    if (h[b]) atomicAdd(&rs.cnt[b], h[b]);
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_job_scatter(TransportArgs A, NeeQ from, NeeQ to, RaySort rs) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* h = sm;
+  uint32_t* base = sm + RAY_BUCKETS;
+  const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
+  for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
+    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    uint32_t key[RS_PER], rank[RS_PER];
+#pragma unroll
+    for (int j = 0; j < RS_PER; ++j) {
+      const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
+      key[j] = 0xFFFFFFFFu;
+      if (i < n) {
+        key[j] = rs.key[i];
+        rank[j] = atomicAdd(&h[key[j]], 1u);
+      }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+      if (h[b]) base[b] = rs.off[b] + atomicAdd(&rs.cursor[b], h[b]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RS_PER; ++j) {
+      if (key[j] == 0xFFFFFFFFu) continue;
+      const uint32_t i = off + c0 + j * RS_THREADS + threadIdx.x;
+      const uint32_t o = off + base[key[j]] + rank[j];
+      to.job[o] = from.job[i];
+      to.jm[o] = from.jm[i];
+      to.jpath[o] = from.jpath[i];
+    }
+    __syncthreads();
+  }
+}
+
+void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, const RaySort& rs, int grid,
+                     cudaStream_t st) {
+  cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st);
+  k_job_keys<<<grid, 256, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, rs);
+  launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
+  k_job_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
+}
+
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st) {
   cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st);
@@ -298,6 +365,12 @@ void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to,
 cudaError_t ray_sort_set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_ray_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(uint32_t) * RAY_BUCKETS));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_job_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(uint32_t) * RAY_BUCKETS));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_job_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(2 * sizeof(uint32_t) * RAY_BUCKETS));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ray_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(2 * sizeof(uint32_t) * RAY_BUCKETS));

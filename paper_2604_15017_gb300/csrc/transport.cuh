@@ -64,6 +64,11 @@ struct RaySort {
 // sorts queue `from` (count live[k]) into `to`
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st);
+// sorts round k's secondary-ray jobs (from.[nee_off[k], + nee[k])) into the same range of `to`
+// by target element and origin cell: jobs aimed at one element from nearby scatterers share a
+// warp
+void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, const RaySort& rs, int grid,
+                     cudaStream_t st);
 cudaError_t ray_sort_set_attrs();
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st);
