@@ -54,8 +54,9 @@ struct TNode {
   int first = 0, count = 0;   // leaf range (count > 0)
 };
 
-const int LEAF_MAX = 4;
+const int LEAF_MAX = 8;    // a node with more primitives is always split
 const int BINS = 16;
+const double C_TRAV = 1.0;  // cost of visiting a node relative to one primitive test (SAH)
 
 struct Builder {
   std::vector<Box> pbox;
@@ -80,7 +81,7 @@ struct Builder {
       b.grow(pbox[idx[i]]);
       cb.grow(&cen[3 * (size_t)idx[i]]);
     }
-    if (count <= LEAF_MAX) return make_leaf(b, first, count);
+    if (count <= 1) return make_leaf(b, first, count);
     // binned SAH over the three axes
     int best_axis = -1, best_split = -1;
     double best_cost = 1e300;
@@ -123,6 +124,13 @@ struct Builder {
           best_split = k;
         }
       }
+    }
+    // surface-area heuristic termination: a leaf costs `count` primitive tests, a split one node
+    // visit plus the children's tests weighted by the probability of entering them
+    const double area = b.area();
+    if (count <= LEAF_MAX) {
+      const double split_cost = best_axis < 0 || !(area > 0) ? 1e300 : C_TRAV + best_cost / area;
+      if ((double)count <= split_cost) return make_leaf(b, first, count);
     }
     int mid;
     if (best_axis < 0) {
