@@ -429,14 +429,14 @@ int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* b
   unsigned long long* key;
   CKS(ws(ctx, W_IRF, (size_t)im.nl * im.nd, st, &irf));
   CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
-  CKS(ws(ctx, W_KEY, 1, st, &key));
+  CKS(ws(ctx, W_KEY, 2, st, &key));
   {
     StageScope sc_(ctx, US_STAGE_DAS, 1, st);
     launch_das(q, im, rf, irf, grid_of(ctx, 8), st);
   }
   {
-    StageScope sc_(ctx, US_STAGE_ENVLOG, 2, st);
-    launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
+    StageScope sc_(ctx, US_STAGE_ENVLOG, 0, st);
+    sc_.nk = launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
   }
   CK(cudaGetLastError());
   return US_OK;
@@ -751,9 +751,9 @@ int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* 
   float* env;
   unsigned long long* key;
   CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
-  CKS(ws(ctx, W_KEY, 1, st, &key));
-  StageScope sc_(ctx, US_STAGE_ENVLOG, 2, st);
-  launch_envlog(im, irf_dev, env, key, bmode_dev, grid_of(ctx, 8), st);
+  CKS(ws(ctx, W_KEY, 2, st, &key));
+  StageScope sc_(ctx, US_STAGE_ENVLOG, 0, st);
+  sc_.nk = launch_envlog(im, irf_dev, env, key, bmode_dev, grid_of(ctx, 8), st);
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -796,7 +796,7 @@ int us_envlog_vjp(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, con
   unsigned long long* key;
   const int np = grid_of(ctx, 2);
   CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
-  CKS(ws(ctx, W_KEY, 1, st, &key));
+  CKS(ws(ctx, W_KEY, 2, st, &key));
   CKS(ws(ctx, W_PART, np, st, &part));
   CKS(ws(ctx, W_SCAL, 4, st, &scal));
   StageScope sc_(ctx, US_STAGE_ENVLOG_VJP, 4, st);

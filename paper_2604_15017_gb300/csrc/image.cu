@@ -208,6 +208,74 @@ __global__ void k_envelope(Img im, const float* __restrict__ irf, float* env, un
 __device__ __forceinline__ float key_emax(unsigned long long k) { return __uint_as_float((uint32_t)(k >> 32)); }
 __device__ __forceinline__ int key_argmax(unsigned long long k) { return (int)(0xFFFFFFFFu - (uint32_t)k); }
 
+// ------------------------------------------------------------------------------------------
+// Fused envelope + log compression: one cooperative launch whose blocks keep the envelope of
+// their lines in shared memory, meet at one grid-wide barrier once every block has folded its
+// maximum into the packed key, then write B = max(20 log10(E / E_max), -DR).  The barrier's
+// wait is bounded in time (cooperative launches are co-resident, so it never expires in
+// practice); should it expire, the block writes NaN instead of a wrong image.
+// keyw[0] = packed maximum, keyw[1] = arrival counter (both zeroed before the launch).
+// ------------------------------------------------------------------------------------------
+constexpr long long BARRIER_CYCLES = 4000000000ll;  // ~2 s at the maximum SM clock
+
+__global__ void k_envlog_fused(Img im, const float* __restrict__ irf, unsigned long long* keyw, float* b) {
+  extern __shared__ float2 sz[];
+  const int N = im.nd;
+  const int logN = 31 - __clz(N);
+  float2* z = sz;
+  float2* tw = sz + N;
+  float* ev = reinterpret_cast<float*>(tw + N / 2);  // envelopes of this block's lines
+  twiddles(tw, N);
+  __shared__ unsigned long long best;
+  if (threadIdx.x == 0) best = 0ull;
+  int j = 0;
+  for (int l = blockIdx.x; l < im.nl; l += gridDim.x, ++j) {
+    const float* x = irf + (size_t)l * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const int r = (int)(__brev((unsigned)i) >> (32 - logN));
+      z[r] = make_float2(__ldg(&x[i]), 0.0f);
+    }
+    __syncthreads();
+    analytic_smem(z, tw, N, logN);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const float e = sqrtf(z[i].x * z[i].x + z[i].y * z[i].y);
+      ev[j * N + i] = e;
+      atomicMax(&best, ((unsigned long long)__float_as_uint(e) << 32) | (0xFFFFFFFFu - (uint32_t)(l * N + i)));
+    }
+    __syncthreads();
+  }
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    atomicMax(&keyw[0], best);
+    __threadfence();
+    atomicAdd(&keyw[1], 1ull);
+    const long long t0 = clock64();
+    while (atomicAdd(&keyw[1], 0ull) < (unsigned long long)gridDim.x) {
+      if (clock64() - t0 > BARRIER_CYCLES) {
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    best = ok ? atomicAdd(&keyw[0], 0ull) : 0xFFFFFFFFFFFFFFFFull;
+  }
+  __syncthreads();
+  const unsigned long long kk = best;
+  const float emax = __uint_as_float((uint32_t)(kk >> 32));
+  const bool valid = kk != 0xFFFFFFFFFFFFFFFFull;
+  j = 0;
+  for (int l = blockIdx.x; l < im.nl; l += gridDim.x, ++j) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const float e = ev[j * N + i];
+      float v = -im.dr;
+      if (!valid) v = __int_as_float(0x7FC00000);
+      else if (emax > 0.0f && e > 0.0f) v = fmaxf(20.0f * log10f(e / emax), -im.dr);
+      b[(size_t)l * N + i] = v;
+    }
+  }
+}
+
 // B = max(20 log10(E / E_max), -DR); E = 0 or E_max = 0 -> -DR
 __global__ void k_logc(Img im, const float* __restrict__ env, const unsigned long long* emax_key, float* b) {
   const int n = im.nl * im.nd;
@@ -322,12 +390,38 @@ void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, in
   cudaMemsetAsync(grf, 0, sizeof(float) * (size_t)q.ntx * q.ne * q.ns, st);
   k_das_adj<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, gi, grf);
 }
-void launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
-                   cudaStream_t st) {
-  cudaMemsetAsync(key, 0, sizeof(unsigned long long), st);
+static int g_fused_blocks_per_sm = -1;
+constexpr int FUSED_SMEM_MAX = 200 * 1024;
+
+int launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
+                  cudaStream_t st) {
+  cudaMemsetAsync(key, 0, 2 * sizeof(unsigned long long), st);
+  if (bmode) {
+    // fused path: every line's envelope stays in the shared memory of a co-resident block
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t base = sizeof(float2) * (size_t)(im.nd + im.nd / 2);
+    for (int lpb = 1; lpb <= 8; ++lpb) {
+      const size_t smem = base + sizeof(float) * (size_t)lpb * im.nd;
+      if (smem > (size_t)FUSED_SMEM_MAX) break;
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_envlog_fused, 256, smem) != cudaSuccess) break;
+      const int nb = (im.nl + lpb - 1) / lpb;
+      if (per_sm > 0 && nb <= per_sm * sms) {
+        void* args[] = {(void*)&im, (void*)&irf, (void*)&key, (void*)&bmode};
+        if (cudaLaunchCooperativeKernel((const void*)k_envlog_fused, dim3(nb), dim3(256), args, smem, st) ==
+            cudaSuccess)
+          return 1;
+        cudaGetLastError();
+        break;
+      }
+    }
+  }
   const int nb = min(im.nl, grid);
   k_envelope<<<nb, 256, sizeof(float2) * (size_t)(im.nd + im.nd / 2), st>>>(im, irf, env, key);
   if (bmode) k_logc<<<grid, 256, 0, st>>>(im, env, key, bmode);
+  return bmode ? 2 : 1;
 }
 void launch_loss(const Img& im, const float* b, const float* bref, float* gb, float* part, int nparts, float* loss,
                  cudaStream_t st) {
@@ -343,6 +437,8 @@ void launch_envlog_vjp(const Img& im, const float* irf, const float* gb, float* 
   k_envlog_vjp<<<nb, 256, sizeof(float2) * (size_t)(2 * im.nd + im.nd / 2), st>>>(im, irf, gb, key, live_sum, gi);
 }
 cudaError_t image_set_attrs(int nd) {
+  cudaError_t e0 = cudaFuncSetAttribute(k_envlog_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM_MAX);
+  if (e0 != cudaSuccess) return e0;
   cudaError_t e = cudaFuncSetAttribute(k_das, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float2) * DAS_THREADS * MAX_TX));
   if (e != cudaSuccess) return e;

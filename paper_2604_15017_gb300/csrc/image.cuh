@@ -7,9 +7,11 @@ namespace usrt {
 
 void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st);
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st);
-// envelope -> env (workspace) + packed (E_max, argmax) key; log compression -> bmode (optional)
-void launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
-                   cudaStream_t st);
+// envelope + log compression.  key points to 2 words (packed (E_max, argmax), barrier counter).
+// With bmode: one cooperative fused kernel when the image fits (env untouched), else envelope
+// -> env then log compression.  Without bmode: envelope -> env and the key only.
+int launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
+                  cudaStream_t st);  // returns the number of kernels launched
 void launch_loss(const Img& im, const float* b, const float* bref, float* gb, float* part, int nparts, float* loss,
                  cudaStream_t st);
 void launch_envlog_vjp(const Img& im, const float* irf, const float* gb, float* env, unsigned long long* key,
