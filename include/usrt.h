@@ -132,6 +132,16 @@ int us_scene_release(us_ctx* ctx, uint64_t scene_id);
 /* Bytes currently allocated by the context, and its budget. */
 int us_memory(us_ctx* ctx, size_t* used, size_t* budget);
 
+/* Context options. */
+enum {
+  /* DAS kernel: 0 (default) reads channel data through the read-only cache; 1 stages each
+   * (element, transmit) window in shared memory with TMA bulk copies (cp.async.bulk +
+   * mbarrier).  Both give the same image; which is faster depends on the shape. */
+  US_OPT_DAS_TMA = 0,
+  US_N_OPTS
+};
+int us_set_option(us_ctx* ctx, int option, int value);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Tracing: per-stage device time and kernel launch counts                                   */
 /* ---------------------------------------------------------------------------------------- */

@@ -67,6 +67,8 @@ struct us_ctx {
   int num_sms = 148;
   int trav_per_sm = 4;  // resident blocks of the persistent traversal kernel
   Counters* h_cnt = nullptr;  // pinned copy of the last forward's counters
+  int* d_status = nullptr;    // device status word of kernels outside the transport (ST_* bits)
+  int opts[US_N_OPTS] = {};
   cudaEvent_t ev_stats = nullptr;
   long long last_paths = 0;
   bool stats_valid = false;
@@ -432,7 +434,7 @@ int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* b
   CKS(ws(ctx, W_KEY, 2, st, &key));
   {
     StageScope sc_(ctx, US_STAGE_DAS, 1, st);
-    launch_das(q, im, rf, irf, grid_of(ctx, 8), st);
+    launch_das(q, im, rf, irf, grid_of(ctx, 8), st, ctx->opts[US_OPT_DAS_TMA] ? ctx->d_status : nullptr);
   }
   {
     StageScope sc_(ctx, US_STAGE_ENVLOG, 0, st);
@@ -465,6 +467,10 @@ int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
     return US_ERR_CUDA;
   }
   ctx->trav_per_sm = traverse_blocks_per_sm();
+  if (dev_alloc(ctx, (void**)&ctx->d_status, 256) != US_OK || cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) {
+    delete ctx;
+    return US_ERR_OOM;
+  }
   if (set_attrs(ctx) != US_OK) {
     delete ctx;
     return US_ERR_CUDA;
@@ -483,6 +489,7 @@ void us_destroy(us_ctx* ctx) {
     if (ctx->ws[i].p) cudaFree(ctx->ws[i].p);
   if (ctx->record.p) cudaFree(ctx->record.p);
   if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->ev_stats) cudaEventDestroy(ctx->ev_stats);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
@@ -513,6 +520,12 @@ int us_profile_read(us_ctx* ctx, double* ms, int64_t* launches, int n) {
   ctx->recs.clear();
   ctx->pool_used = 0;
   for (int i = 0; i < US_N_STAGES; ++i) ctx->stage_launches[i] = 0;
+  return US_OK;
+}
+
+int us_set_option(us_ctx* ctx, int option, int value) {
+  if (!ctx || option < 0 || option >= US_N_OPTS) return fail(ctx, US_ERR_ARG, "unknown option %d", option);
+  ctx->opts[option] = value;
   return US_OK;
 }
 
@@ -693,7 +706,10 @@ int us_get_stats(us_ctx* ctx, us_stats* out) {
   out->nee_queries = nee;
   out->arrivals = c.n_arr;
   out->dropped = c.dropped;
-  out->status = (c.status & ST_OVERFLOW) ? US_ERR_OVERFLOW : (c.status & ST_TIMEOUT ? US_ERR_TIMEOUT : 0);
+  int ds = 0;
+  CK(cudaMemcpy(&ds, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  const int st_bits = c.status | ds;
+  out->status = (st_bits & ST_OVERFLOW) ? US_ERR_OVERFLOW : (st_bits & ST_TIMEOUT ? US_ERR_TIMEOUT : 0);
   return US_OK;
 }
 
@@ -737,7 +753,8 @@ int us_das(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const fl
   CKS(make_img(ctx, img, im));
   if (!rf_dev || !irf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
   StageScope sc_(ctx, US_STAGE_DAS, 1, (cudaStream_t)stream);
-  launch_das(q, im, rf_dev, irf_dev, grid_of(ctx, 8), (cudaStream_t)stream);
+  launch_das(q, im, rf_dev, irf_dev, grid_of(ctx, 8), (cudaStream_t)stream,
+             ctx->opts[US_OPT_DAS_TMA] ? ctx->d_status : nullptr);
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -833,7 +850,7 @@ int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, co
   CKS(ws(ctx, W_GI, (size_t)im.nl * im.nd, st, &gi));
   {
     StageScope sc_(ctx, US_STAGE_DAS, 1, st);
-    launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st);
+    launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st, ctx->opts[US_OPT_DAS_TMA] ? ctx->d_status : nullptr);
   }
   CKS(us_envlog_vjp(ctx, img, irf, dL_dB_dev, gi, stream));
   {

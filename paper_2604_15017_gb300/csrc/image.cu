@@ -89,6 +89,202 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das(Acq q, Img im, const float*
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// DAS with the channel-data windows staged in shared memory by TMA bulk copies.
+// A CTA owns a 4-line x 128-depth pixel tile (two pixels per thread).  For every (element,
+// transmit) the samples the tile can touch form one contiguous window of the row (the delay
+// grows monotonically with depth along each line).  One pipeline stage holds the windows of
+// all transmits of one element: an elected thread issues them as cp.async.bulk copies that
+// complete on the stage's mbarrier, the CTA interpolates from shared memory, and the stage is
+// refilled with a later element once the CTA has moved on.  Every wait is bounded in time:
+// on expiry the CTA records the timeout, stops using the staged buffers and reads the channel
+// data directly (same result).
+// ------------------------------------------------------------------------------------------
+constexpr int DT_THREADS = 256, DT_DEPTHS = 128, DT_LINES = 4, DT_PX = 2;
+constexpr int DT_SMEM_MAX = 200 * 1024;
+constexpr int DT_STAGES = 3;
+constexpr int DT_WIN = 512;            // floats per staged window
+constexpr int DT_MAX_WINDOWS = 4096;   // (element, transmit) windows per tile
+constexpr long long DT_WAIT_CYCLES = 2000000000ll;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// bounded wait for phase `parity` of a stage's barrier; false on expiry
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > DT_WAIT_CYCLES) return false;
+  return true;
+}
+
+// sample window [start, start + len) of (element e, transmit t) for the tile: plain FP32 delays
+// at the tile's corners, padded by 2 samples (len 0: nothing in the record; -1: too long)
+__device__ int2 das_window(const Acq& q, const Img& im, int l0, int l1, int d0, int d1, int e, int t) {
+  const float k = q.fs / q.cbf;
+  const float st = q.sin_tx[t], ct = q.cos_tx[t];
+  const float hw = 0.5f * (q.ne - 1) * q.pitch * fabsf(st);
+  const float xe = (e - 0.5f * (q.ne - 1)) * q.pitch;
+  float lo = 3.0e38f, hi = -3.0e38f;
+  for (int l = l0; l <= l1; ++l) {
+    const float x = im.nl > 1 ? im.x0 + (im.x1 - im.x0) * (float)l / (float)(im.nl - 1) : im.x0;
+    for (int r = 0; r < 2; ++r) {
+      const int d = r ? d1 : d0;
+      const float z = im.nd > 1 ? im.z0 + (im.z1 - im.z0) * (float)d / (float)(im.nd - 1) : im.z0;
+      const float u = (x * st + z * ct + hw) * k + sqrtf((x - xe) * (x - xe) + z * z) * k;
+      lo = fminf(lo, u);
+      hi = fmaxf(hi, u);
+    }
+  }
+  int a = (int)floorf(lo) - 2, b = (int)ceilf(hi) + 3;
+  a = max(0, a) & ~3;
+  b = min(q.ns, (b + 3) & ~3);
+  if (b <= a) return make_int2(0, 0);
+  if (b - a > DT_WIN) return make_int2(a, -1);
+  return make_int2(a, b - a);
+}
+
+__global__ void __launch_bounds__(DT_THREADS) k_das_tma(Acq q, Img im, const float* __restrict__ rf,
+                                                        float* __restrict__ irf, int* status) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int ntx = q.ntx;
+  float* win = reinterpret_cast<float*>(smraw);                                // [DT_STAGES][ntx][DT_WIN]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(win + (size_t)DT_STAGES * ntx * DT_WIN);  // [DT_STAGES]
+  int2* table = reinterpret_cast<int2*>(bar + DT_STAGES);                     // [ne][ntx]
+  float2* utx_s = reinterpret_cast<float2*>(table + q.ne * ntx);              // [ntx][DT_PX][DT_THREADS]
+  __shared__ int use_tma;
+  const int tiles_d = (im.nd + DT_DEPTHS - 1) / DT_DEPTHS;
+  const int l0 = (blockIdx.x / tiles_d) * DT_LINES, d0 = (blockIdx.x % tiles_d) * DT_DEPTHS;
+  const int l1 = min(l0 + DT_LINES - 1, im.nl - 1), d1 = min(d0 + DT_DEPTHS - 1, im.nd - 1);
+  const int d = d0 + (threadIdx.x % DT_DEPTHS);
+  int lp[DT_PX];
+  bool valid[DT_PX];
+  ff x[DT_PX], z[DT_PX];
+  const DasGeo g = das_geo(q);
+#pragma unroll
+  for (int p = 0; p < DT_PX; ++p) {
+    lp[p] = l0 + (threadIdx.x / DT_DEPTHS) + 2 * p;
+    valid[p] = lp[p] < im.nl && d < im.nd;
+    x[p] = grid_coord(im.x0, im.x1, valid[p] ? lp[p] : l0, im.nl);
+    z[p] = grid_coord(im.z0, im.z1, valid[p] ? d : d0, im.nd);
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < DT_STAGES; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    use_tma = 1;
+  }
+  for (int w = threadIdx.x; w < q.ne * ntx; w += blockDim.x)
+    table[w] = das_window(q, im, l0, l1, d0, d1, w / ntx, w % ntx);
+  for (int t = 0; t < ntx; ++t)
+#pragma unroll
+    for (int p = 0; p < DT_PX; ++p) {
+      const ff u = das_utx(q, g, x[p], z[p], t);
+      utx_s[(t * DT_PX + p) * DT_THREADS + threadIdx.x] = make_float2(u.hi, u.lo);
+    }
+  __syncthreads();
+  int issued[DT_STAGES];  // uses issued per stage (meaningful in thread 0, the only issuer)
+  for (int k = 0; k < DT_STAGES; ++k) issued[k] = 0;
+  auto issue = [&](int e) {  // all transmit windows of element e into stage e % DT_STAGES
+    if (e >= q.ne) return;
+    const int s = e % DT_STAGES;
+    ++issued[s];
+    uint32_t bytes = 0;
+    for (int t = 0; t < ntx; ++t) {
+      const int2 b = table[e * ntx + t];
+      if (b.y > 0) bytes += (uint32_t)b.y * 4u;
+    }
+    mbar_arrive_tx(&bar[s], bytes);  // arrival + expected bytes; phase completes when all land
+    for (int t = 0; t < ntx; ++t) {
+      const int2 b = table[e * ntx + t];
+      if (b.y > 0)
+        bulk_g2s(win + ((size_t)s * ntx + t) * DT_WIN, rf + ((size_t)t * q.ne + e) * q.ns + b.x, (uint32_t)b.y * 4u,
+                 &bar[s]);
+    }
+  };
+  if (threadIdx.x == 0)
+    for (int e = 0; e < DT_STAGES; ++e) issue(e);
+  float acc[DT_PX];
+#pragma unroll
+  for (int p = 0; p < DT_PX; ++p) acc[p] = 0.0f;
+  for (int e = 0; e < q.ne; ++e) {
+    const int s = e % DT_STAGES;
+    bool staged = use_tma;
+    if (staged && !mbar_wait_bounded(&bar[s], (uint32_t)((e / DT_STAGES) & 1))) {
+      use_tma = 0;  // benign race: every writer stores 0
+      atomicOr(status, ST_TIMEOUT);
+      staged = false;
+    }
+    ff ur[DT_PX];
+#pragma unroll
+    for (int p = 0; p < DT_PX; ++p) ur[p] = das_urx(q, g, x[p], z[p], e);
+    float se[DT_PX];
+#pragma unroll
+    for (int p = 0; p < DT_PX; ++p) se[p] = 0.0f;
+    for (int t = 0; t < ntx; ++t) {
+      const int2 b = table[e * ntx + t];
+      const float* row = rf + ((size_t)t * q.ne + e) * q.ns;
+      const float* sw = win + ((size_t)s * ntx + t) * DT_WIN;
+#pragma unroll
+      for (int p = 0; p < DT_PX; ++p) {
+        const float2 ut = utx_s[(t * DT_PX + p) * DT_THREADS + threadIdx.x];
+        int i;
+        float f;
+        ff_floor(ff_addx(ff{ut.x, ut.y}, ur[p]), i, f);
+        const int rel = i - b.x;
+        float a0, a1;
+        if (staged && b.y > 0 && rel >= 0 && rel + 1 < b.y) {
+          a0 = sw[rel];
+          a1 = sw[rel + 1];
+        } else {
+          a0 = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
+          a1 = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
+        }
+        se[p] += fmaf(f, a1 - a0, a0);
+      }
+    }
+    const float we = hann_w(e, q.ne);
+#pragma unroll
+    for (int p = 0; p < DT_PX; ++p) acc[p] = fmaf(we, se[p], acc[p]);
+    __syncthreads();  // the CTA is done with stage s
+    if (threadIdx.x == 0 && use_tma) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(e + DT_STAGES);
+    }
+  }
+  // drain: every issued copy was waited on above unless a wait expired; then wait (bounded)
+  // once more for the last use issued into each stage before the CTA's shared memory goes away
+  if (threadIdx.x == 0 && !use_tma)
+    for (int s = 0; s < DT_STAGES; ++s)
+      if (issued[s] > 0) (void)mbar_wait_bounded(&bar[s], (uint32_t)((issued[s] - 1) & 1));
+#pragma unroll
+  for (int p = 0; p < DT_PX; ++p)
+    if (valid[p]) irf[(size_t)lp[p] * im.nd + d] = acc[p];
+}
+
+size_t das_tma_smem(const Acq& q) {
+  return sizeof(float) * DT_STAGES * (size_t)q.ntx * DT_WIN + sizeof(uint64_t) * DT_STAGES +
+         sizeof(int2) * (size_t)q.ne * q.ntx + sizeof(float2) * (size_t)q.ntx * DT_PX * DT_THREADS;
+}
+
 // transposed DAS: every tap scatters w_e (1 - f) g and w_e f g to its two samples
 __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const float* __restrict__ gi, float* grf) {
   extern __shared__ float2 utx_s[];
@@ -383,7 +579,13 @@ __global__ void k_envlog_vjp(Img im, const float* __restrict__ irf, const float*
 }
 
 // ------------------------------------------------------------------------------------------
-void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st) {
+void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st, int* status) {
+  if (status && q.ne * q.ntx <= DT_MAX_WINDOWS && das_tma_smem(q) <= (size_t)DT_SMEM_MAX &&
+      ((uintptr_t)rf & 15u) == 0) {
+    const int tiles = ((im.nl + DT_LINES - 1) / DT_LINES) * ((im.nd + DT_DEPTHS - 1) / DT_DEPTHS);
+    k_das_tma<<<tiles, DT_THREADS, das_tma_smem(q), st>>>(q, im, rf, irf, status);
+    return;
+  }
   k_das<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, rf, irf);
 }
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st) {
@@ -437,6 +639,8 @@ void launch_envlog_vjp(const Img& im, const float* irf, const float* gb, float* 
   k_envlog_vjp<<<nb, 256, sizeof(float2) * (size_t)(2 * im.nd + im.nd / 2), st>>>(im, irf, gb, key, live_sum, gi);
 }
 cudaError_t image_set_attrs(int nd) {
+  cudaError_t ea = cudaFuncSetAttribute(k_das_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, DT_SMEM_MAX);
+  if (ea != cudaSuccess) return ea;
   cudaError_t e0 = cudaFuncSetAttribute(k_envlog_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, FUSED_SMEM_MAX);
   if (e0 != cudaSuccess) return e0;
   cudaError_t e = cudaFuncSetAttribute(k_das, cudaFuncAttributeMaxDynamicSharedMemorySize,

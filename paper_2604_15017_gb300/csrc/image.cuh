@@ -5,7 +5,9 @@
 
 namespace usrt {
 
-void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st);
+// DAS; with a device status word the TMA-staged kernel is used when the shape allows
+void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st,
+                int* status = nullptr);
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st);
 // envelope + log compression.  key points to 2 words (packed (E_max, argmax), barrier counter).
 // With bmode: one cooperative fused kernel when the image fits (env untouched), else envelope

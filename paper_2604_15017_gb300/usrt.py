@@ -25,7 +25,8 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
-           "us_launch_count"]
+           "us_launch_count", "us_set_option"]
+OPT_DAS_TMA = 0
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
 
@@ -107,6 +108,7 @@ def lib():
             l.us_profile.argtypes = [VP, C.c_int]
             l.us_profile_read.argtypes = [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
             l.us_launch_count.argtypes = [VP, C.POINTER(C.c_int64)]
+            l.us_set_option.argtypes = [VP, C.c_int, C.c_int]
             _lib = l
     return _lib
 
@@ -185,6 +187,9 @@ class Context:
         ln = (C.c_int64 * n)()
         self._check(lib().us_profile_read(self.h, ms, ln, n))
         return {STAGES[i]: (ms[i], ln[i]) for i in range(n)}
+
+    def set_option(self, option, value):
+        self._check(lib().us_set_option(self.h, int(option), int(value)))
 
     def launch_count(self):
         v = C.c_int64()

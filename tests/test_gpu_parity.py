@@ -129,12 +129,36 @@ def das_case():
     return acq, img, rf.astype(np.float32).astype(np.float64)
 
 
-def test_das_matches_oracle(ctx):
+@pytest.mark.parametrize("tma", [0, 1])
+def test_das_matches_oracle(ctx, tma):
+    from paper_2604_15017_gb300 import usrt
+
     acq, img, rf = das_case()
     ref = O.das(acq, img, rf)
     bound = 2e-3 * O.das(acq, img, np.abs(rf)) + 1e-6 * np.abs(ref).max()
-    got = ctx.das(acq, img, dev(rf)).cpu().numpy()
+    ctx.set_option(usrt.OPT_DAS_TMA, tma)
+    try:
+        got = ctx.das(acq, img, dev(rf)).cpu().numpy()
+    finally:
+        ctx.set_option(usrt.OPT_DAS_TMA, 0)
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
+
+
+def test_das_tma_staging_equals_direct_loads(ctx):
+    """Both DAS kernels evaluate the same float-float delays: identical images."""
+    from paper_2604_15017_gb300 import usrt
+
+    w = small_inclusions(n_rays=50, n_tx=3)
+    acq, img = w["acq"], w["img"]
+    rng = np.random.default_rng(21)
+    rf = dev(rng.normal(size=(3, acq["n_elem"], acq["n_samples"])))
+    a = ctx.das(acq, img, rf)
+    ctx.set_option(usrt.OPT_DAS_TMA, 1)
+    try:
+        b = ctx.das(acq, img, rf)
+    finally:
+        ctx.set_option(usrt.OPT_DAS_TMA, 0)
+    assert torch.equal(a, b)
 
 
 def test_das_adjoint_matches_oracle_and_dot_product(ctx):
