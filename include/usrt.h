@@ -138,6 +138,9 @@ enum {
    * (element, transmit) window in shared memory with TMA bulk copies (cp.async.bulk +
    * mbarrier).  Both give the same image; which is faster depends on the shape. */
   US_OPT_DAS_TMA = 0,
+  /* lanes (concurrent request pipelines, each with its own stream and workspaces) used by
+   * us_forward_batch; default 4, at most 16 */
+  US_OPT_LANES = 1,
   US_N_OPTS
 };
 int us_set_option(us_ctx* ctx, int option, int value);
@@ -279,6 +282,39 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
 int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
                uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
                float* dL_drf_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Batching (many scenes / probe poses of uneven size)                                       */
+/* ---------------------------------------------------------------------------------------- */
+
+/* One request of a batch.  bref_dev == NULL: forward only (rf_dev, bmode_dev as in
+ * us_forward).  bref_dev != NULL: forward + l1/l2 loss against bref_dev + adjoint in record
+ * mode, writing loss_dev[0] and dL_dtheta_dev (float[3M+2]).  Host pointers must stay valid
+ * for the duration of the call; device buffers until the batch has run. */
+typedef struct {
+  uint64_t scene;
+  const float* theta;
+  const us_acq_desc* acq;
+  const us_img_desc* img;
+  uint64_t seed;
+  float* rf_dev;
+  float* bmode_dev;
+  const float* bref_dev;
+  float* loss_dev;
+  float* dL_dtheta_dev;
+} us_request;
+
+/* Run n requests as one stream-ordered unit on `stream`: they are spread round-robin over
+ * US_OPT_LANES lanes (own stream and workspaces each; forked from and joined back to
+ * `stream`), so small requests overlap on the device.  After one call outside capture has sized
+ * the lanes' workspaces, the call can be captured in a CUDA graph and replayed.  Each
+ * request's results are those of the corresponding single calls. */
+int us_forward_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream);
+
+/* Autotuner: times the batch for lane counts {1, 2, 4, 8} and traversal grids of {1, 2, 4} x
+ * the resident blocks per SM, keeps the fastest on the context and reports it.  Synchronous. */
+int us_autotune_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream, int* best_lanes,
+                      int* best_trav_per_sm);
 
 #ifdef __cplusplus
 }

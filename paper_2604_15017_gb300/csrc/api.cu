@@ -28,7 +28,7 @@ enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
-  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_COUNT
+  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_COUNT
 };
 
 struct SceneGPU {
@@ -53,6 +53,21 @@ struct RecordKey {
   bool valid = false;
 };
 
+// A lane owns one set of workspaces, a path record and the counters of its last forward pass.
+// Single-request calls run on lane 0 with the caller's stream; us_forward_batch spreads the
+// requests of a batch over lanes with their own streams so that they overlap on the device.
+struct Lane {
+  Buf ws[W_COUNT];
+  Buf record;
+  RecordKey rkey;
+  Counters* h_cnt = nullptr;  // pinned copy of the last forward's counters
+  cudaEvent_t ev_stats = nullptr;
+  long long last_paths = 0;
+  bool stats_valid = false;
+  cudaStream_t stream = nullptr;  // lane 0: none (the caller's stream)
+  cudaEvent_t ev_done = nullptr;
+};
+
 }  // namespace
 
 struct us_ctx {
@@ -61,17 +76,12 @@ struct us_ctx {
   std::string err;
   std::map<uint64_t, SceneGPU> scenes;
   uint64_t next_id = 1;
-  Buf ws[W_COUNT];
-  Buf record;
-  RecordKey rkey;
+  std::vector<Lane*> lanes;
+  Lane* L = nullptr;  // lane of the call in progress
   int num_sms = 148;
   int trav_per_sm = 4;  // resident blocks of the persistent traversal kernel
-  Counters* h_cnt = nullptr;  // pinned copy of the last forward's counters
   int* d_status = nullptr;    // device status word of kernels outside the transport (ST_* bits)
   int opts[US_N_OPTS] = {};
-  cudaEvent_t ev_stats = nullptr;
-  long long last_paths = 0;
-  bool stats_valid = false;
   // tracing
   bool prof = false;
   std::vector<StageRec> recs;
@@ -128,7 +138,7 @@ void dev_free(us_ctx* ctx, void* p, size_t bytes) {
 
 // grow-only workspace; growing synchronises the stream before freeing the old buffer
 int ws_get(us_ctx* ctx, int slot, size_t bytes, cudaStream_t st, void** out) {
-  Buf& b = ctx->ws[slot];
+  Buf& b = ctx->L->ws[slot];
   if (b.cap < bytes) {
     if (b.p) {
       CK(cudaStreamSynchronize(st));
@@ -152,6 +162,37 @@ int ws(us_ctx* ctx, int slot, size_t count, cudaStream_t st, T** out) {
 }
 
 int grid_of(us_ctx* ctx, int per_sm) { return ctx->num_sms * per_sm; }
+
+Lane* new_lane(us_ctx* ctx, bool own_stream) {
+  Lane* l = new Lane();
+  if (cudaMallocHost((void**)&l->h_cnt, sizeof(Counters)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&l->ev_stats, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&l->ev_done, cudaEventDisableTiming) != cudaSuccess ||
+      (own_stream && cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess)) {
+    cudaGetLastError();
+    delete l;
+    return nullptr;
+  }
+  ctx->lanes.push_back(l);
+  return l;
+}
+
+void free_lane(us_ctx* ctx, Lane* l) {
+  for (int i = 0; i < W_COUNT; ++i)
+    if (l->ws[i].p) {
+      cudaFree(l->ws[i].p);
+      ctx->used -= l->ws[i].cap;
+    }
+  if (l->record.p) {
+    cudaFree(l->record.p);
+    ctx->used -= l->record.cap;
+  }
+  if (l->h_cnt) cudaFreeHost(l->h_cnt);
+  if (l->ev_stats) cudaEventDestroy(l->ev_stats);
+  if (l->ev_done) cudaEventDestroy(l->ev_done);
+  if (l->stream) cudaStreamDestroy(l->stream);
+  delete l;
+}
 
 cudaEvent_t pool_event(us_ctx* ctx) {
   if (ctx->pool_used < ctx->pool.size()) return ctx->pool[ctx->pool_used++];
@@ -461,11 +502,12 @@ int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
     return US_ERR_CUDA;
   }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
-  if (cudaMallocHost((void**)&ctx->h_cnt, sizeof(Counters)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_stats, cudaEventDisableTiming) != cudaSuccess) {
+  ctx->L = new_lane(ctx, false);
+  if (!ctx->L) {
     delete ctx;
     return US_ERR_CUDA;
   }
+  ctx->opts[US_OPT_LANES] = 4;
   ctx->trav_per_sm = traverse_blocks_per_sm();
   if (dev_alloc(ctx, (void**)&ctx->d_status, 256) != US_OK || cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) {
     delete ctx;
@@ -485,12 +527,10 @@ void us_destroy(us_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& kv : ctx->scenes)
     for (void* p : kv.second.allocs) cudaFree(p);
-  for (int i = 0; i < W_COUNT; ++i)
-    if (ctx->ws[i].p) cudaFree(ctx->ws[i].p);
-  if (ctx->record.p) cudaFree(ctx->record.p);
-  if (ctx->h_cnt) cudaFreeHost(ctx->h_cnt);
+  for (Lane* l : ctx->lanes) free_lane(ctx, l);
+  ctx->lanes.clear();
+  ctx->L = nullptr;
   if (ctx->d_status) cudaFree(ctx->d_status);
-  if (ctx->ev_stats) cudaEventDestroy(ctx->ev_stats);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   delete ctx;
 }
@@ -621,7 +661,8 @@ int us_scene_release(us_ctx* ctx, uint64_t scene_id) {
   for (void* p : sc->allocs) cudaFree(p);
   ctx->used -= sc->bytes;
   ctx->scenes.erase(scene_id);
-  if (ctx->rkey.scene == scene_id) ctx->rkey.valid = false;
+  for (Lane* l : ctx->lanes)
+    if (l->rkey.scene == scene_id) l->rkey.valid = false;
   return US_OK;
 }
 
@@ -650,7 +691,7 @@ int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   CKS(make_media(ctx, theta, sc->n_media_hint, med));
   CKS(make_acq(ctx, acq, seed, q));
   if (bmode_dev) CKS(make_img(ctx, img, im));
-  ctx->rkey.valid = false;  // job buffers and counters are about to be overwritten
+  ctx->L->rkey.valid = false;  // job buffers and counters are about to be overwritten
   const long long n_paths = q.rays_per_tx * q.ntx;
   const long long cap_ll = n_paths * (q.kmax + 1);
   const uint32_t cap = (uint32_t)std::min<long long>(cap_ll, 0xFFFFFFF0ll);
@@ -661,42 +702,42 @@ int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   uint32_t* record = nullptr;
   if (keep_record) {
     size_t bytes = sizeof(uint32_t) * (size_t)n_paths * (q.kmax + 1);
-    if (ctx->record.cap < bytes) {
-      if (ctx->record.p) {
+    if (ctx->L->record.cap < bytes) {
+      if (ctx->L->record.p) {
         CK(cudaStreamSynchronize(st));
-        dev_free(ctx, ctx->record.p, ctx->record.cap);
-        ctx->record.p = nullptr;
-        ctx->record.cap = 0;
+        dev_free(ctx, ctx->L->record.p, ctx->L->record.cap);
+        ctx->L->record.p = nullptr;
+        ctx->L->record.cap = 0;
       }
-      CKS(dev_alloc(ctx, &ctx->record.p, bytes));
-      ctx->record.cap = bytes;
+      CKS(dev_alloc(ctx, &ctx->L->record.p, bytes));
+      ctx->L->record.cap = bytes;
     }
-    record = (uint32_t*)ctx->record.p;
+    record = (uint32_t*)ctx->L->record.p;
   }
   CKS(run_transport(ctx, sc, med, q, 0, (uint32_t)n_paths, arr, cap, record, true, cnt, st));
   CKS(do_splat(ctx, q, med.f0, arr, &cnt->n_arr, cap, rf_dev, st));
   if (bmode_dev) CKS(do_bmode(ctx, q, im, rf_dev, bmode_dev, st));
-  CK(cudaMemcpyAsync(ctx->h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-  CK(cudaEventRecord(ctx->ev_stats, st));
-  ctx->last_paths = n_paths;
-  ctx->stats_valid = true;
+  CK(cudaMemcpyAsync(ctx->L->h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(ctx->L->ev_stats, st));
+  ctx->L->last_paths = n_paths;
+  ctx->L->stats_valid = true;
   if (keep_record) {
-    ctx->rkey.scene = scene;
-    ctx->rkey.seed = seed;
-    ctx->rkey.theta.assign(theta, theta + 3 * sc->n_media_hint + 2);
-    ctx->rkey.acq.assign((const char*)&q, (const char*)&q + sizeof q);
-    ctx->rkey.n_paths = n_paths;
-    ctx->rkey.valid = true;
+    ctx->L->rkey.scene = scene;
+    ctx->L->rkey.seed = seed;
+    ctx->L->rkey.theta.assign(theta, theta + 3 * sc->n_media_hint + 2);
+    ctx->L->rkey.acq.assign((const char*)&q, (const char*)&q + sizeof q);
+    ctx->L->rkey.n_paths = n_paths;
+    ctx->L->rkey.valid = true;
   }
   return US_OK;
 }
 
 int us_get_stats(us_ctx* ctx, us_stats* out) {
   if (!ctx || !out) return US_ERR_ARG;
-  if (!ctx->stats_valid) return fail(ctx, US_ERR_STATE, "no forward pass yet");
-  CK(cudaEventSynchronize(ctx->ev_stats));
-  const Counters& c = *ctx->h_cnt;
-  out->n_paths = ctx->last_paths;
+  if (!ctx->L->stats_valid) return fail(ctx, US_ERR_STATE, "no forward pass yet");
+  CK(cudaEventSynchronize(ctx->L->ev_stats));
+  const Counters& c = *ctx->L->h_cnt;
+  out->n_paths = ctx->L->last_paths;
   long long seg = 0, nee = 0;
   for (int k = 0; k <= MAX_KMAX; ++k) {
     seg += c.live[k];
@@ -715,11 +756,11 @@ int us_get_stats(us_ctx* ctx, us_stats* out) {
 
 int us_get_record(us_ctx* ctx, int64_t path_lo, int64_t n, uint32_t* out_dev, void* stream) {
   if (!ctx || !out_dev || n < 0 || path_lo < 0) return fail(ctx, US_ERR_ARG, "invalid arguments");
-  if (!ctx->rkey.valid) return fail(ctx, US_ERR_STATE, "no record kept");
-  if (path_lo + n > ctx->rkey.n_paths) return fail(ctx, US_ERR_ARG, "path range outside the record");
-  const Acq* q = (const Acq*)ctx->rkey.acq.data();
+  if (!ctx->L->rkey.valid) return fail(ctx, US_ERR_STATE, "no record kept");
+  if (path_lo + n > ctx->L->rkey.n_paths) return fail(ctx, US_ERR_ARG, "path range outside the record");
+  const Acq* q = (const Acq*)ctx->L->rkey.acq.data();
   const size_t K1 = q->kmax + 1;
-  CK(cudaMemcpyAsync(out_dev, (uint32_t*)ctx->record.p + (size_t)path_lo * K1, sizeof(uint32_t) * (size_t)n * K1,
+  CK(cudaMemcpyAsync(out_dev, (uint32_t*)ctx->L->record.p + (size_t)path_lo * K1, sizeof(uint32_t) * (size_t)n * K1,
                      cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return US_OK;
 }
@@ -912,9 +953,9 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
     A.path_base = p0;
     A.n_paths = n;
     A.accumulate = accumulate;
-    A.nee.job = (float4*)ctx->ws[W_NEE_JOB].p;
-    A.nee.jm = (uint32_t*)ctx->ws[W_NEE_JM].p;
-    A.nee.jpath = (uint32_t*)ctx->ws[W_NEE_PATH].p;
+    A.nee.job = (float4*)ctx->L->ws[W_NEE_JOB].p;
+    A.nee.jm = (uint32_t*)ctx->L->ws[W_NEE_JM].p;
+    A.nee.jpath = (uint32_t*)ctx->L->ws[W_NEE_PATH].p;
     A.cnt = cnt;
     CKS(ws(ctx, W_SEEDS, (size_t)n * K1, st, &A.seeds));
     CKS(ws(ctx, W_ACTIVE, (size_t)n + 1, st, &active));
@@ -937,12 +978,12 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
     return US_OK;
   };
   if (mode == 0) {
-    if (!ctx->rkey.valid || ctx->rkey.scene != scene || ctx->rkey.seed != seed || ctx->rkey.n_paths != n_paths ||
-        ctx->rkey.acq.size() != sizeof q || std::memcmp(ctx->rkey.acq.data(), &q, sizeof q) != 0 ||
-        ctx->rkey.theta.size() != (size_t)A.P ||
-        std::memcmp(ctx->rkey.theta.data(), theta, sizeof(float) * A.P) != 0)
+    if (!ctx->L->rkey.valid || ctx->L->rkey.scene != scene || ctx->L->rkey.seed != seed || ctx->L->rkey.n_paths != n_paths ||
+        ctx->L->rkey.acq.size() != sizeof q || std::memcmp(ctx->L->rkey.acq.data(), &q, sizeof q) != 0 ||
+        ctx->L->rkey.theta.size() != (size_t)A.P ||
+        std::memcmp(ctx->L->rkey.theta.data(), theta, sizeof(float) * A.P) != 0)
       return fail(ctx, US_ERR_STATE, "record mode needs the last forward pass, with keep_record, on the same inputs");
-    CKS(sweep((const uint32_t*)ctx->record.p, 0, (uint32_t)n_paths, (Counters*)ctx->ws[W_CNT].p, 0));
+    CKS(sweep((const uint32_t*)ctx->L->record.p, 0, (uint32_t)n_paths, (Counters*)ctx->L->ws[W_CNT].p, 0));
   } else {
     // recompute: regenerate the decisions chunk by chunk, then sweep each chunk
     const long long chunk = std::min<long long>(n_paths, 1ll << 22);
@@ -950,7 +991,7 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
     Counters* cnt;
     CKS(ws(ctx, W_REC_CHUNK, (size_t)chunk * K1, st, &rec));
     CKS(ws(ctx, W_CNT, 1, st, &cnt));
-    ctx->rkey.valid = false;  // the job buffers and counters now hold the recomputed chunk
+    ctx->L->rkey.valid = false;  // the job buffers and counters now hold the recomputed chunk
     for (long long p0 = 0; p0 < n_paths; p0 += chunk) {
       const uint32_t n = (uint32_t)std::min<long long>(chunk, n_paths - p0);
       CKS(run_transport(ctx, sc, med, q, p0, n, nullptr, 0, rec, false, cnt, st));
@@ -976,6 +1017,90 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
   CKS(us_bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream));
   return us_transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, stream);
+}
+
+// -----------------------------------------------------------------------------------------
+// Batches: requests spread round-robin over lanes; each lane runs its requests in order on
+// its own stream, forked from and joined back to the caller's stream, so a whole batch is one
+// stream-ordered unit that can be captured in a CUDA graph (after one call outside capture
+// has grown the lanes' workspaces).
+// -----------------------------------------------------------------------------------------
+static int run_request(us_ctx* ctx, const us_request& r, cudaStream_t st) {
+  CKS(us_forward(ctx, r.scene, r.theta, r.acq, r.img, r.seed, r.bref_dev != nullptr, r.rf_dev, r.bmode_dev, st));
+  if (r.bref_dev) {
+    if (!r.bmode_dev || !r.loss_dev || !r.dL_dtheta_dev)
+      return fail(ctx, US_ERR_ARG, "a forward+adjoint request needs bmode_dev, loss_dev and dL_dtheta_dev");
+    Img im;
+    CKS(make_img(ctx, r.img, im));
+    float* gb;
+    CKS(ws(ctx, W_GB, (size_t)im.nl * im.nd, st, &gb));
+    CKS(us_loss(ctx, r.img, r.bmode_dev, r.bref_dev, r.loss_dev, gb, st));
+    CKS(us_adjoint(ctx, r.scene, r.theta, r.acq, r.img, r.seed, 0, r.rf_dev, gb, r.dL_dtheta_dev, nullptr, st));
+  }
+  return US_OK;
+}
+
+int us_forward_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream) {
+  if (!ctx || n < 0 || (n && !reqs)) return fail(ctx, US_ERR_ARG, "invalid batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nl = std::max(1, std::min(ctx->opts[US_OPT_LANES], 16));
+  while ((int)ctx->lanes.size() < nl + 1)
+    if (!new_lane(ctx, true)) return fail(ctx, US_ERR_CUDA, "cannot create a lane stream");
+  Lane* lane0 = ctx->lanes[0];
+  // fork: every lane waits for the work already on the caller's stream
+  CK(cudaEventRecord(lane0->ev_done, st));
+  for (int i = 1; i <= nl; ++i) CK(cudaStreamWaitEvent(ctx->lanes[i]->stream, lane0->ev_done, 0));
+  int rc = US_OK;
+  for (int j = 0; j < n && rc == US_OK; ++j) {
+    Lane* l = ctx->lanes[1 + j % nl];
+    ctx->L = l;
+    rc = run_request(ctx, reqs[j], l->stream);
+  }
+  ctx->L = lane0;
+  // join: the caller's stream waits for every lane
+  for (int i = 1; i <= nl; ++i) {
+    CK(cudaEventRecord(ctx->lanes[i]->ev_done, ctx->lanes[i]->stream));
+    CK(cudaStreamWaitEvent(st, ctx->lanes[i]->ev_done, 0));
+  }
+  return rc;
+}
+
+int us_autotune_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream, int* best_lanes,
+                      int* best_trav_per_sm) {
+  if (!ctx || n < 1 || !reqs) return fail(ctx, US_ERR_ARG, "invalid batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int base_trav = traverse_blocks_per_sm() / 2;  // resident blocks of the traversal kernel
+  const int lane_opts[] = {1, 2, 4, 8};
+  const int trav_opts[] = {1, 2, 4};
+  float best = 3.0e38f;
+  int bl = ctx->opts[US_OPT_LANES], bt = ctx->trav_per_sm;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int lo : lane_opts)
+    for (int to : trav_opts) {
+      ctx->opts[US_OPT_LANES] = lo;
+      ctx->trav_per_sm = base_trav * to;
+      CKS(us_forward_batch(ctx, n, reqs, stream));  // warm-up: grows the lanes' workspaces
+      CK(cudaEventRecord(e0, st));
+      CKS(us_forward_batch(ctx, n, reqs, stream));
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bl = lo;
+        bt = ctx->trav_per_sm;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->opts[US_OPT_LANES] = bl;
+  ctx->trav_per_sm = bt;
+  if (best_lanes) *best_lanes = bl;
+  if (best_trav_per_sm) *best_trav_per_sm = bt;
+  return US_OK;
 }
 
 }  // extern "C"

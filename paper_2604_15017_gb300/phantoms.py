@@ -221,3 +221,36 @@ def perturbed_theta(theta, seed, frac=0.05):
 
 def rays_for(total_rays_per_tx, n_elem):
     return int(math.ceil(total_rays_per_tx / n_elem))
+
+
+def batch_workloads(n=256, seed=4, scale=1.0, rng_sizes=None):
+    """Scenes of uneven size for batched runs: triangle counts log-uniform in [1e3, 3e5] (1-12
+    ellipsoids, tessellation scaled), rays per transmit log-uniform in [1e4, 1e6], 64/128/192
+    elements, 1024/2048/4096 samples, 1-16 plane waves over +-15 deg (one: 0 deg), scatterers
+    log-uniform in [1e3, 1e5]; even indices forward only, odd forward + adjoint.  `scale`
+    multiplies ray and scatterer counts (smaller test batches)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        n_tris = float(np.exp(rng.uniform(np.log(1e3), np.log(3e5))))
+        n_reg = int(rng.integers(1, 13))
+        per = n_tris / n_reg  # 2 n_lon (n_lat - 1) triangles per ellipsoid, n_lon = 2 n_lat
+        n_lat = max(4, int(round((1 + math.sqrt(1 + 4 * per)) / 4)))
+        rays_tx = float(np.exp(rng.uniform(np.log(1e4), np.log(1e6)))) * scale
+        n_elem = int(rng.choice([64, 128, 192]))
+        n_samples = int(rng.choice([1024, 2048, 4096]))
+        n_tx = int(rng.integers(1, 17))
+        angles = [0.0] if n_tx == 1 else list(np.linspace(-15.0, 15.0, n_tx))
+        n_scat = max(10, int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))) * scale))
+        w = inclusions(n_regions=n_reg, n_scat=n_scat, n_rays=max(1, int(math.ceil(rays_tx / n_elem))), k_max=8,
+                       n_samples=n_samples, angles_deg=angles, n_lines=128, n_depth=512, n_elem=n_elem,
+                       n_lat=n_lat, n_lon=2 * n_lat, seed_geom=1000 + i, seed_scat=2000 + i)
+        depth = min(60 * MM, 1540.0 * (n_samples - 1) / (2 * w["acq"]["fs"]))
+        w["img"] = image(128, 512, w["img"]["x0"], w["img"]["x1"], 0.0, depth)
+        w["name"] = "batch-%d" % i
+        w["seed"] = i
+        w["adjoint"] = bool(i % 2)
+        if w["adjoint"]:
+            w["theta_target"] = perturbed_theta(w["theta"], 7 + i)
+        out.append(w)
+    return out

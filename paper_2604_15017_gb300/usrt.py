@@ -25,8 +25,8 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
-           "us_launch_count", "us_set_option"]
-OPT_DAS_TMA = 0
+           "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch"]
+OPT_DAS_TMA, OPT_LANES = 0, 1
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
 
@@ -55,6 +55,13 @@ class ImgDesc(C.Structure):
     _fields_ = [("n_lines", C.c_int32), ("n_depth", C.c_int32), ("x0", C.c_float), ("x1", C.c_float),
                 ("z0", C.c_float), ("z1", C.c_float), ("dr_db", C.c_float), ("lambda1", C.c_float),
                 ("lambda2", C.c_float)]
+
+
+class Request(C.Structure):
+    _fields_ = [("scene", C.c_uint64), ("theta", C.POINTER(C.c_float)), ("acq", C.POINTER(AcqDesc)),
+                ("img", C.POINTER(ImgDesc)), ("seed", C.c_uint64), ("rf_dev", C.c_void_p),
+                ("bmode_dev", C.c_void_p), ("bref_dev", C.c_void_p), ("loss_dev", C.c_void_p),
+                ("dL_dtheta_dev", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -109,6 +116,9 @@ def lib():
             l.us_profile_read.argtypes = [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
             l.us_launch_count.argtypes = [VP, C.POINTER(C.c_int64)]
             l.us_set_option.argtypes = [VP, C.c_int, C.c_int]
+            l.us_forward_batch.argtypes = [VP, C.c_int, C.POINTER(Request), VP]
+            l.us_autotune_batch.argtypes = [VP, C.c_int, C.POINTER(Request), VP, C.POINTER(C.c_int),
+                                            C.POINTER(C.c_int)]
             _lib = l
     return _lib
 
@@ -333,6 +343,46 @@ class Context:
                                      C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
                                      _ptr(gth), _ptr(grf), _stream(stream)))
         return gth, grf
+
+
+class Batch:
+    """A prepared batch of requests (device outputs allocated once, so the batch can be run
+    repeatedly and captured in a CUDA graph).  items: dicts with scene, theta, acq, img, seed and
+    optionally bref (a device tensor: forward + loss + adjoint)."""
+
+    def __init__(self, ctx, items):
+        self.ctx = ctx
+        self.items = items
+        self._keep = []
+        n = len(items)
+        self.reqs = (Request * n)()
+        self.outputs = []
+        for i, it in enumerate(items):
+            th = _f32(it["theta"])
+            ad, ang = acq_desc(it["acq"])
+            idesc = img_desc(it["img"])
+            rf = torch.empty(ctx.rf_shape(it["acq"]), dtype=torch.float32, device=ctx.device)
+            b = torch.empty((it["img"]["n_lines"], it["img"]["n_depth"]), dtype=torch.float32, device=ctx.device)
+            bref = it.get("bref")
+            loss = torch.zeros(1, dtype=torch.float32, device=ctx.device) if bref is not None else None
+            g = torch.zeros(len(th), dtype=torch.float32, device=ctx.device) if bref is not None else None
+            self._keep += [th, ad, ang, idesc]
+            self.reqs[i] = Request(int(it["scene"]), th.ctypes.data_as(C.POINTER(C.c_float)), C.pointer(ad),
+                                   C.pointer(idesc), int(it.get("seed", 0)) & (2**64 - 1), rf.data_ptr(),
+                                   b.data_ptr(), bref.data_ptr() if bref is not None else None,
+                                   loss.data_ptr() if loss is not None else None,
+                                   g.data_ptr() if g is not None else None)
+            self.outputs.append(dict(rf=rf, bmode=b, loss=loss, grad=g))
+
+    def run(self, stream=None):
+        self.ctx._check(lib().us_forward_batch(self.ctx.h, len(self.items), self.reqs, _stream(stream)))
+        return self.outputs
+
+    def autotune(self, stream=None):
+        bl, bt = C.c_int(), C.c_int()
+        self.ctx._check(lib().us_autotune_batch(self.ctx.h, len(self.items), self.reqs, _stream(stream), C.byref(bl),
+                                                C.byref(bt)))
+        return bl.value, bt.value
 
 
 class BModeSimulation(torch.autograd.Function):

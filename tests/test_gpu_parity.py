@@ -401,3 +401,80 @@ def test_memory_budget_refuses_admission():
         c.upload_workload(w)
     assert ei.value.code == usrt.US_ERR_OOM
     c.close()
+
+
+# ------------------------------------------------------------------------------------------
+# batching: each request of a mixed batch equals its single call
+# ------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_batch_matches_single_calls(ctx, lanes):
+    from paper_2604_15017_gb300 import usrt
+
+    ws = P.batch_workloads(n=6, seed=11, scale=0.01)
+    items, singles = [], []
+    for w in ws:
+        sid = ctx.upload_workload(w)
+        it = dict(scene=sid, theta=w["theta"], acq=w["acq"], img=w["img"], seed=w["seed"])
+        rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=w["adjoint"])
+        single = dict(rf=rf.clone(), bmode=b.clone())
+        if w["adjoint"]:
+            _, bref = ctx.forward(sid, w["theta_target"], w["acq"], w["img"], seed=w["seed"])
+            it["bref"] = bref.clone()
+            rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+            loss, gb = ctx.loss(w["img"], b, it["bref"])
+            g, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, gb)
+            single.update(loss=loss.clone(), grad=g.clone())
+        items.append(it)
+        singles.append(single)
+    ctx.set_option(usrt.OPT_LANES, lanes)
+    batch = usrt.Batch(ctx, items)
+    outs = batch.run()
+    torch.cuda.synchronize()
+    ctx.set_option(usrt.OPT_LANES, 4)
+    for w, o, s_ in zip(ws, outs, singles):
+        assert rel_l2(o["rf"].double().cpu().numpy(), s_["rf"].double().cpu().numpy()) <= 1e-5
+        assert float((o["bmode"] - s_["bmode"]).abs().max()) <= 0.05
+        if w["adjoint"]:
+            assert abs(float(o["loss"]) - float(s_["loss"])) <= 1e-4 * abs(float(s_["loss"])) + 1e-6
+            g1, g2 = o["grad"].double().cpu().numpy(), s_["grad"].double().cpu().numpy()
+            th = np.abs(w["theta"])
+            assert np.all(np.abs(g1 - g2) * th <= 1e-3 * np.abs(g2) * th + 1e-4 * np.max(np.abs(g2) * th))
+    for it in items:
+        ctx.release_scene(it["scene"])
+
+
+def test_batch_graph_capture_and_autotune(ctx):
+    from paper_2604_15017_gb300 import usrt
+
+    ws = P.batch_workloads(n=4, seed=12, scale=0.005)
+    items = []
+    for w in ws:
+        sid = ctx.upload_workload(w)
+        it = dict(scene=sid, theta=w["theta"], acq=w["acq"], img=w["img"], seed=w["seed"])
+        if w["adjoint"]:
+            it["bref"] = torch.full((w["img"]["n_lines"], w["img"]["n_depth"]), -30.0, device="cuda")
+        items.append(it)
+    batch = usrt.Batch(ctx, items)
+    lanes, trav = batch.autotune()
+    assert lanes in (1, 2, 4, 8) and trav >= 1
+    ref = [dict((k, None if v is None else v.clone()) for k, v in o.items()) for o in batch.run()]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.run(stream=s)  # outside capture: workspaces sized
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run()
+    for o in batch.outputs:
+        o["bmode"].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(batch.outputs, ref):
+        assert float((o["bmode"] - r["bmode"]).abs().max()) <= 0.05
+        if r["grad"] is not None:
+            assert torch.allclose(o["grad"], r["grad"], rtol=1e-3, atol=1e-3 * float(r["grad"].abs().max()))
+    for it in items:
+        ctx.release_scene(it["scene"])
