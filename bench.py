@@ -37,6 +37,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-stages", action="store_true")
+    ap.add_argument("--config", default="frame", choices=["frame", "batch", "serve"],
+                    help="frame: one fwd+adj frame per step (the metric line); batch: a batch of scenes of "
+                         "uneven size, batched vs one by one; serve: Poisson arrivals through the serving loop")
+    ap.add_argument("--batch-n", type=int, default=256, help="scenes in the batch")
+    ap.add_argument("--scale", type=float, default=1.0, help="ray/scatterer scale of batch and serve scenes")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: arrival window, s")
+    ap.add_argument("--serve-scenes", type=int, default=32, help="serve: resident scenes requests draw from")
+    ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent lanes")
     return ap.parse_args()
 
 
@@ -231,9 +240,142 @@ def run_reference(args, w):
 
 
 # --------------------------------------------------------------------------------------------
+def _prepare_items(ctx, ws):
+    """Upload the scenes and make each odd-index request a fwd+adj step against a target image
+    rendered at perturbed parameters (outside any timed region)."""
+    items = []
+    for w in ws:
+        sid = ctx.upload_workload(w)
+        it = dict(scene=sid, theta=w["theta"], acq=w["acq"], img=w["img"], seed=w["seed"])
+        if w["adjoint"]:
+            _, bref = ctx.forward(sid, w["theta_target"], w["acq"], w["img"], seed=w["seed"])
+            it["bref"] = bref.clone()
+        items.append(it)
+    return items
+
+
+def _plain(ctx, it):
+    """One request through the plain per-call API on the current stream."""
+    if it.get("bref") is None:
+        return ctx.forward(it["scene"], it["theta"], it["acq"], it["img"], seed=it["seed"])
+    rf, b = ctx.forward(it["scene"], it["theta"], it["acq"], it["img"], seed=it["seed"], keep_record=True)
+    loss, gb = ctx.loss(it["img"], b, it["bref"])
+    return ctx.adjoint(it["scene"], it["theta"], it["acq"], it["img"], it["seed"], rf, gb)
+
+
+def run_batch(args):
+    """Batched (lanes + CUDA graph, autotuned) vs one-by-one: path-segments/s over the batch."""
+    import torch
+    from paper_2604_15017_gb300 import phantoms as P, usrt
+
+    ws = P.batch_workloads(n=args.batch_n, seed=4, scale=args.scale)
+    ctx = usrt.Context(0)
+    items = _prepare_items(ctx, ws)
+    segs = 0
+    for it in items:  # per-request work counts (also the plain path's warm-up)
+        _plain(ctx, it)
+        st_ = ctx.stats()
+        segs += st_["segments"] + st_["nee_queries"]
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    ms_plain = timed(lambda: [_plain(ctx, it) for it in items])
+    batch = usrt.Batch(ctx, items)
+    lanes, trav = batch.autotune()
+    launches0 = ctx.launch_count()
+    with ClockSampler(0) as clk:
+        ms_batch = timed(batch.run)
+    launches = (ctx.launch_count() - launches0) // (args.steps + args.warmup)
+    side = torch.cuda.Stream()
+    side.wait_stream(st)
+    with torch.cuda.stream(side):
+        batch.run(stream=side)
+    st.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.run()
+    ms_graph = timed(g.replay)
+    n_paths = sum(w["acq"]["n_rays"] * w["acq"]["n_elem"] * len(w["acq"]["angles"]) for w in ws)
+    best = min(ms_batch, ms_graph)
+    out = {"metric": METRIC, "value": segs / (best * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": best, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch-%d-scenes-seed4-scale%g" % (args.batch_n, args.scale),
+                      "step": "whole batch (even fwd, odd fwd+loss+adj)", "paths_per_step": n_paths,
+                      "segments_per_step": segs, "autotuned_lanes": lanes, "autotuned_trav_blocks_per_sm": trav,
+                      "l2": "per-step working set exceeds L2"},
+           "plain": {"ms_per_step": ms_plain, "value": segs / (ms_plain * 1e-3)},
+           "batched": {"ms_per_step": ms_batch, "value": segs / (ms_batch * 1e-3)},
+           "graph": {"ms_per_step": ms_graph, "value": segs / (ms_graph * 1e-3)},
+           "speedup_vs_plain": ms_plain / best, "gpu_launches": launches * args.steps, "clocks": clk.summary()}
+    print(json.dumps(out))
+    ctx.close()
+
+
+def run_serve(args):
+    """Poisson arrivals of requests on resident scenes (70 % fwd B-mode, 30 % fwd+loss+adj), served
+    by the continuous-batching loop under a memory budget, against the plain sequential path."""
+    import torch
+    from paper_2604_15017_gb300 import phantoms as P, serve, usrt
+
+    ws = P.batch_workloads(n=args.serve_scenes, seed=5, scale=args.scale)
+    ctx = usrt.Context(0)
+    items = _prepare_items(ctx, ws)
+    for w, it in zip(ws, items):
+        if it.get("bref") is None:  # every scene can take both kinds of request
+            _, bref = ctx.forward(it["scene"], P.perturbed_theta(w["theta"], 99), w["acq"], w["img"], seed=w["seed"])
+            it["bref_fa"] = bref.clone()
+        else:
+            it["bref_fa"] = it["bref"]
+    torch.cuda.synchronize()
+    times = serve.poisson_arrivals(args.rate, args.serve_seconds, seed=5)
+    rng = np.random.default_rng(5)
+    arrivals = []
+    n_adj = 0
+    for t in times:
+        it = dict(items[int(rng.integers(len(items)))])
+        adj = rng.random() < 0.3
+        n_adj += adj
+        it["bref"] = it["bref_fa"] if adj else None
+        it.pop("bref_fa")
+        arrivals.append((t, it))
+    srv = serve.Server(ctx, n_lanes=args.lanes, mem_budget_bytes=120 << 30)
+    srv.warmup([a[1] for a in arrivals])
+    with ClockSampler(0) as clk:
+        served = srv.run(arrivals)
+    seq = serve.run_sequential(ctx, arrivals)
+    out = {"metric": "requests/s", "value": served["throughput"], "unit": "requests/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "serve-poisson-%grps-%gs-%d-scenes-seed5-scale%g" %
+                      (args.rate, args.serve_seconds, args.serve_scenes, args.scale), "lanes": args.lanes,
+                      "requests": len(arrivals), "fwd_adj_requests": int(n_adj), "mem_budget_gb": 120},
+           "served": served, "sequential": seq, "max_running": srv.max_running, "clocks": clk.summary()}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     args = parse()
     from paper_2604_15017_gb300 import phantoms as P
+
+    if args.impl == "ours" and args.config == "batch":
+        run_batch(args)
+        return
+    if args.impl == "ours" and args.config == "serve":
+        run_serve(args)
+        return
 
     w = P.inclusions(n_rays=args.rays)
     if args.impl == "reference":

@@ -316,6 +316,14 @@ int us_forward_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream);
 int us_autotune_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream, int* best_lanes,
                       int* best_trav_per_sm);
 
+/* Serving: run one request on lane `lane` (1..16; lane 0 belongs to the single-request calls)
+ * on the caller's `stream`.  Requests on different lanes may run concurrently on different
+ * streams; requests on one lane must be stream-ordered.  */
+int us_run_request(us_ctx* ctx, int lane, const us_request* req, void* stream);
+
+/* Device memory [bytes] a request's workspaces need on a lane (admission control). */
+int us_request_bytes(us_ctx* ctx, const us_request* req, size_t* bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1065,6 +1065,30 @@ int us_forward_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream) {
   return rc;
 }
 
+int us_run_request(us_ctx* ctx, int lane, const us_request* req, void* stream) {
+  if (!ctx || !req || lane < 1 || lane > 16) return fail(ctx, US_ERR_ARG, "lane must lie in [1, 16]");
+  while ((int)ctx->lanes.size() <= lane)
+    if (!new_lane(ctx, true)) return fail(ctx, US_ERR_CUDA, "cannot create a lane");
+  Lane* lane0 = ctx->lanes[0];
+  ctx->L = ctx->lanes[lane];
+  const int rc = run_request(ctx, *req, (cudaStream_t)stream);
+  ctx->L = lane0;
+  return rc;
+}
+
+int us_request_bytes(us_ctx* ctx, const us_request* req, size_t* bytes) {
+  if (!ctx || !req || !bytes) return fail(ctx, US_ERR_ARG, "null argument");
+  Acq q;
+  CKS(make_acq(ctx, req->acq, 0, q));
+  const size_t n = (size_t)(q.rays_per_tx * q.ntx), K1 = q.kmax + 1, jobs = n * std::max(1, q.kmax);
+  size_t b = n * (2 * 48 + 8 + 4) + jobs * 2 * 24 + n * K1 * 16 * 2;  // queues, hits, keys, jobs, arrivals
+  if (req->bref_dev) b += n * K1 * (4 + 8) + n * 4;                    // record, seeds, active list
+  if (req->img) b += (size_t)req->img->n_lines * req->img->n_depth * 4 * 5;
+  b += (size_t)q.ntx * q.ne * q.ns * 4;                                 // dL/dRF
+  *bytes = b;
+  return US_OK;
+}
+
 int us_autotune_batch(us_ctx* ctx, int n, const us_request* reqs, void* stream, int* best_lanes,
                       int* best_trav_per_sm) {
   if (!ctx || n < 1 || !reqs) return fail(ctx, US_ERR_ARG, "invalid batch");

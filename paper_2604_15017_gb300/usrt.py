@@ -25,7 +25,8 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
-           "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch"]
+           "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch",
+           "us_run_request", "us_request_bytes"]
 OPT_DAS_TMA, OPT_LANES = 0, 1
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
@@ -117,6 +118,8 @@ def lib():
             l.us_launch_count.argtypes = [VP, C.POINTER(C.c_int64)]
             l.us_set_option.argtypes = [VP, C.c_int, C.c_int]
             l.us_forward_batch.argtypes = [VP, C.c_int, C.POINTER(Request), VP]
+            l.us_run_request.argtypes = [VP, C.c_int, C.POINTER(Request), VP]
+            l.us_request_bytes.argtypes = [VP, C.POINTER(Request), C.POINTER(C.c_size_t)]
             l.us_autotune_batch.argtypes = [VP, C.c_int, C.POINTER(Request), VP, C.POINTER(C.c_int),
                                             C.POINTER(C.c_int)]
             _lib = l
@@ -377,6 +380,16 @@ class Batch:
     def run(self, stream=None):
         self.ctx._check(lib().us_forward_batch(self.ctx.h, len(self.items), self.reqs, _stream(stream)))
         return self.outputs
+
+    def run_one(self, i, lane, stream=None):
+        """Request i alone on `lane` (1..16) and `stream` (serving)."""
+        self.ctx._check(lib().us_run_request(self.ctx.h, int(lane), C.byref(self.reqs[i]), _stream(stream)))
+        return self.outputs[i]
+
+    def bytes_needed(self, i):
+        v = C.c_size_t()
+        self.ctx._check(lib().us_request_bytes(self.ctx.h, C.byref(self.reqs[i]), C.byref(v)))
+        return v.value
 
     def autotune(self, stream=None):
         bl, bt = C.c_int(), C.c_int()
