@@ -79,7 +79,8 @@ struct us_ctx {
   std::vector<Lane*> lanes;
   Lane* L = nullptr;  // lane of the call in progress
   int num_sms = 148;
-  int trav_per_sm = 4;  // resident blocks of the persistent traversal kernel
+  int trav_per_sm = 4;   // blocks per SM of the traversal grid
+  int march_per_sm = 4;  // resident blocks per SM of the scatterer march
   int* d_status = nullptr;    // device status word of kernels outside the transport (ST_* bits)
   int opts[US_N_OPTS] = {};
   // tracing
@@ -420,8 +421,9 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     A.qout = Q.a;
     if (sort_jobs) A.nee = unsorted;
     {
-      StageScope sc_(ctx, US_STAGE_TRAVERSE, 1, st);
+      StageScope sc_(ctx, US_STAGE_TRAVERSE, sc->dev.n_scat > 0 ? 2 : 1, st);
       launch_traverse(A, grid_of(ctx, ctx->trav_per_sm), st);
+      if (sc->dev.n_scat > 0) launch_march(A, grid_of(ctx, ctx->march_per_sm), st);
     }
     {
       StageScope sc_(ctx, US_STAGE_INTERACT, 1, st);
@@ -509,6 +511,7 @@ int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
   }
   ctx->opts[US_OPT_LANES] = 4;
   ctx->trav_per_sm = traverse_blocks_per_sm();
+  ctx->march_per_sm = march_blocks_per_sm();
   if (dev_alloc(ctx, (void**)&ctx->d_status, 256) != US_OK || cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) {
     delete ctx;
     return US_ERR_OOM;
@@ -605,43 +608,60 @@ int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
   in.r_s = d->r_s;
   HostSceneOut o;
   build_scene_host(in, o);
+  if (o.gn[0] < 0) return fail(ctx, US_ERR_ARG, "more than 255 scatterer spheres overlap one grid cell at every cell size");
   SceneGPU sc;
   sc.n_media_hint = d->n_media;
-  auto up = [&](const std::vector<float>& v, const float4** dst) -> int {
+  auto up_bytes = [&](const void* src, size_t bytes, const void** dst) -> int {
     void* p = nullptr;
-    size_t bytes = v.size() * sizeof(float);
     CKS(dev_alloc(ctx, &p, bytes));
     sc.allocs.push_back(p);
     sc.bytes += bytes;
-    if (bytes) CK(cudaMemcpy(p, v.data(), bytes, cudaMemcpyHostToDevice));
-    *dst = (const float4*)p;
+    if (bytes) CK(cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice));
+    *dst = p;
     return US_OK;
   };
+  auto up = [&](const std::vector<float>& v, const float4** dst) -> int {
+    return up_bytes(v.data(), v.size() * sizeof(float), reinterpret_cast<const void**>(dst));
+  };
   int s;
-  if ((s = up(o.nodes, &sc.dev.nodes)) || (s = up(o.prims, &sc.dev.prims)) || (s = up(o.tri_nrm, &sc.dev.tri_nrm)) ||
-      (s = up(o.tri_v0, &sc.dev.tri_v0)) || (s = up(o.scat, &sc.dev.scat)) ||
-      (s = up(o.nodes_t, &sc.dev.nodes_t)) || (s = up(o.prims_t, &sc.dev.prims_t))) {
+  if ((s = up(o.tri_nrm, &sc.dev.tri_nrm)) || (s = up(o.tri_v0, &sc.dev.tri_v0)) || (s = up(o.scat, &sc.dev.scat)) ||
+      (s = up(o.nodes_t, &sc.dev.nodes_t)) || (s = up(o.prims_t, &sc.dev.prims_t)) ||
+      (s = up(o.cell_sph, &sc.dev.cell_sph)) ||
+      (s = up_bytes(o.cell.data(), o.cell.size() * sizeof(uint32_t), reinterpret_cast<const void**>(&sc.dev.cell)))) {
     for (void* p : sc.allocs) cudaFree(p);
     ctx->used -= sc.bytes;
     return s;
   }
-  // root box = union of the two children of node 0: x at words (0,1)/(4,5), y at (2,3)/(6,7),
-  // z at (8,9)/(10,11)
+  // scene bounds (ray-sort cells): the triangle BVH's root box (union of node 0's two child
+  // boxes: x at words (0,1)/(4,5), y at (2,3)/(6,7), z at (8,9)/(10,11)) and the scatterer grid
   const int lo_w[3][2] = {{0, 4}, {2, 6}, {8, 10}};
+  const float glo[3] = {o.glo[0], o.glo[1], o.glo[2]};
   for (int a = 0; a < 3; ++a) {
-    sc.lo[a] = std::min(o.nodes[lo_w[a][0]], o.nodes[lo_w[a][1]]);
-    sc.hi[a] = std::max(o.nodes[lo_w[a][0] + 1], o.nodes[lo_w[a][1] + 1]);
+    sc.lo[a] = 3.0e38f;
+    sc.hi[a] = -3.0e38f;
+    if (d->n_tris) {
+      sc.lo[a] = std::min(o.nodes_t[lo_w[a][0]], o.nodes_t[lo_w[a][1]]);
+      sc.hi[a] = std::max(o.nodes_t[lo_w[a][0] + 1], o.nodes_t[lo_w[a][1] + 1]);
+    }
+    if (d->n_scat) {
+      sc.lo[a] = std::min(sc.lo[a], glo[a]);
+      sc.hi[a] = std::max(sc.hi[a], glo[a] + o.gn[a] * o.gh);
+    }
     if (!(sc.lo[a] <= sc.hi[a])) {
       sc.lo[a] = -1.0f;
       sc.hi[a] = 1.0f;
     }
   }
-  sc.dev.n_nodes = o.n_nodes;
+  sc.dev.glo = make_float3(o.glo[0], o.glo[1], o.glo[2]);
+  sc.dev.gh = o.gh;
+  sc.dev.gnx = o.gn[0];
+  sc.dev.gny = o.gn[1];
+  sc.dev.gnz = o.gn[2];
   sc.dev.n_tris = d->n_tris;
   sc.dev.n_scat = d->n_scat;
   sc.dev.rs2 = d->r_s * d->r_s;
   // depth check: the traversal stacks hold 64 entries
-  sc.depth = std::max(o.depth, o.depth_t);
+  sc.depth = o.depth_t;
   if (sc.depth > 60) {
     for (void* p : sc.allocs) cudaFree(p);
     ctx->used -= sc.bytes;

@@ -1,8 +1,11 @@
-// Host-side BVH construction for the usrt scene (binned surface-area heuristic).
+// Host-side acceleration structures of the usrt scene.
 //
-// Two BVHs are built: one over triangles and point-scatterer spheres (closest hits of primary
-// rays) and one over triangles only (all-crossings queries of secondary rays, which ignore the
-// scatterers).  The device layout is a BVH2 whose
+// Triangles: a BVH2 built by binned surface-area heuristic, used by both closest-hit queries and
+// the all-crossings queries of secondary rays.  Scatterer spheres (tiny, spread through whole
+// regions of tissue) go into a uniform grid instead: a ray marches its cells front to back (3D
+// DDA), so finding the nearest sphere costs a short sequence of independent cell reads rather
+// than a long chain of dependent BVH node reads through a dense cloud of tiny boxes.  The
+// device layout of the BVH2 is one whose
 // inner nodes hold both children's boxes in four 16-byte words, so a traversal step is four
 // 128-bit loads of one 64-byte (32-byte aligned) node:
 //   n0 = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)   n1 = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
@@ -175,31 +178,20 @@ float bits_f(uint32_t u) {
 
 }  // namespace
 
-// BVH over the primitive subset `ids` (0..nt-1 triangles, nt.. scatterers): device nodes and
-// primitives in leaf order
-static void build_one(const HostSceneIn& in, const std::vector<int>& ids, std::vector<float>& nodes_out,
-                      std::vector<float>& prims_out, int& n_nodes_out, int& depth_out) {
-  const int nt = in.n_tris;
-  const int n = (int)ids.size();
+// BVH over the triangles: device nodes and triangles in leaf order
+static void build_tri_bvh(const HostSceneIn& in, std::vector<float>& nodes_out, std::vector<float>& prims_out,
+                          int& n_nodes_out, int& depth_out) {
+  const int n = in.n_tris;
   Builder B;
   B.pbox.resize(n);
   B.cen.resize(3 * (size_t)n);
   B.idx.resize(n);
   for (int k = 0; k < n; ++k) {
-    const int i = ids[k];
     Box b;
-    if (i < nt) {
-      b.empty();
-      for (int v = 0; v < 3; ++v) {
-        double p[3] = {in.tris[9 * (size_t)i + 3 * v], in.tris[9 * (size_t)i + 3 * v + 1], in.tris[9 * (size_t)i + 3 * v + 2]};
-        b.grow(p);
-      }
-    } else {
-      const int j = i - nt;
-      for (int a = 0; a < 3; ++a) {
-        b.lo[a] = (double)in.scat_pos[3 * (size_t)j + a] - in.r_s;
-        b.hi[a] = (double)in.scat_pos[3 * (size_t)j + a] + in.r_s;
-      }
+    b.empty();
+    for (int v = 0; v < 3; ++v) {
+      double p[3] = {in.tris[9 * (size_t)k + 3 * v], in.tris[9 * (size_t)k + 3 * v + 1], in.tris[9 * (size_t)k + 3 * v + 2]};
+      b.grow(p);
     }
     B.pbox[k] = b;
     for (int a = 0; a < 3; ++a) B.cen[3 * (size_t)k + a] = 0.5 * (b.lo[a] + b.hi[a]);
@@ -272,38 +264,113 @@ static void build_one(const HostSceneIn& in, const std::vector<int>& ids, std::v
   }
   n_nodes_out = (int)(nodes_out.size() / 16);
 
-  // primitives in leaf order
+  // triangles in leaf order: (v0, code) (e1, -) (e2, -)
   prims_out.assign(12 * (size_t)n, 0.0f);
   for (int k = 0; k < n; ++k) {
-    const int p = ids[B.idx[k]];
+    const int p = B.idx[k];
     float* o = &prims_out[12 * (size_t)k];
-    if (p < nt) {
-      const float* t = &in.tris[9 * (size_t)p];
-      o[0] = t[0];
-      o[1] = t[1];
-      o[2] = t[2];
-      o[3] = bits_f((2u << 20) | (uint32_t)p);
-      for (int a = 0; a < 3; ++a) {
-        o[4 + a] = (float)((double)t[3 + a] - (double)t[a]);
-        o[8 + a] = (float)((double)t[6 + a] - (double)t[a]);
-      }
-    } else {
-      const int j = p - nt;
-      o[0] = in.scat_pos[3 * (size_t)j];
-      o[1] = in.scat_pos[3 * (size_t)j + 1];
-      o[2] = in.scat_pos[3 * (size_t)j + 2];
-      o[3] = bits_f((3u << 20) | (uint32_t)j);
+    const float* t = &in.tris[9 * (size_t)p];
+    o[0] = t[0];
+    o[1] = t[1];
+    o[2] = t[2];
+    o[3] = bits_f((2u << 20) | (uint32_t)p);
+    for (int a = 0; a < 3; ++a) {
+      o[4 + a] = (float)((double)t[3 + a] - (double)t[a]);
+      o[8 + a] = (float)((double)t[6 + a] - (double)t[a]);
     }
   }
 }
 
+// Uniform grid over the scatterer spheres.  The cell edge targets GRID_CELLS_PER_SPHERE cells
+// per sphere over the spheres' bounding box (a ray then tests about one sphere per two or three
+// cells it crosses), but is never below the sphere diameter (each sphere then overlaps at most
+// 2 x 2 x 2 cells); it is raised until the grid has at most GRID_MAX_CELLS cells and no cell
+// holds more than 255 spheres (clustered scatterers).  Boxes are inflated by GRID_PAD cell
+// edges so that a closest-approach point within float rounding of a cell face is listed on
+// both sides.
+const double GRID_CELLS_PER_SPHERE = 8.0;
+const double GRID_MAX_CELLS = 16.0 * 1024 * 1024;
+const double GRID_PAD = 1e-2;
+
+static void build_scatter_grid(const HostSceneIn& in, HostSceneOut& out) {
+  const int ns = in.n_scat;
+  out.cell.clear();
+  out.cell_sph.clear();
+  if (ns == 0) {
+    out.gn[0] = out.gn[1] = out.gn[2] = 0;
+    return;
+  }
+  const double rs = in.r_s;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int j = 0; j < ns; ++j)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], (double)in.scat_pos[3 * (size_t)j + a] - rs);
+      hi[a] = std::max(hi[a], (double)in.scat_pos[3 * (size_t)j + a] + rs);
+    }
+  double ext[3], vol = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    ext[a] = std::max(hi[a] - lo[a], 1e-9);
+    vol *= ext[a];
+  }
+  double h = std::max(std::max(std::cbrt(vol / (GRID_CELLS_PER_SPHERE * ns)), 2.0 * rs), 1e-9);
+  for (int attempt = 0; attempt < 200; ++attempt, h *= 1.25) {
+    int n[3];
+    double cells = 1.0;
+    for (int a = 0; a < 3; ++a) {
+      n[a] = std::max(1, (int)std::ceil(ext[a] / h));
+      cells *= n[a];
+    }
+    if (cells > GRID_MAX_CELLS || n[0] > 4096 || n[1] > 4096 || n[2] > 4096) continue;
+    // the device marches the float description; cells of a coordinate are taken from it here too
+    for (int a = 0; a < 3; ++a) {
+      out.glo[a] = round_down(lo[a]);
+      out.gn[a] = n[a];
+    }
+    out.gh = (float)h;
+    const double pad = GRID_PAD * h;
+    auto cell_range = [&](double c, int a, int& c0, int& c1) {
+      c0 = std::max(0, std::min(n[a] - 1, (int)std::floor((c - rs - pad - out.glo[a]) / out.gh)));
+      c1 = std::max(0, std::min(n[a] - 1, (int)std::floor((c + rs + pad - out.glo[a]) / out.gh)));
+    };
+    const size_t n_cells = (size_t)n[0] * n[1] * n[2];
+    std::vector<uint32_t> count(n_cells, 0), first(n_cells, 0);
+    auto for_cells = [&](int j, auto&& fn) {
+      int r0[3], r1[3];
+      for (int a = 0; a < 3; ++a) cell_range(in.scat_pos[3 * (size_t)j + a], a, r0[a], r1[a]);
+      for (int z = r0[2]; z <= r1[2]; ++z)
+        for (int y = r0[1]; y <= r1[1]; ++y)
+          for (int x = r0[0]; x <= r1[0]; ++x) fn(((uint32_t)z * n[1] + y) * n[0] + x);
+    };
+    for (int j = 0; j < ns; ++j) for_cells(j, [&](uint32_t c) { count[c]++; });
+    uint64_t acc = 0;
+    uint32_t most = 0;
+    for (size_t c = 0; c < n_cells; ++c) {
+      first[c] = (uint32_t)acc;
+      acc += count[c];
+      most = std::max(most, count[c]);
+    }
+    if (most > 255 || acc >= (1u << 24)) continue;
+    out.cell.resize(n_cells);
+    for (size_t c = 0; c < n_cells; ++c) out.cell[c] = first[c] << 8 | count[c];
+    out.cell_sph.assign(4 * (size_t)acc, 0.0f);
+    for (int j = 0; j < ns; ++j)
+      for_cells(j, [&](uint32_t c) {
+        float* e = &out.cell_sph[4 * (size_t)first[c]++];
+        e[0] = in.scat_pos[3 * (size_t)j];
+        e[1] = in.scat_pos[3 * (size_t)j + 1];
+        e[2] = in.scat_pos[3 * (size_t)j + 2];
+        e[3] = bits_f((3u << 20) | (uint32_t)j);
+      });
+    return;
+  }
+  // unreachable for scenes the upload accepts (< 2^20 spheres): an empty grid would lose hits
+  out.gn[0] = out.gn[1] = out.gn[2] = -1;
+}
+
 void build_scene_host(const HostSceneIn& in, HostSceneOut& out) {
   const int nt = in.n_tris, ns = in.n_scat;
-  std::vector<int> all(nt + ns), tris(nt);
-  for (int i = 0; i < nt + ns; ++i) all[i] = i;
-  for (int i = 0; i < nt; ++i) tris[i] = i;
-  build_one(in, all, out.nodes, out.prims, out.n_nodes, out.depth);
-  build_one(in, tris, out.nodes_t, out.prims_t, out.n_nodes_t, out.depth_t);
+  build_tri_bvh(in, out.nodes_t, out.prims_t, out.n_nodes_t, out.depth_t);
+  build_scatter_grid(in, out);
 
   // per-triangle normal + media, vertex 0; per-scatterer centre + amplitude
   out.tri_nrm.assign(4 * (size_t)nt, 0.0f);

@@ -17,12 +17,17 @@ struct HostSceneIn {
 };
 
 struct HostSceneOut {
-  int n_nodes = 0, depth = 0;      // BVH over triangles and scatterers (closest hits)
-  std::vector<float> nodes;        // 16 floats per node
-  std::vector<float> prims;        // 12 floats per primitive, leaf order
-  int n_nodes_t = 0, depth_t = 0;  // BVH over triangles only (secondary-ray crossings)
-  std::vector<float> nodes_t;
-  std::vector<float> prims_t;
+  int n_nodes_t = 0, depth_t = 0;  // BVH over the triangles (closest hits, secondary-ray crossings)
+  std::vector<float> nodes_t;      // 16 floats per node
+  std::vector<float> prims_t;      // 12 floats per triangle, leaf order
+  // uniform grid over the scatterer spheres: cell (x, y, z) covers glo + h [x, x+1) x [y, y+1) x
+  // [z, z+1).  cell[(z * gn[1] + y) * gn[0] + x] = first << 8 | count names the (centre, code)
+  // entries of every sphere whose (slightly inflated) bounding box overlaps the cell:
+  // cell_sph[first .. first + count)
+  float glo[3] = {0, 0, 0}, gh = 1.0f;
+  int gn[3] = {0, 0, 0};
+  std::vector<uint32_t> cell;
+  std::vector<float> cell_sph;  // 4 floats per entry
   std::vector<float> tri_nrm;  // 4 per triangle
   std::vector<float> tri_v0;   // 4 per triangle
   std::vector<float> scat;     // 4 per scatterer

@@ -89,17 +89,12 @@ __device__ __forceinline__ void xdcr_test(const Acq& q, float3 o, float3 w, floa
 __device__ __forceinline__ void leaf_closest(const SceneDev& S, int first, int count, float3 o, float3 w,
                                              uint32_t prev, float& tbest, uint32_t& cbest) {
   for (int i = first; i < first + count; ++i) {
-    const float4 A = __ldg(&S.prims[3 * i]);
+    const float4 A = __ldg(&S.prims_t[3 * i]);
     const uint32_t code = __float_as_uint(A.w);
     if (code == prev) continue;
-    float t;
-    if (code_cls(code) == CLS_TRI) {
-      const float4 B = __ldg(&S.prims[3 * i + 1]);
-      const float4 C = __ldg(&S.prims[3 * i + 2]);
-      t = tri_test(o, w, xyz(A), xyz(B), xyz(C));
-    } else {
-      t = scat_test(o, w, xyz(A), S.rs2);
-    }
+    const float4 B = __ldg(&S.prims_t[3 * i + 1]);
+    const float4 C = __ldg(&S.prims_t[3 * i + 2]);
+    const float t = tri_test(o, w, xyz(A), xyz(B), xyz(C));
     if (t > 0.0f && hit_better(t, code, tbest, cbest)) {
       tbest = t;
       cbest = code;
@@ -107,92 +102,68 @@ __device__ __forceinline__ void leaf_closest(const SceneDev& S, int first, int c
   }
 }
 
-// closest-hit traversal as a resumable state machine: trav_init sets a ray up (transducer face
-// tested first), every trav_step visits one BVH node (testing the primitives of leaf children)
-// and returns false once the traversal is complete.  Nearer child first; the far child is
-// pushed with its entry distance so that it is skipped if a closer hit has been found since.
-struct Trav {
-  float3 o, w;
-  RayInv r;
-  uint32_t prev;
-  float tbest;
-  uint32_t cbest;
-  int node, sp;
-  float node_t;
-};
-
-__device__ __forceinline__ void trav_init(const Acq& q, float3 o, float3 w, uint32_t prev, Trav& T) {
-  T.o = o;
-  T.w = w;
-  T.prev = prev;
-  T.tbest = 3.0e38f;
-  T.cbest = 0xFFFFFFFFu;
-  xdcr_test(q, o, w, T.tbest, T.cbest);
-  T.r = ray_inv(o, w);
-  T.node = 0;
-  T.node_t = 0.0f;
-  T.sp = 0;
-}
-
-__device__ __forceinline__ bool trav_step(const SceneDev& S, Trav& T, int* stack, float* stt) {
-  if (T.node_t <= T.tbest) {
-    const float4 n0 = __ldg(&S.nodes[4 * T.node]);
-    const float4 n1 = __ldg(&S.nodes[4 * T.node + 1]);
-    const float4 n2 = __ldg(&S.nodes[4 * T.node + 2]);
-    const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes[4 * T.node + 3]));
-    bool h0, h1;
-    float t0, t1;
-    node_boxes(T.r, n0, n1, n2, T.tbest, h0, h1, t0, t1);
-    if (h0 && n3.z > 0) {
-      leaf_closest(S, n3.x, n3.z, T.o, T.w, T.prev, T.tbest, T.cbest);
-      h0 = false;
-    }
-    if (h1 && n3.w > 0) {
-      leaf_closest(S, n3.y, n3.w, T.o, T.w, T.prev, T.tbest, T.cbest);
-      h1 = false;
-    }
-    h0 = h0 && n3.x >= 0;
-    h1 = h1 && n3.y >= 0;
-    if (h0 && h1) {
-      const bool first0 = t0 <= t1;
-      if (T.sp < BVH_STACK) {
-        stack[T.sp] = first0 ? n3.y : n3.x;
-        stt[T.sp] = first0 ? t1 : t0;
-        ++T.sp;
-      }
-      T.node = first0 ? n3.x : n3.y;
-      T.node_t = first0 ? t0 : t1;
-      return true;
-    }
-    if (h0 || h1) {
-      T.node = h0 ? n3.x : n3.y;
-      T.node_t = h0 ? t0 : t1;
-      return true;
-    }
-  }
-  if (T.sp == 0) return false;
-  --T.sp;
-  T.node = stack[T.sp];
-  T.node_t = stt[T.sp];
-  return true;
-}
-
-__device__ __forceinline__ uint32_t trav_result(const Trav& T) {
-  return T.cbest == 0xFFFFFFFFu ? prim_code(CLS_NONE, 0) : T.cbest;
-}
-
-// closest hit over the transducer, triangles and scatterers, excluding the primitive `prev`
-// the ray leaves from.  cbest = prim_code(CLS_NONE, 0) when the ray escapes.
-__device__ __forceinline__ void closest_hit(const SceneDev& S, const Acq& q, float3 o, float3 w, uint32_t prev,
-                                            float& tbest, uint32_t& cbest) {
-  Trav T;
+// closest triangle hit: BVH2 traversal, nearer child first; the far child is pushed with its
+// entry distance and skipped once a closer hit has been found
+__device__ __forceinline__ void tri_closest(const SceneDev& S, float3 o, float3 w, uint32_t prev, float& tbest,
+                                            uint32_t& cbest) {
+  const RayInv r = ray_inv(o, w);
   int stack[BVH_STACK];
   float stt[BVH_STACK];
-  trav_init(q, o, w, prev, T);
-  while (trav_step(S, T, stack, stt)) {
+  int sp = 0, node = 0;
+  float node_t = 0.0f;
+  while (true) {
+    if (node_t <= tbest) {
+      const float4 n0 = __ldg(&S.nodes_t[4 * node]);
+      const float4 n1 = __ldg(&S.nodes_t[4 * node + 1]);
+      const float4 n2 = __ldg(&S.nodes_t[4 * node + 2]);
+      const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes_t[4 * node + 3]));
+      bool h0, h1;
+      float t0, t1;
+      node_boxes(r, n0, n1, n2, tbest, h0, h1, t0, t1);
+      if (h0 && n3.z > 0) {
+        leaf_closest(S, n3.x, n3.z, o, w, prev, tbest, cbest);
+        h0 = false;
+      }
+      if (h1 && n3.w > 0) {
+        leaf_closest(S, n3.y, n3.w, o, w, prev, tbest, cbest);
+        h1 = false;
+      }
+      h0 = h0 && n3.x >= 0;
+      h1 = h1 && n3.y >= 0;
+      if (h0 && h1) {
+        const bool first0 = t0 <= t1;
+        if (sp < BVH_STACK) {
+          stack[sp] = first0 ? n3.y : n3.x;
+          stt[sp] = first0 ? t1 : t0;
+          ++sp;
+        }
+        node = first0 ? n3.x : n3.y;
+        node_t = first0 ? t0 : t1;
+        continue;
+      }
+      if (h0 || h1) {
+        node = h0 ? n3.x : n3.y;
+        node_t = h0 ? t0 : t1;
+        continue;
+      }
+    }
+    if (sp == 0) break;
+    --sp;
+    node = stack[sp];
+    node_t = stt[sp];
   }
-  tbest = T.tbest;
-  cbest = trav_result(T);
+}
+
+// closest hit over the transducer face and the triangles, excluding the primitive `prev` the
+// ray leaves from; cbest = 0xFFFFFFFF when there is none.  The scatterers are searched after
+// it (grid march) below the distance found here; the order (t, class, id) decides ties, so the
+// result is the closest hit over the union whichever structure reports a candidate first.
+__device__ __forceinline__ void surface_hit(const SceneDev& S, const Acq& q, float3 o, float3 w, uint32_t prev,
+                                            float& tbest, uint32_t& cbest) {
+  tbest = 3.0e38f;
+  cbest = 0xFFFFFFFFu;
+  xdcr_test(q, o, w, tbest, cbest);
+  tri_closest(S, o, w, prev, tbest, cbest);
 }
 
 // all triangle crossings T_MIN < t < tmax of the segment o + t d (secondary rays; triangle-only

@@ -59,10 +59,10 @@ __global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long pat
 }
 
 // ------------------------------------------------------------------------------------------
-// Closest-hit traversal of every live path (one ray per thread, grid-stride).  The lanes of a
-// warp start their rays at the root together, so the upper levels of the BVH are fetched once
-// per warp; a variant that refilled each lane as soon as its ray finished was measured slower
-// (lanes at different depths lose that sharing).
+// Closest surface hit (transducer face, triangle BVH) of every live path, one ray per thread,
+// grid-stride.  The lanes of a warp start their rays at the root together, so the upper levels
+// of the BVH are fetched once per warp.  The scatterers are searched next by k_march below the
+// distance written here.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
   if (blockIdx.x == 0 && threadIdx.x == 0)  // secondary jobs of this round follow the previous rounds'
@@ -74,8 +74,148 @@ __global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
     const uint32_t prev = A.qin.meta[i].y;
     float t;
     uint32_t c;
-    closest_hit(A.S, A.acq, xyz(pa), xyz(wt), prev, t, c);
-    A.hits[i] = make_float2(t, __uint_as_float(c));
+    surface_hit(A.S, A.acq, xyz(pa), xyz(wt), prev, t, c);
+    A.hits[i] = make_float2(t, __uint_as_float(c == 0xFFFFFFFFu ? prim_code(CLS_NONE, 0) : c));
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Closest scatterer event of every live path before its surface hit: a 3D DDA through the
+// uniform sphere grid, cells in the order the ray crosses them.  Every sphere whose
+// closest-approach point lies on the ray at parameter t is listed in the cell holding that
+// point, and that cell is entered at a parameter <= t, so a ray stops at the first cell it
+// would enter beyond its best hit.  Cell faces are computed from the grid origin at every step
+// (no accumulated increments).
+//
+// Path lengths to the first event are spread roughly exponentially, so with one ray per thread
+// a warp would run as long as its longest ray with most lanes idle.  Instead every loop
+// iteration does one unit of work per lane (one sphere test, or one step to the next cell and
+// the read of its word), and a lane whose ray has finished takes the next ray from a pool the
+// warp claims in chunks of MARCH_CHUNK consecutive (coherence-sorted) queue slots.
+// ------------------------------------------------------------------------------------------
+constexpr int MARCH_CHUNK = 64;
+
+__global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
+  const SceneDev& S = A.S;
+  const uint32_t n = A.cnt->live[A.k];
+  if (S.n_scat == 0 || n == 0) return;
+  uint32_t* claim = &A.cnt->march[A.k];
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
+  const float h = S.gh, inv_h = 1.0f / h;
+  const float3 lo = S.glo;
+  const int nx = S.gnx, ny = S.gny, nz = S.gnz;
+  const int dy = nx, dz = nx * ny;
+  // lane state
+  uint32_t ray = 0xFFFFFFFFu;  // queue slot of the current ray; none when 0xFFFFFFFF
+  float3 o = f3(0.0f, 0.0f, 0.0f), w = o;
+  float ix = 0.0f, iy = 0.0f, iz = 0.0f, tnx = 0.0f, tny = 0.0f, tnz = 0.0f, tbest = 0.0f;
+  uint32_t prev = 0u, cbest = 0u, code0 = 0u, e = 0u, e_end = 0u;
+  int cx = 0, cy = 0, cz = 0, idx = 0, sx = 1, sy = 1, sz = 1, ux = 0, uy = 0, uz = 0;
+  uint32_t pool = 0u, pool_end = 0u;  // warp-uniform
+  bool exhausted = false;             // warp-uniform
+  while (true) {
+    // hand the pool's rays to idle lanes; rays that miss the grid leave their lane idle
+    uint32_t idle = __ballot_sync(0xFFFFFFFFu, ray == 0xFFFFFFFFu);
+    while (idle && !exhausted) {
+      if (pool == pool_end) {
+        uint32_t b = 0u;
+        if (lane == 0) b = atomicAdd(claim, (uint32_t)MARCH_CHUNK);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (b >= n) {
+          exhausted = true;
+          break;
+        }
+        pool = b;
+        pool_end = min(b + (uint32_t)MARCH_CHUNK, n);
+      }
+      const uint32_t take = min((uint32_t)__popc(idle), pool_end - pool);
+      const uint32_t rank = __popc(idle & below);
+      if (((idle >> lane) & 1u) && rank < take) {
+        ray = pool + rank;
+        const float4 pa = A.qin.pa[ray];
+        const float4 wt = A.qin.wt[ray];
+        const float2 hit = A.hits[ray];
+        o = xyz(pa);
+        w = xyz(wt);
+        prev = A.qin.meta[ray].y;
+        tbest = hit.x;
+        cbest = code0 = __float_as_uint(hit.y);
+        ix = safe_inv(w.x);
+        iy = safe_inv(w.y);
+        iz = safe_inv(w.z);
+        const float ax = (lo.x - o.x) * ix, bx = (fmaf((float)nx, h, lo.x) - o.x) * ix;
+        const float ay = (lo.y - o.y) * iy, by = (fmaf((float)ny, h, lo.y) - o.y) * iy;
+        const float az = (lo.z - o.z) * iz, bz = (fmaf((float)nz, h, lo.z) - o.z) * iz;
+        const float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
+        const float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tbest));
+        if (t0 > t1) {
+          ray = 0xFFFFFFFFu;  // misses the grid before its surface hit: nothing to do
+        } else {
+          cx = min(nx - 1, max(0, (int)floorf((fmaf(w.x, t0, o.x) - lo.x) * inv_h)));
+          cy = min(ny - 1, max(0, (int)floorf((fmaf(w.y, t0, o.y) - lo.y) * inv_h)));
+          cz = min(nz - 1, max(0, (int)floorf((fmaf(w.z, t0, o.z) - lo.z) * inv_h)));
+          sx = w.x > 0.0f ? 1 : -1;
+          sy = w.y > 0.0f ? 1 : -1;
+          sz = w.z > 0.0f ? 1 : -1;
+          ux = w.x > 0.0f;
+          uy = w.y > 0.0f;
+          uz = w.z > 0.0f;
+          tnx = w.x == 0.0f ? 3.0e38f : (fmaf((float)(cx + ux), h, lo.x) - o.x) * ix;
+          tny = w.y == 0.0f ? 3.0e38f : (fmaf((float)(cy + uy), h, lo.y) - o.y) * iy;
+          tnz = w.z == 0.0f ? 3.0e38f : (fmaf((float)(cz + uz), h, lo.z) - o.z) * iz;
+          idx = (cz * ny + cy) * nx + cx;
+          const uint32_t word = __ldg(&S.cell[idx]);
+          e = word >> 8;
+          e_end = e + (word & 0xFFu);
+        }
+      }
+      pool += take;
+      idle = __ballot_sync(0xFFFFFFFFu, ray == 0xFFFFFFFFu);
+    }
+    if (__all_sync(0xFFFFFFFFu, ray == 0xFFFFFFFFu)) break;  // pool exhausted, every lane idle
+    if (ray == 0xFFFFFFFFu) continue;
+    if (e < e_end) {  // one sphere of the current cell
+      const float4 sp = __ldg(&S.cell_sph[e]);
+      ++e;
+      const uint32_t code = __float_as_uint(sp.w);
+      const float t = code == prev ? -1.0f : scat_test(o, w, xyz(sp), S.rs2);
+      if (t > 0.0f && hit_better(t, code, tbest, cbest)) {
+        tbest = t;
+        cbest = code;
+      }
+      continue;
+    }
+    // the current cell is done: step to the next one, or finish the ray
+    float tn;
+    bool inside;
+    if (tnx <= tny && tnx <= tnz) {
+      tn = tnx;
+      cx += sx;
+      idx += sx;
+      inside = (unsigned)cx < (unsigned)nx;
+      tnx = (fmaf((float)(cx + ux), h, lo.x) - o.x) * ix;
+    } else if (tny <= tnz) {
+      tn = tny;
+      cy += sy;
+      idx += sy * dy;
+      inside = (unsigned)cy < (unsigned)ny;
+      tny = (fmaf((float)(cy + uy), h, lo.y) - o.y) * iy;
+    } else {
+      tn = tnz;
+      cz += sz;
+      idx += sz * dz;
+      inside = (unsigned)cz < (unsigned)nz;
+      tnz = (fmaf((float)(cz + uz), h, lo.z) - o.z) * iz;
+    }
+    if (inside && tn <= tbest) {
+      const uint32_t word = __ldg(&S.cell[idx]);
+      e = word >> 8;
+      e_end = e + (word & 0xFFu);
+    } else {
+      if (cbest != code0) A.hits[ray] = make_float2(tbest, __uint_as_float(cbest));
+      ray = 0xFFFFFFFFu;
+    }
   }
 }
 
@@ -380,6 +520,12 @@ void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int gr
   k_generate<<<grid, 256, 0, st>>>(a, path0, n);
 }
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st) { k_traverse<<<grid, TRAV_THREADS, 0, st>>>(a); }
+void launch_march(const TransportArgs& a, int grid, cudaStream_t st) { k_march<<<grid, MARCH_THREADS, 0, st>>>(a); }
+int march_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_march, MARCH_THREADS, 0) != cudaSuccess || b < 1) b = 4;
+  return b;  // one wave of resident blocks: lanes refill from the pool until it is empty
+}
 int traverse_blocks_per_sm() {
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_traverse, TRAV_THREADS, 0) != cudaSuccess || b < 1) b = 4;

@@ -25,6 +25,7 @@ struct Counters {
   uint32_t live[MAX_KMAX + 2];  // paths entering segment k
   uint32_t nee[MAX_KMAX + 2];   // secondary jobs produced at segment k
   uint32_t nee_off[MAX_KMAX + 2]; // first job of round k in the job buffer
+  uint32_t march[MAX_KMAX + 2]; // queue slots claimed by the scatterer march of round k
   uint32_t n_arr;               // arrivals appended
   uint32_t dropped;             // arrivals dropped (crossing list overflow)
   int status;                   // ST_* bits
@@ -75,6 +76,9 @@ void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int gr
 constexpr int TRAV_THREADS = 128;
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st);
 int traverse_blocks_per_sm();  // blocks per SM of the traversal grid
+constexpr int MARCH_THREADS = 256;
+void launch_march(const TransportArgs& a, int grid, cudaStream_t st);
+int march_blocks_per_sm();  // resident blocks per SM of the scatterer march (persistent grid)
 void launch_interact(const TransportArgs& a, int grid, cudaStream_t st);
 void launch_nee(const TransportArgs& a, int grid, cudaStream_t st);
 

@@ -71,16 +71,21 @@ struct Img {
   float x0, x1, z0, z1, dr, l1, l2;
 };
 
-// device-resident scene (BVH2 nodes of 4 float4; primitives in leaf order, 3 float4 each)
+// device-resident scene: triangle BVH2 (nodes of 4 float4, triangles in leaf order, 3 float4
+// each) and the uniform grid over the scatterer spheres
 struct SceneDev {
-  const float4* nodes;   // n0=(c0.lo.x,c0.hi.x,c0.lo.y,c0.hi.y) n1=(same for c1) n2=(c0 z, c1 z) n3=int4
-  const float4* prims;   // triangle: (v0, code) (e1, -) (e2, -); scatterer: (p, code) (-) (-)
-  const float4* tri_nrm; // by triangle id: (unit normal, bits(m_front | m_back << 16))
-  const float4* tri_v0;  // by triangle id: (v0, 0)
-  const float4* scat;    // by scatterer id: (p, amplitude)
-  const float4* nodes_t; // triangle-only BVH (secondary rays)
-  const float4* prims_t;
-  int n_nodes, n_tris, n_scat;
+  const float4* tri_nrm;     // by triangle id: (unit normal, bits(m_front | m_back << 16))
+  const float4* tri_v0;      // by triangle id: (v0, 0)
+  const float4* scat;        // by scatterer id: (p, amplitude)
+  const float4* nodes_t;     // triangle BVH2: n0=(c0.lo.x,c0.hi.x,c0.lo.y,c0.hi.y) n1=(same, c1)
+                             // n2=(c0 z, c1 z) n3=int4(child0, child1, count0, count1)
+  const float4* prims_t;     // triangles in leaf order: (v0, code) (e1, -) (e2, -)
+  const uint32_t* cell;        // scatterer grid, per cell (z * gny + y) * gnx + x: first entry << 8 | count
+  const float4* cell_sph;      // per (cell, sphere): (centre, bits(code))
+  float3 glo;                  // grid origin and cell edge
+  float gh;
+  int gnx, gny, gnz;
+  int n_tris, n_scat;
   float rs2;
 };
 
