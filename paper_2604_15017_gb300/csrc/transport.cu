@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
 //
 // Path lengths to the first event are spread roughly exponentially, so with one ray per thread
 // a warp would run as long as its longest ray with most lanes idle.  Instead every loop
-// iteration does one unit of work per lane (one sphere test, or one step to the next cell and
-// the read of its word), and a lane whose ray has finished takes the next ray from a pool the
-// warp claims in chunks of MARCH_CHUNK consecutive (coherence-sorted) queue slots.
+// iteration does one unit of work per lane (one sphere test, then, once the cell has no sphere
+// left, one step to the next cell and the read of its word), and a lane whose ray has finished
+// takes the next ray from a pool the warp claims in chunks of MARCH_CHUNK consecutive
+// (coherence-sorted) queue slots.  A sphere listed in two consecutive cells is tested once.
 // ------------------------------------------------------------------------------------------
 constexpr int MARCH_CHUNK = 64;
 
@@ -110,8 +111,37 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
   uint32_t ray = 0xFFFFFFFFu;  // queue slot of the current ray; none when 0xFFFFFFFF
   float3 o = f3(0.0f, 0.0f, 0.0f), w = o;
   float ix = 0.0f, iy = 0.0f, iz = 0.0f, tnx = 0.0f, tny = 0.0f, tnz = 0.0f, tbest = 0.0f;
-  uint32_t prev = 0u, cbest = 0u, code0 = 0u, e = 0u, e_end = 0u;
+  uint32_t prev = 0u, cbest = 0u, code0 = 0u, last = 0xFFFFFFFFu, e = 0u, e_end = 0u;
   int cx = 0, cy = 0, cz = 0, idx = 0, sx = 1, sy = 1, sz = 1, ux = 0, uy = 0, uz = 0;
+  // the DDA runs one cell ahead of the cell whose spheres are being tested: (cx, cy, cz, idx)
+  // is the next cell, entered at t_ahead, and its word is read as soon as the DDA gets there,
+  // so the read has a whole iteration (or more) to arrive.  It is read only while t_ahead <=
+  // tbest; tbest only decreases, so a word not read is a word never needed.
+  float t_ahead = 0.0f;
+  bool ahead_ok = false;
+  uint32_t word_ahead = 0u;
+  auto step_ahead = [&]() {
+    if (tnx <= tny && tnx <= tnz) {
+      t_ahead = tnx;
+      cx += sx;
+      idx += sx;
+      ahead_ok = (unsigned)cx < (unsigned)nx;
+      tnx = (fmaf((float)(cx + ux), h, lo.x) - o.x) * ix;
+    } else if (tny <= tnz) {
+      t_ahead = tny;
+      cy += sy;
+      idx += sy * dy;
+      ahead_ok = (unsigned)cy < (unsigned)ny;
+      tny = (fmaf((float)(cy + uy), h, lo.y) - o.y) * iy;
+    } else {
+      t_ahead = tnz;
+      cz += sz;
+      idx += sz * dz;
+      ahead_ok = (unsigned)cz < (unsigned)nz;
+      tnz = (fmaf((float)(cz + uz), h, lo.z) - o.z) * iz;
+    }
+    word_ahead = ahead_ok && t_ahead <= tbest ? __ldg(&S.cell[idx]) : 0u;
+  };
   uint32_t pool = 0u, pool_end = 0u;  // warp-uniform
   bool exhausted = false;             // warp-uniform
   while (true) {
@@ -141,6 +171,7 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
         prev = A.qin.meta[ray].y;
         tbest = hit.x;
         cbest = code0 = __float_as_uint(hit.y);
+        last = 0xFFFFFFFFu;
         ix = safe_inv(w.x);
         iy = safe_inv(w.y);
         iz = safe_inv(w.z);
@@ -168,6 +199,7 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
           const uint32_t word = __ldg(&S.cell[idx]);
           e = word >> 8;
           e_end = e + (word & 0xFFu);
+          step_ahead();
         }
       }
       pool += take;
@@ -175,43 +207,23 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
     }
     if (__all_sync(0xFFFFFFFFu, ray == 0xFFFFFFFFu)) break;  // pool exhausted, every lane idle
     if (ray == 0xFFFFFFFFu) continue;
-    if (e < e_end) {  // one sphere of the current cell
+    if (e < e_end) {  // one sphere of the current cell (a sphere just tested in the previous cell is skipped)
       const float4 sp = __ldg(&S.cell_sph[e]);
       ++e;
       const uint32_t code = __float_as_uint(sp.w);
-      const float t = code == prev ? -1.0f : scat_test(o, w, xyz(sp), S.rs2);
+      const float t = code == prev || code == last ? -1.0f : scat_test(o, w, xyz(sp), S.rs2);
+      last = code;
       if (t > 0.0f && hit_better(t, code, tbest, cbest)) {
         tbest = t;
         cbest = code;
       }
-      continue;
+      if (e < e_end) continue;
     }
-    // the current cell is done: step to the next one, or finish the ray
-    float tn;
-    bool inside;
-    if (tnx <= tny && tnx <= tnz) {
-      tn = tnx;
-      cx += sx;
-      idx += sx;
-      inside = (unsigned)cx < (unsigned)nx;
-      tnx = (fmaf((float)(cx + ux), h, lo.x) - o.x) * ix;
-    } else if (tny <= tnz) {
-      tn = tny;
-      cy += sy;
-      idx += sy * dy;
-      inside = (unsigned)cy < (unsigned)ny;
-      tny = (fmaf((float)(cy + uy), h, lo.y) - o.y) * iy;
-    } else {
-      tn = tnz;
-      cz += sz;
-      idx += sz * dz;
-      inside = (unsigned)cz < (unsigned)nz;
-      tnz = (fmaf((float)(cz + uz), h, lo.z) - o.z) * iz;
-    }
-    if (inside && tn <= tbest) {
-      const uint32_t word = __ldg(&S.cell[idx]);
-      e = word >> 8;
-      e_end = e + (word & 0xFFu);
+    // the current cell is done: enter the next one (its word is already here), or finish the ray
+    if (ahead_ok && t_ahead <= tbest) {
+      e = word_ahead >> 8;
+      e_end = e + (word_ahead & 0xFFu);
+      step_ahead();
     } else {
       if (cbest != code0) A.hits[ray] = make_float2(tbest, __uint_as_float(cbest));
       ray = 0xFFFFFFFFu;

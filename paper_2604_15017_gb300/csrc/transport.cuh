@@ -76,7 +76,7 @@ void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int gr
 constexpr int TRAV_THREADS = 128;
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st);
 int traverse_blocks_per_sm();  // blocks per SM of the traversal grid
-constexpr int MARCH_THREADS = 256;
+constexpr int MARCH_THREADS = 128;
 void launch_march(const TransportArgs& a, int grid, cudaStream_t st);
 int march_blocks_per_sm();  // resident blocks per SM of the scatterer march (persistent grid)
 void launch_interact(const TransportArgs& a, int grid, cudaStream_t st);
