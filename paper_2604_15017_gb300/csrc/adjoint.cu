@@ -355,7 +355,30 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     const float4 sc = __ldg(&A.S.scat[jid]);
     float3 d;
     float D;
-    const NeeOut no = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
+    NeeOut no;
+    const uint2 xo = A.nres.xo ? A.nres.xo[i] : make_uint2(0u, NEE_UNSTORED);
+    if (xo.y == NEE_UNSTORED) {  // trace the secondary ray again
+      no = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
+    } else {  // the forward pass's result: same arithmetic, read back
+      no.ok = xo.y != NEE_NONE;
+      no.overflow = false;
+      no.n = no.ok ? (int)xo.y : 0;
+      if (no.ok) {
+        const float4 rs = A.nres.res[i];
+        nh = rs.x;
+        nl = rs.y;
+        no.gain = rs.z;
+        no.sum_al = rs.w;
+        for (int c = 0; c < no.n; ++c) {
+          const uint2 x = A.nres.xing[xo.x + c];
+          xt[c] = __uint_as_float(x.x);
+          xid[c] = x.y;
+        }
+        const float3 dv = f3(elem_x(q, e2), 0.0f, 0.0f) - xyz(sc);
+        D = sqrtf(dot3(dv, dv));
+        d = dv * (1.0f / D);
+      }
+    }
     if (!no.ok) {
       *seed = make_float2(0.0f, 0.0f);
       continue;

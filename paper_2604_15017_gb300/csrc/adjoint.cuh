@@ -26,6 +26,7 @@ struct AdjArgs {
   int P;
   int accumulate;          // add into gpart instead of overwriting
   NeeQ nee;                // the pass's secondary-ray jobs
+  NeeRes nres;             // their stored results (null members: trace them again)
   const Counters* cnt;     // job counts per round
   float2* seeds;           // per (path - path_base, k): (dL/da, dL/dtau) seeded by secondary rays
   const uint32_t* active;  // paths with an arrival, grouped by event count

@@ -28,7 +28,7 @@ enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
-  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_COUNT
+  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_COUNT
 };
 
 struct SceneGPU {
@@ -387,6 +387,14 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     CKS(ws(ctx, W_JOBU_JOB, jobs, st, &unsorted.job));
     CKS(ws(ctx, W_JOBU_JM, jobs, st, &unsorted.jm));
     CKS(ws(ctx, W_JOBU_PATH, jobs, st, &unsorted.jpath));
+  }
+  if (record && do_nee && sc->dev.n_scat > 0) {
+    // secondary-ray results kept for the adjoint; crossings beyond the buffer are traced again
+    CKS(ws(ctx, W_NEE_RES, jobs, st, &A.nres.res));
+    CKS(ws(ctx, W_NEE_XO, jobs, st, &A.nres.xo));
+    const size_t xcap = std::min<size_t>(2 * jobs, 0xFFFFFFF0u);
+    CKS(ws(ctx, W_XING, xcap, st, &A.nres.xing));
+    A.nres.xcap = (uint32_t)xcap;
   }
   A.arr = arr;
   A.arr_cap = arr_cap;
@@ -976,6 +984,13 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
     A.nee.job = (float4*)ctx->L->ws[W_NEE_JOB].p;
     A.nee.jm = (uint32_t*)ctx->L->ws[W_NEE_JM].p;
     A.nee.jpath = (uint32_t*)ctx->L->ws[W_NEE_PATH].p;
+    if (rec == (const uint32_t*)ctx->L->record.p) {  // a recorded pass kept its secondary-ray results
+      A.nres.res = (float4*)ctx->L->ws[W_NEE_RES].p;
+      A.nres.xo = (uint2*)ctx->L->ws[W_NEE_XO].p;
+      A.nres.xing = (uint2*)ctx->L->ws[W_XING].p;
+    } else {
+      A.nres = NeeRes{};
+    }
     A.cnt = cnt;
     CKS(ws(ctx, W_SEEDS, (size_t)n * K1, st, &A.seeds));
     CKS(ws(ctx, W_ACTIVE, (size_t)n + 1, st, &active));
@@ -1102,7 +1117,8 @@ int us_request_bytes(us_ctx* ctx, const us_request* req, size_t* bytes) {
   CKS(make_acq(ctx, req->acq, 0, q));
   const size_t n = (size_t)(q.rays_per_tx * q.ntx), K1 = q.kmax + 1, jobs = n * std::max(1, q.kmax);
   size_t b = n * (2 * 48 + 8 + 4) + jobs * 2 * 24 + n * K1 * 16 * 2;  // queues, hits, keys, jobs, arrivals
-  if (req->bref_dev) b += n * K1 * (4 + 8) + n * 4;                    // record, seeds, active list
+  if (req->bref_dev) b += n * K1 * (4 + 8) + n * 4 + jobs * (16 + 8 + 16);  // record, seeds, active list,
+                                                                               // secondary-ray results
   if (req->img) b += (size_t)req->img->n_lines * req->img->n_depth * 4 * 5;
   b += (size_t)q.ntx * q.ne * q.ns * 4;                                 // dL/dRF
   *bytes = b;

@@ -5,6 +5,7 @@
 // capturable in a CUDA graph).  Live paths are compacted after every interaction with
 // warp-aggregated appends (one atomic per coalesced group).
 #include <cooperative_groups.h>
+#include <cooperative_groups/scan.h>
 
 #include "bvh_query.cuh"
 #include "splat.cuh"
@@ -351,6 +352,24 @@ __global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
     const float4 sc = __ldg(&A.S.scat[j]);
     float th = job.y, tl = job.z;
     const NeeOut r = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, th, tl, xt, xid, nullptr, nullptr);
+    if (A.nres.res) {  // keep the result for the adjoint
+      uint2 xo = make_uint2(0u, NEE_NONE);
+      if (r.ok) {
+        cg::coalesced_group g = cg::coalesced_threads();
+        const uint32_t before = cg::exclusive_scan(g, (uint32_t)r.n);
+        unsigned long long base = 0ull;
+        if (g.thread_rank() == g.size() - 1) base = atomicAdd(&A.cnt->n_xing, (unsigned long long)(before + r.n));
+        base = g.shfl(base, g.size() - 1) + before;
+        if (base + (unsigned)r.n <= A.nres.xcap) {
+          for (int c = 0; c < r.n; ++c) A.nres.xing[base + c] = make_uint2(__float_as_uint(xt[c]), xid[c]);
+          xo = make_uint2((uint32_t)base, (uint32_t)r.n);
+        } else {
+          xo = make_uint2(0u, NEE_UNSTORED);
+        }
+        A.nres.res[i] = make_float4(th, tl, r.gain, r.sum_al);
+      }
+      A.nres.xo[i] = xo;
+    }
     if (r.overflow) {
       atomicOr(&A.cnt->status, ST_OVERFLOW);
       atomicAdd(&A.cnt->dropped, 1u);

@@ -20,12 +20,27 @@ struct NeeQ {
   uint32_t* jpath;  // path id
 };
 
+// what the secondary-ray kernel found for each job, kept for the adjoint of a recorded pass so
+// that it need not trace the secondary rays again: per job slot, res = (bits(t_hi), bits(t_lo)
+// at the element, gain, sum alpha l) and xo = (first crossing, count), count NEE_NONE for a job
+// with no contribution and NEE_UNSTORED when the crossing buffer was full (the adjoint then
+// traces that job again); crossings (bits(t), triangle id) in order along the ray.
+constexpr uint32_t NEE_NONE = 0xFFFFFFFFu;
+constexpr uint32_t NEE_UNSTORED = 0xFFFFFFFEu;
+struct NeeRes {
+  float4* res;
+  uint2* xo;
+  uint2* xing;
+  uint32_t xcap;
+};
+
 // device counters of one transport pass
 struct Counters {
   uint32_t live[MAX_KMAX + 2];  // paths entering segment k
   uint32_t nee[MAX_KMAX + 2];   // secondary jobs produced at segment k
   uint32_t nee_off[MAX_KMAX + 2]; // first job of round k in the job buffer
   uint32_t march[MAX_KMAX + 2]; // queue slots claimed by the scatterer march of round k
+  unsigned long long n_xing;    // secondary-ray crossings appended (NeeRes; may pass xcap)
   uint32_t n_arr;               // arrivals appended
   uint32_t dropped;             // arrivals dropped (crossing list overflow)
   int status;                   // ST_* bits
@@ -42,6 +57,7 @@ struct TransportArgs {
   PathQ qin, qout;
   float2* hits;       // (t, bits(code)) per queue slot
   NeeQ nee;
+  NeeRes nres;        // null members unless the pass is recorded for the adjoint
   Arrival* arr;       // may be null (adjoint recompute: no arrivals)
   uint32_t arr_cap;
   uint32_t* record;   // may be null; index (path - path_base) * (kmax + 1) + k

@@ -329,13 +329,16 @@ def test_transport_vjp_matches_oracle_gradient(ctx, mode):
     ctx.release_scene(sid)
 
 
-def test_transport_vjp_inclusions(ctx):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_transport_vjp_inclusions(ctx, mode):
+    """Record mode reads the forward pass's secondary-ray crossings back; recompute mode traces
+    them again: both against the oracle on a scene whose secondary rays cross interfaces."""
     w = small_inclusions(n_rays=300, k_max=5, n_tx=1)
     sid, rf, b, ref = forward_pair(ctx, w)
     rng = np.random.default_rng(15)
     grf = rng.normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
     g_ref = ref["run"].gradient(grf)
-    g = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=0).double().cpu().numpy()
+    g = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode).double().cpu().numpy()
     scale = np.abs(g_ref * w["theta"])
     err = np.abs(g - g_ref) * np.abs(w["theta"])
     assert np.all(err <= 1e-3 * scale + 1e-4 * scale.max()), np.c_[g, g_ref]
