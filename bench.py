@@ -142,12 +142,12 @@ def stage_work(stage, w, stats, n_prims):
     return "hbm", 8 * img["n_lines"] * img["n_depth"]
 
 
-def profile_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary of `kernel`, or None when the
-    kernel's sources changed since the capture (the summary records their hash)."""
+def profile_traffic(name):
+    """DRAM bytes per launch from the committed ncu summary `profiles/<name>.md`, or None when
+    the kernels' sources changed since the capture (the summary records their hash)."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", kernel + ".md")
+    path = os.path.join(ROOT, "profiles", name + ".md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -479,10 +479,11 @@ def main():
         achieved = work / (dom_ms * 1e-3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
         unit = "GB/s"
-    kernel_of = {"traverse": "k_traverse", "path_adj": "k_path_adjoint", "nee": "k_nee", "das": "k_das",
+    kernel_of = {"traverse": "k_traverse+k_march", "path_adj": "k_path_adjoint", "nee": "k_nee", "das": "k_das",
                  "splat_rows": "k_row_splat", "nee_adj": "k_nee_adjoint"}
+    kern = kernel_of.get(dom, dom)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": profile_traffic(kernel_of.get(dom, dom)), "kernel": kernel_of.get(dom, dom),
+                "traffic": profile_traffic(kern.replace("+", "_") + "_inclusions"), "kernel": kern,
                 "stage_ms_per_step": dom_ms, "launches_per_step": dom_launches,
                 "work_per_step": work, "peak_source": "measured" if bound == "hbm" else
                 "derived: SMs x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)"}
