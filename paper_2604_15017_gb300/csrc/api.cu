@@ -338,6 +338,7 @@ SceneGPU* get_scene(us_ctx* ctx, uint64_t id) {
 
 int set_attrs(us_ctx* ctx) {
   SplatGeom g;
+  g.ns = MAX_SPLAT_NS;
   g.nbins = MAX_SPLAT_NS + 2 * HALO;
   g.ntaps = MAX_TAPS;
   CK(splat_set_attrs(g));

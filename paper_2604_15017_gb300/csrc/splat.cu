@@ -146,14 +146,19 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_splat(SplatGeom g, const ui
                                                            uint2* scratch, const float* Gtab, float* rf) {
   extern __shared__ float smf[];
   const int row = blockIdx.x;
-  const int NB = g.nbins;        // bins -HALO .. ns + HALO - 1
-  float* M = smf;                // [K_MOM][NB]
-  uint32_t* hist = reinterpret_cast<uint32_t*>(M + K_MOM * NB);  // [NB + 1]
-  float* G = reinterpret_cast<float*>(hist + NB + 1);            // [K_MOM][ntaps]
+  const int NB = g.nbins;         // bins -HALO .. ns + HALO - 1
+  const int MS = row_mom_stride(g.ns);
+  const int sh = row_mom_shift(g);  // bin x is stored at mom_slot(x + sh)
+  float* M = smf;                 // [K_MOM][MS], padded: one spare slot after every 8
+  uint32_t* hist = reinterpret_cast<uint32_t*>(M + K_MOM * MS);  // [NB + 1]
+  float* G = reinterpret_cast<float*>(hist + NB + 1);            // [K_MOM][MAX_TAPS], zero past ntaps
   const uint32_t a0 = off[row], a1 = off[row + 1];
-  for (int i = threadIdx.x; i < K_MOM * NB; i += blockDim.x) M[i] = 0.0f;
+  for (int i = threadIdx.x; i < K_MOM * MS; i += blockDim.x) M[i] = 0.0f;
   for (int i = threadIdx.x; i <= NB; i += blockDim.x) hist[i] = 0;
-  for (int i = threadIdx.x; i < K_MOM * g.ntaps; i += blockDim.x) G[i] = Gtab[i];
+  for (int i = threadIdx.x; i < K_MOM * MAX_TAPS; i += blockDim.x) {
+    const int j = i / MAX_TAPS, d = i - j * MAX_TAPS;
+    G[i] = d < g.ntaps ? Gtab[j * g.ntaps + d] : 0.0f;
+  }
   __syncthreads();
   const uint32_t mask = (1u << TQ_FRAC) - 1u;
   // pass 1: histogram of bins
@@ -230,34 +235,48 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_splat(SplatGeom g, const ui
     const bool tail = (b >= 0) && (lane == 31 || bn != b);
     if (tail) {
 #pragma unroll
-      for (int j = 0; j < K_MOM; ++j) atomicAdd(&M[j * NB + b], m[j]);
+      for (int j = 0; j < K_MOM; ++j) atomicAdd(&M[j * MS + mom_slot(b + sh)], m[j]);
     }
   }
   __syncthreads();
-  // convolution: each thread produces R consecutive samples of the row
-  const int ns = g.ns;
-  const int R = (ns + blockDim.x - 1) / blockDim.x;
-  const int n0 = threadIdx.x * R;
-  const int Rv = max(0, min(R, ns - n0));
-  float acc[ROW_MAX_R];
+  // convolution: each thread produces 8 consecutive samples n0 .. n0 + 7 of the row,
+  // out[n] = sum_j sum_d G_j[d] M_j[bin n - dlo - d].  Taps go in blocks of 8: the 15 moments a
+  // block touches are read once into registers (a sliding window) and feed 64 FMAs.  The
+  // shift sh puts every window start on a multiple of 8, so the padded slots of the window are
+  // fixed offsets and the lanes of a warp read addresses 9 apart: no bank conflicts.
+  const int n0 = 8 * threadIdx.x;
+  if (n0 < g.ns) {
+    float acc[8];
 #pragma unroll
-  for (int r = 0; r < ROW_MAX_R; ++r) acc[r] = 0.0f;
-  for (int j = 0; j < K_MOM; ++j) {
-    const float* Mj = M + j * NB;
-    const float* Gj = G + j * g.ntaps;
-    for (int d = 0; d < g.ntaps; ++d) {
-      const float gv = Gj[d];
-      // bin of sample n for tap d: n - (dlo + d); shifted by HALO
-      const int bb = n0 - (g.dlo + d) + HALO;
+    for (int r = 0; r < 8; ++r) acc[r] = 0.0f;
+    const int xs0 = n0 - g.dlo + HALO + sh - 7;  // window start for taps 0..7, a multiple of 8
+    const int ntp = (g.ntaps + 7) & ~7;
+    for (int j = 0; j < K_MOM; ++j) {
+      const float* Mj = M + j * MS;
+      const float* Gj = G + j * MAX_TAPS;
+      for (int d0 = 0; d0 < ntp; d0 += 8) {
+        const float* W = Mj + 9 * ((xs0 - d0) >> 3);
+        float w[15];
 #pragma unroll
-      for (int r = 0; r < ROW_MAX_R; ++r)
-        if (r < Rv) acc[r] = fmaf(gv, Mj[bb + r], acc[r]);
+        for (int k = 0; k < 15; ++k) w[k] = W[k + (k >= 8 ? 1 : 0)];
+#pragma unroll
+        for (int dd = 0; dd < 8; ++dd) {
+          const float gv = Gj[d0 + dd];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) acc[r] = fmaf(gv, w[r - dd + 7], acc[r]);
+        }
+      }
+    }
+    float* out = rf + (size_t)row * g.ns + n0;
+    if (n0 + 8 <= g.ns) {
+      reinterpret_cast<float4*>(out)[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      reinterpret_cast<float4*>(out)[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (n0 + r < g.ns) out[r] = acc[r];
     }
   }
-  float* out = rf + (size_t)row * ns;
-#pragma unroll
-  for (int r = 0; r < ROW_MAX_R; ++r)
-    if (r < Rv) out[n0 + r] = acc[r];
 }
 
 // standalone arrival list -> packed arrivals
@@ -276,9 +295,10 @@ __global__ void k_pack_arrivals(const int32_t* tx, const int32_t* e, const float
 
 // ------------------------------------------------------------------------------------------
 size_t row_splat_smem(const SplatGeom& g) {
-  return sizeof(float) * (size_t)K_MOM * g.nbins + sizeof(uint32_t) * (g.nbins + 1) +
-         sizeof(float) * (size_t)K_MOM * g.ntaps;
+  return sizeof(float) * (size_t)K_MOM * row_mom_stride(g.ns) + sizeof(uint32_t) * (g.nbins + 1) +
+         sizeof(float) * (size_t)K_MOM * MAX_TAPS;
 }
+int row_splat_threads(const SplatGeom& g) { return ((g.ns + 7) / 8 + 31) / 32 * 32; }
 
 void launch_pulse_table(const SplatGeom& g, float* G, cudaStream_t st) { k_pulse_table<<<1, 128, 0, st>>>(g, G); }
 
@@ -292,7 +312,7 @@ void launch_splat_sort(const SplatGeom& g, const Arrival* arr, const uint32_t* n
                                                                          w.bucket, nrows);
 }
 void launch_splat_rows(const SplatGeom& g, SplatWork w, const float* G, float* rf, cudaStream_t st) {
-  k_row_splat<<<g.nrows, ROW_THREADS, row_splat_smem(g), st>>>(g, w.bucket, w.row_off, w.scratch, G, rf);
+  k_row_splat<<<g.nrows, row_splat_threads(g), row_splat_smem(g), st>>>(g, w.bucket, w.row_off, w.scratch, G, rf);
 }
 
 void launch_pack_arrivals(const int32_t* tx, const int32_t* e, const float* tau, const float* a, long long n, int ne,

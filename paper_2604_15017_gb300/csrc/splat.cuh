@@ -18,6 +18,15 @@ struct SplatGeom {
   float Sig, Om;         // sigma * fs^2, 2 pi f0 / fs
 };
 
+// moments of a row live in shared memory with one spare slot after every 8 (slot of x: x + x/8),
+// bins shifted so that each thread's convolution window starts on a multiple of 8
+__host__ __device__ inline int mom_slot(int x) { return x + (x >> 3); }
+__host__ __device__ inline int row_mom_stride(int ns) {
+  const int xn = ns + 2 * HALO + 16;
+  return mom_slot(xn) + 8;
+}
+__host__ __device__ inline int row_mom_shift(const SplatGeom& g) { return (((g.dlo - HALO + 7) % 8) + 8) % 8; }
+
 struct SplatWork {
   uint32_t* row_cnt;     // [nrows]
   uint32_t* row_off;     // [nrows + 1]
@@ -27,6 +36,7 @@ struct SplatWork {
 };
 
 size_t row_splat_smem(const SplatGeom& g);
+int row_splat_threads(const SplatGeom& g);  // 8 output samples per thread
 void launch_pulse_table(const SplatGeom& g, float* G, cudaStream_t st);
 // row bucketing (3 kernels), then the per-row sort / reduction / convolution (1 kernel)
 void launch_splat_sort(const SplatGeom& g, const Arrival* arr, const uint32_t* n_arr, uint32_t cap, SplatWork w,
