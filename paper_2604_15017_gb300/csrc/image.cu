@@ -48,6 +48,23 @@ __device__ __forceinline__ ff das_urx(const Acq& q, const DasGeo& g, ff x, ff z,
 __device__ __forceinline__ float hann_w(int e, int ne) {
   return 0.5f * (1.0f - cospif(2.0f * (float)(e + 1) / (float)(ne + 1)));
 }
+// The transmit and receive delays of a pixel are each split once into whole samples and a
+// fraction in [0, 1) (exactly, from their float-float values); a tap then adds the two parts:
+// the one float addition of the fractions rounds by at most 2^-24 samples.
+__device__ __forceinline__ float2 das_split(ff u) {
+  int i;
+  float f;
+  ff_floor(u, i, f);
+  return make_float2(__int_as_float(i), f);
+}
+__device__ __forceinline__ void das_tap(float2 a, float2 b, int& i, float& f) {
+  f = __fadd_rn(a.y, b.y);
+  i = __float_as_int(a.x) + __float_as_int(b.x);
+  if (f >= 1.0f) {
+    f = __fsub_rn(f, 1.0f);  // exact on [1, 2)
+    ++i;
+  }
+}
 
 // DAS: one pixel per thread; transmit delays staged per pixel in shared memory, the receive
 // delay computed once per (pixel, element) and reused for every transmit; channel data read
@@ -63,20 +80,16 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das(Acq q, Img im, const float*
     const bool valid = p < npx;
     const int l = valid ? p / im.nd : 0, d = valid ? p - l * im.nd : 0;
     const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
-    for (int t = 0; t < q.ntx; ++t) {
-      const ff u = das_utx(q, g, x, z, t);
-      utx_s[t * DAS_THREADS + threadIdx.x] = make_float2(u.hi, u.lo);
-    }
+    for (int t = 0; t < q.ntx; ++t) utx_s[t * DAS_THREADS + threadIdx.x] = das_split(das_utx(q, g, x, z, t));
     float acc = 0.0f;
     if (valid) {
       for (int e = 0; e < q.ne; ++e) {
-        const ff ur = das_urx(q, g, x, z, e);
+        const float2 ur = das_split(das_urx(q, g, x, z, e));
         float s = 0.0f;
         for (int t = 0; t < q.ntx; ++t) {
-          const float2 ut = utx_s[t * DAS_THREADS + threadIdx.x];
           int i;
           float f;
-          ff_floor(ff_addx(ff{ut.x, ut.y}, ur), i, f);
+          das_tap(utx_s[t * DAS_THREADS + threadIdx.x], ur, i, f);
           const float* row = rf + ((size_t)t * q.ne + e) * q.ns;
           const float a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
           const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
@@ -196,10 +209,8 @@ __global__ void __launch_bounds__(DT_THREADS) k_das_tma(Acq q, Img im, const flo
     table[w] = das_window(q, im, l0, l1, d0, d1, w / ntx, w % ntx);
   for (int t = 0; t < ntx; ++t)
 #pragma unroll
-    for (int p = 0; p < DT_PX; ++p) {
-      const ff u = das_utx(q, g, x[p], z[p], t);
-      utx_s[(t * DT_PX + p) * DT_THREADS + threadIdx.x] = make_float2(u.hi, u.lo);
-    }
+    for (int p = 0; p < DT_PX; ++p)
+      utx_s[(t * DT_PX + p) * DT_THREADS + threadIdx.x] = das_split(das_utx(q, g, x[p], z[p], t));
   __syncthreads();
   int issued[DT_STAGES];  // uses issued per stage (meaningful in thread 0, the only issuer)
   for (int k = 0; k < DT_STAGES; ++k) issued[k] = 0;
@@ -233,9 +244,9 @@ __global__ void __launch_bounds__(DT_THREADS) k_das_tma(Acq q, Img im, const flo
       atomicOr(status, ST_TIMEOUT);
       staged = false;
     }
-    ff ur[DT_PX];
+    float2 ur[DT_PX];
 #pragma unroll
-    for (int p = 0; p < DT_PX; ++p) ur[p] = das_urx(q, g, x[p], z[p], e);
+    for (int p = 0; p < DT_PX; ++p) ur[p] = das_split(das_urx(q, g, x[p], z[p], e));
     float se[DT_PX];
 #pragma unroll
     for (int p = 0; p < DT_PX; ++p) se[p] = 0.0f;
@@ -245,10 +256,9 @@ __global__ void __launch_bounds__(DT_THREADS) k_das_tma(Acq q, Img im, const flo
       const float* sw = win + ((size_t)s * ntx + t) * DT_WIN;
 #pragma unroll
       for (int p = 0; p < DT_PX; ++p) {
-        const float2 ut = utx_s[(t * DT_PX + p) * DT_THREADS + threadIdx.x];
         int i;
         float f;
-        ff_floor(ff_addx(ff{ut.x, ut.y}, ur[p]), i, f);
+        das_tap(utx_s[(t * DT_PX + p) * DT_THREADS + threadIdx.x], ur[p], i, f);
         const int rel = i - b.x;
         float a0, a1;
         if (staged && b.y > 0 && rel >= 0 && rel + 1 < b.y) {
@@ -295,20 +305,16 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
     const bool valid = p < npx;
     const int l = valid ? p / im.nd : 0, d = valid ? p - l * im.nd : 0;
     const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
-    for (int t = 0; t < q.ntx; ++t) {
-      const ff u = das_utx(q, g, x, z, t);
-      utx_s[t * DAS_THREADS + threadIdx.x] = make_float2(u.hi, u.lo);
-    }
+    for (int t = 0; t < q.ntx; ++t) utx_s[t * DAS_THREADS + threadIdx.x] = das_split(das_utx(q, g, x, z, t));
     const float gv = valid ? gi[p] : 0.0f;
     if (gv != 0.0f) {
       for (int e = 0; e < q.ne; ++e) {
-        const ff ur = das_urx(q, g, x, z, e);
+        const float2 ur = das_split(das_urx(q, g, x, z, e));
         const float wg = hann_w(e, q.ne) * gv;
         for (int t = 0; t < q.ntx; ++t) {
-          const float2 ut = utx_s[t * DAS_THREADS + threadIdx.x];
           int i;
           float f;
-          ff_floor(ff_addx(ff{ut.x, ut.y}, ur), i, f);
+          das_tap(utx_s[t * DAS_THREADS + threadIdx.x], ur, i, f);
           float* row = grf + ((size_t)t * q.ne + e) * q.ns;
           if (i >= 0 && i < q.ns) atomicAdd(&row[i], wg * (1.0f - f));
           if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], wg * f);
