@@ -458,12 +458,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, Pat
   }
 }
 
-__device__ __forceinline__ uint32_t job_key(const RaySort& rs, const SceneDev& S, float4 job, uint32_t jm) {
+// a job the receive directivity cuts off (Eq. cutoff) ends at once: those go to the last bucket so
+// that they do not share warps with jobs that trace
+__device__ __forceinline__ uint32_t job_key(const RaySort& rs, const SceneDev& S, const Acq& q, float4 job,
+                                            uint32_t jm) {
   const float3 p = xyz(__ldg(&S.scat[__float_as_uint(job.w)]));
-  const int cx = min(3, max(0, (int)((p.x - rs.lo.x) * rs.inv_ext.x * 4.0f)));
-  const int cz = min(7, max(0, (int)((p.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
   const uint32_t e2 = (jm >> 8) & 0xFF;
   const uint32_t tx = (jm >> 16) & 0xFF;
+  const float3 dv = f3(elem_x(q, (int)e2), 0.0f, 0.0f) - p;
+  if (f_rx(-dv.z * rsqrtf(dot3(dv, dv)), q.alpha_m, q.alpha_c) == 0.0f) return RAY_BUCKETS - 1;
+  const int cx = min(3, max(0, (int)((p.x - rs.lo.x) * rs.inv_ext.x * 4.0f)));
+  const int cz = min(7, max(0, (int)((p.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
   return (((tx & 1u) << 13) | (e2 << 5) | ((uint32_t)cz << 2) | (uint32_t)cx) & (RAY_BUCKETS - 1);
 }
 
@@ -473,7 +478,7 @@ __global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, Ra
   __syncthreads();
   const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t key = job_key(rs, A.S, from.job[off + i], from.jm[off + i]);
+    const uint32_t key = job_key(rs, A.S, A.acq, from.job[off + i], from.jm[off + i]);
     rs.key[i] = key;
     atomicAdd(&h[key], 1u);
   }
