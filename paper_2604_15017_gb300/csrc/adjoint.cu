@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     NeeOut no;
     const uint2 xo = A.nres.xo ? A.nres.xo[i] : make_uint2(0u, NEE_UNSTORED);
     if (xo.y == NEE_UNSTORED) {  // trace the secondary ray again
-      no = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
+      no = nee_eval(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
     } else {  // the forward pass's result: same arithmetic, read back
       no.ok = xo.y != NEE_NONE;
       no.overflow = false;

@@ -81,6 +81,7 @@ struct us_ctx {
   int num_sms = 148;
   int trav_per_sm = 4;   // blocks per SM of the traversal grid
   int march_per_sm = 4;  // resident blocks per SM of the scatterer march
+  int nee_per_sm = 4;    // resident blocks per SM of the secondary-ray kernel
   int* d_status = nullptr;    // device status word of kernels outside the transport (ST_* bits)
   int opts[US_N_OPTS] = {};
   // tracing
@@ -445,7 +446,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     A.nee = sorted;
     if (do_nee && sc->dev.n_scat > 0) {
       StageScope sc_(ctx, US_STAGE_NEE, 1, st);
-      launch_nee(A, grid_of(ctx, 16), st);
+      launch_nee(A, grid_of(ctx, ctx->nee_per_sm), st);
     }
   }
   CK(cudaGetLastError());
@@ -521,6 +522,7 @@ int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
   ctx->opts[US_OPT_LANES] = 4;
   ctx->trav_per_sm = traverse_blocks_per_sm();
   ctx->march_per_sm = march_blocks_per_sm();
+  ctx->nee_per_sm = nee_blocks_per_sm();
   if (dev_alloc(ctx, (void**)&ctx->d_status, 256) != US_OK || cudaMemset(ctx->d_status, 0, 256) != cudaSuccess) {
     delete ctx;
     return US_ERR_OOM;

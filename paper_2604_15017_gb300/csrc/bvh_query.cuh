@@ -166,65 +166,77 @@ __device__ __forceinline__ void surface_hit(const SceneDev& S, const Acq& q, flo
   tri_closest(S, o, w, prev, tbest, cbest);
 }
 
-// all triangle crossings T_MIN < t < tmax of the segment o + t d (secondary rays; triangle-only
-// BVH), sorted by t.
-// Returns the count, or -1 when more than MAX_XINGS crossings were found.
-__device__ __forceinline__ int all_crossings(const SceneDev& S, float3 o, float3 d, float tmax, float* xt,
-                                             uint32_t* xid) {
-  const RayInv r = ray_inv(o, d);
-  int stack[BVH_STACK];
-  int sp = 0;
-  int node = 0;
-  int n = 0;
-  bool overflow = false;
-  while (true) {
-    const float4 n0 = __ldg(&S.nodes_t[4 * node]);
-    const float4 n1 = __ldg(&S.nodes_t[4 * node + 1]);
-    const float4 n2 = __ldg(&S.nodes_t[4 * node + 2]);
-    const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes_t[4 * node + 3]));
-    bool h0, h1;
-    float t0, t1;
-    node_boxes(r, n0, n1, n2, tmax, h0, h1, t0, t1);
-    for (int c = 0; c < 2; ++c) {
-      const bool h = c ? h1 : h0;
-      const int cnt = c ? n3.w : n3.z;
-      const int first = c ? n3.y : n3.x;
-      if (!h || cnt == 0) continue;
-      for (int i = first; i < first + cnt; ++i) {
-        const float4 A = __ldg(&S.prims_t[3 * i]);
-        const uint32_t code = __float_as_uint(A.w);
-        if (code_cls(code) != CLS_TRI) continue;
-        const float4 B = __ldg(&S.prims_t[3 * i + 1]);
-        const float4 C = __ldg(&S.prims_t[3 * i + 2]);
-        const float t = tri_test(o, d, xyz(A), xyz(B), xyz(C));
-        if (t > 0.0f && t < tmax) {
-          if (n < MAX_XINGS) {
-            xt[n] = t;
-            xid[n] = code_id(code);
-            ++n;
-          } else {
-            overflow = true;
-          }
+// all triangle crossings T_MIN < t < tmax of the segment o + t d (secondary rays), as a
+// resumable traversal: xtrav_step visits one node of the triangle BVH (testing the triangles of
+// leaf children) and returns false once the traversal is complete; xtrav_finish sorts the
+// crossings by t (ties by id) and returns their count, or -1 when more than MAX_XINGS were found.
+struct XTrav {
+  RayInv r;
+  float tmax;
+  int node, sp, n;
+  bool overflow;
+};
+
+__device__ __forceinline__ void xtrav_init(float3 o, float3 d, float tmax, XTrav& T) {
+  T.r = ray_inv(o, d);
+  T.tmax = tmax;
+  T.node = 0;
+  T.sp = 0;
+  T.n = 0;
+  T.overflow = false;
+}
+
+__device__ __forceinline__ bool xtrav_step(const SceneDev& S, float3 o, float3 d, XTrav& T, int* stack, float* xt,
+                                           uint32_t* xid) {
+  const float4 n0 = __ldg(&S.nodes_t[4 * T.node]);
+  const float4 n1 = __ldg(&S.nodes_t[4 * T.node + 1]);
+  const float4 n2 = __ldg(&S.nodes_t[4 * T.node + 2]);
+  const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes_t[4 * T.node + 3]));
+  bool h0, h1;
+  float t0, t1;
+  node_boxes(T.r, n0, n1, n2, T.tmax, h0, h1, t0, t1);
+  for (int c = 0; c < 2; ++c) {
+    const bool h = c ? h1 : h0;
+    const int cnt = c ? n3.w : n3.z;
+    const int first = c ? n3.y : n3.x;
+    if (!h || cnt == 0) continue;
+    for (int i = first; i < first + cnt; ++i) {
+      const float4 A = __ldg(&S.prims_t[3 * i]);
+      const uint32_t code = __float_as_uint(A.w);
+      const float4 B = __ldg(&S.prims_t[3 * i + 1]);
+      const float4 C = __ldg(&S.prims_t[3 * i + 2]);
+      const float t = tri_test(o, d, xyz(A), xyz(B), xyz(C));
+      if (t > 0.0f && t < T.tmax) {
+        if (T.n < MAX_XINGS) {
+          xt[T.n] = t;
+          xid[T.n] = code_id(code);
+          ++T.n;
+        } else {
+          T.overflow = true;
         }
       }
     }
-    const bool i0 = h0 && n3.z == 0 && n3.x >= 0;
-    const bool i1 = h1 && n3.w == 0 && n3.y >= 0;
-    if (i0 && i1) {
-      if (sp < BVH_STACK) stack[sp++] = n3.y;
-      node = n3.x;
-      continue;
-    }
-    if (i0 || i1) {
-      node = i0 ? n3.x : n3.y;
-      continue;
-    }
-    if (sp == 0) break;
-    node = stack[--sp];
   }
-  if (overflow) return -1;
-  // insertion sort by t (ties by id)
-  for (int i = 1; i < n; ++i) {
+  const bool i0 = h0 && n3.z == 0 && n3.x >= 0;
+  const bool i1 = h1 && n3.w == 0 && n3.y >= 0;
+  if (i0 && i1) {
+    if (T.sp < BVH_STACK) stack[T.sp++] = n3.y;
+    T.node = n3.x;
+    return true;
+  }
+  if (i0 || i1) {
+    T.node = i0 ? n3.x : n3.y;
+    return true;
+  }
+  if (T.sp == 0) return false;
+  T.node = stack[--T.sp];
+  return true;
+}
+
+__device__ __forceinline__ int xtrav_finish(const XTrav& T, float* xt, uint32_t* xid) {
+  if (T.overflow) return -1;
+  const int n = T.n;
+  for (int i = 1; i < n; ++i) {  // insertion sort by t (ties by id)
     const float t = xt[i];
     const uint32_t id = xid[i];
     int j = i - 1;
@@ -239,9 +251,17 @@ __device__ __forceinline__ int all_crossings(const SceneDev& S, float3 o, float3
   return n;
 }
 
-// secondary ray from a scatterer centre to element e (Sec. 2.3.3): straight segment, product
-// of transmission coefficients (zero under total internal reflection), attenuation and time
-// per sub-segment in the medium tracked across the crossings, receive directivity (Eq. cutoff).
+__device__ __forceinline__ int all_crossings(const SceneDev& S, float3 o, float3 d, float tmax, float* xt,
+                                             uint32_t* xid) {
+  XTrav T;
+  int stack[BVH_STACK];
+  xtrav_init(o, d, tmax, T);
+  while (xtrav_step(S, o, d, T, stack, xt, xid)) {
+  }
+  return xtrav_finish(T, xt, xid);
+}
+
+// result of one secondary ray (Sec. 2.3.3)
 struct NeeOut {
   bool ok;        // false: no contribution (directivity cutoff, TIR or overflow)
   bool overflow;
@@ -252,25 +272,28 @@ struct NeeOut {
 
 __device__ __forceinline__ float elem_x(const Acq& q, int e) { return (e - 0.5f * (q.ne - 1)) * q.pitch; }
 
-template <bool DERIV>
-__device__ __forceinline__ NeeOut nee_eval(const SceneDev& S, const Media& med, const Acq& q, float3 p, int e2,
-                                           int m_start, float& t_hi, float& t_lo, float* xt, uint32_t* xid,
-                                           float3* dir_out, float* D_out) {
+// secondary-ray geometry: unit direction d and length D from p to the centre of element e2;
+// the receive directivity (Eq. cutoff) of that direction
+__device__ __forceinline__ float nee_setup(const Acq& q, float3 p, int e2, float3& d, float& D) {
+  const float3 tgt = f3(elem_x(q, e2), 0.0f, 0.0f);
+  const float3 dv = tgt - p;
+  D = sqrtf(dot3(dv, dv));
+  d = dv * (1.0f / D);
+  return f_rx(-d.z, q.alpha_m, q.alpha_c);
+}
+
+// weight of a secondary ray from its sorted crossings (n of them; -1: overflow): product of
+// the transmission coefficients (zero under total internal reflection), attenuation and time
+// per sub-segment in the medium tracked across the crossings
+__device__ __forceinline__ NeeOut nee_shade(const SceneDev& S, const Media& med, const Acq& q, float3 d, float D,
+                                            float frx, int n, int m_start, float& t_hi, float& t_lo, const float* xt,
+                                            const uint32_t* xid) {
   NeeOut r;
   r.ok = false;
   r.overflow = false;
   r.gain = 0.0f;
   r.sum_al = 0.0f;
   r.n = 0;
-  const float3 tgt = f3(elem_x(q, e2), 0.0f, 0.0f);
-  const float3 dv = tgt - p;
-  const float D = sqrtf(dot3(dv, dv));
-  const float3 d = dv * (1.0f / D);
-  if (dir_out) *dir_out = d;
-  if (D_out) *D_out = D;
-  const float frx = f_rx(-d.z, q.alpha_m, q.alpha_c);
-  if (frx == 0.0f) return r;
-  const int n = all_crossings(S, p, d, D, xt, xid);
   if (n < 0) {
     r.overflow = true;
     return r;
@@ -302,6 +325,29 @@ __device__ __forceinline__ NeeOut nee_eval(const SceneDev& S, const Media& med, 
   r.gain = prodT * expf(-KAPPA_F * med.f0 * sa) * frx * (float)q.ne;
   r.ok = true;
   return r;
+}
+
+// secondary ray from a scatterer centre to element e (Sec. 2.3.3): straight segment, weight
+// as in nee_shade, receive directivity (Eq. cutoff)
+__device__ __forceinline__ NeeOut nee_eval(const SceneDev& S, const Media& med, const Acq& q, float3 p, int e2,
+                                           int m_start, float& t_hi, float& t_lo, float* xt, uint32_t* xid,
+                                           float3* dir_out, float* D_out) {
+  float3 d;
+  float D;
+  const float frx = nee_setup(q, p, e2, d, D);
+  if (dir_out) *dir_out = d;
+  if (D_out) *D_out = D;
+  if (frx == 0.0f) {
+    NeeOut r;
+    r.ok = false;
+    r.overflow = false;
+    r.gain = 0.0f;
+    r.sum_al = 0.0f;
+    r.n = 0;
+    return r;
+  }
+  const int n = all_crossings(S, p, d, D, xt, xid);
+  return nee_shade(S, med, q, d, D, frx, n, m_start, t_hi, t_lo, xt, xid);
 }
 
 }  // namespace usrt

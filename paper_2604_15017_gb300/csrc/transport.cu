@@ -335,41 +335,105 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
 
 // ------------------------------------------------------------------------------------------
 // Secondary rays of the scatterer events of segment k (Sec. 2.3.3)
+//
+// The lengths of the all-crossings traversals differ a lot within a warp, so lanes are refilled:
+// a lane whose traversal is complete waits until at most NEE_REFILL_AT lanes of its warp still
+// trace, then every waiting lane weighs its ray (nee_shade), stores and appends the arrival
+// together, and takes the next job from a pool the warp claims in chunks of NEE_CHUNK
+// consecutive (sorted) job slots.  Jobs the receive directivity cuts off finish at the claim.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
+constexpr int NEE_CHUNK = 64;
+constexpr int NEE_REFILL_AT = 16;
+
+__device__ __forceinline__ void nee_store(const TransportArgs& A, uint32_t i, const NeeOut& r, float th, float tl,
+                                          const float* xt, const uint32_t* xid) {
+  uint2 xo = make_uint2(0u, NEE_NONE);
+  if (r.ok) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    const uint32_t before = cg::exclusive_scan(g, (uint32_t)r.n);
+    unsigned long long base = 0ull;
+    if (g.thread_rank() == g.size() - 1) base = atomicAdd(&A.cnt->n_xing, (unsigned long long)(before + r.n));
+    base = g.shfl(base, g.size() - 1) + before;
+    if (base + (unsigned)r.n <= A.nres.xcap) {
+      for (int c = 0; c < r.n; ++c) A.nres.xing[base + c] = make_uint2(__float_as_uint(xt[c]), xid[c]);
+      xo = make_uint2((uint32_t)base, (uint32_t)r.n);
+    } else {
+      xo = make_uint2(0u, NEE_UNSTORED);
+    }
+    A.nres.res[i] = make_float4(th, tl, r.gain, r.sum_al);
+  }
+  A.nres.xo[i] = xo;
+}
+
+__global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
   const Acq& q = A.acq;
   const Media& med = A.med;
   const uint32_t n = A.cnt->nee[A.k];
   const uint32_t off = A.cnt->nee_off[A.k];
+  if (n == 0) return;
+  uint32_t* claim = &A.cnt->nee_claim[A.k];
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
   float xt[MAX_XINGS];
   uint32_t xid[MAX_XINGS];
-  for (uint32_t ii = blockIdx.x * blockDim.x + threadIdx.x; ii < n; ii += gridDim.x * blockDim.x) {
-    const uint32_t i = off + ii;
-    const float4 job = A.nee.job[i];
-    const uint32_t jm = A.nee.jm[i];
-    const uint32_t j = __float_as_uint(job.w);
-    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
-    const float4 sc = __ldg(&A.S.scat[j]);
-    float th = job.y, tl = job.z;
-    const NeeOut r = nee_eval<false>(A.S, med, q, xyz(sc), e2, m, th, tl, xt, xid, nullptr, nullptr);
-    if (A.nres.res) {  // keep the result for the adjoint
-      uint2 xo = make_uint2(0u, NEE_NONE);
-      if (r.ok) {
-        cg::coalesced_group g = cg::coalesced_threads();
-        const uint32_t before = cg::exclusive_scan(g, (uint32_t)r.n);
-        unsigned long long base = 0ull;
-        if (g.thread_rank() == g.size() - 1) base = atomicAdd(&A.cnt->n_xing, (unsigned long long)(before + r.n));
-        base = g.shfl(base, g.size() - 1) + before;
-        if (base + (unsigned)r.n <= A.nres.xcap) {
-          for (int c = 0; c < r.n; ++c) A.nres.xing[base + c] = make_uint2(__float_as_uint(xt[c]), xid[c]);
-          xo = make_uint2((uint32_t)base, (uint32_t)r.n);
-        } else {
-          xo = make_uint2(0u, NEE_UNSTORED);
+  int stack[BVH_STACK];
+  uint32_t job = 0xFFFFFFFFu;  // job slot (from off) of this lane; none when 0xFFFFFFFF
+  bool tracing = false;
+  float3 p = f3(0.0f, 0.0f, 0.0f), d = p;
+  float D = 0.0f, frx = 0.0f;
+  XTrav T;
+  xtrav_init(p, f3(0.0f, 0.0f, 1.0f), 0.0f, T);
+  uint32_t pool = 0u, pool_end = 0u;  // warp-uniform
+  bool exhausted = false;             // warp-uniform
+  while (true) {
+    uint32_t idle = __ballot_sync(0xFFFFFFFFu, job == 0xFFFFFFFFu);
+    while (idle && !exhausted) {
+      if (pool == pool_end) {
+        uint32_t b = 0u;
+        if (lane == 0) b = atomicAdd(claim, (uint32_t)NEE_CHUNK);
+        b = __shfl_sync(0xFFFFFFFFu, b, 0);
+        if (b >= n) {
+          exhausted = true;
+          break;
         }
-        A.nres.res[i] = make_float4(th, tl, r.gain, r.sum_al);
+        pool = b;
+        pool_end = min(b + (uint32_t)NEE_CHUNK, n);
       }
-      A.nres.xo[i] = xo;
+      const uint32_t take = min((uint32_t)__popc(idle), pool_end - pool);
+      const uint32_t rank = __popc(idle & below);
+      if (((idle >> lane) & 1u) && rank < take) {
+        job = pool + rank;
+        const uint32_t jm = A.nee.jm[off + job];
+        p = xyz(__ldg(&A.S.scat[__float_as_uint(A.nee.job[off + job].w)]));
+        frx = nee_setup(q, p, (int)((jm >> 8) & 0xFF), d, D);
+        if (frx == 0.0f) {  // cut off: no contribution
+          if (A.nres.res) A.nres.xo[off + job] = make_uint2(0u, NEE_NONE);
+          job = 0xFFFFFFFFu;
+        } else {
+          xtrav_init(p, d, D, T);
+          tracing = true;
+        }
+      }
+      pool += take;
+      idle = __ballot_sync(0xFFFFFFFFu, job == 0xFFFFFFFFu);
     }
+    if (__all_sync(0xFFFFFFFFu, job == 0xFFFFFFFFu)) break;
+    // trace until at most NEE_REFILL_AT lanes still trace (until none, once the pool is empty)
+    while (true) {
+      const int still = __popc(__ballot_sync(0xFFFFFFFFu, tracing));
+      if (still == 0 || (!exhausted && still <= NEE_REFILL_AT)) break;
+      if (tracing) tracing = xtrav_step(A.S, p, d, T, stack, xt, xid);
+    }
+    if (job == 0xFFFFFFFFu || tracing) continue;
+    // weigh the finished rays, keep them for the adjoint, append their arrivals
+    const uint32_t i = off + job;
+    job = 0xFFFFFFFFu;
+    const float4 jb = A.nee.job[i];
+    const uint32_t jm = A.nee.jm[i];
+    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
+    float th = jb.y, tl = jb.z;
+    const NeeOut r = nee_shade(A.S, med, q, d, D, frx, xtrav_finish(T, xt, xid), m, th, tl, xt, xid);
+    if (A.nres.res) nee_store(A, i, r, th, tl, xt, xid);
     if (r.overflow) {
       atomicOr(&A.cnt->status, ST_OVERFLOW);
       atomicAdd(&A.cnt->dropped, 1u);
@@ -378,7 +442,7 @@ __global__ void __launch_bounds__(128) k_nee(TransportArgs A) {
     if (!r.ok || !A.arr) continue;
     const uint32_t tq = time_to_tq(th, tl, q.fs);
     if (tq == 0xFFFFFFFFu) continue;
-    const float amp = job.x * med.As * sc.w * r.gain;
+    const float amp = jb.x * med.As * __ldg(&A.S.scat[__float_as_uint(jb.w)]).w * r.gain;
     const uint32_t slot = append_slot(&A.cnt->n_arr);
     if (slot < A.arr_cap) A.arr[slot] = make_uint4((uint32_t)(tx * q.ne + e2), tq, __float_as_uint(amp), 0xFFFFFFFFu);
   }
@@ -568,6 +632,11 @@ int traverse_blocks_per_sm() {
   return 2 * b;  // two waves of resident blocks: a short tail without a long grid-stride loop
 }
 void launch_interact(const TransportArgs& a, int grid, cudaStream_t st) { k_interact<<<grid, 256, 0, st>>>(a); }
-void launch_nee(const TransportArgs& a, int grid, cudaStream_t st) { k_nee<<<grid, 128, 0, st>>>(a); }
+void launch_nee(const TransportArgs& a, int grid, cudaStream_t st) { k_nee<<<grid, NEE_THREADS, 0, st>>>(a); }
+int nee_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_nee, NEE_THREADS, 0) != cudaSuccess || b < 1) b = 4;
+  return b;  // one wave of resident blocks: lanes refill from the pool until it is empty
+}
 
 }  // namespace usrt

@@ -40,6 +40,7 @@ struct Counters {
   uint32_t nee[MAX_KMAX + 2];   // secondary jobs produced at segment k
   uint32_t nee_off[MAX_KMAX + 2]; // first job of round k in the job buffer
   uint32_t march[MAX_KMAX + 2]; // queue slots claimed by the scatterer march of round k
+  uint32_t nee_claim[MAX_KMAX + 2]; // job slots claimed by the secondary-ray kernel of round k
   unsigned long long n_xing;    // secondary-ray crossings appended (NeeRes; may pass xcap)
   uint32_t n_arr;               // arrivals appended
   uint32_t dropped;             // arrivals dropped (crossing list overflow)
@@ -96,6 +97,8 @@ constexpr int MARCH_THREADS = 128;
 void launch_march(const TransportArgs& a, int grid, cudaStream_t st);
 int march_blocks_per_sm();  // resident blocks per SM of the scatterer march (persistent grid)
 void launch_interact(const TransportArgs& a, int grid, cudaStream_t st);
+constexpr int NEE_THREADS = 128;
 void launch_nee(const TransportArgs& a, int grid, cudaStream_t st);
+int nee_blocks_per_sm();  // resident blocks per SM of the secondary-ray kernel (persistent grid)
 
 }  // namespace usrt
