@@ -362,6 +362,22 @@ static void build_scatter_grid(const HostSceneIn& in, HostSceneOut& out) {
         e[2] = in.scat_pos[3 * (size_t)j + 2];
         e[3] = bits_f((3u << 20) | (uint32_t)j);
       });
+    // the first two entries of every cell inline, so that a ray reads one 32-byte record per
+    // cell: code 0 marks an empty slot, bit 31 of the second code that the cell holds more
+    out.cell2.assign(8 * n_cells, 0.0f);
+    for (size_t c = 0; c < n_cells; ++c) {
+      const uint32_t f0 = out.cell[c] >> 8, k = out.cell[c] & 0xFFu;
+      for (uint32_t slot = 0; slot < 2 && slot < k; ++slot) {
+        const float* e = &out.cell_sph[4 * (size_t)(f0 + slot)];
+        float* o = &out.cell2[8 * c + 4 * slot];
+        o[0] = e[0];
+        o[1] = e[1];
+        o[2] = e[2];
+        uint32_t code;
+        std::memcpy(&code, &e[3], 4);
+        o[3] = bits_f(code | (slot == 1 && k > 2 ? 0x80000000u : 0u));
+      }
+    }
     return;
   }
   // unreachable for scenes the upload accepts (< 2^20 spheres): an empty grid would lose hits

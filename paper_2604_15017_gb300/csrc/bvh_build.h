@@ -28,6 +28,7 @@ struct HostSceneOut {
   int gn[3] = {0, 0, 0};
   std::vector<uint32_t> cell;
   std::vector<float> cell_sph;  // 4 floats per entry
+  std::vector<float> cell2;     // per cell its first two entries (8 floats); see build_scatter_grid
   std::vector<float> tri_nrm;  // 4 per triangle
   std::vector<float> tri_v0;   // 4 per triangle
   std::vector<float> scat;     // 4 per scatterer

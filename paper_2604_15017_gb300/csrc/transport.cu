@@ -90,12 +90,14 @@ __global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
 //
 // Path lengths to the first event are spread roughly exponentially, so with one ray per thread
 // a warp would run as long as its longest ray with most lanes idle.  Instead every loop
-// iteration does one unit of work per lane (one sphere test, then, once the cell has no sphere
-// left, one step to the next cell and the read of its word), and a lane whose ray has finished
-// takes the next ray from a pool the warp claims in chunks of MARCH_CHUNK consecutive
-// (coherence-sorted) queue slots.  A sphere listed in two consecutive cells is tested once.
+// iteration does the same work in every lane: enter one cell, test the two entries its 32-byte
+// record holds inline, step the DDA and read the next cell's record (entries past the second,
+// in crowded cells, take one iteration each).  Lanes whose rays have finished take the next
+// rays, once MARCH_REFILL_MIN of them wait, from a pool the warp claims in chunks of MARCH_CHUNK
+// consecutive (coherence-sorted) queue slots.
 // ------------------------------------------------------------------------------------------
 constexpr int MARCH_CHUNK = 64;
+constexpr int MARCH_REFILL_MIN = 8;
 
 __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
   const SceneDev& S = A.S;
@@ -112,15 +114,23 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
   uint32_t ray = 0xFFFFFFFFu;  // queue slot of the current ray; none when 0xFFFFFFFF
   float3 o = f3(0.0f, 0.0f, 0.0f), w = o;
   float ix = 0.0f, iy = 0.0f, iz = 0.0f, tnx = 0.0f, tny = 0.0f, tnz = 0.0f, tbest = 0.0f;
-  uint32_t prev = 0u, cbest = 0u, code0 = 0u, last = 0xFFFFFFFFu, e = 0u, e_end = 0u;
+  uint32_t prev = 0u, cbest = 0u, code0 = 0u, e = 0u, e_end = 0u;
   int cx = 0, cy = 0, cz = 0, idx = 0, sx = 1, sy = 1, sz = 1, ux = 0, uy = 0, uz = 0;
-  // the DDA runs one cell ahead of the cell whose spheres are being tested: (cx, cy, cz, idx)
-  // is the next cell, entered at t_ahead, and its word is read as soon as the DDA gets there,
-  // so the read has a whole iteration (or more) to arrive.  It is read only while t_ahead <=
-  // tbest; tbest only decreases, so a word not read is a word never needed.
+  // The DDA runs one cell ahead: (cx, cy, cz, idx) is the next cell to enter, at t_ahead, and
+  // its inline record (first two entries) is read as soon as the DDA gets there, so the read has
+  // an iteration to arrive.  It is read only while t_ahead <= tbest; tbest only decreases, so a
+  // record not read is a record never needed.
   float t_ahead = 0.0f;
   bool ahead_ok = false;
-  uint32_t word_ahead = 0u;
+  float4 slot_a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), slot_b = slot_a;
+  auto fetch_ahead = [&]() {
+    if (ahead_ok && t_ahead <= tbest) {
+      slot_a = __ldg(&S.cell2[2 * idx]);
+      slot_b = __ldg(&S.cell2[2 * idx + 1]);
+    } else {
+      slot_a.w = slot_b.w = 0.0f;
+    }
+  };
   auto step_ahead = [&]() {
     if (tnx <= tny && tnx <= tnz) {
       t_ahead = tnx;
@@ -141,13 +151,23 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
       ahead_ok = (unsigned)cz < (unsigned)nz;
       tnz = (fmaf((float)(cz + uz), h, lo.z) - o.z) * iz;
     }
-    word_ahead = ahead_ok && t_ahead <= tbest ? __ldg(&S.cell[idx]) : 0u;
+    fetch_ahead();
+  };
+  auto test = [&](float4 sp) {
+    const uint32_t code = __float_as_uint(sp.w) & 0x7FFFFFFFu;
+    const float t = code == 0u || code == prev ? -1.0f : scat_test(o, w, xyz(sp), S.rs2);
+    if (t > 0.0f && hit_better(t, code, tbest, cbest)) {
+      tbest = t;
+      cbest = code;
+    }
   };
   uint32_t pool = 0u, pool_end = 0u;  // warp-uniform
   bool exhausted = false;             // warp-uniform
   while (true) {
-    // hand the pool's rays to idle lanes; rays that miss the grid leave their lane idle
+    // hand the pool's rays to idle lanes once MARCH_REFILL_MIN of them wait, so that the setup
+    // of new rays runs on many lanes at once; rays that miss the grid leave their lane idle
     uint32_t idle = __ballot_sync(0xFFFFFFFFu, ray == 0xFFFFFFFFu);
+    if (__popc(idle) < MARCH_REFILL_MIN) idle = 0u;
     while (idle && !exhausted) {
       if (pool == pool_end) {
         uint32_t b = 0u;
@@ -172,7 +192,6 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
         prev = A.qin.meta[ray].y;
         tbest = hit.x;
         cbest = code0 = __float_as_uint(hit.y);
-        last = 0xFFFFFFFFu;
         ix = safe_inv(w.x);
         iy = safe_inv(w.y);
         iz = safe_inv(w.z);
@@ -197,10 +216,10 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
           tny = w.y == 0.0f ? 3.0e38f : (fmaf((float)(cy + uy), h, lo.y) - o.y) * iy;
           tnz = w.z == 0.0f ? 3.0e38f : (fmaf((float)(cz + uz), h, lo.z) - o.z) * iz;
           idx = (cz * ny + cy) * nx + cx;
-          const uint32_t word = __ldg(&S.cell[idx]);
-          e = word >> 8;
-          e_end = e + (word & 0xFFu);
-          step_ahead();
+          t_ahead = t0;  // the first cell is the one ahead
+          ahead_ok = true;
+          e = e_end = 0u;
+          fetch_ahead();
         }
       }
       pool += take;
@@ -208,27 +227,27 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
     }
     if (__all_sync(0xFFFFFFFFu, ray == 0xFFFFFFFFu)) break;  // pool exhausted, every lane idle
     if (ray == 0xFFFFFFFFu) continue;
-    if (e < e_end) {  // one sphere of the current cell (a sphere just tested in the previous cell is skipped)
-      const float4 sp = __ldg(&S.cell_sph[e]);
+    if (e < e_end) {  // entries past the first two of a crowded cell
+      test(__ldg(&S.cell_sph[e]));
       ++e;
-      const uint32_t code = __float_as_uint(sp.w);
-      const float t = code == prev || code == last ? -1.0f : scat_test(o, w, xyz(sp), S.rs2);
-      last = code;
-      if (t > 0.0f && hit_better(t, code, tbest, cbest)) {
-        tbest = t;
-        cbest = code;
-      }
-      if (e < e_end) continue;
+      continue;
     }
-    // the current cell is done: enter the next one (its word is already here), or finish the ray
-    if (ahead_ok && t_ahead <= tbest) {
-      e = word_ahead >> 8;
-      e_end = e + (word_ahead & 0xFFu);
-      step_ahead();
-    } else {
+    if (!(ahead_ok && t_ahead <= tbest)) {  // no cell left to enter below tbest: done
       if (cbest != code0) A.hits[ray] = make_float2(tbest, __uint_as_float(cbest));
       ray = 0xFFFFFFFFu;
+      continue;
     }
+    // enter the cell ahead: test its inline entries, then step the DDA past it
+    const float4 a = slot_a, b = slot_b;
+    const int cell = idx;
+    test(a);
+    test(b);
+    if (__float_as_uint(b.w) >> 31) {
+      const uint32_t word = __ldg(&S.cell[cell]);
+      e = (word >> 8) + 2u;
+      e_end = (word >> 8) + (word & 0xFFu);
+    }
+    step_ahead();
   }
 }
 

@@ -82,6 +82,7 @@ struct SceneDev {
   const float4* prims_t;     // triangles in leaf order: (v0, code) (e1, -) (e2, -)
   const uint32_t* cell;        // scatterer grid, per cell (z * gny + y) * gnx + x: first entry << 8 | count
   const float4* cell_sph;      // per (cell, sphere): (centre, bits(code))
+  const float4* cell2;         // per cell its first two entries; code 0: empty, bit 31: more follow
   float3 glo;                  // grid origin and cell edge
   float gh;
   int gnx, gny, gnz;
