@@ -278,7 +278,10 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
                      int mode, const float* dL_drf_dev, float* dL_dtheta_dev, void* stream);
 
 /* Full adjoint: dL/dB -> dL/dRF (us_bmode_vjp) -> dL/dtheta (us_transport_vjp).
- * dL_drf_dev is an optional output (NULL: a library workspace is used). */
+ * dL_drf_dev is an optional output (NULL: a library workspace is used).  In mode 0 rf_dev must
+ * hold the RF of that same forward pass, unchanged: when it is the buffer the forward pass
+ * wrote (and B-mode was formed there), the beamformed image the forward pass made from it is
+ * reused instead of beamforming the RF again. */
 int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
                uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
                float* dL_drf_dev, void* stream);

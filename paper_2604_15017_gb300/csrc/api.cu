@@ -56,10 +56,21 @@ struct RecordKey {
 // A lane owns one set of workspaces, a path record and the counters of its last forward pass.
 // Single-request calls run on lane 0 with the caller's stream; us_forward_batch spreads the
 // requests of a batch over lanes with their own streams so that they overlap on the device.
+// what the beamformed image in a lane's W_IRF workspace was made from: the RF pointer, the
+// image grid and the acquisition quantities DAS reads; lets a record-mode adjoint reuse the
+// forward pass's image instead of beamforming the same RF again
+struct IrfKey {
+  bool valid = false;
+  const float* rf = nullptr;
+  const void* irf = nullptr;
+  std::vector<float> sig;
+};
+
 struct Lane {
   Buf ws[W_COUNT];
   Buf record;
   RecordKey rkey;
+  IrfKey ikey;
   Counters* h_cnt = nullptr;  // pinned copy of the last forward's counters
   cudaEvent_t ev_stats = nullptr;
   long long last_paths = 0;
@@ -479,6 +490,25 @@ int do_splat(us_ctx* ctx, const Acq& q, float f0, const Arrival* arr, const uint
   return US_OK;
 }
 
+std::vector<float> das_signature(const Acq& q, const Img& im) {
+  std::vector<float> v = {(float)q.ne, q.pitch, (float)q.ntx, q.fs, (float)q.ns, q.cbf, (float)im.nl, (float)im.nd,
+                          im.x0, im.x1, im.z0, im.z1};
+  for (int t = 0; t < q.ntx; ++t) {
+    v.push_back(q.sin_tx[t]);
+    v.push_back(q.cos_tx[t]);
+    v.push_back(q.cos_lo[t]);
+  }
+  return v;
+}
+
+void irf_made(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, const float* irf) {
+  IrfKey& k = ctx->L->ikey;
+  k.valid = true;
+  k.rf = rf;
+  k.irf = irf;
+  k.sig = das_signature(q, im);
+}
+
 int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* bmode, cudaStream_t st) {
   float *irf, *env;
   unsigned long long* key;
@@ -489,6 +519,7 @@ int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* b
     StageScope sc_(ctx, US_STAGE_DAS, 1, st);
     launch_das(q, im, rf, irf, grid_of(ctx, 8), st, ctx->opts[US_OPT_DAS_TMA] ? ctx->d_status : nullptr);
   }
+  irf_made(ctx, q, im, rf, irf);
   {
     StageScope sc_(ctx, US_STAGE_ENVLOG, 0, st);
     sc_.nk = launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
@@ -723,6 +754,7 @@ int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   CKS(make_acq(ctx, acq, seed, q));
   if (bmode_dev) CKS(make_img(ctx, img, im));
   ctx->L->rkey.valid = false;  // job buffers and counters are about to be overwritten
+  ctx->L->ikey.valid = false;  // and rf_dev, which the lane's beamformed image may have come from
   const long long n_paths = q.rays_per_tx * q.ntx;
   const long long cap_ll = n_paths * (q.kmax + 1);
   const uint32_t cap = (uint32_t)std::min<long long>(cap_ll, 0xFFFFFFF0ll);
@@ -804,6 +836,7 @@ int us_splat(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int
   CKS(make_acq(ctx, acq, 0, q));
   if (n < 0 || n >= 0xFFFFFFF0ll || !rf_dev || !aligned16(rf_dev) || (n && (!tx_dev || !e_dev || !tau_dev || !a_dev)))
     return fail(ctx, US_ERR_ARG, "invalid arrival list");
+  ctx->L->ikey.valid = false;  // rf_dev is rewritten
   Arrival* arr;
   uint32_t* n_out;
   CKS(ws(ctx, W_PACK, (size_t)n + 1, st, &arr));
@@ -908,8 +941,10 @@ int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, 
   return US_OK;
 }
 
-int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
-                 const float* dL_dB_dev, float* dL_drf_dev, void* stream) {
+// reuse_irf: the lane's beamformed image may be reused when it was made from rf_dev with the
+// same grid and acquisition (a record-mode adjoint right after its forward pass)
+static int bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+                     const float* dL_dB_dev, float* dL_drf_dev, void* stream, bool reuse_irf) {
   if (!ctx) return US_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   Acq q;
@@ -920,9 +955,11 @@ int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, co
   float *irf, *gi;
   CKS(ws(ctx, W_IRF, (size_t)im.nl * im.nd, st, &irf));
   CKS(ws(ctx, W_GI, (size_t)im.nl * im.nd, st, &gi));
-  {
+  const IrfKey& k = ctx->L->ikey;
+  if (!(reuse_irf && k.valid && k.rf == rf_dev && k.irf == irf && k.sig == das_signature(q, im))) {
     StageScope sc_(ctx, US_STAGE_DAS, 1, st);
     launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st, ctx->opts[US_OPT_DAS_TMA] ? ctx->d_status : nullptr);
+    irf_made(ctx, q, im, rf_dev, irf);
   }
   CKS(us_envlog_vjp(ctx, img, irf, dL_dB_dev, gi, stream));
   {
@@ -931,6 +968,11 @@ int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, co
   }
   CK(cudaGetLastError());
   return US_OK;
+}
+
+int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+                 const float* dL_dB_dev, float* dL_drf_dev, void* stream) {
+  return bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, dL_drf_dev, stream, false);
 }
 
 int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int32_t* tx_dev,
@@ -1053,7 +1095,7 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   CKS(make_acq(ctx, acq, seed, q));
   float* grf = dL_drf_dev;
   if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
-  CKS(us_bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream));
+  CKS(bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream, mode == 0));
   return us_transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, stream);
 }
 

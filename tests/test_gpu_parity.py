@@ -368,6 +368,27 @@ def test_adjoint_end_to_end_and_autograd(ctx):
     ctx.release_scene(sid)
 
 
+def test_record_adjoint_reusing_the_forward_image_equals_recomputing_it(ctx):
+    """A record-mode adjoint on the forward pass's own RF buffer reuses the image that pass
+    beamformed; beamforming the RF again (a copy of the buffer, or the two calls us_adjoint
+    makes, issued by hand) gives the same gradient up to the order of the transposed DAS's
+    float atomics."""
+    w = small_inclusions(n_rays=200, k_max=4, n_tx=2)
+    sid = ctx.upload_workload(w)
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    gb = torch.randn_like(b) * (b > -60)
+    g_reuse, grf_reuse = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, gb, want_grf=True)
+    g_copy, grf_copy = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf.clone(), gb, want_grf=True)
+    grf_hand = ctx.bmode_vjp(w["acq"], w["img"], rf, gb)
+    g_hand = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], grf_hand)
+    torch.cuda.synchronize()
+    for other in (grf_copy, grf_hand):
+        assert float((grf_reuse - other).norm()) <= 1e-5 * float(grf_reuse.norm())
+    for other in (g_copy, g_hand):
+        assert torch.allclose(g_reuse, other, rtol=1e-4, atol=1e-5 * float(g_reuse.abs().max()))
+    ctx.release_scene(sid)
+
+
 def test_record_mode_needs_matching_forward(ctx):
     from paper_2604_15017_gb300 import usrt
 
