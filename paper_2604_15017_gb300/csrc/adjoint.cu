@@ -455,9 +455,10 @@ __device__ __forceinline__ int path_class(const uint32_t* rec, int kmax) {
   return active ? nseg : -1;
 }
 
-__global__ void k_active_count(const uint32_t* record, uint32_t n, int kmax, uint32_t* work) {
+__global__ void k_active_count(const uint32_t* record, uint32_t n, int kmax, uint32_t* work, uint8_t* pclass) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = path_class(record + (size_t)i * (kmax + 1), kmax);
+    pclass[i] = (uint8_t)(c < 0 ? 0xFF : c);  // read back by k_active_fill instead of the record
     if (c < 0) continue;
     const unsigned same = __match_any_sync(__activemask(), c);  // lanes of this class
     if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&work[c], (uint32_t)__popc(same));
@@ -476,9 +477,9 @@ __global__ void k_active_scan(uint32_t* work) {
   }
 }
 
-__global__ void k_active_fill(const uint32_t* record, uint32_t n, int kmax, uint32_t* work, uint32_t* active) {
+__global__ void k_active_fill(const uint8_t* pclass, uint32_t n, uint32_t* work, uint32_t* active) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = path_class(record + (size_t)i * (kmax + 1), kmax);
+    const int c = pclass[i] == 0xFF ? -1 : (int)pclass[i];
     if (c < 0) continue;
     const unsigned same = __match_any_sync(__activemask(), c);
     const int lane = threadIdx.x & 31;
@@ -510,12 +511,12 @@ __global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   k_nee_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);
 }
-void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint32_t* active,
-                         int grid, cudaStream_t st) {
+void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint8_t* pclass,
+                         uint32_t* active, int grid, cudaStream_t st) {
   cudaMemsetAsync(work, 0, sizeof(uint32_t) * 52, st);
-  k_active_count<<<grid, 256, 0, st>>>(record, n_paths, kmax, work);
+  k_active_count<<<grid, 256, 0, st>>>(record, n_paths, kmax, work, pclass);
   k_active_scan<<<1, 32, 0, st>>>(work);
-  k_active_fill<<<grid, 256, 0, st>>>(record, n_paths, kmax, work, active);
+  k_active_fill<<<grid, 256, 0, st>>>(pclass, n_paths, work, active);
 }
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   k_path_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);

@@ -35,9 +35,10 @@ struct AdjArgs {
 
 // secondary-ray adjoint (job-parallel): seeds + direct parameter derivatives
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
-// active paths of the record grouped by event count: work = 2 counters + 17 offsets + n entries
-void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint32_t* active,
-                         int grid, cudaStream_t st);
+// active paths of the record grouped by event count: work = 2 counters + 17 offsets + n entries;
+// pclass: n_paths bytes of scratch (each path's class)
+void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint8_t* pclass,
+                         uint32_t* active, int grid, cudaStream_t st);
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
 cudaError_t adjoint_set_attrs();
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st);

@@ -28,7 +28,7 @@ enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
-  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_COUNT
+  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS, W_COUNT
 };
 
 struct SceneGPU {
@@ -1051,7 +1051,9 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
     }
     {
       StageScope sc_(ctx, US_STAGE_PATH_ADJ, 4, st);
-      launch_active_paths(rec, n, q.kmax, work, active, grid_of(ctx, 4), st);
+      uint8_t* pclass;
+      CKS(ws(ctx, W_PCLASS, (size_t)n, st, &pclass));
+      launch_active_paths(rec, n, q.kmax, work, pclass, active, grid_of(ctx, 4), st);
       A.gpart = gpart;
       launch_path_adjoint(A, grid, st);
     }

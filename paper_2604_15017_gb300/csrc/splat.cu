@@ -77,27 +77,55 @@ __global__ void k_row_hist(const Arrival* arr, const uint32_t* n_arr, uint32_t c
 }
 
 // exclusive scan of the row counts (one block of 1024 threads); off[nrows] = total
+// exclusive scan of nrows counts by one block: warp w owns a contiguous segment, read and written
+// 32 entries at a time (coalesced) with a shuffle scan per chunk; the 32 segment totals are
+// scanned by warp 0
 __global__ void k_row_scan(const uint32_t* cnt, uint32_t* off, uint32_t* cursor, int nrows) {
-  __shared__ uint32_t part[1024];
-  const int per = (nrows + blockDim.x - 1) / blockDim.x;
-  const int lo = threadIdx.x * per, hi = min(nrows, lo + per);
-  uint32_t s = 0;
-  for (int r = lo; r < hi; ++r) s += cnt[r];
-  part[threadIdx.x] = s;
+  __shared__ uint32_t seg_total[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int seg = (nrows + nw - 1) / nw;
+  const int lo = warp * seg, hi = min(nrows, lo + seg);
+  uint32_t run = 0;
+  for (int b = lo; b < hi; b += 32) {
+    const int r = b + lane;
+    uint32_t v = r < hi ? cnt[r] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += u;
+    }
+    run += __shfl_sync(0xFFFFFFFFu, v, 31);
+  }
+  if (lane == 0) seg_total[warp] = run;
   __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    uint32_t v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < nw ? seg_total[lane] : 0u;
+    const uint32_t own = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane < nw) seg_total[lane] = v - own;  // exclusive
+    if (lane == 31) off[nrows] = v;
   }
-  uint32_t run = part[threadIdx.x] - s;
-  for (int r = lo; r < hi; ++r) {
-    off[r] = run;
-    cursor[r] = 0;
-    run += cnt[r];
+  __syncthreads();
+  run = seg_total[warp];
+  for (int b = lo; b < hi; b += 32) {
+    const int r = b + lane;
+    const uint32_t c = r < hi ? cnt[r] : 0u;
+    uint32_t v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (r < hi) {
+      off[r] = run + v - c;
+      cursor[r] = 0;
+    }
+    run += __shfl_sync(0xFFFFFFFFu, v, 31);
   }
-  if (threadIdx.x == blockDim.x - 1) off[nrows] = part[threadIdx.x];
 }
 
 // scatter into row buckets: each block takes chunks of CH arrivals, ranks them per row in
