@@ -668,6 +668,7 @@ int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
   int s;
   if ((s = up(o.tri_nrm, &sc.dev.tri_nrm)) || (s = up(o.tri_v0, &sc.dev.tri_v0)) || (s = up(o.scat, &sc.dev.scat)) ||
       (s = up(o.nodes_t, &sc.dev.nodes_t)) || (s = up(o.prims_t, &sc.dev.prims_t)) ||
+      (s = up(o.nodes4, &sc.dev.nodes4)) ||
       (s = up(o.cell_sph, &sc.dev.cell_sph)) || (s = up(o.cell2, &sc.dev.cell2)) ||
       (s = up_bytes(o.cell.data(), o.cell.size() * sizeof(uint32_t), reinterpret_cast<const void**>(&sc.dev.cell)))) {
     for (void* p : sc.allocs) cudaFree(p);
@@ -703,7 +704,7 @@ int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
   sc.dev.n_scat = d->n_scat;
   sc.dev.rs2 = d->r_s * d->r_s;
   // depth check: the traversal stacks hold 64 entries
-  sc.depth = o.depth_t;
+  sc.depth = std::max(o.depth_t, 3 * o.depth4 + 1);  // a 4-wide node pushes up to 3 entries
   if (sc.depth > 60) {
     for (void* p : sc.allocs) cudaFree(p);
     ctx->used -= sc.bytes;

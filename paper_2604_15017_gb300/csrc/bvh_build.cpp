@@ -180,7 +180,8 @@ float bits_f(uint32_t u) {
 
 // BVH over the triangles: device nodes and triangles in leaf order
 static void build_tri_bvh(const HostSceneIn& in, std::vector<float>& nodes_out, std::vector<float>& prims_out,
-                          int& n_nodes_out, int& depth_out) {
+                          int& n_nodes_out, int& depth_out, std::vector<float>& nodes4_out, int& n_nodes4_out,
+                          int& depth4_out) {
   const int n = in.n_tris;
   Builder B;
   B.pbox.resize(n);
@@ -263,6 +264,88 @@ static void build_tri_bvh(const HostSceneIn& in, std::vector<float>& nodes_out, 
     for (int t : order) emit(B.tree[t].left, B.tree[t].right);
   }
   n_nodes_out = (int)(nodes_out.size() / 16);
+
+  // 4-wide BVH by collapsing the binary tree: a node's children are found by repeatedly
+  // replacing its inner child of largest surface area with that child's two children, until
+  // there are four or only leaves remain.  Device layout, 32 floats (128 bytes) per node:
+  // lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4], hi.z[4], int child[4], int count[4]; count > 0:
+  // a leaf of `count` triangles from `child`; count 0: an inner node (child >= 0) or an empty
+  // slot (child -1, inverted box).
+  nodes4_out.clear();
+  depth4_out = 1;
+  std::vector<int> work;  // binary inner nodes waiting to become 4-wide nodes
+  std::vector<int> id4(B.tree.size(), -1), dep4(B.tree.size(), 1);
+  auto children4 = [&](int t, int* ch) {
+    int nc = 2;
+    ch[0] = B.tree[t].left;
+    ch[1] = B.tree[t].right;
+    while (nc < 4) {
+      int best = -1;
+      double area = -1.0;
+      for (int i = 0; i < nc; ++i)
+        if (B.tree[ch[i]].count == 0 && B.tree[ch[i]].box.area() > area) {
+          area = B.tree[ch[i]].box.area();
+          best = i;
+        }
+      if (best < 0) break;
+      const int c = ch[best];
+      ch[best] = B.tree[c].left;
+      ch[nc++] = B.tree[c].right;
+    }
+    for (int i = nc; i < 4; ++i) ch[i] = -1;
+    return nc;
+  };
+  std::vector<int> order4;
+  if (root >= 0 && B.tree[root].count == 0) {
+    // number the 4-wide nodes in DFS order
+    std::vector<int> st(1, root);
+    while (!st.empty()) {
+      const int t = st.back();
+      st.pop_back();
+      id4[t] = (int)order4.size();
+      order4.push_back(t);
+      depth4_out = std::max(depth4_out, dep4[t]);
+      int ch[4];
+      children4(t, ch);
+      for (int i = 3; i >= 0; --i)
+        if (ch[i] >= 0 && B.tree[ch[i]].count == 0) {
+          dep4[ch[i]] = dep4[t] + 1;
+          st.push_back(ch[i]);
+        }
+    }
+  }
+  auto emit4 = [&](const int* ch) {
+    float w[32];
+    for (int i = 0; i < 4; ++i) {
+      float lo[3], hi[3];
+      int ci, cnt;
+      child_fields(ch[i], lo, hi, ci, cnt);
+      if (ch[i] >= 0 && B.tree[ch[i]].count == 0) ci = id4[ch[i]];
+      w[0 + i] = lo[0];
+      w[4 + i] = hi[0];
+      w[8 + i] = lo[1];
+      w[12 + i] = hi[1];
+      w[16 + i] = lo[2];
+      w[20 + i] = hi[2];
+      w[24 + i] = bits_f((uint32_t)ci);
+      w[28 + i] = bits_f((uint32_t)cnt);
+    }
+    nodes4_out.insert(nodes4_out.end(), w, w + 32);
+  };
+  if (root < 0) {
+    const int ch[4] = {-1, -1, -1, -1};
+    emit4(ch);
+  } else if (B.tree[root].count > 0) {
+    const int ch[4] = {root, -1, -1, -1};
+    emit4(ch);
+  } else {
+    for (int t : order4) {
+      int ch[4];
+      children4(t, ch);
+      emit4(ch);
+    }
+  }
+  n_nodes4_out = (int)(nodes4_out.size() / 32);
 
   // triangles in leaf order: (v0, code) (e1, -) (e2, -)
   prims_out.assign(12 * (size_t)n, 0.0f);
@@ -386,7 +469,7 @@ static void build_scatter_grid(const HostSceneIn& in, HostSceneOut& out) {
 
 void build_scene_host(const HostSceneIn& in, HostSceneOut& out) {
   const int nt = in.n_tris, ns = in.n_scat;
-  build_tri_bvh(in, out.nodes_t, out.prims_t, out.n_nodes_t, out.depth_t);
+  build_tri_bvh(in, out.nodes_t, out.prims_t, out.n_nodes_t, out.depth_t, out.nodes4, out.n_nodes4, out.depth4);
   build_scatter_grid(in, out);
 
   // per-triangle normal + media, vertex 0; per-scatterer centre + amplitude

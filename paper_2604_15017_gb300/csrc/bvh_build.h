@@ -20,6 +20,8 @@ struct HostSceneOut {
   int n_nodes_t = 0, depth_t = 0;  // BVH over the triangles (closest hits, secondary-ray crossings)
   std::vector<float> nodes_t;      // 16 floats per node
   std::vector<float> prims_t;      // 12 floats per triangle, leaf order
+  int n_nodes4 = 0, depth4 = 0;    // the same tree collapsed to 4-wide nodes (same leaves)
+  std::vector<float> nodes4;       // 32 floats per node
   // uniform grid over the scatterer spheres: cell (x, y, z) covers glo + h [x, x+1) x [y, y+1) x
   // [z, z+1).  cell[(z * gn[1] + y) * gn[0] + x] = first << 8 | count names the (centre, code)
   // entries of every sphere whose (slightly inflated) bounding box overlaps the cell:

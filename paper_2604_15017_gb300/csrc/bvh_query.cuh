@@ -166,9 +166,50 @@ __device__ __forceinline__ void surface_hit(const SceneDev& S, const Acq& q, flo
   tri_closest(S, o, w, prev, tbest, cbest);
 }
 
+// ---- 4-wide BVH (the secondary rays' all-crossings queries) ----------------------------
+// Closest hits walk the binary tree: measured, the 4-wide one halved their node visits but was
+// not faster (their cost is the scattered node reads, not the count); for all-crossings queries,
+// which visit every node the segment overlaps, it is.  A node is 8 float4 (128 bytes): lo.x, hi.x, lo.y, hi.y, lo.z, hi.z of its 4 children, then
+// int4 child and int4 count (count > 0: a leaf of count triangles from child; count 0: an inner
+// node, or an empty slot with child -1 and an inverted box).
+struct Node4 {
+  float4 lx, hx, ly, hy, lz, hz;
+  int4 ch, cn;
+};
+__device__ __forceinline__ Node4 load_node4(const float4* nodes, int node) {
+  const float4* p = nodes + 8 * node;
+  Node4 n;
+  n.lx = __ldg(p);
+  n.hx = __ldg(p + 1);
+  n.ly = __ldg(p + 2);
+  n.hy = __ldg(p + 3);
+  n.lz = __ldg(p + 4);
+  n.hz = __ldg(p + 5);
+  n.ch = __ldg(reinterpret_cast<const int4*>(p + 6));
+  n.cn = __ldg(reinterpret_cast<const int4*>(p + 7));
+  return n;
+}
+// slab test of one child box; entry distance returned, hit when entry <= exit (robust, as
+// node_boxes)
+__device__ __forceinline__ bool box_hit(const RayInv& r, float lx, float hx, float ly, float hy, float lz, float hz,
+                                        float tlimit, float& tn) {
+  const float ax = fmaf(lx, r.inv.x, -r.oi.x), bx = fmaf(hx, r.inv.x, -r.oi.x);
+  const float ay = fmaf(ly, r.inv.y, -r.oi.y), by = fmaf(hy, r.inv.y, -r.oi.y);
+  const float az = fmaf(lz, r.inv.z, -r.oi.z), bz = fmaf(hz, r.inv.z, -r.oi.z);
+  const float lo = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), 0.0f));
+  const float hi = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), tlimit));
+  tn = lo;
+  return lo <= hi * 1.0000004f;
+}
+__device__ __forceinline__ void node4_boxes(const RayInv& r, const Node4& n, float tlimit, float* tn, bool* h) {
+  h[0] = box_hit(r, n.lx.x, n.hx.x, n.ly.x, n.hy.x, n.lz.x, n.hz.x, tlimit, tn[0]);
+  h[1] = box_hit(r, n.lx.y, n.hx.y, n.ly.y, n.hy.y, n.lz.y, n.hz.y, tlimit, tn[1]);
+  h[2] = box_hit(r, n.lx.z, n.hx.z, n.ly.z, n.hy.z, n.lz.z, n.hz.z, tlimit, tn[2]);
+  h[3] = box_hit(r, n.lx.w, n.hx.w, n.ly.w, n.hy.w, n.lz.w, n.hz.w, tlimit, tn[3]);
+}
 // all triangle crossings T_MIN < t < tmax of the segment o + t d (secondary rays), as a
-// resumable traversal: xtrav_step visits one node of the triangle BVH (testing the triangles of
-// leaf children) and returns false once the traversal is complete; xtrav_finish sorts the
+// resumable traversal: xtrav_step visits one node of the 4-wide triangle BVH (testing the
+// triangles of leaf children) and returns false once the traversal is complete; xtrav_finish sorts the
 // crossings by t (ties by id) and returns their count, or -1 when more than MAX_XINGS were found.
 struct XTrav {
   RayInv r;
@@ -188,44 +229,42 @@ __device__ __forceinline__ void xtrav_init(float3 o, float3 d, float tmax, XTrav
 
 __device__ __forceinline__ bool xtrav_step(const SceneDev& S, float3 o, float3 d, XTrav& T, int* stack, float* xt,
                                            uint32_t* xid) {
-  const float4 n0 = __ldg(&S.nodes_t[4 * T.node]);
-  const float4 n1 = __ldg(&S.nodes_t[4 * T.node + 1]);
-  const float4 n2 = __ldg(&S.nodes_t[4 * T.node + 2]);
-  const int4 n3 = __ldg(reinterpret_cast<const int4*>(&S.nodes_t[4 * T.node + 3]));
-  bool h0, h1;
-  float t0, t1;
-  node_boxes(T.r, n0, n1, n2, T.tmax, h0, h1, t0, t1);
-  for (int c = 0; c < 2; ++c) {
-    const bool h = c ? h1 : h0;
-    const int cnt = c ? n3.w : n3.z;
-    const int first = c ? n3.y : n3.x;
-    if (!h || cnt == 0) continue;
-    for (int i = first; i < first + cnt; ++i) {
-      const float4 A = __ldg(&S.prims_t[3 * i]);
-      const uint32_t code = __float_as_uint(A.w);
-      const float4 B = __ldg(&S.prims_t[3 * i + 1]);
-      const float4 C = __ldg(&S.prims_t[3 * i + 2]);
-      const float t = tri_test(o, d, xyz(A), xyz(B), xyz(C));
-      if (t > 0.0f && t < T.tmax) {
-        if (T.n < MAX_XINGS) {
-          xt[T.n] = t;
-          xid[T.n] = code_id(code);
-          ++T.n;
-        } else {
-          T.overflow = true;
+  const Node4 n = load_node4(S.nodes4, T.node);
+  float tn[4];
+  bool h[4];
+  node4_boxes(T.r, n, T.tmax, tn, h);
+  const int ch[4] = {n.ch.x, n.ch.y, n.ch.z, n.ch.w}, cn[4] = {n.cn.x, n.cn.y, n.cn.z, n.cn.w};
+  int next = -1;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (!h[c]) continue;
+    if (cn[c] > 0) {
+      for (int i = ch[c]; i < ch[c] + cn[c]; ++i) {
+        const float4 A = __ldg(&S.prims_t[3 * i]);
+        const uint32_t code = __float_as_uint(A.w);
+        const float4 B = __ldg(&S.prims_t[3 * i + 1]);
+        const float4 C = __ldg(&S.prims_t[3 * i + 2]);
+        const float t = tri_test(o, d, xyz(A), xyz(B), xyz(C));
+        if (t > 0.0f && t < T.tmax) {
+          if (T.n < MAX_XINGS) {
+            xt[T.n] = t;
+            xid[T.n] = code_id(code);
+            ++T.n;
+          } else {
+            T.overflow = true;
+          }
         }
+      }
+    } else if (ch[c] >= 0) {
+      if (next < 0) {
+        next = ch[c];
+      } else if (T.sp < BVH_STACK) {
+        stack[T.sp++] = ch[c];
       }
     }
   }
-  const bool i0 = h0 && n3.z == 0 && n3.x >= 0;
-  const bool i1 = h1 && n3.w == 0 && n3.y >= 0;
-  if (i0 && i1) {
-    if (T.sp < BVH_STACK) stack[T.sp++] = n3.y;
-    T.node = n3.x;
-    return true;
-  }
-  if (i0 || i1) {
-    T.node = i0 ? n3.x : n3.y;
+  if (next >= 0) {
+    T.node = next;
     return true;
   }
   if (T.sp == 0) return false;

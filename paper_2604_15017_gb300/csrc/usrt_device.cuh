@@ -80,6 +80,7 @@ struct SceneDev {
   const float4* nodes_t;     // triangle BVH2: n0=(c0.lo.x,c0.hi.x,c0.lo.y,c0.hi.y) n1=(same, c1)
                              // n2=(c0 z, c1 z) n3=int4(child0, child1, count0, count1)
   const float4* prims_t;     // triangles in leaf order: (v0, code) (e1, -) (e2, -)
+  const float4* nodes4;      // the triangle tree as a 4-wide BVH (8 float4 per node, same leaves)
   const uint32_t* cell;        // scatterer grid, per cell (z * gny + y) * gnx + x: first entry << 8 | count
   const float4* cell_sph;      // per (cell, sphere): (centre, bits(code))
   const float4* cell2;         // per cell its first two entries; code 0: empty, bit 31: more follow
