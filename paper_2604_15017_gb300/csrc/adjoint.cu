@@ -16,6 +16,10 @@ namespace usrt {
 // S11: splat adjoint of one arrival (time t_hi + t_lo [s], amplitude a) against the row g:
 //   ga = sum_n g[n] s(x_n),  gt = -a sum_n g[n] s'(x_n),  gf = a sum_n g[n] ds(x_n)/df0,
 // x_n = n / fs - tau, s(x) = sin(2 pi f0 x) exp(-x^2 / sigma), sigma = 4 ln2 / (pi bw f0)^2.
+// The taps are consecutive samples, so the carrier and the Gaussian are stepped by recurrences
+// from the first tap (a rotation by 2 pi f0 / fs; E_{n+1} = E_n q_n, q_{n+1} = q_n exp(-2 /
+// (fs^2 sigma))) instead of a sin/cos and an exp per tap; over the <= 96 taps of the support
+// their rounding grows to a few 1e-6 relative.
 // ------------------------------------------------------------------------------------------
 __device__ __forceinline__ void splat_adj_gather(const float* __restrict__ g, float t_hi, float t_lo, float a,
                                                  const PulseP& P, float& ga, float& gt, float& gf) {
@@ -27,21 +31,30 @@ __device__ __forceinline__ void splat_adj_gather(const float* __restrict__ g, fl
   const int lo = max(0, n0 + (int)ceilf(fr - P.half));
   const int hi = min(P.ns - 1, n0 + (int)floorf(fr + P.half));
   float sa = 0.0f, st = 0.0f, sf = 0.0f;
-  const float w = 2.0f * PI_F * P.f0;
-  const float inv_sig = 1.0f / P.sig;
-  for (int n = lo; n <= hi; ++n) {
-    const float gn = __ldg(&g[n]);
-    if (gn == 0.0f) continue;
-    const float x = ((float)(n - n0) - fr) / P.fs;
+  if (lo <= hi) {
+    const float w = 2.0f * PI_F * P.f0;
+    const float inv_sig = 1.0f / P.sig;
+    const float dt = 1.0f / P.fs;
+    const float x0 = ((float)(lo - n0) - fr) / P.fs;
     float sn, cs;
-    sincosf(w * x, &sn, &cs);
-    const float E = expf(-x * x * inv_sig);
-    const float s = sn * E;
-    const float ds_dx = (w * cs - 2.0f * x * inv_sig * sn) * E;
-    const float ds_df = (2.0f * PI_F * x * cs - sn * 2.0f * x * x * inv_sig / P.f0) * E;
-    sa = fmaf(gn, s, sa);
-    st = fmaf(gn, -ds_dx, st);
-    sf = fmaf(gn, ds_df, sf);
+    sincosf(w * x0, &sn, &cs);
+    float E = expf(-x0 * x0 * inv_sig);
+    float q = expf(-(2.0f * x0 + dt) * dt * inv_sig);  // E(x0 + dt) / E(x0)
+    for (int n = lo; n <= hi; ++n) {
+      const float gn = __ldg(&g[n]);
+      const float x = fmaf((float)(n - lo), dt, x0);
+      const float s = sn * E;
+      const float ds_dx = (w * cs - 2.0f * x * inv_sig * sn) * E;
+      const float ds_df = (2.0f * PI_F * x * cs - sn * 2.0f * x * x * inv_sig / P.f0) * E;
+      sa = fmaf(gn, s, sa);
+      st = fmaf(gn, -ds_dx, st);
+      sf = fmaf(gn, ds_df, sf);
+      const float sn1 = fmaf(sn, P.rot_c, cs * P.rot_s);
+      cs = fmaf(cs, P.rot_c, -sn * P.rot_s);
+      sn = sn1;
+      E *= q;
+      q *= P.env_qq;
+    }
   }
   ga = sa;
   gt = a * st;

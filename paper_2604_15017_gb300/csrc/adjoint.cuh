@@ -11,6 +11,10 @@ constexpr int MAX_P = 3 * MAX_MEDIA + 2;
 struct PulseP {
   float f0, sig, fs, half;  // half = 4 sqrt(sigma) fs (support in samples)
   int ns;
+  // per-sample steps of the gather's recurrences: the carrier phase advances by 2 pi f0 / fs
+  // (cos, sin), and the Gaussian's ratio E(x + 1/fs) / E(x) is multiplied by
+  // exp(-2 / (fs^2 sigma)) every sample
+  float rot_c, rot_s, env_qq;
 };
 
 struct AdjArgs {

@@ -336,6 +336,9 @@ int splat_geom(us_ctx* ctx, const Acq& q, float f0, SplatGeom& g, PulseP& P) {
   P.fs = q.fs;
   P.half = (float)half;
   P.ns = q.ns;
+  P.rot_c = (float)std::cos(2.0 * M_PI * (double)f0 / q.fs);
+  P.rot_s = (float)std::sin(2.0 * M_PI * (double)f0 / q.fs);
+  P.env_qq = (float)std::exp(-2.0 / ((double)q.fs * q.fs * sig));
   return US_OK;
 }
 
