@@ -504,6 +504,7 @@ __global__ void __launch_bounds__(256) k_ray_keys(TransportArgs A, PathQ from, R
 }
 
 constexpr int RS_THREADS = 512;
+constexpr int JOB_BUCKETS = 1024;  // <= RAY_BUCKETS (the sort buffers are shared)
 constexpr int RS_PER = 16;
 constexpr int RS_CH = RS_THREADS * RS_PER;
 __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, PathQ from, PathQ to, RaySort rs) {
@@ -541,23 +542,23 @@ __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, Pat
   }
 }
 
-// a job the receive directivity cuts off (Eq. cutoff) ends at once: those go to the last bucket so
-// that they do not share warps with jobs that trace
+// key of a secondary-ray job: target element and origin depth cell (jobs aimed at one element
+// from nearby scatterers share a warp); a job the receive directivity cuts off (Eq. cutoff) ends
+// at once: those go to the last bucket so that they do not share warps with jobs that trace.
+// 1024 buckets: few enough that each sort chunk writes runs of several jobs per bucket
 __device__ __forceinline__ uint32_t job_key(const RaySort& rs, const SceneDev& S, const Acq& q, float4 job,
                                             uint32_t jm) {
   const float3 p = xyz(__ldg(&S.scat[__float_as_uint(job.w)]));
   const uint32_t e2 = (jm >> 8) & 0xFF;
-  const uint32_t tx = (jm >> 16) & 0xFF;
   const float3 dv = f3(elem_x(q, (int)e2), 0.0f, 0.0f) - p;
-  if (f_rx(-dv.z * rsqrtf(dot3(dv, dv)), q.alpha_m, q.alpha_c) == 0.0f) return RAY_BUCKETS - 1;
-  const int cx = min(3, max(0, (int)((p.x - rs.lo.x) * rs.inv_ext.x * 4.0f)));
-  const int cz = min(7, max(0, (int)((p.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
-  return (((tx & 1u) << 13) | (e2 << 5) | ((uint32_t)cz << 2) | (uint32_t)cx) & (RAY_BUCKETS - 1);
+  if (f_rx(-dv.z * rsqrtf(dot3(dv, dv)), q.alpha_m, q.alpha_c) == 0.0f) return JOB_BUCKETS - 1;
+  const int cz = min(3, max(0, (int)((p.z - rs.lo.z) * rs.inv_ext.z * 4.0f)));
+  return ((e2 << 2) | (uint32_t)cz) & (JOB_BUCKETS - 1);
 }
 
 __global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, RaySort rs) {
   extern __shared__ uint32_t h[];
-  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+  for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x) h[b] = 0;
   __syncthreads();
   const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -566,17 +567,17 @@ __global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, Ra
     atomicAdd(&h[key], 1u);
   }
   __syncthreads();
-  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+  for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x)
     if (h[b]) atomicAdd(&rs.cnt[b], h[b]);
 }
 
 __global__ void __launch_bounds__(RS_THREADS) k_job_scatter(TransportArgs A, NeeQ from, NeeQ to, RaySort rs) {
   extern __shared__ uint32_t sm[];
   uint32_t* h = sm;
-  uint32_t* base = sm + RAY_BUCKETS;
+  uint32_t* base = sm + JOB_BUCKETS;
   const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
   for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
-    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+    for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x) h[b] = 0;
     __syncthreads();
     uint32_t key[RS_PER], rank[RS_PER];
 #pragma unroll
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_job_scatter(TransportArgs A, Nee
       }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+    for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x)
       if (h[b]) base[b] = rs.off[b] + atomicAdd(&rs.cursor[b], h[b]);
     __syncthreads();
 #pragma unroll
@@ -607,10 +608,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_job_scatter(TransportArgs A, Nee
 
 void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, const RaySort& rs, int grid,
                      cudaStream_t st) {
-  cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st);
-  k_job_keys<<<grid, 256, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, rs);
-  launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
-  k_job_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
+  cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * JOB_BUCKETS, st);
+  k_job_keys<<<grid, 256, sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, rs);
+  launch_count_scan(rs.cnt, rs.off, rs.cursor, JOB_BUCKETS, st);
+  k_job_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, to, rs);
 }
 
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
