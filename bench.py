@@ -37,9 +37,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-stages", action="store_true")
-    ap.add_argument("--config", default="frame", choices=["frame", "batch", "serve"],
+    ap.add_argument("--config", default="frame", choices=["frame", "batch", "serve", "optim"],
                     help="frame: one fwd+adj frame per step (the metric line); batch: a batch of scenes of "
-                         "uneven size, batched vs one by one; serve: Poisson arrivals through the serving loop")
+                         "uneven size, batched vs one by one; serve: Poisson arrivals through the serving loop; "
+                         "optim: iterations of the micro-batched inverse problem (Alg. 1)")
     ap.add_argument("--batch-n", type=int, default=256, help="scenes in the batch")
     ap.add_argument("--scale", type=float, default=1.0, help="ray/scatterer scale of batch and serve scenes")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate, requests/s")
@@ -366,6 +367,47 @@ def run_serve(args):
     ctx.close()
 
 
+def run_optim(args):
+    """Iterations of the micro-batched inverse problem (Alg. 1) on the differentiation workload
+    (inclusion phantom, one 0-deg plane wave, K_max 4, 1e5 rays): two ray micro-batches per
+    iteration, each forward + loss + adjoint in record mode, then one Adam step; every
+    parameter free within +-20 %, target at theta0 +-5 %."""
+    import torch
+    from paper_2604_15017_gb300 import phantoms as P, optim, usrt
+
+    w = P.differentiation()
+    ctx = usrt.Context(0)
+    sid = ctx.upload_workload(w)
+    th0 = np.asarray(w["theta"], np.float64)
+    prob = optim.InverseProblem(ctx, sid, th0, 0.8 * th0, 1.2 * th0, 0.01, optim.split_rays(w["acq"], 2), w["img"],
+                                seed=w["seed"])
+    prob.set_targets(w["theta_target"])
+    for _ in range(args.warmup):
+        prob.step()
+    torch.cuda.synchronize()
+    segs = 0
+    for b, acq in enumerate(prob.batches):  # work per iteration (the realisations are fixed)
+        ctx.forward(sid, prob.physical(), acq, w["img"], seed=prob.seed + b)
+        st_ = ctx.stats()
+        segs += st_["segments"] + st_["nee_queries"]
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        losses = prob.run(args.steps)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+    out = {"metric": "optimiser iterations/s", "value": 1.0 / dt, "unit": "iterations/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "differentiation-inclusions-1tx-1e5rays-kmax4", "micro_batches": 2,
+                      "parameters": int(th0.size), "segments_per_iteration": segs,
+                      "step": "2 x (fwd + loss + adj, record mode) + Adam"},
+           "path_segments_per_s": segs / dt, "loss_first": losses[0], "loss_last": losses[-1],
+           "clocks": clk.summary()}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     args = parse()
     from paper_2604_15017_gb300 import phantoms as P
@@ -375,6 +417,9 @@ def main():
         return
     if args.impl == "ours" and args.config == "serve":
         run_serve(args)
+        return
+    if args.impl == "ours" and args.config == "optim":
+        run_optim(args)
         return
 
     w = P.inclusions(n_rays=args.rays)

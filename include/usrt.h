@@ -287,6 +287,29 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
                float* dL_drf_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Inverse problem: parameterisation and optimiser step (Sec. 3.4, Sec. 3.7, Alg. 1)         */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Physical parameters from the optimiser's unconstrained variables (Sec. 3.4, Eq. clip01 and
+ * Eq. scale_phys): theta[j] = lo[j] + clip(theta_u[j], 0, 1) (hi[j] - lo[j]).  All arrays are
+ * DEVICE float[n], caller-owned; 1 <= n <= 1024.  Stream-ordered. */
+int us_param_map(us_ctx* ctx, int n, const float* theta_u_dev, const float* lo_dev, const float* hi_dev,
+                 float* theta_dev, void* stream);
+
+/* One Adam step on theta_u (Sec. 3.7, Eq. adam) from the gradient with respect to the PHYSICAL
+ * parameters (dL/dtheta, e.g. from us_adjoint): the gradient is carried back through the scale
+ * and the clip (Eq. clip_grad: zero where theta_u lies outside (0, 1)), scaled down to global
+ * L2 norm clip_norm when it is longer (clip_norm <= 0: no clipping), then
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   theta_u -= lr[j] (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps).
+ * lr_dev holds one learning rate per parameter (parameter groups).  step counts from 1.
+ * theta_u_dev, m_dev, v_dev are updated in place (m, v start at zero).  All arrays DEVICE
+ * float[n], caller-owned; 1 <= n <= 1024. */
+int us_adam_step(us_ctx* ctx, int n, float* theta_u_dev, const float* dL_dtheta_dev, const float* lo_dev,
+                 const float* hi_dev, const float* lr_dev, float beta1, float beta2, float eps, float clip_norm,
+                 int step, float* m_dev, float* v_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Batching (many scenes / probe poses of uneven size)                                       */
 /* ---------------------------------------------------------------------------------------- */
 

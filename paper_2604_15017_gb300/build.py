@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libusrt.so")
-SOURCES = ["transport.cu", "splat.cu", "image.cu", "adjoint.cu", "api.cu", "noalloc.cu", "bvh_build.cpp"]
+SOURCES = ["transport.cu", "splat.cu", "image.cu", "adjoint.cu", "api.cu", "optim.cu", "noalloc.cu", "bvh_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"] + ARCH
 

@@ -534,6 +534,13 @@ int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* b
 }  // namespace
 
 // =========================================================================================
+namespace usrt {  // optim.cu
+void launch_param_map(int n, const float* theta_u, const float* lo, const float* hi, float* theta, cudaStream_t st);
+void launch_adam_step(int n, float* theta_u, const float* grad, const float* lo, const float* hi, const float* lr,
+                      float beta1, float beta2, float eps, float clip_norm, float bc1, float bc2, float* m, float* v,
+                      cudaStream_t st);
+}  // namespace usrt
+
 extern "C" {
 
 int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
@@ -608,6 +615,36 @@ int us_profile_read(us_ctx* ctx, double* ms, int64_t* launches, int n) {
   ctx->recs.clear();
   ctx->pool_used = 0;
   for (int i = 0; i < US_N_STAGES; ++i) ctx->stage_launches[i] = 0;
+  return US_OK;
+}
+
+int us_param_map(us_ctx* ctx, int n, const float* theta_u_dev, const float* lo_dev, const float* hi_dev,
+                 float* theta_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  if (n < 1 || n > 1024 || !theta_u_dev || !lo_dev || !hi_dev || !theta_dev)
+    return fail(ctx, US_ERR_ARG, "param_map: 1 <= n <= 1024 and four device arrays");
+  CK(cudaSetDevice(ctx->device));
+  StageScope sc_(ctx, US_STAGE_OTHER, 1, (cudaStream_t)stream);
+  launch_param_map(n, theta_u_dev, lo_dev, hi_dev, theta_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_adam_step(us_ctx* ctx, int n, float* theta_u_dev, const float* dL_dtheta_dev, const float* lo_dev,
+                 const float* hi_dev, const float* lr_dev, float beta1, float beta2, float eps, float clip_norm,
+                 int step, float* m_dev, float* v_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  if (n < 1 || n > 1024 || !theta_u_dev || !dL_dtheta_dev || !lo_dev || !hi_dev || !lr_dev || !m_dev || !v_dev)
+    return fail(ctx, US_ERR_ARG, "adam_step: 1 <= n <= 1024 and seven device arrays");
+  if (step < 1 || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+    return fail(ctx, US_ERR_ARG, "adam_step: step >= 1, 0 <= beta < 1, eps > 0");
+  CK(cudaSetDevice(ctx->device));
+  const float bc1 = (float)(1.0 - std::pow((double)beta1, (double)step));
+  const float bc2 = (float)(1.0 - std::pow((double)beta2, (double)step));
+  StageScope sc_(ctx, US_STAGE_OTHER, 1, (cudaStream_t)stream);
+  launch_adam_step(n, theta_u_dev, dL_dtheta_dev, lo_dev, hi_dev, lr_dev, beta1, beta2, eps, clip_norm, bc1, bc2,
+                   m_dev, v_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
   return US_OK;
 }
 

@@ -26,7 +26,7 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
            "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch",
-           "us_run_request", "us_request_bytes"]
+           "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step"]
 OPT_DAS_TMA, OPT_LANES = 0, 1
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
@@ -122,6 +122,9 @@ def lib():
             l.us_request_bytes.argtypes = [VP, C.POINTER(Request), C.POINTER(C.c_size_t)]
             l.us_autotune_batch.argtypes = [VP, C.c_int, C.POINTER(Request), VP, C.POINTER(C.c_int),
                                             C.POINTER(C.c_int)]
+            l.us_param_map.argtypes = [VP, C.c_int, VP, VP, VP, VP, VP]
+            l.us_adam_step.argtypes = [VP, C.c_int, VP, VP, VP, VP, VP, C.c_float, C.c_float, C.c_float, C.c_float,
+                                       C.c_int, VP, VP, VP]
             _lib = l
     return _lib
 
@@ -346,6 +349,22 @@ class Context:
                                      C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
                                      _ptr(gth), _ptr(grf), _stream(stream)))
         return gth, grf
+
+    # ---- inverse problem: parameterisation and optimiser step (Sec. 3.4, 3.7) ----
+    def param_map(self, theta_u, lo, hi, out=None, stream=None):
+        """Physical parameters lo + clip(theta_u, 0, 1) (hi - lo) (device tensors)."""
+        out = torch.empty_like(theta_u) if out is None else out
+        self._check(lib().us_param_map(self.h, theta_u.numel(), _ptr(theta_u), _ptr(lo), _ptr(hi), _ptr(out),
+                                       _stream(stream)))
+        return out
+
+    def adam_step(self, theta_u, grad_phys, lo, hi, lr, m, v, step, beta1=0.9, beta2=0.999, eps=1e-8, clip_norm=0.0,
+                  stream=None):
+        """One Adam step on theta_u (in place) from dL/dtheta of the physical parameters."""
+        self._check(lib().us_adam_step(self.h, theta_u.numel(), _ptr(theta_u), _ptr(grad_phys), _ptr(lo), _ptr(hi),
+                                       _ptr(lr), float(beta1), float(beta2), float(eps), float(clip_norm), int(step),
+                                       _ptr(m), _ptr(v), _stream(stream)))
+        return theta_u
 
 
 class Batch:
