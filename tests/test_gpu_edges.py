@@ -1,0 +1,129 @@
+"""Edge cases of the CUDA path against the FP64 oracle: ragged sizes (records, image lines and
+element counts that fill no tile), scenes with scatterers but no triangles and with nothing at
+all, one ray per element, the smallest and largest interaction budgets, more transmits than
+the tiled kernels stage, tiny sample records, and an empty batch.  Tolerances as in
+test_gpu_parity.py."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2604_15017_gb300 import phantoms as P
+
+pytestmark = pytest.mark.gpu
+
+MM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_15017_gb300 import usrt
+
+    c = usrt.Context(0)
+    yield c
+    c.close()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype).cuda()
+
+
+def no_triangles(w):
+    w = dict(w)
+    w["tris"] = np.zeros((0, 9))
+    w["media"] = np.zeros((0, 2), dtype=np.int32)
+    return w
+
+
+def parity(ctx, w, seq_min=0.9999):
+    sid = ctx.upload_workload(w)
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    torch.cuda.synchronize()
+    ref = O.forward(w)
+    st = ctx.stats()
+    assert st["status"] == 0 and st["dropped"] == 0
+    acq = w["acq"]
+    n_paths = len(acq["angles"]) * acq["n_elem"] * acq["n_rays"]
+    rec = ctx.record(0, n_paths, acq["k_max"]).cpu().numpy()
+    ora = ref["run"].records()
+    r = rec.astype(np.int64) & 0xFFFFFFFF
+    same = (((r >> 20) & 3) == ora["cls"]) & (((r & 0xFFFFF) == ora["id"]) | (ora["cls"] == 0))
+    assert same.all(axis=1).mean() >= seq_min
+    rf_g = rf.double().cpu().numpy()
+    if np.abs(ref["rf"]).max() == 0:
+        assert np.all(rf_g == 0)
+    else:
+        assert rel_l2(rf_g, ref["rf"]) <= 1e-4, rel_l2(rf_g, ref["rf"])
+        live = ref["b"] > -60.0
+        assert np.max(np.abs(b.cpu().numpy() - ref["b"])[live]) <= 0.05
+    ctx.release_scene(sid)
+    return ref
+
+
+def test_ragged_record_image_and_element_count(ctx):
+    # 2044 samples (not a multiple of the splat's 8 samples per thread), 37 lines (not a multiple
+    # of the DAS tiles), 20 elements
+    ref = parity(ctx, P.two_layer(n_rays=300, n_samples=2044, n_lines=37, n_depth=256, n_elem=20))
+    assert np.abs(ref["rf"]).max() > 0
+
+
+def test_scatterers_without_triangles(ctx):
+    parity(ctx, no_triangles(P.slab_scatterers(n_rays=600)))
+
+
+def test_empty_scene_records_nothing(ctx):
+    w = no_triangles(P.two_layer(n_rays=50))
+    ref = parity(ctx, w)
+    assert np.abs(ref["rf"]).max() == 0
+
+
+def test_one_ray_per_element_and_budget_of_one_interaction(ctx):
+    ref = parity(ctx, no_triangles(P.slab_scatterers(n_rays=1, n_scat=20000, k_max=1)))
+    assert np.abs(ref["rf"]).max() > 0
+
+
+def test_largest_interaction_budget(ctx):
+    w = P.inclusions(n_regions=3, n_scat=2000, n_rays=60, k_max=15, n_samples=2048, angles_deg=[0.0], n_lines=64,
+                     n_depth=512, n_elem=32, n_lat=24, n_lon=40)
+    parity(ctx, w)
+
+
+def test_twenty_transmits_das_and_transposed_das(ctx):
+    acq = P.acquisition(24, 0.3 * MM, 1024, list(np.linspace(-15, 15, 20)), 1, 1, 1540.0)
+    img = P.image(37, 256, -3.5 * MM, 3.5 * MM, 1 * MM, 18 * MM)
+    rng = np.random.default_rng(9)
+    n = 8000
+    rf = O.splat(acq, 5e6, rng.integers(0, 20, n), rng.integers(0, 24, n), rng.uniform(0, 1024 / 40e6, n),
+                 rng.normal(size=n)).astype(np.float32).astype(np.float64)
+    ref = O.das(acq, img, rf)
+    bound = 2e-3 * O.das(acq, img, np.abs(rf)) + 1e-6 * np.abs(ref).max()
+    got = ctx.das(acq, img, dev(rf)).cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound)
+    gi = rng.normal(size=ref.shape).astype(np.float32).astype(np.float64)
+    adj = ctx.das_adjoint(acq, img, dev(gi)).double().cpu().numpy()
+    aref = O.das_adjoint(acq, img, gi)
+    assert rel_l2(adj, aref) <= 1e-3
+
+
+@pytest.mark.parametrize("ns", [4, 1020])
+def test_splat_tiny_and_ragged_records(ctx, ns):
+    acq = P.acquisition(6, 0.3 * MM, ns, [0.0, 4.0], 1, 1, 1540.0)
+    rng = np.random.default_rng(ns)
+    n = 3000
+    tx = rng.integers(0, 2, n).astype(np.int32)
+    e = rng.integers(0, 6, n).astype(np.int32)
+    tau = rng.uniform(-1e-6, ns / 40e6 + 1e-6, n).astype(np.float32).astype(np.float64)
+    a = rng.normal(size=n).astype(np.float32).astype(np.float64)
+    ref = O.splat(acq, 5e6, tx, e, tau, a)
+    got = ctx.splat(acq, 5e6, dev(tx, torch.int32), dev(e, torch.int32), dev(tau), dev(a)).cpu().numpy()
+    assert rel_l2(got, ref) <= 1e-5, rel_l2(got, ref)
+
+
+def test_empty_batch_is_a_no_op(ctx):
+    from paper_2604_15017_gb300 import usrt
+
+    assert usrt.Batch(ctx, []).run() == []
