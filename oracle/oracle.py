@@ -82,6 +82,7 @@ def lib():
             l.ora_splat_adjoint.argtypes = [D, D, C.c_double, C.c_longlong, I, I, D, D, D, D, D, D]
             l.ora_das.argtypes = [D, D, D, D, D]
             l.ora_das_adjoint.argtypes = [D, D, D, D, D]
+            l.ora_das_acq_vjp.argtypes = [D, D, D, D, D, D]
             l.ora_hilbert.argtypes = [D, C.c_int, D]
             l.ora_envelope.argtypes = [D, D, D]
             l.ora_log_compress.restype = C.c_longlong
@@ -91,6 +92,7 @@ def lib():
             l.ora_envlog_vjp.argtypes = [D, D, D, D]
             l.ora_replay_rf.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D]
             l.ora_gradient.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
+            l.ora_gradient_acq.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
             l.ora_trace_injected.restype = C.c_int
             l.ora_trace_injected.argtypes = [C.c_void_p, D, C.c_int, D, D, C.c_uint64, D, D, C.c_double, C.c_double,
                                              C.c_int, C.c_longlong, I, C.c_int, C.c_int, C.c_int, I, D, D, I, I, D]
@@ -246,6 +248,21 @@ class Run:
                            out.ctypes.data_as(D))
         return out
 
+    def gradient_acq(self, grf, theta=None, nthreads=None, full=False):
+        """d/d(c_bf, steering angles) of sum(grf * RF) on this frozen realisation: the acquisition
+        parameters move the emission time stamps only (Sec. 2.3.1).  Returns 1 + n_tx values, or
+        with ``full`` the scene gradient followed by them."""
+        th = self.theta if theta is None else np.asarray(theta, np.float64)
+        th, thp = _d(th)
+        g, gp = _d(grf)
+        n_th = 3 * self.M + 2
+        out = np.zeros(n_th + 1 + len(self.acq["angles"]))
+        rc = lib().ora_gradient_acq(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
+                                    out.ctypes.data_as(D))
+        if rc != 0:
+            raise ValueError("too many parameters for the oracle's dual numbers")
+        return out if full else out[n_th:]
+
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.ora_run_free(self.h)
@@ -289,6 +306,17 @@ def das_adjoint(acq, img, gi):
     out = np.zeros((len(acq["angles"]), acq["n_elem"], acq["n_samples"]))
     g, gp = _d(gi)
     lib().ora_das_adjoint(a_arr.ctypes.data_as(D), ang.ctypes.data_as(D), img_array(img).ctypes.data_as(D), gp,
+                          out.ctypes.data_as(D))
+    return out
+
+
+def das_acq_vjp(acq, img, rf, gi):
+    """sum_p gi(p) dI(p)/d(c_bf, steering angles), the RF held fixed: 1 + n_tx values."""
+    a_arr, ang = acq_array(acq)
+    out = np.zeros(1 + len(acq["angles"]))
+    r, rp = _d(rf)
+    g, gp = _d(gi)
+    lib().ora_das_acq_vjp(a_arr.ctypes.data_as(D), ang.ctypes.data_as(D), img_array(img).ctypes.data_as(D), rp, gp,
                           out.ctypes.data_as(D))
     return out
 

@@ -457,7 +457,19 @@ struct Phys {
   int M;
   std::vector<S> c, rho, al;
   S As, f0;
+  int acq_base = -1;  // >= 0: duals also carry d/d c_bf (slot acq_base) and d/d steering angle of
+                      // transmit t (slot acq_base + 1 + t), through the emission time stamp
 };
+
+// emission time stamp tau_tx = (x_e sin th + W/2 |sin th|) / c_bf (Sec. 2.3.1) and its
+// derivatives in c_bf and th; d|sin th|/d th = sgn(sin th) cos th with sgn(0) = 0
+void tau_acq(double&, int, int, double, double, double, const Acq&) {}
+void tau_acq(Dual& tau, int base, int tx, double tau0, double xe, double th, const Acq& q) {
+  if (base < 0) return;
+  const double st = std::sin(th), ct = std::cos(th), sg = st > 0 ? 1.0 : (st < 0 ? -1.0 : 0.0);
+  tau.d[base] += -tau0 / q.cbf;
+  tau.d[base + 1 + tx] += (xe * ct + 0.5 * q.aperture() * sg * ct) / q.cbf;
+}
 
 Phys<double> phys_double(const double* th, int M) {
   Phys<double> p;
@@ -649,7 +661,7 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
   const bool replay = rec_in != nullptr;
   const uint32_t ray32 = (uint32_t)io.ray;
   D3 o0, w0;
-  double a0, tau0;
+  double a0, tau0, xe_emit = 0.0;
   if (io.inject) {
     o0 = io.o0;
     w0 = io.w0;
@@ -666,10 +678,12 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
     a0 = PI / q.nr;
     double st = std::sin(q.angles[io.tx]);
     tau0 = (xe * st + 0.5 * q.aperture() * std::fabs(st)) / q.cbf;
+    xe_emit = xe;
   }
   V3<S> o = mk3<S>(S(o0.x), S(o0.y), S(o0.z));
   V3<S> w = mk3<S>(S(w0.x), S(w0.y), S(w0.z));
   S a(a0), tau(tau0);
+  if (!io.inject) tau_acq(tau, P.acq_base, io.tx, tau0, xe_emit, q.angles[io.tx], q);
   int m = 0;
   int xcls = CLS_NONE, xid = -1;
   std::vector<std::pair<double, int>> xs;
@@ -936,6 +950,36 @@ void das(const Acq& q, const Img& im, const double* rf, double* irf) {
           acc += hann(e, q.ne) * ((1.0 - f) * a + f * b);
         }
       irf[(size_t)l * im.nd + d] = acc;
+    }
+}
+
+// Derivative of the beamformed image in the beamforming sound speed and the steering angles,
+// contracted with an image gradient: out[0] = sum_p gi(p) dI(p)/d c_bf, out[1 + t] = sum_p
+// gi(p) dI(p)/d th_t, the RF held fixed.  d u/d c_bf = -u / c_bf; the transmit delay's
+// d/d th = (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf (sgn(0) = 0); the linear
+// interpolation's slope is that of the interval [floor(u), floor(u) + 1] holding u.
+void das_acq_vjp(const Acq& q, const Img& im, const double* rf, const double* gi, double* out) {
+  for (int t = 0; t <= q.ntx; ++t) out[t] = 0.0;
+  for (int l = 0; l < im.nl; ++l)
+    for (int d = 0; d < im.nd; ++d) {
+      double x = line_x(im, l), z = depth_z(im, d), g = gi[(size_t)l * im.nd + d];
+      if (g == 0.0) continue;
+      for (int tx = 0; tx < q.ntx; ++tx) {
+        const double th = q.angles[tx], st = std::sin(th), ct = std::cos(th);
+        const double sg = st > 0 ? 1.0 : (st < 0 ? -1.0 : 0.0);
+        const double du_dth = (x * ct - z * st + 0.5 * q.aperture() * sg * ct) * q.fs / q.cbf;
+        for (int e = 0; e < q.ne; ++e) {
+          double u = das_delay_samples(q, x, z, e, th);
+          double fl = std::floor(u);
+          long long i = (long long)fl;
+          const double* row = rf + ((size_t)tx * q.ne + e) * q.ns;
+          double a = (i >= 0 && i < q.ns) ? row[i] : 0.0;
+          double b = (i + 1 >= 0 && i + 1 < q.ns) ? row[i + 1] : 0.0;
+          const double gs = g * hann(e, q.ne) * (b - a);
+          out[0] += gs * (-u / q.cbf);
+          out[1 + tx] += gs * du_dth;
+        }
+      }
     }
 }
 
@@ -1259,6 +1303,10 @@ void ora_das(const double* acq, const double* angles, const double* img, const d
 void ora_das_adjoint(const double* acq, const double* angles, const double* img, const double* gi, double* grf) {
   das_adjoint(make_acq(acq, angles), make_img(img), gi, grf);
 }
+void ora_das_acq_vjp(const double* acq, const double* angles, const double* img, const double* rf, const double* gi,
+                     double* out) {
+  das_acq_vjp(make_acq(acq, angles), make_img(img), rf, gi, out);
+}
 void ora_hilbert(const double* x, int n, double* y) { hilbert(x, n, y); }
 void ora_envelope(const double* img, const double* irf, double* env) { envelope(make_img(img), irf, env); }
 long long ora_log_compress(const double* img, const double* env, double* b) { return log_compress(make_img(img), env, b); }
@@ -1291,13 +1339,21 @@ void ora_replay_rf(void* scene, void* rp, const double* theta, uint64_t seed, in
 
 // gradient of sum_{tx,e,n} grf[tx][e][n] * RF[tx][e][n] w.r.t. theta on the run's frozen
 // realisation (forward-mode duals through replay and the pulse; Eq. chain_rule)
-void ora_gradient(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
-                  double* gtheta) {
+// gradient of sum(grf * RF) on the frozen realisation; with_acq: also in c_bf and the steering
+// angles (through the emission time stamps), appended after the 3M + 2 scene parameters.
+// Returns -1 when the duals cannot hold that many parameters.
+static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
+                         double* gtheta, bool with_acq) {
   Run* r = (Run*)rp;
   const Scene& sc = *(Scene*)scene;
   const Acq& q = r->q;
   Phys<Dual> P = phys_dual(theta, r->M);
   int np = 3 * r->M + 2;
+  if (with_acq) {
+    P.acq_base = np;
+    np += 1 + q.ntx;
+  }
+  if (np > NP) return -1;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   int nb = std::max(1, nthreads);
   std::vector<std::vector<double>> acc(nb, std::vector<double>(np, 0.0));
@@ -1328,6 +1384,17 @@ void ora_gradient(void* scene, void* rp, const double* theta, uint64_t seed, int
     for (int b = 0; b < nb; ++b) s += acc[b][k];
     gtheta[k] = s;
   }
+  return 0;
+}
+
+void ora_gradient(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
+                  double* gtheta) {
+  gradient_impl(scene, rp, theta, seed, nthreads, grf, gtheta, false);
+}
+
+int ora_gradient_acq(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
+                     double* gtheta) {
+  return gradient_impl(scene, rp, theta, seed, nthreads, grf, gtheta, true);
 }
 
 // single injected path (tests): emission state given, optional forced interface choices,
