@@ -287,6 +287,35 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
                float* dL_drf_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Acquisition-parameter gradients: the beamforming sound speed c_bf and the steering angles  */
+/* ---------------------------------------------------------------------------------------- */
+/* These parameters enter the forward model in two places only: the emission time stamp of
+ * every ray, tau_tx = (x_e sin th + W/2 |sin th|) / c_bf with W = (N_e - 1) pitch (Sec. 2.3.1,
+ * ray emission), and the plane-wave DAS delays of Eq. das.  Neither moves a ray, so on a fixed
+ * realisation the gradient is exact (no decision depends on them).  d|sin th|/dth is taken as
+ * sgn(sin th) cos th with sgn(0) = 0, i.e. the mean of the two one-sided derivatives at th = 0.
+ * Gradient layout (dL_dacq_dev, DEVICE float[1 + n_tx], caller-owned, overwritten):
+ *   [0] = dL/dc_bf (per m/s), [1 + t] = dL/d(steering angle of transmit t) (per radian). */
+
+/* DAS part alone: sum_p dL/dI_rf(p) dI_rf(p)/d(c_bf, th_t) with the RF held fixed.  The slope
+ * of each tap is that of the linear-interpolation interval holding its delay.  rf_dev: DEVICE
+ * float[n_tx][n_elem][n_samples]; dL_dirf_dev: DEVICE float[n_lines][n_depth]. */
+int us_das_acq_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+                   const float* dL_dirf_dev, float* dL_dacq_dev, void* stream);
+
+/* Transport part alone: us_transport_vjp (same arguments, modes and record-mode requirements)
+ * that also carries each path's time adjoint at emission into dL_dacq_dev. */
+int us_transport_vjp_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                         int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev,
+                         void* stream);
+
+/* Full adjoint with the acquisition gradient: us_adjoint (same arguments and requirements) plus
+ * dL_dacq_dev = DAS part + transport part. */
+int us_adjoint_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+                   uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
+                   float* dL_dacq_dev, float* dL_drf_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Inverse problem: parameterisation and optimiser step (Sec. 3.4, Sec. 3.7, Alg. 1)         */
 /* ---------------------------------------------------------------------------------------- */
 

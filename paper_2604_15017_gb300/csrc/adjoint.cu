@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
     float3 w = f3(r0 * cp, r0 * sp, sqrtf(1.0f - u01(u.z)));
     float a = PI_F / q.nr;
     const float st0 = q.sin_tx[tx];
-    float th = (xe * st0 + 0.5f * (q.ne - 1) * q.pitch * fabsf(st0)) / q.cbf, tl = 0.0f;
+    const float tau0 = (xe * st0 + 0.5f * (q.ne - 1) * q.pitch * fabsf(st0)) / q.cbf;
+    float th = tau0, tl = 0.0f;
     int m = 0;
     int nseg = 0;
     float gxa = 0.0f, gxt = 0.0f;
@@ -323,6 +324,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       ob = obn;
       wb = wbn;
     }
+    if (A.acq_slot >= 0) {
+      // tb = dL/dtau0, tau0 = (x_e sin th + W/2 |sin th|) / c_bf (Sec. 2.3.1): its derivative in
+      // c_bf, and in this transmit's steering angle (d|sin th|/dth = sgn(sin th) cos th, sgn(0) = 0)
+      const float sg = st0 > 0.0f ? 1.0f : (st0 < 0.0f ? -1.0f : 0.0f);
+      ADD(acc[A.acq_slot], tb * (-tau0 / q.cbf));
+      ADD(acc[A.acq_slot + 1 + tx], tb * (xe + 0.5f * (q.ne - 1) * q.pitch * sg) * q.cos_tx[tx] / q.cbf);
+    }
   }
   __syncthreads();
   float* out = A.gpart + (size_t)blockIdx.x * P;
@@ -504,11 +512,16 @@ __global__ void k_active_fill(const uint8_t* pclass, uint32_t n, uint32_t* work,
   }
 }
 
-__global__ void k_grad_reduce(const float* gpart, int nblocks, int P, float* g) {
+// column sums of gpart [nblocks][P] in block order: columns [0, Ps) to g, the rest to g2
+// (added to it when acc2)
+__global__ void k_grad_reduce(const float* gpart, int nblocks, int P, int Ps, float* g, float* g2, int acc2) {
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     float s = 0.0f;
     for (int b = 0; b < nblocks; ++b) s += gpart[(size_t)b * P + p];
-    g[p] = s;
+    if (p < Ps)
+      g[p] = s;
+    else
+      g2[p - Ps] = (acc2 ? g2[p - Ps] : 0.0f) + s;
   }
 }
 
@@ -536,13 +549,17 @@ void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
 }
 cudaError_t adjoint_set_attrs() {
   cudaError_t e = cudaFuncSetAttribute(k_path_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P)));
+                                       (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ)));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_nee_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P)));
+                              (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ)));
 }
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st) {
-  k_grad_reduce<<<1, 128, 0, st>>>(gpart, nblocks, P, g);
+  k_grad_reduce<<<1, 128, 0, st>>>(gpart, nblocks, P, P, g, nullptr, 0);
+}
+void launch_grad_reduce_split(const float* gpart, int nblocks, int P, int Ps, float* g, float* g2, int acc2,
+                              cudaStream_t st) {
+  k_grad_reduce<<<1, 128, 0, st>>>(gpart, nblocks, P, Ps, g, g2, acc2);
 }
 void launch_splat_adjoint(const Acq& q, const PulseP& P, const int32_t* tx, const int32_t* e, const float* tau,
                           const float* a, long long n, const float* grf, float* ga, float* gt, float* gf, int grid,

@@ -7,6 +7,7 @@
 namespace usrt {
 
 constexpr int MAX_P = 3 * MAX_MEDIA + 2;
+constexpr int MAX_P_ACQ = MAX_P + 1 + MAX_TX;  // with the acquisition slots (c_bf, steering angles)
 
 struct PulseP {
   float f0, sig, fs, half;  // half = 4 sqrt(sigma) fs (support in samples)
@@ -27,7 +28,8 @@ struct AdjArgs {
   uint32_t n_paths;
   const float* grf;        // dL/dRF [ntx][ne][ns]
   float* gpart;            // [gridDim.x][P] per-block partial gradients
-  int P;
+  int P;                   // gradient slots: 3M + 2 scene parameters (+ 1 + ntx with acq_slot)
+  int acq_slot;            // >= 0: slot of dL/dc_bf, followed by dL/dth_t for every transmit t
   int accumulate;          // add into gpart instead of overwriting
   NeeQ nee;                // the pass's secondary-ray jobs
   NeeRes nres;             // their stored results (null members: trace them again)
@@ -46,6 +48,9 @@ void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uin
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
 cudaError_t adjoint_set_attrs();
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st);
+// columns [0, Ps) of gpart to g, the others to g2 (added to it when acc2)
+void launch_grad_reduce_split(const float* gpart, int nblocks, int P, int Ps, float* g, float* g2, int acc2,
+                              cudaStream_t st);
 void launch_splat_adjoint(const Acq& q, const PulseP& P, const int32_t* tx, const int32_t* e, const float* tau,
                           const float* a, long long n, const float* grf, float* ga, float* gt, float* gf, int grid,
                           cudaStream_t st);

@@ -28,7 +28,8 @@ enum Slot {
   W_QA_PA, W_QA_WT, W_QA_META, W_QB_PA, W_QB_WT, W_QB_META, W_HITS, W_NEE_JOB, W_NEE_JM, W_ARR, W_CNT,
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
-  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS, W_COUNT
+  W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS,
+  W_ACQ_PART, W_COUNT
 };
 
 struct SceneGPU {
@@ -1036,8 +1037,11 @@ int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, c
   return US_OK;
 }
 
-int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
-                     int mode, const float* dL_drf_dev, float* dL_dtheta_dev, void* stream) {
+// dL_dacq_dev != NULL: also the acquisition gradient (c_bf, steering angles) through the
+// emission time stamps, written (or added when acc_acq) to dL_dacq_dev[1 + ntx]
+static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                         int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev, int acc_acq,
+                         void* stream) {
   if (!ctx) return US_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   SceneGPU* sc = get_scene(ctx, scene);
@@ -1055,7 +1059,13 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
   A.med = med;
   A.acq = q;
   A.grf = dL_drf_dev;
-  A.P = 3 * med.M + 2;
+  const int Ps = 3 * med.M + 2;
+  A.P = Ps;
+  A.acq_slot = -1;
+  if (dL_dacq_dev) {
+    A.acq_slot = Ps;
+    A.P = Ps + 1 + q.ntx;
+  }
   const int grid = grid_of(ctx, 8);
   float* gpart;  // [0, grid) rows: path sweep; [grid, 2 grid): secondary rays
   CKS(ws(ctx, W_GPART, (size_t)2 * grid * A.P, st, &gpart));
@@ -1103,8 +1113,8 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
   if (mode == 0) {
     if (!ctx->L->rkey.valid || ctx->L->rkey.scene != scene || ctx->L->rkey.seed != seed || ctx->L->rkey.n_paths != n_paths ||
         ctx->L->rkey.acq.size() != sizeof q || std::memcmp(ctx->L->rkey.acq.data(), &q, sizeof q) != 0 ||
-        ctx->L->rkey.theta.size() != (size_t)A.P ||
-        std::memcmp(ctx->L->rkey.theta.data(), theta, sizeof(float) * A.P) != 0)
+        ctx->L->rkey.theta.size() != (size_t)Ps ||
+        std::memcmp(ctx->L->rkey.theta.data(), theta, sizeof(float) * Ps) != 0)
       return fail(ctx, US_ERR_STATE, "record mode needs the last forward pass, with keep_record, on the same inputs");
     CKS(sweep((const uint32_t*)ctx->L->record.p, 0, (uint32_t)n_paths, (Counters*)ctx->L->ws[W_CNT].p, 0));
   } else {
@@ -1123,10 +1133,45 @@ int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_a
   }
   {
     StageScope sc_(ctx, US_STAGE_PATH_ADJ, 1, st);
-    launch_grad_reduce(gpart, 2 * grid, A.P, dL_dtheta_dev, st);
+    launch_grad_reduce_split(gpart, 2 * grid, A.P, Ps, dL_dtheta_dev, dL_dacq_dev, acc_acq, st);
   }
   CK(cudaGetLastError());
   return US_OK;
+}
+
+int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                     int mode, const float* dL_drf_dev, float* dL_dtheta_dev, void* stream) {
+  return transport_vjp(ctx, scene, theta, acq, seed, mode, dL_drf_dev, dL_dtheta_dev, nullptr, 0, stream);
+}
+
+int us_transport_vjp_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                         int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev, void* stream) {
+  if (ctx && !dL_dacq_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  return transport_vjp(ctx, scene, theta, acq, seed, mode, dL_drf_dev, dL_dtheta_dev, dL_dacq_dev, 0, stream);
+}
+
+// S7' (DAS derivative in the acquisition parameters) contracted with dL/dI_rf; acc: add
+static int das_acq_vjp(us_ctx* ctx, const Acq& q, const Img& im, const float* rf_dev, const float* gi_dev,
+                       float* dL_dacq_dev, int acc, cudaStream_t st) {
+  float* part;
+  const int nb = das_acq_blocks(im);
+  CKS(ws(ctx, W_ACQ_PART, (size_t)nb * (1 + q.ntx), st, &part));
+  StageScope sc_(ctx, US_STAGE_DAS_ADJ, 2, st);
+  launch_das_acq(q, im, rf_dev, gi_dev, part, st);
+  launch_grad_reduce_split(part, nb, 1 + q.ntx, 0, nullptr, dL_dacq_dev, acc, st);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
+int us_das_acq_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
+                   const float* dL_dirf_dev, float* dL_dacq_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  Acq q;
+  Img im;
+  CKS(make_acq(ctx, acq, 0, q));
+  CKS(make_img(ctx, img, im));
+  if (!rf_dev || !dL_dirf_dev || !dL_dacq_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  return das_acq_vjp(ctx, q, im, rf_dev, dL_dirf_dev, dL_dacq_dev, 0, (cudaStream_t)stream);
 }
 
 int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
@@ -1140,6 +1185,24 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
   CKS(bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream, mode == 0));
   return us_transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, stream);
+}
+
+int us_adjoint_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+                   uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
+                   float* dL_dacq_dev, float* dL_drf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!dL_dacq_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  Acq q;
+  Img im;
+  CKS(make_acq(ctx, acq, seed, q));
+  CKS(make_img(ctx, img, im));
+  float* grf = dL_drf_dev;
+  if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
+  CKS(bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream, mode == 0));
+  // dL/dI_rf is left in the lane's W_GI workspace by bmode_vjp
+  CKS(das_acq_vjp(ctx, q, im, rf_dev, (const float*)ctx->L->ws[W_GI].p, dL_dacq_dev, 0, st));
+  return transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, dL_dacq_dev, 1, stream);
 }
 
 // -----------------------------------------------------------------------------------------

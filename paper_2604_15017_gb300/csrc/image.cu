@@ -585,6 +585,76 @@ __global__ void k_envlog_vjp(Img im, const float* __restrict__ irf, const float*
 }
 
 // ------------------------------------------------------------------------------------------
+// DAS derivative in the acquisition parameters (Eq. das with the delays of Sec. 2.3.1),
+// contracted with an image gradient gi, the RF held fixed:
+//   out[0] = sum_p gi(p) dI(p)/dc_bf,   out[1 + t] = sum_p gi(p) dI(p)/dth_t.
+// A tap at u = i + f has dI/du = w_e (rf[i + 1] - rf[i]) (the slope of its interpolation
+// interval); du/dc_bf = -u / c_bf, and only the transmit delay holds th_t:
+// du/dth = (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf, sgn(0) = 0.  So a pixel
+// needs, per transmit, S1 = sum_e w_e slope and S2 = sum_e w_e slope u.  One pixel per thread
+// (one pass, no grid stride), transmits in register chunks of DA_TXC; each block writes one
+// row of 1 + ntx sums, reduced in a fixed order (deterministic).
+// ------------------------------------------------------------------------------------------
+constexpr int DA_THREADS = 256, DA_TXC = 8;
+__global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const float* __restrict__ rf,
+                                                        const float* __restrict__ gi, float* part) {
+  const int npx = im.nl * im.nd;
+  const DasGeo g = das_geo(q);
+  const int p = blockIdx.x * DA_THREADS + threadIdx.x;
+  const bool valid = p < npx;
+  const int l = valid ? p / im.nd : 0, d = valid ? p - l * im.nd : 0;
+  const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
+  const float gp = valid ? __ldg(&gi[p]) : 0.0f;
+  const float kfs = q.fs / q.cbf, hw = 0.5f * (float)(q.ne - 1) * q.pitch;
+  float* out = part + (size_t)blockIdx.x * (1 + q.ntx);
+  float c0 = 0.0f;
+  for (int t0 = 0; t0 < q.ntx; t0 += DA_TXC) {
+    float2 ut[DA_TXC];
+    float s1[DA_TXC], s2[DA_TXC];
+#pragma unroll
+    for (int j = 0; j < DA_TXC; ++j) {
+      ut[j] = t0 + j < q.ntx ? das_split(das_utx(q, g, x, z, t0 + j)) : make_float2(0.0f, 0.0f);
+      s1[j] = 0.0f;
+      s2[j] = 0.0f;
+    }
+    if (gp != 0.0f) {
+      for (int e = 0; e < q.ne; ++e) {
+        const float2 ur = das_split(das_urx(q, g, x, z, e));
+        const float w = hann_w(e, q.ne);
+#pragma unroll
+        for (int j = 0; j < DA_TXC; ++j) {
+          if (t0 + j < q.ntx) {
+            int i;
+            float f;
+            das_tap(ut[j], ur, i, f);
+            const float* row = rf + ((size_t)(t0 + j) * q.ne + e) * q.ns;
+            const float a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
+            const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
+            const float sl = w * (b - a);
+            s1[j] += sl;
+            s2[j] = fmaf(sl, (float)i + f, s2[j]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < DA_TXC; ++j) {
+      const int t = t0 + j;
+      if (t < q.ntx) {  // uniform over the block
+        const float st = q.sin_tx[t], ct = q.cos_tx[t];
+        const float sg = st > 0.0f ? 1.0f : (st < 0.0f ? -1.0f : 0.0f);
+        const float du = (x.hi * ct - z.hi * st + hw * sg * ct) * kfs;
+        c0 = fmaf(gp, s2[j], c0);
+        const float v = block_sum(gp * du * s1[j]);
+        if (threadIdx.x == 0) out[1 + t] = v;
+      }
+    }
+  }
+  const float v = block_sum(c0);
+  if (threadIdx.x == 0) out[0] = -v / q.cbf;
+}
+
+// ------------------------------------------------------------------------------------------
 void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st, int* status) {
   if (status && q.ne * q.ntx <= DT_MAX_WINDOWS && das_tma_smem(q) <= (size_t)DT_SMEM_MAX &&
       ((uintptr_t)rf & 15u) == 0) {
@@ -593,6 +663,10 @@ void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int gr
     return;
   }
   k_das<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, rf, irf);
+}
+int das_acq_blocks(const Img& im) { return (im.nl * im.nd + DA_THREADS - 1) / DA_THREADS; }
+void launch_das_acq(const Acq& q, const Img& im, const float* rf, const float* gi, float* part, cudaStream_t st) {
+  k_das_acq<<<das_acq_blocks(im), DA_THREADS, 0, st>>>(q, im, rf, gi, part);
 }
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st) {
   cudaMemsetAsync(grf, 0, sizeof(float) * (size_t)q.ntx * q.ne * q.ns, st);

@@ -9,6 +9,10 @@ namespace usrt {
 void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st,
                 int* status = nullptr);
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st);
+// DAS derivative in (c_bf, steering angles) contracted with gi: das_acq_blocks(im) partial rows
+// of 1 + ntx floats into part (reduce them with launch_grad_reduce)
+int das_acq_blocks(const Img& im);
+void launch_das_acq(const Acq& q, const Img& im, const float* rf, const float* gi, float* part, cudaStream_t st);
 // envelope + log compression.  key points to 2 words (packed (E_max, argmax), barrier counter).
 // With bmode: one cooperative fused kernel when the image fits (env untouched), else envelope
 // -> env then log compression.  Without bmode: envelope -> env and the key only.

@@ -26,7 +26,8 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
            "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch",
-           "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step"]
+           "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step", "us_das_acq_vjp",
+           "us_transport_vjp_acq", "us_adjoint_acq"]
 OPT_DAS_TMA, OPT_LANES = 0, 1
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
@@ -113,6 +114,11 @@ def lib():
                                            C.c_int, VP, VP, VP]
             l.us_adjoint.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc), C.POINTER(ImgDesc),
                                      C.c_uint64, C.c_int, VP, VP, VP, VP, VP]
+            l.us_das_acq_vjp.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP, VP]
+            l.us_transport_vjp_acq.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc),
+                                               C.c_uint64, C.c_int, VP, VP, VP, VP]
+            l.us_adjoint_acq.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc),
+                                         C.POINTER(ImgDesc), C.c_uint64, C.c_int, VP, VP, VP, VP, VP, VP]
             l.us_profile.argtypes = [VP, C.c_int]
             l.us_profile_read.argtypes = [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
             l.us_launch_count.argtypes = [VP, C.POINTER(C.c_int64)]
@@ -349,6 +355,39 @@ class Context:
                                      C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
                                      _ptr(gth), _ptr(grf), _stream(stream)))
         return gth, grf
+
+    # ---- acquisition-parameter gradients: [dL/dc_bf, dL/dth_0, ..., dL/dth_{ntx-1}] ----
+    def das_acq_vjp(self, acq, img, rf, gi, stream=None):
+        """DAS part: sum_p gi(p) dI_rf(p)/d(c_bf, steering angles), the RF held fixed."""
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        out = torch.empty(1 + len(acq["angles"]), dtype=torch.float32, device=self.device)
+        self._check(lib().us_das_acq_vjp(self.h, C.byref(ad), C.byref(idesc), _ptr(rf), _ptr(gi), _ptr(out),
+                                         _stream(stream)))
+        return out
+
+    def transport_vjp_acq(self, scene, theta, acq, seed, grf, mode=MODE_RECORD, stream=None):
+        """Transport part: (dL/dtheta, dL/d(c_bf, steering angles)) from dL/dRF."""
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
+        gacq = torch.empty(1 + len(acq["angles"]), dtype=torch.float32, device=self.device)
+        self._check(lib().us_transport_vjp_acq(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)),
+                                               C.byref(ad), int(seed) & (2**64 - 1), int(mode), _ptr(grf), _ptr(gth),
+                                               _ptr(gacq), _stream(stream)))
+        return gth, gacq
+
+    def adjoint_acq(self, scene, theta, acq, img, seed, rf, gb, mode=MODE_RECORD, stream=None):
+        """Full adjoint with the acquisition gradient: (dL/dtheta, dL/d(c_bf, steering angles))."""
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
+        gacq = torch.empty(1 + len(acq["angles"]), dtype=torch.float32, device=self.device)
+        self._check(lib().us_adjoint_acq(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad),
+                                         C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
+                                         _ptr(gth), _ptr(gacq), None, _stream(stream)))
+        return gth, gacq
 
     # ---- inverse problem: parameterisation and optimiser step (Sec. 3.4, 3.7) ----
     def param_map(self, theta_u, lo, hi, out=None, stream=None):

@@ -1,0 +1,148 @@
+"""Acquisition-parameter gradients on the GPU (the beamforming sound speed c_bf and the
+steering angles, through the emission time stamps of Sec. 2.3.1 and the delays of Eq. das)
+against the FP64 oracle's derivatives, which tests/test_oracle_acq_pins.py pins to finite
+differences.
+
+The DAS part's slope is that of the interpolation interval holding each delay, so GPU and
+oracle must place the delays in the same intervals: the geometry is given in float32-exact
+values (the library takes pitch, image corners and angles as float32), and the angles are
+float32 values whose sine is a float32 to ~1e-13 (the library rounds sin and cos to float32
+before the delays).  With ordinary values a delay shifts by ~1e-6 samples and about one tap in
+3e5 lands in the neighbouring interval, moving a component by ~0.3 %.  Tolerances:
+
+* DAS part: 1e-3 relative per component (FP32 sums over ~1e5 taps; the delays agree to ~1e-7
+  samples, so the interpolation intervals are the oracle's).
+* transport part: 2e-3 relative per component, as the scene gradient's 1e-3 with the time
+  adjoint's extra FP32 steps; its scene slots equal us_transport_vjp's up to summation order.
+* full chain (GPU forward RF vs oracle forward RF, 1e-4 apart): 2e-2 relative + 1e-3 of the
+  largest component, as the scene gradient's end-to-end test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2604_15017_gb300 import phantoms as P
+
+pytestmark = pytest.mark.gpu
+
+MM = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2604_15017_gb300 import usrt
+
+    c = usrt.Context(0)
+    yield c
+    c.close()
+
+
+def dev(x, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dtype).cuda()
+
+
+def f32(x):
+    return np.asarray(x, np.float64).astype(np.float32).astype(np.float64)
+
+
+def exact_sine_angle(deg):
+    """The float32 angle near `deg` degrees whose sine is closest to a float32 value."""
+    if deg == 0:
+        return 0.0
+    t = np.float32(np.deg2rad(deg))
+    c = (t + np.arange(-50000, 50000, dtype=np.float64) * float(np.spacing(t))).astype(np.float32).astype(np.float64)
+    s = np.sin(c)
+    return float(c[np.argmin(np.abs(s - s.astype(np.float32).astype(np.float64)))])
+
+
+def exact_angles(degs):
+    return [exact_sine_angle(d) for d in degs]
+
+
+def within(got, ref, rel, floor=0.0):
+    err = np.abs(np.asarray(got, np.float64) - ref)
+    return np.all(err <= rel * np.abs(ref) + floor * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n_tx,n_lines,n_depth", [(3, 24, 128), (20, 37, 256)])
+def test_das_acq_vjp_matches_oracle(ctx, n_tx, n_lines, n_depth):
+    """20 transmits: three register chunks of 8 with a ragged tail; 37 x 256 pixels: a ragged
+    last block."""
+    degs = [-9.0, 0.0, 11.0] if n_tx == 3 else list(np.linspace(-15, 15, n_tx - 1)) + [0.0]
+    acq = dict(P.acquisition(32, float(np.float32(0.3 * MM)), 1024, degs, 1, 1, 1540.0), angles=exact_angles(degs))
+    img = P.image(n_lines, n_depth, *(float(np.float32(v)) for v in (-4 * MM, 4 * MM, 2 * MM, 18 * MM)))
+    rng = np.random.default_rng(n_tx)
+    n = 3000 * n_tx
+    rf = f32(O.splat(acq, 5e6, rng.integers(0, n_tx, n), rng.integers(0, 32, n), rng.uniform(0, 1024 / 40e6, n),
+                     rng.normal(size=n)))
+    gi = f32(rng.normal(size=(n_lines, n_depth)))
+    ref = O.das_acq_vjp(acq, img, rf, gi)
+    got = ctx.das_acq_vjp(acq, img, dev(rf), dev(gi)).double().cpu().numpy()
+    assert within(got, ref, 1e-3), np.c_[got, ref]
+
+
+def slab_with_angles(n_rays, degs):
+    w = P.slab_scatterers(n_rays=n_rays)
+    w["acq"] = dict(w["acq"], angles=exact_angles(degs))
+    return w
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_transport_vjp_acq_matches_oracle(ctx, mode):
+    w = slab_with_angles(1500, [-6.0, 0.0, 7.0])
+    sid = ctx.upload_workload(w)
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    ref = O.forward(w)
+    grf = f32(np.random.default_rng(21).normal(size=ref["rf"].shape))
+    full = ref["run"].gradient_acq(grf, full=True)
+    n_th = len(w["theta"])
+    gth, gacq = ctx.transport_vjp_acq(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode)
+    assert within(gacq.double().cpu().numpy(), full[n_th:], 2e-3), np.c_[gacq.cpu().numpy(), full[n_th:]]
+    # the scene slots are those of the plain transport VJP (the active-path list is built with
+    # atomics, so the FP32 sums may run in another order)
+    g_plain = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode)
+    assert torch.allclose(gth, g_plain, rtol=1e-5, atol=1e-6 * float(g_plain.abs().max()))
+    ctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_adjoint_acq_end_to_end(ctx, mode):
+    w = slab_with_angles(800, [-5.0, 0.0, 4.0])
+    sid = ctx.upload_workload(w)
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    ref = O.forward(w)
+    rng = np.random.default_rng(22)
+    gb = f32(rng.normal(size=ref["b"].shape) * (ref["b"] > -60))
+    gth, gacq = ctx.adjoint_acq(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, dev(gb), mode=mode)
+    # oracle: the same chain on its own forward pass
+    irf = O.das(w["acq"], w["img"], ref["rf"])
+    gi = O.envlog_vjp(w["img"], irf, gb)
+    grf = O.das_adjoint(w["acq"], w["img"], gi)
+    g_das = O.das_acq_vjp(w["acq"], w["img"], ref["rf"], gi)
+    full = ref["run"].gradient_acq(grf, full=True)
+    n_th = len(w["theta"])
+    g_ref = full[n_th:] + g_das
+    got = gacq.double().cpu().numpy()
+    assert within(got, g_ref, 2e-2, 1e-3), np.c_[got, g_ref, g_das]
+    # the scene part equals the plain adjoint's
+    gth_plain, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, dev(gb), mode=mode)
+    assert torch.allclose(gth, gth_plain, rtol=1e-4, atol=1e-5 * float(gth_plain.abs().max()))
+    ctx.release_scene(sid)
+
+
+def test_acq_gradient_is_refused_without_an_output(ctx):
+    from paper_2604_15017_gb300 import usrt
+
+    w = P.two_layer(n_rays=50)
+    sid = ctx.upload_workload(w)
+    grf = torch.zeros(ctx.rf_shape(w["acq"]), device="cuda")
+    th = usrt._f32(w["theta"])
+    ad, ang = usrt.acq_desc(w["acq"])
+    gth = torch.empty(len(th), device="cuda")
+    import ctypes as C
+
+    rc = usrt.lib().us_transport_vjp_acq(ctx.h, int(sid), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad), 1,
+                                         1, usrt._ptr(grf), usrt._ptr(gth), None, None)
+    assert rc == usrt.US_ERR_ARG
+    ctx.release_scene(sid)
