@@ -249,14 +249,14 @@ class Run:
         return out
 
     def gradient_acq(self, grf, theta=None, nthreads=None, full=False):
-        """d/d(c_bf, steering angles) of sum(grf * RF) on this frozen realisation: the acquisition
-        parameters move the emission time stamps only (Sec. 2.3.1).  Returns 1 + n_tx values, or
-        with ``full`` the scene gradient followed by them."""
+        """d/d(c_bf, pitch, steering angles) of sum(grf * RF) on this frozen realisation (Sec.
+        2.3.1 emission: time stamps and origins; Sec. 2.3.3 secondary rays: their target element
+        centres).  Returns 2 + n_tx values, or with ``full`` the scene gradient followed by them."""
         th = self.theta if theta is None else np.asarray(theta, np.float64)
         th, thp = _d(th)
         g, gp = _d(grf)
         n_th = 3 * self.M + 2
-        out = np.zeros(n_th + 1 + len(self.acq["angles"]))
+        out = np.zeros(n_th + 2 + len(self.acq["angles"]))
         rc = lib().ora_gradient_acq(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
                                     out.ctypes.data_as(D))
         if rc != 0:
@@ -311,9 +311,9 @@ def das_adjoint(acq, img, gi):
 
 
 def das_acq_vjp(acq, img, rf, gi):
-    """sum_p gi(p) dI(p)/d(c_bf, steering angles), the RF held fixed: 1 + n_tx values."""
+    """sum_p gi(p) dI(p)/d(c_bf, pitch, steering angles), the RF held fixed: 2 + n_tx values."""
     a_arr, ang = acq_array(acq)
-    out = np.zeros(1 + len(acq["angles"]))
+    out = np.zeros(2 + len(acq["angles"]))
     r, rp = _d(rf)
     g, gp = _d(gi)
     lib().ora_das_acq_vjp(a_arr.ctypes.data_as(D), ang.ctypes.data_as(D), img_array(img).ctypes.data_as(D), rp, gp,

@@ -457,18 +457,28 @@ struct Phys {
   int M;
   std::vector<S> c, rho, al;
   S As, f0;
-  int acq_base = -1;  // >= 0: duals also carry d/d c_bf (slot acq_base) and d/d steering angle of
-                      // transmit t (slot acq_base + 1 + t), through the emission time stamp
+  int acq_base = -1;  // >= 0: duals also carry the acquisition parameters: d/d c_bf (slot
+                      // acq_base), d/d pitch (acq_base + 1), d/d steering angle of transmit t
+                      // (acq_base + 2 + t)
 };
 
-// emission time stamp tau_tx = (x_e sin th + W/2 |sin th|) / c_bf (Sec. 2.3.1) and its
-// derivatives in c_bf and th; d|sin th|/d th = sgn(sin th) cos th with sgn(0) = 0
-void tau_acq(double&, int, int, double, double, double, const Acq&) {}
-void tau_acq(Dual& tau, int base, int tx, double tau0, double xe, double th, const Acq& q) {
+// Emission (Sec. 2.3.1) in the acquisition parameters.  The time stamp tau_tx = (x_e sin th +
+// W/2 |sin th|) / c_bf with W = (N_e - 1) p: d/dc_bf = -tau_tx / c_bf, d/dp = tau_tx / p (x_e
+// and W are both proportional to p), d/dth with d|sin th|/dth = sgn(sin th) cos th, sgn(0) = 0.
+// The origin's x = x_e + (u - 1/2) p = p (e - (N_e - 1)/2 + u - 1/2): d/dp = x / p.
+void emit_acq(double&, double&, int, int, double, double, double, double, const Acq&) {}
+void emit_acq(Dual& ox, Dual& tau, int base, int tx, double ox0, double tau0, double xe, double th, const Acq& q) {
   if (base < 0) return;
   const double st = std::sin(th), ct = std::cos(th), sg = st > 0 ? 1.0 : (st < 0 ? -1.0 : 0.0);
   tau.d[base] += -tau0 / q.cbf;
-  tau.d[base + 1 + tx] += (xe * ct + 0.5 * q.aperture() * sg * ct) / q.cbf;
+  tau.d[base + 1] += tau0 / q.pitch;
+  tau.d[base + 2 + tx] += (xe * ct + 0.5 * q.aperture() * sg * ct) / q.cbf;
+  ox.d[base + 1] += ox0 / q.pitch;
+}
+// an element centre x_e = p (e - (N_e - 1)/2) with its pitch derivative x_e / p
+void elem_acq(double&, int, double, const Acq&) {}
+void elem_acq(Dual& x, int base, double xe, const Acq& q) {
+  if (base >= 0) x.d[base + 1] += xe / q.pitch;
 }
 
 Phys<double> phys_double(const double* th, int M) {
@@ -584,43 +594,50 @@ Iface<S> interface_event(const V3<S>& w, const V3<S>& nin, const S& c1, const S&
 // under total internal reflection), attenuation and travel time per sub-segment in the medium
 // tracked across the crossings, receive directivity at the element.
 // ------------------------------------------------------------------------------------------
+// The target element centre carries the pitch derivative (when the duals hold it), so the
+// geometry below (length, direction, crossing distances on the crossed triangles' planes,
+// incidence cosines, directivity) is evaluated in S; which triangles are crossed is decided
+// in double.
 template <class S>
 bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, int m_start, S& gain, S& dt,
                 std::vector<std::pair<double, int>>& xs, double* frx_out) {
   D3 p = sc.sp[j];
-  D3 tgt = d3(q.elem_x(e2), 0.0, 0.0);
-  D3 dv = subd(tgt, p);
-  double D = std::sqrt(dotd(dv, dv));
-  D3 d = d3(dv.x / D, dv.y / D, dv.z / D);
-  double frx = val(f_rx<double>(std::acos(std::max(-1.0, std::min(1.0, -d.z))), q.alpha_m, q.alpha_c));
-  *frx_out = frx;
-  if (frx == 0.0) return false;
-  all_crossings(sc, p, d, D, xs);
+  S xt(q.elem_x(e2));
+  elem_acq(xt, P.acq_base, q.elem_x(e2), q);
+  V3<S> dv = mk3<S>(xt + (-p.x), S(-p.y), S(-p.z));
+  S D = sqrt(dot(dv, dv));
+  V3<S> d = scale(dv, 1.0 / D);
+  S cosd = -d.z;
+  double cv = std::max(-1.0, std::min(1.0, val(cosd)));
+  S th = (cv == val(cosd)) ? acos(cosd) : S(std::acos(cv));
+  S frx = f_rx<S>(th, q.alpha_m, q.alpha_c);
+  *frx_out = val(frx);
+  if (val(frx) == 0.0) return false;
+  all_crossings(sc, p, d3(val(d.x), val(d.y), val(d.z)), val(D), xs);
   S prodT(1.0), path_alpha(0.0);
   S time(0.0);
   int m = m_start;
-  double tprev = 0.0;
+  S tprev(0.0);
   for (size_t i = 0; i < xs.size(); ++i) {
-    double t = xs[i].first;
     int tri = xs[i].second;
-    double l = t - tprev;
+    D3 N = cross(subd(sc.v1[tri], sc.v0[tri]), subd(sc.v2[tri], sc.v0[tri]));
+    S t = dotd(subd(sc.v0[tri], p), N) / dot(d, mk3<double>(N.x, N.y, N.z));
+    S l = t - tprev;
     path_alpha = path_alpha + P.al[m] * l;
     time = time + l / P.c[m];
-    D3 n = cross(subd(sc.v1[tri], sc.v0[tri]), subd(sc.v2[tri], sc.v0[tri]));
-    double nl = std::sqrt(dotd(n, n));
-    n = d3(n.x / nl, n.y / nl, n.z / nl);
-    double dn = dotd(d, n);
+    double nl = std::sqrt(dotd(N, N));
+    D3 n = d3(N.x / nl, N.y / nl, N.z / nl);
+    double dn = val(dot(d, n));
     int m1 = dn < 0 ? sc.mfront[tri] : sc.mback[tri];
     int m2 = dn < 0 ? sc.mback[tri] : sc.mfront[tri];
-    V3<S> ws = mk3<S>(S(d.x), S(d.y), S(d.z));
     V3<S> nin = dn < 0 ? mk3<S>(S(n.x), S(n.y), S(n.z)) : mk3<S>(S(-n.x), S(-n.y), S(-n.z));
-    Iface<S> f = interface_event<S>(ws, nin, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
+    Iface<S> f = interface_event<S>(d, nin, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
     if (f.tir) return false;  // total internal reflection: no transmitted pressure
     prodT = prodT * f.T;
     m = m2;
     tprev = t;
   }
-  double l = D - tprev;
+  S l = D - tprev;
   path_alpha = path_alpha + P.al[m] * l;
   time = time + l / P.c[m];
   gain = prodT * exp(-KAPPA * P.f0 * path_alpha) * frx * (double)q.ne;
@@ -683,7 +700,7 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
   V3<S> o = mk3<S>(S(o0.x), S(o0.y), S(o0.z));
   V3<S> w = mk3<S>(S(w0.x), S(w0.y), S(w0.z));
   S a(a0), tau(tau0);
-  if (!io.inject) tau_acq(tau, P.acq_base, io.tx, tau0, xe_emit, q.angles[io.tx], q);
+  if (!io.inject) emit_acq(o.x, tau, P.acq_base, io.tx, o0.x, tau0, xe_emit, q.angles[io.tx], q);
   int m = 0;
   int xcls = CLS_NONE, xid = -1;
   std::vector<std::pair<double, int>> xs;
@@ -953,13 +970,15 @@ void das(const Acq& q, const Img& im, const double* rf, double* irf) {
     }
 }
 
-// Derivative of the beamformed image in the beamforming sound speed and the steering angles,
-// contracted with an image gradient: out[0] = sum_p gi(p) dI(p)/d c_bf, out[1 + t] = sum_p
-// gi(p) dI(p)/d th_t, the RF held fixed.  d u/d c_bf = -u / c_bf; the transmit delay's
-// d/d th = (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf (sgn(0) = 0); the linear
-// interpolation's slope is that of the interval [floor(u), floor(u) + 1] holding u.
+// Derivative of the beamformed image in the acquisition parameters, contracted with an image
+// gradient, the RF held fixed: out[0] = sum_p gi(p) dI(p)/d c_bf, out[1] = .../d pitch,
+// out[2 + t] = .../d th_t.  With u the delay in samples: d u/d c_bf = -u / c_bf; d u/d pitch =
+// (W/2 |sin th| / p - (x - x_e) / r (e - (N_e - 1)/2)) fs / c_bf (the transmit term's aperture
+// and the receive distance r to x_e = p (e - (N_e - 1)/2)); the transmit delay's d u/d th =
+// (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf (sgn(0) = 0).  dI/du is the slope of
+// the linear-interpolation interval [floor(u), floor(u) + 1] holding u.
 void das_acq_vjp(const Acq& q, const Img& im, const double* rf, const double* gi, double* out) {
-  for (int t = 0; t <= q.ntx; ++t) out[t] = 0.0;
+  for (int t = 0; t < 2 + q.ntx; ++t) out[t] = 0.0;
   for (int l = 0; l < im.nl; ++l)
     for (int d = 0; d < im.nd; ++d) {
       double x = line_x(im, l), z = depth_z(im, d), g = gi[(size_t)l * im.nd + d];
@@ -975,9 +994,12 @@ void das_acq_vjp(const Acq& q, const Img& im, const double* rf, const double* gi
           const double* row = rf + ((size_t)tx * q.ne + e) * q.ns;
           double a = (i >= 0 && i < q.ns) ? row[i] : 0.0;
           double b = (i + 1 >= 0 && i + 1 < q.ns) ? row[i + 1] : 0.0;
+          const double dx = x - q.elem_x(e), r = std::sqrt(dx * dx + z * z);
+          const double du_dp = (0.5 * (q.ne - 1) * std::fabs(st) - dx / r * (e - 0.5 * (q.ne - 1))) * q.fs / q.cbf;
           const double gs = g * hann(e, q.ne) * (b - a);
           out[0] += gs * (-u / q.cbf);
-          out[1 + tx] += gs * du_dth;
+          out[1] += gs * du_dp;
+          out[2 + tx] += gs * du_dth;
         }
       }
     }
@@ -1339,8 +1361,9 @@ void ora_replay_rf(void* scene, void* rp, const double* theta, uint64_t seed, in
 
 // gradient of sum_{tx,e,n} grf[tx][e][n] * RF[tx][e][n] w.r.t. theta on the run's frozen
 // realisation (forward-mode duals through replay and the pulse; Eq. chain_rule)
-// gradient of sum(grf * RF) on the frozen realisation; with_acq: also in c_bf and the steering
-// angles (through the emission time stamps), appended after the 3M + 2 scene parameters.
+// gradient of sum(grf * RF) on the frozen realisation; with_acq: also in c_bf, the pitch and the
+// steering angles (emission and secondary-ray targets), appended after the 3M + 2 scene
+// parameters.
 // Returns -1 when the duals cannot hold that many parameters.
 static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
                          double* gtheta, bool with_acq) {
@@ -1351,7 +1374,7 @@ static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t se
   int np = 3 * r->M + 2;
   if (with_acq) {
     P.acq_base = np;
-    np += 1 + q.ntx;
+    np += 2 + q.ntx;
   }
   if (np > NP) return -1;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);

@@ -19,18 +19,21 @@ MM = 1e-3
 
 
 def perturbed(acq, which, h):
+    """which: 0 = c_bf, 1 = pitch (relative steps), 2 + t = steering angle t (radians)"""
     a = dict(acq)
     if which == 0:
         a["c_bf"] = acq["c_bf"] * (1.0 + h)
+    elif which == 1:
+        a["pitch"] = acq["pitch"] * (1.0 + h)
     else:
         ang = list(acq["angles"])
-        ang[which - 1] = ang[which - 1] + h
+        ang[which - 2] = ang[which - 2] + h
         a["angles"] = ang
     return a
 
 
 def step(acq, which, h):
-    return acq["c_bf"] * h if which == 0 else h
+    return acq["c_bf"] * h if which == 0 else (acq["pitch"] * h if which == 1 else h)
 
 
 def test_das_acquisition_derivatives_match_finite_differences():
@@ -42,7 +45,7 @@ def test_das_acquisition_derivatives_match_finite_differences():
                  rng.normal(size=n))
     gi = rng.normal(size=(24, 128))
     g = O.das_acq_vjp(acq, img, rf, gi)
-    for which in range(4):
+    for which in range(5):
         h = 1e-9
         fp = np.sum(gi * O.das(perturbed(acq, which, h), img, rf))
         fm = np.sum(gi * O.das(perturbed(acq, which, -h), img, rf))
@@ -58,9 +61,9 @@ def test_transport_acquisition_derivatives_match_finite_differences():
     rng = np.random.default_rng(4)
     grf = rng.normal(size=ref["rf"].shape)
     g = run.gradient_acq(grf)
-    assert g.shape == (4,) and np.abs(g).max() > 0
+    assert g.shape == (5,) and np.abs(g).max() > 0
     rec0 = run.records()
-    for which in range(4):
+    for which in range(5):
         h = 1e-8
         wp = dict(w, acq=perturbed(w["acq"], which, h))
         wm = dict(w, acq=perturbed(w["acq"], which, -h))
@@ -79,5 +82,5 @@ def test_scene_gradient_unchanged_by_the_acquisition_slots():
     assert np.all(np.isfinite(g_scene))
     # the extended gradient's scene part is the plain gradient (same duals, more slots)
     full = ref["run"].gradient_acq(grf, full=True)
-    assert full.shape == (len(g_scene) + 1 + len(w["acq"]["angles"]),)
+    assert full.shape == (len(g_scene) + 2 + len(w["acq"]["angles"]),)
     assert np.allclose(full[:len(g_scene)], g_scene, rtol=1e-12, atol=1e-12 * np.abs(g_scene).max())
