@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-stages", action="store_true")
+    ap.add_argument("--acq-grad", action="store_true",
+                    help="frame: the adjoint also returns dL/d(c_bf, pitch, steering angles) (us_adjoint_acq)")
     ap.add_argument("--config", default="frame", choices=["frame", "batch", "serve", "optim"],
                     help="frame: one fwd+adj frame per step (the metric line); batch: a batch of scenes of "
                          "uneven size, batched vs one by one; serve: Poisson arrivals through the serving loop; "
@@ -447,10 +449,15 @@ def main():
     theta = w["theta"]
     st = torch.cuda.current_stream()
 
+    def adjoint(rf, gb):
+        if args.acq_grad:
+            return ctx.adjoint_acq(sid, theta, acq, img, seed, rf, gb, mode=mode)
+        return ctx.adjoint(sid, theta, acq, img, seed, rf, gb, mode=mode)[0], None
+
     def step():
         rf, b = ctx.forward(sid, theta, acq, img, seed=seed, keep_record=(mode == usrt.MODE_RECORD))
         loss, gb = ctx.loss(img, b, bref)
-        gth, _ = ctx.adjoint(sid, theta, acq, img, seed, rf, gb, mode=mode)
+        gth, gacq = adjoint(rf, gb)
         return loss, gth
 
     for _ in range(args.warmup):
@@ -493,6 +500,7 @@ def main():
     # loss and gradient device -> host each step
     bref_h = bref.cpu().pin_memory()
     gth_h = torch.empty(len(theta), dtype=torch.float32).pin_memory()
+    gacq_h = torch.empty(2 + len(acq["angles"]), dtype=torch.float32).pin_memory()
     loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
     bref_d = torch.empty_like(bref)
     torch.cuda.synchronize()
@@ -501,13 +509,15 @@ def main():
         bref_d.copy_(bref_h, non_blocking=True)
         rf, b = ctx.forward(sid, theta, acq, img, seed=seed, keep_record=(mode == usrt.MODE_RECORD))
         loss, gb = ctx.loss(img, b, bref_d)
-        gth, _ = ctx.adjoint(sid, theta, acq, img, seed, rf, gb, mode=mode)
+        gth, gacq = adjoint(rf, gb)
         gth_h.copy_(gth, non_blocking=True)
+        if gacq is not None:
+            gacq_h.copy_(gacq, non_blocking=True)
         loss_h.copy_(loss, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e = {"value": segs_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bref_h.numel() * 4,
-           "d2h_bytes_per_step": 4 * (len(theta) + 1)}
+           "d2h_bytes_per_step": 4 * (len(theta) + 1 + (gacq_h.numel() if args.acq_grad else 0))}
 
     # roofline of the dominant stage, from its live CUDA-event time over the timed region
     n_prims = int(w["tris"].shape[0] + w["scat_pos"].shape[0])
@@ -536,7 +546,8 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "inclusions-200k-tris-1e5-scatterers-16tx-1e6rays", "step": "fwd+adj",
+           "config": {"workload": "inclusions-200k-tris-1e5-scatterers-16tx-1e6rays",
+                      "step": "fwd+adj+acq" if args.acq_grad else "fwd+adj",
                       "adjoint_mode": args.mode, "paths_per_step": stats["n_paths"],
                       "segments_per_step": stats["segments"], "nee_queries_per_step": stats["nee_queries"],
                       "arrivals_per_step": stats["arrivals"], "frames_per_s": world * 1e3 / ms,

@@ -287,24 +287,29 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
                float* dL_drf_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
-/* Acquisition-parameter gradients: the beamforming sound speed c_bf and the steering angles  */
+/* Acquisition-parameter gradients: beamforming sound speed c_bf, element pitch, steer angles */
 /* ---------------------------------------------------------------------------------------- */
-/* These parameters enter the forward model in two places only: the emission time stamp of
- * every ray, tau_tx = (x_e sin th + W/2 |sin th|) / c_bf with W = (N_e - 1) pitch (Sec. 2.3.1,
- * ray emission), and the plane-wave DAS delays of Eq. das.  Neither moves a ray, so on a fixed
- * realisation the gradient is exact (no decision depends on them).  d|sin th|/dth is taken as
- * sgn(sin th) cos th with sgn(0) = 0, i.e. the mean of the two one-sided derivatives at th = 0.
- * Gradient layout (dL_dacq_dev, DEVICE float[1 + n_tx], caller-owned, overwritten):
- *   [0] = dL/dc_bf (per m/s), [1 + t] = dL/d(steering angle of transmit t) (per radian). */
+/* These parameters enter the forward model through the emission (Sec. 2.3.1: ray origins on
+ * the element faces, x = p (e - (N_e - 1)/2 + u - 1/2), and the time stamp tau_tx = (x_e sin th +
+ * W/2 |sin th|) / c_bf with W = (N_e - 1) p), through the secondary rays' targets (Sec. 2.3.3:
+ * the element centres x_e = p (e - (N_e - 1)/2)), and through the plane-wave DAS delays of
+ * Eq. das.  The gradient is that of the fixed realisation (Sec. 3.2): which element a ray
+ * reaches, and whether it reaches the array at all, are decisions held fixed, so the pitch's
+ * effect on the element binning is not part of it.  d|sin th|/dth is taken as
+ * sgn(sin th) cos th with sgn(0) = 0, the mean of the two one-sided derivatives at th = 0.
+ * Gradient layout (dL_dacq_dev, DEVICE float[2 + n_tx], caller-owned, overwritten):
+ *   [0] = dL/dc_bf (per m/s), [1] = dL/dpitch (per m),
+ *   [2 + t] = dL/d(steering angle of transmit t) (per radian). */
 
-/* DAS part alone: sum_p dL/dI_rf(p) dI_rf(p)/d(c_bf, th_t) with the RF held fixed.  The slope
+/* DAS part alone: sum_p dL/dI_rf(p) dI_rf(p)/d(c_bf, pitch, th_t) with the RF held fixed.  The slope
  * of each tap is that of the linear-interpolation interval holding its delay.  rf_dev: DEVICE
  * float[n_tx][n_elem][n_samples]; dL_dirf_dev: DEVICE float[n_lines][n_depth]. */
 int us_das_acq_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
                    const float* dL_dirf_dev, float* dL_dacq_dev, void* stream);
 
 /* Transport part alone: us_transport_vjp (same arguments, modes and record-mode requirements)
- * that also carries each path's time adjoint at emission into dL_dacq_dev. */
+ * that also carries each path's time and origin adjoints at emission, and each secondary ray's
+ * sensitivity to its target element's position, into dL_dacq_dev. */
 int us_transport_vjp_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
                          int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev,
                          void* stream);

@@ -325,11 +325,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       wb = wbn;
     }
     if (A.acq_slot >= 0) {
-      // tb = dL/dtau0, tau0 = (x_e sin th + W/2 |sin th|) / c_bf (Sec. 2.3.1): its derivative in
-      // c_bf, and in this transmit's steering angle (d|sin th|/dth = sgn(sin th) cos th, sgn(0) = 0)
+      // tb = dL/dtau0 and ob = dL/do0 at emission (Sec. 2.3.1).  tau0 = (x_e sin th + W/2 |sin th|)
+      // / c_bf: d/dc_bf = -tau0 / c_bf; x_e, W and the origin's x are proportional to the pitch p,
+      // so d/dp = tau0 / p and o0.x / p; d/dth with d|sin th|/dth = sgn(sin th) cos th, sgn(0) = 0
       const float sg = st0 > 0.0f ? 1.0f : (st0 < 0.0f ? -1.0f : 0.0f);
       ADD(acc[A.acq_slot], tb * (-tau0 / q.cbf));
-      ADD(acc[A.acq_slot + 1 + tx], tb * (xe + 0.5f * (q.ne - 1) * q.pitch * sg) * q.cos_tx[tx] / q.cbf);
+      ADD(acc[A.acq_slot + 1], (tb * tau0 + ob.x * O[0].x) / q.pitch);
+      ADD(acc[A.acq_slot + 2 + tx], tb * (xe + 0.5f * (q.ne - 1) * q.pitch * sg) * q.cos_tx[tx] / q.cbf);
     }
   }
   __syncthreads();
@@ -411,6 +413,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     const float Ga = ga * a_n;  // adjoint of log a_n
     ADD(acc[iF0], gf + Ga * (-kap * no.sum_al));
     ADD(acc[iAs], ga * a1 * sc.w * no.gain);
+    // pitch: the target x_e = p (e2 - (N_e - 1)/2) moves along x; dX below are derivatives in x_e
+    // (direction dd = (e_x - d d.x) / D, crossing distances t_c = A_c / (d.n_c), lengths, cosines)
+    const bool acq = A.acq_slot >= 0;
+    float gX = 0.0f, dt_prev = 0.0f;
+    if (acq) {  // receive directivity: d log f_rx / dX on its ramp
+      const float frx = f_rx(-d.z, q.alpha_m, q.alpha_c);
+      const float thd = acosf(fminf(1.0f, fmaxf(-1.0f, -d.z)));
+      if (thd > q.alpha_m && frx > 0.0f) {
+        const float ddz = -d.x * d.z / D;
+        gX += Ga * (-(ddz / sqrtf(fmaxf(1e-30f, 1.0f - d.z * d.z))) / (q.alpha_c - q.alpha_m)) / frx;
+      }
+    }
     float tprev = 0.0f;
     int mm_cur = m;
     for (int c = 0; c <= no.n; ++c) {
@@ -418,6 +432,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       const float l = tc - tprev;
       ADD(acc[3 * mm_cur + 2], Ga * (-kap * med.f0 * l));
       ADD(acc[3 * mm_cur + 0], gt * (-l / (med.c[mm_cur] * med.c[mm_cur])));
+      if (acq) {
+        float dtc = d.x;  // dD/dX
+        if (c < no.n) {
+          const float3 nn = xyz(__ldg(&A.S.tri_nrm[xid[c]]));
+          const float dn = dot3(d, nn);
+          dtc = -tc * ((nn.x - d.x * dn) / D) / dn;
+        }
+        gX += (Ga * (-kap * med.f0 * med.al[mm_cur]) + gt / med.c[mm_cur]) * (dtc - dt_prev);
+        dt_prev = dtc;
+      }
       if (c == no.n) break;
       const float4 nr = __ldg(&A.S.tri_nrm[xid[c]]);
       const uint32_t mm = __float_as_uint(nr.w);
@@ -444,9 +468,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       }
       ADD(acc[3 * m2 + 0], c2b);
       ADD(acc[3 * m1 + 0], c1b);
+      if (acq) {  // the transmission coefficient through its incidence cosine ci = |d.n|
+        const float dci = (dn < 0.0f ? -1.0f : 1.0f) * (nr.x - d.x * dn) / D;
+        const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
+        gX += (Ab * r2 * c2 + Bb * r1 * c1 * dct) * dci;
+      }
       mm_cur = m2;
       tprev = tc;
     }
+    if (acq) ADD(acc[A.acq_slot + 1], gX * ((float)e2 - 0.5f * (float)(q.ne - 1)));
     *seed = make_float2(ga * k_n, gt);
   }
   __syncthreads();

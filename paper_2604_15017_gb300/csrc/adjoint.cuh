@@ -7,7 +7,7 @@
 namespace usrt {
 
 constexpr int MAX_P = 3 * MAX_MEDIA + 2;
-constexpr int MAX_P_ACQ = MAX_P + 1 + MAX_TX;  // with the acquisition slots (c_bf, steering angles)
+constexpr int MAX_P_ACQ = MAX_P + 2 + MAX_TX;  // with the acquisition slots (c_bf, pitch, steering angles)
 
 struct PulseP {
   float f0, sig, fs, half;  // half = 4 sqrt(sigma) fs (support in samples)
@@ -28,8 +28,8 @@ struct AdjArgs {
   uint32_t n_paths;
   const float* grf;        // dL/dRF [ntx][ne][ns]
   float* gpart;            // [gridDim.x][P] per-block partial gradients
-  int P;                   // gradient slots: 3M + 2 scene parameters (+ 1 + ntx with acq_slot)
-  int acq_slot;            // >= 0: slot of dL/dc_bf, followed by dL/dth_t for every transmit t
+  int P;                   // gradient slots: 3M + 2 scene parameters (+ 2 + ntx with acq_slot)
+  int acq_slot;            // >= 0: slot of dL/dc_bf, then dL/dpitch, then dL/dth_t for every transmit t
   int accumulate;          // add into gpart instead of overwriting
   NeeQ nee;                // the pass's secondary-ray jobs
   NeeRes nres;             // their stored results (null members: trace them again)

@@ -1037,8 +1037,9 @@ int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, c
   return US_OK;
 }
 
-// dL_dacq_dev != NULL: also the acquisition gradient (c_bf, steering angles) through the
-// emission time stamps, written (or added when acc_acq) to dL_dacq_dev[1 + ntx]
+// dL_dacq_dev != NULL: also the acquisition gradient (c_bf, pitch, steering angles) through the
+// emission and the secondary rays' targets, written (or added when acc_acq) to
+// dL_dacq_dev[2 + ntx]
 static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
                          int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev, int acc_acq,
                          void* stream) {
@@ -1064,7 +1065,7 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
   A.acq_slot = -1;
   if (dL_dacq_dev) {
     A.acq_slot = Ps;
-    A.P = Ps + 1 + q.ntx;
+    A.P = Ps + 2 + q.ntx;
   }
   const int grid = grid_of(ctx, 8);
   float* gpart;  // [0, grid) rows: path sweep; [grid, 2 grid): secondary rays
@@ -1155,10 +1156,10 @@ static int das_acq_vjp(us_ctx* ctx, const Acq& q, const Img& im, const float* rf
                        float* dL_dacq_dev, int acc, cudaStream_t st) {
   float* part;
   const int nb = das_acq_blocks(im);
-  CKS(ws(ctx, W_ACQ_PART, (size_t)nb * (1 + q.ntx), st, &part));
+  CKS(ws(ctx, W_ACQ_PART, (size_t)nb * (2 + q.ntx), st, &part));
   StageScope sc_(ctx, US_STAGE_DAS_ADJ, 2, st);
   launch_das_acq(q, im, rf_dev, gi_dev, part, st);
-  launch_grad_reduce_split(part, nb, 1 + q.ntx, 0, nullptr, dL_dacq_dev, acc, st);
+  launch_grad_reduce_split(part, nb, 2 + q.ntx, 0, nullptr, dL_dacq_dev, acc, st);
   CK(cudaGetLastError());
   return US_OK;
 }

@@ -587,13 +587,14 @@ __global__ void k_envlog_vjp(Img im, const float* __restrict__ irf, const float*
 // ------------------------------------------------------------------------------------------
 // DAS derivative in the acquisition parameters (Eq. das with the delays of Sec. 2.3.1),
 // contracted with an image gradient gi, the RF held fixed:
-//   out[0] = sum_p gi(p) dI(p)/dc_bf,   out[1 + t] = sum_p gi(p) dI(p)/dth_t.
+//   out[0] = sum_p gi(p) dI(p)/dc_bf,  out[1] = .../dpitch,  out[2 + t] = .../dth_t.
 // A tap at u = i + f has dI/du = w_e (rf[i + 1] - rf[i]) (the slope of its interpolation
-// interval); du/dc_bf = -u / c_bf, and only the transmit delay holds th_t:
-// du/dth = (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf, sgn(0) = 0.  So a pixel
-// needs, per transmit, S1 = sum_e w_e slope and S2 = sum_e w_e slope u.  One pixel per thread
-// (one pass, no grid stride), transmits in register chunks of DA_TXC; each block writes one
-// row of 1 + ntx sums, reduced in a fixed order (deterministic).
+// interval); du/dc_bf = -u / c_bf; du/dpitch = (W/2 |sin th| / p - (x - x_e) / r (e - (N_e -
+// 1)/2)) fs / c_bf (transmit aperture and receive distance r); only the transmit delay holds
+// th_t: du/dth = (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf, sgn(0) = 0.  So a
+// pixel needs, per transmit, S1 = sum_e w_e slope and S2 = sum_e w_e slope u, and over all taps
+// sum w_e slope dr_e/dp.  One pixel per thread (one pass, no grid stride), transmits in register
+// chunks of DA_TXC; each block writes one row of 2 + ntx sums, reduced in a fixed order.
 // ------------------------------------------------------------------------------------------
 constexpr int DA_THREADS = 256, DA_TXC = 8;
 __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const float* __restrict__ rf,
@@ -605,9 +606,9 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
   const int l = valid ? p / im.nd : 0, d = valid ? p - l * im.nd : 0;
   const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
   const float gp = valid ? __ldg(&gi[p]) : 0.0f;
-  const float kfs = q.fs / q.cbf, hw = 0.5f * (float)(q.ne - 1) * q.pitch;
-  float* out = part + (size_t)blockIdx.x * (1 + q.ntx);
-  float c0 = 0.0f;
+  const float kfs = q.fs / q.cbf, hn = 0.5f * (float)(q.ne - 1), hw = hn * q.pitch;
+  float* out = part + (size_t)blockIdx.x * (2 + q.ntx);
+  float c0 = 0.0f, cp = 0.0f;
   for (int t0 = 0; t0 < q.ntx; t0 += DA_TXC) {
     float2 ut[DA_TXC];
     float s1[DA_TXC], s2[DA_TXC];
@@ -621,6 +622,9 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
       for (int e = 0; e < q.ne; ++e) {
         const float2 ur = das_split(das_urx(q, g, x, z, e));
         const float w = hann_w(e, q.ne);
+        const float ce = (float)e - hn;
+        const float dx = x.hi - ce * q.pitch;
+        const float drp = -dx * ce * kfs / sqrtf(fmaf(dx, dx, z.hi * z.hi));  // d(receive delay)/dp
 #pragma unroll
         for (int j = 0; j < DA_TXC; ++j) {
           if (t0 + j < q.ntx) {
@@ -633,6 +637,7 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
             const float sl = w * (b - a);
             s1[j] += sl;
             s2[j] = fmaf(sl, (float)i + f, s2[j]);
+            cp = fmaf(sl, drp, cp);
           }
         }
       }
@@ -645,13 +650,16 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
         const float sg = st > 0.0f ? 1.0f : (st < 0.0f ? -1.0f : 0.0f);
         const float du = (x.hi * ct - z.hi * st + hw * sg * ct) * kfs;
         c0 = fmaf(gp, s2[j], c0);
+        cp = fmaf(s1[j], hn * fabsf(st) * kfs, cp);
         const float v = block_sum(gp * du * s1[j]);
-        if (threadIdx.x == 0) out[1 + t] = v;
+        if (threadIdx.x == 0) out[2 + t] = v;
       }
     }
   }
-  const float v = block_sum(c0);
-  if (threadIdx.x == 0) out[0] = -v / q.cbf;
+  const float v0 = block_sum(c0);
+  if (threadIdx.x == 0) out[0] = -v0 / q.cbf;
+  const float v1 = block_sum(gp * cp);
+  if (threadIdx.x == 0) out[1] = v1;
 }
 
 // ------------------------------------------------------------------------------------------

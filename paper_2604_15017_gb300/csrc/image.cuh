@@ -9,8 +9,8 @@ namespace usrt {
 void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st,
                 int* status = nullptr);
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st);
-// DAS derivative in (c_bf, steering angles) contracted with gi: das_acq_blocks(im) partial rows
-// of 1 + ntx floats into part (reduce them with launch_grad_reduce)
+// DAS derivative in (c_bf, pitch, steering angles) contracted with gi: das_acq_blocks(im)
+// partial rows of 2 + ntx floats into part (reduce them with launch_grad_reduce_split)
 int das_acq_blocks(const Img& im);
 void launch_das_acq(const Acq& q, const Img& im, const float* rf, const float* gi, float* part, cudaStream_t st);
 // envelope + log compression.  key points to 2 words (packed (E_max, argmax), barrier counter).

@@ -356,34 +356,34 @@ class Context:
                                      _ptr(gth), _ptr(grf), _stream(stream)))
         return gth, grf
 
-    # ---- acquisition-parameter gradients: [dL/dc_bf, dL/dth_0, ..., dL/dth_{ntx-1}] ----
+    # ---- acquisition-parameter gradients: [dL/dc_bf, dL/dpitch, dL/dth_0, ..., dL/dth_{ntx-1}] ----
     def das_acq_vjp(self, acq, img, rf, gi, stream=None):
-        """DAS part: sum_p gi(p) dI_rf(p)/d(c_bf, steering angles), the RF held fixed."""
+        """DAS part: sum_p gi(p) dI_rf(p)/d(c_bf, pitch, steering angles), the RF held fixed."""
         ad, ang = acq_desc(acq)
         idesc = img_desc(img)
-        out = torch.empty(1 + len(acq["angles"]), dtype=torch.float32, device=self.device)
+        out = torch.empty(2 + len(acq["angles"]), dtype=torch.float32, device=self.device)
         self._check(lib().us_das_acq_vjp(self.h, C.byref(ad), C.byref(idesc), _ptr(rf), _ptr(gi), _ptr(out),
                                          _stream(stream)))
         return out
 
     def transport_vjp_acq(self, scene, theta, acq, seed, grf, mode=MODE_RECORD, stream=None):
-        """Transport part: (dL/dtheta, dL/d(c_bf, steering angles)) from dL/dRF."""
+        """Transport part: (dL/dtheta, dL/d(c_bf, pitch, steering angles)) from dL/dRF."""
         th = _f32(theta)
         ad, ang = acq_desc(acq)
         gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
-        gacq = torch.empty(1 + len(acq["angles"]), dtype=torch.float32, device=self.device)
+        gacq = torch.empty(2 + len(acq["angles"]), dtype=torch.float32, device=self.device)
         self._check(lib().us_transport_vjp_acq(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)),
                                                C.byref(ad), int(seed) & (2**64 - 1), int(mode), _ptr(grf), _ptr(gth),
                                                _ptr(gacq), _stream(stream)))
         return gth, gacq
 
     def adjoint_acq(self, scene, theta, acq, img, seed, rf, gb, mode=MODE_RECORD, stream=None):
-        """Full adjoint with the acquisition gradient: (dL/dtheta, dL/d(c_bf, steering angles))."""
+        """Full adjoint with the acquisition gradient: (dL/dtheta, dL/d(c_bf, pitch, steering angles))."""
         th = _f32(theta)
         ad, ang = acq_desc(acq)
         idesc = img_desc(img)
         gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
-        gacq = torch.empty(1 + len(acq["angles"]), dtype=torch.float32, device=self.device)
+        gacq = torch.empty(2 + len(acq["angles"]), dtype=torch.float32, device=self.device)
         self._check(lib().us_adjoint_acq(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad),
                                          C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
                                          _ptr(gth), _ptr(gacq), None, _stream(stream)))

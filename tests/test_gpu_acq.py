@@ -1,7 +1,7 @@
-"""Acquisition-parameter gradients on the GPU (the beamforming sound speed c_bf and the
-steering angles, through the emission time stamps of Sec. 2.3.1 and the delays of Eq. das)
-against the FP64 oracle's derivatives, which tests/test_oracle_acq_pins.py pins to finite
-differences.
+"""Acquisition-parameter gradients on the GPU (the beamforming sound speed c_bf, the element
+pitch and the steering angles, through the emission of Sec. 2.3.1, the secondary rays' target
+elements of Sec. 2.3.3 and the delays of Eq. das) against the FP64 oracle's derivatives, which
+tests/test_oracle_acq_pins.py pins to finite differences.
 
 The DAS part's slope is that of the interpolation interval holding each delay, so GPU and
 oracle must place the delays in the same intervals: the geometry is given in float32-exact
@@ -14,8 +14,8 @@ before the delays).  With ordinary values a delay shifts by ~1e-6 samples and ab
   samples, so the interpolation intervals are the oracle's).
 * transport part: 2e-3 relative per component, as the scene gradient's 1e-3 with the time
   adjoint's extra FP32 steps; its scene slots equal us_transport_vjp's up to summation order.
-* full chain (GPU forward RF vs oracle forward RF, 1e-4 apart): 2e-2 relative + 1e-3 of the
-  largest component, as the scene gradient's end-to-end test.
+* full chain: its parts on the same inputs as the oracle's, within 2e-3 of the two parts'
+  magnitudes (they cancel in some components).
 """
 import numpy as np
 import pytest
@@ -83,8 +83,10 @@ def test_das_acq_vjp_matches_oracle(ctx, n_tx, n_lines, n_depth):
 
 
 def slab_with_angles(n_rays, degs):
+    """The slab phantom with float32-exact pitch and image corners and exact-sine angles."""
     w = P.slab_scatterers(n_rays=n_rays)
-    w["acq"] = dict(w["acq"], angles=exact_angles(degs))
+    w["acq"] = dict(w["acq"], angles=exact_angles(degs), pitch=float(np.float32(w["acq"]["pitch"])))
+    w["img"] = dict(w["img"], **{k: float(np.float32(w["img"][k])) for k in ("x0", "x1", "z0", "z1")})
     return w
 
 
@@ -108,25 +110,36 @@ def test_transport_vjp_acq_matches_oracle(ctx, mode):
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_adjoint_acq_end_to_end(ctx, mode):
+    """The full chain equals its two parts issued by hand (same kernels, FP32 summation order
+    aside), and each part matches the oracle's on the same inputs (the GPU's RF, dL/dI_rf and
+    dL/dRF; the envelope/log VJP that makes them is parity-tested on its own).  The DAS and
+    transport parts cancel to a few per cent in some components (a longer array moves where
+    echoes are recorded and where the beamformer looks alike), so the bound is relative to
+    |DAS part| + |transport part|."""
     w = slab_with_angles(800, [-5.0, 0.0, 4.0])
     sid = ctx.upload_workload(w)
-    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    acq, img = w["acq"], w["img"]
+    rf, b = ctx.forward(sid, w["theta"], acq, img, seed=w["seed"], keep_record=True)
     ref = O.forward(w)
     rng = np.random.default_rng(22)
-    gb = f32(rng.normal(size=ref["b"].shape) * (ref["b"] > -60))
-    gth, gacq = ctx.adjoint_acq(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, dev(gb), mode=mode)
-    # oracle: the same chain on its own forward pass
-    irf = O.das(w["acq"], w["img"], ref["rf"])
-    gi = O.envlog_vjp(w["img"], irf, gb)
-    grf = O.das_adjoint(w["acq"], w["img"], gi)
-    g_das = O.das_acq_vjp(w["acq"], w["img"], ref["rf"], gi)
-    full = ref["run"].gradient_acq(grf, full=True)
-    n_th = len(w["theta"])
-    g_ref = full[n_th:] + g_das
+    gb_d = dev(rng.normal(size=ref["b"].shape) * (ref["b"] > -60))
+    gth, gacq = ctx.adjoint_acq(sid, w["theta"], acq, img, w["seed"], rf, gb_d, mode=mode)
     got = gacq.double().cpu().numpy()
-    assert within(got, g_ref, 2e-2, 1e-3), np.c_[got, g_ref, g_das]
+    # the two parts by hand
+    gi_d = ctx.envlog_vjp(img, ctx.das(acq, img, rf), gb_d)
+    grf_d = ctx.das_adjoint(acq, img, gi_d)
+    p_das = ctx.das_acq_vjp(acq, img, rf, gi_d).double().cpu().numpy()
+    p_tr = ctx.transport_vjp_acq(sid, w["theta"], acq, w["seed"], grf_d, mode=mode)[1].double().cpu().numpy()
+    size = np.abs(p_das) + np.abs(p_tr)
+    assert np.all(np.abs(got - (p_das + p_tr)) <= 1e-4 * size + 1e-6 * size.max()), np.c_[got, p_das + p_tr]
+    # each part against the oracle on the same inputs
+    rf_g, gi_g, grf_g = (t.double().cpu().numpy() for t in (rf, gi_d, grf_d))
+    g_das = O.das_acq_vjp(acq, img, rf_g, gi_g)
+    g_tr = ref["run"].gradient_acq(grf_g)
+    size = np.abs(g_das) + np.abs(g_tr)
+    assert np.all(np.abs(got - (g_das + g_tr)) <= 2e-3 * size + 1e-4 * size.max()), np.c_[got, g_das + g_tr, g_das]
     # the scene part equals the plain adjoint's
-    gth_plain, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, dev(gb), mode=mode)
+    gth_plain, _ = ctx.adjoint(sid, w["theta"], acq, img, w["seed"], rf, gb_d, mode=mode)
     assert torch.allclose(gth, gth_plain, rtol=1e-4, atol=1e-5 * float(gth_plain.abs().max()))
     ctx.release_scene(sid)
 
