@@ -154,7 +154,7 @@ int us_set_option(us_ctx* ctx, int option, int value);
 enum {
   US_STAGE_GENERATE = 0, US_STAGE_TRAVERSE, US_STAGE_INTERACT, US_STAGE_NEE, US_STAGE_SPLAT_SORT,
   US_STAGE_SPLAT_ROWS, US_STAGE_DAS, US_STAGE_ENVLOG, US_STAGE_LOSS, US_STAGE_ENVLOG_VJP, US_STAGE_DAS_ADJ,
-  US_STAGE_NEE_ADJ, US_STAGE_PATH_ADJ, US_STAGE_OTHER, US_N_STAGES
+  US_STAGE_NEE_ADJ, US_STAGE_PATH_ADJ, US_STAGE_OTHER, US_STAGE_DAS_ACQ, US_N_STAGES
 };
 
 /* enable != 0 starts recording stage events (and clears what was accumulated); 0 stops. */

@@ -1157,7 +1157,7 @@ static int das_acq_vjp(us_ctx* ctx, const Acq& q, const Img& im, const float* rf
   float* part;
   const int nb = das_acq_blocks(im);
   CKS(ws(ctx, W_ACQ_PART, (size_t)nb * (2 + q.ntx), st, &part));
-  StageScope sc_(ctx, US_STAGE_DAS_ADJ, 2, st);
+  StageScope sc_(ctx, US_STAGE_DAS_ACQ, 2, st);
   launch_das_acq(q, im, rf_dev, gi_dev, part, st);
   launch_grad_reduce_split(part, nb, 2 + q.ntx, 0, nullptr, dL_dacq_dev, acc, st);
   CK(cudaGetLastError());

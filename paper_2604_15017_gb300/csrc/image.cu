@@ -592,13 +592,21 @@ __global__ void k_envlog_vjp(Img im, const float* __restrict__ irf, const float*
 // interval); du/dc_bf = -u / c_bf; du/dpitch = (W/2 |sin th| / p - (x - x_e) / r (e - (N_e -
 // 1)/2)) fs / c_bf (transmit aperture and receive distance r); only the transmit delay holds
 // th_t: du/dth = (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf, sgn(0) = 0.  So a
-// pixel needs, per transmit, S1 = sum_e w_e slope and S2 = sum_e w_e slope u, and over all taps
-// sum w_e slope dr_e/dp.  One pixel per thread (one pass, no grid stride), transmits in register
-// chunks of DA_TXC; each block writes one row of 2 + ntx sums, reduced in a fixed order.
+// pixel needs, per transmit, S1 = sum_e w_e slope, and over all its taps sum w_e slope u and
+// sum w_e slope du/dp.  One pixel per thread (one pass, no grid stride), elements outer and
+// transmits inner as in k_das, so the receive delay, its pitch derivative and the element
+// weight are evaluated once per (pixel, element); the transmit delays and the per-transmit
+// sums S1 sit in shared memory in thread-major rows; the other two sums are per-pixel scalars
+// (their transmit weights are known before the sum).  Each block writes one
+// row of 2 + ntx sums, reduced in a fixed order (deterministic).
 // ------------------------------------------------------------------------------------------
-constexpr int DA_THREADS = 256, DA_TXC = 8;
+constexpr int DA_THREADS = 256;
+__host__ __device__ constexpr size_t das_acq_smem(int ntx) { return (sizeof(float2) + sizeof(float)) * DA_THREADS * ntx; }
 __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const float* __restrict__ rf,
                                                         const float* __restrict__ gi, float* part) {
+  extern __shared__ float2 da_sm[];
+  float2* ut_s = da_sm;                                              // [ntx][DA_THREADS]
+  float* s1_s = reinterpret_cast<float*>(da_sm + q.ntx * DA_THREADS);  // [ntx][DA_THREADS]
   const int npx = im.nl * im.nd;
   const DasGeo g = das_geo(q);
   const int p = blockIdx.x * DA_THREADS + threadIdx.x;
@@ -607,56 +615,41 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
   const ff x = grid_coord(im.x0, im.x1, l, im.nl), z = grid_coord(im.z0, im.z1, d, im.nd);
   const float gp = valid ? __ldg(&gi[p]) : 0.0f;
   const float kfs = q.fs / q.cbf, hn = 0.5f * (float)(q.ne - 1), hw = hn * q.pitch;
-  float* out = part + (size_t)blockIdx.x * (2 + q.ntx);
-  float c0 = 0.0f, cp = 0.0f;
-  for (int t0 = 0; t0 < q.ntx; t0 += DA_TXC) {
-    float2 ut[DA_TXC];
-    float s1[DA_TXC], s2[DA_TXC];
-#pragma unroll
-    for (int j = 0; j < DA_TXC; ++j) {
-      ut[j] = t0 + j < q.ntx ? das_split(das_utx(q, g, x, z, t0 + j)) : make_float2(0.0f, 0.0f);
-      s1[j] = 0.0f;
-      s2[j] = 0.0f;
-    }
-    if (gp != 0.0f) {
-      for (int e = 0; e < q.ne; ++e) {
-        const float2 ur = das_split(das_urx(q, g, x, z, e));
-        const float w = hann_w(e, q.ne);
-        const float ce = (float)e - hn;
-        const float dx = x.hi - ce * q.pitch;
-        const float drp = -dx * ce * kfs / sqrtf(fmaf(dx, dx, z.hi * z.hi));  // d(receive delay)/dp
-#pragma unroll
-        for (int j = 0; j < DA_TXC; ++j) {
-          if (t0 + j < q.ntx) {
-            int i;
-            float f;
-            das_tap(ut[j], ur, i, f);
-            const float* row = rf + ((size_t)(t0 + j) * q.ne + e) * q.ns;
-            const float a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
-            const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
-            const float sl = w * (b - a);
-            s1[j] += sl;
-            s2[j] = fmaf(sl, (float)i + f, s2[j]);
-            cp = fmaf(sl, drp, cp);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < DA_TXC; ++j) {
-      const int t = t0 + j;
-      if (t < q.ntx) {  // uniform over the block
-        const float st = q.sin_tx[t], ct = q.cos_tx[t];
-        const float sg = st > 0.0f ? 1.0f : (st < 0.0f ? -1.0f : 0.0f);
-        const float du = (x.hi * ct - z.hi * st + hw * sg * ct) * kfs;
-        c0 = fmaf(gp, s2[j], c0);
-        cp = fmaf(s1[j], hn * fabsf(st) * kfs, cp);
-        const float v = block_sum(gp * du * s1[j]);
-        if (threadIdx.x == 0) out[2 + t] = v;
+  for (int t = 0; t < q.ntx; ++t) {
+    ut_s[t * DA_THREADS + threadIdx.x] = das_split(das_utx(q, g, x, z, t));
+    s1_s[t * DA_THREADS + threadIdx.x] = 0.0f;
+  }
+  float c0 = 0.0f, cp = 0.0f;  // sum slope u; sum slope du/dp
+  if (gp != 0.0f) {
+    for (int e = 0; e < q.ne; ++e) {
+      const float2 ur = das_split(das_urx(q, g, x, z, e));
+      const float w = hann_w(e, q.ne);
+      const float ce = (float)e - hn;
+      const float dx = x.hi - ce * q.pitch;
+      const float drp = -dx * ce * kfs / sqrtf(fmaf(dx, dx, z.hi * z.hi));  // d(receive delay)/dp
+      for (int t = 0; t < q.ntx; ++t) {
+        int i;
+        float f;
+        das_tap(ut_s[t * DA_THREADS + threadIdx.x], ur, i, f);
+        const float* row = rf + ((size_t)t * q.ne + e) * q.ns;
+        const float a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
+        const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
+        const float sl = w * (b - a);
+        s1_s[t * DA_THREADS + threadIdx.x] += sl;
+        c0 = fmaf(sl, (float)i + f, c0);
+        cp = fmaf(sl, fmaf(hn * fabsf(q.sin_tx[t]), kfs, drp), cp);
       }
     }
   }
-  const float v0 = block_sum(c0);
+  float* out = part + (size_t)blockIdx.x * (2 + q.ntx);
+  for (int t = 0; t < q.ntx; ++t) {
+    const float st = q.sin_tx[t], ct = q.cos_tx[t];
+    const float sg = st > 0.0f ? 1.0f : (st < 0.0f ? -1.0f : 0.0f);
+    const float du = (x.hi * ct - z.hi * st + hw * sg * ct) * kfs;
+    const float v = block_sum(gp * du * s1_s[t * DA_THREADS + threadIdx.x]);
+    if (threadIdx.x == 0) out[2 + t] = v;
+  }
+  const float v0 = block_sum(gp * c0);
   if (threadIdx.x == 0) out[0] = -v0 / q.cbf;
   const float v1 = block_sum(gp * cp);
   if (threadIdx.x == 0) out[1] = v1;
@@ -674,7 +667,7 @@ void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int gr
 }
 int das_acq_blocks(const Img& im) { return (im.nl * im.nd + DA_THREADS - 1) / DA_THREADS; }
 void launch_das_acq(const Acq& q, const Img& im, const float* rf, const float* gi, float* part, cudaStream_t st) {
-  k_das_acq<<<das_acq_blocks(im), DA_THREADS, 0, st>>>(q, im, rf, gi, part);
+  k_das_acq<<<das_acq_blocks(im), DA_THREADS, das_acq_smem(q.ntx), st>>>(q, im, rf, gi, part);
 }
 void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st) {
   cudaMemsetAsync(grf, 0, sizeof(float) * (size_t)q.ntx * q.ne * q.ns, st);
@@ -736,6 +729,8 @@ cudaError_t image_set_attrs(int nd) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_das_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(float2) * DAS_THREADS * MAX_TX));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_das_acq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)das_acq_smem(MAX_TX));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_envelope, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float2) * (size_t)(nd + nd / 2)));

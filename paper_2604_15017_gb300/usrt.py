@@ -30,7 +30,7 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_transport_vjp_acq", "us_adjoint_acq"]
 OPT_DAS_TMA, OPT_LANES = 0, 1
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
-          "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other"]
+          "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq"]
 
 
 class UsrtError(RuntimeError):
