@@ -93,6 +93,7 @@ def lib():
             l.ora_replay_rf.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D]
             l.ora_gradient.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
             l.ora_gradient_acq.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
+            l.ora_gradient_shape.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, C.c_int, D, D]
             l.ora_trace_injected.restype = C.c_int
             l.ora_trace_injected.argtypes = [C.c_void_p, D, C.c_int, D, D, C.c_uint64, D, D, C.c_double, C.c_double,
                                              C.c_int, C.c_longlong, I, C.c_int, C.c_int, C.c_int, I, D, D, I, I, D]
@@ -259,6 +260,25 @@ class Run:
         out = np.zeros(n_th + 2 + len(self.acq["angles"]))
         rc = lib().ora_gradient_acq(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
                                     out.ctypes.data_as(D))
+        if rc != 0:
+            raise ValueError("too many parameters for the oracle's dual numbers")
+        return out if full else out[n_th:]
+
+    def gradient_shape(self, grf, vtan, theta=None, nthreads=None, full=False):
+        """Directional derivatives of sum(grf * RF) along vertex tangent fields vtan
+        [n_shape, n_tris, 9] (d tris / d q_j) on this frozen realisation: hit distances, normals
+        and secondary-ray crossings follow the moved triangles, the decisions stay.  Returns
+        n_shape values, or with ``full`` the scene gradient followed by them."""
+        th = self.theta if theta is None else np.asarray(theta, np.float64)
+        th, thp = _d(th)
+        g, gp = _d(grf)
+        vt = np.ascontiguousarray(vtan, dtype=np.float64)
+        n_shape = vt.shape[0]
+        assert vt.shape[1:] == (len(self.scene.tris), 9)
+        n_th = 3 * self.M + 2
+        out = np.zeros(n_th + n_shape)
+        rc = lib().ora_gradient_shape(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(),
+                                      gp, n_shape, vt.ctypes.data_as(D), out.ctypes.data_as(D))
         if rc != 0:
             raise ValueError("too many parameters for the oracle's dual numbers")
         return out if full else out[n_th:]

@@ -460,6 +460,9 @@ struct Phys {
   int acq_base = -1;  // >= 0: duals also carry the acquisition parameters: d/d c_bf (slot
                       // acq_base), d/d pitch (acq_base + 1), d/d steering angle of transmit t
                       // (acq_base + 2 + t)
+  int shape_base = -1;          // >= 0: slots shape_base + j carry d/d q_j of n_shape shape parameters,
+  int n_shape = 0;              // whose vertex tangents d v / d q_j are vtan[(j * n_tris + tri) * 9 + 3 k + a]
+  const double* vtan = nullptr;  // (vertex k of triangle tri, coordinate a)
 };
 
 // Emission (Sec. 2.3.1) in the acquisition parameters.  The time stamp tau_tx = (x_e sin th +
@@ -475,6 +478,33 @@ void emit_acq(Dual& ox, Dual& tau, int base, int tx, double ox0, double tau0, do
   tau.d[base + 2 + tx] += (xe * ct + 0.5 * q.aperture() * sg * ct) / q.cbf;
   ox.d[base + 1] += ox0 / q.pitch;
 }
+// Vertex k of triangle tri; with shape slots its dual parts are the tangents d v / d q_j.
+void shape_dual(double&, const Phys<double>&, int, int, int, int) {}
+void shape_dual(Dual& x, const Phys<Dual>& P, int nt, int tri, int k, int a) {
+  for (int j = 0; j < P.n_shape; ++j) x.d[P.shape_base + j] += P.vtan[((size_t)j * nt + tri) * 9 + 3 * k + a];
+}
+template <class S>
+V3<S> tri_vtx(const Scene& sc, const Phys<S>& P, int tri, int k) {
+  const D3& v = k == 0 ? sc.v0[tri] : (k == 1 ? sc.v1[tri] : sc.v2[tri]);
+  V3<S> r = mk3<S>(S(v.x), S(v.y), S(v.z));
+  if (P.shape_base >= 0) {
+    shape_dual(r.x, P, sc.nt, tri, k, 0);
+    shape_dual(r.y, P, sc.nt, tri, k, 1);
+    shape_dual(r.z, P, sc.nt, tri, k, 2);
+  }
+  return r;
+}
+template <class S>
+V3<S> cross3(const V3<S>& a, const V3<S>& b) {
+  return mk3<S>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// unnormalised normal (v1 - v0) x (v2 - v0) of a triangle, and its first vertex
+template <class S>
+V3<S> tri_normal(const Scene& sc, const Phys<S>& P, int tri, V3<S>& v0) {
+  v0 = tri_vtx(sc, P, tri, 0);
+  return cross3(sub(tri_vtx(sc, P, tri, 1), v0), sub(tri_vtx(sc, P, tri, 2), v0));
+}
+
 // an element centre x_e = p (e - (N_e - 1)/2) with its pitch derivative x_e / p
 void elem_acq(double&, int, double, const Acq&) {}
 void elem_acq(Dual& x, int base, double xe, const Acq& q) {
@@ -594,10 +624,10 @@ Iface<S> interface_event(const V3<S>& w, const V3<S>& nin, const S& c1, const S&
 // under total internal reflection), attenuation and travel time per sub-segment in the medium
 // tracked across the crossings, receive directivity at the element.
 // ------------------------------------------------------------------------------------------
-// The target element centre carries the pitch derivative (when the duals hold it), so the
-// geometry below (length, direction, crossing distances on the crossed triangles' planes,
-// incidence cosines, directivity) is evaluated in S; which triangles are crossed is decided
-// in double.
+// The target element centre carries the pitch derivative and the triangles their shape
+// tangents (when the duals hold them), so the geometry below (length, direction, crossing
+// distances on the crossed triangles' planes, incidence cosines, directivity) is evaluated in
+// S; which triangles are crossed is decided in double.
 template <class S>
 bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, int m_start, S& gain, S& dt,
                 std::vector<std::pair<double, int>>& xs, double* frx_out) {
@@ -618,19 +648,20 @@ bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, 
   S time(0.0);
   int m = m_start;
   S tprev(0.0);
+  const V3<S> ps = mk3<S>(S(p.x), S(p.y), S(p.z));
   for (size_t i = 0; i < xs.size(); ++i) {
     int tri = xs[i].second;
-    D3 N = cross(subd(sc.v1[tri], sc.v0[tri]), subd(sc.v2[tri], sc.v0[tri]));
-    S t = dotd(subd(sc.v0[tri], p), N) / dot(d, mk3<double>(N.x, N.y, N.z));
+    V3<S> v0;
+    V3<S> N = tri_normal(sc, P, tri, v0);
+    S t = dot(sub(v0, ps), N) / dot(d, N);  // the crossing on the triangle's plane
     S l = t - tprev;
     path_alpha = path_alpha + P.al[m] * l;
     time = time + l / P.c[m];
-    double nl = std::sqrt(dotd(N, N));
-    D3 n = d3(N.x / nl, N.y / nl, N.z / nl);
+    V3<S> n = scale(N, 1.0 / sqrt(dot(N, N)));
     double dn = val(dot(d, n));
     int m1 = dn < 0 ? sc.mfront[tri] : sc.mback[tri];
     int m2 = dn < 0 ? sc.mback[tri] : sc.mfront[tri];
-    V3<S> nin = dn < 0 ? mk3<S>(S(n.x), S(n.y), S(n.z)) : mk3<S>(S(-n.x), S(-n.y), S(-n.z));
+    V3<S> nin = dn < 0 ? n : scale(n, -1.0);
     Iface<S> f = interface_event<S>(d, nin, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
     if (f.tir) return false;  // total internal reflection: no transmitted pressure
     prodT = prodT * f.T;
@@ -741,8 +772,9 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
     } else if (h.cls == CLS_XDCR) {
       t = -o.z / w.z;
     } else if (h.cls == CLS_TRI) {
-      D3 N = cross(subd(sc.v1[h.id], sc.v0[h.id]), subd(sc.v2[h.id], sc.v0[h.id]));
-      t = dot(sub(mk3<S>(S(sc.v0[h.id].x), S(sc.v0[h.id].y), S(sc.v0[h.id].z)), o), N) / dot(w, N);
+      V3<S> v0;
+      V3<S> N = tri_normal(sc, P, h.id, v0);
+      t = dot(sub(v0, o), N) / dot(w, N);
     } else {
       V3<S> d = sub(mk3<S>(S(sc.sp[h.id].x), S(sc.sp[h.id].y), S(sc.sp[h.id].z)), o);
       t = dot(d, w);
@@ -778,15 +810,13 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
     }
     U4 u = philox(ray32, (uint32_t)io.tx, q.stream, (uint32_t)(k + 1), k0, k1);
     if (h.cls == CLS_TRI) {
-      D3 N = cross(subd(sc.v1[h.id], sc.v0[h.id]), subd(sc.v2[h.id], sc.v0[h.id]));
-      double nl = std::sqrt(dotd(N, N));
-      D3 n = d3(N.x / nl, N.y / nl, N.z / nl);
-      double wn = val(w.x) * n.x + val(w.y) * n.y + val(w.z) * n.z;
-      bool front = wn < 0;  // arriving from the side the normal points to
-      D3 nin = front ? n : d3(-n.x, -n.y, -n.z);  // unit normal pointing back into medium 1
+      V3<S> v0;
+      V3<S> N = tri_normal(sc, P, h.id, v0);
+      V3<S> n = scale(N, 1.0 / sqrt(dot(N, N)));
+      bool front = val(dot(w, n)) < 0;  // arriving from the side the normal points to
+      V3<S> nn = front ? n : scale(n, -1.0);  // unit normal pointing back into medium 1
       int m1 = front ? sc.mfront[h.id] : sc.mback[h.id];
       int m2 = front ? sc.mback[h.id] : sc.mfront[h.id];
-      V3<S> nn = mk3<S>(S(nin.x), S(nin.y), S(nin.z));
       Iface<S> f = interface_event<S>(w, nn, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
       int choice;
       if (replay) {
@@ -1365,8 +1395,10 @@ void ora_replay_rf(void* scene, void* rp, const double* theta, uint64_t seed, in
 // steering angles (emission and secondary-ray targets), appended after the 3M + 2 scene
 // parameters.
 // Returns -1 when the duals cannot hold that many parameters.
+// n_shape > 0: also in n_shape shape parameters whose vertex tangents are vtan
+// [n_shape][n_tris][9], appended after the others.
 static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
-                         double* gtheta, bool with_acq) {
+                         double* gtheta, bool with_acq, int n_shape = 0, const double* vtan = nullptr) {
   Run* r = (Run*)rp;
   const Scene& sc = *(Scene*)scene;
   const Acq& q = r->q;
@@ -1375,6 +1407,12 @@ static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t se
   if (with_acq) {
     P.acq_base = np;
     np += 2 + q.ntx;
+  }
+  if (n_shape > 0) {
+    P.shape_base = np;
+    P.n_shape = n_shape;
+    P.vtan = vtan;
+    np += n_shape;
   }
   if (np > NP) return -1;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
@@ -1418,6 +1456,14 @@ void ora_gradient(void* scene, void* rp, const double* theta, uint64_t seed, int
 int ora_gradient_acq(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
                      double* gtheta) {
   return gradient_impl(scene, rp, theta, seed, nthreads, grf, gtheta, true);
+}
+
+// gradient in the scene parameters followed by the derivatives along n_shape vertex tangent
+// fields vtan [n_shape][n_tris][9] (fixed-sample: the hit and crossed triangles held fixed)
+int ora_gradient_shape(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
+                       int n_shape, const double* vtan, double* gtheta) {
+  if (n_shape < 1) return -1;
+  return gradient_impl(scene, rp, theta, seed, nthreads, grf, gtheta, false, n_shape, vtan);
 }
 
 // single injected path (tests): emission state given, optional forced interface choices,

@@ -27,6 +27,10 @@ Workloads (the paper prints no scene data, so every one is synthetic and seeded)
   reference ones scaled by (1 +- 5 %).
 * ``slab_scatterers`` -- the two-layer slab with 1000 scatterers inside the slab (a small
   differentiation case with 8 parameters).
+* ``hollow_cylinder`` -- a tube of outer radius R = 5 mm (wall 1 mm) whose axis runs along the
+  elevation direction at 15 mm depth, in scattering tissue; the lumen holds a fluid without
+  scatterers.  ``dtris_dR`` is the vertex tangent of the radius (both surfaces move outward
+  with R, the wall thickness fixed).
 """
 from __future__ import annotations
 
@@ -88,6 +92,30 @@ def ellipsoid_mesh(center, semi, rot, n_lat=65, n_lon=130):
     flip = out < 0
     t[flip] = np.concatenate([v0[flip], v2[flip], v1[flip]], axis=1)
     return t
+
+
+def tube_mesh(radius, zc, half_len, n_phi, n_y, outward=True):
+    """Open cylinder of the given radius around the axis x = 0, z = zc (along y): n_phi x n_y
+    quads, two triangles each, normals pointing away from the axis (outward) or toward it.
+    Returns (tris (2 n_phi n_y, 9), radial unit vector of every vertex (same shape))."""
+    phi = np.linspace(0.0, 2.0 * np.pi, n_phi + 1)[:-1]
+    ys = np.linspace(-half_len, half_len, n_y + 1)
+    tris, rad = [], []
+    for i in range(n_phi):
+        a0, a1 = phi[i], phi[(i + 1) % n_phi]
+        for j in range(n_y):
+            q = [(a0, ys[j]), (a1, ys[j]), (a1, ys[j + 1]), (a0, ys[j + 1])]
+            pts = [np.array([radius * math.cos(a), y, zc + radius * math.sin(a)]) for a, y in q]
+            rds = [np.array([math.cos(a), 0.0, math.sin(a)]) for a, _ in q]
+            for k in ((0, 1, 2), (0, 2, 3)):
+                v = [pts[m] for m in k]
+                n = np.cross(v[1] - v[0], v[2] - v[0])
+                centre_dir = sum(rds[m] for m in k)
+                if (np.dot(n, centre_dir) > 0) != outward:
+                    k = (k[0], k[2], k[1])
+                tris.append(np.concatenate([pts[m] for m in k]))
+                rad.append(np.concatenate([rds[m] for m in k]))
+    return np.asarray(tris), np.asarray(rad)
 
 
 def random_rotation(rng):
@@ -210,6 +238,36 @@ def slab_scatterers(n_rays=2000, n_scat=1000, k_max=4, seed_scat=3):
                    rng.uniform(21 * MM, 37 * MM, n_scat)], axis=1)
     w.update(name="slab_scatterers", scat_pos=sp, scat_amp=rng.normal(size=n_scat))
     w["theta_target"] = perturbed_theta(w["theta"], 7)
+    return w
+
+
+def hollow_cylinder(radius=5 * MM, wall=1 * MM, depth=15 * MM, n_rays=2000, n_scat=3000, k_max=4, n_phi=96,
+                    n_y=6, half_len=8 * MM, angles_deg=(0.0,), n_elem=64, n_samples=2048, seed_scat=11):
+    """Tube along y at depth `depth` (axis): outer surface (tissue | wall) with outward normals,
+    inner surface (lumen | wall) with normals toward the axis.  Media: 0 tissue, 1 wall,
+    2 lumen fluid.  Scatterers uniform in the imaged slab outside the lumen."""
+    outer, r_out = tube_mesh(radius, depth, half_len, n_phi, n_y, outward=True)
+    inner, r_in = tube_mesh(radius - wall, depth, half_len, n_phi, n_y, outward=False)
+    tris = np.concatenate([outer, inner])
+    media = np.concatenate([np.tile(np.array([[0, 1]], dtype=np.int32), (len(outer), 1)),
+                            np.tile(np.array([[2, 1]], dtype=np.int32), (len(inner), 1))])
+    rng = np.random.default_rng(seed_scat)
+    pts = []
+    while len(pts) < n_scat:
+        p = np.array([rng.uniform(-10 * MM, 10 * MM), rng.uniform(-2 * MM, 2 * MM), rng.uniform(4 * MM, 28 * MM)])
+        if math.hypot(p[0], p[2] - depth) > radius - wall + 0.2 * MM:
+            pts.append(p)
+    sp = np.asarray(pts)
+    sa = rng.normal(size=n_scat)
+    theta = theta_vector([(1540.0, 1000.0, 0.5), (1600.0, 1100.0, 0.8), (1480.0, 1000.0, 0.002)])
+    pitch = 0.3 * MM
+    acq = acquisition(n_elem, pitch, n_samples, list(angles_deg), n_rays, k_max, 1540.0)
+    half = 0.5 * (n_elem - 1) * pitch
+    img = image(128, 512, -half, half, 5 * MM, 30 * MM)
+    w = dict(name="hollow_cylinder", tris=tris, media=media, scat_pos=sp, scat_amp=sa, r_s=0.1 * MM, M=3,
+             theta=theta, acq=acq, img=img, seed=0, radius=float(radius),
+             dtris_dR=np.concatenate([r_out, r_in]))
+    w["theta_target"] = perturbed_theta(theta, 7)
     return w
 
 
