@@ -321,6 +321,36 @@ int us_adjoint_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq
                    float* dL_dacq_dev, float* dL_drf_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Shape gradients: dL/d(triangle vertices)                                                   */
+/* ---------------------------------------------------------------------------------------- */
+/* The gradient of the fixed realisation (Sec. 3.2) with respect to the scene's triangle
+ * vertices: every path keeps the triangles it hits and the secondary rays keep the triangles
+ * they cross, while the planes and normals of those triangles move with their vertices (hit
+ * distances, specular and Snell directions, Fresnel coefficients, secondary-ray crossing
+ * distances and transmission coefficients).  Whether a ray hits a triangle at all is a
+ * decision held fixed, so silhouette terms are not part of it.  dL_dtris_dev: DEVICE
+ * float[n_tris][9] (v0, v1, v2 of each triangle in the order of the scene's tris), caller-
+ * owned, overwritten; accumulated with float atomics, so the last bits vary between runs. */
+
+/* Transport part: us_transport_vjp (same arguments, modes and record-mode requirements) plus
+ * dL/d(triangle vertices). */
+int us_transport_vjp_shape(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                           int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dtris_dev,
+                           void* stream);
+
+/* Full adjoint: us_adjoint (same arguments and requirements) plus dL/d(triangle vertices). */
+int us_adjoint_shape(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+                     uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
+                     float* dL_dtris_dev, float* dL_drf_dev, void* stream);
+
+/* Chain rule to shape parameters q_j (a radius, a thickness, ...):
+ * dL_dq_dev[j] = sum_i dL_dtris_dev[i] * dtris_dq_dev[j * 9 n_tris + i] for j < n_param, with
+ * dtris_dq_dev the parameters' vertex tangents (DEVICE float[n_param][n_tris][9]).
+ * 1 <= n_param <= 65535; fixed summation order. */
+int us_shape_param_grad(us_ctx* ctx, int64_t n_tris, const float* dL_dtris_dev, int n_param, const float* dtris_dq_dev,
+                        float* dL_dq_dev, void* stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Inverse problem: parameterisation and optimiser step (Sec. 3.4, Sec. 3.7, Alg. 1)         */
 /* ---------------------------------------------------------------------------------------- */
 

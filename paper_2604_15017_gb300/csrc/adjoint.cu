@@ -86,6 +86,29 @@ __device__ __forceinline__ float frozen_t(const SceneDev& S, uint32_t cls, uint3
   return dot3(p - o, w);
 }
 
+// Shape adjoint of one triangle (fixed-sample: the same triangle is hit or crossed, its plane
+// and normal move with its vertices): from the adjoint nhb of its unit normal n = N / |N|,
+// N = e1 x e2 (e1 = v1 - v0, e2 = v2 - v0), and the adjoint v0b of its first vertex through
+// the plane offset, the adjoints of its three vertices are added to g[9 id, 9 id + 9).
+__device__ __forceinline__ void tri_shape_add(const SceneDev& S, uint32_t id, float3 n, float3 nhb, float3 v0b,
+                                              float* g) {
+  const float4 E1 = __ldg(&S.tri_e1[id]);
+  const float3 e1 = xyz(E1), e2 = xyz(__ldg(&S.tri_e2[id]));
+  const float3 Nb = (nhb - n * dot3(n, nhb)) * (1.0f / E1.w);
+  const float3 e1b = cross3(e2, Nb), e2b = cross3(Nb, e1);
+  const float3 a = v0b - e1b - e2b;
+  float* r = g + 9 * (size_t)id;
+  atomicAdd(r + 0, a.x);
+  atomicAdd(r + 1, a.y);
+  atomicAdd(r + 2, a.z);
+  atomicAdd(r + 3, e1b.x);
+  atomicAdd(r + 4, e1b.y);
+  atomicAdd(r + 5, e1b.z);
+  atomicAdd(r + 6, e2b.x);
+  atomicAdd(r + 7, e2b.y);
+  atomicAdd(r + 8, e2b.z);
+}
+
 // ------------------------------------------------------------------------------------------
 // S12: path adjoint
 // ------------------------------------------------------------------------------------------
@@ -210,6 +233,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       const float a1 = ak * att;
       float a1b, t1b;
       float3 xb, wpb;
+      float3 nhb = f3(0.f, 0.f, 0.f);  // shape adjoint: dL/d(unit normal) of a hit triangle
       if (cls == CLS_XDCR) {
         const float cosd = -wk.z;
         const float frx = f_rx(cosd, q.alpha_m, q.alpha_c);
@@ -288,6 +312,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           ADD(acc[3 * m1 + 0], c1b);
         }
         wpb = wpb + nin * (-cib);
+        if (A.g_tris) {  // nin enters through ci = -w.nin and the outgoing direction
+          const bool refl = choice == CH_TIR || f.tir || choice == CH_REFLECT;
+          const float3 nb = wk * (-cib) + wb * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct);
+          nhb = front ? nb : nb * -1.0f;
+        }
       } else {  // scatterer
         a1b = ab + SA[k];
         t1b = tb + ST[k];
@@ -311,6 +340,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         const float den = dot3(wk, n);
         obn = obn + n * (-ttb / den);
         wbn = wbn + n * (-ttb * t / den);
+        if (A.g_tris) {  // t = (v0 - o).n / (w.n): d/dn = (v0 - x) / (w.n), d/dv0 = n / (w.n)
+          const float3 xk = ok + wk * t;
+          const float3 v0 = xyz(__ldg(&A.S.tri_v0[id]));
+          tri_shape_add(A.S, id, n, nhb + (v0 - xk) * (ttb / den), n * (ttb / den), A.g_tris);
+        }
       } else if (cls == CLS_SCAT) {
         const float3 pp = xyz(__ldg(&A.S.scat[id]));
         obn = obn + wk * (-ttb);
@@ -473,6 +507,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
         const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
         gX += (Ab * r2 * c2 + Bb * r1 * c1 * dct) * dci;
       }
+      if (A.g_tris) {  // the crossed triangle: its plane (crossing distance) and normal (ci)
+        const float3 n = xyz(nr);
+        const float tcb = (Ga * (-kap * med.f0 * med.al[mm_cur]) + gt / med.c[mm_cur]) -
+                          (Ga * (-kap * med.f0 * med.al[m2]) + gt / med.c[m2]);  // dL/dt_c
+        const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
+        const float cib = Ab * r2 * c2 + Bb * r1 * c1 * dct;
+        const float3 xc = xyz(sc) + d * tc;
+        const float3 v0 = xyz(__ldg(&A.S.tri_v0[xid[c]]));
+        const float3 nhb = d * (dn < 0.0f ? -cib : cib) + (v0 - xc) * (tcb / dn);
+        tri_shape_add(A.S, xid[c], n, nhb, n * (tcb / dn), A.g_tris);
+      }
       mm_cur = m2;
       tprev = tc;
     }
@@ -555,6 +600,22 @@ __global__ void k_grad_reduce(const float* gpart, int nblocks, int P, int Ps, fl
   }
 }
 
+// chain rule to shape parameters: out[j] = sum_i g[i] tan[j n + i], one block per parameter,
+// block-strided partial sums combined in a fixed order
+__global__ void k_tangent_dot(long long n, const float* __restrict__ g, const float* __restrict__ tan, float* out) {
+  __shared__ float red[256];
+  const float* t = tan + (size_t)blockIdx.x * n;
+  float s = 0.0f;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) s = fmaf(g[i], t[i], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
 // S1 as a standalone stream: Philox blocks with consecutive first counter words
 __global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
                               long long n, uint32_t* out) {
@@ -590,6 +651,9 @@ void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaSt
 void launch_grad_reduce_split(const float* gpart, int nblocks, int P, int Ps, float* g, float* g2, int acc2,
                               cudaStream_t st) {
   k_grad_reduce<<<1, 128, 0, st>>>(gpart, nblocks, P, Ps, g, g2, acc2);
+}
+void launch_tangent_dot(long long n, const float* g, int n_param, const float* tan, float* out, cudaStream_t st) {
+  k_tangent_dot<<<n_param, 256, 0, st>>>(n, g, tan, out);
 }
 void launch_splat_adjoint(const Acq& q, const PulseP& P, const int32_t* tx, const int32_t* e, const float* tau,
                           const float* a, long long n, const float* grf, float* ga, float* gt, float* gf, int grid,

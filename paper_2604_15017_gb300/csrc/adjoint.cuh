@@ -31,6 +31,7 @@ struct AdjArgs {
   int P;                   // gradient slots: 3M + 2 scene parameters (+ 2 + ntx with acq_slot)
   int acq_slot;            // >= 0: slot of dL/dc_bf, then dL/dpitch, then dL/dth_t for every transmit t
   int accumulate;          // add into gpart instead of overwriting
+  float* g_tris;           // non-null: dL/d(triangle vertices) [n_tris][9], accumulated atomically
   NeeQ nee;                // the pass's secondary-ray jobs
   NeeRes nres;             // their stored results (null members: trace them again)
   const Counters* cnt;     // job counts per round
@@ -51,6 +52,8 @@ void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaSt
 // columns [0, Ps) of gpart to g, the others to g2 (added to it when acc2)
 void launch_grad_reduce_split(const float* gpart, int nblocks, int P, int Ps, float* g, float* g2, int acc2,
                               cudaStream_t st);
+// dL/dq_j = sum_i g[i] * tan[j * n + i] for j < n_param (one block per parameter, fixed order)
+void launch_tangent_dot(long long n, const float* g, int n_param, const float* tan, float* out, cudaStream_t st);
 void launch_splat_adjoint(const Acq& q, const PulseP& P, const int32_t* tx, const int32_t* e, const float* tau,
                           const float* a, long long n, const float* grf, float* ga, float* gt, float* gf, int grid,
                           cudaStream_t st);

@@ -707,7 +707,8 @@ int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
     return up_bytes(v.data(), v.size() * sizeof(float), reinterpret_cast<const void**>(dst));
   };
   int s;
-  if ((s = up(o.tri_nrm, &sc.dev.tri_nrm)) || (s = up(o.tri_v0, &sc.dev.tri_v0)) || (s = up(o.scat, &sc.dev.scat)) ||
+  if ((s = up(o.tri_nrm, &sc.dev.tri_nrm)) || (s = up(o.tri_v0, &sc.dev.tri_v0)) || (s = up(o.tri_e1, &sc.dev.tri_e1)) ||
+      (s = up(o.tri_e2, &sc.dev.tri_e2)) || (s = up(o.scat, &sc.dev.scat)) ||
       (s = up(o.nodes_t, &sc.dev.nodes_t)) || (s = up(o.prims_t, &sc.dev.prims_t)) ||
       (s = up(o.nodes4, &sc.dev.nodes4)) ||
       (s = up(o.cell_sph, &sc.dev.cell_sph)) || (s = up(o.cell2, &sc.dev.cell2)) ||
@@ -1040,9 +1041,10 @@ int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, c
 // dL_dacq_dev != NULL: also the acquisition gradient (c_bf, pitch, steering angles) through the
 // emission and the secondary rays' targets, written (or added when acc_acq) to
 // dL_dacq_dev[2 + ntx]
+// dL_dtris_dev != NULL: also dL/d(triangle vertices) [n_tris][9] (overwritten)
 static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
                          int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev, int acc_acq,
-                         void* stream) {
+                         void* stream, float* dL_dtris_dev = nullptr) {
   if (!ctx) return US_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   SceneGPU* sc = get_scene(ctx, scene);
@@ -1067,6 +1069,9 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     A.acq_slot = Ps;
     A.P = Ps + 2 + q.ntx;
   }
+  A.g_tris = dL_dtris_dev;
+  if (dL_dtris_dev && sc->dev.n_tris)
+    CK(cudaMemsetAsync(dL_dtris_dev, 0, sizeof(float) * 9 * (size_t)sc->dev.n_tris, st));
   const int grid = grid_of(ctx, 8);
   float* gpart;  // [0, grid) rows: path sweep; [grid, 2 grid): secondary rays
   CKS(ws(ctx, W_GPART, (size_t)2 * grid * A.P, st, &gpart));
@@ -1151,6 +1156,25 @@ int us_transport_vjp_acq(us_ctx* ctx, uint64_t scene, const float* theta, const 
   return transport_vjp(ctx, scene, theta, acq, seed, mode, dL_drf_dev, dL_dtheta_dev, dL_dacq_dev, 0, stream);
 }
 
+int us_transport_vjp_shape(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
+                           int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dtris_dev,
+                           void* stream) {
+  if (ctx && !dL_dtris_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  return transport_vjp(ctx, scene, theta, acq, seed, mode, dL_drf_dev, dL_dtheta_dev, nullptr, 0, stream,
+                       dL_dtris_dev);
+}
+
+int us_shape_param_grad(us_ctx* ctx, int64_t n_tris, const float* dL_dtris_dev, int n_param, const float* dtris_dq_dev,
+                        float* dL_dq_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  if (n_tris < 0 || n_param < 1 || n_param > 65535 || !dL_dtris_dev || !dtris_dq_dev || !dL_dq_dev)
+    return fail(ctx, US_ERR_ARG, "invalid arguments");
+  StageScope sc_(ctx, US_STAGE_OTHER, 1, (cudaStream_t)stream);
+  launch_tangent_dot(9 * n_tris, dL_dtris_dev, n_param, dtris_dq_dev, dL_dq_dev, (cudaStream_t)stream);
+  CK(cudaGetLastError());
+  return US_OK;
+}
+
 // S7' (DAS derivative in the acquisition parameters) contracted with dL/dI_rf; acc: add
 static int das_acq_vjp(us_ctx* ctx, const Acq& q, const Img& im, const float* rf_dev, const float* gi_dev,
                        float* dL_dacq_dev, int acc, cudaStream_t st) {
@@ -1186,6 +1210,20 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
   CKS(bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream, mode == 0));
   return us_transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, stream);
+}
+
+int us_adjoint_shape(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
+                     uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
+                     float* dL_dtris_dev, float* dL_drf_dev, void* stream) {
+  if (!ctx) return US_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!dL_dtris_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  Acq q;
+  CKS(make_acq(ctx, acq, seed, q));
+  float* grf = dL_drf_dev;
+  if (!grf) CKS(ws(ctx, W_GRF, (size_t)q.ntx * q.ne * q.ns, st, &grf));
+  CKS(bmode_vjp(ctx, acq, img, rf_dev, dL_dB_dev, grf, stream, mode == 0));
+  return transport_vjp(ctx, scene, theta, acq, seed, mode, grf, dL_dtheta_dev, nullptr, 0, stream, dL_dtris_dev);
 }
 
 int us_adjoint_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,

@@ -475,6 +475,8 @@ void build_scene_host(const HostSceneIn& in, HostSceneOut& out) {
   // per-triangle normal + media, vertex 0; per-scatterer centre + amplitude
   out.tri_nrm.assign(4 * (size_t)nt, 0.0f);
   out.tri_v0.assign(4 * (size_t)nt, 0.0f);
+  out.tri_e1.assign(4 * (size_t)nt, 0.0f);
+  out.tri_e2.assign(4 * (size_t)nt, 0.0f);
   for (int i = 0; i < nt; ++i) {
     const float* t = &in.tris[9 * (size_t)i];
     double e1[3], e2[3];
@@ -493,6 +495,11 @@ void build_scene_host(const HostSceneIn& in, HostSceneOut& out) {
     out.tri_v0[4 * (size_t)i] = t[0];
     out.tri_v0[4 * (size_t)i + 1] = t[1];
     out.tri_v0[4 * (size_t)i + 2] = t[2];
+    for (int a = 0; a < 3; ++a) {
+      out.tri_e1[4 * (size_t)i + a] = (float)e1[a];
+      out.tri_e2[4 * (size_t)i + a] = (float)e2[a];
+    }
+    out.tri_e1[4 * (size_t)i + 3] = (float)l;
   }
   out.scat.assign(4 * (size_t)ns, 0.0f);
   for (int j = 0; j < ns; ++j) {

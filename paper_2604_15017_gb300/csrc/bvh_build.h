@@ -33,6 +33,8 @@ struct HostSceneOut {
   std::vector<float> cell2;     // per cell its first two entries (8 floats); see build_scatter_grid
   std::vector<float> tri_nrm;  // 4 per triangle
   std::vector<float> tri_v0;   // 4 per triangle
+  std::vector<float> tri_e1;   // 4 per triangle: (v1 - v0, |(v1 - v0) x (v2 - v0)|)
+  std::vector<float> tri_e2;   // 4 per triangle: (v2 - v0, 0)
   std::vector<float> scat;     // 4 per scatterer
 };
 

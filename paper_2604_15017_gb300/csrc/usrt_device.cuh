@@ -76,6 +76,8 @@ struct Img {
 struct SceneDev {
   const float4* tri_nrm;     // by triangle id: (unit normal, bits(m_front | m_back << 16))
   const float4* tri_v0;      // by triangle id: (v0, 0)
+  const float4* tri_e1;      // by triangle id: (v1 - v0, |(v1 - v0) x (v2 - v0)|)  (shape adjoint)
+  const float4* tri_e2;      // by triangle id: (v2 - v0, 0)
   const float4* scat;        // by scatterer id: (p, amplitude)
   const float4* nodes_t;     // triangle BVH2: n0=(c0.lo.x,c0.hi.x,c0.lo.y,c0.hi.y) n1=(same, c1)
                              // n2=(c0 z, c1 z) n3=int4(child0, child1, count0, count1)

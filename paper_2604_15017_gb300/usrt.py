@@ -27,7 +27,8 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
            "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch",
            "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step", "us_das_acq_vjp",
-           "us_transport_vjp_acq", "us_adjoint_acq"]
+           "us_transport_vjp_acq", "us_adjoint_acq", "us_transport_vjp_shape", "us_adjoint_shape",
+           "us_shape_param_grad"]
 OPT_DAS_TMA, OPT_LANES = 0, 1
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq"]
@@ -119,6 +120,11 @@ def lib():
                                                C.c_uint64, C.c_int, VP, VP, VP, VP]
             l.us_adjoint_acq.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc),
                                          C.POINTER(ImgDesc), C.c_uint64, C.c_int, VP, VP, VP, VP, VP, VP]
+            l.us_transport_vjp_shape.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc),
+                                                 C.c_uint64, C.c_int, VP, VP, VP, VP]
+            l.us_adjoint_shape.argtypes = [VP, C.c_uint64, C.POINTER(C.c_float), C.POINTER(AcqDesc),
+                                           C.POINTER(ImgDesc), C.c_uint64, C.c_int, VP, VP, VP, VP, VP, VP]
+            l.us_shape_param_grad.argtypes = [VP, C.c_int64, VP, C.c_int, VP, VP, VP]
             l.us_profile.argtypes = [VP, C.c_int]
             l.us_profile_read.argtypes = [VP, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
             l.us_launch_count.argtypes = [VP, C.POINTER(C.c_int64)]
@@ -388,6 +394,38 @@ class Context:
                                          C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
                                          _ptr(gth), _ptr(gacq), None, _stream(stream)))
         return gth, gacq
+
+    # ---- shape gradients: dL/d(triangle vertices) [n_tris, 9] ----
+    def transport_vjp_shape(self, scene, theta, acq, seed, grf, n_tris, mode=MODE_RECORD, stream=None):
+        """Transport part: (dL/dtheta, dL/dtris) from dL/dRF."""
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
+        gtris = torch.empty((int(n_tris), 9), dtype=torch.float32, device=self.device)
+        self._check(lib().us_transport_vjp_shape(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)),
+                                                 C.byref(ad), int(seed) & (2**64 - 1), int(mode), _ptr(grf),
+                                                 _ptr(gth), _ptr(gtris), _stream(stream)))
+        return gth, gtris
+
+    def adjoint_shape(self, scene, theta, acq, img, seed, rf, gb, n_tris, mode=MODE_RECORD, stream=None):
+        """Full adjoint: (dL/dtheta, dL/dtris)."""
+        th = _f32(theta)
+        ad, ang = acq_desc(acq)
+        idesc = img_desc(img)
+        gth = torch.empty(len(th), dtype=torch.float32, device=self.device)
+        gtris = torch.empty((int(n_tris), 9), dtype=torch.float32, device=self.device)
+        self._check(lib().us_adjoint_shape(self.h, int(scene), th.ctypes.data_as(C.POINTER(C.c_float)), C.byref(ad),
+                                           C.byref(idesc), int(seed) & (2**64 - 1), int(mode), _ptr(rf), _ptr(gb),
+                                           _ptr(gth), _ptr(gtris), None, _stream(stream)))
+        return gth, gtris
+
+    def shape_param_grad(self, gtris, dtris_dq, stream=None):
+        """dL/dq_j = sum dL/dtris * dtris/dq_j for the tangents dtris_dq [n_param, n_tris, 9]."""
+        n_param = int(dtris_dq.shape[0])
+        out = torch.empty(n_param, dtype=torch.float32, device=self.device)
+        self._check(lib().us_shape_param_grad(self.h, int(gtris.shape[0]), _ptr(gtris), n_param, _ptr(dtris_dq),
+                                              _ptr(out), _stream(stream)))
+        return out
 
     # ---- inverse problem: parameterisation and optimiser step (Sec. 3.4, 3.7) ----
     def param_map(self, theta_u, lo, hi, out=None, stream=None):
