@@ -13,6 +13,12 @@ the same ray realisations.
 Micro-batches are acquisitions: subsets of the transmit angles (``split_angles``: an exact
 partition of the compounded acquisition) or independent realisations with a share of the rays
 (``split_rays``: the stochastic split).
+
+Shape parameters (a radius, a wall thickness, ...) join the material ones through a
+``ShapeModel``: a mesh generator q -> (triangles, vertex tangents d tris / d q).  Every
+iteration rebuilds and re-uploads the mesh at the current q, takes the adjoint with the vertex
+gradient (``us_adjoint_shape``) and contracts it with the tangents (``us_shape_param_grad``);
+Adam then steps materials and shape together.
 """
 from __future__ import annotations
 
@@ -44,14 +50,32 @@ def split_rays(acq, n_batches):
     return out
 
 
+class ShapeModel:
+    """make(q) -> (tris [n_tris, 9], dtris_dq [n_shape, n_tris, 9]) for physical shape
+    parameters q; the scene's media, scatterers and r_s come from the workload dict w (the
+    triangle count and media must not depend on q)."""
+
+    def __init__(self, make, w, q0):
+        self.make, self.w = make, w
+        self.q0 = np.atleast_1d(np.asarray(q0, dtype=np.float64))
+
+    def upload(self, ctx, q):
+        tris, dq = self.make(np.asarray(q, dtype=np.float64))
+        w = self.w
+        sid = ctx.upload_scene(tris, w["media"], w["M"], w["scat_pos"], w["scat_amp"], w["r_s"])
+        return sid, torch.tensor(np.asarray(dq), dtype=torch.float32, device=ctx.device), len(tris)
+
+
 class InverseProblem:
     """theta: initial physical parameters (3M + 2: c, rho, alpha per medium, A_s, f0); lo / hi:
     admissible ranges (lo == hi keeps a parameter fixed); lr: one learning rate per parameter
     (or a scalar); batches: the micro-batch acquisitions; seed: base seed (micro-batch b uses
-    seed + b)."""
+    seed + b).  With a ShapeModel the parameter vector continues with its shape parameters
+    (theta, lo, hi and lr then cover 3M + 2 + n_shape entries) and ``scene`` is ignored: the
+    mesh is rebuilt at every iteration."""
 
     def __init__(self, ctx, scene, theta, lo, hi, lr, batches, img, seed, beta1=0.9, beta2=0.999, eps=1e-8,
-                 clip_norm=0.0, mode=usrt.MODE_RECORD):
+                 clip_norm=0.0, mode=usrt.MODE_RECORD, shape=None):
         dev = ctx.device
         lo = np.asarray(lo, dtype=np.float64)
         hi = np.asarray(hi, dtype=np.float64)
@@ -71,31 +95,55 @@ class InverseProblem:
         self.hyper = dict(beta1=beta1, beta2=beta2, eps=eps, clip_norm=clip_norm)
         self.k = 0
         self.targets = None
+        self.shape = shape
+        self.n_shape = 0 if shape is None else len(shape.q0)
+        self.n_mat = n - self.n_shape
 
     def physical(self):
         """The physical parameters the next iteration uses (host float32 array)."""
         self.ctx.param_map(self.theta_u, self.lo, self.hi, out=self.theta)
         return self.theta.cpu().numpy()
 
+    def _scene_at(self, q):
+        """(scene id, vertex tangents or None, n_tris, owned) for shape parameters q."""
+        if self.shape is None:
+            return self.scene, None, 0, False
+        sid, dq, nt = self.shape.upload(self.ctx, q)
+        return sid, dq, nt, True
+
     def set_targets(self, theta_target):
-        """Render each micro-batch's target image at theta_target with that micro-batch's seed."""
+        """Render each micro-batch's target image at theta_target (with a ShapeModel: materials
+        then shape parameters) with that micro-batch's seed."""
+        theta_target = np.asarray(theta_target, dtype=np.float64)
+        sid, _, _, owned = self._scene_at(theta_target[self.n_mat:])
         self.targets = []
         for b, acq in enumerate(self.batches):
-            _, bref = self.ctx.forward(self.scene, theta_target, acq, self.img, seed=self.seed + b)
+            _, bref = self.ctx.forward(sid, theta_target[:self.n_mat], acq, self.img, seed=self.seed + b)
             self.targets.append(bref.clone())
+        if owned:
+            self.ctx.release_scene(sid)
 
     def step(self):
         """One iteration of Alg. 1; returns the summed micro-batch loss (host float)."""
-        th = self.physical()
+        full = self.physical()
+        th = full[:self.n_mat]
+        sid, dq, nt, owned = self._scene_at(full[self.n_mat:])
         self.grad.zero_()
         loss = 0.0
         for b, acq in enumerate(self.batches):
-            rf, bm = self.ctx.forward(self.scene, th, acq, self.img, seed=self.seed + b,
+            rf, bm = self.ctx.forward(sid, th, acq, self.img, seed=self.seed + b,
                                       keep_record=self.mode == usrt.MODE_RECORD)
             lb, gb = self.ctx.loss(self.img, bm, self.targets[b])
-            g, _ = self.ctx.adjoint(self.scene, th, acq, self.img, self.seed + b, rf, gb, mode=self.mode)
-            self.grad += g
+            if dq is None:
+                g, _ = self.ctx.adjoint(sid, th, acq, self.img, self.seed + b, rf, gb, mode=self.mode)
+                self.grad += g
+            else:
+                g, gtris = self.ctx.adjoint_shape(sid, th, acq, self.img, self.seed + b, rf, gb, nt, mode=self.mode)
+                self.grad[:self.n_mat] += g
+                self.grad[self.n_mat:] += self.ctx.shape_param_grad(gtris, dq)
             loss += float(lb)
+        if owned:
+            self.ctx.release_scene(sid)
         self.k += 1
         self.ctx.adam_step(self.theta_u, self.grad, self.lo, self.hi, self.lr, self.m, self.v, self.k, **self.hyper)
         return loss

@@ -241,16 +241,22 @@ def slab_scatterers(n_rays=2000, n_scat=1000, k_max=4, seed_scat=3):
     return w
 
 
-def hollow_cylinder(radius=5 * MM, wall=1 * MM, depth=15 * MM, n_rays=2000, n_scat=3000, k_max=4, n_phi=96,
-                    n_y=6, half_len=8 * MM, angles_deg=(0.0,), n_elem=64, n_samples=2048, seed_scat=11):
-    """Tube along y at depth `depth` (axis): outer surface (tissue | wall) with outward normals,
-    inner surface (lumen | wall) with normals toward the axis.  Media: 0 tissue, 1 wall,
-    2 lumen fluid.  Scatterers uniform in the imaged slab outside the lumen."""
+def hollow_cylinder_mesh(radius=5 * MM, wall=1 * MM, depth=15 * MM, half_len=8 * MM, n_phi=96, n_y=6):
+    """The tube's triangles and media and d tris / d radius (both surfaces move outward, the
+    wall thickness fixed): outer surface (tissue | wall) with outward normals, inner surface
+    (lumen | wall) with normals toward the axis."""
     outer, r_out = tube_mesh(radius, depth, half_len, n_phi, n_y, outward=True)
     inner, r_in = tube_mesh(radius - wall, depth, half_len, n_phi, n_y, outward=False)
-    tris = np.concatenate([outer, inner])
     media = np.concatenate([np.tile(np.array([[0, 1]], dtype=np.int32), (len(outer), 1)),
                             np.tile(np.array([[2, 1]], dtype=np.int32), (len(inner), 1))])
+    return np.concatenate([outer, inner]), media, np.concatenate([r_out, r_in])
+
+
+def hollow_cylinder(radius=5 * MM, wall=1 * MM, depth=15 * MM, n_rays=2000, n_scat=3000, k_max=4, n_phi=96,
+                    n_y=6, half_len=8 * MM, angles_deg=(0.0,), n_elem=64, n_samples=2048, seed_scat=11):
+    """Tube along y at depth `depth` (axis), see hollow_cylinder_mesh.  Media: 0 tissue,
+    1 wall, 2 lumen fluid.  Scatterers uniform in the imaged slab outside the lumen."""
+    tris, media, dtris_dR = hollow_cylinder_mesh(radius, wall, depth, half_len, n_phi, n_y)
     rng = np.random.default_rng(seed_scat)
     pts = []
     while len(pts) < n_scat:
@@ -265,8 +271,7 @@ def hollow_cylinder(radius=5 * MM, wall=1 * MM, depth=15 * MM, n_rays=2000, n_sc
     half = 0.5 * (n_elem - 1) * pitch
     img = image(128, 512, -half, half, 5 * MM, 30 * MM)
     w = dict(name="hollow_cylinder", tris=tris, media=media, scat_pos=sp, scat_amp=sa, r_s=0.1 * MM, M=3,
-             theta=theta, acq=acq, img=img, seed=0, radius=float(radius),
-             dtris_dR=np.concatenate([r_out, r_in]))
+             theta=theta, acq=acq, img=img, seed=0, radius=float(radius), dtris_dR=dtris_dR)
     w["theta_target"] = perturbed_theta(theta, 7)
     return w
 
