@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-stages", action="store_true")
+    ap.add_argument("--shape-grad", action="store_true",
+                    help="frame: the adjoint also returns dL/d(triangle vertices) (us_adjoint_shape)")
     ap.add_argument("--acq-grad", action="store_true",
                     help="frame: the adjoint also returns dL/d(c_bf, pitch, steering angles) (us_adjoint_acq)")
     ap.add_argument("--config", default="frame", choices=["frame", "batch", "serve", "optim"],
@@ -449,9 +451,13 @@ def main():
     theta = w["theta"]
     st = torch.cuda.current_stream()
 
+    n_tris = int(w["tris"].shape[0])
+
     def adjoint(rf, gb):
         if args.acq_grad:
             return ctx.adjoint_acq(sid, theta, acq, img, seed, rf, gb, mode=mode)
+        if args.shape_grad:
+            return ctx.adjoint_shape(sid, theta, acq, img, seed, rf, gb, n_tris, mode=mode)
         return ctx.adjoint(sid, theta, acq, img, seed, rf, gb, mode=mode)[0], None
 
     def step():
@@ -500,7 +506,8 @@ def main():
     # loss and gradient device -> host each step
     bref_h = bref.cpu().pin_memory()
     gth_h = torch.empty(len(theta), dtype=torch.float32).pin_memory()
-    gacq_h = torch.empty(2 + len(acq["angles"]), dtype=torch.float32).pin_memory()
+    gacq_h = torch.empty((n_tris, 9) if args.shape_grad else (2 + len(acq["angles"]),),
+                         dtype=torch.float32).pin_memory()
     loss_h = torch.empty(1, dtype=torch.float32).pin_memory()
     bref_d = torch.empty_like(bref)
     torch.cuda.synchronize()
@@ -517,7 +524,7 @@ def main():
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e = {"value": segs_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bref_h.numel() * 4,
-           "d2h_bytes_per_step": 4 * (len(theta) + 1 + (gacq_h.numel() if args.acq_grad else 0))}
+           "d2h_bytes_per_step": 4 * (len(theta) + 1 + (gacq_h.numel() if (args.acq_grad or args.shape_grad) else 0))}
 
     # roofline of the dominant stage, from its live CUDA-event time over the timed region
     n_prims = int(w["tris"].shape[0] + w["scat_pos"].shape[0])
@@ -547,7 +554,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "inclusions-200k-tris-1e5-scatterers-16tx-1e6rays",
-                      "step": "fwd+adj+acq" if args.acq_grad else "fwd+adj",
+                      "step": "fwd+adj" + ("+acq" if args.acq_grad else ("+shape" if args.shape_grad else "")),
                       "adjoint_mode": args.mode, "paths_per_step": stats["n_paths"],
                       "segments_per_step": stats["segments"], "nee_queries_per_step": stats["nee_queries"],
                       "arrivals_per_step": stats["arrivals"], "frames_per_s": world * 1e3 / ms,

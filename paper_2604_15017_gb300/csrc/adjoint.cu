@@ -119,6 +119,11 @@ constexpr int ADJ_THREADS = 128;
 #define ADD(slot, v) ((slot) += (v))
 __host__ __device__ constexpr int adj_row_stride(int P) { return P | 1; }
 
+// Options compiled in, so that the plain adjoint carries none of their code: bit 0 = the
+// acquisition slots (acq_slot), bit 1 = the vertex gradient (g_tris).
+constexpr int ADJ_ACQ = 1, ADJ_SHAPE = 2;
+
+template <int OPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
   extern __shared__ float gsm[];
   const Acq& q = A.acq;
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           ADD(acc[3 * m1 + 0], c1b);
         }
         wpb = wpb + nin * (-cib);
-        if (A.g_tris) {  // nin enters through ci = -w.nin and the outgoing direction
+        if (OPT & ADJ_SHAPE) {  // nin enters through ci = -w.nin and the outgoing direction
           const bool refl = choice == CH_TIR || f.tir || choice == CH_REFLECT;
           const float3 nb = wk * (-cib) + wb * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct);
           nhb = front ? nb : nb * -1.0f;
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         const float den = dot3(wk, n);
         obn = obn + n * (-ttb / den);
         wbn = wbn + n * (-ttb * t / den);
-        if (A.g_tris) {  // t = (v0 - o).n / (w.n): d/dn = (v0 - x) / (w.n), d/dv0 = n / (w.n)
+        if (OPT & ADJ_SHAPE) {  // t = (v0 - o).n / (w.n): d/dn = (v0 - x) / (w.n), d/dv0 = n / (w.n)
           const float3 xk = ok + wk * t;
           const float3 v0 = xyz(__ldg(&A.S.tri_v0[id]));
           tri_shape_add(A.S, id, n, nhb + (v0 - xk) * (ttb / den), n * (ttb / den), A.g_tris);
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       ob = obn;
       wb = wbn;
     }
-    if (A.acq_slot >= 0) {
+    if (OPT & ADJ_ACQ) {
       // tb = dL/dtau0 and ob = dL/do0 at emission (Sec. 2.3.1).  tau0 = (x_e sin th + W/2 |sin th|)
       // / c_bf: d/dc_bf = -tau0 / c_bf; x_e, W and the origin's x are proportional to the pitch p,
       // so d/dp = tau0 / p and o0.x / p; d/dth with d|sin th|/dth = sgn(sin th) cos th, sgn(0) = 0
@@ -384,6 +389,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
 // tau_n = tau' + sum l / c go to theta, and the seeds (dL/da', dL/dtau') are left for the
 // path's reverse sweep.
 // ------------------------------------------------------------------------------------------
+template <int OPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
   extern __shared__ float gsm[];
   const Acq& q = A.acq;
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     ADD(acc[iAs], ga * a1 * sc.w * no.gain);
     // pitch: the target x_e = p (e2 - (N_e - 1)/2) moves along x; dX below are derivatives in x_e
     // (direction dd = (e_x - d d.x) / D, crossing distances t_c = A_c / (d.n_c), lengths, cosines)
-    const bool acq = A.acq_slot >= 0;
+    constexpr bool acq = (OPT & ADJ_ACQ) != 0;
     float gX = 0.0f, dt_prev = 0.0f;
     if (acq) {  // receive directivity: d log f_rx / dX on its ramp
       const float frx = f_rx(-d.z, q.alpha_m, q.alpha_c);
@@ -507,7 +513,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
         const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
         gX += (Ab * r2 * c2 + Bb * r1 * c1 * dct) * dci;
       }
-      if (A.g_tris) {  // the crossed triangle: its plane (crossing distance) and normal (ci)
+      if (OPT & ADJ_SHAPE) {  // the crossed triangle: its plane (crossing distance) and normal (ci)
         const float3 n = xyz(nr);
         const float tcb = (Ga * (-kap * med.f0 * med.al[mm_cur]) + gt / med.c[mm_cur]) -
                           (Ga * (-kap * med.f0 * med.al[m2]) + gt / med.c[m2]);  // dL/dt_c
@@ -625,8 +631,15 @@ __global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
   }
 }
 
+static int adj_opt(const AdjArgs& a) { return (a.acq_slot >= 0 ? ADJ_ACQ : 0) | (a.g_tris ? ADJ_SHAPE : 0); }
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
-  k_nee_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);
+  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);
+  switch (adj_opt(a)) {
+    case 0: k_nee_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 1: k_nee_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 2: k_nee_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    default: k_nee_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+  }
 }
 void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint8_t* pclass,
                          uint32_t* active, int grid, cudaStream_t st) {
@@ -636,14 +649,24 @@ void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uin
   k_active_fill<<<grid, 256, 0, st>>>(pclass, n_paths, work, active);
 }
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
-  k_path_adjoint<<<grid, ADJ_THREADS, sizeof(float) * ADJ_THREADS * adj_row_stride(a.P), st>>>(a);
+  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);
+  switch (adj_opt(a)) {
+    case 0: k_path_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 1: k_path_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 2: k_path_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    default: k_path_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+  }
 }
 cudaError_t adjoint_set_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_path_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ)));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_nee_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ)));
+  const int sm = (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ));
+  const void* ks[8] = {(const void*)k_path_adjoint<0>, (const void*)k_path_adjoint<1>, (const void*)k_path_adjoint<2>,
+                       (const void*)k_path_adjoint<3>, (const void*)k_nee_adjoint<0>, (const void*)k_nee_adjoint<1>,
+                       (const void*)k_nee_adjoint<2>, (const void*)k_nee_adjoint<3>};
+  for (const void* k : ks) {
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st) {
   k_grad_reduce<<<1, 128, 0, st>>>(gpart, nblocks, P, P, g, nullptr, 0);
