@@ -30,7 +30,8 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 # flat descriptor layouts (mirrors the enums of usrt_oracle.cpp)
 ACQ_KEYS = ["n_elem", "pitch", "h_el", "n_tx", "fs", "n_samples", "k_max", "n_rays", "bw", "alpha_m",
             "alpha_c", "c_bf", "split_mode", "split_q", "stream_id", "tx_elem"]
-IMG_KEYS = ["n_lines", "n_depth", "x0", "x1", "z0", "z1", "dr_db", "lambda1", "lambda2"]
+IMG_KEYS = ["n_lines", "n_depth", "x0", "x1", "z0", "z1", "dr_db", "lambda1", "lambda2", "f_number"]
+IMG_DEFAULTS = {"dr_db": 60.0, "lambda1": 0.0, "lambda2": 1.0, "f_number": 0.0}
 
 CLS_NONE, CLS_XDCR, CLS_TRI, CLS_SCAT = 0, 1, 2, 3
 CH_NONE, CH_REFLECT, CH_TRANSMIT, CH_TIR = 0, 1, 2, 3
@@ -124,7 +125,7 @@ def acq_array(acq):
 
 
 def img_array(img):
-    return np.array([float(img[k]) for k in IMG_KEYS], dtype=np.float64)
+    return np.array([float(img[k] if k in img else IMG_DEFAULTS[k]) for k in IMG_KEYS], dtype=np.float64)
 
 
 # --------------------------------------------------------------------------------------------

@@ -170,7 +170,7 @@ enum {
   A_NE = 0, A_PITCH, A_HEL, A_NTX, A_FS, A_NS, A_KMAX, A_NR, A_BW, A_ALPHA_M, A_ALPHA_C, A_CBF,
   A_SPLIT_MODE, A_SPLIT_Q, A_STREAM, A_TX_ELEM, A_COUNT
 };
-enum { I_NL = 0, I_ND, I_X0, I_X1, I_Z0, I_Z1, I_DR, I_L1, I_L2, I_COUNT };
+enum { I_NL = 0, I_ND, I_X0, I_X1, I_Z0, I_Z1, I_DR, I_L1, I_L2, I_FNUM, I_COUNT };
 
 struct Acq {
   int ne, ntx, ns, kmax, nr, split_mode, tx_elem;
@@ -209,6 +209,7 @@ Acq make_acq(const double* a, const double* angles) {
 struct Img {
   int nl, nd;
   double x0, x1, z0, z1, dr, l1, l2;
+  double fnum;  // receive F-number of the dynamic aperture (<= 0: the whole array)
 };
 Img make_img(const double* p) {
   Img m;
@@ -221,6 +222,7 @@ Img make_img(const double* p) {
   m.dr = p[I_DR];
   m.l1 = p[I_L1];
   m.l2 = p[I_L2];
+  m.fnum = p[I_FNUM];
   return m;
 }
 double line_x(const Img& m, int l) { return m.nl > 1 ? m.x0 + (m.x1 - m.x0) * l / (m.nl - 1) : m.x0; }
@@ -970,6 +972,24 @@ void splat_direct(const Acq& q, double f0, const Arrival<double>* arr, long long
 // ------------------------------------------------------------------------------------------
 double hann(int e, int ne) { return 0.5 * (1.0 - std::cos(2.0 * PI * (e + 1) / (ne + 1))); }
 
+// Element weight w_e(x, z) of Eq. das.  F-number <= 0: the pixel-independent Hann window over
+// the array.  F-number F > 0 (dynamic receive aperture): a Hann window cos^2(pi xi / 2), |xi| < 1,
+// of the element's lateral offset from the pixel, xi = (x_e - x) / a, over the half-width
+// a = max(z / (2 F), p) (at least one pitch, so that shallow pixels keep an aperture).
+// dw_dp: the weight's derivative in the pitch p (x_e = p (e - (N_e - 1)/2); a = p when clamped).
+double apod(const Acq& q, const Img& im, double x, double z, int e, double* dw_dp = nullptr) {
+  if (dw_dp) *dw_dp = 0.0;
+  if (!(im.fnum > 0)) return hann(e, q.ne);
+  const double ce = e - 0.5 * (q.ne - 1);
+  const bool clamped = z / (2.0 * im.fnum) < q.pitch;
+  const double a = clamped ? q.pitch : z / (2.0 * im.fnum);
+  const double xi = (ce * q.pitch - x) / a;
+  if (std::fabs(xi) >= 1.0) return 0.0;
+  const double c = std::cos(0.5 * PI * xi);
+  if (dw_dp) *dw_dp = -0.5 * PI * std::sin(PI * xi) * (ce - (clamped ? xi : 0.0)) / a;
+  return c * c;
+}
+
 // two-way plane-wave delay in samples for pixel (x, z), element e, steering angle th  [Eq. das]
 double das_delay_samples(const Acq& q, double x, double z, int e, double th) {
   double st = std::sin(th), ct = std::cos(th);
@@ -994,7 +1014,7 @@ void das(const Acq& q, const Img& im, const double* rf, double* irf) {
           const double* row = rf + ((size_t)tx * q.ne + e) * q.ns;
           double a = (i >= 0 && i < q.ns) ? row[i] : 0.0;
           double b = (i + 1 >= 0 && i + 1 < q.ns) ? row[i + 1] : 0.0;
-          acc += hann(e, q.ne) * ((1.0 - f) * a + f * b);
+          acc += apod(q, im, x, z, e) * ((1.0 - f) * a + f * b);
         }
       irf[(size_t)l * im.nd + d] = acc;
     }
@@ -1006,7 +1026,8 @@ void das(const Acq& q, const Img& im, const double* rf, double* irf) {
 // (W/2 |sin th| / p - (x - x_e) / r (e - (N_e - 1)/2)) fs / c_bf (the transmit term's aperture
 // and the receive distance r to x_e = p (e - (N_e - 1)/2)); the transmit delay's d u/d th =
 // (x cos th - z sin th + W/2 sgn(sin th) cos th) fs / c_bf (sgn(0) = 0).  dI/du is the slope of
-// the linear-interpolation interval [floor(u), floor(u) + 1] holding u.
+// the linear-interpolation interval [floor(u), floor(u) + 1] holding u.  With a dynamic aperture
+// the element weights depend on the pitch too: that term multiplies the interpolated sample.
 void das_acq_vjp(const Acq& q, const Img& im, const double* rf, const double* gi, double* out) {
   for (int t = 0; t < 2 + q.ntx; ++t) out[t] = 0.0;
   for (int l = 0; l < im.nl; ++l)
@@ -1026,7 +1047,10 @@ void das_acq_vjp(const Acq& q, const Img& im, const double* rf, const double* gi
           double b = (i + 1 >= 0 && i + 1 < q.ns) ? row[i + 1] : 0.0;
           const double dx = x - q.elem_x(e), r = std::sqrt(dx * dx + z * z);
           const double du_dp = (0.5 * (q.ne - 1) * std::fabs(st) - dx / r * (e - 0.5 * (q.ne - 1))) * q.fs / q.cbf;
-          const double gs = g * hann(e, q.ne) * (b - a);
+          double dw_dp;
+          const double w = apod(q, im, x, z, e, &dw_dp);
+          const double gs = g * w * (b - a);
+          out[1] += g * dw_dp * ((1.0 - (u - fl)) * a + (u - fl) * b);  // the weight's own pitch term
           out[0] += gs * (-u / q.cbf);
           out[1] += gs * du_dp;
           out[2 + tx] += gs * du_dth;
@@ -1047,7 +1071,7 @@ void das_adjoint(const Acq& q, const Img& im, const double* gi, double* grf) {
           long long i = (long long)fl;
           double f = u - fl;
           double* row = grf + ((size_t)tx * q.ne + e) * q.ns;
-          double w = hann(e, q.ne);
+          double w = apod(q, im, x, z, e);
           if (i >= 0 && i < q.ns) row[i] += w * (1.0 - f) * g;
           if (i + 1 >= 0 && i + 1 < q.ns) row[i + 1] += w * f * g;
         }

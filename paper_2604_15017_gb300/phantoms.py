@@ -139,9 +139,11 @@ def acquisition(n_elem, pitch, n_samples, angles_deg, n_rays, k_max, c_bf, fs=40
                 tx_elem=int(tx_elem), angles=[float(a) * DEG for a in angles_deg])
 
 
-def image(n_lines, n_depth, x0, x1, z0, z1, dr_db=60.0, lambda1=0.0, lambda2=1.0):
+def image(n_lines, n_depth, x0, x1, z0, z1, dr_db=60.0, lambda1=0.0, lambda2=1.0, f_number=0.0):
+    """Image grid; f_number > 0 selects a dynamic receive aperture (0: the whole array)."""
     return dict(n_lines=int(n_lines), n_depth=int(n_depth), x0=float(x0), x1=float(x1), z0=float(z0),
-                z1=float(z1), dr_db=float(dr_db), lambda1=float(lambda1), lambda2=float(lambda2))
+                z1=float(z1), dr_db=float(dr_db), lambda1=float(lambda1), lambda2=float(lambda2),
+                f_number=float(f_number))
 
 
 def theta_vector(media, amp_scale=1.0, f0=5e6):
