@@ -95,6 +95,10 @@ typedef struct {
   float x0, x1, z0, z1;
   float dr_db;           /* dynamic range: B = max(20 log10(E / E_max), -dr_db) */
   float lambda1, lambda2;/* loss weights (Eq. weighted_l1_l2_loss) */
+  float f_number;        /* DAS element weights w_e(x, z) of Eq. das: <= 0 a Hann window over the
+                            array; > 0 a dynamic receive aperture, the Hann window
+                            cos^2(pi xi / 2), |xi| < 1, of xi = (x_e - x) / a with half-width
+                            a = max(z / (2 f_number), pitch) */
 } us_img_desc;
 
 /* Transport statistics of the most recent us_forward / us_trace on a context. */

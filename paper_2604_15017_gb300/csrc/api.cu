@@ -316,6 +316,7 @@ int make_img(us_ctx* ctx, const us_img_desc* d, Img& im) {
   im.dr = d->dr_db;
   im.l1 = d->lambda1;
   im.l2 = d->lambda2;
+  im.fnum = d->f_number;
   return US_OK;
 }
 
@@ -496,7 +497,7 @@ int do_splat(us_ctx* ctx, const Acq& q, float f0, const Arrival* arr, const uint
 
 std::vector<float> das_signature(const Acq& q, const Img& im) {
   std::vector<float> v = {(float)q.ne, q.pitch, (float)q.ntx, q.fs, (float)q.ns, q.cbf, (float)im.nl, (float)im.nd,
-                          im.x0, im.x1, im.z0, im.z1};
+                          im.x0, im.x1, im.z0, im.z1, im.fnum};
   for (int t = 0; t < q.ntx; ++t) {
     v.push_back(q.sin_tx[t]);
     v.push_back(q.cos_tx[t]);

@@ -48,6 +48,24 @@ __device__ __forceinline__ ff das_urx(const Acq& q, const DasGeo& g, ff x, ff z,
 __device__ __forceinline__ float hann_w(int e, int ne) {
   return 0.5f * (1.0f - cospif(2.0f * (float)(e + 1) / (float)(ne + 1)));
 }
+// Element weight w_e(x, z) of Eq. das: F-number <= 0, the Hann window over the array; F > 0,
+// the dynamic receive aperture: cos^2(pi xi / 2) for |xi| < 1, xi = (x_e - x) / a, half-width
+// a = max(z / 2F, pitch).  dw_dp (optional): its derivative in the pitch (x_e = p (e - (N_e -
+// 1)/2), and a = p where clamped).
+__device__ __forceinline__ float apod_w(const Acq& q, const Img& im, float x, float z, int e,
+                                        float* dw_dp = nullptr) {
+  if (dw_dp) *dw_dp = 0.0f;
+  if (!(im.fnum > 0.0f)) return hann_w(e, q.ne);
+  const float ce = (float)e - 0.5f * (float)(q.ne - 1);
+  const float ad = z / (2.0f * im.fnum);
+  const bool clamped = ad < q.pitch;
+  const float a = clamped ? q.pitch : ad;
+  const float xi = (ce * q.pitch - x) / a;
+  if (fabsf(xi) >= 1.0f) return 0.0f;
+  const float c = cospif(0.5f * xi);
+  if (dw_dp) *dw_dp = -0.5f * PI_F * sinpif(xi) * (ce - (clamped ? xi : 0.0f)) / a;
+  return c * c;
+}
 // The transmit and receive delays of a pixel are each split once into whole samples and a
 // fraction in [0, 1) (exactly, from their float-float values); a tap then adds the two parts:
 // the one float addition of the fractions rounds by at most 2^-24 samples.
@@ -95,7 +113,7 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das(Acq q, Img im, const float*
           const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
           s += fmaf(f, b - a, a);
         }
-        acc = fmaf(hann_w(e, q.ne), s, acc);
+        acc = fmaf(apod_w(q, im, x.hi, z.hi, e), s, acc);
       }
       irf[p] = acc;
     }
@@ -271,9 +289,8 @@ __global__ void __launch_bounds__(DT_THREADS) k_das_tma(Acq q, Img im, const flo
         se[p] += fmaf(f, a1 - a0, a0);
       }
     }
-    const float we = hann_w(e, q.ne);
 #pragma unroll
-    for (int p = 0; p < DT_PX; ++p) acc[p] = fmaf(we, se[p], acc[p]);
+    for (int p = 0; p < DT_PX; ++p) acc[p] = fmaf(apod_w(q, im, x[p].hi, z[p].hi, e), se[p], acc[p]);
     __syncthreads();  // the CTA is done with stage s
     if (threadIdx.x == 0 && use_tma) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -310,7 +327,7 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
     if (gv != 0.0f) {
       for (int e = 0; e < q.ne; ++e) {
         const float2 ur = das_split(das_urx(q, g, x, z, e));
-        const float wg = hann_w(e, q.ne) * gv;
+        const float wg = apod_w(q, im, x.hi, z.hi, e) * gv;
         for (int t = 0; t < q.ntx; ++t) {
           int i;
           float f;
@@ -623,7 +640,8 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
   if (gp != 0.0f) {
     for (int e = 0; e < q.ne; ++e) {
       const float2 ur = das_split(das_urx(q, g, x, z, e));
-      const float w = hann_w(e, q.ne);
+      float dwp;
+      const float w = apod_w(q, im, x.hi, z.hi, e, &dwp);
       const float ce = (float)e - hn;
       const float dx = x.hi - ce * q.pitch;
       const float drp = -dx * ce * kfs / sqrtf(fmaf(dx, dx, z.hi * z.hi));  // d(receive delay)/dp
@@ -638,6 +656,7 @@ __global__ void __launch_bounds__(DA_THREADS) k_das_acq(Acq q, Img im, const flo
         s1_s[t * DA_THREADS + threadIdx.x] += sl;
         c0 = fmaf(sl, (float)i + f, c0);
         cp = fmaf(sl, fmaf(hn * fabsf(q.sin_tx[t]), kfs, drp), cp);
+        cp = fmaf(dwp, fmaf(f, b - a, a), cp);  // the weight's own pitch term (dynamic aperture)
       }
     }
   }

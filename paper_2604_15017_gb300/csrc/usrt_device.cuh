@@ -69,6 +69,7 @@ struct Acq {
 struct Img {
   int nl, nd;
   float x0, x1, z0, z1, dr, l1, l2;
+  float fnum;  // receive F-number of the dynamic aperture (<= 0: the whole array)
 };
 
 // device-resident scene: triangle BVH2 (nodes of 4 float4, triangles in leaf order, 3 float4

@@ -57,7 +57,7 @@ class AcqDesc(C.Structure):
 class ImgDesc(C.Structure):
     _fields_ = [("n_lines", C.c_int32), ("n_depth", C.c_int32), ("x0", C.c_float), ("x1", C.c_float),
                 ("z0", C.c_float), ("z1", C.c_float), ("dr_db", C.c_float), ("lambda1", C.c_float),
-                ("lambda2", C.c_float)]
+                ("lambda2", C.c_float), ("f_number", C.c_float)]
 
 
 class Request(C.Structure):
@@ -169,7 +169,7 @@ def acq_desc(acq):
 def img_desc(img):
     return ImgDesc(int(img["n_lines"]), int(img["n_depth"]), float(img["x0"]), float(img["x1"]), float(img["z0"]),
                    float(img["z1"]), float(img.get("dr_db", 60.0)), float(img.get("lambda1", 0.0)),
-                   float(img.get("lambda2", 1.0)))
+                   float(img.get("lambda2", 1.0)), float(img.get("f_number", 0.0)))
 
 
 class Context:

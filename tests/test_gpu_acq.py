@@ -65,13 +65,14 @@ def within(got, ref, rel, floor=0.0):
     return np.all(err <= rel * np.abs(ref) + floor * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("n_tx,n_lines,n_depth", [(3, 24, 128), (20, 37, 256)])
-def test_das_acq_vjp_matches_oracle(ctx, n_tx, n_lines, n_depth):
-    """20 transmits: three register chunks of 8 with a ragged tail; 37 x 256 pixels: a ragged
-    last block."""
+@pytest.mark.parametrize("n_tx,n_lines,n_depth,f_number", [(3, 24, 128, 0.0), (20, 37, 256, 0.0), (3, 24, 128, 1.5)])
+def test_das_acq_vjp_matches_oracle(ctx, n_tx, n_lines, n_depth, f_number):
+    """20 transmits with a ragged tail; 37 x 256 pixels: a ragged last block; F-number 1.5: the
+    dynamic aperture, whose weights move with the pitch too."""
     degs = [-9.0, 0.0, 11.0] if n_tx == 3 else list(np.linspace(-15, 15, n_tx - 1)) + [0.0]
     acq = dict(P.acquisition(32, float(np.float32(0.3 * MM)), 1024, degs, 1, 1, 1540.0), angles=exact_angles(degs))
-    img = P.image(n_lines, n_depth, *(float(np.float32(v)) for v in (-4 * MM, 4 * MM, 2 * MM, 18 * MM)))
+    img = P.image(n_lines, n_depth, *(float(np.float32(v)) for v in (-4 * MM, 4 * MM, 2 * MM, 18 * MM)),
+                  f_number=f_number)
     rng = np.random.default_rng(n_tx)
     n = 3000 * n_tx
     rf = f32(O.splat(acq, 5e6, rng.integers(0, n_tx, n), rng.integers(0, 32, n), rng.uniform(0, 1024 / 40e6, n),
@@ -80,6 +81,32 @@ def test_das_acq_vjp_matches_oracle(ctx, n_tx, n_lines, n_depth):
     ref = O.das_acq_vjp(acq, img, rf, gi)
     got = ctx.das_acq_vjp(acq, img, dev(rf), dev(gi)).double().cpu().numpy()
     assert within(got, ref, 1e-3), np.c_[got, ref]
+
+
+def test_das_and_transposed_das_with_a_dynamic_aperture(ctx):
+    """F-number 1.2 (aperture clamped to one pitch above 0.72 mm): DAS per pixel within the
+    interpolation bound of the fixed-window test, and the transposed DAS, on both the direct and
+    the TMA-staged kernels."""
+    from paper_2604_15017_gb300 import usrt
+
+    degs = [-8.0, 0.0, 8.0]
+    acq = dict(P.acquisition(32, float(np.float32(0.3 * MM)), 1024, degs, 1, 1, 1540.0), angles=exact_angles(degs))
+    img = P.image(37, 256, *(float(np.float32(v)) for v in (-4 * MM, 4 * MM, 0.3 * MM, 18 * MM)), f_number=1.2)
+    rng = np.random.default_rng(41)
+    n = 9000
+    rf = f32(O.splat(acq, 5e6, rng.integers(0, 3, n), rng.integers(0, 32, n), rng.uniform(0, 1024 / 40e6, n),
+                     rng.normal(size=n)))
+    ref = O.das(acq, img, rf)
+    bound = 2e-3 * O.das(acq, img, np.abs(rf)) + 1e-6 * np.abs(ref).max()
+    for tma in (0, 1):
+        ctx.set_option(usrt.OPT_DAS_TMA, tma)
+        got = ctx.das(acq, img, dev(rf)).cpu().numpy()
+        assert np.all(np.abs(got - ref) <= bound), (tma, np.max(np.abs(got - ref) - bound))
+    ctx.set_option(usrt.OPT_DAS_TMA, 0)  # the library's default
+    gi = f32(rng.normal(size=ref.shape))
+    adj = ctx.das_adjoint(acq, img, dev(gi)).double().cpu().numpy()
+    aref = O.das_adjoint(acq, img, gi)
+    assert np.linalg.norm(adj - aref) <= 1e-3 * np.linalg.norm(aref)
 
 
 def slab_with_angles(n_rays, degs):
