@@ -66,7 +66,8 @@ def lib():
             l.ora_philox.argtypes = [C.c_uint32] * 6 + [U]
             l.ora_philox_fill.argtypes = [C.c_uint32] * 6 + [C.c_longlong, U]
             l.ora_scene_create.restype = C.c_void_p
-            l.ora_scene_create.argtypes = [C.c_int, D, I, C.c_int, D, D, C.c_double, C.c_int]
+            l.ora_scene_create.argtypes = [C.c_int, D, I, C.c_int, D, D, C.c_double, C.c_int, C.c_int]
+            l.ora_ggx_normal.argtypes = [D, C.c_double, C.c_double, C.c_double, D]
             l.ora_scene_free.argtypes = [C.c_void_p]
             l.ora_closest.argtypes = [C.c_void_p, D, D, C.c_int, C.c_int, D]
             l.ora_interface.argtypes = [D, D, C.c_double, C.c_double, C.c_double, C.c_double, D]
@@ -154,7 +155,8 @@ def interface(w, nin, c1, c2, rho1, rho2):
 class Scene:
     """Triangles (nt, 9) with media (nt, 2) = (front, back); scatterers (ns, 3) + amplitudes."""
 
-    def __init__(self, tris, media, scat_pos, scat_amp, r_s, bvh=None):
+    def __init__(self, tris, media, scat_pos, scat_amp, r_s, bvh=None, rough=False):
+        self.rough = bool(rough)  # theta carries a GGX roughness per medium (4M + 2 entries)
         self.tris, tp = _d(np.asarray(tris).reshape(-1, 9))
         self.media, mp = _i(np.asarray(media).reshape(-1, 2))
         self.sp, spp = _d(np.asarray(scat_pos).reshape(-1, 3))
@@ -162,11 +164,11 @@ class Scene:
         nt, ns = len(self.tris), len(self.sa)
         if bvh is None:
             bvh = nt + ns > 10000
-        self.h = lib().ora_scene_create(nt, tp, mp, ns, spp, sap, float(r_s), int(bool(bvh)))
+        self.h = lib().ora_scene_create(nt, tp, mp, ns, spp, sap, float(r_s), int(bool(bvh)), int(self.rough))
 
     @classmethod
     def from_workload(cls, w, bvh=None):
-        return cls(w["tris"], w["media"], w["scat_pos"], w["scat_amp"], w["r_s"], bvh=bvh)
+        return cls(w["tris"], w["media"], w["scat_pos"], w["scat_amp"], w["r_s"], bvh=bvh, rough=w.get("rough", False))
 
     def closest(self, o, w, xcls=0, xid=-1):
         out = np.zeros(3)
@@ -240,12 +242,17 @@ class Run:
                             out.ctypes.data_as(D))
         return out
 
+    @property
+    def n_theta(self):
+        """3M + 2 scene parameters, 4M + 2 with a roughness per medium."""
+        return 3 * self.M + 2 + (self.M if self.scene.rough else 0)
+
     def gradient(self, grf, theta=None, nthreads=None):
         """d/dtheta of sum(grf * RF) on this frozen realisation."""
         th = self.theta if theta is None else np.asarray(theta, np.float64)
         th, thp = _d(th)
         g, gp = _d(grf)
-        out = np.zeros(3 * self.M + 2)
+        out = np.zeros(self.n_theta)
         lib().ora_gradient(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
                            out.ctypes.data_as(D))
         return out
@@ -257,7 +264,7 @@ class Run:
         th = self.theta if theta is None else np.asarray(theta, np.float64)
         th, thp = _d(th)
         g, gp = _d(grf)
-        n_th = 3 * self.M + 2
+        n_th = self.n_theta
         out = np.zeros(n_th + 2 + len(self.acq["angles"]))
         rc = lib().ora_gradient_acq(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
                                     out.ctypes.data_as(D))
@@ -276,7 +283,7 @@ class Run:
         vt = np.ascontiguousarray(vtan, dtype=np.float64)
         n_shape = vt.shape[0]
         assert vt.shape[1:] == (len(self.scene.tris), 9)
-        n_th = 3 * self.M + 2
+        n_th = self.n_theta
         out = np.zeros(n_th + n_shape)
         rc = lib().ora_gradient_shape(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(),
                                       gp, n_shape, vt.ctypes.data_as(D), out.ctypes.data_as(D))
@@ -288,6 +295,13 @@ class Run:
         if getattr(self, "h", None) and _lib is not None:
             _lib.ora_run_free(self.h)
             self.h = None
+
+
+def ggx_normal(n, alpha, u2, u3):
+    """GGX microfacet normal around the unit normal n for the uniforms u2, u3."""
+    h = np.zeros(3)
+    lib().ora_ggx_normal(_d(n)[1], float(alpha), float(u2), float(u3), h.ctypes.data_as(D))
+    return h
 
 
 def splat(acq, f0, tx, e, tau, a):

@@ -252,6 +252,7 @@ struct BNode {
 
 struct Scene {
   int nt = 0, nsct = 0;
+  bool rough = false;  // theta carries a roughness per medium after A_s and f0
   std::vector<D3> v0, v1, v2;
   std::vector<int> mfront, mback;
   std::vector<D3> sp;
@@ -459,6 +460,7 @@ struct Phys {
   int M;
   std::vector<S> c, rho, al;
   S As, f0;
+  std::vector<S> rough;  // GGX roughness alpha per medium (empty: every interface smooth)
   int acq_base = -1;  // >= 0: duals also carry the acquisition parameters: d/d c_bf (slot
                       // acq_base), d/d pitch (acq_base + 1), d/d steering angle of transmit t
                       // (acq_base + 2 + t)
@@ -513,7 +515,9 @@ void elem_acq(Dual& x, int base, double xe, const Acq& q) {
   if (base >= 0) x.d[base + 1] += xe / q.pitch;
 }
 
-Phys<double> phys_double(const double* th, int M) {
+// theta = [c, rho, alpha] x M, A_s, f0 (3M + 2), then with rough a GGX roughness per medium
+// (4M + 2 in all)
+Phys<double> phys_double(const double* th, int M, bool rough = false) {
   Phys<double> p;
   p.M = M;
   for (int m = 0; m < M; ++m) {
@@ -523,10 +527,12 @@ Phys<double> phys_double(const double* th, int M) {
   }
   p.As = th[3 * M];
   p.f0 = th[3 * M + 1];
+  if (rough)
+    for (int m = 0; m < M; ++m) p.rough.push_back(th[3 * M + 2 + m]);
   return p;
 }
 
-Phys<Dual> phys_dual(const double* th, int M) {
+Phys<Dual> phys_dual(const double* th, int M, bool rough = false) {
   Phys<Dual> p;
   p.M = M;
   for (int m = 0; m < M; ++m) {
@@ -543,6 +549,12 @@ Phys<Dual> phys_dual(const double* th, int M) {
   f.d[3 * M + 1] = 1;
   p.As = as;
   p.f0 = f;
+  if (rough)
+    for (int m = 0; m < M; ++m) {
+      Dual r(th[3 * M + 2 + m]);
+      r.d[3 * M + 2 + m] = 1;
+      p.rough.push_back(r);
+    }
   return p;
 }
 
@@ -691,6 +703,42 @@ bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, 
 // pressure coefficients R, T = 1 + R; split probability P_r = R^2 (or a fixed q), weight
 // amplitude / selection probability.  Attenuation per segment (exp(-kappa alpha f0 L)).
 // ------------------------------------------------------------------------------------------
+// ------------------------------------------------------------------------------------------
+// Rough interfaces [Sec. 2.3.2, Eq. GGX_PDF].  A microfacet normal h is drawn with density
+// D(h) (h.n) over the hemisphere around n, D the GGX distribution of roughness alpha: inverting
+// its cumulative distribution gives tan^2(theta_h) = alpha^2 u / (1 - u) and a uniform azimuth.
+// The event then reflects or refracts about h with the pressure coefficients of h (Fresnel and
+// Snell as at a smooth interface), and the amplitude takes the microfacet weight of this
+// sampling (Walter et al. 2007): |w_i.h| G(w_i, w_o) / (|w_i.n| |h.n|), G the separable Smith
+// masking-shadowing of GGX, G1(v) = 2 |v.n| / (|v.n| + sqrt(alpha^2 + (1 - alpha^2) (v.n)^2)).
+// A facet the ray meets from behind (w_i.h >= 0), or an outgoing direction on the wrong side
+// of the macro surface, ends the path.  alpha -> 0 gives h = n and weight 1: the smooth event.
+// ------------------------------------------------------------------------------------------
+// orthonormal tangents of a unit normal (the branch-free construction of Duff et al., 2017)
+template <class S>
+void tangent_frame(const V3<S>& n, V3<S>& t1, V3<S>& t2) {
+  const double sg = val(n.z) >= 0.0 ? 1.0 : -1.0;
+  const S a = -1.0 / (n.z + sg);
+  const S b = n.x * n.y * a;
+  t1 = mk3<S>(1.0 + sg * n.x * n.x * a, sg * b, -sg * n.x);
+  t2 = mk3<S>(b, sg + n.y * n.y * a, -1.0 * n.y);
+}
+template <class S>
+V3<S> ggx_normal(const V3<S>& n, const S& alpha, double u2, double u3) {
+  V3<S> t1, t2;
+  tangent_frame(n, t1, t2);
+  const S tn = alpha * std::sqrt(u2 / (1.0 - u2));  // tan(theta_h)
+  const S ct = 1.0 / sqrt(1.0 + tn * tn);
+  const S st = tn * ct;
+  const double ph = 2.0 * PI * u3;
+  return add(scale(n, ct), add(scale(t1, st * std::cos(ph)), scale(t2, st * std::sin(ph))));
+}
+template <class S>
+S smith_g1(const S& vn, const S& alpha) {
+  const S c = vn * (val(vn) < 0 ? -1.0 : 1.0);
+  return 2.0 * c / (c + sqrt(alpha * alpha + (1.0 - alpha * alpha) * c * c));
+}
+
 struct PathIO {
   // injected emission (tests); when inject is false the emission is sampled from Philox
   bool inject = false;
@@ -819,11 +867,18 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
       V3<S> nn = front ? n : scale(n, -1.0);  // unit normal pointing back into medium 1
       int m1 = front ? sc.mfront[h.id] : sc.mback[h.id];
       int m2 = front ? sc.mback[h.id] : sc.mfront[h.id];
-      Iface<S> f = interface_event<S>(w, nn, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
+      // the facet normal: the macro normal, or a GGX microfacet normal (roughness of the
+      // medium the triangle bounds, its back side)
+      const bool rough = !P.rough.empty() && val(P.rough[sc.mback[h.id]]) > 0.0;
+      V3<S> hf = nn;
+      if (rough) hf = ggx_normal<S>(nn, P.rough[sc.mback[h.id]], u01(u.v[2]), u01(u.v[3]));
+      const V3<S> w_in = w;
+      if (rough && !replay && val(dot(w, hf)) >= 0.0) break;  // facet met from behind: the path ends
+      Iface<S> f = interface_event<S>(w, hf, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2]);
       int choice;
       if (replay) {
         choice = rec_in[k].choice;
-        if (choice != CH_TIR && f.tir) f = interface_event<S>(w, nn, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2], true);
+        if (choice != CH_TIR && f.tir) f = interface_event<S>(w, hf, P.c[m1], P.c[m2], P.rho[m1], P.rho[m2], true);
       } else if (f.tir) {
         choice = CH_TIR;
       } else {
@@ -845,6 +900,13 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
         a = io.physical ? a * f.T : a * f.T / (1.0 - pr);
         w = f.wt;
         m = m2;
+      }
+      if (rough) {
+        const S on = dot(w, nn);  // > 0: back into medium 1
+        if (!replay && ((m == m1) != (val(on) > 0.0))) break;  // wrong side of the macro surface: the path ends
+        const S inn = dot(w_in, nn), hn = dot(hf, nn), ih = dot(w_in, hf);
+        const S alpha = P.rough[sc.mback[h.id]];
+        a = a * (-1.0 * ih) * smith_g1(inn, alpha) * smith_g1(on, alpha) / ((-1.0 * inn) * hn);
       }
       o = x;
       xcls = CLS_TRI;
@@ -934,7 +996,7 @@ PathIO path_io(const Acq& q, long long path) {
 void forward_run(const Scene& sc, const double* th, Run& run, uint64_t seed, int nthreads,
                  long long path_lo, long long path_hi) {
   const Acq& q = run.q;
-  Phys<double> P = phys_double(th, run.M);
+  Phys<double> P = phys_double(th, run.M, sc.rough);
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   long long n = path_hi - path_lo;
   std::vector<std::vector<Arrival<double>>> parts(std::max(1, nthreads));
@@ -1233,9 +1295,10 @@ void ora_philox_fill(uint32_t c0_base, uint32_t c1, uint32_t c2, uint32_t c3, ui
 }
 
 void* ora_scene_create(int nt, const double* tri, const int* media, int ns, const double* sp, const double* samp,
-                       double rs, int use_bvh) {
+                       double rs, int use_bvh, int rough) {
   Scene* s = new Scene();
   s->nt = nt;
+  s->rough = rough != 0;
   for (int i = 0; i < nt; ++i) {
     const double* t = tri + 9 * (size_t)i;
     s->v0.push_back(d3(t[0], t[1], t[2]));
@@ -1255,6 +1318,14 @@ void* ora_scene_create(int nt, const double* tri, const int* media, int ns, cons
 }
 
 void ora_scene_free(void* s) { delete (Scene*)s; }
+
+// GGX microfacet normal around the unit normal n for the uniforms (u2, u3) (tests)
+void ora_ggx_normal(const double* n, double alpha, double u2, double u3, double* h) {
+  D3 r = ggx_normal<double>(d3(n[0], n[1], n[2]), alpha, u2, u3);
+  h[0] = r.x;
+  h[1] = r.y;
+  h[2] = r.z;
+}
 
 // interface event (tests): out = {tir, cos_i, cos_t, R, T, wr[3], wt[3]}
 void ora_interface(const double* w, const double* nin, double c1, double c2, double rho1, double rho2, double* out) {
@@ -1399,7 +1470,7 @@ void ora_replay_rf(void* scene, void* rp, const double* theta, uint64_t seed, in
   Run* r = (Run*)rp;
   const Scene& sc = *(Scene*)scene;
   const Acq& q = r->q;
-  Phys<double> P = phys_double(theta, r->M);
+  Phys<double> P = phys_double(theta, r->M, ((Scene*)scene)->rough);
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   std::vector<std::vector<Arrival<double>>> parts(std::max(1, nthreads));
   std::vector<Counters> cnts(std::max(1, nthreads));
@@ -1426,8 +1497,8 @@ static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t se
   Run* r = (Run*)rp;
   const Scene& sc = *(Scene*)scene;
   const Acq& q = r->q;
-  Phys<Dual> P = phys_dual(theta, r->M);
-  int np = 3 * r->M + 2;
+  Phys<Dual> P = phys_dual(theta, r->M, sc.rough);
+  int np = 3 * r->M + 2 + (sc.rough ? r->M : 0);
   if (with_acq) {
     P.acq_base = np;
     np += 2 + q.ntx;
@@ -1497,7 +1568,7 @@ int ora_trace_injected(void* scene, const double* theta, int M, const double* ac
                        const int* forced, int n_forced, int physical, int cap, int* e_out, double* tau_out,
                        double* a_out, int* kind_out, int* rec_out, double* last_state) {
   Acq q = make_acq(acq, angles);
-  Phys<double> P = phys_double(theta, M);
+  Phys<double> P = phys_double(theta, M, ((Scene*)scene)->rough);
   PathIO io;
   io.inject = true;
   io.o0 = d3(o[0], o[1], o[2]);

@@ -278,6 +278,20 @@ def hollow_cylinder(radius=5 * MM, wall=1 * MM, depth=15 * MM, n_rays=2000, n_sc
     return w
 
 
+def with_roughness(w, rough):
+    """The workload with rough interfaces: theta (and theta_target) extended by a GGX roughness
+    per medium, the roughness of the interfaces bounding that medium (triangles whose back side
+    it is)."""
+    w = dict(w)
+    r = np.asarray(rough, dtype=np.float64)
+    assert r.shape == (w["M"],)
+    w["rough"] = True
+    w["theta"] = np.concatenate([np.asarray(w["theta"], np.float64), r])
+    if "theta_target" in w:
+        w["theta_target"] = np.concatenate([np.asarray(w["theta_target"], np.float64), r])
+    return w
+
+
 def perturbed_theta(theta, seed, frac=0.05):
     rng = np.random.default_rng(seed)
     s = rng.choice([-1.0, 1.0], size=len(theta))
