@@ -15,6 +15,8 @@
  *   - Parameter vector theta (HOST, float[3*M+2]):
  *       [c_0, rho_0, alpha_0, c_1, rho_1, alpha_1, ..., c_{M-1}, rho_{M-1}, alpha_{M-1}, A_s, f0]
  *     M media (medium 0 holds the probe), scatterer amplitude scale A_s, centre frequency f0.
+ *     A scene uploaded with rough != 0 takes M more entries, a GGX roughness per medium
+ *     (float[4*M+2]); dL/dtheta then has the same length.
  *   - Probe: elements e = 0..n_elem-1 at x_e = (e - (n_elem-1)/2) * pitch, z = 0, normal +z,
  *     element face pitch x h_el.  Transmit tx uses plane-wave steering angle angles[tx].
  *   - Channel data rf: DEVICE float[n_tx][n_elem][n_samples], sample n at t = n / fs.
@@ -64,6 +66,11 @@ typedef struct {
   const float* scat_amp; /* HOST, n_scat: per-scatterer amplitude s_j */
   float r_s;             /* scatterer radius: a primary ray interacts at its closest approach
                             when that lies within r_s of the centre */
+  int32_t rough;         /* != 0: rough interfaces (Sec. 2.3.2, Eq. GGX_PDF).  theta then
+                            carries, after A_s and f0, a GGX roughness alpha in [0, 1] per medium
+                            (4M + 2 parameters, and dL/dtheta as many): a triangle's interface
+                            takes the roughness of its back-side medium (the region it bounds);
+                            alpha = 0 is the smooth interface */
 } us_scene_desc;
 
 /* Acquisition: probe, transmits, sampling and transport limits (Sec. 2.3.1-2.3.4). */
@@ -277,7 +284,7 @@ int us_splat_adjoint(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, c
  * the realisation fixed by seed.  mode 0 = record (uses the record kept by the last
  * us_forward with keep_record on this scene, theta, acq and seed), mode 1 = recompute (re-runs
  * the transport in chunks of paths to regenerate the decisions).  dL_dtheta_dev: DEVICE
- * float[3M+2], overwritten. */
+ * float[3M+2] (4M+2 in a rough scene), overwritten. */
 int us_transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
                      int mode, const float* dL_drf_dev, float* dL_dtheta_dev, void* stream);
 

@@ -121,7 +121,16 @@ __host__ __device__ constexpr int adj_row_stride(int P) { return P | 1; }
 
 // Options compiled in, so that the plain adjoint carries none of their code: bit 0 = the
 // acquisition slots (acq_slot), bit 1 = the vertex gradient (g_tris).
-constexpr int ADJ_ACQ = 1, ADJ_SHAPE = 2;
+constexpr int ADJ_ACQ = 1, ADJ_SHAPE = 2, ADJ_ROUGH = 4;  // bit 2: a rough scene (GGX events)
+
+// d log G1 / d(v.n) and d log G1 / d alpha of the Smith masking G1 of GGX (see smith_g1)
+__device__ __forceinline__ void g1_log_grad(float vn, float alpha, float& d_vn, float& d_alpha) {
+  const float c = fabsf(vn);
+  const float q = sqrtf(fmaf(1.0f - alpha * alpha, c * c, alpha * alpha));
+  const float dc = 1.0f / c - (1.0f + (1.0f - alpha * alpha) * c / q) / (c + q);
+  d_vn = vn < 0.0f ? -dc : dc;
+  d_alpha = -(alpha * (1.0f - c * c) / q) / (c + q);
+}
 
 template <int OPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
@@ -200,21 +209,36 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         const float3 nin = front ? nn : nn * -1.0f;
         const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
         const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
-        const Iface f = iface(w, nin, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
+        float3 fn = nin;  // facet normal (a GGX microfacet normal at a rough event)
+        float alpha = 0.0f;
+        if (OPT & ADJ_ROUGH) {
+          alpha = med.rough[mm >> 16];
+          if (alpha > 0.0f) {
+            const uint4 uk = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, (uint32_t)(k + 1)),
+                                           make_uint2(q.key0, q.key1));
+            fn = ggx_sample(nin, alpha, u01(uk.z), u01(uk.w)).h;
+          }
+        }
+        const float3 w_in = w;
+        const Iface f = iface(w, fn, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
         const uint32_t choice = (r >> 22) & 3u;
         const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
         if (choice == CH_TIR || f.tir) {
-          w = w + nin * (2.0f * f.ci);
+          w = w + fn * (2.0f * f.ci);
           m = m1;
           a = a1;
         } else if (choice == CH_REFLECT) {
           a = a1 * (f.R / pr);
-          w = w + nin * (2.0f * f.ci);
+          w = w + fn * (2.0f * f.ci);
           m = m1;
         } else {
           a = a1 * (f.T / (1.0f - pr));
-          w = w * f.r + nin * (f.r * f.ci - f.ct);
+          w = w * f.r + fn * (f.r * f.ci - f.ct);
           m = m2;
+        }
+        if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {  // microfacet weight (a killed event has no successor)
+          const float inn = dot3(w_in, nin), on = dot3(w, nin);
+          a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
         }
       } else {  // scatterer: the secondary ray's adjoint seeds come from k_nee_adjoint
         const float2 sd = A.seeds[(size_t)i * K1 + k];
@@ -260,37 +284,75 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
         const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
         const float c1 = med.c[m1], c2 = med.c[m2], r1 = med.rho[m1], r2 = med.rho[m2];
-        const Iface f = iface(wk, nin, c1, c2, r1, r2);
+        float3 fn = nin;  // facet normal (a GGX microfacet normal at a rough event)
+        float alpha = 0.0f;
+        GgxSample gs;
+        if (OPT & ADJ_ROUGH) {
+          alpha = med.rough[mm >> 16];
+          if (alpha > 0.0f) {
+            const uint4 uk = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, (uint32_t)(k + 1)),
+                                           make_uint2(q.key0, q.key1));
+            gs = ggx_sample(nin, alpha, u01(uk.z), u01(uk.w));
+            fn = gs.h;
+          }
+        }
+        const Iface f = iface(wk, fn, c1, c2, r1, r2);
         const uint32_t choice = (r >> 22) & 3u;
+        const bool refl = choice == CH_TIR || f.tir || choice == CH_REFLECT;
+        // microfacet weight W = -(w.h) G1(w.n) G1(w'.n) / (-(w.n) (h.n)): a' W leaves the event,
+        // so the smooth event below sees ab W and wb + dW/dw' terms; log W's adjoint goes to
+        // w, h and alpha
+        float abx = ab, ihb = 0.0f, inb = 0.0f, hnb = 0.0f, alb = 0.0f;
+        float3 wbx = wb;
+        if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {
+          const float3 wo = refl ? wk + fn * (2.0f * f.ci) : wk * f.r + fn * (f.r * f.ci - f.ct);
+          const float ih = dot3(wk, fn), inn = dot3(wk, nin), on = dot3(wo, nin), hn = dot3(fn, nin);
+          if (ih < 0.0f && refl == (on > 0.0f)) {  // a live event (a killed one passes no adjoint)
+            const float Wv = -ih * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * hn);
+            const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+            const float ap = (choice == CH_TIR || f.tir) ? a1 : (choice == CH_REFLECT ? a1 * f.R / pr
+                                                                                      : a1 * f.T / (1.0f - pr));
+            const float Wl = ab * ap * Wv;  // adjoint of log W
+            abx = ab * Wv;
+            float gi_n, gi_a, go_n, go_a;
+            g1_log_grad(inn, alpha, gi_n, gi_a);
+            g1_log_grad(on, alpha, go_n, go_a);
+            ihb = Wl / ih;
+            inb = Wl * (gi_n - 1.0f / inn);
+            hnb = -Wl / hn;
+            alb = Wl * (gi_a + go_a);
+            wbx = wb + nin * (Wl * go_n);
+          }
+        }
         t1b = tb;
         xb = ob;
         float cib = 0.0f, ctb = 0.0f, rb = 0.0f, Rb = 0.0f, Tb = 0.0f;
         if (choice == CH_TIR || f.tir) {
-          a1b = ab;
-          wpb = wb;
-          cib += 2.0f * dot3(wb, nin);
+          a1b = abx;
+          wpb = wbx;
+          cib += 2.0f * dot3(wbx, fn);
         } else if (choice == CH_REFLECT) {
           if (q.split_mode == 0) {
-            a1b = ab / f.R;
-            Rb = ab * a1 * (-1.0f / (f.R * f.R));
+            a1b = abx / f.R;
+            Rb = abx * a1 * (-1.0f / (f.R * f.R));
           } else {
-            a1b = ab * (f.R / q.split_q);
-            Rb = ab * a1 / q.split_q;
+            a1b = abx * (f.R / q.split_q);
+            Rb = abx * a1 / q.split_q;
           }
-          wpb = wb;
-          cib += 2.0f * dot3(wb, nin);
+          wpb = wbx;
+          cib += 2.0f * dot3(wbx, fn);
         } else {
           if (q.split_mode == 0) {
             const float om = 1.0f - f.R;
-            a1b = ab / om;
-            Rb = ab * a1 / (om * om);
+            a1b = abx / om;
+            Rb = abx * a1 / (om * om);
           } else {
-            a1b = ab * (f.T / (1.0f - q.split_q));
-            Tb = ab * a1 / (1.0f - q.split_q);
+            a1b = abx * (f.T / (1.0f - q.split_q));
+            Tb = abx * a1 / (1.0f - q.split_q);
           }
-          wpb = wb * f.r;
-          rb += dot3(wb, wk + nin * f.ci);
-          const float wn = dot3(wb, nin);
+          wpb = wbx * f.r;
+          rb += dot3(wbx, wk + fn * f.ci);
+          const float wn = dot3(wbx, fn);
           cib += f.r * wn;
           ctb -= wn;
         }
@@ -316,7 +378,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           ADD(acc[3 * m2 + 0], c2b);
           ADD(acc[3 * m1 + 0], c1b);
         }
-        wpb = wpb + nin * (-cib);
+        wpb = wpb + fn * (-cib);
+        if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {
+          // h = cos(theta) n + sin(theta) b with tan(theta) = alpha s: dh/dalpha = s cos^3 (b - tan n)
+          wpb = wpb + fn * ihb + nin * inb;
+          const float3 hb = wk * (ihb - cib) + wbx * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct) + nin * hnb;
+          const float tn = alpha * gs.s, ct = rsqrtf(1.0f + tn * tn);
+          alb += dot3(hb, (gs.b - nin * tn) * (gs.s * ct * ct * ct));
+          ADD(acc[3 * med.M + 2 + (int)(mm >> 16)], alb);
+        }
         if (OPT & ADJ_SHAPE) {  // nin enters through ci = -w.nin and the outgoing direction
           const bool refl = choice == CH_TIR || f.tir || choice == CH_REFLECT;
           const float3 nb = wk * (-cib) + wb * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct);
@@ -631,10 +701,12 @@ __global__ void k_philox_fill(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
   }
 }
 
-static int adj_opt(const AdjArgs& a) { return (a.acq_slot >= 0 ? ADJ_ACQ : 0) | (a.g_tris ? ADJ_SHAPE : 0); }
+static int adj_opt(const AdjArgs& a) {
+  return (a.acq_slot >= 0 ? ADJ_ACQ : 0) | (a.g_tris ? ADJ_SHAPE : 0) | (a.med.has_rough ? ADJ_ROUGH : 0);
+}
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);
-  switch (adj_opt(a)) {
+  switch (adj_opt(a) & (ADJ_ACQ | ADJ_SHAPE)) {  // secondary rays cross rough interfaces as smooth ones
     case 0: k_nee_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 1: k_nee_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 2: k_nee_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
@@ -654,14 +726,18 @@ void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
     case 0: k_path_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 1: k_path_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 2: k_path_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
-    default: k_path_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 3: k_path_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 4: k_path_adjoint<4><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    default: k_path_adjoint<5><<<grid, ADJ_THREADS, sm, st>>>(a); break;  // rough + acq (shape excluded)
   }
 }
 cudaError_t adjoint_set_attrs() {
   const int sm = (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ));
-  const void* ks[8] = {(const void*)k_path_adjoint<0>, (const void*)k_path_adjoint<1>, (const void*)k_path_adjoint<2>,
-                       (const void*)k_path_adjoint<3>, (const void*)k_nee_adjoint<0>, (const void*)k_nee_adjoint<1>,
-                       (const void*)k_nee_adjoint<2>, (const void*)k_nee_adjoint<3>};
+  const void* ks[10] = {(const void*)k_path_adjoint<0>, (const void*)k_path_adjoint<1>,
+                        (const void*)k_path_adjoint<2>, (const void*)k_path_adjoint<3>,
+                        (const void*)k_path_adjoint<4>, (const void*)k_path_adjoint<5>,
+                        (const void*)k_nee_adjoint<0>,  (const void*)k_nee_adjoint<1>,
+                        (const void*)k_nee_adjoint<2>,  (const void*)k_nee_adjoint<3>};
   for (const void* k : ks) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;

@@ -6,7 +6,7 @@
 
 namespace usrt {
 
-constexpr int MAX_P = 3 * MAX_MEDIA + 2;
+constexpr int MAX_P = 4 * MAX_MEDIA + 2;  // with a roughness per medium
 constexpr int MAX_P_ACQ = MAX_P + 2 + MAX_TX;  // with the acquisition slots (c_bf, pitch, steering angles)
 
 struct PulseP {

@@ -38,6 +38,7 @@ struct SceneGPU {
   std::vector<void*> allocs;
   size_t bytes = 0;
   int n_media_hint = 0;
+  bool rough = false;  // theta carries a GGX roughness per medium
   int depth = 0;
 };
 
@@ -240,11 +241,18 @@ struct StageScope {
   }
 };
 
-int make_media(us_ctx* ctx, const float* theta, int M, Media& med) {
+int make_media(us_ctx* ctx, const float* theta, int M, Media& med, bool rough = false) {
   if (!theta) return fail(ctx, US_ERR_ARG, "theta is NULL");
   if (M < 1 || M > MAX_MEDIA) return fail(ctx, US_ERR_ARG, "n_media %d outside [1, %d]", M, MAX_MEDIA);
   std::memset(&med, 0, sizeof med);
   med.M = M;
+  med.has_rough = rough ? 1 : 0;
+  if (rough)
+    for (int m = 0; m < M; ++m) {
+      med.rough[m] = theta[3 * M + 2 + m];
+      if (!(med.rough[m] >= 0.0f && med.rough[m] <= 1.0f))
+        return fail(ctx, US_ERR_ARG, "roughness of medium %d outside [0, 1]", m);
+    }
   for (int m = 0; m < M; ++m) {
     med.c[m] = theta[3 * m];
     med.rho[m] = theta[3 * m + 1];
@@ -695,6 +703,7 @@ int us_scene_upload(us_ctx* ctx, const us_scene_desc* d, uint64_t* scene_id) {
   if (o.gn[0] < 0) return fail(ctx, US_ERR_ARG, "more than 255 scatterer spheres overlap one grid cell at every cell size");
   SceneGPU sc;
   sc.n_media_hint = d->n_media;
+  sc.rough = d->rough != 0;
   auto up_bytes = [&](const void* src, size_t bytes, const void** dst) -> int {
     void* p = nullptr;
     CKS(dev_alloc(ctx, &p, bytes));
@@ -794,7 +803,7 @@ int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   Media med;
   Acq q;
   Img im;
-  CKS(make_media(ctx, theta, sc->n_media_hint, med));
+  CKS(make_media(ctx, theta, sc->n_media_hint, med, sc->rough));
   CKS(make_acq(ctx, acq, seed, q));
   if (bmode_dev) CKS(make_img(ctx, img, im));
   ctx->L->rkey.valid = false;  // job buffers and counters are about to be overwritten
@@ -831,7 +840,7 @@ int us_forward(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
   if (keep_record) {
     ctx->L->rkey.scene = scene;
     ctx->L->rkey.seed = seed;
-    ctx->L->rkey.theta.assign(theta, theta + 3 * sc->n_media_hint + 2);
+    ctx->L->rkey.theta.assign(theta, theta + n_theta(med));
     ctx->L->rkey.acq.assign((const char*)&q, (const char*)&q + sizeof q);
     ctx->L->rkey.n_paths = n_paths;
     ctx->L->rkey.valid = true;
@@ -1053,7 +1062,7 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
   if (!dL_drf_dev || !dL_dtheta_dev) return fail(ctx, US_ERR_ARG, "null buffer");
   Media med;
   Acq q;
-  CKS(make_media(ctx, theta, sc->n_media_hint, med));
+  CKS(make_media(ctx, theta, sc->n_media_hint, med, sc->rough));
   CKS(make_acq(ctx, acq, seed, q));
   SplatGeom g;
   AdjArgs A;
@@ -1063,13 +1072,15 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
   A.med = med;
   A.acq = q;
   A.grf = dL_drf_dev;
-  const int Ps = 3 * med.M + 2;
+  const int Ps = n_theta(med);
   A.P = Ps;
   A.acq_slot = -1;
   if (dL_dacq_dev) {
     A.acq_slot = Ps;
     A.P = Ps + 2 + q.ntx;
   }
+  if (dL_dtris_dev && sc->rough)
+    return fail(ctx, US_ERR_ARG, "shape gradients of scenes with rough interfaces are not supported");
   A.g_tris = dL_dtris_dev;
   if (dL_dtris_dev && sc->dev.n_tris)
     CK(cudaMemsetAsync(dL_dtris_dev, 0, sizeof(float) * 9 * (size_t)sc->dev.n_tris, st));

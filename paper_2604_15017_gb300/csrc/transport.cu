@@ -313,7 +313,22 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
       const float3 nin = front ? nn : nn * -1.0f;
       const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
       const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
-      const Iface f = iface(w, nin, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
+      // facet normal: the macro normal, or a GGX microfacet normal (roughness of the medium the
+      // triangle bounds, its back side)
+      const float alpha = med.rough[mm >> 16];
+      float3 fn = nin;
+      if (alpha > 0.0f) {
+        fn = ggx_sample(nin, alpha, u01(u.z), u01(u.w)).h;
+        if (dot3(w, fn) >= 0.0f) {  // facet met from behind: the path ends here
+          if (rec) {
+            *rec = word;
+            rec[1] = 0u;
+          }
+          continue;
+        }
+      }
+      const float3 w_in = w;
+      const Iface f = iface(w, fn, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
       uint32_t choice;
       if (f.tir) {
         choice = CH_TIR;
@@ -322,20 +337,31 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
         choice = u01(u.x) < pr ? CH_REFLECT : CH_TRANSMIT;
       }
       if (choice == CH_TIR) {
-        w = w + nin * (2.0f * f.ci);
+        w = w + fn * (2.0f * f.ci);
         m = m1;
       } else if (choice == CH_REFLECT) {
         const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
         a = a * (f.R / pr);
-        w = w + nin * (2.0f * f.ci);
+        w = w + fn * (2.0f * f.ci);
         m = m1;
       } else {
         const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
         a = a * (f.T / (1.0f - pr));
-        w = w * f.r + nin * (f.r * f.ci - f.ct);
+        w = w * f.r + fn * (f.r * f.ci - f.ct);
         m = m2;
       }
       word |= choice << 22;
+      if (alpha > 0.0f) {
+        const float on = dot3(w, nin), inn = dot3(w_in, nin);
+        if ((m == m1) != (on > 0.0f)) {  // outgoing direction on the wrong side: the path ends
+          if (rec) {
+            *rec = word;
+            rec[1] = 0u;
+          }
+          continue;
+        }
+        a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
+      }
     } else {  // scatterer: secondary ray to a uniformly chosen element; Born pass-through
       const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
       word |= (uint32_t)e2 << 24;

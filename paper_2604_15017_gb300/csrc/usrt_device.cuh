@@ -55,7 +55,11 @@ struct Media {
   int M;
   float c[MAX_MEDIA], rho[MAX_MEDIA], al[MAX_MEDIA];
   float As, f0;
+  float rough[MAX_MEDIA];  // GGX roughness of the interfaces bounding each medium (0: smooth)
+  int has_rough;           // theta carries the roughness values (4M + 2 parameters)
 };
+// parameters in theta: 3M + 2, and M roughness values after them in a rough scene
+__host__ __device__ __forceinline__ int n_theta(const Media& m) { return 3 * m.M + 2 + (m.has_rough ? m.M : 0); }
 
 struct Acq {
   int ne, ntx, ns, kmax, nr, n_emit, tx_elem, split_mode;
@@ -225,6 +229,41 @@ __device__ __forceinline__ Iface iface(float3 w, float3 nin, float c1, float c2,
   f.R = (A - B) * inv;
   f.T = 2.0f * A * inv;
   return f;
+}
+
+// ------------------------------------------------------------------------------------------
+// Rough interfaces (Sec. 2.3.2, Eq. GGX_PDF): a microfacet normal h drawn with density
+// D(h) (h.n) around the macro normal n, D the GGX distribution of roughness alpha.  Inverting
+// its cumulative distribution: tan(theta_h) = alpha s with s = sqrt(u / (1 - u)), and a uniform
+// azimuth phi about n, in the tangent frame of Duff et al. (2017, branch-free orthonormal basis).
+// The event reflects or refracts about h; the amplitude takes the microfacet weight of this
+// sampling, |w_i.h| G1(w_i) G1(w_o) / (|w_i.n| |h.n|) with the Smith masking of GGX,
+// G1(v) = 2 |v.n| / (|v.n| + sqrt(alpha^2 + (1 - alpha^2) (v.n)^2)).
+// ------------------------------------------------------------------------------------------
+struct GgxSample {
+  float3 h;  // microfacet normal
+  float3 b;  // unit tangent direction of the tilt (h = cos(theta) n + sin(theta) b)
+  float s;   // tan(theta_h) / alpha
+};
+__device__ __forceinline__ GgxSample ggx_sample(float3 n, float alpha, float u2, float u3) {
+  const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
+  const float a = -1.0f / (sg + n.z);
+  const float bb = n.x * n.y * a;
+  const float3 t1 = make_float3(1.0f + sg * n.x * n.x * a, sg * bb, -sg * n.x);
+  const float3 t2 = make_float3(bb, sg + n.y * n.y * a, -n.y);
+  float sp, cp;
+  sincospif(2.0f * u3, &sp, &cp);
+  GgxSample g;
+  g.b = make_float3(cp * t1.x + sp * t2.x, cp * t1.y + sp * t2.y, cp * t1.z + sp * t2.z);
+  g.s = sqrtf(u2 / (1.0f - u2));
+  const float tn = alpha * g.s;
+  const float ct = rsqrtf(1.0f + tn * tn), st = tn * ct;
+  g.h = make_float3(ct * n.x + st * g.b.x, ct * n.y + st * g.b.y, ct * n.z + st * g.b.z);
+  return g;
+}
+__device__ __forceinline__ float smith_g1(float vn, float alpha) {
+  const float c = fabsf(vn);
+  return 2.0f * c / (c + sqrtf(fmaf(1.0f - alpha * alpha, c * c, alpha * alpha)));
 }
 
 }  // namespace usrt

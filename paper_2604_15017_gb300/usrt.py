@@ -43,7 +43,7 @@ class UsrtError(RuntimeError):
 class SceneDesc(C.Structure):
     _fields_ = [("n_tris", C.c_int32), ("tris", C.POINTER(C.c_float)), ("media", C.POINTER(C.c_int32)),
                 ("n_media", C.c_int32), ("n_scat", C.c_int32), ("scat_pos", C.POINTER(C.c_float)),
-                ("scat_amp", C.POINTER(C.c_float)), ("r_s", C.c_float)]
+                ("scat_amp", C.POINTER(C.c_float)), ("r_s", C.c_float), ("rough", C.c_int32)]
 
 
 class AcqDesc(C.Structure):
@@ -225,21 +225,22 @@ class Context:
         return v.value
 
     # ---- scenes ---------------------------------------------------------------------------
-    def upload_scene(self, tris, media, n_media, scat_pos, scat_amp, r_s):
+    def upload_scene(self, tris, media, n_media, scat_pos, scat_amp, r_s, rough=False):
         tris = _f32(np.asarray(tris).reshape(-1, 9))
         media = np.ascontiguousarray(np.asarray(media, dtype=np.int32).reshape(-1, 2))
         sp = _f32(np.asarray(scat_pos).reshape(-1, 3))
         sa = _f32(np.asarray(scat_amp).reshape(-1))
         d = SceneDesc(len(tris), tris.ctypes.data_as(C.POINTER(C.c_float)), media.ctypes.data_as(C.POINTER(C.c_int32)),
                       int(n_media), len(sa), sp.ctypes.data_as(C.POINTER(C.c_float)),
-                      sa.ctypes.data_as(C.POINTER(C.c_float)), float(r_s))
+                      sa.ctypes.data_as(C.POINTER(C.c_float)), float(r_s), int(bool(rough)))
         sid = C.c_uint64()
         self._check(lib().us_scene_upload(self.h, C.byref(d), C.byref(sid)))
         self.scene_media[sid.value] = int(n_media)
         return sid.value
 
     def upload_workload(self, w):
-        return self.upload_scene(w["tris"], w["media"], w["M"], w["scat_pos"], w["scat_amp"], w["r_s"])
+        return self.upload_scene(w["tris"], w["media"], w["M"], w["scat_pos"], w["scat_amp"], w["r_s"],
+                                 rough=w.get("rough", False))
 
     def release_scene(self, sid):
         self._check(lib().us_scene_release(self.h, int(sid)))
