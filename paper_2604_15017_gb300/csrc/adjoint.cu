@@ -302,10 +302,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         // microfacet weight W = -(w.h) G1(w.n) G1(w'.n) / (-(w.n) (h.n)): a' W leaves the event,
         // so the smooth event below sees ab W and wb + dW/dw' terms; log W's adjoint goes to
         // w, h and alpha
-        float abx = ab, ihb = 0.0f, inb = 0.0f, hnb = 0.0f, alb = 0.0f;
-        float3 wbx = wb;
+        float abx = ab, ihb = 0.0f, inb = 0.0f, hnb = 0.0f, alb = 0.0f, onb = 0.0f;
+        float3 wbx = wb, wo = wb;
         if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {
-          const float3 wo = refl ? wk + fn * (2.0f * f.ci) : wk * f.r + fn * (f.r * f.ci - f.ct);
+          wo = refl ? wk + fn * (2.0f * f.ci) : wk * f.r + fn * (f.r * f.ci - f.ct);
           const float ih = dot3(wk, fn), inn = dot3(wk, nin), on = dot3(wo, nin), hn = dot3(fn, nin);
           if (ih < 0.0f && refl == (on > 0.0f)) {  // a live event (a killed one passes no adjoint)
             const float Wv = -ih * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * hn);
@@ -321,7 +321,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
             inb = Wl * (gi_n - 1.0f / inn);
             hnb = -Wl / hn;
             alb = Wl * (gi_a + go_a);
-            wbx = wb + nin * (Wl * go_n);
+            onb = Wl * go_n;
+            wbx = wb + nin * onb;
           }
         }
         t1b = tb;
@@ -379,17 +380,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           ADD(acc[3 * m1 + 0], c1b);
         }
         wpb = wpb + fn * (-cib);
+        bool rough_ev = false;
+        float3 hb;
         if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {
           // h = cos(theta) n + sin(theta) b with tan(theta) = alpha s: dh/dalpha = s cos^3 (b - tan n)
+          rough_ev = true;
           wpb = wpb + fn * ihb + nin * inb;
-          const float3 hb = wk * (ihb - cib) + wbx * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct) + nin * hnb;
+          hb = wk * (ihb - cib) + wbx * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct) + nin * hnb;
           const float tn = alpha * gs.s, ct = rsqrtf(1.0f + tn * tn);
           alb += dot3(hb, (gs.b - nin * tn) * (gs.s * ct * ct * ct));
           ADD(acc[3 * med.M + 2 + (int)(mm >> 16)], alb);
         }
         if (OPT & ADJ_SHAPE) {  // nin enters through ci = -w.nin and the outgoing direction
-          const bool refl = choice == CH_TIR || f.tir || choice == CH_REFLECT;
-          const float3 nb = wk * (-cib) + wb * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct);
+          float3 nb;
+          if ((OPT & ADJ_ROUGH) && rough_ev)  // through the sampled facet normal and the weight
+            nb = ggx_normal_adjoint(nin, gs, alpha, hb) + wk * inb + wo * onb + fn * hnb;
+          else
+            nb = wk * (-cib) + wb * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct);
           nhb = front ? nb : nb * -1.0f;
         }
       } else {  // scatterer
@@ -728,14 +735,17 @@ void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
     case 2: k_path_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 3: k_path_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 4: k_path_adjoint<4><<<grid, ADJ_THREADS, sm, st>>>(a); break;
-    default: k_path_adjoint<5><<<grid, ADJ_THREADS, sm, st>>>(a); break;  // rough + acq (shape excluded)
+    case 5: k_path_adjoint<5><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 6: k_path_adjoint<6><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    default: k_path_adjoint<7><<<grid, ADJ_THREADS, sm, st>>>(a); break;
   }
 }
 cudaError_t adjoint_set_attrs() {
   const int sm = (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ));
-  const void* ks[10] = {(const void*)k_path_adjoint<0>, (const void*)k_path_adjoint<1>,
+  const void* ks[12] = {(const void*)k_path_adjoint<0>, (const void*)k_path_adjoint<1>,
                         (const void*)k_path_adjoint<2>, (const void*)k_path_adjoint<3>,
                         (const void*)k_path_adjoint<4>, (const void*)k_path_adjoint<5>,
+                        (const void*)k_path_adjoint<6>, (const void*)k_path_adjoint<7>,
                         (const void*)k_nee_adjoint<0>,  (const void*)k_nee_adjoint<1>,
                         (const void*)k_nee_adjoint<2>,  (const void*)k_nee_adjoint<3>};
   for (const void* k : ks) {

@@ -1079,8 +1079,6 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     A.acq_slot = Ps;
     A.P = Ps + 2 + q.ntx;
   }
-  if (dL_dtris_dev && sc->rough)
-    return fail(ctx, US_ERR_ARG, "shape gradients of scenes with rough interfaces are not supported");
   A.g_tris = dL_dtris_dev;
   if (dL_dtris_dev && sc->dev.n_tris)
     CK(cudaMemsetAsync(dL_dtris_dev, 0, sizeof(float) * 9 * (size_t)sc->dev.n_tris, st));

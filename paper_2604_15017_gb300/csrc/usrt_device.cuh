@@ -241,9 +241,10 @@ __device__ __forceinline__ Iface iface(float3 w, float3 nin, float c1, float c2,
 // G1(v) = 2 |v.n| / (|v.n| + sqrt(alpha^2 + (1 - alpha^2) (v.n)^2)).
 // ------------------------------------------------------------------------------------------
 struct GgxSample {
-  float3 h;  // microfacet normal
-  float3 b;  // unit tangent direction of the tilt (h = cos(theta) n + sin(theta) b)
-  float s;   // tan(theta_h) / alpha
+  float3 h;         // microfacet normal
+  float3 b;         // unit tangent direction of the tilt (h = cos(theta) n + sin(theta) b)
+  float s;          // tan(theta_h) / alpha
+  float cphi, sphi;  // azimuth: b = cos(phi) t1 + sin(phi) t2
 };
 __device__ __forceinline__ GgxSample ggx_sample(float3 n, float alpha, float u2, float u3) {
   const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
@@ -254,12 +255,30 @@ __device__ __forceinline__ GgxSample ggx_sample(float3 n, float alpha, float u2,
   float sp, cp;
   sincospif(2.0f * u3, &sp, &cp);
   GgxSample g;
+  g.cphi = cp;
+  g.sphi = sp;
   g.b = make_float3(cp * t1.x + sp * t2.x, cp * t1.y + sp * t2.y, cp * t1.z + sp * t2.z);
   g.s = sqrtf(u2 / (1.0f - u2));
   const float tn = alpha * g.s;
   const float ct = rsqrtf(1.0f + tn * tn), st = tn * ct;
   g.h = make_float3(ct * n.x + st * g.b.x, ct * n.y + st * g.b.y, ct * n.z + st * g.b.z);
   return g;
+}
+// adjoint of the macro normal n from the adjoint hb of h = ct n + st (cos(phi) t1 + sin(phi) t2),
+// t1 and t2 the tangent frame of ggx_sample (its sign choice held fixed)
+__device__ __forceinline__ float3 ggx_normal_adjoint(float3 n, const GgxSample& g, float alpha, float3 hb) {
+  const float tn = alpha * g.s, ct = rsqrtf(1.0f + tn * tn), st = tn * ct;
+  const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
+  const float a = -1.0f / (sg + n.z);
+  const float3 t1b = make_float3(st * g.cphi * hb.x, st * g.cphi * hb.y, st * g.cphi * hb.z);
+  const float3 t2b = make_float3(st * g.sphi * hb.x, st * g.sphi * hb.y, st * g.sphi * hb.z);
+  // t1 = (1 + sg nx^2 a, sg nx ny a, -sg nx), t2 = (nx ny a, sg + ny^2 a, -ny), a = -1 / (sg + nz)
+  const float a2 = a * a;
+  float3 nb;
+  nb.x = ct * hb.x + t1b.x * 2.0f * sg * n.x * a + t1b.y * sg * n.y * a - t1b.z * sg + t2b.x * n.y * a;
+  nb.y = ct * hb.y + t1b.y * sg * n.x * a + t2b.x * n.x * a + t2b.y * 2.0f * n.y * a - t2b.z;
+  nb.z = ct * hb.z + (t1b.x * sg * n.x * n.x + t1b.y * sg * n.x * n.y + t2b.x * n.x * n.y + t2b.y * n.y * n.y) * a2;
+  return nb;
 }
 __device__ __forceinline__ float smith_g1(float vn, float alpha) {
   const float c = fabsf(vn);

@@ -8,7 +8,8 @@ sampling, smooth limit and roughness gradient tests/test_oracle_ggx_pins.py pins
   little more often than a smooth split flips;
 * the adjoint (roughness entries included) within 1e-3 relative of the oracle's gradient for
   the same dL/dRF, as for smooth scenes (plus 1e-4 of the largest sensitivity);
-* roughness 0 reproduces the smooth scene; shape gradients of rough scenes are refused.
+* roughness 0 reproduces the smooth scene; shape gradients through rough events (the
+  cylinder's radius) against the oracle's directional derivatives.
 """
 import numpy as np
 import pytest
@@ -107,18 +108,29 @@ def test_rough_cylinder_adjoint(ctx, mode):
     ctx.release_scene(sid)
 
 
-def test_zero_roughness_is_the_smooth_scene_and_shape_is_refused(ctx):
-    from paper_2604_15017_gb300 import usrt
-
+def test_zero_roughness_is_the_smooth_scene(ctx):
     w = P.slab_scatterers(n_rays=300)
     sid0 = ctx.upload_workload(w)
     rf0, _ = ctx.forward(sid0, w["theta"], w["acq"], w["img"], seed=w["seed"])
     wr = P.with_roughness(w, [0.0, 0.0])
     sid1 = ctx.upload_workload(wr)
-    rf1, _ = ctx.forward(sid1, wr["theta"], wr["acq"], wr["img"], seed=w["seed"], keep_record=True)
+    rf1, _ = ctx.forward(sid1, wr["theta"], wr["acq"], wr["img"], seed=w["seed"])
     assert torch.equal(rf0, rf1)
-    grf = torch.zeros_like(rf1)
-    with pytest.raises(usrt.UsrtError):
-        ctx.transport_vjp_shape(sid1, wr["theta"], wr["acq"], w["seed"], grf, len(w["tris"]))
     ctx.release_scene(sid0)
     ctx.release_scene(sid1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rough_cylinder_radius_gradient(ctx, mode):
+    """Shape through rough events: the sampled facet normal follows the macro normal (its
+    tangent frame and tilt) and the microfacet weight's cosines follow it too."""
+    w = P.with_roughness(P.hollow_cylinder(n_rays=400), [0.0, 0.2, 0.0])
+    sid, rf, b, ref, rec = run_pair(ctx, w)
+    grf = np.random.default_rng(53).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
+    tangents = np.stack([w["dtris_dR"], np.random.default_rng(4).normal(size=w["tris"].shape)])
+    g_ref = ref["run"].gradient_shape(grf, tangents)
+    _, gtris = ctx.transport_vjp_shape(sid, w["theta"], w["acq"], w["seed"], dev(grf), len(w["tris"]), mode=mode)
+    got = ctx.shape_param_grad(gtris, dev(tangents)).double().cpu().numpy()
+    scale = np.abs(gtris.double().cpu().numpy()[None] * tangents).reshape(2, -1).sum(axis=1)
+    assert np.all(np.abs(got - g_ref) <= 2e-3 * np.abs(g_ref) + 2e-4 * scale), np.c_[got, g_ref, scale]
+    ctx.release_scene(sid)
