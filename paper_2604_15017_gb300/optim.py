@@ -62,7 +62,8 @@ class ShapeModel:
     def upload(self, ctx, q):
         tris, dq = self.make(np.asarray(q, dtype=np.float64))
         w = self.w
-        sid = ctx.upload_scene(tris, w["media"], w["M"], w["scat_pos"], w["scat_amp"], w["r_s"])
+        sid = ctx.upload_scene(tris, w["media"], w["M"], w["scat_pos"], w["scat_amp"], w["r_s"],
+                               rough=w.get("rough", False))
         return sid, torch.tensor(np.asarray(dq), dtype=torch.float32, device=ctx.device), len(tris)
 
 

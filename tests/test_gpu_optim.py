@@ -147,9 +147,44 @@ def test_sim_to_sim_recovery_of_the_cylinder_radius_and_wall_density(ctx):
     prob = optim.InverseProblem(ctx, None, th0, lo, hi, 0.02, optim.split_rays(w["acq"], 2), w["img"],
                                 seed=w["seed"], shape=shape)
     prob.set_targets(tgt)
-    losses = prob.run(30)
-    th = prob.physical().astype(np.float64)
-    assert losses[-1] < 0.5 * losses[0], losses
+    hist = []
+    for _ in range(45):
+        th = prob.physical().astype(np.float64)  # the parameters this iteration's loss belongs to
+        hist.append((prob.step(), th))
+    best_loss, th = min(hist, key=lambda t: t[0])
+    assert best_loss < 0.2 * hist[0][0], [h[0] for h in hist]
     assert np.all(np.abs(th[free] - tgt[free]) < 0.5 * np.abs(th0[free] - tgt[free])), np.c_[th[free], tgt[free]]
     fixed = np.setdiff1d(np.arange(len(th0)), free)
     assert np.allclose(th[fixed], th0[fixed], rtol=1e-6)
+
+
+def test_sim_to_sim_recovery_on_a_rough_walled_cylinder(ctx):
+    """The same recovery with a rough wall (GGX roughness 0.2, held fixed): the radius gradient
+    runs through rough events (sampled facet normals follow the moving mesh).  The loss is flat
+    in R for the first 0.05 mm here and Adam overshoots the density afterwards, so the check is
+    on the best iterate of 45: its loss below a fifth of the first, both parameters more than
+    halfway to the target."""
+    from paper_2604_15017_gb300 import optim
+
+    w = P.with_roughness(P.hollow_cylinder(n_rays=1500), [0.0, 0.2, 0.0])
+    n_mat = len(w["theta"])
+    shape = optim.ShapeModel(lambda q: (lambda m: (m[0], m[2][None]))(P.hollow_cylinder_mesh(radius=q[0])), w,
+                             [w["radius"]])
+    th0 = np.concatenate([w["theta"], [w["radius"]]])
+    free = np.array([4, n_mat])
+    tgt = th0.copy()
+    tgt[4] *= 1.08
+    tgt[n_mat] = 5.15e-3
+    lo, hi = th0.copy(), th0.copy()
+    lo[4], hi[4] = 0.85 * th0[4], 1.15 * th0[4]
+    lo[n_mat], hi[n_mat] = 4.7e-3, 5.3e-3
+    prob = optim.InverseProblem(ctx, None, th0, lo, hi, 0.02, optim.split_rays(w["acq"], 2), w["img"],
+                                seed=w["seed"], shape=shape)
+    prob.set_targets(tgt)
+    hist = []
+    for _ in range(45):
+        th = prob.physical().astype(np.float64)  # the parameters this iteration's loss belongs to
+        hist.append((prob.step(), th))
+    best_loss, th = min(hist, key=lambda t: t[0])
+    assert best_loss < 0.2 * hist[0][0], [h[0] for h in hist]
+    assert np.all(np.abs(th[free] - tgt[free]) < 0.5 * np.abs(th0[free] - tgt[free])), np.c_[th[free], tgt[free]]
