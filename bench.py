@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-stages", action="store_true")
+    ap.add_argument("--rough", type=float, default=0.0,
+                    help="frame: GGX roughness of every inclusion's interface (0: smooth, the default workload)")
     ap.add_argument("--shape-grad", action="store_true",
                     help="frame: the adjoint also returns dL/d(triangle vertices) (us_adjoint_shape)")
     ap.add_argument("--acq-grad", action="store_true",
@@ -427,6 +429,8 @@ def main():
         return
 
     w = P.inclusions(n_rays=args.rays)
+    if args.rough > 0.0:
+        w = P.with_roughness(w, [0.0] + [args.rough] * (w["M"] - 1))
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -555,6 +559,7 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "inclusions-200k-tris-1e5-scatterers-16tx-1e6rays",
                       "step": "fwd+adj" + ("+acq" if args.acq_grad else ("+shape" if args.shape_grad else "")),
+                      "roughness": args.rough,
                       "adjoint_mode": args.mode, "paths_per_step": stats["n_paths"],
                       "segments_per_step": stats["segments"], "nee_queries_per_step": stats["nee_queries"],
                       "arrivals_per_step": stats["arrivals"], "frames_per_s": world * 1e3 / ms,
