@@ -466,16 +466,22 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
 // tau_n = tau' + sum l / c go to theta, and the seeds (dL/da', dL/dtau') are left for the
 // path's reverse sweep.
 // ------------------------------------------------------------------------------------------
+// The rows hold only the slots a secondary ray touches (nee_row_len): the 3M + 2 material
+// parameters and, with the acquisition option, the pitch at 3M + 2; no roughness slots (the
+// crossings are smooth), so a rough scene costs no more shared memory (and L1) than a smooth one.
+__host__ __device__ inline int nee_row_len(int M, bool acq) { return 3 * M + 2 + (acq ? 1 : 0); }
+
 template <int OPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
   extern __shared__ float gsm[];
   const Acq& q = A.acq;
   const Media& med = A.med;
   const int P = A.P;
-  const int PS = adj_row_stride(P);
+  const int R = nee_row_len(med.M, (OPT & ADJ_ACQ) != 0);
+  const int PS = adj_row_stride(R);
   float* acc = gsm + threadIdx.x * PS;
   const int iAs = 3 * med.M, iF0 = 3 * med.M + 1;
-  for (int p = 0; p < P; ++p) acc[p] = 0.0f;
+  for (int p = 0; p < R; ++p) acc[p] = 0.0f;
   const int K1 = q.kmax + 1;
   const float kap = KAPPA_F;
   uint32_t total = 0;
@@ -604,14 +610,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       mm_cur = m2;
       tprev = tc;
     }
-    if (acq) ADD(acc[A.acq_slot + 1], gX * ((float)e2 - 0.5f * (float)(q.ne - 1)));
+    if (acq) ADD(acc[3 * med.M + 2], gX * ((float)e2 - 0.5f * (float)(q.ne - 1)));  // the pitch
     *seed = make_float2(ga * k_n, gt);
   }
   __syncthreads();
   float* out = A.gpart + (size_t)blockIdx.x * P;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    // the row slot of gradient slot p (-1: a slot secondary rays do not touch)
+    const int rp = p < 3 * med.M + 2 ? p : (((OPT & ADJ_ACQ) && p == A.acq_slot + 1) ? 3 * med.M + 2 : -1);
     float s = 0.0f;
-    for (int t = 0; t < (int)blockDim.x; ++t) s += gsm[t * PS + p];
+    if (rp >= 0)
+      for (int t = 0; t < (int)blockDim.x; ++t) s += gsm[t * PS + rp];
     out[p] = (A.accumulate ? out[p] : 0.0f) + s;
   }
 }
@@ -712,7 +721,7 @@ static int adj_opt(const AdjArgs& a) {
   return (a.acq_slot >= 0 ? ADJ_ACQ : 0) | (a.g_tris ? ADJ_SHAPE : 0) | (a.med.has_rough ? ADJ_ROUGH : 0);
 }
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
-  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);
+  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(nee_row_len(a.med.M, a.acq_slot >= 0));
   switch (adj_opt(a) & (ADJ_ACQ | ADJ_SHAPE)) {  // secondary rays cross rough interfaces as smooth ones
     case 0: k_nee_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 1: k_nee_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
