@@ -29,7 +29,7 @@ UNIT = "segments/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="record", choices=["record", "recompute"])
@@ -37,6 +37,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-stages", action="store_true")
+    ap.add_argument("--nee-stream", type=int, default=-1,
+                    help="frame: US_OPT_NEE_STREAM (secondary rays on a second stream, %% of their grid; -1: default)")
     ap.add_argument("--rough", type=float, default=0.0,
                     help="frame: GGX roughness of every inclusion's interface (0: smooth, the default workload)")
     ap.add_argument("--shape-grad", action="store_true",
@@ -445,6 +447,8 @@ def main():
     from paper_2604_15017_gb300 import usrt
 
     ctx = usrt.Context(local)
+    if args.nee_stream >= 0:
+        ctx.set_option(usrt.OPT_NEE_STREAM, args.nee_stream)
     sid = ctx.upload_workload(w)
     acq, img = w["acq"], w["img"]
     seed = w["seed"] + 1000 * rank  # independent frames per rank

@@ -152,6 +152,11 @@ enum {
   /* lanes (concurrent request pipelines, each with its own stream and workspaces) used by
    * us_forward_batch; default 4, at most 16 */
   US_OPT_LANES = 1,
+  /* secondary rays on a second stream: 0 runs each round's secondary-ray kernel after that
+   * round's primary rays on the call's stream; p in 1..100 (default 100) runs it on a second
+   * stream of the lane (forked and joined with events, so the call stays one stream-ordered
+   * unit), overlapping the next rounds' primary rays, with p % of its resident grid. */
+  US_OPT_NEE_STREAM = 2,
   US_N_OPTS
 };
 int us_set_option(us_ctx* ctx, int option, int value);

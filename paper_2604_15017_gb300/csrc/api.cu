@@ -79,6 +79,10 @@ struct Lane {
   bool stats_valid = false;
   cudaStream_t stream = nullptr;  // lane 0: none (the caller's stream)
   cudaEvent_t ev_done = nullptr;
+  // second stream for the secondary rays (US_OPT_NEE_STREAM): fork events per round, a join event
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork[MAX_KMAX + 2] = {};
+  cudaEvent_t ev_join = nullptr;
 };
 
 }  // namespace
@@ -205,6 +209,10 @@ void free_lane(us_ctx* ctx, Lane* l) {
   if (l->h_cnt) cudaFreeHost(l->h_cnt);
   if (l->ev_stats) cudaEventDestroy(l->ev_stats);
   if (l->ev_done) cudaEventDestroy(l->ev_done);
+  for (cudaEvent_t e : l->ev_fork)
+    if (e) cudaEventDestroy(e);
+  if (l->ev_join) cudaEventDestroy(l->ev_join);
+  if (l->side) cudaStreamDestroy(l->side);
   if (l->stream) cudaStreamDestroy(l->stream);
   delete l;
 }
@@ -429,6 +437,18 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   A.cnt = cnt;
   CK(cudaMemsetAsync(cnt, 0, sizeof(Counters), st));
   if (record) CK(cudaMemsetAsync(record, 0, sizeof(uint32_t) * (size_t)n * (q.kmax + 1), st));
+  // secondary rays on the lane's second stream (US_OPT_NEE_STREAM): round k's kernel waits for
+  // its sorted jobs (fork event k), and the call's stream waits for all of them at the end
+  const int nee_pct = std::min(100, std::max(0, ctx->opts[US_OPT_NEE_STREAM]));
+  const bool side = do_nee && sc->dev.n_scat > 0 && nee_pct > 0;
+  Lane* L = ctx->L;
+  if (side && !L->side) {
+    CK(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : L->ev_fork) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
+  }
+  const int nee_grid = side ? std::max(ctx->num_sms, grid_of(ctx, ctx->nee_per_sm) * nee_pct / 100)
+                            : grid_of(ctx, ctx->nee_per_sm);
   RaySort rs;
   for (int a = 0; a < 3; ++a) {
     const float ext = std::max(sc->hi[a] - sc->lo[a], 1e-6f);
@@ -469,9 +489,19 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     }
     A.nee = sorted;
     if (do_nee && sc->dev.n_scat > 0) {
-      StageScope sc_(ctx, US_STAGE_NEE, 1, st);
-      launch_nee(A, grid_of(ctx, ctx->nee_per_sm), st);
+      cudaStream_t ns = st;
+      if (side) {
+        CK(cudaEventRecord(L->ev_fork[k], st));
+        CK(cudaStreamWaitEvent(L->side, L->ev_fork[k], 0));
+        ns = L->side;
+      }
+      StageScope sc_(ctx, US_STAGE_NEE, 1, ns);
+      launch_nee(A, nee_grid, ns);
     }
+  }
+  if (side) {
+    CK(cudaEventRecord(L->ev_join, L->side));
+    CK(cudaStreamWaitEvent(st, L->ev_join, 0));
   }
   CK(cudaGetLastError());
   return US_OK;
@@ -571,6 +601,7 @@ int us_create(us_ctx** out, int device, size_t mem_budget_bytes) {
     return US_ERR_CUDA;
   }
   ctx->opts[US_OPT_LANES] = 4;
+  ctx->opts[US_OPT_NEE_STREAM] = 100;
   ctx->trav_per_sm = traverse_blocks_per_sm();
   ctx->march_per_sm = march_blocks_per_sm();
   ctx->nee_per_sm = nee_blocks_per_sm();

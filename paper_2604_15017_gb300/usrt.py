@@ -29,7 +29,7 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step", "us_das_acq_vjp",
            "us_transport_vjp_acq", "us_adjoint_acq", "us_transport_vjp_shape", "us_adjoint_shape",
            "us_shape_param_grad"]
-OPT_DAS_TMA, OPT_LANES = 0, 1
+OPT_DAS_TMA, OPT_LANES, OPT_NEE_STREAM = 0, 1, 2
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq"]
 
