@@ -143,10 +143,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
   const int iAs = 3 * med.M, iF0 = 3 * med.M + 1;
   for (int p = 0; p < P; ++p) acc[p] = 0.0f;
   const int K1 = q.kmax + 1;
+  // per-event state kept for the reverse sweep (local memory): origin, direction, amplitude;
+  // the record word, the medium and the secondary-ray seeds are read or derived again there
   float3 O[MAX_KMAX + 1], W[MAX_KMAX + 1];
-  float Aa[MAX_KMAX + 1], SA[MAX_KMAX + 1], ST[MAX_KMAX + 1];
-  int Mk[MAX_KMAX + 1];
-  uint32_t Rw[MAX_KMAX + 1];
+  float Aa[MAX_KMAX + 1];
   const float kap = KAPPA_F;
   const uint32_t n_act = *A.n_active;
   for (uint32_t ai = blockIdx.x * blockDim.x + threadIdx.x; ai < n_act; ai += gridDim.x * blockDim.x) {
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
     const float st0 = q.sin_tx[tx];
     const float tau0 = (xe * st0 + 0.5f * (q.ne - 1) * q.pitch * fabsf(st0)) / q.cbf;
     float th = tau0, tl = 0.0f;
-    int m = 0;
+    int m = 0, m_last = 0;
     int nseg = 0;
     float gxa = 0.0f, gxt = 0.0f;
     const uint32_t* rec = A.record + (size_t)i * K1;
@@ -180,10 +180,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       O[k] = o;
       W[k] = w;
       Aa[k] = a;
-      Mk[k] = m;
-      Rw[k] = r;
-      SA[k] = 0.0f;
-      ST[k] = 0.0f;
+      m_last = m;
       nseg = k + 1;
       const float t = frozen_t(A.S, cls, id, o, w);
       const float a1 = a * expf(-kap * med.al[m] * med.f0 * t);
@@ -240,23 +237,29 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           const float inn = dot3(w_in, nin), on = dot3(w, nin);
           a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
         }
-      } else {  // scatterer: the secondary ray's adjoint seeds come from k_nee_adjoint
-        const float2 sd = A.seeds[(size_t)i * K1 + k];
-        SA[k] = sd.x;
-        ST[k] = sd.y;
-        a = a1;  // Born pass-through: amplitude after the segment, direction unchanged
+      } else {  // scatterer: Born pass-through (amplitude after the segment, direction unchanged)
+        a = a1;
       }
       o = x;
     }
     // ---- reverse sweep ----
     float ab = 0.0f, tb = 0.0f;
     float3 ob = f3(0.f, 0.f, 0.f), wb = f3(0.f, 0.f, 0.f);
+    int m_next = m_last;  // medium of segment k + 1 (of the last segment to start with)
     for (int k = nseg - 1; k >= 0; --k) {
       const float3 ok = O[k], wk = W[k];
       const float ak = Aa[k];
-      const int mk = Mk[k];
-      const uint32_t r = Rw[k];
+      const uint32_t r = rec[k];
       const uint32_t cls = code_cls(r), id = code_id(r);
+      // medium of segment k: the incident side of a hit triangle, else that of segment k + 1
+      // (a scatterer keeps the medium; the last segment's was kept)
+      int mk = m_next;
+      if (cls == CLS_TRI && k < nseg - 1) {
+        const float4 nr = __ldg(&A.S.tri_nrm[id]);
+        const uint32_t mm = __float_as_uint(nr.w);
+        mk = dot3(wk, xyz(nr)) < 0.0f ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+      }
+      m_next = mk;
       const float t = frozen_t(A.S, cls, id, ok, wk);
       const float att = expf(-kap * med.al[mk] * med.f0 * t);
       const float a1 = ak * att;
@@ -400,8 +403,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           nhb = front ? nb : nb * -1.0f;
         }
       } else {  // scatterer
-        a1b = ab + SA[k];
-        t1b = tb + ST[k];
+        const float2 sd = A.seeds[(size_t)i * K1 + k];  // the secondary ray's adjoint seeds
+        a1b = ab + sd.x;
+        t1b = tb + sd.y;
         xb = ob;
         wpb = wb;
       }
