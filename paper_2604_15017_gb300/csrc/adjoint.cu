@@ -647,14 +647,33 @@ __device__ __forceinline__ int path_class(const uint32_t* rec, int kmax) {
   return active ? nseg : -1;
 }
 
-__global__ void k_active_count(const uint32_t* record, uint32_t n, int kmax, uint32_t* work, uint8_t* pclass) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = path_class(record + (size_t)i * (kmax + 1), kmax);
-    pclass[i] = (uint8_t)(c < 0 ? 0xFF : c);  // read back by k_active_fill instead of the record
-    if (c < 0) continue;
-    const unsigned same = __match_any_sync(__activemask(), c);  // lanes of this class
-    if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&work[c], (uint32_t)__popc(same));
+// One tile of ACT_TILE paths per block iteration: the tile's record rows are read into shared
+// memory with coalesced loads, each thread classifies its path from there, and the per-class
+// counts go through shared memory to one global atomic per class and block.
+constexpr int ACT_TILE = 256;
+__global__ void __launch_bounds__(ACT_TILE) k_active_count(const uint32_t* record, uint32_t n, int kmax,
+                                                           uint32_t* work, uint8_t* pclass) {
+  extern __shared__ uint32_t rows[];  // [ACT_TILE][kmax + 1]
+  __shared__ uint32_t cnt[17];
+  const int K1 = kmax + 1;
+  if (threadIdx.x < 17) cnt[threadIdx.x] = 0u;
+  for (uint32_t base = blockIdx.x * ACT_TILE; base < n; base += gridDim.x * ACT_TILE) {
+    const uint32_t m = min((uint32_t)ACT_TILE, n - base);
+    __syncthreads();
+    const uint32_t* src = record + (size_t)base * K1;
+    for (uint32_t j = threadIdx.x; j < m * (uint32_t)K1; j += ACT_TILE) rows[j] = __ldg(&src[j]);
+    __syncthreads();
+    if (threadIdx.x < m) {
+      const int c = path_class(rows + threadIdx.x * K1, kmax);
+      pclass[base + threadIdx.x] = (uint8_t)(c < 0 ? 0xFF : c);  // read back by k_active_fill
+      if (c >= 0) {
+        const unsigned same = __match_any_sync(__activemask(), c);  // lanes of this class
+        if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[c], (uint32_t)__popc(same));
+      }
+    }
   }
+  __syncthreads();
+  if (threadIdx.x < 17 && cnt[threadIdx.x]) atomicAdd(&work[threadIdx.x], cnt[threadIdx.x]);
 }
 
 __global__ void k_active_scan(uint32_t* work) {
@@ -669,17 +688,31 @@ __global__ void k_active_scan(uint32_t* work) {
   }
 }
 
-__global__ void k_active_fill(const uint8_t* pclass, uint32_t n, uint32_t* work, uint32_t* active) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = pclass[i] == 0xFF ? -1 : (int)pclass[i];
-    if (c < 0) continue;
-    const unsigned same = __match_any_sync(__activemask(), c);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(same) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(&work[34 + c], (uint32_t)__popc(same));
-    base = __shfl_sync(same, base, leader);
-    active[work[17 + c] + base + __popc(same & ((1u << lane) - 1u))] = i;
+// Per block iteration: the tile's paths are counted per class in shared memory, one global
+// atomic per class reserves the tile's range in that class, and the tile's paths take slots
+// in it through shared-memory counters (the order inside a class is free).
+__global__ void __launch_bounds__(ACT_TILE) k_active_fill(const uint8_t* pclass, uint32_t n, uint32_t* work,
+                                                          uint32_t* active) {
+  __shared__ uint32_t cnt[17], at[17];
+  for (uint32_t base = blockIdx.x * ACT_TILE; base < n; base += gridDim.x * ACT_TILE) {
+    if (threadIdx.x < 17) cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint32_t i = base + threadIdx.x;
+    const int c = i < n && pclass[i] != 0xFF ? (int)pclass[i] : -1;
+    uint32_t off = 0u;
+    if (c >= 0) {
+      const unsigned same = __match_any_sync(__activemask(), c);
+      const int lane = threadIdx.x & 31, leader = __ffs(same) - 1;
+      uint32_t b = 0u;
+      if (lane == leader) b = atomicAdd(&cnt[c], (uint32_t)__popc(same));
+      off = __shfl_sync(same, b, leader) + __popc(same & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    if (threadIdx.x < 17)
+      at[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&work[34 + threadIdx.x], cnt[threadIdx.x]) : 0u;
+    __syncthreads();
+    if (c >= 0) active[work[17 + c] + at[c] + off] = i;
+    __syncthreads();
   }
 }
 
@@ -736,9 +769,10 @@ void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
 void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint8_t* pclass,
                          uint32_t* active, int grid, cudaStream_t st) {
   cudaMemsetAsync(work, 0, sizeof(uint32_t) * 52, st);
-  k_active_count<<<grid, 256, 0, st>>>(record, n_paths, kmax, work, pclass);
+  k_active_count<<<grid, ACT_TILE, sizeof(uint32_t) * ACT_TILE * (kmax + 1), st>>>(record, n_paths, kmax, work,
+                                                                                  pclass);
   k_active_scan<<<1, 32, 0, st>>>(work);
-  k_active_fill<<<grid, 256, 0, st>>>(pclass, n_paths, work, active);
+  k_active_fill<<<grid, ACT_TILE, 0, st>>>(pclass, n_paths, work, active);
 }
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);

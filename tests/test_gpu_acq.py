@@ -128,10 +128,11 @@ def test_transport_vjp_acq_matches_oracle(ctx, mode):
     n_th = len(w["theta"])
     gth, gacq = ctx.transport_vjp_acq(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode)
     assert within(gacq.double().cpu().numpy(), full[n_th:], 2e-3), np.c_[gacq.cpu().numpy(), full[n_th:]]
-    # the scene slots are those of the plain transport VJP (the active-path list is built with
-    # atomics, so the FP32 sums may run in another order)
+    # the scene slots are those of the plain transport VJP up to FP32 summation order (the
+    # active-path list and, in recompute mode, the job order come from atomics): 1e-4, as for
+    # the record-mode image reuse in test_gpu_parity.py
     g_plain = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode)
-    assert torch.allclose(gth, g_plain, rtol=1e-5, atol=1e-6 * float(g_plain.abs().max()))
+    assert torch.allclose(gth, g_plain, rtol=1e-4, atol=1e-5 * float(g_plain.abs().max()))
     ctx.release_scene(sid)
 
 

@@ -69,7 +69,7 @@ def test_transport_vjp_shape_matches_oracle(ctx, mode):
     gth, gtris = ctx.transport_vjp_shape(sid, w["theta"], w["acq"], w["seed"], dev(grf), len(w["tris"]), mode=mode)
     compare(ctx, gtris, tangents, g_ref)
     g_plain = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode)
-    assert torch.allclose(gth, g_plain, rtol=1e-5, atol=1e-6 * float(g_plain.abs().max()))
+    assert torch.allclose(gth, g_plain, rtol=1e-4, atol=1e-5 * float(g_plain.abs().max()))
     ctx.release_scene(sid)
 
 
