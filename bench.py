@@ -117,7 +117,8 @@ def peaks():
         return {}
 
 
-# algorithmic work per unit of each stage
+# algorithmic work per unit of each stage: a closest-hit query is a log-depth search over the
+# scene's primitives (box tests per node visit plus a few primitive tests), counted in FP32 flop
 FMA_LANES_PER_SM = 128  # FP32 lanes per SM (sm_100-class)
 
 
