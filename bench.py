@@ -65,6 +65,28 @@ def dist_env():
     return rank, world, local
 
 
+# Replicas (one process per GPU, independent frames, no data-path collective): each rank
+# renders its own realisation, the slowest rank's time sets the whole job's throughput.
+def replica_seed(base, rank):
+    return base + 1000 * rank
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks (a collective on the process group; x itself with one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -452,7 +474,7 @@ def main():
         ctx.set_option(usrt.OPT_NEE_STREAM, args.nee_stream)
     sid = ctx.upload_workload(w)
     acq, img = w["acq"], w["img"]
-    seed = w["seed"] + 1000 * rank  # independent frames per rank
+    seed = replica_seed(w["seed"], rank)  # independent frames per rank
     mode = usrt.MODE_RECORD if args.mode == "record" else usrt.MODE_RECOMPUTE
     # target image at the perturbed parameters (outside the timed region)
     _, bref = ctx.forward(sid, P.perturbed_theta(w["theta"], 7), acq, img, seed=seed)
@@ -503,13 +525,8 @@ def main():
     stages = ctx.profile_read()
     ctx.profile(False)
     gpu_launches = ctx.launch_count() - launches0
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t)
-    value = segs_per_step * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = whole_job_rate(segs_per_step, world, ms * 1e-3)
 
     # end to end through the public API with host buffers: B_ref host -> device each step,
     # loss and gradient device -> host each step
@@ -531,8 +548,8 @@ def main():
             gacq_h.copy_(gacq, non_blocking=True)
         loss_h.copy_(loss, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e = {"value": segs_per_step * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bref_h.numel() * 4,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, "cuda")
+    e2e = {"value": whole_job_rate(segs_per_step, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": bref_h.numel() * 4,
            "d2h_bytes_per_step": 4 * (len(theta) + 1 + (gacq_h.numel() if (args.acq_grad or args.shape_grad) else 0))}
 
     # roofline of the dominant stage, from its live CUDA-event time over the timed region
