@@ -35,7 +35,7 @@ def _rank(rank, world, port, out):
 
 def test_two_gloo_ranks_agree_on_the_slowest_time():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork from a multi-threaded test process
         out = m.dict()
         mp.start_processes(_rank, args=(world, free_port(), out), nprocs=world, join=True, start_method="spawn")
         res = dict(out)
