@@ -64,3 +64,10 @@ def test_shape_gradient_is_linear_in_the_tangent_and_keeps_the_scene_gradient():
     assert np.allclose(full[n_th + 2], 2.0 * full[n_th] - 3.0 * full[n_th + 1], rtol=1e-9,
                        atol=1e-12 * np.abs(full[n_th:]).max())
     assert np.allclose(full[:n_th], ref["run"].gradient(grf), rtol=1e-12, atol=1e-12 * np.abs(full[:n_th]).max())
+
+
+def test_rough_walled_cylinder_radius():
+    """d/dR through rough events: the sampled facet normal follows the moving macro normal (its
+    tangent frame and tilt), and so do the microfacet weight's cosines."""
+    w = P.with_roughness(P.hollow_cylinder(n_rays=100), [0.0, 0.2, 0.0])
+    check(w, [w["dtris_dR"]], 6)
