@@ -134,3 +134,43 @@ def test_rough_cylinder_radius_gradient(ctx, mode):
     scale = np.abs(gtris.double().cpu().numpy()[None] * tangents).reshape(2, -1).sum(axis=1)
     assert np.all(np.abs(got - g_ref) <= 2e-3 * np.abs(g_ref) + 2e-4 * scale), np.c_[got, g_ref, scale]
     ctx.release_scene(sid)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_rough_acquisition_gradient(ctx, mode):
+    """Acquisition gradients on a rough scene (the path adjoint's rough + acquisition variant):
+    the acquisition slots follow the roughness slots."""
+    w = P.with_roughness(P.slab_scatterers(n_rays=800), [0.0, 0.25])
+    sid, rf, b, ref, rec = run_pair(ctx, w)
+    grf = np.random.default_rng(54).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
+    full = ref["run"].gradient_acq(grf, full=True)
+    n_th = len(w["theta"])
+    gth, gacq = ctx.transport_vjp_acq(sid, w["theta"], w["acq"], w["seed"], dev(grf), mode=mode)
+    ga, fa = gacq.double().cpu().numpy(), full[n_th:]
+    assert np.all(np.abs(ga - fa) <= 2e-3 * np.abs(fa) + 1e-4 * np.abs(fa).max()), np.c_[ga, fa]
+    g = gth.double().cpu().numpy()
+    scale = np.abs(full[:n_th] * np.maximum(np.abs(w["theta"]), 1e-2))
+    err = np.abs(g - full[:n_th]) * np.maximum(np.abs(w["theta"]), 1e-2)
+    assert np.all(err <= 1e-3 * scale + 1e-4 * scale.max()), np.c_[g, full[:n_th]]
+    ctx.release_scene(sid)
+
+
+def test_rough_scene_through_a_batch(ctx):
+    """A rough scene's 4M + 2 parameters through the batched request path (forward, loss and
+    adjoint in one request) equal the single calls."""
+    from paper_2604_15017_gb300 import usrt
+
+    w = P.with_roughness(P.slab_scatterers(n_rays=300), [0.0, 0.2])
+    sid = ctx.upload_workload(w)
+    _, bref = ctx.forward(sid, w["theta_target"], w["acq"], w["img"], seed=w["seed"])
+    bref = bref.clone()
+    out = usrt.Batch(ctx, [dict(scene=sid, theta=w["theta"], acq=w["acq"], img=w["img"], seed=w["seed"],
+                                bref=bref)]).run()[0]
+    torch.cuda.synchronize()
+    rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    loss, gb = ctx.loss(w["img"], b, bref)
+    g, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, gb)
+    assert out["grad"].shape == (4 * w["M"] + 2,)
+    assert abs(float(out["loss"]) - float(loss)) <= 1e-4 * abs(float(loss))
+    assert torch.allclose(out["grad"], g, rtol=1e-3, atol=1e-4 * float(g.abs().max()))
+    ctx.release_scene(sid)
