@@ -29,7 +29,7 @@ enum Slot {
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
   W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS,
-  W_ACQ_PART, W_COUNT
+  W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_COUNT
 };
 
 struct SceneGPU {
@@ -459,6 +459,15 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   CKS(ws(ctx, W_RAY_CNT, RAY_BUCKETS, st, &rs.cnt));
   CKS(ws(ctx, W_RAY_OFF, RAY_BUCKETS + 1, st, &rs.off));
   CKS(ws(ctx, W_RAY_CUR, RAY_BUCKETS, st, &rs.cursor));
+  // the job sort's scratch: the ray sort's, or its own when it runs on the second stream
+  // beside the next round's ray sort
+  RaySort js = rs;
+  if (side) {
+    CKS(ws(ctx, W_JOB_KEY, n, st, &js.key));
+    CKS(ws(ctx, W_JOB_CNT, RAY_BUCKETS, st, &js.cnt));
+    CKS(ws(ctx, W_JOB_OFF, RAY_BUCKETS + 1, st, &js.off));
+    CKS(ws(ctx, W_JOB_CUR, RAY_BUCKETS, st, &js.cursor));
+  }
   // Q.a: rays as generated / as the interaction kernel appends them; Q.b: coherence-sorted
   A.qout = Q.a;
   {
@@ -483,18 +492,19 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
       StageScope sc_(ctx, US_STAGE_INTERACT, 1, st);
       launch_interact(A, grid_of(ctx, 8), st);
     }
+    // the round's secondary rays (job sort, then the kernel): on the second stream from here
+    cudaStream_t ns = st;
+    if (side) {
+      CK(cudaEventRecord(L->ev_fork[k], st));
+      CK(cudaStreamWaitEvent(L->side, L->ev_fork[k], 0));
+      ns = L->side;
+    }
     if (sort_jobs && k < q.kmax) {
-      StageScope sc_(ctx, US_STAGE_GENERATE, 3, st);
-      launch_job_sort(A, unsorted, sorted, rs, grid_of(ctx, 2), st);
+      StageScope sc_(ctx, US_STAGE_GENERATE, 3, ns);
+      launch_job_sort(A, unsorted, sorted, js, grid_of(ctx, 2), ns);
     }
     A.nee = sorted;
     if (do_nee && sc->dev.n_scat > 0) {
-      cudaStream_t ns = st;
-      if (side) {
-        CK(cudaEventRecord(L->ev_fork[k], st));
-        CK(cudaStreamWaitEvent(L->side, L->ev_fork[k], 0));
-        ns = L->side;
-      }
       StageScope sc_(ctx, US_STAGE_NEE, 1, ns);
       launch_nee(A, nee_grid, ns);
     }
