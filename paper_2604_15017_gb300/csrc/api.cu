@@ -83,6 +83,7 @@ struct Lane {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork[MAX_KMAX + 2] = {};
   cudaEvent_t ev_join = nullptr;
+  cudaEvent_t ev_afork = nullptr, ev_ajoin = nullptr;  // the adjoint's fork and join
 };
 
 }  // namespace
@@ -212,6 +213,8 @@ void free_lane(us_ctx* ctx, Lane* l) {
   for (cudaEvent_t e : l->ev_fork)
     if (e) cudaEventDestroy(e);
   if (l->ev_join) cudaEventDestroy(l->ev_join);
+  if (l->ev_afork) cudaEventDestroy(l->ev_afork);
+  if (l->ev_ajoin) cudaEventDestroy(l->ev_ajoin);
   if (l->side) cudaStreamDestroy(l->side);
   if (l->stream) cudaStreamDestroy(l->stream);
   delete l;
@@ -399,6 +402,17 @@ int alloc_queues(us_ctx* ctx, long long n, cudaStream_t st, Queues& Q) {
 
 // transport of paths [path0, path0 + n): generate + (k_max + 1) rounds of traverse / interact /
 // secondary rays.  arr may be null (no arrivals: decisions only).
+// the lane's second stream and its events (US_OPT_NEE_STREAM), made on first use
+int ensure_side(us_ctx* ctx, Lane* L) {
+  if (L->side) return US_OK;
+  CK(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : L->ev_fork) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&L->ev_afork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&L->ev_ajoin, cudaEventDisableTiming));
+  return US_OK;
+}
+
 int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& q, long long path0, uint32_t n,
                   Arrival* arr, uint32_t arr_cap, uint32_t* record, bool do_nee, Counters* cnt, cudaStream_t st) {
   Queues Q;
@@ -442,11 +456,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   const int nee_pct = std::min(100, std::max(0, ctx->opts[US_OPT_NEE_STREAM]));
   const bool side = do_nee && sc->dev.n_scat > 0 && nee_pct > 0;
   Lane* L = ctx->L;
-  if (side && !L->side) {
-    CK(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking));
-    for (cudaEvent_t& e : L->ev_fork) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&L->ev_join, cudaEventDisableTiming));
-  }
+  if (side) CKS(ensure_side(ctx, L));
   const int nee_grid = side ? std::max(ctx->num_sms, grid_of(ctx, ctx->nee_per_sm) * nee_pct / 100)
                             : grid_of(ctx, ctx->nee_per_sm);
   RaySort rs;
@@ -1150,18 +1160,37 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     CKS(ws(ctx, W_ACT_CNT, 64, st, &work));
     A.active = active;
     A.n_active = work + 51;
-    if (sc->dev.n_scat > 0 && A.nee.job) {
+    uint8_t* pclass;
+    CKS(ws(ctx, W_PCLASS, (size_t)n, st, &pclass));
+    // the active-path lists (a pass over the record) do not depend on the secondary-ray
+    // adjoint: on the lane's second stream they run beside it
+    const bool nee_adj = sc->dev.n_scat > 0 && A.nee.job;
+    const bool fork = nee_adj && ctx->opts[US_OPT_NEE_STREAM] > 0;
+    Lane* L = ctx->L;
+    cudaStream_t as = st;
+    if (fork) {
+      CKS(ensure_side(ctx, L));
+      CK(cudaEventRecord(L->ev_afork, st));
+      CK(cudaStreamWaitEvent(L->side, L->ev_afork, 0));
+      as = L->side;
+    }
+    {
+      StageScope sc_(ctx, US_STAGE_PATH_ADJ, 3, as);
+      launch_active_paths(rec, n, q.kmax, work, pclass, active, grid_of(ctx, 4), as);
+    }
+    if (nee_adj) {
       A.gpart = gpart + (size_t)grid * A.P;
       StageScope sc_(ctx, US_STAGE_NEE_ADJ, 1, st);
       launch_nee_adjoint(A, grid, st);
     } else if (!accumulate) {
       CK(cudaMemsetAsync(gpart + (size_t)grid * A.P, 0, sizeof(float) * grid * A.P, st));
     }
+    if (fork) {
+      CK(cudaEventRecord(L->ev_ajoin, L->side));
+      CK(cudaStreamWaitEvent(st, L->ev_ajoin, 0));
+    }
     {
-      StageScope sc_(ctx, US_STAGE_PATH_ADJ, 4, st);
-      uint8_t* pclass;
-      CKS(ws(ctx, W_PCLASS, (size_t)n, st, &pclass));
-      launch_active_paths(rec, n, q.kmax, work, pclass, active, grid_of(ctx, 4), st);
+      StageScope sc_(ctx, US_STAGE_PATH_ADJ, 1, st);
       A.gpart = gpart;
       launch_path_adjoint(A, grid, st);
     }
