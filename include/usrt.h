@@ -319,19 +319,23 @@ int us_adjoint(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_des
 
 /* DAS part alone: sum_p dL/dI_rf(p) dI_rf(p)/d(c_bf, pitch, th_t) with the RF held fixed.  The slope
  * of each tap is that of the linear-interpolation interval holding its delay.  rf_dev: DEVICE
- * float[n_tx][n_elem][n_samples]; dL_dirf_dev: DEVICE float[n_lines][n_depth]. */
+ * float[n_tx][n_elem][n_samples]; dL_dirf_dev: DEVICE float[n_lines][n_depth].  Errors:
+ * US_ERR_ARG (a null buffer, an invalid descriptor), US_ERR_OOM (workspace), US_ERR_CUDA. */
 int us_das_acq_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
                    const float* dL_dirf_dev, float* dL_dacq_dev, void* stream);
 
 /* Transport part alone: us_transport_vjp (same arguments, modes and record-mode requirements)
  * that also carries each path's time and origin adjoints at emission, and each secondary ray's
- * sensitivity to its target element's position, into dL_dacq_dev. */
+ * sensitivity to its target element's position, into dL_dacq_dev.  Errors: those of
+ * us_transport_vjp (US_ERR_STATE in record mode without the matching forward pass), and
+ * US_ERR_ARG for a null dL_dacq_dev. */
 int us_transport_vjp_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
                          int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dacq_dev,
                          void* stream);
 
 /* Full adjoint with the acquisition gradient: us_adjoint (same arguments and requirements) plus
- * dL_dacq_dev = DAS part + transport part. */
+ * dL_dacq_dev = DAS part + transport part.  Errors: those of us_adjoint, and US_ERR_ARG for a
+ * null dL_dacq_dev. */
 int us_adjoint_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
                    uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
                    float* dL_dacq_dev, float* dL_drf_dev, void* stream);
@@ -349,20 +353,24 @@ int us_adjoint_acq(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq
  * owned, overwritten; accumulated with float atomics, so the last bits vary between runs. */
 
 /* Transport part: us_transport_vjp (same arguments, modes and record-mode requirements) plus
- * dL/d(triangle vertices). */
+ * dL/d(triangle vertices).  Errors: those of us_transport_vjp, and US_ERR_ARG for a null
+ * dL_dtris_dev. */
 int us_transport_vjp_shape(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, uint64_t seed,
                            int mode, const float* dL_drf_dev, float* dL_dtheta_dev, float* dL_dtris_dev,
                            void* stream);
 
-/* Full adjoint: us_adjoint (same arguments and requirements) plus dL/d(triangle vertices). */
+/* Full adjoint: us_adjoint (same arguments and requirements) plus dL/d(triangle vertices).
+ * Errors: those of us_adjoint, and US_ERR_ARG for a null dL_dtris_dev. */
 int us_adjoint_shape(us_ctx* ctx, uint64_t scene, const float* theta, const us_acq_desc* acq, const us_img_desc* img,
                      uint64_t seed, int mode, const float* rf_dev, const float* dL_dB_dev, float* dL_dtheta_dev,
                      float* dL_dtris_dev, float* dL_drf_dev, void* stream);
 
 /* Chain rule to shape parameters q_j (a radius, a thickness, ...):
  * dL_dq_dev[j] = sum_i dL_dtris_dev[i] * dtris_dq_dev[j * 9 n_tris + i] for j < n_param, with
- * dtris_dq_dev the parameters' vertex tangents (DEVICE float[n_param][n_tris][9]).
- * 1 <= n_param <= 65535; fixed summation order. */
+ * dtris_dq_dev the parameters' vertex tangents (DEVICE float[n_param][n_tris][9]) and dL_dq_dev
+ * DEVICE float[n_param], caller-owned, overwritten.  1 <= n_param <= 65535; fixed summation
+ * order (the same result bit for bit on every call).  Errors: US_ERR_ARG (a null buffer,
+ * n_tris < 0, n_param outside its range), US_ERR_CUDA. */
 int us_shape_param_grad(us_ctx* ctx, int64_t n_tris, const float* dL_dtris_dev, int n_param, const float* dtris_dq_dev,
                         float* dL_dq_dev, void* stream);
 
