@@ -97,25 +97,31 @@ def ellipsoid_mesh(center, semi, rot, n_lat=65, n_lon=130):
 def tube_mesh(radius, zc, half_len, n_phi, n_y, outward=True):
     """Open cylinder of the given radius around the axis x = 0, z = zc (along y): n_phi x n_y
     quads, two triangles each, normals pointing away from the axis (outward) or toward it.
-    Returns (tris (2 n_phi n_y, 9), radial unit vector of every vertex (same shape))."""
+    Returns (tris (2 n_phi n_y, 9), radial unit vector of every vertex (same shape)); quad
+    (i, j) (azimuth i, along-axis j) gives triangles 2 (i n_y + j) and 2 (i n_y + j) + 1."""
     phi = np.linspace(0.0, 2.0 * np.pi, n_phi + 1)[:-1]
     ys = np.linspace(-half_len, half_len, n_y + 1)
+    a0, a1 = np.repeat(phi, n_y), np.repeat(np.roll(phi, -1), n_y)
+    y0, y1 = np.tile(ys[:-1], n_phi), np.tile(ys[1:], n_phi)
+
+    def point(a, y):
+        return np.stack([radius * np.cos(a), y, zc + radius * np.sin(a)], axis=1)
+
+    def radial(a):
+        return np.stack([np.cos(a), np.zeros_like(a), np.sin(a)], axis=1)
+
+    corners = [point(a0, y0), point(a1, y0), point(a1, y1), point(a0, y1)]
+    rads = [radial(a0), radial(a1), radial(a1), radial(a0)]
     tris, rad = [], []
-    for i in range(n_phi):
-        a0, a1 = phi[i], phi[(i + 1) % n_phi]
-        for j in range(n_y):
-            q = [(a0, ys[j]), (a1, ys[j]), (a1, ys[j + 1]), (a0, ys[j + 1])]
-            pts = [np.array([radius * math.cos(a), y, zc + radius * math.sin(a)]) for a, y in q]
-            rds = [np.array([math.cos(a), 0.0, math.sin(a)]) for a, _ in q]
-            for k in ((0, 1, 2), (0, 2, 3)):
-                v = [pts[m] for m in k]
-                n = np.cross(v[1] - v[0], v[2] - v[0])
-                centre_dir = sum(rds[m] for m in k)
-                if (np.dot(n, centre_dir) > 0) != outward:
-                    k = (k[0], k[2], k[1])
-                tris.append(np.concatenate([pts[m] for m in k]))
-                rad.append(np.concatenate([rds[m] for m in k]))
-    return np.asarray(tris), np.asarray(rad)
+    for k in ((0, 1, 2), (0, 2, 3)):
+        v0, v1, v2 = (corners[m] for m in k)
+        n = np.cross(v1 - v0, v2 - v0)
+        # orientation: swap the last two corners where the normal points the wrong way
+        flip = ((np.sum(n * (rads[k[0]] + rads[k[1]] + rads[k[2]]), axis=1) > 0) != outward)[:, None]
+        tris.append(np.concatenate([v0, np.where(flip, v2, v1), np.where(flip, v1, v2)], axis=1))
+        rad.append(np.concatenate([rads[k[0]], np.where(flip, rads[k[2]], rads[k[1]]),
+                                   np.where(flip, rads[k[1]], rads[k[2]])], axis=1))
+    return np.stack(tris, axis=1).reshape(-1, 9), np.stack(rad, axis=1).reshape(-1, 9)
 
 
 def random_rotation(rng):
