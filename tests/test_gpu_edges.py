@@ -127,3 +127,28 @@ def test_empty_batch_is_a_no_op(ctx):
     from paper_2604_15017_gb300 import usrt
 
     assert usrt.Batch(ctx, []).run() == []
+
+
+def test_second_stream_gives_the_sequential_results(ctx):
+    """Secondary rays and their job sort on the lane's second stream (the default) against the
+    same call with everything on one stream: RF and gradient equal up to FP32 summation order
+    (the arrival and job orders come from atomics either way)."""
+    from paper_2604_15017_gb300 import usrt
+
+    w = P.slab_scatterers(n_rays=600)
+    sid = ctx.upload_workload(w)
+    out = {}
+    for opt in (0, 100):
+        ctx.set_option(usrt.OPT_NEE_STREAM, opt)
+        rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+        gb = torch.ones_like(b) * (b > -60)
+        g, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, gb)
+        torch.cuda.synchronize()
+        out[opt] = (rf.clone(), g.clone(), ctx.stats())
+    ctx.set_option(usrt.OPT_NEE_STREAM, 100)
+    (rf0, g0, s0), (rf1, g1, s1) = out[0], out[100]
+    assert s0["segments"] == s1["segments"] and s0["nee_queries"] == s1["nee_queries"]
+    assert s0["arrivals"] == s1["arrivals"]
+    assert float((rf0 - rf1).norm()) <= 1e-5 * float(rf0.norm())
+    assert torch.allclose(g0, g1, rtol=1e-4, atol=1e-5 * float(g0.abs().max()))
+    ctx.release_scene(sid)
