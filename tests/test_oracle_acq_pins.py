@@ -123,3 +123,24 @@ def test_dynamic_aperture_weights():
     lhs = np.sum(O.das(acq, img2, x) * y)
     rhs = np.sum(x * O.das_adjoint(acq, img2, y))
     assert abs(lhs - rhs) <= 1e-10 * np.abs(x).sum()
+
+
+def test_transport_acquisition_derivatives_on_a_rough_scene():
+    """The acquisition slots follow the roughness slots (theta of 4M + 2), and rough events move
+    with the pitch's emission origins like smooth ones."""
+    w = P.with_roughness(P.slab_scatterers(n_rays=200), [0.0, 0.25])
+    w["acq"] = dict(w["acq"], angles=[-0.1, 0.12])
+    ref = O.forward(w)
+    grf = np.random.default_rng(9).normal(size=ref["rf"].shape)
+    full = ref["run"].gradient_acq(grf, full=True)
+    assert full.shape == (4 * w["M"] + 2 + 2 + 2,)
+    g = full[4 * w["M"] + 2:]
+    rec0 = ref["run"].records()
+    for which in range(4):
+        h = 1e-8
+        rp = O.forward(dict(w, acq=perturbed(w["acq"], which, h)))
+        rm = O.forward(dict(w, acq=perturbed(w["acq"], which, -h)))
+        for k in rec0:
+            assert np.array_equal(rp["run"].records()[k], rec0[k])
+        fd = (np.sum(grf * rp["rf"]) - np.sum(grf * rm["rf"])) / (2 * step(w["acq"], which, h))
+        assert abs(fd - g[which]) <= 1e-4 * abs(g[which]) + 1e-6 * np.abs(g).max(), (which, fd, g[which])
