@@ -92,7 +92,12 @@ typedef struct {
   float split_q;
   uint32_t stream_id;    /* third Philox counter word (independent scenes / requests) */
   int32_t tx_elem;       /* -1: every element emits; else only this element (single-element
-                            transmit) */
+                            transmit), or the sub-aperture below */
+  int32_t n_tx_elem;     /* with tx_elem >= 0: elements tx_elem .. tx_elem + n_tx_elem - 1 emit
+                            (0 or 1: tx_elem alone); tx_elem + n_tx_elem <= n_elem.  A ray keeps
+                            its index (element x n_rays + ray) whatever the sub-aperture, so
+                            disjoint sub-apertures with one seed partition the full aperture's
+                            realisation exactly (micro-batches over elements) */
 } us_acq_desc;
 
 /* Image grid, dynamic range and loss weights. */

@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 
 # flat descriptor layouts (mirrors the enums of usrt_oracle.cpp)
 ACQ_KEYS = ["n_elem", "pitch", "h_el", "n_tx", "fs", "n_samples", "k_max", "n_rays", "bw", "alpha_m",
-            "alpha_c", "c_bf", "split_mode", "split_q", "stream_id", "tx_elem"]
+            "alpha_c", "c_bf", "split_mode", "split_q", "stream_id", "tx_elem", "n_tx_elem"]
 IMG_KEYS = ["n_lines", "n_depth", "x0", "x1", "z0", "z1", "dr_db", "lambda1", "lambda2", "f_number"]
 IMG_DEFAULTS = {"dr_db": 60.0, "lambda1": 0.0, "lambda2": 1.0, "f_number": 0.0}
 
@@ -120,6 +120,7 @@ def default_threads():
 def acq_array(acq):
     vals = dict(acq)
     vals["n_tx"] = len(acq["angles"])
+    vals.setdefault("n_tx_elem", 0)
     arr = np.array([float(vals[k]) for k in ACQ_KEYS], dtype=np.float64)
     ang = np.asarray(acq["angles"], dtype=np.float64)
     return arr, ang
@@ -197,7 +198,7 @@ class Run:
         self.h = lib().ora_trace(scene.h, thp, self.M, a.ctypes.data_as(D), ang.ctypes.data_as(D),
                                  C.c_uint64(self.seed), n, path_lo, path_hi)
         ntx = len(acq["angles"])
-        per_tx = (acq["n_elem"] if acq.get("tx_elem", -1) < 0 else 1) * acq["n_rays"]
+        per_tx = (acq["n_elem"] if acq.get("tx_elem", -1) < 0 else max(1, acq.get("n_tx_elem", 0))) * acq["n_rays"]
         self.path_lo = path_lo
         self.n_paths = (ntx * per_tx if path_hi < 0 else path_hi) - path_lo
 

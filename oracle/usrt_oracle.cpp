@@ -168,16 +168,17 @@ D3 subd(const D3& a, const D3& b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); 
 // ------------------------------------------------------------------------------------------
 enum {
   A_NE = 0, A_PITCH, A_HEL, A_NTX, A_FS, A_NS, A_KMAX, A_NR, A_BW, A_ALPHA_M, A_ALPHA_C, A_CBF,
-  A_SPLIT_MODE, A_SPLIT_Q, A_STREAM, A_TX_ELEM, A_COUNT
+  A_SPLIT_MODE, A_SPLIT_Q, A_STREAM, A_TX_ELEM, A_N_TX_ELEM, A_COUNT
 };
 enum { I_NL = 0, I_ND, I_X0, I_X1, I_Z0, I_Z1, I_DR, I_L1, I_L2, I_FNUM, I_COUNT };
 
 struct Acq {
-  int ne, ntx, ns, kmax, nr, split_mode, tx_elem;
+  int ne, ntx, ns, kmax, nr, split_mode, tx_elem, n_tx_elem;
   double pitch, hel, fs, bw, alpha_m, alpha_c, cbf, split_q;
   uint32_t stream;
   std::vector<double> angles;
-  int n_emit() const { return tx_elem < 0 ? ne : 1; }
+  // emitting elements: all, or tx_elem .. tx_elem + max(1, n_tx_elem) - 1 (a sub-aperture)
+  int n_emit() const { return tx_elem < 0 ? ne : std::max(1, n_tx_elem); }
   long long rays_per_tx() const { return (long long)n_emit() * nr; }
   long long n_paths() const { return rays_per_tx() * ntx; }
   double elem_x(int e) const { return (e - 0.5 * (ne - 1)) * pitch; }
@@ -202,6 +203,7 @@ Acq make_acq(const double* a, const double* angles) {
   q.split_q = a[A_SPLIT_Q];
   q.stream = (uint32_t)a[A_STREAM];
   q.tx_elem = (int)a[A_TX_ELEM];
+  q.n_tx_elem = (int)a[A_N_TX_ELEM];
   q.angles.assign(angles, angles + q.ntx);
   return q;
 }

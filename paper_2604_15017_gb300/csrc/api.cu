@@ -287,6 +287,8 @@ int make_acq(us_ctx* ctx, const us_acq_desc* d, uint64_t seed, Acq& q) {
     return fail(ctx, US_ERR_ARG, "n_samples %d: multiple of 4 in [4, %d]", d->n_samples, MAX_SPLAT_NS);
   if (d->n_rays < 1) return fail(ctx, US_ERR_ARG, "n_rays must be >= 1");
   if (d->tx_elem >= d->n_elem) return fail(ctx, US_ERR_ARG, "tx_elem %d >= n_elem", d->tx_elem);
+  if (d->tx_elem >= 0 && (d->n_tx_elem < 0 || d->tx_elem + std::max(1, d->n_tx_elem) > d->n_elem))
+    return fail(ctx, US_ERR_ARG, "sub-aperture %d + %d outside the array", d->tx_elem, d->n_tx_elem);
   if (!(d->fs > 0) || !(d->pitch > 0) || !(d->c_bf > 0) || !(d->bw > 0))
     return fail(ctx, US_ERR_ARG, "fs, pitch, c_bf and bw must be > 0");
   if (d->split_mode != 0 && !(d->split_q > 0 && d->split_q < 1))
@@ -297,7 +299,7 @@ int make_acq(us_ctx* ctx, const us_acq_desc* d, uint64_t seed, Acq& q) {
   q.kmax = d->k_max;
   q.nr = d->n_rays;
   q.tx_elem = d->tx_elem < 0 ? -1 : d->tx_elem;
-  q.n_emit = q.tx_elem < 0 ? q.ne : 1;
+  q.n_emit = q.tx_elem < 0 ? q.ne : std::max(1, d->n_tx_elem);
   q.split_mode = d->split_mode;
   q.pitch = d->pitch;
   q.hel = d->h_el;

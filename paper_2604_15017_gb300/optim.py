@@ -11,8 +11,9 @@ Carlo seeds stay fixed per micro-batch (common random numbers), so successive it
 the same ray realisations.
 
 Micro-batches are acquisitions: subsets of the transmit angles (``split_angles``: an exact
-partition of the compounded acquisition) or independent realisations with a share of the rays
-(``split_rays``: the stochastic split).
+partition of the compounded acquisition), sub-apertures of emitting elements
+(``split_elements``: an exact partition too, the rays keeping their indices), or independent
+realisations with a share of the rays (``split_rays``: the stochastic split).
 
 Shape parameters (a radius, a wall thickness, ...) join the material ones through a
 ``ShapeModel``: a mesh generator q -> (triangles, vertex tangents d tris / d q).  Every
@@ -35,6 +36,21 @@ def split_angles(acq, n_batches):
     for b in range(min(n_batches, len(ang))):
         a = dict(acq)
         a["angles"] = ang[b::n_batches]
+        out.append(a)
+    return out
+
+
+def split_elements(acq, n_batches):
+    """Micro-batches over emitting elements: n_batches contiguous sub-apertures (tx_elem,
+    n_tx_elem).  With one seed they partition the full aperture's realisation exactly (a ray
+    keeps its index), so the micro-batch losses' RF adds up to the full acquisition's."""
+    ne = int(acq["n_elem"])
+    n_batches = max(1, min(n_batches, ne))
+    bounds = [round(b * ne / n_batches) for b in range(n_batches + 1)]
+    out = []
+    for b in range(n_batches):
+        a = dict(acq)
+        a["tx_elem"], a["n_tx_elem"] = bounds[b], bounds[b + 1] - bounds[b]
         out.append(a)
     return out
 

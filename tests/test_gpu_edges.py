@@ -152,3 +152,29 @@ def test_second_stream_gives_the_sequential_results(ctx):
     assert float((rf0 - rf1).norm()) <= 1e-5 * float(rf0.norm())
     assert torch.allclose(g0, g1, rtol=1e-4, atol=1e-5 * float(g0.abs().max()))
     ctx.release_scene(sid)
+
+
+def test_element_sub_apertures_partition_the_frame(ctx):
+    """Micro-batches over emitting elements (sub-apertures with one seed) add up to the full
+    aperture's RF and gradient for one dL/dRF, as the oracle's do; a sub-aperture past the array
+    is refused."""
+    from paper_2604_15017_gb300 import optim, usrt
+
+    w = P.slab_scatterers(n_rays=300)
+    sid = ctx.upload_workload(w)
+    rf_full, _ = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    grf = torch.randn_like(rf_full)
+    g_full = ctx.transport_vjp(sid, w["theta"], w["acq"], w["seed"], grf)
+    rf_sum = torch.zeros_like(rf_full)
+    g_sum = torch.zeros_like(g_full)
+    for a in optim.split_elements(w["acq"], 3):
+        rf, _ = ctx.forward(sid, w["theta"], a, w["img"], seed=w["seed"], keep_record=True)
+        rf_sum += rf
+        g_sum += ctx.transport_vjp(sid, w["theta"], a, w["seed"], grf)
+    torch.cuda.synchronize()
+    assert float((rf_sum - rf_full).norm()) <= 1e-5 * float(rf_full.norm())
+    assert torch.allclose(g_sum, g_full, rtol=1e-4, atol=1e-5 * float(g_full.abs().max()))
+    bad = dict(w["acq"], tx_elem=60, n_tx_elem=8)
+    with pytest.raises(usrt.UsrtError):
+        ctx.forward(sid, w["theta"], bad, w["img"], seed=w["seed"])
+    ctx.release_scene(sid)
