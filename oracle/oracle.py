@@ -71,6 +71,7 @@ def lib():
             l.ora_scene_free.argtypes = [C.c_void_p]
             l.ora_closest.argtypes = [C.c_void_p, D, D, C.c_int, C.c_int, D]
             l.ora_interface.argtypes = [D, D, C.c_double, C.c_double, C.c_double, C.c_double, D]
+            l.ora_emit.argtypes = [D, D, C.c_uint64, C.c_int, C.c_longlong, C.c_longlong, D]
             l.ora_trace.restype = C.c_void_p
             l.ora_trace.argtypes = [C.c_void_p, D, C.c_int, D, D, C.c_uint64, C.c_int, C.c_longlong, C.c_longlong]
             l.ora_run_free.argtypes = [C.c_void_p]
@@ -143,6 +144,16 @@ def philox_fill(c0_base, c1, c2, c3, k0, k1, n):
     out = np.zeros(4 * n, dtype=np.uint32)
     lib().ora_philox_fill(c0_base & 0xFFFFFFFF, c1, c2, c3, k0, k1, n, out.ctypes.data_as(U))
     return out.reshape(n, 4)
+
+
+def emit(acq, seed, tx, ray_lo, n):
+    """Emission of rays ray_lo .. ray_lo + n - 1 of transmit tx (Sec. 2.3.1): arrays of origins
+    (n, 3), directions (n, 3), weights (n,) and transmit time stamps (n,)."""
+    a_arr, ang = acq_array(acq)
+    out = np.zeros((n, 8))
+    lib().ora_emit(a_arr.ctypes.data_as(D), ang.ctypes.data_as(D), C.c_uint64(seed), int(tx), int(ray_lo), int(n),
+                   out.ctypes.data_as(D))
+    return out[:, 0:3], out[:, 3:6], out[:, 6], out[:, 7]
 
 
 def interface(w, nin, c1, c2, rho1, rho2):

@@ -741,6 +741,27 @@ S smith_g1(const S& vn, const S& alpha) {
   return 2.0 * c / (c + sqrt(alpha * alpha + (1.0 - alpha * alpha) * c * c));
 }
 
+// Emission [Sec. 2.3.1, Eq. directivity, Eq. pressure_mc] of ray `ray` (= element x N_r +
+// index) of transmit tx from its Philox block (ray, tx, stream, 0): the origin uniform over the
+// element face (u0 across the pitch, u1 along the element height); the direction drawn with the
+// density p(w) = cos(theta) / pi over the hemisphere around the element normal +z (r = sqrt(u2)
+// is sin(theta), u3 the azimuth), so that the directivity f_d = n.w over that density is the
+// constant pi and, with the 1/N average over the element's rays, the weight is pi / N_r; the
+// steering delay as a time stamp at the element centre.
+void emit_ray(const Acq& q, uint32_t k0, uint32_t k1, int tx, long long ray, D3& o0, D3& w0, double& a0,
+              double& tau0, double& xe) {
+  U4 u = philox((uint32_t)ray, (uint32_t)tx, q.stream, 0u, k0, k1);
+  int e = (int)(ray / q.nr);
+  xe = q.elem_x(e);
+  double u0 = u01(u.v[0]), u1 = u01(u.v[1]), u2 = u01(u.v[2]), u3 = u01(u.v[3]);
+  o0 = d3(xe + (u0 - 0.5) * q.pitch, (u1 - 0.5) * q.hel, 0.0);
+  double r = std::sqrt(u2), ph = 2.0 * PI * u3;
+  w0 = d3(r * std::cos(ph), r * std::sin(ph), std::sqrt(1.0 - u2));
+  a0 = PI / q.nr;
+  double st = std::sin(q.angles[tx]);
+  tau0 = (xe * st + 0.5 * q.aperture() * std::fabs(st)) / q.cbf;
+}
+
 struct PathIO {
   // injected emission (tests); when inject is false the emission is sampled from Philox
   bool inject = false;
@@ -768,17 +789,7 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
     a0 = io.a0;
     tau0 = io.tau0;
   } else {
-    U4 u = philox(ray32, (uint32_t)io.tx, q.stream, 0u, k0, k1);
-    int e = (int)(io.ray / q.nr);
-    double xe = q.elem_x(e);
-    double u0 = u01(u.v[0]), u1 = u01(u.v[1]), u2 = u01(u.v[2]), u3 = u01(u.v[3]);
-    o0 = d3(xe + (u0 - 0.5) * q.pitch, (u1 - 0.5) * q.hel, 0.0);
-    double r = std::sqrt(u2), ph = 2.0 * PI * u3;
-    w0 = d3(r * std::cos(ph), r * std::sin(ph), std::sqrt(1.0 - u2));
-    a0 = PI / q.nr;
-    double st = std::sin(q.angles[io.tx]);
-    tau0 = (xe * st + 0.5 * q.aperture() * std::fabs(st)) / q.cbf;
-    xe_emit = xe;
+    emit_ray(q, k0, k1, io.tx, io.ray, o0, w0, a0, tau0, xe_emit);
   }
   V3<S> o = mk3<S>(S(o0.x), S(o0.y), S(o0.z));
   V3<S> w = mk3<S>(S(w0.x), S(w0.y), S(w0.z));
@@ -1327,6 +1338,23 @@ void ora_ggx_normal(const double* n, double alpha, double u2, double u3, double*
   h[0] = r.x;
   h[1] = r.y;
   h[2] = r.z;
+}
+
+// emission of n consecutive rays ray_lo .. ray_lo + n - 1 of transmit tx (tests):
+// out[8 i ..] = {o0 (3), w0 (3), a0, tau0}
+void ora_emit(const double* acq, const double* angles, uint64_t seed, int tx, long long ray_lo, long long n,
+              double* out) {
+  Acq q = make_acq(acq, angles);
+  for (long long i = 0; i < n; ++i) {
+    D3 o0, w0;
+    double a0, tau0, xe;
+    emit_ray(q, (uint32_t)seed, (uint32_t)(seed >> 32), tx, ray_lo + i, o0, w0, a0, tau0, xe);
+    double* r = out + 8 * i;
+    r[0] = o0.x; r[1] = o0.y; r[2] = o0.z;
+    r[3] = w0.x; r[4] = w0.y; r[5] = w0.z;
+    r[6] = a0;
+    r[7] = tau0;
+  }
 }
 
 // interface event (tests): out = {tir, cos_i, cos_t, R, T, wr[3], wt[3]}
