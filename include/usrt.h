@@ -162,9 +162,29 @@ enum {
    * stream of the lane (forked and joined with events, so the call stays one stream-ordered
    * unit), overlapping the next rounds' primary rays, with p % of its resident grid. */
   US_OPT_NEE_STREAM = 2,
+  /* fault injection for tests of the timeout report (default 0): 1 makes the fused envelope
+   * kernel's grid barrier wait for one arrival more than there are blocks, with a 1 ms limit,
+   * so that the wait runs out: the image is written as NaN and us_get_status returns
+   * US_ERR_TIMEOUT.  The fault is injected from the host (a kernel argument); nothing faults. */
+  US_OPT_FAULT_BARRIER = 3,
   US_N_OPTS
 };
 int us_set_option(us_ctx* ctx, int option, int value);
+
+/* Status of the context's kernels outside the transport (TMA-staged DAS waits, the fused
+ * envelope kernel's grid barrier): synchronises the device, then *device_status = US_OK, or
+ * US_ERR_TIMEOUT / US_ERR_OVERFLOW if any of them gave up since the last clear (their bounded
+ * waits return instead of hanging).  clear != 0 resets the word.  The transport's own status
+ * is reported by us_get_stats.  Returns US_ERR_ARG for a null argument, US_ERR_CUDA if the
+ * synchronisation fails. */
+int us_get_status(us_ctx* ctx, int clear, int* device_status);
+
+/* Envelope + log compression kernels, process-wide: enable != 0 (the default) uses the
+ * cooperative fused kernel whenever the image's lines fit co-resident blocks; 0 always takes
+ * the two-kernel path (envelope, then log compression; the path images too large for the fused
+ * kernel take).  Both give the same image.  Applies to every call that forms a B-mode image
+ * (us_forward, us_bmode, us_envlog, us_envlog_noalloc); meant for tests of the second path. */
+void us_set_envlog_fused(int enable);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Tracing: per-stage device time and kernel launch counts                                   */
@@ -223,6 +243,15 @@ int us_get_stats(us_ctx* ctx, us_stats* out);
  * element.  Path p = tx * rays_per_tx + local ray. */
 int us_get_record(us_ctx* ctx, int64_t path_lo, int64_t n, uint32_t* out_dev, void* stream);
 
+/* Copy arrivals [lo, lo + n) of the most recent forward pass on this context (us_get_stats:
+ * `arrivals` of them, in the order the transport appended them, which varies between runs) to
+ * out_dev (DEVICE uint32[n][4], caller-owned).  Arrival word 0: row = tx * n_elem + element;
+ * word 1: time as fixed point, t = (word1 * 2^-18 - 64) / fs; word 2: the amplitude's float
+ * bits; word 3: the path p = tx * rays_per_tx + local ray whose transducer hit or secondary ray
+ * (Sec. 2.3.3) made it.  Errors: US_ERR_ARG (range outside the list, null out_dev with n > 0),
+ * US_ERR_STATE (no forward pass yet).  Synchronises the stream of that pass. */
+int us_get_arrivals(us_ctx* ctx, int64_t lo, int64_t n, uint32_t* out_dev, void* stream);
+
 /* S6 alone: splat an explicit arrival list into rf_dev (zeroed first).  Arrival i lands on
  * row tx_dev[i] * n_elem + e_dev[i] at time tau_dev[i] [s] with amplitude a_dev[i] (Eq.
  * axial_sig, pulse centre frequency f0). */
@@ -248,7 +277,12 @@ int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* 
  *     US_ENVLOG_NOALLOC_MAX_PIXELS = n_lines * n_depth pixels (1 MiB of floats), that every GPU
  *     which loads the library holds until the process exits.
  *   - Runs on the current CUDA device.  The first call on each device resolves that array's
- *     address and the launch shape; make that first call before any stream capture.
+ *     address and the launch shape, and so does the first call after the device's context
+ *     changed (a device reset, a new primary context); make such a call before any stream
+ *     capture.
+ *   - Reports only its own launches' status: an error pending from unrelated earlier work is
+ *     neither returned nor cleared.  The fused kernel's bounded barrier, should it ever expire,
+ *     writes NaN (this entry point keeps no status word).
  *   - All calls share the one array and each call overwrites it (the maximum is cleared at the
  *     start of every call), so calls whose work overlaps on the GPU (other streams, other host
  *     threads) race and must be serialised by the caller.

@@ -95,6 +95,7 @@ def lib():
             l.ora_envlog_vjp.argtypes = [D, D, D, D]
             l.ora_replay_rf.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D]
             l.ora_gradient.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
+            l.ora_gradient_cond.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D, D]
             l.ora_gradient_acq.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
             l.ora_gradient_shape.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, C.c_int, D, D]
             l.ora_trace_injected.restype = C.c_int
@@ -268,6 +269,18 @@ class Run:
         lib().ora_gradient(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
                            out.ctypes.data_as(D))
         return out
+
+    def gradient_cond(self, grf, theta=None, nthreads=None):
+        """(gradient, condition): the gradient of gradient() and, per component, the sum over
+        arrivals of the absolute value of each arrival's contribution to it."""
+        th = self.theta if theta is None else np.asarray(theta, np.float64)
+        th, thp = _d(th)
+        g, gp = _d(grf)
+        out = np.zeros(self.n_theta)
+        cond = np.zeros(self.n_theta)
+        lib().ora_gradient_cond(self.scene.h, self.h, thp, C.c_uint64(self.seed), nthreads or default_threads(), gp,
+                                out.ctypes.data_as(D), cond.ctypes.data_as(D))
+        return out, cond
 
     def gradient_acq(self, grf, theta=None, nthreads=None, full=False):
         """d/d(c_bf, pitch, steering angles) of sum(grf * RF) on this frozen realisation (Sec.

@@ -983,6 +983,8 @@ struct Run {
   Counters cnt;
 };
 
+int host_threads() { return std::max(1, (int)std::thread::hardware_concurrency()); }
+
 template <class F>
 void parallel_blocks(long long n, int nthreads, F f) {
   if (nthreads <= 1 || n < 2) {
@@ -1076,8 +1078,11 @@ double das_delay_samples(const Acq& q, double x, double z, int e, double th) {
 
 // Eq. das: I_rf(x,z) = sum_tx sum_e w_e P(e, tau_e(x,z)), P read by linear interpolation,
 // samples outside [0, N_s - 1] count as zero; transmits compounded coherently.
+// Lines are independent outputs: they are computed on the host's threads, each line's sums in
+// the same order as one thread would take them.
 void das(const Acq& q, const Img& im, const double* rf, double* irf) {
-  for (int l = 0; l < im.nl; ++l)
+  parallel_blocks(im.nl, host_threads(), [&](int, long long l_lo, long long l_hi) {
+  for (int l = (int)l_lo; l < (int)l_hi; ++l)
     for (int d = 0; d < im.nd; ++d) {
       double x = line_x(im, l), z = depth_z(im, d), acc = 0;
       for (int tx = 0; tx < q.ntx; ++tx)
@@ -1093,6 +1098,7 @@ void das(const Acq& q, const Img& im, const double* rf, double* irf) {
         }
       irf[(size_t)l * im.nd + d] = acc;
     }
+  });
 }
 
 // Derivative of the beamformed image in the acquisition parameters, contracted with an image
@@ -1134,23 +1140,27 @@ void das_acq_vjp(const Acq& q, const Img& im, const double* rf, const double* gi
     }
 }
 
-// Eq. das_adjoint: scatter the image gradient back to the two interpolation samples.
+// Eq. das_adjoint: scatter the image gradient back to the two interpolation samples.  Channel
+// rows (transmit, element) are independent outputs, computed on the host's threads; every row
+// takes its pixels in line-then-depth order.
 void das_adjoint(const Acq& q, const Img& im, const double* gi, double* grf) {
-  for (int l = 0; l < im.nl; ++l)
-    for (int d = 0; d < im.nd; ++d) {
-      double x = line_x(im, l), z = depth_z(im, d), g = gi[(size_t)l * im.nd + d];
-      for (int tx = 0; tx < q.ntx; ++tx)
-        for (int e = 0; e < q.ne; ++e) {
+  parallel_blocks((long long)q.ntx * q.ne, host_threads(), [&](int, long long r_lo, long long r_hi) {
+    for (long long r = r_lo; r < r_hi; ++r) {
+      const int tx = (int)(r / q.ne), e = (int)(r % q.ne);
+      double* row = grf + (size_t)r * q.ns;
+      for (int l = 0; l < im.nl; ++l)
+        for (int d = 0; d < im.nd; ++d) {
+          double x = line_x(im, l), z = depth_z(im, d), g = gi[(size_t)l * im.nd + d];
           double u = das_delay_samples(q, x, z, e, q.angles[tx]);
           double fl = std::floor(u);
           long long i = (long long)fl;
           double f = u - fl;
-          double* row = grf + ((size_t)tx * q.ne + e) * q.ns;
           double w = apod(q, im, x, z, e);
           if (i >= 0 && i < q.ns) row[i] += w * (1.0 - f) * g;
           if (i + 1 >= 0 && i + 1 < q.ns) row[i + 1] += w * f * g;
         }
     }
+  });
 }
 
 // discrete Fourier transform, sign -1 forward / +1 inverse (unnormalised).  Radix-2
@@ -1522,8 +1532,11 @@ void ora_replay_rf(void* scene, void* rp, const double* theta, uint64_t seed, in
 // Returns -1 when the duals cannot hold that many parameters.
 // n_shape > 0: also in n_shape shape parameters whose vertex tangents are vtan
 // [n_shape][n_tris][9], appended after the others.
+// gabs (may be null): per component the sum over arrivals of |contribution|, the scale below
+// which a sum of those terms in finite precision cannot be resolved (its condition)
 static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
-                         double* gtheta, bool with_acq, int n_shape = 0, const double* vtan = nullptr) {
+                         double* gtheta, bool with_acq, int n_shape = 0, const double* vtan = nullptr,
+                         double* gabs = nullptr) {
   Run* r = (Run*)rp;
   const Scene& sc = *(Scene*)scene;
   const Acq& q = r->q;
@@ -1542,7 +1555,7 @@ static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t se
   if (np > NP) return -1;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   int nb = std::max(1, nthreads);
-  std::vector<std::vector<double>> acc(nb, std::vector<double>(np, 0.0));
+  std::vector<std::vector<double>> acc(nb, std::vector<double>(np, 0.0)), aabs(nb, std::vector<double>(np, 0.0));
   parallel_blocks(r->n_paths, nthreads, [&](int b, long long lo, long long hi) {
     std::vector<Arrival<Dual>> arr;
     Counters c;
@@ -1561,16 +1574,29 @@ static int gradient_impl(void* scene, void* rp, const double* theta, uint64_t se
           s = s + row[n] * pulse<Dual>(Dual(n / q.fs) - A.tau, P.f0, sig);
         }
         Dual contrib = A.a * s;
-        for (int k = 0; k < np; ++k) acc[b][k] += contrib.d[k];
+        for (int k = 0; k < np; ++k) {
+          acc[b][k] += contrib.d[k];
+          aabs[b][k] += std::fabs(contrib.d[k]);
+        }
       }
     }
   });
   for (int k = 0; k < np; ++k) {
-    double s = 0;
-    for (int b = 0; b < nb; ++b) s += acc[b][k];
+    double s = 0, sa = 0;
+    for (int b = 0; b < nb; ++b) {
+      s += acc[b][k];
+      sa += aabs[b][k];
+    }
     gtheta[k] = s;
+    if (gabs) gabs[k] = sa;
   }
   return 0;
+}
+
+// the gradient and, per component, the sum over arrivals of |contribution|
+void ora_gradient_cond(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,
+                       double* gtheta, double* gabs) {
+  gradient_impl(scene, rp, theta, seed, nthreads, grf, gtheta, false, 0, nullptr, gabs);
 }
 
 void ora_gradient(void* scene, void* rp, const double* theta, uint64_t seed, int nthreads, const double* grf,

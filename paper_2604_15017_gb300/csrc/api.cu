@@ -587,7 +587,8 @@ int do_bmode(us_ctx* ctx, const Acq& q, const Img& im, const float* rf, float* b
   irf_made(ctx, q, im, rf, irf);
   {
     StageScope sc_(ctx, US_STAGE_ENVLOG, 0, st);
-    sc_.nk = launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st);
+    sc_.nk = launch_envlog(im, irf, env, key, bmode, grid_of(ctx, 8), st, ctx->d_status,
+                           ctx->opts[US_OPT_FAULT_BARRIER]);
   }
   CK(cudaGetLastError());
   return US_OK;
@@ -713,7 +714,20 @@ int us_adam_step(us_ctx* ctx, int n, float* theta_u_dev, const float* dL_dtheta_
 
 int us_set_option(us_ctx* ctx, int option, int value) {
   if (!ctx || option < 0 || option >= US_N_OPTS) return fail(ctx, US_ERR_ARG, "unknown option %d", option);
+  if (option == US_OPT_FAULT_BARRIER && value != 0 && value != 1)
+    return fail(ctx, US_ERR_ARG, "US_OPT_FAULT_BARRIER takes 0 or 1");
   ctx->opts[option] = value;
+  return US_OK;
+}
+
+int us_get_status(us_ctx* ctx, int clear, int* device_status) {
+  if (!ctx || !device_status) return fail(ctx, US_ERR_ARG, "null argument");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaDeviceSynchronize());
+  int ds = 0;
+  CK(cudaMemcpy(&ds, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (clear) CK(cudaMemset(ctx->d_status, 0, sizeof(int)));
+  *device_status = (ds & ST_OVERFLOW) ? US_ERR_OVERFLOW : ((ds & ST_TIMEOUT) ? US_ERR_TIMEOUT : US_OK);
   return US_OK;
 }
 
@@ -934,6 +948,20 @@ int us_get_record(us_ctx* ctx, int64_t path_lo, int64_t n, uint32_t* out_dev, vo
   return US_OK;
 }
 
+int us_get_arrivals(us_ctx* ctx, int64_t lo, int64_t n, uint32_t* out_dev, void* stream) {
+  if (!ctx || (n && !out_dev) || n < 0 || lo < 0) return fail(ctx, US_ERR_ARG, "invalid arguments");
+  if (!ctx->L->stats_valid) return fail(ctx, US_ERR_STATE, "no forward pass yet");
+  CK(cudaEventSynchronize(ctx->L->ev_stats));
+  // the list of the lane's last forward pass: only us_forward writes (or grows) W_ARR
+  const Buf& b = ctx->L->ws[W_ARR];
+  const long long have = std::min<long long>(ctx->L->h_cnt->n_arr, (long long)(b.cap / sizeof(Arrival)));
+  if (lo + n > have) return fail(ctx, US_ERR_ARG, "arrival range outside the list");
+  if (!n) return US_OK;
+  CK(cudaMemcpyAsync(out_dev, (const Arrival*)b.p + lo, sizeof(Arrival) * (size_t)n, cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  return US_OK;
+}
+
 int us_splat(us_ctx* ctx, const us_acq_desc* acq, float f0, int64_t n, const int32_t* tx_dev, const int32_t* e_dev,
              const float* tau_dev, const float* a_dev, float* rf_dev, void* stream) {
   if (!ctx) return US_ERR_ARG;
@@ -981,7 +1009,8 @@ int us_envlog(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, float* 
   CKS(ws(ctx, W_ENV, (size_t)im.nl * im.nd, st, &env));
   CKS(ws(ctx, W_KEY, 2, st, &key));
   StageScope sc_(ctx, US_STAGE_ENVLOG, 0, st);
-  sc_.nk = launch_envlog(im, irf_dev, env, key, bmode_dev, grid_of(ctx, 8), st);
+  sc_.nk = launch_envlog(im, irf_dev, env, key, bmode_dev, grid_of(ctx, 8), st, ctx->d_status,
+                         ctx->opts[US_OPT_FAULT_BARRIER]);
   CK(cudaGetLastError());
   return US_OK;
 }

@@ -103,9 +103,12 @@ __device__ __forceinline__ void leaf_closest(const SceneDev& S, int first, int c
 }
 
 // closest triangle hit: BVH2 traversal, nearer child first; the far child is pushed with its
-// entry distance and skipped once a closer hit has been found
+// entry distance and skipped once a closer hit has been found.  The stack holds at most one
+// entry per tree level below the root, and us_scene_upload refuses trees deeper than 60, so it
+// cannot fill up; should it ever, the far child is dropped and `overflow` is set so that the
+// caller reports it (the hit may then be missed).
 __device__ __forceinline__ void tri_closest(const SceneDev& S, float3 o, float3 w, uint32_t prev, float& tbest,
-                                            uint32_t& cbest) {
+                                            uint32_t& cbest, bool& overflow) {
   const RayInv r = ray_inv(o, w);
   int stack[BVH_STACK];
   float stt[BVH_STACK];
@@ -136,6 +139,8 @@ __device__ __forceinline__ void tri_closest(const SceneDev& S, float3 o, float3 
           stack[sp] = first0 ? n3.y : n3.x;
           stt[sp] = first0 ? t1 : t0;
           ++sp;
+        } else {
+          overflow = true;
         }
         node = first0 ? n3.x : n3.y;
         node_t = first0 ? t0 : t1;
@@ -159,11 +164,11 @@ __device__ __forceinline__ void tri_closest(const SceneDev& S, float3 o, float3 
 // it (grid march) below the distance found here; the order (t, class, id) decides ties, so the
 // result is the closest hit over the union whichever structure reports a candidate first.
 __device__ __forceinline__ void surface_hit(const SceneDev& S, const Acq& q, float3 o, float3 w, uint32_t prev,
-                                            float& tbest, uint32_t& cbest) {
+                                            float& tbest, uint32_t& cbest, bool& overflow) {
   tbest = 3.0e38f;
   cbest = 0xFFFFFFFFu;
   xdcr_test(q, o, w, tbest, cbest);
-  tri_closest(S, o, w, prev, tbest, cbest);
+  tri_closest(S, o, w, prev, tbest, cbest, overflow);
 }
 
 // ---- 4-wide BVH (the secondary rays' all-crossings queries) ----------------------------

@@ -1,6 +1,8 @@
 // Image formation and its adjoint: delay-and-sum (Eq. das) and its transpose (Eq.
 // das_adjoint), the Hilbert envelope along depth, log compression with the dynamic-range clip
 // (Sec. 2.3.4), the l1/l2 loss (Eq. weighted_l1_l2_loss) and the envelope/log VJP.
+#include <atomic>
+
 #include "image.cuh"
 
 namespace usrt {
@@ -432,12 +434,17 @@ __device__ __forceinline__ int key_argmax(unsigned long long k) { return (int)(0
 // their lines in shared memory, meet at one grid-wide barrier once every block has folded its
 // maximum into the packed key, then write B = max(20 log10(E / E_max), -DR).  The barrier's
 // wait is bounded in time (cooperative launches are co-resident, so it never expires in
-// practice); should it expire, the block writes NaN instead of a wrong image.
+// practice); should it expire, the block writes NaN instead of a wrong image and raises
+// ST_TIMEOUT in the status word (when one is given).  `extra` arrivals beyond the grid are
+// awaited as well: 0 in normal use; 1 injects the fault (an arrival no block makes) so that
+// the timeout report can be tested, with the short limit `limit` (clock cycles).
 // keyw[0] = packed maximum, keyw[1] = arrival counter (both zeroed before the launch).
 // ------------------------------------------------------------------------------------------
-constexpr long long BARRIER_CYCLES = 4000000000ll;  // ~2 s at the maximum SM clock
+constexpr long long BARRIER_CYCLES = 4000000000ll;     // ~2 s at the maximum SM clock
+constexpr long long FAULT_BARRIER_CYCLES = 2000000ll;  // ~1 ms: the injected fault's wait
 
-__global__ void k_envlog_fused(Img im, const float* __restrict__ irf, unsigned long long* keyw, float* b) {
+__global__ void k_envlog_fused(Img im, const float* __restrict__ irf, unsigned long long* keyw, float* b, int* status,
+                               int extra, long long limit) {
   extern __shared__ float2 sz[];
   const int N = im.nd;
   const int logN = 31 - __clz(N);
@@ -469,8 +476,8 @@ __global__ void k_envlog_fused(Img im, const float* __restrict__ irf, unsigned l
     __threadfence();
     atomicAdd(&keyw[1], 1ull);
     const long long t0 = clock64();
-    while (atomicAdd(&keyw[1], 0ull) < (unsigned long long)gridDim.x) {
-      if (clock64() - t0 > BARRIER_CYCLES) {
+    while (atomicAdd(&keyw[1], 0ull) < (unsigned long long)gridDim.x + (unsigned long long)extra) {
+      if (clock64() - t0 > limit) {
         ok = false;
         break;
       }
@@ -478,6 +485,7 @@ __global__ void k_envlog_fused(Img im, const float* __restrict__ irf, unsigned l
     }
     __threadfence();
     best = ok ? atomicAdd(&keyw[0], 0ull) : 0xFFFFFFFFFFFFFFFFull;
+    if (!ok && status) atomicOr(status, ST_TIMEOUT);
   }
   __syncthreads();
   const unsigned long long kk = best;
@@ -692,13 +700,22 @@ void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, in
   cudaMemsetAsync(grf, 0, sizeof(float) * (size_t)q.ntx * q.ne * q.ns, st);
   k_das_adj<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, gi, grf);
 }
-static int g_fused_blocks_per_sm = -1;
 constexpr int FUSED_SMEM_MAX = 200 * 1024;
+static std::atomic<int> g_envlog_fused{1};
+
+}  // namespace usrt
+
+extern "C" void us_set_envlog_fused(int enable) { usrt::g_envlog_fused.store(enable ? 1 : 0); }
+
+namespace usrt {
 
 int launch_envlog(const Img& im, const float* irf, float* env, unsigned long long* key, float* bmode, int grid,
-                  cudaStream_t st) {
-  cudaMemsetAsync(key, 0, 2 * sizeof(unsigned long long), st);
-  if (bmode) {
+                  cudaStream_t st, int* status, int fault_barrier, cudaError_t* launch_err) {
+  // every launch reports its own status: no cudaGetLastError, which would also take (and
+  // clear) an error left by unrelated earlier work
+  cudaError_t err = cudaMemsetAsync(key, 0, 2 * sizeof(unsigned long long), st);
+  int launched = 0;
+  if (bmode && g_envlog_fused.load() && err == cudaSuccess) {
     // fused path: every line's envelope stays in the shared memory of a co-resident block
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -711,19 +728,35 @@ int launch_envlog(const Img& im, const float* irf, float* env, unsigned long lon
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_envlog_fused, 256, smem) != cudaSuccess) break;
       const int nb = (im.nl + lpb - 1) / lpb;
       if (per_sm > 0 && nb <= per_sm * sms) {
-        void* args[] = {(void*)&im, (void*)&irf, (void*)&key, (void*)&bmode};
+        int extra = fault_barrier ? 1 : 0;
+        long long limit = fault_barrier ? FAULT_BARRIER_CYCLES : BARRIER_CYCLES;
+        void* args[] = {(void*)&im, (void*)&irf, (void*)&key, (void*)&bmode, (void*)&status, (void*)&extra,
+                        (void*)&limit};
         if (cudaLaunchCooperativeKernel((const void*)k_envlog_fused, dim3(nb), dim3(256), args, smem, st) ==
-            cudaSuccess)
+            cudaSuccess) {
+          if (launch_err) *launch_err = cudaSuccess;
           return 1;
-        cudaGetLastError();
+        }
+        cudaGetLastError();  // the refused cooperative launch: fall back to two kernels
         break;
       }
     }
   }
   const int nb = min(im.nl, grid);
-  k_envelope<<<nb, 256, sizeof(float2) * (size_t)(im.nd + im.nd / 2), st>>>(im, irf, env, key);
-  if (bmode) k_logc<<<grid, 256, 0, st>>>(im, env, key, bmode);
-  return bmode ? 2 : 1;
+  if (err == cudaSuccess) {
+    void* args[] = {(void*)&im, (void*)&irf, (void*)&env, (void*)&key};
+    err = cudaLaunchKernel((const void*)k_envelope, dim3(nb), dim3(256), args,
+                           sizeof(float2) * (size_t)(im.nd + im.nd / 2), st);
+    launched += err == cudaSuccess;
+  }
+  if (bmode && err == cudaSuccess) {
+    const unsigned long long* ckey = key;
+    void* args[] = {(void*)&im, (void*)&env, (void*)&ckey, (void*)&bmode};
+    err = cudaLaunchKernel((const void*)k_logc, dim3(grid), dim3(256), args, 0, st);
+    launched += err == cudaSuccess;
+  }
+  if (launch_err) *launch_err = err;
+  return launched;
 }
 void launch_loss(const Img& im, const float* b, const float* bref, float* gb, float* part, int nparts, float* loss,
                  cudaStream_t st) {

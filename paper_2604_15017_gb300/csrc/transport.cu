@@ -69,15 +69,17 @@ __global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
   if (blockIdx.x == 0 && threadIdx.x == 0)  // secondary jobs of this round follow the previous rounds'
     A.cnt->nee_off[A.k] = A.k ? A.cnt->nee_off[A.k - 1] + A.cnt->nee[A.k - 1] : 0u;
   const uint32_t n = A.cnt->live[A.k];
+  bool overflow = false;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float4 pa = A.qin.pa[i];
     const float4 wt = A.qin.wt[i];
     const uint32_t prev = A.qin.meta[i].y;
     float t;
     uint32_t c;
-    surface_hit(A.S, A.acq, xyz(pa), xyz(wt), prev, t, c);
+    surface_hit(A.S, A.acq, xyz(pa), xyz(wt), prev, t, c, overflow);
     A.hits[i] = make_float2(t, __uint_as_float(c == 0xFFFFFFFFu ? prim_code(CLS_NONE, 0) : c));
   }
+  if (overflow) atomicOr(&A.cnt->status, ST_OVERFLOW);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -489,7 +491,7 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
     if (tq == 0xFFFFFFFFu) continue;
     const float amp = jb.x * med.As * __ldg(&A.S.scat[__float_as_uint(jb.w)]).w * r.gain;
     const uint32_t slot = append_slot(&A.cnt->n_arr);
-    if (slot < A.arr_cap) A.arr[slot] = make_uint4((uint32_t)(tx * q.ne + e2), tq, __float_as_uint(amp), 0xFFFFFFFFu);
+    if (slot < A.arr_cap) A.arr[slot] = make_uint4((uint32_t)(tx * q.ne + e2), tq, __float_as_uint(amp), A.nee.jpath[i]);
   }
 }
 

@@ -108,6 +108,7 @@ class InverseProblem:
         self.m = torch.zeros(n, dtype=torch.float32, device=dev)
         self.v = torch.zeros(n, dtype=torch.float32, device=dev)
         self.grad = torch.zeros(n, dtype=torch.float32, device=dev)
+        self.losses = torch.zeros(len(self.batches), dtype=torch.float32, device=dev)  # per micro-batch
         self.theta = torch.empty(n, dtype=torch.float32, device=dev)
         self.hyper = dict(beta1=beta1, beta2=beta2, eps=eps, clip_norm=clip_norm)
         self.k = 0
@@ -141,16 +142,19 @@ class InverseProblem:
             self.ctx.release_scene(sid)
 
     def step(self):
-        """One iteration of Alg. 1; returns the summed micro-batch loss (host float)."""
+        """One iteration of Alg. 1; returns the summed micro-batch loss (host float).
+
+        The host waits for the device twice per iteration: for the physical parameters (the
+        forward call takes them from host memory) and for the summed loss at the end; the
+        micro-batches' losses stay on the device until then."""
         full = self.physical()
         th = full[:self.n_mat]
         sid, dq, nt, owned = self._scene_at(full[self.n_mat:])
         self.grad.zero_()
-        loss = 0.0
         for b, acq in enumerate(self.batches):
             rf, bm = self.ctx.forward(sid, th, acq, self.img, seed=self.seed + b,
                                       keep_record=self.mode == usrt.MODE_RECORD)
-            lb, gb = self.ctx.loss(self.img, bm, self.targets[b])
+            _, gb = self.ctx.loss(self.img, bm, self.targets[b], out=self.losses[b:b + 1])
             if dq is None:
                 g, _ = self.ctx.adjoint(sid, th, acq, self.img, self.seed + b, rf, gb, mode=self.mode)
                 self.grad += g
@@ -158,12 +162,11 @@ class InverseProblem:
                 g, gtris = self.ctx.adjoint_shape(sid, th, acq, self.img, self.seed + b, rf, gb, nt, mode=self.mode)
                 self.grad[:self.n_mat] += g
                 self.grad[self.n_mat:] += self.ctx.shape_param_grad(gtris, dq)
-            loss += float(lb)
         if owned:
             self.ctx.release_scene(sid)
         self.k += 1
         self.ctx.adam_step(self.theta_u, self.grad, self.lo, self.hi, self.lr, self.m, self.v, self.k, **self.hyper)
-        return loss
+        return float(self.losses.sum())
 
     def run(self, n_iter):
         """n_iter iterations; returns the loss history."""

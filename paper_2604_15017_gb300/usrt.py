@@ -22,14 +22,14 @@ MODE_RECORD, MODE_RECOMPUTE = 0, 1
 
 # the C ABI's entry points (each declared in include/usrt.h)
 EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_scene_release", "us_memory",
-           "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_splat", "us_das", "us_envlog",
+           "us_philox_fill", "us_forward", "us_get_stats", "us_get_record", "us_get_arrivals", "us_splat", "us_das", "us_envlog",
            "us_bmode", "us_loss", "us_envlog_vjp", "us_das_adjoint", "us_bmode_vjp", "us_splat_adjoint",
            "us_transport_vjp", "us_adjoint", "us_envlog_noalloc", "us_profile", "us_profile_read",
            "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch",
            "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step", "us_das_acq_vjp",
            "us_transport_vjp_acq", "us_adjoint_acq", "us_transport_vjp_shape", "us_adjoint_shape",
-           "us_shape_param_grad"]
-OPT_DAS_TMA, OPT_LANES, OPT_NEE_STREAM = 0, 1, 2
+           "us_shape_param_grad", "us_get_status", "us_set_envlog_fused"]
+OPT_DAS_TMA, OPT_LANES, OPT_NEE_STREAM, OPT_FAULT_BARRIER = 0, 1, 2, 3
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq"]
 
@@ -101,6 +101,10 @@ def lib():
                                      C.c_uint64, C.c_int, VP, VP, VP]
             l.us_get_stats.argtypes = [VP, C.POINTER(Stats)]
             l.us_get_record.argtypes = [VP, C.c_int64, C.c_int64, VP, VP]
+            l.us_get_arrivals.argtypes = [VP, C.c_int64, C.c_int64, VP, VP]
+            l.us_get_status.argtypes = [VP, C.c_int, C.POINTER(C.c_int)]
+            l.us_set_envlog_fused.argtypes = [C.c_int]
+            l.us_set_envlog_fused.restype = None
             l.us_splat.argtypes = [VP, C.POINTER(AcqDesc), C.c_float, C.c_int64, VP, VP, VP, VP, VP, VP]
             l.us_das.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP]
             l.us_envlog.argtypes = [VP, C.POINTER(ImgDesc), VP, VP, VP]
@@ -172,6 +176,12 @@ def img_desc(img):
                    float(img.get("lambda2", 1.0)), float(img.get("f_number", 0.0)))
 
 
+def set_envlog_fused(enable):
+    """Process-wide: the cooperative fused envelope kernel (True, default) or always the
+    two-kernel path (False)."""
+    lib().us_set_envlog_fused(int(bool(enable)))
+
+
 class Context:
     """One library context on one CUDA device (scenes, records and workspaces stay resident)."""
 
@@ -218,6 +228,13 @@ class Context:
 
     def set_option(self, option, value):
         self._check(lib().us_set_option(self.h, int(option), int(value)))
+
+    def device_status(self, clear=True):
+        """Status of the kernels outside the transport since the last clear (0, or a negative
+        us_status such as US_ERR_TIMEOUT); synchronises the device."""
+        st = C.c_int(0)
+        self._check(lib().us_get_status(self.h, int(bool(clear)), C.byref(st)))
+        return st.value
 
     def launch_count(self):
         v = C.c_int64()
@@ -278,6 +295,20 @@ class Context:
         self._check(lib().us_get_record(self.h, int(path_lo), int(n), _ptr(out), _stream(stream)))
         return out
 
+    def arrivals(self, acq, stream=None):
+        """The last forward pass's arrival list as (tx, e, tau [s], a, path) tensors on the device,
+        in append order."""
+        n = int(self.stats()["arrivals"])
+        raw = torch.empty((max(n, 1), 4), dtype=torch.int32, device=self.device)
+        self._check(lib().us_get_arrivals(self.h, 0, n, _ptr(raw), _stream(stream)))
+        raw = raw[:n]
+        ne = int(acq["n_elem"])
+        row = raw[:, 0].to(torch.int64)
+        tq = raw[:, 1].to(torch.int64) & 0xFFFFFFFF
+        tau = (tq.double() * 2.0 ** -18 - 64.0) / float(acq["fs"])
+        return dict(tx=(row // ne).to(torch.int32), e=(row % ne).to(torch.int32), tau=tau,
+                    a=raw[:, 2].contiguous().view(torch.float32), path=raw[:, 3].to(torch.int64) & 0xFFFFFFFF)
+
     def splat(self, acq, f0, tx, e, tau, a, rf=None, stream=None):
         ad, ang = acq_desc(acq)
         rf = rf if rf is not None else torch.empty(self.rf_shape(acq), dtype=torch.float32, device=self.device)
@@ -308,9 +339,9 @@ class Context:
         return out
 
     # ---- loss and adjoint -------------------------------------------------------------------
-    def loss(self, img, b, bref, grad=True, stream=None):
+    def loss(self, img, b, bref, grad=True, stream=None, out=None):
         idesc = img_desc(img)
-        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        loss = out if out is not None else torch.empty(1, dtype=torch.float32, device=self.device)
         gb = torch.empty_like(b) if grad else None
         self._check(lib().us_loss(self.h, C.byref(idesc), _ptr(b), _ptr(bref), _ptr(loss), _ptr(gb), _stream(stream)))
         return loss, gb

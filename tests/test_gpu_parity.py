@@ -167,14 +167,20 @@ def test_das_adjoint_matches_oracle_and_dot_product(ctx):
     gi = rng.normal(size=(img["n_lines"], img["n_depth"])).astype(np.float32).astype(np.float64)
     ref = O.das_adjoint(acq, img, gi)
     got = ctx.das_adjoint(acq, img, dev(gi)).cpu().numpy()
-    bound = 2e-3 * O.das_adjoint(acq, img, np.abs(gi)) + 1e-6 * np.abs(ref).max()
-    # transposed taps land on the same two samples; the bound covers a shifted split
-    assert rel_l2(got, ref) <= 2e-3
+    # A tap whose FP32 interpolation position (error ~1e-3 samples) falls into the neighbouring
+    # interval moves a share of at most that error times w |g| onto the next sample, so every
+    # entry is bounded by 2e-3 of the transposed |gi| at that sample or a neighbour.
+    a = O.das_adjoint(acq, img, np.abs(gi))
+    near = a.copy()
+    near[..., 1:] = np.maximum(near[..., 1:], a[..., :-1])
+    near[..., :-1] = np.maximum(near[..., :-1], a[..., 1:])
+    bound = 2e-3 * near + 1e-6 * np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
+    assert rel_l2(got, ref) <= 2e-4
     x = rng.normal(size=rf.shape)
     lhs = float((ctx.das(acq, img, dev(x)).double().cpu().numpy() * gi).sum())
     rhs = float((x * got).sum())
     assert abs(lhs - rhs) <= 1e-4 * (np.abs(x).sum() * np.abs(gi).max())
-    assert np.mean(np.abs(got - ref) <= bound + 1e-5 * np.abs(ref).max()) > 0.999
 
 
 def test_envlog_matches_oracle(ctx):
@@ -346,6 +352,14 @@ def test_transport_vjp_inclusions(ctx, mode):
 
 
 def test_adjoint_end_to_end_and_autograd(ctx):
+    """The autograd bridge, and the whole adjoint chain against the oracle's.
+
+    (1) theta -> B-mode -> loss through BModeSimulation: its gradient is the one us_adjoint
+    returns for the same dL/dB (the bridge adds no arithmetic).  (2) For the oracle's dL/dB,
+    the GPU's chain (envelope/log VJP on its own image, transposed DAS, splat and path adjoints)
+    against the oracle's chain: 1e-3 per component.  (3) Each side with its own loss gradient:
+    the two images differ by up to 0.05 dB and pixels near the -60 dB clip may fall on either
+    side of it, which moves dL/dB itself; that end-to-end difference is bounded at 5e-3."""
     from paper_2604_15017_gb300 import usrt
 
     w = P.slab_scatterers(n_rays=800)
@@ -354,9 +368,14 @@ def test_adjoint_end_to_end_and_autograd(ctx):
     bref = dev(bref_ref)
     th = torch.tensor(w["theta"], dtype=torch.float32, requires_grad=True)
     b = usrt.BModeSimulation.apply(th, ctx, sid, w["acq"], w["img"], w["seed"])
+    b.retain_grad()
     loss = ((b - bref) ** 2).mean()
     loss.backward()
     g_gpu = th.grad.double().numpy()
+    rf, b2 = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    g_direct, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, b.grad.contiguous())
+    g_direct = g_direct.double().cpu().numpy()
+    assert np.allclose(g_gpu, g_direct, rtol=1e-4, atol=1e-6 * np.abs(g_direct).max())
     # oracle: same chain on its own forward
     ref = O.forward(w)
     _, gb = O.loss(w["img"], ref["b"], bref_ref)
@@ -364,7 +383,15 @@ def test_adjoint_end_to_end_and_autograd(ctx):
     g_ref = ref["run"].gradient(grf)
     scale = np.abs(g_ref * w["theta"])
     err = np.abs(g_gpu - g_ref) * np.abs(w["theta"])
-    assert np.all(err <= 2e-2 * scale + 1e-3 * scale.max()), np.c_[g_gpu, g_ref]
+    assert np.all(err <= 5e-3 * scale + 1e-4 * scale.max()), np.c_[g_gpu, g_ref]
+    # the chain for an oracle dL/dB that is zero within 0.1 dB of the clip (where the two images,
+    # 0.05 dB apart, could disagree on the clip mask)
+    gb = np.where(np.abs(ref["b"] + w["img"]["dr_db"]) > 0.1, gb, 0.0)
+    g_ref, cond = ref["run"].gradient_cond(O.bmode_vjp(w["acq"], w["img"], ref["rf"], gb))
+    g_chain, _ = ctx.adjoint(sid, w["theta"], w["acq"], w["img"], w["seed"], rf, dev(gb))
+    err = np.abs(g_chain.double().cpu().numpy() - g_ref)
+    print("slab chain", err / np.abs(g_ref), err / cond)
+    assert np.all(err <= 1e-3 * np.abs(g_ref) + 2e-5 * cond), np.c_[g_chain.cpu().numpy(), g_ref, cond]
     ctx.release_scene(sid)
 
 

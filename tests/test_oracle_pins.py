@@ -551,3 +551,47 @@ def test_gradient_matches_replay_finite_differences():
             fd = (L(tp) - L(tm)) / (2 * h * th[k])
             errs.append(abs(fd - g[k]) * abs(th[k]))
         assert min(errs) <= 1e-2 * abs(g[k] * th[k]) + 1e-4 * sens.max(), (k, g[k], errs)
+
+
+def test_gradient_41_parameters_differentiation_scene_vs_finite_differences():
+    """The differentiation configuration's 41 parameters (c, rho, alpha of 13 media, A_s, f0) on
+    its own scene (12 ellipsoids of 16,640 triangles, 1e5 scatterers; one 0-deg plane wave, at
+    most 4 interactions), with fewer rays and a coarser image to keep the check short.
+
+    (1) d/dtheta of the linear functional <dL/dRF, RF> against central differences of the replay
+    at a 1e-6 relative step: 1e-4 per component.  (2) The whole loss at the stated central
+    step of 1e-3 relative: every density and attenuation entry within 1e-2; a sound speed or f0
+    moves every echo's phase by ~1 rad at that step, so those are asked for at the best step of
+    the sweep 1e-4..1e-7 (Sec. 4.2.1's FD-vs-AD methodology)."""
+    w = P.differentiation(n_rays=40)
+    w["img"] = P.image(64, 256, w["img"]["x0"], w["img"]["x1"], 0.0, w["img"]["z1"])
+    sc = O.Scene.from_workload(w)
+    th, acq, img, M = w["theta"], w["acq"], w["img"], w["M"]
+    assert M == 13 and len(th) == 41
+    run = O.Run(sc, th, M, acq, 0)
+    tgt = O.Run(sc, w["theta_target"], M, acq, 0)
+    _, _, bref = O.bmode(acq, img, tgt.rf())
+    rf = run.rf()
+    _, _, b = O.bmode(acq, img, rf)
+    _, gb = O.loss(img, b, bref)
+    grf = O.bmode_vjp(acq, img, rf, gb)
+    g = run.gradient(grf)
+    sens = np.abs(g * th)
+
+    def L(t):
+        _, _, bb = O.bmode(acq, img, run.replay_rf(t))
+        return O.loss(img, bb, bref)[0]
+
+    def central(f, k, h):
+        tp, tm = th.copy(), th.copy()
+        tp[k] *= 1 + h
+        tm[k] *= 1 - h
+        return (f(tp) - f(tm)) / (2 * h * th[k])
+
+    for k in range(len(th)):
+        fd = central(lambda t: (grf * run.replay_rf(t)).sum(), k, 1e-6)
+        assert abs(fd - g[k]) * abs(th[k]) <= 1e-4 * sens[k] + 1e-7 * sens.max(), (k, g[k], fd)
+        phase = k == len(th) - 1 or (k < 3 * M and k % 3 == 0)
+        steps = (1e-4, 1e-5, 1e-6, 1e-7) if phase else (1e-3,)
+        err = min(abs(central(L, k, h) - g[k]) * abs(th[k]) for h in steps)
+        assert err <= 1e-2 * sens[k] + 1e-4 * sens.max(), (k, g[k], err)

@@ -57,6 +57,29 @@ def test_noalloc_envlog_matches_allocating_entry_point_twice():
     ctx.close()
 
 
+@pytest.mark.parametrize("shape", [(96, 512), (256, 1024)])
+def test_noalloc_envlog_two_kernel_path_matches(shape):
+    """The two-kernel path (envelope into the array's image region, then log compression), forced
+    for both entry points, up to the largest image the array holds; two calls in a row."""
+    ctx = usrt.Context(0)
+    nl, nd = shape
+    usrt.set_envlog_fused(False)
+    try:
+        for seed in (3, 4):
+            img = P.image(nl, nd, 0.0, 1.0, 0.0, 1.0, dr_db=60.0)
+            irf = image_input(seed, nl, nd)
+            ref = ctx.envlog(img, irf)
+            out = torch.full_like(irf, 123.0)
+            assert noalloc(img, irf, out) == usrt.US_OK
+            torch.cuda.synchronize()
+            assert torch.isfinite(out).all()
+            assert float((out - ref).abs().max()) <= TOL_DB
+            assert float(out.max()) == 0.0 and float(out.min()) >= -60.0
+    finally:
+        usrt.set_envlog_fused(True)
+    ctx.close()
+
+
 def test_noalloc_envlog_rejects_oversize_images():
     img = P.image(512, 1024, 0.0, 1.0, 0.0, 1.0)  # 512 * 1024 pixels > 256 * 1024
     irf = torch.zeros(1, device="cuda")
