@@ -29,7 +29,7 @@ enum Slot {
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
   W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS,
-  W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_COUNT
+  W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_QA_SURF, W_KEEP, W_COUNT
 };
 
 struct SceneGPU {
@@ -396,6 +396,8 @@ int alloc_queues(us_ctx* ctx, long long n, cudaStream_t st, Queues& Q) {
   CKS(ws(ctx, W_QA_PA, n, st, &Q.a.pa));
   CKS(ws(ctx, W_QA_WT, n, st, &Q.a.wt));
   CKS(ws(ctx, W_QA_META, n, st, &Q.a.meta));
+  CKS(ws(ctx, W_QA_SURF, n, st, &Q.a.surf));
+  Q.b.surf = nullptr;  // the sorted queue's carried hits go straight into the hit array
   CKS(ws(ctx, W_QB_PA, n, st, &Q.b.pa));
   CKS(ws(ctx, W_QB_WT, n, st, &Q.b.wt));
   CKS(ws(ctx, W_QB_META, n, st, &Q.b.meta));
@@ -425,6 +427,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   A.med = med;
   A.acq = q;
   CKS(ws(ctx, W_HITS, n, st, &A.hits));
+  CKS(ws(ctx, W_KEEP, n, st, &A.keep));
   // secondary-ray jobs: the interaction kernel appends into `unsorted`, each round's jobs are
   // sorted into A.nee, which the secondary-ray kernel and the adjoint read
   const size_t jobs = (size_t)n * std::max(1, q.kmax);  // at most one job per path and round
@@ -470,6 +473,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   CKS(ws(ctx, W_RAY_KEY, n, st, &rs.key));
   CKS(ws(ctx, W_RAY_CNT, RAY_BUCKETS, st, &rs.cnt));
   CKS(ws(ctx, W_RAY_OFF, RAY_BUCKETS + 1, st, &rs.off));
+  A.trav_n = rs.off + RAY_KEY_BUCKETS;  // written by each round's ray sort
   CKS(ws(ctx, W_RAY_CUR, RAY_BUCKETS, st, &rs.cursor));
   // the job sort's scratch: the ray sort's, or its own when it runs on the second stream
   // beside the next round's ray sort

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long pat
     A.qout.pa[i] = make_float4(xe + (u0 - 0.5f) * q.pitch, (u1 - 0.5f) * q.hel, 0.0f, 3.14159265358979f / q.nr);
     A.qout.wt[i] = make_float4(r * cp, r * sp, wz, tau0);
     A.qout.meta[i] = make_uint4((uint32_t)path, 0xFFFFFFFFu, 0u, __float_as_uint(0.0f));
+    A.qout.surf[i] = make_float2(-1.0f, 0.0f);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt->live[0] = n;
 }
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long pat
 __global__ void __launch_bounds__(TRAV_THREADS) k_traverse(TransportArgs A) {
   if (blockIdx.x == 0 && threadIdx.x == 0)  // secondary jobs of this round follow the previous rounds'
     A.cnt->nee_off[A.k] = A.k ? A.cnt->nee_off[A.k - 1] + A.cnt->nee[A.k - 1] : 0u;
-  const uint32_t n = A.cnt->live[A.k];
+  const uint32_t n = *A.trav_n;  // the rest of the queue carries its surface hit
   bool overflow = false;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const float4 pa = A.qin.pa[i];
@@ -235,7 +236,10 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
       continue;
     }
     if (!(ahead_ok && t_ahead <= tbest)) {  // no cell left to enter below tbest: done
-      if (cbest != code0) A.hits[ray] = make_float2(tbest, __uint_as_float(cbest));
+      if (cbest != code0) {  // a scatterer comes first; its pass-through carries the surface hit on
+        A.keep[ray] = A.hits[ray];
+        A.hits[ray] = make_float2(tbest, __uint_as_float(cbest));
+      }
       ray = 0xFFFFFFFFu;
       continue;
     }
@@ -373,10 +377,20 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
       A.nee.jpath[slot] = (uint32_t)path;
     }
     if (rec) *rec = word;
+    // past a scatterer the ray goes on unchanged, so the surface hit found this round is the
+    // next one: it is carried, at its distance from the new origin, unless it lies within the
+    // minimum hit distance (a fresh query would pass over it)
+    float2 carry = make_float2(-1.0f, 0.0f);
+    if (cls == CLS_SCAT) {
+      const float2 ks = A.keep[i];
+      const float t_rem = ks.x - t;
+      if (t_rem > 2.0f * T_MIN) carry = make_float2(t_rem, ks.y);
+    }
     const uint32_t o = append_slot(&A.cnt->live[A.k + 1]);
     A.qout.pa[o] = make_float4(x.x, x.y, x.z, a);
     A.qout.wt[o] = make_float4(w.x, w.y, w.z, tau_hi);
     A.qout.meta[o] = make_uint4(meta.x, code, (uint32_t)m | ((uint32_t)(A.k + 1) << 8), __float_as_uint(tau_lo));
+    A.qout.surf[o] = carry;
   }
 }
 
@@ -498,7 +512,7 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
 // ------------------------------------------------------------------------------------------
 // Coherence sort of a ray queue (one counting-sort pass, 14-bit key)
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 w) {
+__device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 w, bool carried) {
   // origin: 8 x 8 cells over the scene's x and z extent
   const int cx = min(7, max(0, (int)((o.x - rs.lo.x) * rs.inv_ext.x * 8.0f)));
   const int cz = min(7, max(0, (int)((o.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
@@ -513,6 +527,8 @@ __device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 
   }
   const int bu = min(15, max(0, (int)((u + 1.0f) * 8.0f)));
   const int bv = min(15, max(0, (int)((v + 1.0f) * 8.0f)));
+  if (carried)  // 4 x 4 origin cells, 8 x 8 direction bins, after the rays that need a query
+    return (uint32_t)RAY_KEY_BUCKETS + (uint32_t)(((((cz >> 1) << 2) | (cx >> 1)) << 6) | ((bu >> 1) << 3) | (bv >> 1));
   return (uint32_t)((((cz << 3) | cx) << 8) | (bu << 4) | bv);
 }
 
@@ -522,7 +538,7 @@ __global__ void __launch_bounds__(256) k_ray_keys(TransportArgs A, PathQ from, R
   __syncthreads();
   const uint32_t n = A.cnt->live[A.k];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t key = ray_key(rs, xyz(from.pa[i]), xyz(from.wt[i]));
+    const uint32_t key = ray_key(rs, xyz(from.pa[i]), xyz(from.wt[i]), from.surf[i].x >= 0.0f);
     rs.key[i] = key;
     atomicAdd(&h[key], 1u);
   }
@@ -565,6 +581,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, Pat
       to.pa[o] = from.pa[i];
       to.wt[o] = from.wt[i];
       to.meta[o] = from.meta[i];
+      if (key[j] >= (uint32_t)RAY_KEY_BUCKETS) A.hits[o] = from.surf[i];  // the carried surface hit
     }
     __syncthreads();
   }

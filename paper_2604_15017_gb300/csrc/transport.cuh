@@ -10,6 +10,8 @@ struct PathQ {
   float4* pa;   // (o.x, o.y, o.z, a)
   float4* wt;   // (w.x, w.y, w.z, tau_hi)
   uint4* meta;  // (path id, previous primitive code, medium | k << 8, bits(tau_lo))
+  float2* surf; // the surface hit carried across a scatterer event: (distance from o, bits(code)),
+                // distance < 0 when there is none (the queue the interaction kernel appends to)
 };
 
 // secondary-ray jobs queued by the interaction kernels; round k appends at nee_off[k], so the
@@ -57,6 +59,8 @@ struct TransportArgs {
   Acq acq;
   PathQ qin, qout;
   float2* hits;       // (t, bits(code)) per queue slot
+  float2* keep;       // per queue slot: the surface hit a scatterer event replaced in hits
+  const uint32_t* trav_n;  // rays of the sorted queue that need a surface query (the rest carry one)
   NeeQ nee;
   NeeRes nres;        // null members unless the pass is recorded for the adjoint
   Arrival* arr;       // may be null (adjoint recompute: no arrivals)
@@ -69,9 +73,13 @@ struct TransportArgs {
 
 // coherence sort of a ray queue: one counting-sort pass over a 14-bit key (origin cell in x and
 // z, octahedral direction bin), so that the lanes of a warp start near each other and point the
-// same way
+// same way.  Rays that carry their surface hit across a scatterer event (a pass-through: the
+// surface ahead is the one already found) follow in RAY_CARRY_BUCKETS coarser buckets of their
+// own, so the surface query runs over the first RAY_KEY_BUCKETS buckets only.
 constexpr int RAY_KEY_BITS = 14;
-constexpr int RAY_BUCKETS = 1 << RAY_KEY_BITS;
+constexpr int RAY_KEY_BUCKETS = 1 << RAY_KEY_BITS;
+constexpr int RAY_CARRY_BUCKETS = 1024;
+constexpr int RAY_BUCKETS = RAY_KEY_BUCKETS + RAY_CARRY_BUCKETS;
 struct RaySort {
   float3 lo, inv_ext;   // scene bounds for the origin cells
   uint32_t* key;        // per ray
