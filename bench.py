@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="serve: arrival window, s")
     ap.add_argument("--serve-scenes", type=int, default=32, help="serve: resident scenes requests draw from")
     ap.add_argument("--lanes", type=int, default=4, help="serve: concurrent lanes")
+    ap.add_argument("--frame-only", action="store_true", help="frame config: skip the embedded batch and serve modes")
+    ap.add_argument("--default-serve-seconds", type=float, default=20.0,
+                    help="frame config: arrival window of the embedded serve measurement")
     return ap.parse_args()
 
 
@@ -296,7 +299,14 @@ def _plain(ctx, it):
 
 
 def run_batch(args):
-    """Batched (lanes + CUDA graph, autotuned) vs one-by-one: path-segments/s over the batch."""
+    print(json.dumps(measure_batch(args, args.steps, args.warmup)))
+
+
+def measure_batch(args, steps, warmup, frame_rate=None):
+    """Batched (lanes + CUDA graph, autotuned) vs one-by-one: path-segments/s over the batch.
+    frame_rate (path-segments/s of the full single frame, fwd + adj) gives the reasoned bound on
+    any launch organisation of these kernels, a persistent whole-batch launch included: the
+    batch's segments at the rate the kernels reach when one frame fills the GPU."""
     import torch
     from paper_2604_15017_gb300 import phantoms as P, usrt
 
@@ -313,15 +323,15 @@ def run_batch(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         e0.record(st)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record(st)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps
+        return e0.elapsed_time(e1) / steps
 
     ms_plain = timed(lambda: [_plain(ctx, it) for it in items])
     batch = usrt.Batch(ctx, items)
@@ -329,7 +339,7 @@ def run_batch(args):
     launches0 = ctx.launch_count()
     with ClockSampler(0) as clk:
         ms_batch = timed(batch.run)
-    launches = (ctx.launch_count() - launches0) // (args.steps + args.warmup)
+    launches = (ctx.launch_count() - launches0) // (steps + warmup)
     side = torch.cuda.Stream()
     side.wait_stream(st)
     with torch.cuda.stream(side):
@@ -342,8 +352,8 @@ def run_batch(args):
     ms_graph = timed(g.replay)
     n_paths = sum(w["acq"]["n_rays"] * w["acq"]["n_elem"] * len(w["acq"]["angles"]) for w in ws)
     best = min(ms_batch, ms_graph)
-    out = {"metric": METRIC, "value": segs / (best * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": best, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    out = {"metric": METRIC, "value": segs / (best * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+           "warmup": warmup, "ms_per_step": best, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "batch-%d-scenes-seed4-scale%g" % (args.batch_n, args.scale),
                       "step": "whole batch (even fwd, odd fwd+loss+adj)", "paths_per_step": n_paths,
                       "segments_per_step": segs, "autotuned_lanes": lanes, "autotuned_trav_blocks_per_sm": trav,
@@ -351,12 +361,21 @@ def run_batch(args):
            "plain": {"ms_per_step": ms_plain, "value": segs / (ms_plain * 1e-3)},
            "batched": {"ms_per_step": ms_batch, "value": segs / (ms_batch * 1e-3)},
            "graph": {"ms_per_step": ms_graph, "value": segs / (ms_graph * 1e-3)},
-           "speedup_vs_plain": ms_plain / best, "gpu_launches": launches * args.steps, "clocks": clk.summary()}
-    print(json.dumps(out))
+           "speedup_vs_plain": ms_plain / best, "gpu_launches": launches * steps, "clocks": clk.summary()}
+    if frame_rate:
+        out["full_gpu_bound_ms"] = segs / frame_rate * 1e3
+        out["fraction_of_full_gpu_rate"] = out["full_gpu_bound_ms"] / best
+    for it in items:
+        ctx.release_scene(it["scene"])
     ctx.close()
+    return out
 
 
 def run_serve(args):
+    print(json.dumps(measure_serve(args, args.serve_seconds)))
+
+
+def measure_serve(args, seconds):
     """Poisson arrivals of requests on resident scenes (70 % fwd B-mode, 30 % fwd+loss+adj), served
     by the continuous-batching loop under a memory budget, against the plain sequential path."""
     import torch
@@ -372,7 +391,7 @@ def run_serve(args):
         else:
             it["bref_fa"] = it["bref"]
     torch.cuda.synchronize()
-    times = serve.poisson_arrivals(args.rate, args.serve_seconds, seed=5)
+    times = serve.poisson_arrivals(args.rate, seconds, seed=5)
     rng = np.random.default_rng(5)
     arrivals = []
     n_adj = 0
@@ -391,11 +410,13 @@ def run_serve(args):
     out = {"metric": "requests/s", "value": served["throughput"], "unit": "requests/s", "n_gpus": 1,
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "serve-poisson-%grps-%gs-%d-scenes-seed5-scale%g" %
-                      (args.rate, args.serve_seconds, args.serve_scenes, args.scale), "lanes": args.lanes,
+                      (args.rate, seconds, args.serve_scenes, args.scale), "lanes": args.lanes,
                       "requests": len(arrivals), "fwd_adj_requests": int(n_adj), "mem_budget_gb": 120},
            "served": served, "sequential": seq, "max_running": srv.max_running, "clocks": clk.summary()}
-    print(json.dumps(out))
+    for it in items:
+        ctx.release_scene(it["scene"])
     ctx.close()
+    return out
 
 
 def run_optim(args):
@@ -576,6 +597,21 @@ def main():
     ms = max_over_ranks(ms, world, "cuda")
     value = whole_job_rate(segs_per_step, world, ms * 1e-3)
 
+    # forward only (transport, splat, DAS, envelope/log: the B-mode frame), same frame
+    for _ in range(args.warmup):
+        ctx.forward(sid, theta, acq, img, seed=seed)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.forward(sid, theta, acq, img, seed=seed)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms_fwd = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    fwd = {"ms_per_step": ms_fwd, "value": whole_job_rate(segs_per_step, world, ms_fwd * 1e-3), "unit": UNIT,
+           "frames_per_s": world * 1e3 / ms_fwd, "step": "fwd (transport + splat + DAS + envelope/log)"}
+
     # end to end through the public API with host buffers: B_ref host -> device each step,
     # loss and gradient device -> host each step
     bref_h = bref.cpu().pin_memory()
@@ -636,11 +672,18 @@ def main():
                       "l2": "per-step working set (path queues + arrivals, ~4 GB) exceeds L2; scene BVH resident"},
            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
            "stages_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in stages.items() if v[1]}}
+    out["fwd"] = fwd
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds, seed)
+    ctx.release_scene(sid)
+    ctx.close()
+    if rank == 0 and world == 1 and not args.frame_only:
+        # the batched (many scenes of uneven size) and served (Poisson arrivals) modes of the
+        # metric, at their own configurations; one GPU
+        out["batch"] = measure_batch(args, 2, 1, frame_rate=value)
+        out["serve"] = measure_serve(args, args.default_serve_seconds)
     if rank == 0:
         print(json.dumps(out))
-    ctx.close()
 
 
 if __name__ == "__main__":

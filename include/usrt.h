@@ -195,7 +195,11 @@ void us_set_envlog_fused(int enable);
 enum {
   US_STAGE_GENERATE = 0, US_STAGE_TRAVERSE, US_STAGE_INTERACT, US_STAGE_NEE, US_STAGE_SPLAT_SORT,
   US_STAGE_SPLAT_ROWS, US_STAGE_DAS, US_STAGE_ENVLOG, US_STAGE_LOSS, US_STAGE_ENVLOG_VJP, US_STAGE_DAS_ADJ,
-  US_STAGE_NEE_ADJ, US_STAGE_PATH_ADJ, US_STAGE_OTHER, US_STAGE_DAS_ACQ, US_N_STAGES
+  US_STAGE_NEE_ADJ, US_STAGE_PATH_ADJ, US_STAGE_OTHER, US_STAGE_DAS_ACQ,
+  US_STAGE_RAY_SORT,  /* each round's coherence sort of the path queue */
+  US_STAGE_JOB_SORT,  /* each round's sort of the secondary-ray jobs (on the lane's second stream
+                         when US_OPT_NEE_STREAM is on: its span then overlaps other stages) */
+  US_N_STAGES
 };
 
 /* enable != 0 starts recording stage events (and clears what was accumulated); 0 stops. */

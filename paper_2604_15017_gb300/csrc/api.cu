@@ -493,7 +493,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   for (int k = 0; k <= q.kmax; ++k) {
     A.k = k;
     {
-      StageScope sc_(ctx, US_STAGE_GENERATE, 3, st);
+      StageScope sc_(ctx, US_STAGE_RAY_SORT, 3, st);
       launch_ray_sort(A, Q.a, Q.b, rs, grid_of(ctx, 2), st);
     }
     A.qin = Q.b;
@@ -516,7 +516,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
       ns = L->side;
     }
     if (sort_jobs && k < q.kmax) {
-      StageScope sc_(ctx, US_STAGE_GENERATE, 3, ns);
+      StageScope sc_(ctx, US_STAGE_JOB_SORT, 3, ns);
       launch_job_sort(A, unsorted, sorted, js, grid_of(ctx, 2), ns);
     }
     A.nee = sorted;

@@ -31,7 +31,7 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_shape_param_grad", "us_get_status", "us_set_envlog_fused"]
 OPT_DAS_TMA, OPT_LANES, OPT_NEE_STREAM, OPT_FAULT_BARRIER = 0, 1, 2, 3
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
-          "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq"]
+          "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq", "ray_sort", "job_sort"]
 
 
 class UsrtError(RuntimeError):
