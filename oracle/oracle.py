@@ -29,7 +29,7 @@ LIB_PATH = os.path.join(BUILD_DIR, "liboracle.so")
 
 # flat descriptor layouts (mirrors the enums of usrt_oracle.cpp)
 ACQ_KEYS = ["n_elem", "pitch", "h_el", "n_tx", "fs", "n_samples", "k_max", "n_rays", "bw", "alpha_m",
-            "alpha_c", "c_bf", "split_mode", "split_q", "stream_id", "tx_elem", "n_tx_elem"]
+            "alpha_c", "c_bf", "split_mode", "split_q", "stream_id", "tx_elem", "n_tx_elem", "rough_nee"]
 IMG_KEYS = ["n_lines", "n_depth", "x0", "x1", "z0", "z1", "dr_db", "lambda1", "lambda2", "f_number"]
 IMG_DEFAULTS = {"dr_db": 60.0, "lambda1": 0.0, "lambda2": 1.0, "f_number": 0.0}
 
@@ -98,6 +98,7 @@ def lib():
             l.ora_gradient_cond.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D, D]
             l.ora_gradient_acq.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, D]
             l.ora_gradient_shape.argtypes = [C.c_void_p, C.c_void_p, D, C.c_uint64, C.c_int, D, C.c_int, D, D]
+            l.ora_inject_sums.argtypes = [C.c_void_p, D, C.c_int, D, D, C.c_uint64, C.c_longlong, D, D, C.c_int, D, D]
             l.ora_trace_injected.restype = C.c_int
             l.ora_trace_injected.argtypes = [C.c_void_p, D, C.c_int, D, D, C.c_uint64, D, D, C.c_double, C.c_double,
                                              C.c_int, C.c_longlong, I, C.c_int, C.c_int, C.c_int, I, D, D, I, I, D]
@@ -123,6 +124,7 @@ def acq_array(acq):
     vals = dict(acq)
     vals["n_tx"] = len(acq["angles"])
     vals.setdefault("n_tx_elem", 0)
+    vals.setdefault("rough_nee", 1)
     arr = np.array([float(vals[k]) for k in ACQ_KEYS], dtype=np.float64)
     ang = np.asarray(acq["angles"], dtype=np.float64)
     return arr, ang
@@ -464,3 +466,16 @@ def trace_injected(scene, theta, M, acq, o, w, a0=1.0, tau0=0.0, tx=0, ray=0, fo
                                  kind.ctypes.data_as(I), rec.ctypes.data_as(I), last.ctypes.data_as(D))
     arr = [(int(e[i]), float(tau[i]), float(a[i]), int(kind[i])) for i in range(n)]
     return arr, rec.reshape(-1, 4), last
+
+
+def inject_sums(scene, theta, M, acq, o, w, seed=0, nthreads=None):
+    """Injected paths (origins o[n, 3], unit directions w[n, 3], weight 1): per element, the
+    sum of what the paths deposit there and the sum of the squares of the per-path amounts."""
+    a_arr, ang = acq_array(acq)
+    o, op = _d(np.asarray(o).reshape(-1, 3))
+    w, wp = _d(np.asarray(w).reshape(-1, 3))
+    s = np.zeros(acq["n_elem"])
+    s2 = np.zeros(acq["n_elem"])
+    lib().ora_inject_sums(scene.h, _d(theta)[1], M, a_arr.ctypes.data_as(D), ang.ctypes.data_as(D), C.c_uint64(seed),
+                          len(o), op, wp, nthreads or default_threads(), s.ctypes.data_as(D), s2.ctypes.data_as(D))
+    return s, s2

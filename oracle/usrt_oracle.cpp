@@ -168,12 +168,15 @@ D3 subd(const D3& a, const D3& b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); 
 // ------------------------------------------------------------------------------------------
 enum {
   A_NE = 0, A_PITCH, A_HEL, A_NTX, A_FS, A_NS, A_KMAX, A_NR, A_BW, A_ALPHA_M, A_ALPHA_C, A_CBF,
-  A_SPLIT_MODE, A_SPLIT_Q, A_STREAM, A_TX_ELEM, A_N_TX_ELEM, A_COUNT
+  A_SPLIT_MODE, A_SPLIT_Q, A_STREAM, A_TX_ELEM, A_N_TX_ELEM, A_ROUGH_NEE, A_COUNT
 };
 enum { I_NL = 0, I_ND, I_X0, I_X1, I_Z0, I_Z1, I_DR, I_L1, I_L2, I_FNUM, I_COUNT };
 
 struct Acq {
   int ne, ntx, ns, kmax, nr, split_mode, tx_elem, n_tx_elem;
+  int rough_nee;  // secondary rays at rough interface events too (else at scatterers only);
+                  // 2 (tests of the estimator): the secondary ray alone estimates the rough
+                  // event's direct contribution (no balance weights, primary direct hits dropped)
   double pitch, hel, fs, bw, alpha_m, alpha_c, cbf, split_q;
   uint32_t stream;
   std::vector<double> angles;
@@ -204,6 +207,7 @@ Acq make_acq(const double* a, const double* angles) {
   q.stream = (uint32_t)a[A_STREAM];
   q.tx_elem = (int)a[A_TX_ELEM];
   q.n_tx_elem = (int)a[A_N_TX_ELEM];
+  q.rough_nee = (int)a[A_ROUGH_NEE];
   q.angles.assign(angles, angles + q.ntx);
   return q;
 }
@@ -635,36 +639,41 @@ Iface<S> interface_event(const V3<S>& w, const V3<S>& nin, const S& c1, const S&
 }
 
 // ------------------------------------------------------------------------------------------
-// Secondary (receiver-directed) ray from a scatterer centre to the chosen element centre
-// [Sec. 2.3.3]: straight segment, transmission coefficient at every crossed interface (zero
-// under total internal reflection), attenuation and travel time per sub-segment in the medium
-// tracked across the crossings, receive directivity at the element.
+// Secondary (receiver-directed) rays [Sec. 2.3.3]: a straight segment from the event to the
+// chosen element's centre, the transmission coefficient at every crossed interface (zero under
+// total internal reflection), attenuation and travel time per sub-segment in the medium tracked
+// across the crossings, receive directivity (Eq. cutoff) at the element.
 // ------------------------------------------------------------------------------------------
 // The target element centre carries the pitch derivative and the triangles their shape
 // tangents (when the duals hold them), so the geometry below (length, direction, crossing
 // distances on the crossed triangles' planes, incidence cosines, directivity) is evaluated in
-// S; which triangles are crossed is decided in double.
+// S; which triangles are crossed is decided in double.  `skip` is a triangle the segment starts
+// on (it is not a crossing).  Returns false when nothing arrives (directivity cutoff, total
+// internal reflection at a crossing); else trans = prod T * attenuation * f_rx and the time.
 template <class S>
-bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, int m_start, S& gain, S& dt,
-                std::vector<std::pair<double, int>>& xs, double* frx_out) {
-  D3 p = sc.sp[j];
+bool secondary_segment(const Scene& sc, const Phys<S>& P, const Acq& q, const V3<S>& ps, int skip, int e2, int m_start,
+                       S& trans, S& dt, V3<S>& dir, S& dist, std::vector<std::pair<double, int>>& xs,
+                       double* frx_out) {
   S xt(q.elem_x(e2));
   elem_acq(xt, P.acq_base, q.elem_x(e2), q);
-  V3<S> dv = mk3<S>(xt + (-p.x), S(-p.y), S(-p.z));
+  V3<S> dv = mk3<S>(xt + (-1.0 * ps.x), -1.0 * ps.y, -1.0 * ps.z);
   S D = sqrt(dot(dv, dv));
   V3<S> d = scale(dv, 1.0 / D);
-  S cosd = -d.z;
+  dir = d;
+  dist = D;
+  S cosd = -1.0 * d.z;
   double cv = std::max(-1.0, std::min(1.0, val(cosd)));
   S th = (cv == val(cosd)) ? acos(cosd) : S(std::acos(cv));
   S frx = f_rx<S>(th, q.alpha_m, q.alpha_c);
   *frx_out = val(frx);
   if (val(frx) == 0.0) return false;
-  all_crossings(sc, p, d3(val(d.x), val(d.y), val(d.z)), val(D), xs);
+  all_crossings(sc, d3(val(ps.x), val(ps.y), val(ps.z)), d3(val(d.x), val(d.y), val(d.z)), val(D), xs);
+  if (skip >= 0) xs.erase(std::remove_if(xs.begin(), xs.end(), [&](const std::pair<double, int>& c) { return c.second == skip; }),
+                          xs.end());
   S prodT(1.0), path_alpha(0.0);
   S time(0.0);
   int m = m_start;
   S tprev(0.0);
-  const V3<S> ps = mk3<S>(S(p.x), S(p.y), S(p.z));
   for (size_t i = 0; i < xs.size(); ++i) {
     int tri = xs[i].second;
     V3<S> v0;
@@ -687,8 +696,119 @@ bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, 
   S l = D - tprev;
   path_alpha = path_alpha + P.al[m] * l;
   time = time + l / P.c[m];
-  gain = prodT * exp(-KAPPA * P.f0 * path_alpha) * frx * (double)q.ne;
+  trans = prodT * exp(-KAPPA * P.f0 * path_alpha) * frx;
   dt = time;
+  return true;
+}
+
+// At a scatterer [Sec. 2.3.3]: the segment from the scatterer's centre; the element is chosen
+// uniformly, so the weight carries N_e.  gain = N_e * prod T * attenuation * f_rx.
+template <class S>
+bool nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int j, int e2, int m_start, S& gain, S& dt,
+                std::vector<std::pair<double, int>>& xs, double* frx_out) {
+  const D3 p = sc.sp[j];
+  const V3<S> ps = mk3<S>(S(p.x), S(p.y), S(p.z));
+  S trans, D;
+  V3<S> d;
+  if (!secondary_segment<S>(sc, P, q, ps, -1, e2, m_start, trans, dt, d, D, xs, frx_out)) return false;
+  gain = trans * (double)q.ne;
+  return true;
+}
+
+template <class S>
+S smith_g1(const S& vn, const S& alpha);  // Smith masking of GGX, defined with the sampling below
+
+// |dh/do| of refraction about the facet h (Walter et al. 2007) with indices 1 / c: o.h < 0
+template <class S>
+S refract_jacobian(const S& ih, const S& oh, const S& c1, const S& c2) {
+  const S den = ih / c1 + oh / c2;
+  return (-1.0 * oh) / (c2 * c2 * den * den);
+}
+
+// solid angle of an element face (pitch x h_el) seen along unit direction o from distance^2 r2
+template <class S>
+S element_solid_angle(const Phys<S>& P, const Acq& q, const V3<S>& o, const S& r2) {
+  S pitch(q.pitch);
+  if (P.acq_base >= 0) elem_acq(pitch, P.acq_base, q.pitch, q);  // d pitch / d pitch = 1
+  return pitch * q.hel * (val(o.z) < 0.0 ? -1.0 * o.z : o.z) / r2;
+}
+
+// GGX distribution of microfacet normals, Eq. GGX_PDF
+template <class S>
+S ggx_d(const S& nh, const S& alpha) {
+  const S a2 = alpha * alpha;
+  const S k = nh * nh * (a2 - 1.0) + 1.0;
+  return a2 / (PI * k * k);
+}
+
+// Direction density of the primary's own sampling at a rough event (reading of Sec. 2.3.2): the
+// facet normal h ~ D(h) (h.n), then reflection with probability P_r(h) (R(h)^2, or the fixed
+// split q; 1 under total internal reflection) or refraction: toward o it is D(h) (h.n) |dh/do|
+// P(choice), with h the facet that maps the incident direction onto o.
+template <class S>
+S bsdf_pdf(const Acq& q, const S& nh, const S& alpha, const S& J, const Iface<S>& f, bool reflect) {
+  const S pr = f.tir ? S(1.0) : (q.split_mode == 0 ? f.R * f.R : S(q.split_q));
+  return ggx_d(nh, alpha) * nh * J * (reflect ? pr : 1.0 - pr);
+}
+
+// At a rough interface [Sec. 2.3.2-2.3.3, Eq. GGX_PDF] (reading): the secondary ray leaves the
+// event point x toward the chosen element's centre, direction o.  The microfacet BSDF gives the
+// amplitude the interface sends per unit solid angle toward o, for the incident direction w (i =
+// -w points back to the side it came from, n the macro normal on that side): with the half
+// vector h of reflection (h ~ i + o, o on the incident side) or of refraction (h ~ -(i / c1 +
+// o / c2), o on the far side; Snell with sound speeds), the density the primary sampling
+// itself has there, g = D(h) G1(i) G1(o) C(h) |i.h| |dh/do| / |i.n|, with C the pressure
+// reflection or transmission coefficient of the facet h and |dh/do| = 1 / (4 |o.h|) for
+// reflection, |o.h| / (c2^2 (i.h / c1 + o.h / c2)^2) for refraction (Walter et al. 2007).  The
+// primary itself reaches the array from the event too, so the two estimates are combined by
+// multiple importance sampling (balance heuristic) over the element's solid angle Omega (face
+// pitch x h_el, cosine at the element, 1 / r^2): the secondary ray's density is that of a
+// uniform element and direction within it, 1 / (N_e Omega), the primary's is bsdf_pdf, and the
+// secondary ray carries g / (1 / (N_e Omega) + bsdf_pdf) times the transmissions, attenuation
+// and f_rx of the segment; the primary's own direct arrival takes the complementary weight.
+// A facet toward o that is met from behind, or that reflects totally where o asks for
+// transmission, sends nothing.
+template <class S>
+bool rough_nee_weight(const Scene& sc, const Phys<S>& P, const Acq& q, int tri, const V3<S>& x, const V3<S>& w,
+                      const V3<S>& nin, int m1, int m2, const S& alpha, int e2, S& gain, S& dt,
+                      std::vector<std::pair<double, int>>& xs, double* frx_out) {
+  S xt(q.elem_x(e2));
+  elem_acq(xt, P.acq_base, q.elem_x(e2), q);
+  V3<S> dv = mk3<S>(xt + (-1.0 * x.x), -1.0 * x.y, -1.0 * x.z);
+  const S r2 = dot(dv, dv);
+  const V3<S> o = scale(dv, 1.0 / sqrt(r2));
+  const V3<S> i = scale(w, -1.0);
+  const S in = dot(i, nin), on = dot(o, nin);
+  const bool reflect = val(on) > 0.0;
+  const S c1 = P.c[m1], c2 = P.c[m2];
+  V3<S> h;
+  if (reflect) {
+    V3<S> hv = add(i, o);
+    h = scale(hv, 1.0 / sqrt(dot(hv, hv)));
+  } else {
+    V3<S> hv = scale(add(scale(i, 1.0 / c1), scale(o, 1.0 / c2)), -1.0);
+    h = scale(hv, 1.0 / sqrt(dot(hv, hv)));
+    if (val(dot(h, nin)) < 0.0) h = scale(h, -1.0);
+  }
+  const S ih = dot(i, h), oh = dot(o, h), nh = dot(nin, h);
+  if (!(val(ih) > 0.0) || !(val(nh) > 0.0)) return false;  // facet met from behind
+  if (!reflect && !(val(oh) < 0.0)) return false;
+  Iface<S> f = interface_event<S>(w, h, c1, c2, P.rho[m1], P.rho[m2]);
+  S C, J;
+  if (reflect) {
+    C = f.R;
+    J = 1.0 / (4.0 * ih);
+  } else {
+    if (f.tir) return false;
+    C = f.T;
+    J = refract_jacobian(ih, oh, c1, c2);
+  }
+  const S g = ggx_d(nh, alpha) * smith_g1(in, alpha) * smith_g1(on, alpha) * C * ih * J / in;
+  const S p_nee = 1.0 / ((double)q.ne * element_solid_angle(P, q, o, r2));
+  S trans, D;
+  V3<S> d;
+  if (!secondary_segment<S>(sc, P, q, x, tri, e2, reflect ? m1 : m2, trans, dt, d, D, xs, frx_out)) return false;
+  gain = q.rough_nee == 2 ? g * trans / p_nee : g * trans / (p_nee + bsdf_pdf(q, nh, alpha, J, f, reflect));
   return true;
 }
 
@@ -798,6 +918,11 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
   int m = 0;
   int xcls = CLS_NONE, xid = -1;
   std::vector<std::pair<double, int>> xs;
+  // the primary's direction density at its last rough event (0: the last event was not rough)
+  // and the distance travelled since, straight on through scatterer pass-throughs: a primary
+  // that reaches the array from there takes the balance weight against that event's secondary
+  // ray
+  S last_pdf(0.0), since(0.0);
   for (int k = 0; k <= q.kmax; ++k) {
     Hit h;
     if (!replay) {
@@ -855,6 +980,11 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
       S th = (cv == val(cosd)) ? acos(cosd) : S(std::acos(cv));
       S f = f_rx<S>(th, q.alpha_m, q.alpha_c);
       int e = replay ? rec_in[k].aux : h.id;
+      if (val(last_pdf) > 0.0) {  // balance weight against the last rough event's secondary ray
+        const S r = since + t;
+        const S p_nee = 1.0 / ((double)q.ne * element_solid_angle(P, q, w, r * r));
+        f = q.rough_nee == 2 ? S(0.0) : f * last_pdf / (last_pdf + p_nee);
+      }
       if (val(f) != 0.0) {
         Arrival<S> A;
         A.tx = io.tx;
@@ -883,6 +1013,24 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
       // the facet normal: the macro normal, or a GGX microfacet normal (roughness of the
       // medium the triangle bounds, its back side)
       const bool rough = !P.rough.empty() && val(P.rough[sc.mback[h.id]]) > 0.0;
+      if (rough && q.rough_nee) {  // secondary ray to a uniformly chosen element [Sec. 2.3.3]
+        const int e2 = replay ? rec_in[k].aux : std::min(q.ne - 1, (int)std::floor(u01(u.v[1]) * q.ne));
+        if (rec_out) rec_out[k].aux = e2;
+        if (!replay) cnt.nee++;
+        S gain, dt;
+        double frx;
+        if (rough_nee_weight<S>(sc, P, q, h.id, x, w, nn, m1, m2, P.rough[sc.mback[h.id]], e2, gain, dt, xs, &frx)) {
+          Arrival<S> A;
+          A.tx = io.tx;
+          A.e = e2;
+          A.kind = 1;
+          A.ev = k;
+          A.path = path;
+          A.tau = tau + dt;
+          A.a = a * gain;
+          arr.push_back(A);
+        }
+      }
       V3<S> hf = nn;
       if (rough) hf = ggx_normal<S>(nn, P.rough[sc.mback[h.id]], u01(u.v[2]), u01(u.v[3]));
       const V3<S> w_in = w;
@@ -920,11 +1068,20 @@ void trace_path(const Scene& sc, const Phys<S>& P, const Acq& q, uint32_t k0, ui
         const S inn = dot(w_in, nn), hn = dot(hf, nn), ih = dot(w_in, hf);
         const S alpha = P.rough[sc.mback[h.id]];
         a = a * (-1.0 * ih) * smith_g1(inn, alpha) * smith_g1(on, alpha) / ((-1.0 * inn) * hn);
+        if (q.rough_nee) {  // the density of the direction just sampled, for the balance weight
+          const S J = choice == CH_TRANSMIT ? refract_jacobian(-1.0 * ih, dot(w, hf), P.c[m1], P.c[m2])
+                                            : 1.0 / (4.0 * (-1.0 * ih));
+          last_pdf = bsdf_pdf(q, hn, alpha, J, f, choice != CH_TRANSMIT);
+          since = S(0.0);
+        }
+      } else {
+        last_pdf = S(0.0);
       }
       o = x;
       xcls = CLS_TRI;
       xid = h.id;
     } else {  // scatterer: secondary ray to a uniformly chosen element, Born pass-through
+      since = since + t;  // the ray goes on straight: still the last rough event's direction
       int e2 = replay ? rec_in[k].aux : std::min(q.ne - 1, (int)std::floor(u01(u.v[1]) * q.ne));
       if (rec_out) rec_out[k].aux = e2;
       if (!replay) cnt.nee++;
@@ -1615,6 +1772,47 @@ int ora_gradient_shape(void* scene, void* rp, const double* theta, uint64_t seed
                        int n_shape, const double* vtan, double* gtheta) {
   if (n_shape < 1) return -1;
   return gradient_impl(scene, rp, theta, seed, nthreads, grf, gtheta, false, n_shape, vtan);
+}
+
+// n injected paths (tests): origins o[3 n], unit directions w[3 n], weight 1, time 0, ray
+// index = path index.  Per element: the sum of what each path deposits there and the sum of
+// the squares of those per-path amounts (sum_e[n_elem], sq_e[n_elem], zeroed here).
+void ora_inject_sums(void* scene, const double* theta, int M, const double* acq, const double* angles, uint64_t seed,
+                     long long n, const double* o, const double* w, int nthreads, double* sum_e, double* sq_e) {
+  Acq q = make_acq(acq, angles);
+  const Scene& sc = *(Scene*)scene;
+  Phys<double> P = phys_double(theta, M, sc.rough);
+  const int nb = std::max(1, nthreads);
+  std::vector<std::vector<double>> s(nb, std::vector<double>(q.ne, 0.0)), s2(nb, std::vector<double>(q.ne, 0.0));
+  parallel_blocks(n, nthreads, [&](int b, long long lo, long long hi) {
+    std::vector<Arrival<double>> arr;
+    std::vector<double> per(q.ne);
+    Counters c;
+    for (long long i = lo; i < hi; ++i) {
+      PathIO io;
+      io.inject = true;
+      io.o0 = d3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
+      io.w0 = d3(w[3 * i], w[3 * i + 1], w[3 * i + 2]);
+      io.a0 = 1.0;
+      io.tau0 = 0.0;
+      io.ray = i;
+      arr.clear();
+      trace_path<double>(sc, P, q, (uint32_t)seed, (uint32_t)(seed >> 32), io, i, nullptr, nullptr, arr, c);
+      std::fill(per.begin(), per.end(), 0.0);
+      for (const auto& A : arr) per[A.e] += A.a;
+      for (int e = 0; e < q.ne; ++e) {
+        s[b][e] += per[e];
+        s2[b][e] += per[e] * per[e];
+      }
+    }
+  });
+  for (int e = 0; e < q.ne; ++e) {
+    sum_e[e] = sq_e[e] = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      sum_e[e] += s[b][e];
+      sq_e[e] += s2[b][e];
+    }
+  }
 }
 
 // single injected path (tests): emission state given, optional forced interface choices,

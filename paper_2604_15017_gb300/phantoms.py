@@ -138,12 +138,13 @@ def random_rotation(rng):
 # --------------------------------------------------------------------------------------------
 def acquisition(n_elem, pitch, n_samples, angles_deg, n_rays, k_max, c_bf, fs=40e6, bw=0.6, h_el=5 * MM,
                 alpha_m_deg=20.0, alpha_c_deg=45.0, split_mode=0, split_q=0.5, stream_id=0, tx_elem=-1,
-                n_tx_elem=0):
+                n_tx_elem=0, rough_nee=0):
     return dict(n_elem=int(n_elem), pitch=float(pitch), h_el=float(h_el), fs=float(fs),
                 n_samples=int(n_samples), k_max=int(k_max), n_rays=int(n_rays), bw=float(bw),
                 alpha_m=alpha_m_deg * DEG, alpha_c=alpha_c_deg * DEG, c_bf=float(c_bf),
                 split_mode=int(split_mode), split_q=float(split_q), stream_id=int(stream_id),
-                tx_elem=int(tx_elem), n_tx_elem=int(n_tx_elem), angles=[float(a) * DEG for a in angles_deg])
+                tx_elem=int(tx_elem), n_tx_elem=int(n_tx_elem), rough_nee=int(rough_nee),
+                angles=[float(a) * DEG for a in angles_deg])
 
 
 def image(n_lines, n_depth, x0, x1, z0, z1, dr_db=60.0, lambda1=0.0, lambda2=1.0, f_number=0.0):

@@ -71,3 +71,76 @@ def test_roughness_gradient_matches_finite_differences():
     tm[i] *= 1 - 1e-7
     fd = (np.sum(grf * O.forward(w, theta=tp)["rf"]) - np.sum(grf * O.forward(w, theta=tm)["rf"])) / (2e-7 * w["theta"][i])
     assert abs(fd - g[i]) <= 1e-4 * abs(g[i]), (fd, g[i])
+
+
+# ------------------------------------------------------------------------------------------
+# secondary rays at rough interface events (Sec. 2.3.3) combined with the primary by the
+# balance heuristic: the same expectation as the primary's own sampling alone
+# ------------------------------------------------------------------------------------------
+MM = 1e-3
+
+
+def per_element_sums(e, a, n_elem):
+    s = np.bincount(e, weights=a, minlength=n_elem)
+    v = np.bincount(e, weights=a * a, minlength=n_elem)  # variance of a sum of rare contributions
+    return s, v
+
+
+def rough_box(depth, alpha, c_in=2000.0):
+    tris = P.box_mesh((-60 * MM, -60 * MM, depth), (60 * MM, 60 * MM, depth + 40 * MM))
+    media = np.tile(np.array([[0, 1]], dtype=np.int32), (len(tris), 1))
+    sp, sa = P.empty_scatterers()
+    theta = np.concatenate([P.theta_vector([(1500.0, 1000.0, 0.0), (c_in, 1300.0, 0.0)]), [0.0, alpha]])
+    return O.Scene(tris, media, sp, sa, 0.1 * MM, rough=True), theta
+
+
+def compare_modes(sums):
+    """mode 0 (the primary's sampling alone) against mode 2 (the secondary ray alone: every
+    factor of the BSDF evaluation) and mode 1 (both, balance heuristic), per element.  The
+    secondary ray aims at the element's centre, a midpoint rule over the element's solid angle,
+    so the elements here are small next to the angular scale on which the BSDF varies."""
+    s0, v0 = sums[0]
+    for mode in (1, 2):
+        s1, v1 = sums[mode]
+        sig = np.sqrt(v0 + v1)
+        assert np.all(np.abs(s1 - s0) <= 4.5 * sig + 1e-12), (mode, np.c_[s0, s1, sig])
+        assert abs(s1.sum() - s0.sum()) <= 4 * np.sqrt(v0.sum() + v1.sum()), (mode, s0.sum(), s1.sum())
+        assert abs(s1.sum() / s0.sum() - 1.0) < 0.03, (mode, s0.sum(), s1.sum())
+    # the balance heuristic lowers the variance below the primary's alone
+    assert np.sqrt(sums[1][1].sum()) < np.sqrt(v0.sum())
+
+
+def injected(n_ray, z0, sx, seed=3):
+    rng = np.random.default_rng(seed)
+    o = np.stack([rng.uniform(-1.5, 1.5, n_ray) * MM, rng.uniform(-0.2, 0.2, n_ray) * MM, np.full(n_ray, z0)], 1)
+    w = np.stack([rng.normal(0, sx, n_ray), rng.normal(0, 0.05, n_ray), -np.ones(n_ray)], 1)
+    return o, w / np.linalg.norm(w, axis=1)[:, None]
+
+
+def test_rough_secondary_rays_reflection_keep_the_expectation():
+    """Rays injected above a rough interface at 6 mm (alpha 0.6, always reflected, facets that
+    reflect totally included): what reaches each element directly after the reflection, out to
+    elements seen at 65 deg from the interface normal (Smith masking of the outgoing side)."""
+    sc, theta = rough_box(6 * MM, 0.6)
+    o, w = injected(2_000_000, 2 * MM, 0.3)
+    w[:, 2] *= -1.0  # downward
+    sums = {}
+    for nee in (0, 1, 2):
+        acq = P.acquisition(128, 0.2 * MM, 4096, [0.0], 1, 1, 1500.0, h_el=0.4 * MM, alpha_m_deg=90.0,
+                            alpha_c_deg=90.0, split_mode=1, split_q=1.0, rough_nee=nee)
+        sums[nee] = O.inject_sums(sc, theta, 2, acq, o, w)
+    compare_modes(sums)
+
+
+def test_rough_secondary_rays_refraction_keep_the_expectation():
+    """Rays injected inside a slower medium toward its rough upper face at 10 mm (alpha 0.5,
+    always transmitted into the faster medium above, where the probe is): what reaches each
+    element directly after the refraction."""
+    sc, theta = rough_box(10 * MM, 0.5)
+    o, w = injected(1_000_000, 14 * MM, 0.2)
+    sums = {}
+    for nee in (0, 1, 2):
+        acq = P.acquisition(64, 0.2 * MM, 4096, [0.0], 1, 1, 1500.0, h_el=0.4 * MM, alpha_m_deg=90.0,
+                            alpha_c_deg=90.0, split_mode=1, split_q=0.0, rough_nee=nee)
+        sums[nee] = O.inject_sums(sc, theta, 2, acq, o, w)
+    compare_modes(sums)
