@@ -98,6 +98,10 @@ typedef struct {
                             its index (element x n_rays + ray) whatever the sub-aperture, so
                             disjoint sub-apertures with one seed partition the full aperture's
                             realisation exactly (micro-batches over elements) */
+  int32_t rough_nee;     /* != 0: secondary rays also at rough interface events (Sec. 2.3.3), the
+                            microfacet BSDF evaluated toward the element; they and the primary's
+                            own direct hits after such an event are combined by the balance
+                            heuristic of multiple importance sampling (scenes with rough != 0) */
 } us_acq_desc;
 
 /* Image grid, dynamic range and loss weights. */

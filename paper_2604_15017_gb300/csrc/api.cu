@@ -29,7 +29,8 @@ enum Slot {
   W_ROW_CNT, W_ROW_OFF, W_ROW_CUR, W_BUCKET, W_SCRATCH, W_GTAB, W_IRF, W_ENV, W_KEY, W_PART, W_SCAL, W_GI,
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
   W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS,
-  W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_QA_SURF, W_KEEP, W_COUNT
+  W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_QA_SURF, W_KEEP, W_NEE_JX, W_NEE_JW, W_JOBU_JX,
+  W_JOBU_JW, W_QA_MIS, W_QB_MIS, W_COUNT
 };
 
 struct SceneGPU {
@@ -301,6 +302,8 @@ int make_acq(us_ctx* ctx, const us_acq_desc* d, uint64_t seed, Acq& q) {
   q.tx_elem = d->tx_elem < 0 ? -1 : d->tx_elem;
   q.n_emit = q.tx_elem < 0 ? q.ne : std::max(1, d->n_tx_elem);
   q.split_mode = d->split_mode;
+  if (d->rough_nee != 0 && d->rough_nee != 1) return fail(ctx, US_ERR_ARG, "rough_nee takes 0 or 1");
+  q.rough_nee = d->rough_nee;
   q.pitch = d->pitch;
   q.hel = d->h_el;
   q.fs = d->fs;
@@ -398,6 +401,7 @@ int alloc_queues(us_ctx* ctx, long long n, cudaStream_t st, Queues& Q) {
   CKS(ws(ctx, W_QA_META, n, st, &Q.a.meta));
   CKS(ws(ctx, W_QA_SURF, n, st, &Q.a.surf));
   Q.b.surf = nullptr;  // the sorted queue's carried hits go straight into the hit array
+  Q.a.mis = Q.b.mis = nullptr;
   CKS(ws(ctx, W_QB_PA, n, st, &Q.b.pa));
   CKS(ws(ctx, W_QB_WT, n, st, &Q.b.wt));
   CKS(ws(ctx, W_QB_META, n, st, &Q.b.meta));
@@ -434,14 +438,31 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   CKS(ws(ctx, W_NEE_JOB, jobs, st, &A.nee.job));
   CKS(ws(ctx, W_NEE_JM, jobs, st, &A.nee.jm));
   CKS(ws(ctx, W_NEE_PATH, jobs, st, &A.nee.jpath));
+  // secondary rays start at scatterers and, with rough_nee, at rough interface events, whose
+  // jobs also keep the event point and the incident direction
+  const bool rough_jobs = q.rough_nee && sc->rough;
+  const bool any_jobs = sc->dev.n_scat > 0 || rough_jobs;
+  A.mis_on = rough_jobs;
+  A.nee.jx = A.nee.jw = nullptr;
+  if (rough_jobs) {
+    CKS(ws(ctx, W_NEE_JX, jobs, st, &A.nee.jx));
+    CKS(ws(ctx, W_NEE_JW, jobs, st, &A.nee.jw));
+    CKS(ws(ctx, W_QA_MIS, n, st, &Q.a.mis));
+    CKS(ws(ctx, W_QB_MIS, n, st, &Q.b.mis));
+  }
   NeeQ sorted = A.nee, unsorted;
-  const bool sort_jobs = sc->dev.n_scat > 0;
+  const bool sort_jobs = any_jobs;
   if (sort_jobs) {
     CKS(ws(ctx, W_JOBU_JOB, jobs, st, &unsorted.job));
     CKS(ws(ctx, W_JOBU_JM, jobs, st, &unsorted.jm));
     CKS(ws(ctx, W_JOBU_PATH, jobs, st, &unsorted.jpath));
+    unsorted.jx = unsorted.jw = nullptr;
+    if (rough_jobs) {
+      CKS(ws(ctx, W_JOBU_JX, jobs, st, &unsorted.jx));
+      CKS(ws(ctx, W_JOBU_JW, jobs, st, &unsorted.jw));
+    }
   }
-  if (record && do_nee && sc->dev.n_scat > 0) {
+  if (record && do_nee && any_jobs) {
     // secondary-ray results kept for the adjoint; crossings beyond the buffer are traced again
     CKS(ws(ctx, W_NEE_RES, jobs, st, &A.nres.res));
     CKS(ws(ctx, W_NEE_XO, jobs, st, &A.nres.xo));
@@ -459,7 +480,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   // secondary rays on the lane's second stream (US_OPT_NEE_STREAM): round k's kernel waits for
   // its sorted jobs (fork event k), and the call's stream waits for all of them at the end
   const int nee_pct = std::min(100, std::max(0, ctx->opts[US_OPT_NEE_STREAM]));
-  const bool side = do_nee && sc->dev.n_scat > 0 && nee_pct > 0;
+  const bool side = do_nee && any_jobs && nee_pct > 0;
   Lane* L = ctx->L;
   if (side) CKS(ensure_side(ctx, L));
   const int nee_grid = side ? std::max(ctx->num_sms, grid_of(ctx, ctx->nee_per_sm) * nee_pct / 100)
@@ -520,7 +541,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
       launch_job_sort(A, unsorted, sorted, js, grid_of(ctx, 2), ns);
     }
     A.nee = sorted;
-    if (do_nee && sc->dev.n_scat > 0) {
+    if (do_nee && any_jobs) {
       StageScope sc_(ctx, US_STAGE_NEE, 1, ns);
       launch_nee(A, nee_grid, ns);
     }
@@ -1150,6 +1171,8 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
   Acq q;
   CKS(make_media(ctx, theta, sc->n_media_hint, med, sc->rough));
   CKS(make_acq(ctx, acq, seed, q));
+  if (q.rough_nee && sc->rough)
+    return fail(ctx, US_ERR_ARG, "the adjoint of secondary rays at rough events is not available (rough_nee = 0)");
   SplatGeom g;
   AdjArgs A;
   std::memset(&A, 0, sizeof A);

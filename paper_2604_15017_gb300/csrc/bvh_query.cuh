@@ -221,15 +221,17 @@ struct XTrav {
   float tmax;
   int node, sp, n;
   bool overflow;
+  uint32_t skip;  // a triangle the segment starts on (not a crossing), or 0xFFFFFFFF
 };
 
-__device__ __forceinline__ void xtrav_init(float3 o, float3 d, float tmax, XTrav& T) {
+__device__ __forceinline__ void xtrav_init(float3 o, float3 d, float tmax, XTrav& T, uint32_t skip = 0xFFFFFFFFu) {
   T.r = ray_inv(o, d);
   T.tmax = tmax;
   T.node = 0;
   T.sp = 0;
   T.n = 0;
   T.overflow = false;
+  T.skip = skip;
 }
 
 __device__ __forceinline__ bool xtrav_step(const SceneDev& S, float3 o, float3 d, XTrav& T, int* stack, float* xt,
@@ -250,7 +252,7 @@ __device__ __forceinline__ bool xtrav_step(const SceneDev& S, float3 o, float3 d
         const float4 B = __ldg(&S.prims_t[3 * i + 1]);
         const float4 C = __ldg(&S.prims_t[3 * i + 2]);
         const float t = tri_test(o, d, xyz(A), xyz(B), xyz(C));
-        if (t > 0.0f && t < T.tmax) {
+        if (t > 0.0f && t < T.tmax && code_id(code) != T.skip) {
           if (T.n < MAX_XINGS) {
             xt[T.n] = t;
             xid[T.n] = code_id(code);

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long pat
     A.qout.wt[i] = make_float4(r * cp, r * sp, wz, tau0);
     A.qout.meta[i] = make_uint4((uint32_t)path, 0xFFFFFFFFu, 0u, __float_as_uint(0.0f));
     A.qout.surf[i] = make_float2(-1.0f, 0.0f);
+    if (A.mis_on) A.qout.mis[i] = make_float2(0.0f, 0.0f);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt->live[0] = n;
 }
@@ -280,6 +281,7 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
     }
     float4 pa = A.qin.pa[i];
     float4 wt = A.qin.wt[i];
+    float2 mis = A.mis_on ? A.qin.mis[i] : make_float2(0.0f, 0.0f);
     int m = (int)(meta.z & 0xFF);
     float tau_lo = __uint_as_float(meta.w);
     const float t = h.x;
@@ -293,7 +295,9 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
     path_tx_ray(q, path, tx, ray);
     if (cls == CLS_XDCR) {  // arrival at the receiving element (Sec. 2.3.4)
       if (rec) *rec = code;
-      const float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+      float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+      // straight on from a rough event: balance weight against that event's secondary ray
+      if (mis.x > 0.0f) frx *= rough_hit_weight(q, mis.x, mis.y + t, w);
       if (frx > 0.0f && A.arr) {
         const uint32_t tq = time_to_tq(tau_hi, tau_lo, q.fs);
         if (tq != 0xFFFFFFFFu) {
@@ -323,6 +327,16 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
       // triangle bounds, its back side)
       const float alpha = med.rough[mm >> 16];
       float3 fn = nin;
+      if (alpha > 0.0f && q.rough_nee) {  // secondary ray to a uniformly chosen element (Sec. 2.3.3)
+        const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
+        word |= (uint32_t)e2 << 24;
+        const uint32_t slot = A.cnt->nee_off[A.k] + append_slot(&A.cnt->nee[A.k]);
+        A.nee.job[slot] = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code) | NEE_ROUGH));
+        A.nee.jm[slot] = (uint32_t)m1 | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16) | ((uint32_t)A.k << 24);
+        A.nee.jpath[slot] = (uint32_t)path;
+        A.nee.jx[slot] = make_float4(x.x, x.y, x.z, 0.0f);
+        A.nee.jw[slot] = make_float4(w.x, w.y, w.z, 0.0f);
+      }
       if (alpha > 0.0f) {
         fn = ggx_sample(nin, alpha, u01(u.z), u01(u.w)).h;
         if (dot3(w, fn) >= 0.0f) {  // facet met from behind: the path ends here
@@ -367,8 +381,12 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
           continue;
         }
         a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
+        if (A.mis_on) mis = make_float2(rough_bsdf_pdf(q, med, w_in, w, fn, nin, m1, m2, alpha, f, choice == CH_TRANSMIT), 0.0f);
+      } else {
+        mis = make_float2(0.0f, 0.0f);
       }
     } else {  // scatterer: secondary ray to a uniformly chosen element; Born pass-through
+      mis.y += t;  // straight on: still the last rough event's direction
       const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
       word |= (uint32_t)e2 << 24;
       const uint32_t slot = A.cnt->nee_off[A.k] + append_slot(&A.cnt->nee[A.k]);
@@ -391,6 +409,7 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
     A.qout.wt[o] = make_float4(w.x, w.y, w.z, tau_hi);
     A.qout.meta[o] = make_uint4(meta.x, code, (uint32_t)m | ((uint32_t)(A.k + 1) << 8), __float_as_uint(tau_lo));
     A.qout.surf[o] = carry;
+    if (A.mis_on) A.qout.mis[o] = mis;
   }
 }
 
@@ -442,6 +461,8 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
   bool tracing = false;
   float3 p = f3(0.0f, 0.0f, 0.0f), d = p;
   float D = 0.0f, frx = 0.0f;
+  float jfac = 0.0f;  // a rough event's BSDF factor (its medium in m_start); unused at scatterers
+  int m_start = 0;
   XTrav T;
   xtrav_init(p, f3(0.0f, 0.0f, 1.0f), 0.0f, T);
   uint32_t pool = 0u, pool_end = 0u;  // warp-uniform
@@ -465,13 +486,26 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
       if (((idle >> lane) & 1u) && rank < take) {
         job = pool + rank;
         const uint32_t jm = A.nee.jm[off + job];
-        p = xyz(__ldg(&A.S.scat[__float_as_uint(A.nee.job[off + job].w)]));
+        const uint32_t jid = __float_as_uint(A.nee.job[off + job].w);
+        const bool rough = (jid & NEE_ROUGH) != 0u;
+        p = rough ? xyz(A.nee.jx[off + job]) : xyz(__ldg(&A.S.scat[jid]));
         frx = nee_setup(q, p, (int)((jm >> 8) & 0xFF), d, D);
+        m_start = (int)(jm & 0xFF);
+        if (rough && frx != 0.0f) {  // the microfacet BSDF toward the element
+          const uint32_t tri = jid & ~NEE_ROUGH;
+          const float4 nr = __ldg(&A.S.tri_nrm[tri]);
+          const uint32_t mm = __float_as_uint(nr.w);
+          const float3 wi = xyz(A.nee.jw[off + job]);
+          const bool front = dot3(wi, xyz(nr)) < 0.0f;
+          const float3 nin = front ? xyz(nr) : xyz(nr) * -1.0f;
+          const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+          if (!rough_nee_factor(q, med, wi, nin, m_start, m2, med.rough[mm >> 16], d, D * D, jfac, m_start)) frx = 0.0f;
+        }
         if (frx == 0.0f) {  // cut off: no contribution
           if (A.nres.res) A.nres.xo[off + job] = make_uint2(0u, NEE_NONE);
           job = 0xFFFFFFFFu;
         } else {
-          xtrav_init(p, d, D, T);
+          xtrav_init(p, d, D, T, rough ? (jid & ~NEE_ROUGH) : 0xFFFFFFFFu);
           tracing = true;
         }
       }
@@ -491,9 +525,10 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
     job = 0xFFFFFFFFu;
     const float4 jb = A.nee.job[i];
     const uint32_t jm = A.nee.jm[i];
-    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
+    const int e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
+    const uint32_t jid = __float_as_uint(jb.w);
     float th = jb.y, tl = jb.z;
-    const NeeOut r = nee_shade(A.S, med, q, d, D, frx, xtrav_finish(T, xt, xid), m, th, tl, xt, xid);
+    const NeeOut r = nee_shade(A.S, med, q, d, D, frx, xtrav_finish(T, xt, xid), m_start, th, tl, xt, xid);
     if (A.nres.res) nee_store(A, i, r, th, tl, xt, xid);
     if (r.overflow) {
       atomicOr(&A.cnt->status, ST_OVERFLOW);
@@ -503,7 +538,7 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
     if (!r.ok || !A.arr) continue;
     const uint32_t tq = time_to_tq(th, tl, q.fs);
     if (tq == 0xFFFFFFFFu) continue;
-    const float amp = jb.x * med.As * __ldg(&A.S.scat[__float_as_uint(jb.w)]).w * r.gain;
+    const float amp = jb.x * ((jid & NEE_ROUGH) ? jfac : med.As * __ldg(&A.S.scat[jid]).w) * r.gain;
     const uint32_t slot = append_slot(&A.cnt->n_arr);
     if (slot < A.arr_cap) A.arr[slot] = make_uint4((uint32_t)(tx * q.ne + e2), tq, __float_as_uint(amp), A.nee.jpath[i]);
   }
@@ -582,6 +617,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, Pat
       to.wt[o] = from.wt[i];
       to.meta[o] = from.meta[i];
       if (key[j] >= (uint32_t)RAY_KEY_BUCKETS) A.hits[o] = from.surf[i];  // the carried surface hit
+      if (A.mis_on) to.mis[o] = from.mis[i];
     }
     __syncthreads();
   }
@@ -592,8 +628,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, Pat
 // at once: those go to the last bucket so that they do not share warps with jobs that trace.
 // 1024 buckets: few enough that each sort chunk writes runs of several jobs per bucket
 __device__ __forceinline__ uint32_t job_key(const RaySort& rs, const SceneDev& S, const Acq& q, float4 job,
-                                            uint32_t jm) {
-  const float3 p = xyz(__ldg(&S.scat[__float_as_uint(job.w)]));
+                                            uint32_t jm, float4 jx) {
+  const uint32_t jid = __float_as_uint(job.w);
+  const float3 p = (jid & NEE_ROUGH) ? xyz(jx) : xyz(__ldg(&S.scat[jid]));
   const uint32_t e2 = (jm >> 8) & 0xFF;
   const float3 dv = f3(elem_x(q, (int)e2), 0.0f, 0.0f) - p;
   if (f_rx(-dv.z * rsqrtf(dot3(dv, dv)), q.alpha_m, q.alpha_c) == 0.0f) return JOB_BUCKETS - 1;
@@ -607,7 +644,9 @@ __global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, Ra
   __syncthreads();
   const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t key = job_key(rs, A.S, A.acq, from.job[off + i], from.jm[off + i]);
+    const float4 jb = from.job[off + i];
+    const uint32_t key = job_key(rs, A.S, A.acq, jb, from.jm[off + i],
+                                 (__float_as_uint(jb.w) & NEE_ROUGH) ? from.jx[off + i] : make_float4(0.f, 0.f, 0.f, 0.f));
     rs.key[i] = key;
     atomicAdd(&h[key], 1u);
   }
@@ -643,9 +682,14 @@ __global__ void __launch_bounds__(RS_THREADS) k_job_scatter(TransportArgs A, Nee
       if (key[j] == 0xFFFFFFFFu) continue;
       const uint32_t i = off + c0 + j * RS_THREADS + threadIdx.x;
       const uint32_t o = off + base[key[j]] + rank[j];
-      to.job[o] = from.job[i];
+      const float4 jb = from.job[i];
+      to.job[o] = jb;
       to.jm[o] = from.jm[i];
       to.jpath[o] = from.jpath[i];
+      if (__float_as_uint(jb.w) & NEE_ROUGH) {
+        to.jx[o] = from.jx[i];
+        to.jw[o] = from.jw[i];
+      }
     }
     __syncthreads();
   }

@@ -12,14 +12,20 @@ struct PathQ {
   uint4* meta;  // (path id, previous primitive code, medium | k << 8, bits(tau_lo))
   float2* surf; // the surface hit carried across a scatterer event: (distance from o, bits(code)),
                 // distance < 0 when there is none (the queue the interaction kernel appends to)
+  float2* mis;  // with secondary rays at rough events: the direction density of the path's last
+                // rough event (0: the last event was not rough) and the distance travelled since
 };
 
 // secondary-ray jobs queued by the interaction kernels; round k appends at nee_off[k], so the
 // buffer keeps every job of the pass (the adjoint replays them)
+// job id word: a scatterer's id, or a triangle's id | NEE_ROUGH for a rough interface event
+constexpr uint32_t NEE_ROUGH = 0x80000000u;
 struct NeeQ {
-  float4* job;      // (a, tau_hi, tau_lo, bits(scatterer id)) at the event
+  float4* job;      // (a, tau_hi, tau_lo, bits(job id word)) at the event
   uint32_t* jm;     // medium | element << 8 | tx << 16 | k << 24
   uint32_t* jpath;  // path id
+  float4* jx;       // rough interface events: (event point, 0)
+  float4* jw;       // rough interface events: (incident direction, 0)
 };
 
 // what the secondary-ray kernel found for each job, kept for the adjoint of a recorded pass so
@@ -61,6 +67,7 @@ struct TransportArgs {
   float2* hits;       // (t, bits(code)) per queue slot
   float2* keep;       // per queue slot: the surface hit a scatterer event replaced in hits
   const uint32_t* trav_n;  // rays of the sorted queue that need a surface query (the rest carry one)
+  bool mis_on;        // secondary rays at rough events (the queues' mis fields are live)
   NeeQ nee;
   NeeRes nres;        // null members unless the pass is recorded for the adjoint
   Arrival* arr;       // may be null (adjoint recompute: no arrivals)

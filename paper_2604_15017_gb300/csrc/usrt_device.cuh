@@ -63,6 +63,7 @@ __host__ __device__ __forceinline__ int n_theta(const Media& m) { return 3 * m.M
 
 struct Acq {
   int ne, ntx, ns, kmax, nr, n_emit, tx_elem, split_mode;
+  int rough_nee;  // secondary rays at rough interface events too
   float pitch, hel, fs, bw, alpha_m, alpha_c, cbf, split_q;
   uint32_t stream, key0, key1;
   long long rays_per_tx;
@@ -283,6 +284,88 @@ __device__ __forceinline__ float3 ggx_normal_adjoint(float3 n, const GgxSample& 
 __device__ __forceinline__ float smith_g1(float vn, float alpha) {
   const float c = fabsf(vn);
   return 2.0f * c / (c + sqrtf(fmaf(1.0f - alpha * alpha, c * c, alpha * alpha)));
+}
+
+// GGX distribution of microfacet normals, Eq. GGX_PDF
+__device__ __forceinline__ float ggx_d(float nh, float alpha) {
+  const float a2 = alpha * alpha;
+  const float k = fmaf(nh * nh, a2 - 1.0f, 1.0f);
+  return a2 / (PI_F * k * k);
+}
+
+// Secondary ray from a rough interface event (Sec. 2.3.3) toward unit direction o (distance^2
+// r2 to the element's centre): the microfacet BSDF's amplitude per solid angle toward o for the
+// incident direction w (i = -w; nin the macro normal on the incident side), with the half vector
+// of reflection (o on the incident side) or of refraction (Snell with sound speeds),
+// g = D(h) G1(i) G1(o) C(h) |i.h| |dh/do| / |i.n| (C the facet's pressure reflection or
+// transmission coefficient; |dh/do| = 1 / (4 |o.h|), or |o.h| / (c2^2 (i.h / c1 + o.h / c2)^2)),
+// combined with the primary's own direct hits by the balance heuristic: the ray carries
+// g / (p_nee + p_bsdf), p_nee = 1 / (N_e Omega) the density of a uniform element and direction
+// within it (Omega its face's solid angle), p_bsdf = D(h) (h.n) |dh/do| P(choice) the primary's.
+// Returns false when nothing is sent that way; else fac = that weight / N_e (the segment's
+// shading multiplies by N_e) and the medium the segment starts in.
+__device__ __forceinline__ bool rough_nee_factor(const Acq& q, const Media& med, float3 w, float3 nin, int m1, int m2,
+                                                 float alpha, float3 o, float r2, float& fac, int& m_start) {
+  const float3 i = w * -1.0f;
+  const float in = dot3(i, nin), on = dot3(o, nin);
+  const bool reflect = on > 0.0f;
+  const float c1 = med.c[m1], c2 = med.c[m2];
+  float3 h;
+  if (reflect) {
+    h = i + o;
+  } else {
+    h = (i * (1.0f / c1) + o * (1.0f / c2)) * -1.0f;
+  }
+  h = h * rsqrtf(dot3(h, h));
+  if (!reflect && dot3(h, nin) < 0.0f) h = h * -1.0f;
+  const float ih = dot3(i, h), oh = dot3(o, h), nh = dot3(nin, h);
+  if (!(ih > 0.0f) || !(nh > 0.0f) || (!reflect && !(oh < 0.0f))) return false;
+  const Iface f = iface(w, h, c1, c2, med.rho[m1], med.rho[m2]);
+  float C, J;
+  if (reflect) {
+    C = f.R;
+    J = 1.0f / (4.0f * ih);
+  } else {
+    if (f.tir) return false;
+    C = f.T;
+    const float den = ih / c1 + oh / c2;
+    J = -oh / (c2 * c2 * den * den);
+  }
+  const float D = ggx_d(nh, alpha);
+  const float g = D * smith_g1(in, alpha) * smith_g1(on, alpha) * C * ih * J / in;
+  const float omega = q.pitch * q.hel * fabsf(o.z) / r2;
+  const float p_nee = 1.0f / ((float)q.ne * omega);
+  const float pr = f.tir ? 1.0f : (q.split_mode == 0 ? f.R * f.R : q.split_q);
+  const float p_bsdf = D * nh * J * (reflect ? pr : 1.0f - pr);
+  fac = g / ((float)q.ne * (p_nee + p_bsdf));
+  m_start = reflect ? m1 : m2;
+  return true;
+}
+
+// the primary's direction density at a rough event for its sampled facet fn and choice:
+// D(h) (h.n) |dh/dw'| P(choice), w_in the incident and w_out the outgoing direction
+__device__ __forceinline__ float rough_bsdf_pdf(const Acq& q, const Media& med, float3 w_in, float3 w_out, float3 fn,
+                                                float3 nin, int m1, int m2, float alpha, const Iface& f,
+                                                bool transmit) {
+  const float ih = -dot3(w_in, fn), nh = dot3(fn, nin);
+  float J;
+  if (transmit) {
+    const float oh = dot3(w_out, fn), c1 = med.c[m1], c2 = med.c[m2];
+    const float den = ih / c1 + oh / c2;
+    J = -oh / (c2 * c2 * den * den);
+  } else {
+    J = 1.0f / (4.0f * ih);
+  }
+  const float pr = f.tir ? 1.0f : (q.split_mode == 0 ? f.R * f.R : q.split_q);
+  return ggx_d(nh, alpha) * nh * J * (transmit ? 1.0f - pr : pr);
+}
+
+// balance weight of a primary's direct hit on the array after a rough event: its direction
+// density pdf there, against the secondary ray's 1 / (N_e Omega) for the element face seen from
+// distance r along w
+__device__ __forceinline__ float rough_hit_weight(const Acq& q, float pdf, float r, float3 w) {
+  const float p_nee = r * r / ((float)q.ne * q.pitch * q.hel * fabsf(w.z));
+  return pdf / (pdf + p_nee);
 }
 
 }  // namespace usrt

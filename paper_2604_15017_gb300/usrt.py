@@ -51,7 +51,8 @@ class AcqDesc(C.Structure):
                 ("angles", C.POINTER(C.c_float)), ("fs", C.c_float), ("n_samples", C.c_int32),
                 ("k_max", C.c_int32), ("n_rays", C.c_int32), ("bw", C.c_float), ("alpha_m", C.c_float),
                 ("alpha_c", C.c_float), ("c_bf", C.c_float), ("split_mode", C.c_int32), ("split_q", C.c_float),
-                ("stream_id", C.c_uint32), ("tx_elem", C.c_int32), ("n_tx_elem", C.c_int32)]
+                ("stream_id", C.c_uint32), ("tx_elem", C.c_int32), ("n_tx_elem", C.c_int32),
+                ("rough_nee", C.c_int32)]
 
 
 class ImgDesc(C.Structure):
@@ -166,7 +167,7 @@ def acq_desc(acq):
                 int(acq["k_max"]), int(acq["n_rays"]), float(acq["bw"]), float(acq["alpha_m"]),
                 float(acq["alpha_c"]), float(acq["c_bf"]), int(acq.get("split_mode", 0)),
                 float(acq.get("split_q", 0.5)), int(acq.get("stream_id", 0)) & 0xFFFFFFFF,
-                int(acq.get("tx_elem", -1)), int(acq.get("n_tx_elem", 0)))
+                int(acq.get("tx_elem", -1)), int(acq.get("n_tx_elem", 0)), int(acq.get("rough_nee", 0)))
     return d, ang
 
 

@@ -39,11 +39,15 @@ def rel_l2(a, b):
 
 
 def agreement(rec, ora):
+    """Share of paths with identical events: primitive, class, choice, and the element of the
+    secondary ray of every event that has one (scatterers; rough interfaces with rough_nee)."""
     r = rec.astype(np.int64) & 0xFFFFFFFF
-    cls, pid, ch = (r >> 20) & 3, r & 0xFFFFF, (r >> 22) & 3
+    cls, pid, ch, aux = (r >> 20) & 3, r & 0xFFFFF, (r >> 22) & 3, (r >> 24) & 0xFF
     same = (cls == ora["cls"]) & ((pid == ora["id"]) | (ora["cls"] == 0))
     tri = ora["cls"] == O.CLS_TRI
     same &= ~tri | (ch == ora["choice"]) | (ora["choice"] == O.CH_NONE)
+    with_nee = (ora["cls"] >= O.CLS_TRI) & (ora["aux"] >= 0)
+    same &= ~with_nee | (aux == ora["aux"])
     return same.all(axis=1).mean()
 
 
@@ -74,6 +78,37 @@ def test_rough_forward_matches_oracle(ctx, make):
     sid, rf, b, ref, rec = run_pair(ctx, w)
     assert agreement(rec, ref["run"].records()) >= 0.999
     assert rel_l2(rf.double().cpu().numpy(), ref["rf"]) <= 1e-3, rel_l2(rf.double().cpu().numpy(), ref["rf"])
+    ctx.release_scene(sid)
+
+
+def with_rough_nee(w):
+    w = dict(w)
+    w["acq"] = dict(w["acq"], rough_nee=1)
+    return w
+
+
+@pytest.mark.parametrize("make", ["slab", "inclusions", "cylinder"])
+def test_rough_secondary_rays_forward_matches_oracle(ctx, make):
+    """Secondary rays at rough interface events (Sec. 2.3.3) with the balance weights against
+    the primary's direct hits: the same events (secondary-ray elements included) and RF."""
+    if make == "slab":
+        w = P.with_roughness(P.slab_scatterers(n_rays=800), [0.0, 0.25])
+    elif make == "inclusions":
+        w = rough_inclusions()
+    else:
+        w = P.with_roughness(P.hollow_cylinder(n_rays=400), [0.0, 0.2, 0.0])
+    w = with_rough_nee(w)
+    sid, rf, b, ref, rec = run_pair(ctx, w)
+    assert agreement(rec, ref["run"].records()) >= 0.999
+    arr = ref["run"].arrivals()
+    recs = ref["run"].records()
+    rough_ev = (recs["cls"] == O.CLS_TRI) & (recs["aux"] >= 0)
+    assert rough_ev.any()  # the scene has rough events with secondary rays
+    err = rel_l2(rf.double().cpu().numpy(), ref["rf"])
+    assert err <= 1e-3, err
+    st = ctx.stats()
+    c = ref["run"].counters()
+    assert abs(st["nee_queries"] - c["nee"]) <= 2e-3 * c["nee"]
     ctx.release_scene(sid)
 
 
