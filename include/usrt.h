@@ -232,7 +232,8 @@ int us_philox_fill(us_ctx* ctx, uint32_t c0_base, uint32_t c1, uint32_t c2, uint
 /* ---------------------------------------------------------------------------------------- */
 
 /* Full forward pass (Sec. 2.3; Eq. das): emission, wavefront transport (closest hits,
- * Fresnel/Snell interfaces, attenuation, receiver-guided secondary rays at scatterers), sort-
+ * Fresnel/Snell interfaces, attenuation, receiver-guided secondary rays at scatterers and, with
+ * acq->rough_nee, at rough interface events), sort-
  * based pulse splat -> rf_dev, DAS -> envelope -> log compression -> bmode_dev (dB, in
  * [-dr_db, 0]).  bmode_dev may be NULL (channel data only); img may then be NULL.
  * keep_record != 0 keeps the per-path event record on the context for us_adjoint in record

@@ -122,6 +122,7 @@ __host__ __device__ constexpr int adj_row_stride(int P) { return P | 1; }
 // Options compiled in, so that the plain adjoint carries none of their code: bit 0 = the
 // acquisition slots (acq_slot), bit 1 = the vertex gradient (g_tris).
 constexpr int ADJ_ACQ = 1, ADJ_SHAPE = 2, ADJ_ROUGH = 4;  // bit 2: a rough scene (GGX events)
+constexpr int ADJ_RNEE = 8;  // bit 3: secondary rays at rough events (and the balance weights)
 
 // d log G1 / d(v.n) and d log G1 / d alpha of the Smith masking G1 of GGX (see smith_g1)
 __device__ __forceinline__ void g1_log_grad(float vn, float alpha, float& d_vn, float& d_alpha) {
@@ -171,6 +172,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
     int m = 0, m_last = 0;
     int nseg = 0;
     float gxa = 0.0f, gxt = 0.0f;
+    // secondary rays at rough events: the direction density of the last rough event and the
+    // distance since (the balance weight of a direct hit on the array), as in the forward pass
+    float mis_pdf = 0.0f, mis_since = 0.0f, hit_pdf = 0.0f, hit_since = 0.0f;
     const uint32_t* rec = A.record + (size_t)i * K1;
     // ---- forward replay ----
     for (int k = 0; k <= q.kmax; ++k) {
@@ -187,7 +191,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       ff_add(th, tl, t / med.c[m]);
       const float3 x = o + w * t;
       if (cls == CLS_XDCR) {
-        const float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+        float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+        if ((OPT & ADJ_RNEE) && mis_pdf > 0.0f) {
+          hit_pdf = mis_pdf;
+          hit_since = mis_since;
+          frx *= rough_hit_weight(q, mis_pdf, mis_since + t, w);
+        }
         if (frx > 0.0f) {
           float ga, gt, gf;
           splat_adj_gather(A.grf + ((size_t)tx * q.ne + id) * q.ns, th, tl, a1 * frx, A.pulse, ga, gt, gf);
@@ -236,9 +245,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {  // microfacet weight (a killed event has no successor)
           const float inn = dot3(w_in, nin), on = dot3(w, nin);
           a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
+          if (OPT & ADJ_RNEE) {
+            const bool transmit = !(choice == CH_TIR || f.tir || choice == CH_REFLECT);
+            mis_pdf = rough_bsdf_pdf(q, med, w_in, w, fn, nin, m1, m2, alpha, f, transmit);
+            mis_since = 0.0f;
+          }
+        } else {
+          mis_pdf = 0.0f;
         }
       } else {  // scatterer: Born pass-through (amplitude after the segment, direction unchanged)
         a = a1;
+        mis_since += t;
       }
       o = x;
     }
@@ -246,6 +263,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
     float ab = 0.0f, tb = 0.0f;
     float3 ob = f3(0.f, 0.f, 0.f), wb = f3(0.f, 0.f, 0.f);
     int m_next = m_last;  // medium of segment k + 1 (of the last segment to start with)
+    // the balance weight's adjoints on their way back to the rough event they came from: that of
+    // its direction density, and that of the distance travelled since (every segment after it)
+    float g_pdf = 0.0f, g_since = 0.0f;
     for (int k = nseg - 1; k >= 0; --k) {
       const float3 ok = O[k], wk = W[k];
       const float ak = Aa[k];
@@ -266,17 +286,33 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       float a1b, t1b;
       float3 xb, wpb;
       float3 nhb = f3(0.f, 0.f, 0.f);  // shape adjoint: dL/d(unit normal) of a hit triangle
+      float t_extra = 0.0f;  // further adjoint of this segment's length (the balance weight's)
       if (cls == CLS_XDCR) {
         const float cosd = -wk.z;
         const float frx = f_rx(cosd, q.alpha_m, q.alpha_c);
-        a1b = gxa * frx;
+        float wm = 1.0f;
+        if ((OPT & ADJ_RNEE) && hit_pdf > 0.0f) wm = rough_hit_weight(q, hit_pdf, hit_since + t, wk);
+        a1b = gxa * frx * wm;
         t1b = gxt;
         xb = f3(0.f, 0.f, 0.f);
         wpb = f3(0.f, 0.f, 0.f);
         const float thd = acosf(fminf(1.0f, fmaxf(-1.0f, cosd)));
         if (thd > q.alpha_m && thd <= q.alpha_c && frx > 0.0f) {
           const float s = sqrtf(fmaxf(1e-30f, 1.0f - wk.z * wk.z));
-          wpb.z = gxa * a1 * (-1.0f / ((q.alpha_c - q.alpha_m) * s));
+          wpb.z = gxa * a1 * wm * (-1.0f / ((q.alpha_c - q.alpha_m) * s));
+        }
+        if ((OPT & ADJ_RNEE) && hit_pdf > 0.0f && frx > 0.0f) {
+          // wm = pdf / (pdf + pn), pn = r^2 / (N_e pitch h_el |w.z|), r = since + t
+          const float r = hit_since + t;
+          const float pn = r * r / ((float)q.ne * q.pitch * q.hel * fabsf(wk.z));
+          const float sden = hit_pdf + pn;
+          const float gw = gxa * a1 * frx;
+          g_pdf = gw * pn / (sden * sden);
+          const float gpn = -gw * hit_pdf / (sden * sden);
+          g_since = gpn * 2.0f * pn / r;
+          t_extra = g_since;
+          wpb.z += gpn * (-pn / wk.z);
+          if (OPT & ADJ_ACQ) ADD(acc[A.acq_slot + 1], gpn * (-pn / q.pitch));
         }
       } else if (cls == CLS_TRI) {
         const float4 nr = __ldg(&A.S.tri_nrm[id]);
@@ -307,6 +343,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         // w, h and alpha
         float abx = ab, ihb = 0.0f, inb = 0.0f, hnb = 0.0f, alb = 0.0f, onb = 0.0f;
         float3 wbx = wb, wo = wb;
+        float Rb_pdf = 0.0f;                      // the balance weight's density through P(choice)
+        float3 hb_pdf = f3(0.f, 0.f, 0.f);        // ... and through o.h (refraction), into the facet
         if ((OPT & ADJ_ROUGH) && alpha > 0.0f) {
           wo = refl ? wk + fn * (2.0f * f.ci) : wk * f.r + fn * (f.r * f.ci - f.ct);
           const float ih = dot3(wk, fn), inn = dot3(wk, nin), on = dot3(wo, nin), hn = dot3(fn, nin);
@@ -326,6 +364,30 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
             alb = Wl * (gi_a + go_a);
             onb = Wl * go_n;
             wbx = wb + nin * onb;
+            if ((OPT & ADJ_RNEE) && g_pdf != 0.0f) {
+              // the direction density D(h) (h.n) J P(choice) of this event's sampled direction,
+              // whose balance weight a later direct hit on the array took
+              const bool transmit = !refl;
+              const float pdf = rough_bsdf_pdf(q, med, wk, wo, fn, nin, m1, m2, alpha, f, transmit);
+              const float gl = g_pdf * pdf;  // adjoint of log pdf
+              const float a2 = alpha * alpha, kk = fmaf(hn * hn, a2 - 1.0f, 1.0f);
+              hnb += gl * (-4.0f * hn * (a2 - 1.0f) / kk + 1.0f / hn);
+              alb += gl * (2.0f / alpha - 4.0f * alpha * hn * hn / kk);
+              if (!transmit) {
+                ihb += gl * (-1.0f / ih);  // J = 1 / (4 (-w.h))
+              } else {  // J = -o.h / (c2^2 den^2), den = (-w.h) / c1 + o.h / c2
+                const float ihp = -ih, oh = dot3(wo, fn), c1v = med.c[m1], c2v = med.c[m2];
+                const float den = ihp / c1v + oh / c2v;
+                ihb += gl * (2.0f / (c1v * den));
+                const float goh = gl * (1.0f / oh - 2.0f / (c2v * den));
+                wbx = wbx + fn * goh;
+                hb_pdf = wo * goh;
+                ADD(acc[3 * m1 + 0], gl * 2.0f * ihp / (c1v * c1v * den));
+                ADD(acc[3 * m2 + 0], gl * (-2.0f / c2v + 2.0f * oh / (c2v * c2v * den)));
+              }
+              if (q.split_mode == 0 && !(choice == CH_TIR || f.tir))
+                Rb_pdf = gl * (transmit ? -2.0f * f.R / (1.0f - f.R * f.R) : 2.0f / f.R);
+            }
           }
         }
         t1b = tb;
@@ -360,6 +422,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           cib += f.r * wn;
           ctb -= wn;
         }
+        Rb += Rb_pdf;
         if (!f.tir && choice != CH_TIR) {
           const float Av = r2 * c2 * f.ci, Bv = r1 * c1 * f.ct;
           const float den = Av + Bv;
@@ -389,7 +452,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           // h = cos(theta) n + sin(theta) b with tan(theta) = alpha s: dh/dalpha = s cos^3 (b - tan n)
           rough_ev = true;
           wpb = wpb + fn * ihb + nin * inb;
-          hb = wk * (ihb - cib) + wbx * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct) + nin * hnb;
+          hb = wk * (ihb - cib) + wbx * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct) + nin * hnb + hb_pdf;
           const float tn = alpha * gs.s, ct = rsqrtf(1.0f + tn * tn);
           alb += dot3(hb, (gs.b - nin * tn) * (gs.s * ct * ct * ct));
           ADD(acc[3 * med.M + 2 + (int)(mm >> 16)], alb);
@@ -402,15 +465,26 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
             nb = wk * (-cib) + wb * (refl ? 2.0f * f.ci : f.r * f.ci - f.ct);
           nhb = front ? nb : nb * -1.0f;
         }
+        if ((OPT & ADJ_RNEE) && alpha > 0.0f && k < q.kmax) {  // this rough event's secondary ray
+          const size_t si = (size_t)i * K1 + k;
+          const float2 sd = A.seeds[si];
+          a1b += sd.x;
+          t1b += sd.y;
+          xb = xb + xyz(A.seedv[2 * si]);
+          wpb = wpb + xyz(A.seedv[2 * si + 1]);
+        }
+        g_pdf = 0.0f;  // a triangle event ends the straight run a balance weight belongs to
+        g_since = 0.0f;
       } else {  // scatterer
         const float2 sd = A.seeds[(size_t)i * K1 + k];  // the secondary ray's adjoint seeds
         a1b = ab + sd.x;
         t1b = tb + sd.y;
         xb = ob;
         wpb = wb;
+        if (OPT & ADJ_RNEE) t_extra = g_since;  // a segment after the rough event
       }
       // segment x = o + w t, a1 = a att(t), tau1 = tau + t / c
-      float ttb = dot3(xb, wk);
+      float ttb = dot3(xb, wk) + t_extra;
       float3 obn = xb;
       float3 wbn = wpb + xb * t;
       const float attb = a1b * ak;
@@ -473,7 +547,15 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
 // The rows hold only the slots a secondary ray touches (nee_row_len): the 3M + 2 material
 // parameters and, with the acquisition option, the pitch at 3M + 2; no roughness slots (the
 // crossings are smooth), so a rough scene costs no more shared memory (and L1) than a smooth one.
-__host__ __device__ inline int nee_row_len(int M, bool acq) { return 3 * M + 2 + (acq ? 1 : 0); }
+// With secondary rays at rough events the rows also hold the M roughness slots (3M + 2 ..
+// 4M + 1), and the pitch follows them.
+__host__ __device__ inline int nee_row_len(int M, bool acq, bool rnee = false) {
+  return 3 * M + 2 + (rnee ? M : 0) + (acq ? 1 : 0);
+}
+
+// local derivatives of a rough event's secondary-ray BSDF factor: dual slots of its inputs
+constexpr int RN_C1 = 0, RN_C2 = 1, RN_R1 = 2, RN_R2 = 3, RN_AL = 4, RN_W = 5, RN_N = 8, RN_O = 11, RN_D2 = 14,
+              RN_P = 15, RN_SLOTS = 16;
 
 template <int OPT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
@@ -481,7 +563,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
   const Acq& q = A.acq;
   const Media& med = A.med;
   const int P = A.P;
-  const int R = nee_row_len(med.M, (OPT & ADJ_ACQ) != 0);
+  constexpr bool rnee = (OPT & ADJ_RNEE) != 0;
+  const int R = nee_row_len(med.M, (OPT & ADJ_ACQ) != 0, rnee);
+  const int iPitch = 3 * med.M + 2 + (rnee ? med.M : 0);  // the pitch's row slot (acquisition option)
   const int PS = adj_row_stride(R);
   float* acc = gsm + threadIdx.x * PS;
   const int iAs = 3 * med.M, iF0 = 3 * med.M + 1;
@@ -496,19 +580,50 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     const float4 job = A.nee.job[i];
     const uint32_t jm = A.nee.jm[i];
     const uint32_t jid = __float_as_uint(job.w);
-    const int m = (int)(jm & 0xFF), e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
+    int m = (int)(jm & 0xFF);
+    const int e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
     const int k = (int)(jm >> 24);
     const long long path = A.nee.jpath[i];
     float2* seed = &A.seeds[(size_t)(path - A.path_base) * K1 + k];
     const float a1 = job.x;
     float nh = job.y, nl = job.z;
-    const float4 sc = __ldg(&A.S.scat[jid]);
+    // the ray's start: a scatterer's centre, or (rough events) the event point on triangle tri
+    const bool rough_job = rnee && (jid & NEE_ROUGH) != 0u;
+    const uint32_t tri = jid & ~NEE_ROUGH;
+    float4 sc = make_float4(0.f, 0.f, 0.f, 0.f);
+    float3 p0, wi = f3(0.f, 0.f, 0.f), nin = wi, nn = wi;
+    int m2 = m;
+    bool front = true;
+    if (rough_job) {
+      p0 = xyz(A.nee.jx[i]);
+      wi = xyz(A.nee.jw[i]);
+      const float4 nr = __ldg(&A.S.tri_nrm[tri]);
+      const uint32_t mm = __float_as_uint(nr.w);
+      nn = xyz(nr);
+      front = dot3(wi, nn) < 0.0f;
+      nin = front ? nn : nn * -1.0f;
+      m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+      const float3 dv0 = f3(elem_x(q, e2), 0.0f, 0.0f) - p0;
+      const float r2v = dot3(dv0, dv0);
+      float fac0;
+      int ms;
+      if (!rough_nee_factor(q, med, wi, nin, m, m2, med.rough[mm >> 16], dv0 * rsqrtf(r2v), r2v, fac0, ms)) {
+        *seed = make_float2(0.0f, 0.0f);
+        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      m = ms;  // the medium the segment starts in
+    } else {
+      sc = __ldg(&A.S.scat[jid]);
+      p0 = xyz(sc);
+    }
     float3 d;
     float D;
     NeeOut no;
     const uint2 xo = A.nres.xo ? A.nres.xo[i] : make_uint2(0u, NEE_UNSTORED);
     if (xo.y == NEE_UNSTORED) {  // trace the secondary ray again
-      no = nee_eval(A.S, med, q, xyz(sc), e2, m, nh, nl, xt, xid, &d, &D);
+      no = nee_eval(A.S, med, q, p0, e2, m, nh, nl, xt, xid, &d, &D, rough_job ? tri : 0xFFFFFFFFu);
     } else {  // the forward pass's result: same arithmetic, read back
       no.ok = xo.y != NEE_NONE;
       no.overflow = false;
@@ -524,25 +639,74 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
           xt[c] = __uint_as_float(x.x);
           xid[c] = x.y;
         }
-        const float3 dv = f3(elem_x(q, e2), 0.0f, 0.0f) - xyz(sc);
+        const float3 dv = f3(elem_x(q, e2), 0.0f, 0.0f) - p0;
         D = sqrtf(dot3(dv, dv));
         d = dv * (1.0f / D);
       }
     }
     if (!no.ok) {
       *seed = make_float2(0.0f, 0.0f);
+      if (rough_job) {
+        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
       continue;
     }
-    const float k_n = med.As * sc.w * no.gain;
+    // a rough event's BSDF factor with its derivatives in its 16 local inputs
+    DualN<RN_SLOTS> fd(0.0f);
+    if (rough_job) {
+      const uint32_t mm = __float_as_uint(__ldg(&A.S.tri_nrm[tri]).w);
+      const int m1 = (int)(jm & 0xFF);
+      typedef DualN<RN_SLOTS> DT;
+      const V3<DT> wv = v3(dual_var<RN_SLOTS>(wi.x, RN_W), dual_var<RN_SLOTS>(wi.y, RN_W + 1),
+                           dual_var<RN_SLOTS>(wi.z, RN_W + 2));
+      const V3<DT> nv = v3(dual_var<RN_SLOTS>(nin.x, RN_N), dual_var<RN_SLOTS>(nin.y, RN_N + 1),
+                           dual_var<RN_SLOTS>(nin.z, RN_N + 2));
+      const V3<DT> ov = v3(dual_var<RN_SLOTS>(d.x, RN_O), dual_var<RN_SLOTS>(d.y, RN_O + 1),
+                           dual_var<RN_SLOTS>(d.z, RN_O + 2));
+      bool refl;
+      rough_nee_factor_t<DT>(q, dual_var<RN_SLOTS>(med.c[m1], RN_C1), dual_var<RN_SLOTS>(med.c[m2], RN_C2),
+                             dual_var<RN_SLOTS>(med.rho[m1], RN_R1), dual_var<RN_SLOTS>(med.rho[m2], RN_R2),
+                             dual_var<RN_SLOTS>(med.rough[mm >> 16], RN_AL), wv, nv, ov,
+                             dual_var<RN_SLOTS>(D * D, RN_D2), dual_var<RN_SLOTS>(q.pitch, RN_P), fd, refl);
+    }
+    const float k_n = (rough_job ? fd.v : med.As * sc.w) * no.gain;
     const float a_n = a1 * k_n;
     float ga, gt, gf;
     splat_adj_gather(A.grf + ((size_t)tx * q.ne + e2) * q.ns, nh, nl, a_n, A.pulse, ga, gt, gf);
     const float Ga = ga * a_n;  // adjoint of log a_n
     ADD(acc[iF0], gf + Ga * (-kap * no.sum_al));
-    ADD(acc[iAs], ga * a1 * sc.w * no.gain);
+    if (!rough_job) ADD(acc[iAs], ga * a1 * sc.w * no.gain);
+    // rough events: the segment's direction d, length D and start point p0 take adjoints too
+    float3 gd = f3(0.f, 0.f, 0.f), gP0 = gd;
+    float gD = 0.0f;
+    if (rough_job) {
+      const float Gf = Ga / fd.v;  // adjoint of the factor (log)
+      const uint32_t mm = __float_as_uint(__ldg(&A.S.tri_nrm[tri]).w);
+      const int m1 = (int)(jm & 0xFF);
+      ADD(acc[3 * m1 + 0], Gf * fd.d[RN_C1]);
+      ADD(acc[3 * m2 + 0], Gf * fd.d[RN_C2]);
+      ADD(acc[3 * m1 + 1], Gf * fd.d[RN_R1]);
+      ADD(acc[3 * m2 + 1], Gf * fd.d[RN_R2]);
+      ADD(acc[3 * med.M + 2 + (int)(mm >> 16)], Gf * fd.d[RN_AL]);
+      gd = f3(Gf * fd.d[RN_O], Gf * fd.d[RN_O + 1], Gf * fd.d[RN_O + 2]);
+      gD = Gf * fd.d[RN_D2] * 2.0f * D;
+      if (OPT & ADJ_ACQ) ADD(acc[iPitch], Gf * fd.d[RN_P]);
+      if (OPT & ADJ_SHAPE) {  // the macro normal of the event's triangle
+        const float3 gn = f3(Gf * fd.d[RN_N], Gf * fd.d[RN_N + 1], Gf * fd.d[RN_N + 2]);
+        tri_shape_add(A.S, tri, nn, front ? gn : gn * -1.0f, f3(0.f, 0.f, 0.f), A.g_tris);
+      }
+      // receive directivity f_rx(-d.z) on its ramp
+      const float frx = f_rx(-d.z, q.alpha_m, q.alpha_c);
+      const float thd = acosf(fminf(1.0f, fmaxf(-1.0f, -d.z)));
+      if (thd > q.alpha_m && frx > 0.0f)
+        gd.z += Ga * (-1.0f / ((q.alpha_c - q.alpha_m) * frx * sqrtf(fmaxf(1e-30f, 1.0f - d.z * d.z))));
+    }
     // pitch: the target x_e = p (e2 - (N_e - 1)/2) moves along x; dX below are derivatives in x_e
     // (direction dd = (e_x - d d.x) / D, crossing distances t_c = A_c / (d.n_c), lengths, cosines)
-    constexpr bool acq = (OPT & ADJ_ACQ) != 0;
+    // the pitch moves the target x_e (scatterers: dX below; rough events: the general endpoint
+    // adjoints gd, gD, gP0 above, converted after the loop)
+    const bool acq = (OPT & ADJ_ACQ) != 0 && !rough_job;
     float gX = 0.0f, dt_prev = 0.0f;
     if (acq) {  // receive directivity: d log f_rx / dX on its ramp
       const float frx = f_rx(-d.z, q.alpha_m, q.alpha_c);
@@ -559,6 +723,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       const float l = tc - tprev;
       ADD(acc[3 * mm_cur + 2], Ga * (-kap * med.f0 * l));
       ADD(acc[3 * mm_cur + 0], gt * (-l / (med.c[mm_cur] * med.c[mm_cur])));
+      if (rough_job && c == no.n) gD += Ga * (-kap * med.f0 * med.al[mm_cur]) + gt / med.c[mm_cur];
       if (acq) {
         float dtc = d.x;  // dD/dX
         if (c < no.n) {
@@ -600,13 +765,22 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
         const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
         gX += (Ab * r2 * c2 + Bb * r1 * c1 * dct) * dci;
       }
+      if (rough_job) {  // t_c = (v0 - p0).n / (d.n) and the incidence cosine |d.n|
+        const float3 n = xyz(nr);
+        const float tcb = (Ga * (-kap * med.f0 * med.al[mm_cur]) + gt / med.c[mm_cur]) -
+                          (Ga * (-kap * med.f0 * med.al[m2]) + gt / med.c[m2]);  // dL/dt_c
+        const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
+        const float cib = Ab * r2 * c2 + Bb * r1 * c1 * dct;
+        gP0 = gP0 + n * (-tcb / dn);
+        gd = gd + n * (-tcb * tc / dn + (dn < 0.0f ? -cib : cib));
+      }
       if (OPT & ADJ_SHAPE) {  // the crossed triangle: its plane (crossing distance) and normal (ci)
         const float3 n = xyz(nr);
         const float tcb = (Ga * (-kap * med.f0 * med.al[mm_cur]) + gt / med.c[mm_cur]) -
                           (Ga * (-kap * med.f0 * med.al[m2]) + gt / med.c[m2]);  // dL/dt_c
         const float dct = ct > 0.0f ? rr * rr * ci / ct : 0.0f;
         const float cib = Ab * r2 * c2 + Bb * r1 * c1 * dct;
-        const float3 xc = xyz(sc) + d * tc;
+        const float3 xc = p0 + d * tc;
         const float3 v0 = xyz(__ldg(&A.S.tri_v0[xid[c]]));
         const float3 nhb = d * (dn < 0.0f ? -cib : cib) + (v0 - xc) * (tcb / dn);
         tri_shape_add(A.S, xid[c], n, nhb, n * (tcb / dn), A.g_tris);
@@ -614,14 +788,27 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       mm_cur = m2;
       tprev = tc;
     }
-    if (acq) ADD(acc[3 * med.M + 2], gX * ((float)e2 - 0.5f * (float)(q.ne - 1)));  // the pitch
+    if (acq) ADD(acc[iPitch], gX * ((float)e2 - 0.5f * (float)(q.ne - 1)));  // the pitch
     *seed = make_float2(ga * k_n, gt);
+    if (rough_job) {
+      // d = (x_e - p0) / D, D = |x_e - p0|: the adjoint of the target point is
+      // (gd - d (d.gd)) / D + gD d, that of p0 its negative plus the crossings' direct terms
+      const float3 gT = (gd - d * dot3(d, gd)) * (1.0f / D) + d * gD;
+      gP0 = gP0 - gT;
+      if (OPT & ADJ_ACQ) ADD(acc[iPitch], gT.x * ((float)e2 - 0.5f * (float)(q.ne - 1)));
+      const float Gf = Ga / fd.v;
+      const size_t sv = 2 * ((size_t)(path - A.path_base) * K1 + k);
+      A.seedv[sv] = make_float4(gP0.x, gP0.y, gP0.z, 0.0f);
+      A.seedv[sv + 1] = make_float4(Gf * fd.d[RN_W], Gf * fd.d[RN_W + 1], Gf * fd.d[RN_W + 2], 0.0f);
+    }
   }
   __syncthreads();
   float* out = A.gpart + (size_t)blockIdx.x * P;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     // the row slot of gradient slot p (-1: a slot secondary rays do not touch)
-    const int rp = p < 3 * med.M + 2 ? p : (((OPT & ADJ_ACQ) && p == A.acq_slot + 1) ? 3 * med.M + 2 : -1);
+    const int rp = p < 3 * med.M + 2 ? p
+                   : (rnee && p < 4 * med.M + 2) ? p
+                   : (((OPT & ADJ_ACQ) && p == A.acq_slot + 1) ? iPitch : -1);
     float s = 0.0f;
     if (rp >= 0)
       for (int t = 0; t < (int)blockDim.x; ++t) s += gsm[t * PS + rp];
@@ -635,7 +822,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
 // sweep paths of equal length.  work: [0, 17) counts, [17, 34) offsets, [34, 51) cursors,
 // [51] total.
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ int path_class(const uint32_t* rec, int kmax) {
+// rough_mask: bit m set when medium m is rough and its interfaces' events send secondary rays
+// (a triangle's roughness is its back-side medium's), read through the triangle's media
+__device__ __forceinline__ int path_class(const uint32_t* rec, int kmax, uint32_t rough_mask, const float4* tri_nrm) {
   int nseg = 0;
   bool active = false;
   for (int k = 0; k <= kmax; ++k) {
@@ -643,6 +832,9 @@ __device__ __forceinline__ int path_class(const uint32_t* rec, int kmax) {
     if (c == CLS_NONE) break;
     nseg = k + 1;
     if (c == CLS_XDCR || (c == CLS_SCAT && k < kmax)) active = true;
+    if (rough_mask && c == CLS_TRI && k < kmax &&
+        ((rough_mask >> (__float_as_uint(__ldg(&tri_nrm[code_id(rec[k])]).w) >> 16)) & 1u))
+      active = true;
   }
   return active ? nseg : -1;
 }
@@ -652,7 +844,8 @@ __device__ __forceinline__ int path_class(const uint32_t* rec, int kmax) {
 // counts go through shared memory to one global atomic per class and block.
 constexpr int ACT_TILE = 256;
 __global__ void __launch_bounds__(ACT_TILE) k_active_count(const uint32_t* record, uint32_t n, int kmax,
-                                                           uint32_t* work, uint8_t* pclass) {
+                                                           uint32_t* work, uint8_t* pclass, uint32_t rough_mask,
+                                                           const float4* tri_nrm) {
   extern __shared__ uint32_t rows[];  // [ACT_TILE][kmax + 1]
   __shared__ uint32_t cnt[17];
   const int K1 = kmax + 1;
@@ -664,7 +857,7 @@ __global__ void __launch_bounds__(ACT_TILE) k_active_count(const uint32_t* recor
     for (uint32_t j = threadIdx.x; j < m * (uint32_t)K1; j += ACT_TILE) rows[j] = __ldg(&src[j]);
     __syncthreads();
     if (threadIdx.x < m) {
-      const int c = path_class(rows + threadIdx.x * K1, kmax);
+      const int c = path_class(rows + threadIdx.x * K1, kmax, rough_mask, tri_nrm);
       pclass[base + threadIdx.x] = (uint8_t)(c < 0 ? 0xFF : c);  // read back by k_active_fill
       if (c >= 0) {
         const unsigned same = __match_any_sync(__activemask(), c);  // lanes of this class
@@ -758,25 +951,36 @@ static int adj_opt(const AdjArgs& a) {
   return (a.acq_slot >= 0 ? ADJ_ACQ : 0) | (a.g_tris ? ADJ_SHAPE : 0) | (a.med.has_rough ? ADJ_ROUGH : 0);
 }
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
-  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(nee_row_len(a.med.M, a.acq_slot >= 0));
-  switch (adj_opt(a) & (ADJ_ACQ | ADJ_SHAPE)) {  // secondary rays cross rough interfaces as smooth ones
+  const bool rnee = a.med.has_rough && a.acq.rough_nee;
+  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(nee_row_len(a.med.M, a.acq_slot >= 0, rnee));
+  // secondary rays cross rough interfaces as smooth ones; they start at rough events with rnee
+  switch ((adj_opt(a) & (ADJ_ACQ | ADJ_SHAPE)) | (rnee ? ADJ_RNEE : 0)) {
     case 0: k_nee_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 1: k_nee_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 2: k_nee_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
-    default: k_nee_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 3: k_nee_adjoint<3><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 8: k_nee_adjoint<8><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 9: k_nee_adjoint<9><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 10: k_nee_adjoint<10><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    default: k_nee_adjoint<11><<<grid, ADJ_THREADS, sm, st>>>(a); break;
   }
 }
 void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint8_t* pclass,
-                         uint32_t* active, int grid, cudaStream_t st) {
+                         uint32_t* active, int grid, cudaStream_t st, uint32_t rough_mask, const float4* tri_nrm) {
   cudaMemsetAsync(work, 0, sizeof(uint32_t) * 52, st);
   k_active_count<<<grid, ACT_TILE, sizeof(uint32_t) * ACT_TILE * (kmax + 1), st>>>(record, n_paths, kmax, work,
-                                                                                  pclass);
+                                                                                  pclass, rough_mask, tri_nrm);
   k_active_scan<<<1, 32, 0, st>>>(work);
   k_active_fill<<<grid, ACT_TILE, 0, st>>>(pclass, n_paths, work, active);
 }
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);
-  switch (adj_opt(a)) {
+  const bool rnee = a.med.has_rough && a.acq.rough_nee;
+  switch (adj_opt(a) | (rnee ? ADJ_RNEE : 0)) {
+    case 12: k_path_adjoint<12><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 13: k_path_adjoint<13><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 14: k_path_adjoint<14><<<grid, ADJ_THREADS, sm, st>>>(a); break;
+    case 15: k_path_adjoint<15><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 0: k_path_adjoint<0><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 1: k_path_adjoint<1><<<grid, ADJ_THREADS, sm, st>>>(a); break;
     case 2: k_path_adjoint<2><<<grid, ADJ_THREADS, sm, st>>>(a); break;
@@ -789,12 +993,16 @@ void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
 }
 cudaError_t adjoint_set_attrs() {
   const int sm = (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ));
-  const void* ks[12] = {(const void*)k_path_adjoint<0>, (const void*)k_path_adjoint<1>,
-                        (const void*)k_path_adjoint<2>, (const void*)k_path_adjoint<3>,
-                        (const void*)k_path_adjoint<4>, (const void*)k_path_adjoint<5>,
-                        (const void*)k_path_adjoint<6>, (const void*)k_path_adjoint<7>,
-                        (const void*)k_nee_adjoint<0>,  (const void*)k_nee_adjoint<1>,
-                        (const void*)k_nee_adjoint<2>,  (const void*)k_nee_adjoint<3>};
+  const void* ks[] = {(const void*)k_path_adjoint<0>,  (const void*)k_path_adjoint<1>,
+                      (const void*)k_path_adjoint<2>,  (const void*)k_path_adjoint<3>,
+                      (const void*)k_path_adjoint<4>,  (const void*)k_path_adjoint<5>,
+                      (const void*)k_path_adjoint<6>,  (const void*)k_path_adjoint<7>,
+                      (const void*)k_path_adjoint<12>, (const void*)k_path_adjoint<13>,
+                      (const void*)k_path_adjoint<14>, (const void*)k_path_adjoint<15>,
+                      (const void*)k_nee_adjoint<0>,   (const void*)k_nee_adjoint<1>,
+                      (const void*)k_nee_adjoint<2>,   (const void*)k_nee_adjoint<3>,
+                      (const void*)k_nee_adjoint<8>,   (const void*)k_nee_adjoint<9>,
+                      (const void*)k_nee_adjoint<10>,  (const void*)k_nee_adjoint<11>};
   for (const void* k : ks) {
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;

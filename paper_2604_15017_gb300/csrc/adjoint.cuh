@@ -36,6 +36,8 @@ struct AdjArgs {
   NeeRes nres;             // their stored results (null members: trace them again)
   const Counters* cnt;     // job counts per round
   float2* seeds;           // per (path - path_base, k): (dL/da, dL/dtau) seeded by secondary rays
+  float4* seedv;           // with secondary rays at rough events, per (path - path_base, k) two entries:
+                           // (dL/d(event point), 0), (dL/d(incident direction), 0)
   const uint32_t* active;  // paths with an arrival, grouped by event count
   const uint32_t* n_active;
 };
@@ -44,8 +46,10 @@ struct AdjArgs {
 void launch_nee_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
 // active paths of the record grouped by event count: work = 2 counters + 17 offsets + n entries;
 // pclass: n_paths bytes of scratch (each path's class)
+// rough_mask: media whose interface events send secondary rays (their paths are active too)
 void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uint32_t* work, uint8_t* pclass,
-                         uint32_t* active, int grid, cudaStream_t st);
+                         uint32_t* active, int grid, cudaStream_t st, uint32_t rough_mask = 0u,
+                         const float4* tri_nrm = nullptr);
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st);
 cudaError_t adjoint_set_attrs();
 void launch_grad_reduce(const float* gpart, int nblocks, int P, float* g, cudaStream_t st);

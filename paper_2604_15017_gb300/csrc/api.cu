@@ -30,7 +30,7 @@ enum Slot {
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
   W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS,
   W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_QA_SURF, W_KEEP, W_NEE_JX, W_NEE_JW, W_JOBU_JX,
-  W_JOBU_JW, W_QA_MIS, W_QB_MIS, W_COUNT
+  W_JOBU_JW, W_QA_MIS, W_QB_MIS, W_SEEDV, W_COUNT
 };
 
 struct SceneGPU {
@@ -1171,8 +1171,6 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
   Acq q;
   CKS(make_media(ctx, theta, sc->n_media_hint, med, sc->rough));
   CKS(make_acq(ctx, acq, seed, q));
-  if (q.rough_nee && sc->rough)
-    return fail(ctx, US_ERR_ARG, "the adjoint of secondary rays at rough events is not available (rough_nee = 0)");
   SplatGeom g;
   AdjArgs A;
   std::memset(&A, 0, sizeof A);
@@ -1205,6 +1203,8 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     A.nee.job = (float4*)ctx->L->ws[W_NEE_JOB].p;
     A.nee.jm = (uint32_t*)ctx->L->ws[W_NEE_JM].p;
     A.nee.jpath = (uint32_t*)ctx->L->ws[W_NEE_PATH].p;
+    A.nee.jx = (float4*)ctx->L->ws[W_NEE_JX].p;
+    A.nee.jw = (float4*)ctx->L->ws[W_NEE_JW].p;
     if (rec == (const uint32_t*)ctx->L->record.p) {  // a recorded pass kept its secondary-ray results
       A.nres.res = (float4*)ctx->L->ws[W_NEE_RES].p;
       A.nres.xo = (uint2*)ctx->L->ws[W_NEE_XO].p;
@@ -1214,6 +1214,14 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     }
     A.cnt = cnt;
     CKS(ws(ctx, W_SEEDS, (size_t)n * K1, st, &A.seeds));
+    const bool rnee = q.rough_nee && sc->rough;
+    uint32_t rough_mask = 0u;
+    A.seedv = nullptr;
+    if (rnee) {
+      CKS(ws(ctx, W_SEEDV, 2 * (size_t)n * K1, st, &A.seedv));
+      for (int mi = 0; mi < med.M; ++mi)
+        if (med.rough[mi] > 0.0f) rough_mask |= 1u << mi;
+    }
     CKS(ws(ctx, W_ACTIVE, (size_t)n + 1, st, &active));
     CKS(ws(ctx, W_ACT_CNT, 64, st, &work));
     A.active = active;
@@ -1222,7 +1230,7 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     CKS(ws(ctx, W_PCLASS, (size_t)n, st, &pclass));
     // the active-path lists (a pass over the record) do not depend on the secondary-ray
     // adjoint: on the lane's second stream they run beside it
-    const bool nee_adj = sc->dev.n_scat > 0 && A.nee.job;
+    const bool nee_adj = (sc->dev.n_scat > 0 || rnee) && A.nee.job;
     const bool fork = nee_adj && ctx->opts[US_OPT_NEE_STREAM] > 0;
     Lane* L = ctx->L;
     cudaStream_t as = st;
@@ -1234,7 +1242,7 @@ static int transport_vjp(us_ctx* ctx, uint64_t scene, const float* theta, const 
     }
     {
       StageScope sc_(ctx, US_STAGE_PATH_ADJ, 3, as);
-      launch_active_paths(rec, n, q.kmax, work, pclass, active, grid_of(ctx, 4), as);
+      launch_active_paths(rec, n, q.kmax, work, pclass, active, grid_of(ctx, 4), as, rough_mask, sc->dev.tri_nrm);
     }
     if (nee_adj) {
       A.gpart = gpart + (size_t)grid * A.P;

@@ -298,10 +298,10 @@ __device__ __forceinline__ int xtrav_finish(const XTrav& T, float* xt, uint32_t*
 }
 
 __device__ __forceinline__ int all_crossings(const SceneDev& S, float3 o, float3 d, float tmax, float* xt,
-                                             uint32_t* xid) {
+                                             uint32_t* xid, uint32_t skip = 0xFFFFFFFFu) {
   XTrav T;
   int stack[BVH_STACK];
-  xtrav_init(o, d, tmax, T);
+  xtrav_init(o, d, tmax, T, skip);
   while (xtrav_step(S, o, d, T, stack, xt, xid)) {
   }
   return xtrav_finish(T, xt, xid);
@@ -377,7 +377,7 @@ __device__ __forceinline__ NeeOut nee_shade(const SceneDev& S, const Media& med,
 // as in nee_shade, receive directivity (Eq. cutoff)
 __device__ __forceinline__ NeeOut nee_eval(const SceneDev& S, const Media& med, const Acq& q, float3 p, int e2,
                                            int m_start, float& t_hi, float& t_lo, float* xt, uint32_t* xid,
-                                           float3* dir_out, float* D_out) {
+                                           float3* dir_out, float* D_out, uint32_t skip = 0xFFFFFFFFu) {
   float3 d;
   float D;
   const float frx = nee_setup(q, p, e2, d, D);
@@ -392,7 +392,7 @@ __device__ __forceinline__ NeeOut nee_eval(const SceneDev& S, const Media& med, 
     r.n = 0;
     return r;
   }
-  const int n = all_crossings(S, p, d, D, xt, xid);
+  const int n = all_crossings(S, p, d, D, xt, xid, skip);
   return nee_shade(S, med, q, d, D, frx, n, m_start, t_hi, t_lo, xt, xid);
 }
 

@@ -293,6 +293,116 @@ __device__ __forceinline__ float ggx_d(float nh, float alpha) {
   return a2 / (PI_F * k * k);
 }
 
+// Forward-mode dual number with N derivative slots (the local derivatives of the rough-event
+// secondary ray's BSDF factor in the adjoint), and the few operations that factor needs; the
+// same code instantiated with float is the forward pass's.
+template <int N>
+struct DualN {
+  float v;
+  float d[N];
+  __device__ __forceinline__ DualN() {}
+  __device__ __forceinline__ DualN(float x) : v(x) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = 0.0f;
+  }
+};
+template <int N>
+__device__ __forceinline__ DualN<N> dual_const(float v) {
+  DualN<N> r;
+  r.v = v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = 0.0f;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> dual_var(float v, int slot) {
+  DualN<N> r = dual_const<N>(v);
+  r.d[slot] = 1.0f;
+  return r;
+}
+__device__ __forceinline__ float dval(float x) { return x; }
+template <int N>
+__device__ __forceinline__ float dval(const DualN<N>& x) { return x.v; }
+template <int N>
+__device__ __forceinline__ DualN<N> operator+(const DualN<N>& a, const DualN<N>& b) {
+  DualN<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator-(const DualN<N>& a, const DualN<N>& b) {
+  DualN<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator*(const DualN<N>& a, const DualN<N>& b) {
+  DualN<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = fmaf(a.d[i], b.v, a.v * b.d[i]);
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator*(const DualN<N>& a, float b) {
+  DualN<N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> operator/(const DualN<N>& a, const DualN<N>& b) {
+  const float ib = 1.0f / b.v, q = a.v * ib;
+  DualN<N> r;
+  r.v = q;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - q * b.d[i]) * ib;
+  return r;
+}
+template <int N>
+__device__ __forceinline__ DualN<N> dsqrt(const DualN<N>& a) {
+  const float s = sqrtf(a.v), k = s > 0.0f ? 0.5f / s : 0.0f;
+  DualN<N> r;
+  r.v = s;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * k;
+  return r;
+}
+__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+template <class T>
+__device__ __forceinline__ T dabs(const T& a) {
+  return dval(a) < 0.0f ? a * -1.0f : a;
+}
+template <class T>
+struct V3 {
+  T x, y, z;
+};
+template <class T>
+__device__ __forceinline__ V3<T> v3(const T& x, const T& y, const T& z) {
+  V3<T> r;
+  r.x = x;
+  r.y = y;
+  r.z = z;
+  return r;
+}
+template <class T>
+__device__ __forceinline__ T vdot(const V3<T>& a, const V3<T>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <class T>
+__device__ __forceinline__ V3<T> vscale(const V3<T>& a, const T& k) {
+  return v3(a.x * k, a.y * k, a.z * k);
+}
+template <class T>
+__device__ __forceinline__ V3<T> vadd(const V3<T>& a, const V3<T>& b) {
+  return v3(a.x + b.x, a.y + b.y, a.z + b.z);
+}
+
 // Secondary ray from a rough interface event (Sec. 2.3.3) toward unit direction o (distance^2
 // r2 to the element's centre): the microfacet BSDF's amplitude per solid angle toward o for the
 // incident direction w (i = -w; nin the macro normal on the incident side), with the half vector
@@ -303,41 +413,72 @@ __device__ __forceinline__ float ggx_d(float nh, float alpha) {
 // g / (p_nee + p_bsdf), p_nee = 1 / (N_e Omega) the density of a uniform element and direction
 // within it (Omega its face's solid angle), p_bsdf = D(h) (h.n) |dh/do| P(choice) the primary's.
 // Returns false when nothing is sent that way; else fac = that weight / N_e (the segment's
-// shading multiplies by N_e) and the medium the segment starts in.
+// shading multiplies by N_e) and whether o reflects (the segment starts in m1) or refracts (m2).
+// T is float, or a DualN carrying the derivatives in the inputs.
+template <class T>
+__device__ __forceinline__ T ggx_d_t(const T& nh, const T& alpha) {
+  const T a2 = alpha * alpha;
+  const T k = nh * nh * (a2 - T(1.0f)) + T(1.0f);
+  return a2 / (k * k * PI_F);
+}
+template <class T>
+__device__ __forceinline__ T smith_g1_t(const T& vn, const T& alpha) {
+  const T c = dabs(vn);
+  const T a2 = alpha * alpha;
+  return c * 2.0f / (c + dsqrt(a2 + (T(1.0f) - a2) * c * c));
+}
+template <class T>
+__device__ __forceinline__ bool rough_nee_factor_t(const Acq& q, const T& c1, const T& c2, const T& r1, const T& r2,
+                                                   const T& alpha, const V3<T>& w, const V3<T>& nin, const V3<T>& o,
+                                                   const T& dist2, const T& pitch, T& fac, bool& reflect) {
+  const V3<T> i = vscale(w, T(-1.0f));
+  const T in = vdot(i, nin), on = vdot(o, nin);
+  reflect = dval(on) > 0.0f;
+  V3<T> hv = reflect ? vadd(i, o) : vscale(vadd(vscale(i, T(1.0f) / c1), vscale(o, T(1.0f) / c2)), T(-1.0f));
+  T hl = T(1.0f) / dsqrt(vdot(hv, hv));
+  if (!reflect && dval(vdot(hv, nin)) < 0.0f) hl = hl * -1.0f;  // the facet faces the incident side
+  const V3<T> h = vscale(hv, hl);
+  const T ih = vdot(i, h), oh = vdot(o, h), nh = vdot(nin, h);
+  if (!(dval(ih) > 0.0f) || !(dval(nh) > 0.0f) || (!reflect && !(dval(oh) < 0.0f))) return false;
+  // pressure coefficients of the facet h (Snell with sound speeds), incidence cosine ih
+  const T rr = c2 / c1;
+  T si2 = T(1.0f) - ih * ih;
+  if (dval(si2) < 0.0f) si2 = T(0.0f);
+  const T st2 = rr * rr * si2;
+  const bool tir = dval(st2) >= 1.0f;
+  T R, C, J;
+  if (tir) {
+    if (!reflect) return false;
+    R = T(1.0f);
+    C = R;
+  } else {
+    const T ct = dsqrt(T(1.0f) - st2);
+    const T Av = r2 * c2 * ih, Bv = r1 * c1 * ct;
+    R = (Av - Bv) / (Av + Bv);
+    C = reflect ? R : Av * 2.0f / (Av + Bv);
+  }
+  if (reflect) {
+    J = T(1.0f) / (ih * 4.0f);
+  } else {
+    const T den = ih / c1 + oh / c2;
+    J = oh * -1.0f / (c2 * c2 * den * den);
+  }
+  const T D = ggx_d_t(nh, alpha);
+  const T g = D * smith_g1_t(in, alpha) * smith_g1_t(on, alpha) * C * ih * J / in;
+  const T omega = pitch * dabs(o.z) * q.hel / dist2;
+  const T p_nee = T(1.0f) / (omega * (float)q.ne);
+  const T pr = tir ? T(1.0f) : (q.split_mode == 0 ? R * R : T(q.split_q));
+  const T p_bsdf = D * nh * J * (reflect ? pr : T(1.0f) - pr);
+  fac = g / ((p_nee + p_bsdf) * (float)q.ne);
+  return true;
+}
+
 __device__ __forceinline__ bool rough_nee_factor(const Acq& q, const Media& med, float3 w, float3 nin, int m1, int m2,
                                                  float alpha, float3 o, float r2, float& fac, int& m_start) {
-  const float3 i = w * -1.0f;
-  const float in = dot3(i, nin), on = dot3(o, nin);
-  const bool reflect = on > 0.0f;
-  const float c1 = med.c[m1], c2 = med.c[m2];
-  float3 h;
-  if (reflect) {
-    h = i + o;
-  } else {
-    h = (i * (1.0f / c1) + o * (1.0f / c2)) * -1.0f;
-  }
-  h = h * rsqrtf(dot3(h, h));
-  if (!reflect && dot3(h, nin) < 0.0f) h = h * -1.0f;
-  const float ih = dot3(i, h), oh = dot3(o, h), nh = dot3(nin, h);
-  if (!(ih > 0.0f) || !(nh > 0.0f) || (!reflect && !(oh < 0.0f))) return false;
-  const Iface f = iface(w, h, c1, c2, med.rho[m1], med.rho[m2]);
-  float C, J;
-  if (reflect) {
-    C = f.R;
-    J = 1.0f / (4.0f * ih);
-  } else {
-    if (f.tir) return false;
-    C = f.T;
-    const float den = ih / c1 + oh / c2;
-    J = -oh / (c2 * c2 * den * den);
-  }
-  const float D = ggx_d(nh, alpha);
-  const float g = D * smith_g1(in, alpha) * smith_g1(on, alpha) * C * ih * J / in;
-  const float omega = q.pitch * q.hel * fabsf(o.z) / r2;
-  const float p_nee = 1.0f / ((float)q.ne * omega);
-  const float pr = f.tir ? 1.0f : (q.split_mode == 0 ? f.R * f.R : q.split_q);
-  const float p_bsdf = D * nh * J * (reflect ? pr : 1.0f - pr);
-  fac = g / ((float)q.ne * (p_nee + p_bsdf));
+  bool reflect = false;
+  if (!rough_nee_factor_t<float>(q, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2], alpha, v3(w.x, w.y, w.z),
+                                 v3(nin.x, nin.y, nin.z), v3(o.x, o.y, o.z), r2, q.pitch, fac, reflect))
+    return false;
   m_start = reflect ? m1 : m2;
   return true;
 }

@@ -138,7 +138,7 @@ def random_rotation(rng):
 # --------------------------------------------------------------------------------------------
 def acquisition(n_elem, pitch, n_samples, angles_deg, n_rays, k_max, c_bf, fs=40e6, bw=0.6, h_el=5 * MM,
                 alpha_m_deg=20.0, alpha_c_deg=45.0, split_mode=0, split_q=0.5, stream_id=0, tx_elem=-1,
-                n_tx_elem=0, rough_nee=0):
+                n_tx_elem=0, rough_nee=1):
     return dict(n_elem=int(n_elem), pitch=float(pitch), h_el=float(h_el), fs=float(fs),
                 n_samples=int(n_samples), k_max=int(k_max), n_rays=int(n_rays), bw=float(bw),
                 alpha_m=alpha_m_deg * DEG, alpha_c=alpha_c_deg * DEG, c_bf=float(c_bf),

@@ -167,7 +167,7 @@ def acq_desc(acq):
                 int(acq["k_max"]), int(acq["n_rays"]), float(acq["bw"]), float(acq["alpha_m"]),
                 float(acq["alpha_c"]), float(acq["c_bf"]), int(acq.get("split_mode", 0)),
                 float(acq.get("split_q", 0.5)), int(acq.get("stream_id", 0)) & 0xFFFFFFFF,
-                int(acq.get("tx_elem", -1)), int(acq.get("n_tx_elem", 0)), int(acq.get("rough_nee", 0)))
+                int(acq.get("tx_elem", -1)), int(acq.get("n_tx_elem", 0)), int(acq.get("rough_nee", 1)))
     return d, ang
 
 

@@ -59,6 +59,21 @@ def rough_inclusions(n_rays=200):
     return P.with_roughness(w, r)
 
 
+def with_rough_nee(w):
+    w = dict(w)
+    w["acq"] = dict(w["acq"], rough_nee=1)
+    return w
+
+
+def assert_rough_nee_matters(w, grf, g_ref, tol_scale):
+    """With secondary rays at rough events the oracle's gradient must differ from the one
+    without them by far more than the tolerance, so that an adjoint ignoring them fails."""
+    w0 = dict(w)
+    w0["acq"] = dict(w["acq"], rough_nee=0)
+    g0 = O.forward(w0)["run"].gradient(grf)
+    assert np.max(np.abs(g_ref - g0) / tol_scale) > 5.0
+
+
 def run_pair(ctx, w):
     sid = ctx.upload_workload(w)
     rf, b = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
@@ -79,12 +94,6 @@ def test_rough_forward_matches_oracle(ctx, make):
     assert agreement(rec, ref["run"].records()) >= 0.999
     assert rel_l2(rf.double().cpu().numpy(), ref["rf"]) <= 1e-3, rel_l2(rf.double().cpu().numpy(), ref["rf"])
     ctx.release_scene(sid)
-
-
-def with_rough_nee(w):
-    w = dict(w)
-    w["acq"] = dict(w["acq"], rough_nee=1)
-    return w
 
 
 @pytest.mark.parametrize("make", ["slab", "inclusions", "cylinder"])
@@ -112,9 +121,11 @@ def test_rough_secondary_rays_forward_matches_oracle(ctx, make):
     ctx.release_scene(sid)
 
 
+@pytest.mark.parametrize("rnee", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_rough_adjoint_matches_oracle(ctx, mode):
+def test_rough_adjoint_matches_oracle(ctx, mode, rnee):
     w = P.with_roughness(P.slab_scatterers(n_rays=1200), [0.0, 0.25])
+    w = with_rough_nee(w) if rnee else w
     sid, rf, b, ref, rec = run_pair(ctx, w)
     grf = np.random.default_rng(51).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
     g_ref = ref["run"].gradient(grf)
@@ -123,14 +134,19 @@ def test_rough_adjoint_matches_oracle(ctx, mode):
     scale = np.abs(g_ref * np.maximum(np.abs(w["theta"]), 1e-2))
     err = np.abs(g - g_ref) * np.maximum(np.abs(w["theta"]), 1e-2)
     assert np.all(err <= 1e-3 * scale + 1e-4 * scale.max()), np.c_[g, g_ref]
+    if rnee:
+        assert_rough_nee_matters(w, grf, g_ref, (1e-3 * scale + 1e-4 * scale.max()) / np.maximum(np.abs(w["theta"]), 1e-2))
     ctx.release_scene(sid)
 
 
+@pytest.mark.parametrize("rnee", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_rough_cylinder_adjoint(ctx, mode):
+def test_rough_cylinder_adjoint(ctx, mode, rnee):
     """The hollow cylinder with a rough wall: curved interfaces, refraction into and out of the
-    wall, scatterers behind it whose secondary rays cross it."""
+    wall, scatterers behind it whose secondary rays cross it; with rnee, secondary rays from the
+    wall's events too."""
     w = P.with_roughness(P.hollow_cylinder(n_rays=400), [0.0, 0.2, 0.0])
+    w = with_rough_nee(w) if rnee else w
     sid, rf, b, ref, rec = run_pair(ctx, w)
     assert agreement(rec, ref["run"].records()) >= 0.999
     grf = np.random.default_rng(52).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
@@ -140,6 +156,8 @@ def test_rough_cylinder_adjoint(ctx, mode):
     scale = np.abs(g_ref * np.maximum(np.abs(w["theta"]), 1e-2))
     err = np.abs(g - g_ref) * np.maximum(np.abs(w["theta"]), 1e-2)
     assert np.all(err <= 1e-3 * scale + 1e-4 * scale.max()), np.c_[g, g_ref]
+    if rnee:
+        assert_rough_nee_matters(w, grf, g_ref, (1e-3 * scale + 1e-4 * scale.max()) / np.maximum(np.abs(w["theta"]), 1e-2))
     ctx.release_scene(sid)
 
 
@@ -155,11 +173,15 @@ def test_zero_roughness_is_the_smooth_scene(ctx):
     ctx.release_scene(sid1)
 
 
+@pytest.mark.parametrize("rnee", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_rough_cylinder_radius_gradient(ctx, mode):
+def test_rough_cylinder_radius_gradient(ctx, mode, rnee):
     """Shape through rough events: the sampled facet normal follows the macro normal (its
-    tangent frame and tilt) and the microfacet weight's cosines follow it too."""
+    tangent frame and tilt) and the microfacet weight's cosines follow it too; with rnee, the
+    secondary rays from rough events (the event point on the moving plane, its normal in the
+    BSDF) and the balance weights."""
     w = P.with_roughness(P.hollow_cylinder(n_rays=400), [0.0, 0.2, 0.0])
+    w = with_rough_nee(w) if rnee else w
     sid, rf, b, ref, rec = run_pair(ctx, w)
     grf = np.random.default_rng(53).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
     tangents = np.stack([w["dtris_dR"], np.random.default_rng(4).normal(size=w["tris"].shape)])
@@ -171,11 +193,14 @@ def test_rough_cylinder_radius_gradient(ctx, mode):
     ctx.release_scene(sid)
 
 
+@pytest.mark.parametrize("rnee", [0, 1])
 @pytest.mark.parametrize("mode", [0, 1])
-def test_rough_acquisition_gradient(ctx, mode):
+def test_rough_acquisition_gradient(ctx, mode, rnee):
     """Acquisition gradients on a rough scene (the path adjoint's rough + acquisition variant):
-    the acquisition slots follow the roughness slots."""
+    the acquisition slots follow the roughness slots; with rnee, the secondary rays from rough
+    events move with their target elements and the balance weights with the element faces."""
     w = P.with_roughness(P.slab_scatterers(n_rays=800), [0.0, 0.25])
+    w = with_rough_nee(w) if rnee else w
     sid, rf, b, ref, rec = run_pair(ctx, w)
     grf = np.random.default_rng(54).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
     full = ref["run"].gradient_acq(grf, full=True)
