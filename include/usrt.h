@@ -190,6 +190,13 @@ int us_get_status(us_ctx* ctx, int clear, int* device_status);
  * (us_forward, us_bmode, us_envlog, us_envlog_noalloc); meant for tests of the second path. */
 void us_set_envlog_fused(int enable);
 
+/* Transposed DAS kernels, process-wide: enable != 0 (the default) uses the tiled kernel
+ * (per-tile sample windows in shared memory, one global atomic per window entry) whenever
+ * n_tx <= 32; 0 always takes the untiled kernel (one global atomic per tap).  Both give the
+ * same bits (the same fixed-point contributions).  Applies to us_das_adjoint, us_bmode_vjp and
+ * us_adjoint; meant for tests of the second path. */
+void us_set_das_adj_tiled(int enable);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Tracing: per-stage device time and kernel launch counts                                   */
 /* ---------------------------------------------------------------------------------------- */
@@ -318,11 +325,15 @@ int us_envlog_vjp(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, con
                   float* dL_dirf_dev, void* stream);
 
 /* S10 alone: transposed DAS (Eq. das_adjoint), a scatter of dL/dI_rf back to the two
- * interpolation samples of every tap; dL_drf_dev is overwritten. */
+ * interpolation samples of every tap; dL_drf_dev is overwritten.  Deterministic: the scatter
+ * accumulates in 64-bit fixed point (scale 2^k, the largest power of two with
+ * pixels x max|dL/dI_rf| x 2^k < 2^62), so repeated calls give the same bits whatever the
+ * order of the device's atomics.  A non-finite dL/dI_rf makes every entry NaN. */
 int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* dL_dirf_dev,
                    float* dL_drf_dev, void* stream);
 
-/* dL/dRF from dL/dB through log, envelope and DAS (S7 recomputed, S9b, S10). */
+/* dL/dRF from dL/dB through log, envelope and DAS (S7 recomputed, S9b, S10); deterministic
+ * like us_das_adjoint. */
 int us_bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* rf_dev,
                  const float* dL_dB_dev, float* dL_drf_dev, void* stream);
 

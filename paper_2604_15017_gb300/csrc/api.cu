@@ -30,7 +30,7 @@ enum Slot {
   W_GRF, W_GPART, W_REC_CHUNK, W_PACK, W_NPACK, W_NEE_PATH, W_SEEDS, W_ACTIVE, W_ACT_CNT, W_RAY_KEY, W_RAY_CNT,
   W_RAY_OFF, W_RAY_CUR, W_JOBU_JOB, W_JOBU_JM, W_JOBU_PATH, W_GB, W_NEE_RES, W_NEE_XO, W_XING, W_PCLASS,
   W_ACQ_PART, W_JOB_KEY, W_JOB_CNT, W_JOB_OFF, W_JOB_CUR, W_QA_SURF, W_KEEP, W_NEE_JX, W_NEE_JW, W_JOBU_JX,
-  W_JOBU_JW, W_QA_MIS, W_QB_MIS, W_SEEDV, W_COUNT
+  W_JOBU_JW, W_QA_MIS, W_QB_MIS, W_SEEDV, W_DAS_ACC, W_DAS_MAX, W_COUNT
 };
 
 struct SceneGPU {
@@ -1095,8 +1095,12 @@ int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, 
   CKS(make_acq(ctx, acq, 0, q));
   CKS(make_img(ctx, img, im));
   if (!dL_dirf_dev || !dL_drf_dev) return fail(ctx, US_ERR_ARG, "null buffer");
+  unsigned long long* acc;
+  unsigned int* maxbits;
+  CKS(ws(ctx, W_DAS_ACC, (size_t)q.ntx * q.ne * q.ns, (cudaStream_t)stream, &acc));
+  CKS(ws(ctx, W_DAS_MAX, 1, (cudaStream_t)stream, &maxbits));
   StageScope sc_(ctx, US_STAGE_DAS_ADJ, 1, (cudaStream_t)stream);
-  launch_das_adj(q, im, dL_dirf_dev, dL_drf_dev, grid_of(ctx, 8), (cudaStream_t)stream);
+  launch_das_adj(q, im, dL_dirf_dev, dL_drf_dev, grid_of(ctx, 8), (cudaStream_t)stream, acc, maxbits);
   CK(cudaGetLastError());
   return US_OK;
 }
@@ -1121,10 +1125,14 @@ static int bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img
     launch_das(q, im, rf_dev, irf, grid_of(ctx, 8), st, ctx->opts[US_OPT_DAS_TMA] ? ctx->d_status : nullptr);
     irf_made(ctx, q, im, rf_dev, irf);
   }
+  unsigned long long* acc;
+  unsigned int* maxbits;
+  CKS(ws(ctx, W_DAS_ACC, (size_t)q.ntx * q.ne * q.ns, st, &acc));
+  CKS(ws(ctx, W_DAS_MAX, 1, st, &maxbits));
   CKS(us_envlog_vjp(ctx, img, irf, dL_dB_dev, gi, stream));
   {
     StageScope sc_(ctx, US_STAGE_DAS_ADJ, 1, st);
-    launch_das_adj(q, im, gi, dL_drf_dev, grid_of(ctx, 8), st);
+    launch_das_adj(q, im, gi, dL_drf_dev, grid_of(ctx, 8), st, acc, maxbits);
   }
   CK(cudaGetLastError());
   return US_OK;

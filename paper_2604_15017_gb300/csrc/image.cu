@@ -170,30 +170,37 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// sample window [start, start + len) of (element e, transmit t) for the tile: plain FP32 delays
-// at the tile's corners, padded by 2 samples (len 0: nothing in the record; -1: too long)
-__device__ int2 das_window(const Acq& q, const Img& im, int l0, int l1, int d0, int d1, int e, int t) {
+// plain FP32 delay of pixel (l, d) for (element e, transmit t), in samples
+__device__ __forceinline__ float das_delay_f32(const Acq& q, const Img& im, int l, int d, int e, int t) {
   const float k = q.fs / q.cbf;
   const float st = q.sin_tx[t], ct = q.cos_tx[t];
   const float hw = 0.5f * (q.ne - 1) * q.pitch * fabsf(st);
   const float xe = (e - 0.5f * (q.ne - 1)) * q.pitch;
+  const float x = im.nl > 1 ? im.x0 + (im.x1 - im.x0) * (float)l / (float)(im.nl - 1) : im.x0;
+  const float z = im.nd > 1 ? im.z0 + (im.z1 - im.z0) * (float)d / (float)(im.nd - 1) : im.z0;
+  return (x * st + z * ct + hw) * k + sqrtf((x - xe) * (x - xe) + z * z) * k;
+}
+// sample window [start, start + len) covering delays in [lo, hi], padded by 2 samples and
+// aligned to 4 (len 0: nothing in the record; -1: longer than max_len)
+__device__ __forceinline__ int2 das_window_of(int ns, float lo, float hi, int max_len) {
+  int a = (int)floorf(lo) - 2, b = (int)ceilf(hi) + 3;
+  a = max(0, a) & ~3;
+  b = min(ns, (b + 3) & ~3);
+  if (b <= a) return make_int2(0, 0);
+  if (b - a > max_len) return make_int2(a, -1);
+  return make_int2(a, b - a);
+}
+// sample window of (element e, transmit t) for the tile: the delays at the tile's corners (the
+// delay grows monotonically with depth along each line)
+__device__ int2 das_window(const Acq& q, const Img& im, int l0, int l1, int d0, int d1, int e, int t) {
   float lo = 3.0e38f, hi = -3.0e38f;
-  for (int l = l0; l <= l1; ++l) {
-    const float x = im.nl > 1 ? im.x0 + (im.x1 - im.x0) * (float)l / (float)(im.nl - 1) : im.x0;
+  for (int l = l0; l <= l1; ++l)
     for (int r = 0; r < 2; ++r) {
-      const int d = r ? d1 : d0;
-      const float z = im.nd > 1 ? im.z0 + (im.z1 - im.z0) * (float)d / (float)(im.nd - 1) : im.z0;
-      const float u = (x * st + z * ct + hw) * k + sqrtf((x - xe) * (x - xe) + z * z) * k;
+      const float u = das_delay_f32(q, im, l, r ? d1 : d0, e, t);
       lo = fminf(lo, u);
       hi = fmaxf(hi, u);
     }
-  }
-  int a = (int)floorf(lo) - 2, b = (int)ceilf(hi) + 3;
-  a = max(0, a) & ~3;
-  b = min(q.ns, (b + 3) & ~3);
-  if (b <= a) return make_int2(0, 0);
-  if (b - a > DT_WIN) return make_int2(a, -1);
-  return make_int2(a, b - a);
+  return das_window_of(q.ns, lo, hi, DT_WIN);
 }
 
 __global__ void __launch_bounds__(DT_THREADS) k_das_tma(Acq q, Img im, const float* __restrict__ rf,
@@ -315,10 +322,70 @@ size_t das_tma_smem(const Acq& q) {
 }
 
 // transposed DAS: every tap scatters w_e (1 - f) g and w_e f g to its two samples
-__global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const float* __restrict__ gi, float* grf) {
+// The transposed DAS accumulates in 64-bit fixed point so that its sums do not depend on the
+// order of the atomics (integer addition is associative, and wraps harmlessly in between): a
+// contribution v becomes the integer nearest v 2^k, with 2^k the largest power of two for
+// which max |dL/dI| 2^k < 2^43 and (pixel count) x max |dL/dI| 2^k < 2^62.  The second product
+// bounds every entry's sum, since a pixel adds at most w |dL/dI| <= |dL/dI| (w <= 1 the
+// apodisation) to one row, split between two neighbouring samples; the first lets the tiled
+// kernel hold a tile's partial sums in two 32-bit words (below).  The quantum is thus 2^-43 of
+// the largest pixel's contribution (2^-44 for 2^19 pixels or more), far below FP32 rounding.
+// max |dL/dI| comes from an integer atomicMax on the float bits of |dL/dI| (order-independent
+// too); a non-finite dL/dI makes every entry NaN.
+__global__ void k_das_adj_max(const float* __restrict__ gi, int n, unsigned int* maxbits) {
+  unsigned int m = 0u;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = max(m, __float_as_uint(fabsf(gi[i])));  // NaN's bits lie above +inf's
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(maxbits, m);
+}
+constexpr unsigned int F32_INF_BITS = 0x7F800000u;
+constexpr int DAS_ADJ_V_BITS = 43;  // |contribution| < 2^43 in fixed point
+// the exponent k: max |dL/dI| < 2^e and npx <= 2^c give npx max |dL/dI| < 2^(e + c)
+__device__ __forceinline__ int das_adj_kexp(int npx, unsigned int maxbits) {
+  if (maxbits == 0u) return 0;
+  const int e = ilogbf(__uint_as_float(maxbits)) + 1;
+  const int c = 32 - __clz(max(npx - 1, 1));
+  return min(DAS_ADJ_V_BITS, 62 - c) - e;
+}
+// v (|v| < 2^43) rounded to the nearest integer (ties to even, as __float2ll_rn) and split as
+// hi 2^22 + lo with lo in [0, 2^22), by FP32 additions only: a float -> 64-bit integer
+// conversion runs on the FP64 pipe, a small fraction of the FP32 rate on this part.  Adding
+// 2^23 (same sign as v) leaves an integer, exactly when |v| < 2^23 (larger v are integers
+// already); 1.5 2^23 added with rounding toward -inf gives floor(v / 2^22) in the float's low
+// mantissa bits; the remainder is an exact subtraction.
+constexpr int DAS_ADJ_LO_BITS = 22;
+__device__ __forceinline__ void das_adj_fixed(float v, int& hi, uint32_t& lo) {
+  const float c = copysignf(8388608.0f, v);
+  const float vr = fabsf(v) < 8388608.0f ? __fsub_rn(__fadd_rn(v, c), c) : v;
+  const float h = __fadd_rd(vr * (1.0f / 4194304.0f), 12582912.0f);  // 1.5 2^23 + floor(vr / 2^22)
+  hi = __float_as_int(h) - 0x4B400000;
+  const float hf = __fsub_rn(h, 12582912.0f);
+  const float lf = __fsub_rn(vr, hf * 4194304.0f);  // in [0, 2^22), exact
+  lo = __float_as_uint(__fadd_rn(lf, 8388608.0f)) - 0x4B000000u;
+}
+__device__ __forceinline__ unsigned long long das_adj_fixed64(float v) {
+  int hi;
+  uint32_t lo;
+  das_adj_fixed(v, hi, lo);
+  return (unsigned long long)((long long)hi * (1ll << DAS_ADJ_LO_BITS) + (long long)lo);
+}
+__global__ void k_das_adj_finish(const unsigned long long* __restrict__ acc, long long n, int npx,
+                                 const unsigned int* maxbits, float* grf) {
+  const unsigned int mb = *maxbits;
+  const int k = das_adj_kexp(npx, mb);
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    grf[j] = mb >= F32_INF_BITS ? __int_as_float(0x7FC00000) : ldexpf(__ll2float_rn((long long)acc[j]), -k);
+}
+
+__global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const float* __restrict__ gi,
+                                                         unsigned long long* acc, const unsigned int* maxbits) {
   extern __shared__ float2 utx_s[];
   const int npx = im.nl * im.nd;
   const DasGeo g = das_geo(q);
+  const unsigned int mb = *maxbits;
+  if (mb >= F32_INF_BITS) return;  // k_das_adj_finish writes NaN
+  const int kexp = das_adj_kexp(npx, mb);
   for (int base = blockIdx.x * DAS_THREADS; base < npx; base += gridDim.x * DAS_THREADS) {
     const int p = base + threadIdx.x;
     const bool valid = p < npx;
@@ -329,17 +396,129 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
     if (gv != 0.0f) {
       for (int e = 0; e < q.ne; ++e) {
         const float2 ur = das_split(das_urx(q, g, x, z, e));
-        const float wg = apod_w(q, im, x.hi, z.hi, e) * gv;
+        const float wg = ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp);
         for (int t = 0; t < q.ntx; ++t) {
           int i;
           float f;
           das_tap(utx_s[t * DAS_THREADS + threadIdx.x], ur, i, f);
-          float* row = grf + ((size_t)t * q.ne + e) * q.ns;
-          if (i >= 0 && i < q.ns) atomicAdd(&row[i], wg * (1.0f - f));
-          if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], wg * f);
+          unsigned long long* row = acc + ((size_t)t * q.ne + e) * q.ns;
+          if (i >= 0 && i < q.ns) atomicAdd(&row[i], das_adj_fixed64(wg * (1.0f - f)));
+          if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], das_adj_fixed64(wg * f));
         }
       }
     }
+  }
+}
+
+// Tiled transposed DAS.  A CTA owns a 16-line x 32-depth pixel tile (two pixels per thread; a
+// warp holds 32 consecutive depths of one line).  Element by element, the taps of all transmits
+// go into per-transmit sample windows in shared memory, the window of (e, t) being the samples
+// the tile's delays can reach (FP32 delays at the tile's corners, padded); then every nonzero
+// window entry goes to its row with one global atomic.  A window spans ~100-200 samples against
+// the tile's 1024 taps per (e, t), so the global atomics drop several-fold.  A tap outside its
+// window (an underestimated window, or one longer than DJ_WIN) goes to the row directly.
+// A window entry is two 32-bit words with native shared atomics: a contribution v (|v| < 2^43)
+// splits into v >> 22 (signed, |.| <= 2^21) and its low 22 bits (unsigned); at most 512 pixels
+// add to one entry, so neither word can overflow (2^30 and 2^31), and the flush rebuilds
+// hi 2^22 + lo exactly.  The contributions and their sums are those of k_das_adj, so the two
+// kernels give the same bits.
+constexpr int DJ_THREADS = 512, DJ_LINES = 16, DJ_DEPTHS = 32, DJ_WIN = 256;
+constexpr int DJ_SMEM_MAX = 200 * 1024;
+static_assert(DJ_DEPTHS == 32 && DJ_LINES == 16 && DJ_THREADS / 32 == DJ_LINES, "a warp is one line's 32 depths");
+static_assert(DAS_ADJ_V_BITS - DAS_ADJ_LO_BITS + 9 < 31 && DAS_ADJ_LO_BITS + 9 < 32,
+              "the tile's 512 contributions per entry fit both words");
+__host__ __device__ constexpr size_t das_adj_tile_smem(int ntx) {
+  return (2 * sizeof(uint32_t) * DJ_WIN + sizeof(float2) * DJ_THREADS + 2 * sizeof(int2)) * (size_t)ntx;
+}
+// windows of element e for all transmits: warp w takes transmits w, w + 8, ...; its lanes
+// evaluate the 32 corner delays (16 lines x the two depth ends) and reduce them
+__device__ __forceinline__ void dj_windows(const Acq& q, const Img& im, int l0, int l1, int d0, int d1, int e,
+                                           int2* out, int lane, int warp) {
+  for (int t = warp; t < q.ntx; t += DJ_THREADS / 32) {  // warp-uniform
+    const float u = das_delay_f32(q, im, min(l0 + (lane & 15), l1), (lane & 16) ? d1 : d0, e, t);
+    float lo = u, hi = u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fminf(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+      hi = fmaxf(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+    }
+    if (lane == 0) out[t] = das_window_of(q.ns, lo, hi, DJ_WIN);
+  }
+}
+__global__ void __launch_bounds__(DJ_THREADS) k_das_adj_tile(Acq q, Img im, const float* __restrict__ gi,
+                                                             unsigned long long* acc, const unsigned int* maxbits) {
+  extern __shared__ __align__(16) unsigned char dj_sm[];
+  const int ntx = q.ntx;
+  int* hi_s = reinterpret_cast<int*>(dj_sm);                                   // [ntx][DJ_WIN]
+  uint32_t* lo_s = reinterpret_cast<uint32_t*>(hi_s + (size_t)ntx * DJ_WIN);   // [ntx][DJ_WIN]
+  float2* utx_s = reinterpret_cast<float2*>(lo_s + (size_t)ntx * DJ_WIN);      // [ntx][DJ_THREADS]
+  int2* win_s = reinterpret_cast<int2*>(utx_s + (size_t)ntx * DJ_THREADS);     // [2][ntx]
+  const unsigned int mb = *maxbits;
+  if (mb >= F32_INF_BITS) return;  // k_das_adj_finish writes NaN
+  const int kexp = das_adj_kexp(im.nl * im.nd, mb);
+  const int tiles_d = (im.nd + DJ_DEPTHS - 1) / DJ_DEPTHS;
+  const int l0 = (blockIdx.x / tiles_d) * DJ_LINES, d0 = (blockIdx.x % tiles_d) * DJ_DEPTHS;
+  const int l1 = min(l0 + DJ_LINES - 1, im.nl - 1), d1 = min(d0 + DJ_DEPTHS - 1, im.nd - 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int l = l0 + warp, d = d0 + lane;
+  const bool valid = l < im.nl && d < im.nd;
+  const DasGeo g = das_geo(q);
+  const ff x = grid_coord(im.x0, im.x1, valid ? l : l0, im.nl);
+  const ff z = grid_coord(im.z0, im.z1, valid ? d : d0, im.nd);
+  const float gv = valid ? gi[(size_t)l * im.nd + d] : 0.0f;
+  for (int t = 0; t < ntx; ++t) utx_s[t * DJ_THREADS + threadIdx.x] = das_split(das_utx(q, g, x, z, t));
+  for (int j = threadIdx.x; j < ntx * DJ_WIN; j += DJ_THREADS) {
+    hi_s[j] = 0;
+    lo_s[j] = 0u;
+  }
+  dj_windows(q, im, l0, l1, d0, d1, 0, win_s, lane, warp);
+  __syncthreads();
+  for (int e = 0; e < q.ne; ++e) {
+    const int2* wcur = win_s + (e & 1) * ntx;
+    // the other buffer was last read by the previous element's flush, before its barrier
+    if (e + 1 < q.ne) dj_windows(q, im, l0, l1, d0, d1, e + 1, win_s + ((e + 1) & 1) * ntx, lane, warp);
+    const float wg = gv != 0.0f ? ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp) : 0.0f;
+    if (wg != 0.0f) {
+      const float2 ur = das_split(das_urx(q, g, x, z, e));
+      for (int t = 0; t < ntx; ++t) {
+        int i;
+        float f;
+        das_tap(utx_s[t * DJ_THREADS + threadIdx.x], ur, i, f);
+        int h0, h1;
+        uint32_t o0, o1;
+        das_adj_fixed(wg * (1.0f - f), h0, o0);
+        das_adj_fixed(wg * f, h1, o1);
+        const int2 w = wcur[t];
+        const int rel = i - w.x;
+        if (w.y > 0 && rel >= 0 && rel + 1 < w.y) {
+          const int j = t * DJ_WIN + rel;
+          atomicAdd(&hi_s[j], h0);
+          atomicAdd(&lo_s[j], o0);
+          atomicAdd(&hi_s[j + 1], h1);
+          atomicAdd(&lo_s[j + 1], o1);
+        } else {
+          unsigned long long* row = acc + ((size_t)t * q.ne + e) * q.ns;
+          if (i >= 0 && i < q.ns)
+            atomicAdd(&row[i], (unsigned long long)((long long)h0 * (1ll << DAS_ADJ_LO_BITS) + (long long)o0));
+          if (i + 1 >= 0 && i + 1 < q.ns)
+            atomicAdd(&row[i + 1], (unsigned long long)((long long)h1 * (1ll << DAS_ADJ_LO_BITS) + (long long)o1));
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < ntx * DJ_WIN; j += DJ_THREADS) {
+      const int t = j / DJ_WIN, r = j - t * DJ_WIN;
+      const int2 w = wcur[t];
+      if (r < w.y) {
+        const long long v = (long long)hi_s[j] * (1ll << DAS_ADJ_LO_BITS) + (long long)lo_s[j];
+        if (v) {
+          atomicAdd(acc + ((size_t)t * q.ne + e) * q.ns + w.x + r, (unsigned long long)v);
+          hi_s[j] = 0;
+          lo_s[j] = 0u;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -696,9 +875,21 @@ int das_acq_blocks(const Img& im) { return (im.nl * im.nd + DA_THREADS - 1) / DA
 void launch_das_acq(const Acq& q, const Img& im, const float* rf, const float* gi, float* part, cudaStream_t st) {
   k_das_acq<<<das_acq_blocks(im), DA_THREADS, das_acq_smem(q.ntx), st>>>(q, im, rf, gi, part);
 }
-void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st) {
-  cudaMemsetAsync(grf, 0, sizeof(float) * (size_t)q.ntx * q.ne * q.ns, st);
-  k_das_adj<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, gi, grf);
+static std::atomic<int> g_das_adj_tiled{1};
+void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st,
+                    unsigned long long* acc, unsigned int* maxbits) {
+  const long long n = (long long)q.ntx * q.ne * q.ns;
+  const int npx = im.nl * im.nd;
+  cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (size_t)n, st);
+  cudaMemsetAsync(maxbits, 0, sizeof(unsigned int), st);
+  k_das_adj_max<<<min(grid, (npx + 255) / 256), 256, 0, st>>>(gi, npx, maxbits);
+  if (das_adj_tile_smem(q.ntx) <= (size_t)DJ_SMEM_MAX && g_das_adj_tiled.load()) {
+    const int tiles = ((im.nl + DJ_LINES - 1) / DJ_LINES) * ((im.nd + DJ_DEPTHS - 1) / DJ_DEPTHS);
+    k_das_adj_tile<<<tiles, DJ_THREADS, das_adj_tile_smem(q.ntx), st>>>(q, im, gi, acc, maxbits);
+  } else {
+    k_das_adj<<<grid, DAS_THREADS, sizeof(float2) * DAS_THREADS * q.ntx, st>>>(q, im, gi, acc, maxbits);
+  }
+  k_das_adj_finish<<<grid, 256, 0, st>>>(acc, n, npx, maxbits, grf);
 }
 constexpr int FUSED_SMEM_MAX = 200 * 1024;
 static std::atomic<int> g_envlog_fused{1};
@@ -706,6 +897,7 @@ static std::atomic<int> g_envlog_fused{1};
 }  // namespace usrt
 
 extern "C" void us_set_envlog_fused(int enable) { usrt::g_envlog_fused.store(enable ? 1 : 0); }
+extern "C" void us_set_das_adj_tiled(int enable) { usrt::g_das_adj_tiled.store(enable ? 1 : 0); }
 
 namespace usrt {
 
@@ -781,6 +973,8 @@ cudaError_t image_set_attrs(int nd) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_das_adj, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(float2) * DAS_THREADS * MAX_TX));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_das_adj_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, DJ_SMEM_MAX);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_das_acq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)das_acq_smem(MAX_TX));
   if (e != cudaSuccess) return e;

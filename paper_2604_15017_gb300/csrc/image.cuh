@@ -8,7 +8,10 @@ namespace usrt {
 // DAS; with a device status word the TMA-staged kernel is used when the shape allows
 void launch_das(const Acq& q, const Img& im, const float* rf, float* irf, int grid, cudaStream_t st,
                 int* status = nullptr);
-void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st);
+// transposed DAS, deterministic (64-bit fixed-point accumulation): acc is scratch of
+// ntx * ne * ns words, maxbits one word
+void launch_das_adj(const Acq& q, const Img& im, const float* gi, float* grf, int grid, cudaStream_t st,
+                    unsigned long long* acc, unsigned int* maxbits);
 // DAS derivative in (c_bf, pitch, steering angles) contracted with gi: das_acq_blocks(im)
 // partial rows of 2 + ntx floats into part (reduce them with launch_grad_reduce_split)
 int das_acq_blocks(const Img& im);

@@ -28,7 +28,8 @@ EXPORTS = ["us_create", "us_destroy", "us_last_error", "us_scene_upload", "us_sc
            "us_launch_count", "us_set_option", "us_forward_batch", "us_autotune_batch",
            "us_run_request", "us_request_bytes", "us_param_map", "us_adam_step", "us_das_acq_vjp",
            "us_transport_vjp_acq", "us_adjoint_acq", "us_transport_vjp_shape", "us_adjoint_shape",
-           "us_shape_param_grad", "us_get_status", "us_set_envlog_fused"]
+           "us_shape_param_grad", "us_get_status", "us_set_envlog_fused",
+           "us_set_das_adj_tiled"]
 OPT_DAS_TMA, OPT_LANES, OPT_NEE_STREAM, OPT_FAULT_BARRIER = 0, 1, 2, 3
 STAGES = ["generate", "traverse", "interact", "nee", "splat_sort", "splat_rows", "das", "envlog", "loss",
           "envlog_vjp", "das_adj", "nee_adj", "path_adj", "other", "das_acq", "ray_sort", "job_sort"]
@@ -106,6 +107,8 @@ def lib():
             l.us_get_status.argtypes = [VP, C.c_int, C.POINTER(C.c_int)]
             l.us_set_envlog_fused.argtypes = [C.c_int]
             l.us_set_envlog_fused.restype = None
+            l.us_set_das_adj_tiled.argtypes = [C.c_int]
+            l.us_set_das_adj_tiled.restype = None
             l.us_splat.argtypes = [VP, C.POINTER(AcqDesc), C.c_float, C.c_int64, VP, VP, VP, VP, VP, VP]
             l.us_das.argtypes = [VP, C.POINTER(AcqDesc), C.POINTER(ImgDesc), VP, VP, VP]
             l.us_envlog.argtypes = [VP, C.POINTER(ImgDesc), VP, VP, VP]
@@ -181,6 +184,12 @@ def set_envlog_fused(enable):
     """Process-wide: the cooperative fused envelope kernel (True, default) or always the
     two-kernel path (False)."""
     lib().us_set_envlog_fused(int(bool(enable)))
+
+
+def set_das_adj_tiled(enable):
+    """Process-wide: the tiled transposed-DAS kernel (True, default; n_tx <= 32) or always the
+    untiled one (False).  Same bits either way."""
+    lib().us_set_das_adj_tiled(int(bool(enable)))
 
 
 class Context:
