@@ -113,6 +113,7 @@ __device__ __forceinline__ void tri_shape_add(const SceneDev& S, uint32_t id, fl
 // S12: path adjoint
 // ------------------------------------------------------------------------------------------
 constexpr int ADJ_THREADS = 128;
+constexpr int ADJ_EV_SHARED = 4;  // events per path whose sweep state sits in shared memory
 
 // each thread accumulates dL/dtheta in a private shared-memory row (odd stride: no bank
 // conflicts, no atomics); the block sums the rows once at the end
@@ -144,10 +145,25 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
   const int iAs = 3 * med.M, iF0 = 3 * med.M + 1;
   for (int p = 0; p < P; ++p) acc[p] = 0.0f;
   const int K1 = q.kmax + 1;
-  // per-event state kept for the reverse sweep (local memory): origin, direction, amplitude;
-  // the record word, the medium and the secondary-ray seeds are read or derived again there
-  float3 O[MAX_KMAX + 1], W[MAX_KMAX + 1];
-  float Aa[MAX_KMAX + 1];
+  // per-event state kept for the reverse sweep: origin, direction, amplitude.  The first
+  // ADJ_EV_SHARED events of a path (most paths have no more) sit in shared memory after the
+  // gradient rows, 7 words per event, word-major so that a warp's accesses hit 32 banks; later
+  // events go to local memory.  The record word, the medium and the secondary-ray seeds are read
+  // or derived again in the sweep.
+  float* ev = gsm + ADJ_THREADS * PS + threadIdx.x;
+  float evl[7 * (MAX_KMAX + 1 - ADJ_EV_SHARED)];
+  auto ev_word = [&](int k, int f) -> float& {
+    return k < ADJ_EV_SHARED ? ev[(7 * k + f) * ADJ_THREADS] : evl[7 * (k - ADJ_EV_SHARED) + f];
+  };
+  auto ev_put = [&](int k, float3 o_, float3 w_, float a_) {
+    ev_word(k, 0) = o_.x;
+    ev_word(k, 1) = o_.y;
+    ev_word(k, 2) = o_.z;
+    ev_word(k, 3) = w_.x;
+    ev_word(k, 4) = w_.y;
+    ev_word(k, 5) = w_.z;
+    ev_word(k, 6) = a_;
+  };
   const float kap = KAPPA_F;
   const uint32_t n_act = *A.n_active;
   for (uint32_t ai = blockIdx.x * blockDim.x + threadIdx.x; ai < n_act; ai += gridDim.x * blockDim.x) {
@@ -181,9 +197,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       const uint32_t r = rec[k];
       const uint32_t cls = code_cls(r), id = code_id(r);
       if (cls == CLS_NONE) break;
-      O[k] = o;
-      W[k] = w;
-      Aa[k] = a;
+      ev_put(k, o, w, a);
       m_last = m;
       nseg = k + 1;
       const float t = frozen_t(A.S, cls, id, o, w);
@@ -267,8 +281,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
     // its direction density, and that of the distance travelled since (every segment after it)
     float g_pdf = 0.0f, g_since = 0.0f;
     for (int k = nseg - 1; k >= 0; --k) {
-      const float3 ok = O[k], wk = W[k];
-      const float ak = Aa[k];
+      const float3 ok = f3(ev_word(k, 0), ev_word(k, 1), ev_word(k, 2));
+      const float3 wk = f3(ev_word(k, 3), ev_word(k, 4), ev_word(k, 5));
+      const float ak = ev_word(k, 6);
       const uint32_t r = rec[k];
       const uint32_t cls = code_cls(r), id = code_id(r);
       // medium of segment k: the incident side of a hit triangle, else that of segment k + 1
@@ -524,7 +539,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
       // so d/dp = tau0 / p and o0.x / p; d/dth with d|sin th|/dth = sgn(sin th) cos th, sgn(0) = 0
       const float sg = st0 > 0.0f ? 1.0f : (st0 < 0.0f ? -1.0f : 0.0f);
       ADD(acc[A.acq_slot], tb * (-tau0 / q.cbf));
-      ADD(acc[A.acq_slot + 1], (tb * tau0 + ob.x * O[0].x) / q.pitch);
+      ADD(acc[A.acq_slot + 1], (tb * tau0 + ob.x * ev[0]) / q.pitch);
       ADD(acc[A.acq_slot + 2 + tx], tb * (xe + 0.5f * (q.ne - 1) * q.pitch * sg) * q.cos_tx[tx] / q.cbf);
     }
   }
@@ -973,8 +988,13 @@ void launch_active_paths(const uint32_t* record, uint32_t n_paths, int kmax, uin
   k_active_scan<<<1, 32, 0, st>>>(work);
   k_active_fill<<<grid, ACT_TILE, 0, st>>>(pclass, n_paths, work, active);
 }
+// the path sweep's shared memory: the gradient rows, then 7 words per event and thread for
+// the first ADJ_EV_SHARED events
+__host__ __device__ constexpr size_t path_adj_smem(int P, int kmax) {
+  return sizeof(float) * ADJ_THREADS * (size_t)(adj_row_stride(P) + 7 * (kmax + 1 < ADJ_EV_SHARED ? kmax + 1 : ADJ_EV_SHARED));
+}
 void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
-  const size_t sm = sizeof(float) * ADJ_THREADS * adj_row_stride(a.P);
+  const size_t sm = path_adj_smem(a.P, a.acq.kmax);
   const bool rnee = a.med.has_rough && a.acq.rough_nee;
   switch (adj_opt(a) | (rnee ? ADJ_RNEE : 0)) {
     case 12: k_path_adjoint<12><<<grid, ADJ_THREADS, sm, st>>>(a); break;
@@ -992,7 +1012,8 @@ void launch_path_adjoint(const AdjArgs& a, int grid, cudaStream_t st) {
   }
 }
 cudaError_t adjoint_set_attrs() {
-  const int sm = (int)(sizeof(float) * ADJ_THREADS * adj_row_stride(MAX_P_ACQ));
+  const int sm = (int)path_adj_smem(MAX_P_ACQ, MAX_KMAX);
+  static_assert(path_adj_smem(MAX_P_ACQ, MAX_KMAX) <= 227 * 1024, "path sweep shared memory");
   const void* ks[] = {(const void*)k_path_adjoint<0>,  (const void*)k_path_adjoint<1>,
                       (const void*)k_path_adjoint<2>,  (const void*)k_path_adjoint<3>,
                       (const void*)k_path_adjoint<4>,  (const void*)k_path_adjoint<5>,
