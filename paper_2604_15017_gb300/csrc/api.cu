@@ -496,10 +496,11 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   CKS(ws(ctx, W_RAY_OFF, RAY_BUCKETS + 1, st, &rs.off));
   A.trav_n = rs.off + RAY_KEY_BUCKETS;  // written by each round's ray sort
   CKS(ws(ctx, W_RAY_CUR, RAY_BUCKETS, st, &rs.cursor));
-  // the job sort's scratch: the ray sort's, or its own when it runs on the second stream
-  // beside the next round's ray sort
+  // the interaction kernel keys and counts the next round's rays (A.rk) before the round's job
+  // sort runs, so the job sort has scratch of its own
+  A.rk = rs;
   RaySort js = rs;
-  if (side) {
+  if (sort_jobs) {
     CKS(ws(ctx, W_JOB_KEY, n, st, &js.key));
     CKS(ws(ctx, W_JOB_CNT, RAY_BUCKETS, st, &js.cnt));
     CKS(ws(ctx, W_JOB_OFF, RAY_BUCKETS + 1, st, &js.off));
@@ -509,12 +510,13 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
   A.qout = Q.a;
   {
     StageScope sc_(ctx, US_STAGE_GENERATE, 1, st);
-    launch_generate(A, path0, n, grid_of(ctx, 8), st);
+    CK(cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st));
+    launch_generate(A, path0, n, grid_of(ctx, 2), st);
   }
   for (int k = 0; k <= q.kmax; ++k) {
     A.k = k;
     {
-      StageScope sc_(ctx, US_STAGE_RAY_SORT, 3, st);
+      StageScope sc_(ctx, US_STAGE_RAY_SORT, 2, st);
       launch_ray_sort(A, Q.a, Q.b, rs, grid_of(ctx, 2), st);
     }
     A.qin = Q.b;
@@ -527,6 +529,7 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     }
     {
       StageScope sc_(ctx, US_STAGE_INTERACT, 1, st);
+      CK(cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st));  // this round's sort has scanned them
       launch_interact(A, grid_of(ctx, 8), st);
     }
     // the round's secondary rays (job sort, then the kernel): on the second stream from here

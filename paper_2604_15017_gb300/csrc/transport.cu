@@ -30,12 +30,47 @@ __device__ __forceinline__ void path_tx_ray(const Acq& q, long long path, int& t
   ray = (uint32_t)(q.tx_elem < 0 ? local : (long long)q.tx_elem * q.nr + local);
 }
 
+__device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 w, bool carried) {
+  // origin: 8 x 8 cells over the scene's x and z extent
+  const int cx = min(7, max(0, (int)((o.x - rs.lo.x) * rs.inv_ext.x * 8.0f)));
+  const int cz = min(7, max(0, (int)((o.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
+  // direction: octahedral map of the unit sphere onto [-1, 1]^2, 16 x 16 bins
+  const float l1 = fabsf(w.x) + fabsf(w.y) + fabsf(w.z);
+  float u = w.x / l1, v = w.y / l1;
+  if (w.z < 0.0f) {
+    const float uu = (1.0f - fabsf(v)) * copysignf(1.0f, u);
+    const float vv = (1.0f - fabsf(u)) * copysignf(1.0f, v);
+    u = uu;
+    v = vv;
+  }
+  const int bu = min(15, max(0, (int)((u + 1.0f) * 8.0f)));
+  const int bv = min(15, max(0, (int)((v + 1.0f) * 8.0f)));
+  if (carried)  // 4 x 4 origin cells, 8 x 8 direction bins, after the rays that need a query
+    return (uint32_t)RAY_KEY_BUCKETS + (uint32_t)(((((cz >> 1) << 2) | (cx >> 1)) << 6) | ((bu >> 1) << 3) | (bv >> 1));
+  return (uint32_t)((((cz << 3) | cx) << 8) | (bu << 4) | bv);
+}
+
+// the interaction kernel keys each ray it appends for the next round's coherence sort and
+// counts it: one atomic per key among the lanes appending together
+__device__ __forceinline__ void ray_key_count(const RaySort& rs, uint32_t slot, float3 o, float3 w, bool carried) {
+  const uint32_t key = ray_key(rs, o, w, carried);
+  rs.key[slot] = key;
+  const uint32_t peers = __match_any_sync(__activemask(), key);
+  if ((int)(threadIdx.x & 31u) == __ffs(peers) - 1) atomicAdd(&rs.cnt[key], (uint32_t)__popc(peers));
+}
+
 // ------------------------------------------------------------------------------------------
 // Emission (Sec. 2.3.1, Eq. directivity, Eq. pressure_mc): origin uniform over the element
 // face, cosine-weighted direction (f_d / p = pi), weight pi / N_r, steering delay as a time
 // stamp tau_tx = (x_e sin(theta) + W/2 |sin(theta)|) / c_bf.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long path0, uint32_t n) {
+// The emitted rays share few sort keys (all start on the probe face), so the block counts its
+// rays' keys in shared memory and adds the nonzero counts once.
+constexpr int GEN_THREADS = 512;
+__global__ void __launch_bounds__(GEN_THREADS) k_generate(TransportArgs A, long long path0, uint32_t n) {
+  extern __shared__ uint32_t gen_h[];  // [RAY_BUCKETS]
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) gen_h[b] = 0u;
+  __syncthreads();
   const Acq& q = A.acq;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const long long path = path0 + i;
@@ -52,13 +87,20 @@ __global__ void __launch_bounds__(256) k_generate(TransportArgs A, long long pat
     const float wz = sqrtf(1.0f - u2);
     const float st = q.sin_tx[tx];
     const float tau0 = (xe * st + 0.5f * (q.ne - 1) * q.pitch * fabsf(st)) / q.cbf;
-    A.qout.pa[i] = make_float4(xe + (u0 - 0.5f) * q.pitch, (u1 - 0.5f) * q.hel, 0.0f, 3.14159265358979f / q.nr);
-    A.qout.wt[i] = make_float4(r * cp, r * sp, wz, tau0);
+    const float3 o0 = f3(xe + (u0 - 0.5f) * q.pitch, (u1 - 0.5f) * q.hel, 0.0f), w0 = f3(r * cp, r * sp, wz);
+    A.qout.pa[i] = make_float4(o0.x, o0.y, o0.z, 3.14159265358979f / q.nr);
+    A.qout.wt[i] = make_float4(w0.x, w0.y, w0.z, tau0);
+    const uint32_t key = ray_key(A.rk, o0, w0, false);
+    A.rk.key[i] = key;
+    atomicAdd(&gen_h[key], 1u);
     A.qout.meta[i] = make_uint4((uint32_t)path, 0xFFFFFFFFu, 0u, __float_as_uint(0.0f));
     A.qout.surf[i] = make_float2(-1.0f, 0.0f);
     if (A.mis_on) A.qout.mis[i] = make_float2(0.0f, 0.0f);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt->live[0] = n;
+  __syncthreads();
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
+    if (gen_h[b]) atomicAdd(&A.rk.cnt[b], gen_h[b]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -410,6 +452,7 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
     A.qout.meta[o] = make_uint4(meta.x, code, (uint32_t)m | ((uint32_t)(A.k + 1) << 8), __float_as_uint(tau_lo));
     A.qout.surf[o] = carry;
     if (A.mis_on) A.qout.mis[o] = mis;
+    ray_key_count(A.rk, o, x, w, carry.x >= 0.0f);
   }
 }
 
@@ -547,40 +590,6 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
 // ------------------------------------------------------------------------------------------
 // Coherence sort of a ray queue (one counting-sort pass, 14-bit key)
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 w, bool carried) {
-  // origin: 8 x 8 cells over the scene's x and z extent
-  const int cx = min(7, max(0, (int)((o.x - rs.lo.x) * rs.inv_ext.x * 8.0f)));
-  const int cz = min(7, max(0, (int)((o.z - rs.lo.z) * rs.inv_ext.z * 8.0f)));
-  // direction: octahedral map of the unit sphere onto [-1, 1]^2, 16 x 16 bins
-  const float l1 = fabsf(w.x) + fabsf(w.y) + fabsf(w.z);
-  float u = w.x / l1, v = w.y / l1;
-  if (w.z < 0.0f) {
-    const float uu = (1.0f - fabsf(v)) * copysignf(1.0f, u);
-    const float vv = (1.0f - fabsf(u)) * copysignf(1.0f, v);
-    u = uu;
-    v = vv;
-  }
-  const int bu = min(15, max(0, (int)((u + 1.0f) * 8.0f)));
-  const int bv = min(15, max(0, (int)((v + 1.0f) * 8.0f)));
-  if (carried)  // 4 x 4 origin cells, 8 x 8 direction bins, after the rays that need a query
-    return (uint32_t)RAY_KEY_BUCKETS + (uint32_t)(((((cz >> 1) << 2) | (cx >> 1)) << 6) | ((bu >> 1) << 3) | (bv >> 1));
-  return (uint32_t)((((cz << 3) | cx) << 8) | (bu << 4) | bv);
-}
-
-__global__ void __launch_bounds__(256) k_ray_keys(TransportArgs A, PathQ from, RaySort rs) {
-  extern __shared__ uint32_t h[];
-  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
-  __syncthreads();
-  const uint32_t n = A.cnt->live[A.k];
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t key = ray_key(rs, xyz(from.pa[i]), xyz(from.wt[i]), from.surf[i].x >= 0.0f);
-    rs.key[i] = key;
-    atomicAdd(&h[key], 1u);
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
-    if (h[b]) atomicAdd(&rs.cnt[b], h[b]);
-}
 
 constexpr int RS_THREADS = 512;
 constexpr int JOB_BUCKETS = 1024;  // <= RAY_BUCKETS (the sort buffers are shared)
@@ -705,14 +714,12 @@ void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, c
 
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st) {
-  cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st);
-  k_ray_keys<<<grid, 256, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, rs);
   launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
   k_ray_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
 }
 
 cudaError_t ray_sort_set_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_ray_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_generate, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(uint32_t) * RAY_BUCKETS));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_job_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -726,7 +733,7 @@ cudaError_t ray_sort_set_attrs() {
 }
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {
-  k_generate<<<grid, 256, 0, st>>>(a, path0, n);
+  k_generate<<<grid, GEN_THREADS, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, path0, n);
 }
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st) { k_traverse<<<grid, TRAV_THREADS, 0, st>>>(a); }
 void launch_march(const TransportArgs& a, int grid, cudaStream_t st) { k_march<<<grid, MARCH_THREADS, 0, st>>>(a); }

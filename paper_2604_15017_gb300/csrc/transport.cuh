@@ -59,30 +59,13 @@ struct Counters {
 // arrival: (row = tx * n_elem + e, tq fixed-point time, bits(a), path id)
 typedef uint4 Arrival;
 
-struct TransportArgs {
-  SceneDev S;
-  Media med;
-  Acq acq;
-  PathQ qin, qout;
-  float2* hits;       // (t, bits(code)) per queue slot
-  float2* keep;       // per queue slot: the surface hit a scatterer event replaced in hits
-  const uint32_t* trav_n;  // rays of the sorted queue that need a surface query (the rest carry one)
-  bool mis_on;        // secondary rays at rough events (the queues' mis fields are live)
-  NeeQ nee;
-  NeeRes nres;        // null members unless the pass is recorded for the adjoint
-  Arrival* arr;       // may be null (adjoint recompute: no arrivals)
-  uint32_t arr_cap;
-  uint32_t* record;   // may be null; index (path - path_base) * (kmax + 1) + k
-  long long path_base;
-  Counters* cnt;
-  int k;              // segment index
-};
-
 // coherence sort of a ray queue: one counting-sort pass over a 14-bit key (origin cell in x and
 // z, octahedral direction bin), so that the lanes of a warp start near each other and point the
 // same way.  Rays that carry their surface hit across a scatterer event (a pass-through: the
 // surface ahead is the one already found) follow in RAY_CARRY_BUCKETS coarser buckets of their
-// own, so the surface query runs over the first RAY_KEY_BUCKETS buckets only.
+// own, so the surface query runs over the first RAY_KEY_BUCKETS buckets only.  The kernel that
+// appends a ray to the queue (emission, interaction) writes its key and counts it, so the sort
+// itself is the scan of the counts and one scatter pass.
 constexpr int RAY_KEY_BITS = 14;
 constexpr int RAY_KEY_BUCKETS = 1 << RAY_KEY_BITS;
 constexpr int RAY_CARRY_BUCKETS = 1024;
@@ -94,7 +77,29 @@ struct RaySort {
   uint32_t* off;        // [RAY_BUCKETS + 1]
   uint32_t* cursor;     // [RAY_BUCKETS]
 };
-// sorts queue `from` (count live[k]) into `to`
+
+struct TransportArgs {
+  SceneDev S;
+  Media med;
+  Acq acq;
+  PathQ qin, qout;
+  float2* hits;       // (t, bits(code)) per queue slot
+  float2* keep;       // per queue slot: the surface hit a scatterer event replaced in hits
+  const uint32_t* trav_n;  // rays of the sorted queue that need a surface query (the rest carry one)
+  RaySort rk;         // keys and bucket counts of the rays appended to qout (the next round's sort)
+  bool mis_on;        // secondary rays at rough events (the queues' mis fields are live)
+  NeeQ nee;
+  NeeRes nres;        // null members unless the pass is recorded for the adjoint
+  Arrival* arr;       // may be null (adjoint recompute: no arrivals)
+  uint32_t arr_cap;
+  uint32_t* record;   // may be null; index (path - path_base) * (kmax + 1) + k
+  long long path_base;
+  Counters* cnt;
+  int k;              // segment index
+};
+
+// sorts queue `from` (count live[k]; its keys and counts written by the kernel that filled it,
+// into the counts zeroed before that kernel) into `to`
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st);
 // sorts round k's secondary-ray jobs (from.[nee_off[k], + nee[k])) into the same range of `to`
