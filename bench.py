@@ -668,7 +668,8 @@ def main():
                       "roughness": args.rough,
                       "adjoint_mode": args.mode, "paths_per_step": stats["n_paths"],
                       "segments_per_step": stats["segments"], "nee_queries_per_step": stats["nee_queries"],
-                      "arrivals_per_step": stats["arrivals"], "frames_per_s": world * 1e3 / ms,
+                      "arrivals_per_step": stats["arrivals"],
+                      "paths_per_round": stats["live"][:w["acq"]["k_max"] + 1], "frames_per_s": world * 1e3 / ms,
                       "l2": "per-step working set (path queues + arrivals, ~4 GB) exceeds L2; scene BVH resident"},
            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
            "stages_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in stages.items() if v[1]}}

@@ -118,6 +118,7 @@ typedef struct {
 } us_img_desc;
 
 /* Transport statistics of the most recent us_forward / us_trace on a context. */
+#define US_MAX_ROUNDS 17 /* segments per path: k_max <= 15, plus the last round's arrivals */
 typedef struct {
   int64_t n_paths;
   int64_t segments;      /* primary closest-hit queries (one per path segment) */
@@ -125,6 +126,8 @@ typedef struct {
   int64_t arrivals;      /* arrivals splatted (transducer hits + secondary rays) */
   int64_t dropped;       /* arrivals dropped: crossing-list overflow */
   int32_t status;        /* device status word: 0, or a us_status raised on the device */
+  int32_t pad;
+  int64_t live[US_MAX_ROUNDS];  /* paths entering segment k (rounds past k_max + 1 hold 0) */
 } us_stats;
 
 /* ---------------------------------------------------------------------------------------- */

@@ -956,6 +956,9 @@ int us_get_stats(us_ctx* ctx, us_stats* out) {
   }
   out->segments = seg;
   out->nee_queries = nee;
+  static_assert(US_MAX_ROUNDS == MAX_KMAX + 2, "rounds");
+  for (int k = 0; k < US_MAX_ROUNDS; ++k) out->live[k] = k <= MAX_KMAX ? c.live[k] : 0;
+  out->pad = 0;
   out->arrivals = c.n_arr;
   out->dropped = c.dropped;
   int ds = 0;

@@ -315,14 +315,14 @@ __global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
     const uint32_t code = __float_as_uint(h.y);
     const uint32_t cls = code_cls(code);
     const uint4 meta = A.qin.meta[i];
+    const float4 pa = A.qin.pa[i];  // read with the slot's other words, before the escape test
+    const float4 wt = A.qin.wt[i];
     const long long path = meta.x;
     uint32_t* rec = A.record ? &A.record[(size_t)(path - A.path_base) * K1 + A.k] : nullptr;
     if (cls == CLS_NONE) {  // escape
       if (rec) *rec = 0u;
       continue;
     }
-    float4 pa = A.qin.pa[i];
-    float4 wt = A.qin.wt[i];
     float2 mis = A.mis_on ? A.qin.mis[i] : make_float2(0.0f, 0.0f);
     int m = (int)(meta.z & 0xFF);
     float tau_lo = __uint_as_float(meta.w);
@@ -595,38 +595,61 @@ constexpr int RS_THREADS = 512;
 constexpr int JOB_BUCKETS = 1024;  // <= RAY_BUCKETS (the sort buffers are shared)
 constexpr int RS_PER = 16;
 constexpr int RS_CH = RS_THREADS * RS_PER;
-__global__ void __launch_bounds__(RS_THREADS) k_ray_scatter(TransportArgs A, PathQ from, PathQ to, RaySort rs) {
-  extern __shared__ uint32_t sm[];
-  uint32_t* h = sm;
-  uint32_t* base = sm + RAY_BUCKETS;
+// One block sorts a chunk of RS_CH rays: shared-memory counts of the chunk's keys (in place
+// then the chunk's first slot per key, 68 KB, so that two blocks fit an SM), then every ray is
+// copied to its slot.  Key and rank travel packed in one word (key < 2^15, rank < 2^13).  The
+// copies go RS_BATCH rays at a time, all loads before the stores, so that each thread keeps
+// several reads in flight.
+constexpr int RS_BATCH = 2;
+static_assert(RAY_BUCKETS < (1 << 19) && RS_CH <= (1 << 13) && RS_PER % RS_BATCH == 0, "key and rank packing");
+__global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, PathQ from, PathQ to, RaySort rs) {
+  extern __shared__ uint32_t sm[];  // [RAY_BUCKETS]
   const uint32_t n = A.cnt->live[A.k];
+  constexpr uint32_t NONE = 0xFFFFFFFFu;
   for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
-    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) h[b] = 0;
+    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) sm[b] = 0;
     __syncthreads();
-    uint32_t key[RS_PER], rank[RS_PER];
+    uint32_t kr[RS_PER];
 #pragma unroll
     for (int j = 0; j < RS_PER; ++j) {
       const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
-      key[j] = 0xFFFFFFFFu;
+      kr[j] = NONE;
       if (i < n) {
-        key[j] = rs.key[i];
-        rank[j] = atomicAdd(&h[key[j]], 1u);
+        const uint32_t key = rs.key[i];
+        kr[j] = (key << 13) | atomicAdd(&sm[key], 1u);
       }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
-      if (h[b]) base[b] = rs.off[b] + atomicAdd(&rs.cursor[b], h[b]);
+      if (sm[b]) sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < RS_PER; ++j) {
-      if (key[j] == 0xFFFFFFFFu) continue;
-      const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
-      const uint32_t o = base[key[j]] + rank[j];
-      to.pa[o] = from.pa[i];
-      to.wt[o] = from.wt[i];
-      to.meta[o] = from.meta[i];
-      if (key[j] >= (uint32_t)RAY_KEY_BUCKETS) A.hits[o] = from.surf[i];  // the carried surface hit
-      if (A.mis_on) to.mis[o] = from.mis[i];
+    for (int j0 = 0; j0 < RS_PER; j0 += RS_BATCH) {
+      float4 pa[RS_BATCH], wt[RS_BATCH];
+      uint4 me[RS_BATCH];
+      float2 sf[RS_BATCH], mi[RS_BATCH];
+#pragma unroll
+      for (int u = 0; u < RS_BATCH; ++u) {
+        if (kr[j0 + u] == NONE) continue;
+        const uint32_t i = c0 + (j0 + u) * RS_THREADS + threadIdx.x;
+        pa[u] = __ldg(&from.pa[i]);
+        wt[u] = __ldg(&from.wt[i]);
+        me[u] = __ldg(&from.meta[i]);
+        sf[u] = __ldg(&from.surf[i]);
+        if (A.mis_on) mi[u] = __ldg(&from.mis[i]);
+      }
+#pragma unroll
+      for (int u = 0; u < RS_BATCH; ++u) {
+        const uint32_t v = kr[j0 + u];
+        if (v == NONE) continue;
+        const uint32_t key = v >> 13;
+        const uint32_t o = sm[key] + (v & 0x1FFFu);
+        to.pa[o] = pa[u];
+        to.wt[o] = wt[u];
+        to.meta[o] = me[u];
+        if (key >= (uint32_t)RAY_KEY_BUCKETS) A.hits[o] = sf[u];  // the carried surface hit
+        if (A.mis_on) to.mis[o] = mi[u];
+      }
     }
     __syncthreads();
   }
@@ -715,7 +738,7 @@ void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, c
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st) {
   launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
-  k_ray_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
+  k_ray_scatter<<<grid, RS_THREADS, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
 }
 
 cudaError_t ray_sort_set_attrs() {
@@ -729,7 +752,7 @@ cudaError_t ray_sort_set_attrs() {
                            (int)(2 * sizeof(uint32_t) * RAY_BUCKETS));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ray_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(2 * sizeof(uint32_t) * RAY_BUCKETS));
+                              (int)(sizeof(uint32_t) * RAY_BUCKETS));
 }
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {

@@ -71,7 +71,8 @@ class Request(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_paths", C.c_int64), ("segments", C.c_int64), ("nee_queries", C.c_int64),
-                ("arrivals", C.c_int64), ("dropped", C.c_int64), ("status", C.c_int32)]
+                ("arrivals", C.c_int64), ("dropped", C.c_int64), ("status", C.c_int32), ("pad", C.c_int32),
+                ("live", C.c_int64 * 17)]
 
 
 _lib = None
@@ -298,7 +299,7 @@ class Context:
         s = Stats()
         self._check(lib().us_get_stats(self.h, C.byref(s)))
         return dict(n_paths=s.n_paths, segments=s.segments, nee_queries=s.nee_queries, arrivals=s.arrivals,
-                    dropped=s.dropped, status=s.status)
+                    dropped=s.dropped, status=s.status, live=[int(v) for v in s.live])
 
     def record(self, path_lo, n, k_max, stream=None):
         out = torch.empty((n, k_max + 1), dtype=torch.int32, device=self.device)
