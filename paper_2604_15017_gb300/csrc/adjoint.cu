@@ -112,6 +112,11 @@ __device__ __forceinline__ void tri_shape_add(const SceneDev& S, uint32_t id, fl
 // ------------------------------------------------------------------------------------------
 // S12: path adjoint
 // ------------------------------------------------------------------------------------------
+// slot of the secondary-ray seeds of event k of the pass's path p: event-major, so that the
+// path sweep's lanes (consecutive active paths) read neighbouring words at each event
+__device__ __forceinline__ size_t seed_slot(const AdjArgs& A, uint32_t p, int k) {
+  return (size_t)k * A.n_paths + p;
+}
 constexpr int ADJ_THREADS = 128;
 constexpr int ADJ_EV_SHARED = 4;  // events per path whose sweep state sits in shared memory
 
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
           nhb = front ? nb : nb * -1.0f;
         }
         if ((OPT & ADJ_RNEE) && alpha > 0.0f && k < q.kmax) {  // this rough event's secondary ray
-          const size_t si = (size_t)i * K1 + k;
+          const size_t si = seed_slot(A, i, k);
           const float2 sd = A.seeds[si];
           a1b += sd.x;
           t1b += sd.y;
@@ -491,7 +496,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_path_adjoint(AdjArgs A) {
         g_pdf = 0.0f;  // a triangle event ends the straight run a balance weight belongs to
         g_since = 0.0f;
       } else {  // scatterer
-        const float2 sd = A.seeds[(size_t)i * K1 + k];  // the secondary ray's adjoint seeds
+        // the secondary ray's adjoint seeds; an event at k_max started none (the interaction
+        // budget was spent), so its slot was never written
+        const float2 sd = k < q.kmax ? A.seeds[seed_slot(A, i, k)] : make_float2(0.0f, 0.0f);
         a1b = ab + sd.x;
         t1b = tb + sd.y;
         xb = ob;
@@ -599,7 +606,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     const int e2 = (int)((jm >> 8) & 0xFF), tx = (int)((jm >> 16) & 0xFF);
     const int k = (int)(jm >> 24);
     const long long path = A.nee.jpath[i];
-    float2* seed = &A.seeds[(size_t)(path - A.path_base) * K1 + k];
+    float2* seed = &A.seeds[seed_slot(A, (uint32_t)(path - A.path_base), k)];
     const float a1 = job.x;
     float nh = job.y, nl = job.z;
     // the ray's start: a scatterer's centre, or (rough events) the event point on triangle tri
@@ -624,8 +631,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       int ms;
       if (!rough_nee_factor(q, med, wi, nin, m, m2, med.rough[mm >> 16], dv0 * rsqrtf(r2v), r2v, fac0, ms)) {
         *seed = make_float2(0.0f, 0.0f);
-        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k)] = make_float4(0.f, 0.f, 0.f, 0.f);
-        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.seedv[2 * seed_slot(A, (uint32_t)(path - A.path_base), k)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.seedv[2 * seed_slot(A, (uint32_t)(path - A.path_base), k) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         continue;
       }
       m = ms;  // the medium the segment starts in
@@ -662,8 +669,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
     if (!no.ok) {
       *seed = make_float2(0.0f, 0.0f);
       if (rough_job) {
-        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k)] = make_float4(0.f, 0.f, 0.f, 0.f);
-        A.seedv[2 * ((size_t)(path - A.path_base) * K1 + k) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.seedv[2 * seed_slot(A, (uint32_t)(path - A.path_base), k)] = make_float4(0.f, 0.f, 0.f, 0.f);
+        A.seedv[2 * seed_slot(A, (uint32_t)(path - A.path_base), k) + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       continue;
     }
@@ -812,7 +819,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_nee_adjoint(AdjArgs A) {
       gP0 = gP0 - gT;
       if (OPT & ADJ_ACQ) ADD(acc[iPitch], gT.x * ((float)e2 - 0.5f * (float)(q.ne - 1)));
       const float Gf = Ga / fd.v;
-      const size_t sv = 2 * ((size_t)(path - A.path_base) * K1 + k);
+      const size_t sv = 2 * seed_slot(A, (uint32_t)(path - A.path_base), k);
       A.seedv[sv] = make_float4(gP0.x, gP0.y, gP0.z, 0.0f);
       A.seedv[sv + 1] = make_float4(Gf * fd.d[RN_W], Gf * fd.d[RN_W + 1], Gf * fd.d[RN_W + 2], 0.0f);
     }

@@ -178,3 +178,33 @@ def test_element_sub_apertures_partition_the_frame(ctx):
     with pytest.raises(usrt.UsrtError):
         ctx.forward(sid, w["theta"], bad, w["img"], seed=w["seed"])
     ctx.release_scene(sid)
+
+
+def test_adjoint_reads_no_stale_workspace(ctx):
+    """The transport VJP on a context whose workspaces hold a deeper pass's data, against the
+    oracle.  Paths whose last event (at k_max) is a scatterer started no secondary ray there,
+    so no seed may be read for that event from the buffer a previous call left."""
+    # dense scatterers (mean free path ~0.4 mm): many paths cross the layer interface, scatter
+    # and end at a scatterer at k_max = 2; the deeper pass before it (half the paths, K_max 6)
+    # leaves secondary-ray seeds of its events 4 and 5 where the shallow pass keeps its k_max
+    # events
+    w = P.slab_scatterers(n_rays=300, n_scat=200000, k_max=2)
+    big = P.slab_scatterers(n_rays=150, n_scat=200000, k_max=6)
+    sid = ctx.upload_workload(big)
+    rf, b = ctx.forward(sid, big["theta"], big["acq"], big["img"], seed=big["seed"], keep_record=True)
+    ctx.transport_vjp(sid, big["theta"], big["acq"], big["seed"], torch.randn_like(rf) * 1e6)  # large seeds
+    ctx.release_scene(sid)
+    sid = ctx.upload_workload(w)
+    rf, _ = ctx.forward(sid, w["theta"], w["acq"], w["img"], seed=w["seed"], keep_record=True)
+    acq = w["acq"]
+    rec = ctx.record(0, len(acq["angles"]) * acq["n_elem"] * acq["n_rays"], acq["k_max"]).cpu().numpy()
+    cls = ((rec.astype(np.int64) & 0xFFFFFFFF) >> 20) & 3
+    assert ((cls[:, -1] == 3) & (cls[:, 1] == 3)).mean() > 0.03  # swept paths that end so
+    ref = O.forward(w)
+    grf = np.random.default_rng(61).normal(size=ref["rf"].shape).astype(np.float32).astype(np.float64)
+    g_ref = ref["run"].gradient(grf)
+    g = ctx.transport_vjp(sid, w["theta"], acq, w["seed"], dev(grf)).double().cpu().numpy()
+    scale = np.abs(g_ref * w["theta"])
+    err = np.abs(g - g_ref) * np.abs(w["theta"])
+    assert np.all(err <= 1e-3 * scale + 1e-4 * scale.max()), np.c_[g, g_ref]
+    ctx.release_scene(sid)
