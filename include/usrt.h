@@ -330,8 +330,9 @@ int us_envlog_vjp(us_ctx* ctx, const us_img_desc* img, const float* irf_dev, con
 /* S10 alone: transposed DAS (Eq. das_adjoint), a scatter of dL/dI_rf back to the two
  * interpolation samples of every tap; dL_drf_dev is overwritten.  Deterministic: the scatter
  * accumulates in 64-bit fixed point (scale 2^k, the largest power of two with
- * pixels x max|dL/dI_rf| x 2^k < 2^62), so repeated calls give the same bits whatever the
- * order of the device's atomics.  A non-finite dL/dI_rf makes every entry NaN. */
+ * max|dL/dI_rf| x 2^k < 2^40 and pixels x max|dL/dI_rf| x 2^k < 2^62; a tap splits its
+ * pixel's integer weight exactly between its two samples), so repeated calls give the same bits
+ * whatever the order of the device's atomics.  A non-finite dL/dI_rf makes every entry NaN. */
 int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, const float* dL_dirf_dev,
                    float* dL_drf_dev, void* stream);
 

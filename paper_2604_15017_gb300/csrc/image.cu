@@ -323,15 +323,16 @@ size_t das_tma_smem(const Acq& q) {
 
 // transposed DAS: every tap scatters w_e (1 - f) g and w_e f g to its two samples
 // The transposed DAS accumulates in 64-bit fixed point so that its sums do not depend on the
-// order of the atomics (integer addition is associative, and wraps harmlessly in between): a
-// contribution v becomes the integer nearest v 2^k, with 2^k the largest power of two for
-// which max |dL/dI| 2^k < 2^43 and (pixel count) x max |dL/dI| 2^k < 2^62.  The second product
-// bounds every entry's sum, since a pixel adds at most w |dL/dI| <= |dL/dI| (w <= 1 the
-// apodisation) to one row, split between two neighbouring samples; the first lets the tiled
-// kernel hold a tile's partial sums in two 32-bit words (below).  The quantum is thus 2^-43 of
-// the largest pixel's contribution (2^-44 for 2^19 pixels or more), far below FP32 rounding.
-// max |dL/dI| comes from an integer atomicMax on the float bits of |dL/dI| (order-independent
-// too); a non-finite dL/dI makes every entry NaN.
+// order of the atomics (integer addition is associative, and wraps harmlessly in between).  A
+// pixel's weighted gradient w_e dL/dI becomes the integer W nearest w_e dL/dI 2^k, with 2^k the
+// largest power of two for which max |dL/dI| 2^k < 2^40 and (pixel count) x max |dL/dI| 2^k
+// < 2^62; a tap then splits W exactly into its two samples' shares, s1 = floor(W F / 2^23) and
+// s0 = W - s1, F the interpolation fraction in units of 2^-23.  The second bound holds every
+// entry's sum, since a pixel adds at most |W| to one row (w_e <= 1); the first keeps W F below
+// 2^63 and lets the tiled kernel hold a tile's partial sums in two 32-bit words (below).  The
+// quantum is 2^-40 of the largest pixel's contribution (2^-43 for 2^22 pixels), far below FP32
+// rounding.  max |dL/dI| comes from an integer atomicMax on the float bits of |dL/dI|
+// (order-independent too); a non-finite dL/dI makes every entry NaN.
 __global__ void k_das_adj_max(const float* __restrict__ gi, int n, unsigned int* maxbits) {
   unsigned int m = 0u;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -340,7 +341,9 @@ __global__ void k_das_adj_max(const float* __restrict__ gi, int n, unsigned int*
   if ((threadIdx.x & 31) == 0 && m) atomicMax(maxbits, m);
 }
 constexpr unsigned int F32_INF_BITS = 0x7F800000u;
-constexpr int DAS_ADJ_V_BITS = 43;  // |contribution| < 2^43 in fixed point
+constexpr int DAS_ADJ_V_BITS = 40;  // |W| < 2^40 in fixed point
+constexpr int DAS_ADJ_F_BITS = 23;  // interpolation fraction in units of 2^-23
+static_assert(DAS_ADJ_V_BITS + DAS_ADJ_F_BITS <= 63, "W F fits a signed 64-bit integer");
 // the exponent k: max |dL/dI| < 2^e and npx <= 2^c give npx max |dL/dI| < 2^(e + c)
 __device__ __forceinline__ int das_adj_kexp(int npx, unsigned int maxbits) {
   if (maxbits == 0u) return 0;
@@ -364,11 +367,23 @@ __device__ __forceinline__ void das_adj_fixed(float v, int& hi, uint32_t& lo) {
   const float lf = __fsub_rn(vr, hf * 4194304.0f);  // in [0, 2^22), exact
   lo = __float_as_uint(__fadd_rn(lf, 8388608.0f)) - 0x4B000000u;
 }
-__device__ __forceinline__ unsigned long long das_adj_fixed64(float v) {
+__device__ __forceinline__ long long das_adj_fixed64(float v) {
   int hi;
   uint32_t lo;
   das_adj_fixed(v, hi, lo);
-  return (unsigned long long)((long long)hi * (1ll << DAS_ADJ_LO_BITS) + (long long)lo);
+  return (long long)hi * (1ll << DAS_ADJ_LO_BITS) + (long long)lo;
+}
+// the two samples' shares of W at interpolation fraction f in [0, 1): 1 + f rounded to the
+// float grid of [1, 2) puts F = round(f 2^23) in the mantissa; s0 + s1 = W exactly
+__device__ __forceinline__ void das_adj_shares(long long W, float f, long long& s0, long long& s1) {
+  const long long F = (long long)(__float_as_int(__fadd_rn(1.0f, f)) - 0x3F800000);
+  s1 = (W * F) >> DAS_ADJ_F_BITS;  // arithmetic shift: floor
+  s0 = W - s1;
+}
+// a share as the tiled kernel's two words: hi 2^22 + lo, lo in [0, 2^22)
+__device__ __forceinline__ void das_adj_words(long long v, int& hi, uint32_t& lo) {
+  hi = (int)(v >> DAS_ADJ_LO_BITS);
+  lo = (uint32_t)v & ((1u << DAS_ADJ_LO_BITS) - 1u);
 }
 __global__ void k_das_adj_finish(const unsigned long long* __restrict__ acc, long long n, int npx,
                                  const unsigned int* maxbits, float* grf) {
@@ -396,14 +411,16 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
     if (gv != 0.0f) {
       for (int e = 0; e < q.ne; ++e) {
         const float2 ur = das_split(das_urx(q, g, x, z, e));
-        const float wg = ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp);
+        const long long W = das_adj_fixed64(ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp));
         for (int t = 0; t < q.ntx; ++t) {
           int i;
           float f;
           das_tap(utx_s[t * DAS_THREADS + threadIdx.x], ur, i, f);
+          long long s0, s1;
+          das_adj_shares(W, f, s0, s1);
           unsigned long long* row = acc + ((size_t)t * q.ne + e) * q.ns;
-          if (i >= 0 && i < q.ns) atomicAdd(&row[i], das_adj_fixed64(wg * (1.0f - f)));
-          if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], das_adj_fixed64(wg * f));
+          if (i >= 0 && i < q.ns) atomicAdd(&row[i], (unsigned long long)s0);
+          if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], (unsigned long long)s1);
         }
       }
     }
@@ -417,11 +434,11 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
 // window entry goes to its row with one global atomic.  A window spans ~100-200 samples against
 // the tile's 1024 taps per (e, t), so the global atomics drop several-fold.  A tap outside its
 // window (an underestimated window, or one longer than DJ_WIN) goes to the row directly.
-// A window entry is two 32-bit words with native shared atomics: a contribution v (|v| < 2^43)
-// splits into v >> 22 (signed, |.| <= 2^21) and its low 22 bits (unsigned); at most 512 pixels
-// add to one entry, so neither word can overflow (2^30 and 2^31), and the flush rebuilds
-// hi 2^22 + lo exactly.  The contributions and their sums are those of k_das_adj, so the two
-// kernels give the same bits.
+// A window entry is two 32-bit words with native shared atomics: a share v (|v| <= |W| < 2^40)
+// splits into v >> 22 (signed, |.| <= 2^18) and its low 22 bits (unsigned); at most 512 pixels
+// add to one entry, so neither word can overflow (2^27 and 2^31), and the flush rebuilds
+// hi 2^22 + lo exactly.  The shares and their sums are those of k_das_adj, so the two kernels
+// give the same bits.
 constexpr int DJ_THREADS = 512, DJ_LINES = 16, DJ_DEPTHS = 32, DJ_WIN = 256;
 constexpr int DJ_SMEM_MAX = 200 * 1024;
 static_assert(DJ_DEPTHS == 32 && DJ_LINES == 16 && DJ_THREADS / 32 == DJ_LINES, "a warp is one line's 32 depths");
@@ -477,31 +494,32 @@ __global__ void __launch_bounds__(DJ_THREADS) k_das_adj_tile(Acq q, Img im, cons
     const int2* wcur = win_s + (e & 1) * ntx;
     // the other buffer was last read by the previous element's flush, before its barrier
     if (e + 1 < q.ne) dj_windows(q, im, l0, l1, d0, d1, e + 1, win_s + ((e + 1) & 1) * ntx, lane, warp);
-    const float wg = gv != 0.0f ? ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp) : 0.0f;
-    if (wg != 0.0f) {
+    const long long W = gv != 0.0f ? das_adj_fixed64(ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp)) : 0ll;
+    if (W != 0ll) {
       const float2 ur = das_split(das_urx(q, g, x, z, e));
+#pragma unroll 2
       for (int t = 0; t < ntx; ++t) {
         int i;
         float f;
         das_tap(utx_s[t * DJ_THREADS + threadIdx.x], ur, i, f);
-        int h0, h1;
-        uint32_t o0, o1;
-        das_adj_fixed(wg * (1.0f - f), h0, o0);
-        das_adj_fixed(wg * f, h1, o1);
+        long long s0, s1;
+        das_adj_shares(W, f, s0, s1);
         const int2 w = wcur[t];
         const int rel = i - w.x;
         if (w.y > 0 && rel >= 0 && rel + 1 < w.y) {
           const int j = t * DJ_WIN + rel;
+          int h0, h1;
+          uint32_t o0, o1;
+          das_adj_words(s0, h0, o0);
+          das_adj_words(s1, h1, o1);
           atomicAdd(&hi_s[j], h0);
           atomicAdd(&lo_s[j], o0);
           atomicAdd(&hi_s[j + 1], h1);
           atomicAdd(&lo_s[j + 1], o1);
         } else {
           unsigned long long* row = acc + ((size_t)t * q.ne + e) * q.ns;
-          if (i >= 0 && i < q.ns)
-            atomicAdd(&row[i], (unsigned long long)((long long)h0 * (1ll << DAS_ADJ_LO_BITS) + (long long)o0));
-          if (i + 1 >= 0 && i + 1 < q.ns)
-            atomicAdd(&row[i + 1], (unsigned long long)((long long)h1 * (1ll << DAS_ADJ_LO_BITS) + (long long)o1));
+          if (i >= 0 && i < q.ns) atomicAdd(&row[i], (unsigned long long)s0);
+          if (i + 1 >= 0 && i + 1 < q.ns) atomicAdd(&row[i + 1], (unsigned long long)s1);
         }
       }
     }
