@@ -1382,7 +1382,7 @@ void hilbert(const double* x, int n, double* y) {
   for (int k = 0; k < n; ++k) y[k] = im[k] / n;
 }
 
-// envelope |x + i H(x)| per line along depth ("demodulation to baseband", Sec. 2.3.4)
+// envelope |x + i H(x)| per line along depth (the baseband demodulation of Sec. 2.3.4)
 void envelope(const Img& im, const double* irf, double* env) {
   std::vector<double> y(im.nd);
   for (int l = 0; l < im.nl; ++l) {
