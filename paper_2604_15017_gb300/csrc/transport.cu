@@ -687,40 +687,56 @@ __global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, Ra
     if (h[b]) atomicAdd(&rs.cnt[b], h[b]);
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_job_scatter(TransportArgs A, NeeQ from, NeeQ to, RaySort rs) {
-  extern __shared__ uint32_t sm[];
-  uint32_t* h = sm;
-  uint32_t* base = sm + JOB_BUCKETS;
+// as k_ray_scatter: key and rank packed, the copies JOB_BATCH jobs at a time with all loads
+// ahead of the stores
+constexpr int JOB_BATCH = 4;
+static_assert(RS_PER % JOB_BATCH == 0 && JOB_BUCKETS <= (1 << 19), "job batches, key and rank packing");
+__global__ void __launch_bounds__(RS_THREADS, 2) k_job_scatter(TransportArgs A, NeeQ from, NeeQ to, RaySort rs) {
+  extern __shared__ uint32_t sm[];  // [JOB_BUCKETS]: counts, then the chunk's first slot per key
   const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
+  constexpr uint32_t NONE = 0xFFFFFFFFu;
   for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
-    for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x) h[b] = 0;
+    for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x) sm[b] = 0;
     __syncthreads();
-    uint32_t key[RS_PER], rank[RS_PER];
+    uint32_t kr[RS_PER];
 #pragma unroll
     for (int j = 0; j < RS_PER; ++j) {
       const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
-      key[j] = 0xFFFFFFFFu;
+      kr[j] = NONE;
       if (i < n) {
-        key[j] = rs.key[i];
-        rank[j] = atomicAdd(&h[key[j]], 1u);
+        const uint32_t key = rs.key[i];
+        kr[j] = (key << 13) | atomicAdd(&sm[key], 1u);
       }
     }
     __syncthreads();
     for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x)
-      if (h[b]) base[b] = rs.off[b] + atomicAdd(&rs.cursor[b], h[b]);
+      if (sm[b]) sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < RS_PER; ++j) {
-      if (key[j] == 0xFFFFFFFFu) continue;
-      const uint32_t i = off + c0 + j * RS_THREADS + threadIdx.x;
-      const uint32_t o = off + base[key[j]] + rank[j];
-      const float4 jb = from.job[i];
-      to.job[o] = jb;
-      to.jm[o] = from.jm[i];
-      to.jpath[o] = from.jpath[i];
-      if (__float_as_uint(jb.w) & NEE_ROUGH) {
-        to.jx[o] = from.jx[i];
-        to.jw[o] = from.jw[i];
+    for (int j0 = 0; j0 < RS_PER; j0 += JOB_BATCH) {
+      float4 jb[JOB_BATCH];
+      uint32_t jm[JOB_BATCH], jp[JOB_BATCH];
+#pragma unroll
+      for (int u = 0; u < JOB_BATCH; ++u) {
+        if (kr[j0 + u] == NONE) continue;
+        const uint32_t i = off + c0 + (j0 + u) * RS_THREADS + threadIdx.x;
+        jb[u] = __ldg(&from.job[i]);
+        jm[u] = __ldg(&from.jm[i]);
+        jp[u] = __ldg(&from.jpath[i]);
+      }
+#pragma unroll
+      for (int u = 0; u < JOB_BATCH; ++u) {
+        const uint32_t v = kr[j0 + u];
+        if (v == NONE) continue;
+        const uint32_t i = off + c0 + (j0 + u) * RS_THREADS + threadIdx.x;
+        const uint32_t o = off + sm[v >> 13] + (v & 0x1FFFu);
+        to.job[o] = jb[u];
+        to.jm[o] = jm[u];
+        to.jpath[o] = jp[u];
+        if (__float_as_uint(jb[u].w) & NEE_ROUGH) {
+          to.jx[o] = __ldg(&from.jx[i]);
+          to.jw[o] = __ldg(&from.jw[i]);
+        }
       }
     }
     __syncthreads();
@@ -732,7 +748,7 @@ void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, c
   cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * JOB_BUCKETS, st);
   k_job_keys<<<grid, 256, sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, rs);
   launch_count_scan(rs.cnt, rs.off, rs.cursor, JOB_BUCKETS, st);
-  k_job_scatter<<<grid, RS_THREADS, 2 * sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, to, rs);
+  k_job_scatter<<<grid, RS_THREADS, sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, to, rs);
 }
 
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
@@ -749,7 +765,7 @@ cudaError_t ray_sort_set_attrs() {
                            (int)(sizeof(uint32_t) * RAY_BUCKETS));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_job_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(2 * sizeof(uint32_t) * RAY_BUCKETS));
+                           (int)(sizeof(uint32_t) * JOB_BUCKETS));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ray_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)(sizeof(uint32_t) * RAY_BUCKETS));
