@@ -1105,7 +1105,7 @@ int us_das_adjoint(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img, 
   unsigned int* maxbits;
   CKS(ws(ctx, W_DAS_ACC, (size_t)q.ntx * q.ne * q.ns, (cudaStream_t)stream, &acc));
   CKS(ws(ctx, W_DAS_MAX, 1, (cudaStream_t)stream, &maxbits));
-  StageScope sc_(ctx, US_STAGE_DAS_ADJ, 1, (cudaStream_t)stream);
+  StageScope sc_(ctx, US_STAGE_DAS_ADJ, 3, (cudaStream_t)stream);
   launch_das_adj(q, im, dL_dirf_dev, dL_drf_dev, grid_of(ctx, 8), (cudaStream_t)stream, acc, maxbits);
   CK(cudaGetLastError());
   return US_OK;
@@ -1137,7 +1137,7 @@ static int bmode_vjp(us_ctx* ctx, const us_acq_desc* acq, const us_img_desc* img
   CKS(ws(ctx, W_DAS_MAX, 1, st, &maxbits));
   CKS(us_envlog_vjp(ctx, img, irf, dL_dB_dev, gi, stream));
   {
-    StageScope sc_(ctx, US_STAGE_DAS_ADJ, 1, st);
+    StageScope sc_(ctx, US_STAGE_DAS_ADJ, 3, st);
     launch_das_adj(q, im, gi, dL_drf_dev, grid_of(ctx, 8), st, acc, maxbits);
   }
   CK(cudaGetLastError());
@@ -1466,11 +1466,12 @@ int us_request_bytes(us_ctx* ctx, const us_request* req, size_t* bytes) {
   Acq q;
   CKS(make_acq(ctx, req->acq, 0, q));
   const size_t n = (size_t)(q.rays_per_tx * q.ntx), K1 = q.kmax + 1, jobs = n * std::max(1, q.kmax);
-  size_t b = n * (2 * 48 + 8 + 4) + jobs * 2 * 24 + n * K1 * 16 * 2;  // queues, hits, keys, jobs, arrivals
+  size_t b = n * (2 * 48 + 8 + 2 * 4) + jobs * 2 * 24 + n * K1 * 16 * 2;  // queues, hits, ray and job keys,
+                                                                          // jobs, arrivals
   if (req->bref_dev) b += n * K1 * (4 + 8) + n * 4 + jobs * (16 + 8 + 16);  // record, seeds, active list,
                                                                                // secondary-ray results
   if (req->img) b += (size_t)req->img->n_lines * req->img->n_depth * 4 * 5;
-  b += (size_t)q.ntx * q.ne * q.ns * 4;                                 // dL/dRF
+  b += (size_t)q.ntx * q.ne * q.ns * (req->bref_dev ? 4 + 8 : 4);       // dL/dRF (and its fixed-point sums)
   *bytes = b;
   return US_OK;
 }

@@ -30,6 +30,8 @@ __device__ __forceinline__ void path_tx_ray(const Acq& q, long long path, int& t
   ray = (uint32_t)(q.tx_elem < 0 ? local : (long long)q.tx_elem * q.nr + local);
 }
 
+// coherence-sort key of a ray (RaySort): origin cell and direction bin; rays that carry their
+// surface hit go to the coarser buckets after RAY_KEY_BUCKETS
 __device__ __forceinline__ uint32_t ray_key(const RaySort& rs, float3 o, float3 w, bool carried) {
   // origin: 8 x 8 cells over the scene's x and z extent
   const int cx = min(7, max(0, (int)((o.x - rs.lo.x) * rs.inv_ext.x * 8.0f)));
@@ -588,11 +590,11 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
 }
 
 // ------------------------------------------------------------------------------------------
-// Coherence sort of a ray queue (one counting-sort pass, 14-bit key)
+// Coherence sort of a ray queue (one counting-sort pass over the keys ray_key gave the rays)
 // ------------------------------------------------------------------------------------------
 
 constexpr int RS_THREADS = 512;
-constexpr int JOB_BUCKETS = 1024;  // <= RAY_BUCKETS (the sort buffers are shared)
+constexpr int JOB_BUCKETS = 1024;  // <= RAY_BUCKETS (the job sort's scratch is sized as the ray sort's)
 constexpr int RS_PER = 16;
 constexpr int RS_CH = RS_THREADS * RS_PER;
 // One block sorts a chunk of RS_CH rays: shared-memory counts of the chunk's keys (in place
