@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
   }
 }
 
-// Tiled transposed DAS.  A CTA owns a 16-line x 32-depth pixel tile (two pixels per thread; a
+// Tiled transposed DAS.  A CTA owns a 16-line x 32-depth pixel tile (one pixel per thread; a
 // warp holds 32 consecutive depths of one line).  Element by element, the taps of all transmits
 // go into per-transmit sample windows in shared memory, the window of (e, t) being the samples
 // the tile's delays can reach (FP32 delays at the tile's corners, padded); then every nonzero
@@ -447,7 +447,7 @@ static_assert(DAS_ADJ_V_BITS - DAS_ADJ_LO_BITS + 9 < 31 && DAS_ADJ_LO_BITS + 9 <
 __host__ __device__ constexpr size_t das_adj_tile_smem(int ntx) {
   return (2 * sizeof(uint32_t) * DJ_WIN + sizeof(float2) * DJ_THREADS + 2 * sizeof(int2)) * (size_t)ntx;
 }
-// windows of element e for all transmits: warp w takes transmits w, w + 8, ...; its lanes
+// windows of element e for all transmits: warp w takes transmits w, w + 16, ...; its lanes
 // evaluate the 32 corner delays (16 lines x the two depth ends) and reduce them
 __device__ __forceinline__ void dj_windows(const Acq& q, const Img& im, int l0, int l1, int d0, int d1, int e,
                                            int2* out, int lane, int warp) {
