@@ -307,154 +307,224 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
 // transducer arrival, interface split (Fresnel / Snell, Sec. 2.3.2), or a scatterer (queue a
 // secondary ray, pass through).  Survivors are compacted into the output queue.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_interact(TransportArgs A) {
+// What the interaction of one queue slot emits: the surviving ray, a secondary-ray job, an
+// arrival (each at most once).  The kernel appends a block's emissions with one atomic per
+// counter: per-warp atomics on the three queue counters, which every warp of the grid shares,
+// are serialised in the L2 (2.46 -> 2.01 ms per frame with three blocks of 256 per SM, their
+// registers capped at 80).
+struct Emit {
+  bool ray, job, arr;
+  uint32_t path;   // the slot's path id
+  float4 pa, wt;   // the surviving ray
+  uint4 meta;
+  float2 surf, mis;
+  float4 job4;     // the job: (a, tau_hi, tau_lo, bits(job id word)), medium | element << 8 | ...
+  uint32_t jm;
+  float3 jx, jw;   // a rough event's point and incident direction
+  uint4 arr4;      // the arrival
+};
+__device__ __forceinline__ void interact_one(const TransportArgs& A, uint32_t i, Emit& E) {
   const Acq& q = A.acq;
   const Media& med = A.med;
-  const uint32_t n = A.cnt->live[A.k];
   const int K1 = q.kmax + 1;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const float2 h = A.hits[i];
-    const uint32_t code = __float_as_uint(h.y);
-    const uint32_t cls = code_cls(code);
-    const uint4 meta = A.qin.meta[i];
-    const float4 pa = A.qin.pa[i];  // read with the slot's other words, before the escape test
-    const float4 wt = A.qin.wt[i];
-    const long long path = meta.x;
-    uint32_t* rec = A.record ? &A.record[(size_t)(path - A.path_base) * K1 + A.k] : nullptr;
-    if (cls == CLS_NONE) {  // escape
-      if (rec) *rec = 0u;
-      continue;
+  const float2 h = A.hits[i];
+  const uint32_t code = __float_as_uint(h.y);
+  const uint32_t cls = code_cls(code);
+  const uint4 meta = A.qin.meta[i];
+  const float4 pa = A.qin.pa[i];  // read with the slot's other words, before the escape test
+  const float4 wt = A.qin.wt[i];
+  const long long path = meta.x;
+  E.path = meta.x;
+  uint32_t* rec = A.record ? &A.record[(size_t)(path - A.path_base) * K1 + A.k] : nullptr;
+  if (cls == CLS_NONE) {  // escape
+    if (rec) *rec = 0u;
+    return;
+  }
+  float2 mis = A.mis_on ? A.qin.mis[i] : make_float2(0.0f, 0.0f);
+  int m = (int)(meta.z & 0xFF);
+  float tau_lo = __uint_as_float(meta.w);
+  const float t = h.x;
+  float3 w = xyz(wt);
+  float a = pa.w * expf(-KAPPA_F * med.al[m] * med.f0 * t);
+  float tau_hi = wt.w;
+  ff_add(tau_hi, tau_lo, t / med.c[m]);
+  const float3 x = xyz(pa) + w * t;
+  int tx;
+  uint32_t ray;
+  path_tx_ray(q, path, tx, ray);
+  if (cls == CLS_XDCR) {  // arrival at the receiving element (Sec. 2.3.4)
+    if (rec) *rec = code;
+    float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
+    // straight on from a rough event: balance weight against that event's secondary ray
+    if (mis.x > 0.0f) frx *= rough_hit_weight(q, mis.x, mis.y + t, w);
+    if (frx > 0.0f && A.arr) {
+      const uint32_t tq = time_to_tq(tau_hi, tau_lo, q.fs);
+      if (tq != 0xFFFFFFFFu) {
+        E.arr = true;
+        E.arr4 = make_uint4((uint32_t)(tx * q.ne) + code_id(code), tq, __float_as_uint(a * frx), (uint32_t)path);
+      }
     }
-    float2 mis = A.mis_on ? A.qin.mis[i] : make_float2(0.0f, 0.0f);
-    int m = (int)(meta.z & 0xFF);
-    float tau_lo = __uint_as_float(meta.w);
-    const float t = h.x;
-    float3 w = xyz(wt);
-    float a = pa.w * expf(-KAPPA_F * med.al[m] * med.f0 * t);
-    float tau_hi = wt.w;
-    ff_add(tau_hi, tau_lo, t / med.c[m]);
-    const float3 x = xyz(pa) + w * t;
-    int tx;
-    uint32_t ray;
-    path_tx_ray(q, path, tx, ray);
-    if (cls == CLS_XDCR) {  // arrival at the receiving element (Sec. 2.3.4)
-      if (rec) *rec = code;
-      float frx = f_rx(-w.z, q.alpha_m, q.alpha_c);
-      // straight on from a rough event: balance weight against that event's secondary ray
-      if (mis.x > 0.0f) frx *= rough_hit_weight(q, mis.x, mis.y + t, w);
-      if (frx > 0.0f && A.arr) {
-        const uint32_t tq = time_to_tq(tau_hi, tau_lo, q.fs);
-        if (tq != 0xFFFFFFFFu) {
-          const uint32_t slot = append_slot(&A.cnt->n_arr);
-          if (slot < A.arr_cap)
-            A.arr[slot] = make_uint4((uint32_t)(tx * q.ne) + code_id(code), tq, __float_as_uint(a * frx), (uint32_t)path);
-        }
-      }
-      continue;
-    }
-    if (A.k == q.kmax) {  // interaction budget spent
-      if (rec) *rec = code;
-      continue;
-    }
-    const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, (uint32_t)(A.k + 1)),
-                                  make_uint2(q.key0, q.key1));
-    uint32_t word = code;
-    if (cls == CLS_TRI) {
-      const float4 nr = __ldg(&A.S.tri_nrm[code_id(code)]);
-      const uint32_t mm = __float_as_uint(nr.w);
-      const float3 nn = xyz(nr);
-      const bool front = dot3(w, nn) < 0.0f;
-      const float3 nin = front ? nn : nn * -1.0f;
-      const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
-      const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
-      // facet normal: the macro normal, or a GGX microfacet normal (roughness of the medium the
-      // triangle bounds, its back side)
-      const float alpha = med.rough[mm >> 16];
-      float3 fn = nin;
-      if (alpha > 0.0f && q.rough_nee) {  // secondary ray to a uniformly chosen element (Sec. 2.3.3)
-        const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
-        word |= (uint32_t)e2 << 24;
-        const uint32_t slot = A.cnt->nee_off[A.k] + append_slot(&A.cnt->nee[A.k]);
-        A.nee.job[slot] = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code) | NEE_ROUGH));
-        A.nee.jm[slot] = (uint32_t)m1 | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16) | ((uint32_t)A.k << 24);
-        A.nee.jpath[slot] = (uint32_t)path;
-        A.nee.jx[slot] = make_float4(x.x, x.y, x.z, 0.0f);
-        A.nee.jw[slot] = make_float4(w.x, w.y, w.z, 0.0f);
-      }
-      if (alpha > 0.0f) {
-        fn = ggx_sample(nin, alpha, u01(u.z), u01(u.w)).h;
-        if (dot3(w, fn) >= 0.0f) {  // facet met from behind: the path ends here
-          if (rec) {
-            *rec = word;
-            rec[1] = 0u;
-          }
-          continue;
-        }
-      }
-      const float3 w_in = w;
-      const Iface f = iface(w, fn, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
-      uint32_t choice;
-      if (f.tir) {
-        choice = CH_TIR;
-      } else {
-        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
-        choice = u01(u.x) < pr ? CH_REFLECT : CH_TRANSMIT;
-      }
-      if (choice == CH_TIR) {
-        w = w + fn * (2.0f * f.ci);
-        m = m1;
-      } else if (choice == CH_REFLECT) {
-        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
-        a = a * (f.R / pr);
-        w = w + fn * (2.0f * f.ci);
-        m = m1;
-      } else {
-        const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
-        a = a * (f.T / (1.0f - pr));
-        w = w * f.r + fn * (f.r * f.ci - f.ct);
-        m = m2;
-      }
-      word |= choice << 22;
-      if (alpha > 0.0f) {
-        const float on = dot3(w, nin), inn = dot3(w_in, nin);
-        if ((m == m1) != (on > 0.0f)) {  // outgoing direction on the wrong side: the path ends
-          if (rec) {
-            *rec = word;
-            rec[1] = 0u;
-          }
-          continue;
-        }
-        a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
-        if (A.mis_on) mis = make_float2(rough_bsdf_pdf(q, med, w_in, w, fn, nin, m1, m2, alpha, f, choice == CH_TRANSMIT), 0.0f);
-      } else {
-        mis = make_float2(0.0f, 0.0f);
-      }
-    } else {  // scatterer: secondary ray to a uniformly chosen element; Born pass-through
-      mis.y += t;  // straight on: still the last rough event's direction
+    return;
+  }
+  if (A.k == q.kmax) {  // interaction budget spent
+    if (rec) *rec = code;
+    return;
+  }
+  const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, (uint32_t)(A.k + 1)),
+                                make_uint2(q.key0, q.key1));
+  uint32_t word = code;
+  if (cls == CLS_TRI) {
+    const float4 nr = __ldg(&A.S.tri_nrm[code_id(code)]);
+    const uint32_t mm = __float_as_uint(nr.w);
+    const float3 nn = xyz(nr);
+    const bool front = dot3(w, nn) < 0.0f;
+    const float3 nin = front ? nn : nn * -1.0f;
+    const int m1 = front ? (int)(mm & 0xFFFF) : (int)(mm >> 16);
+    const int m2 = front ? (int)(mm >> 16) : (int)(mm & 0xFFFF);
+    // facet normal: the macro normal, or a GGX microfacet normal (roughness of the medium the
+    // triangle bounds, its back side)
+    const float alpha = med.rough[mm >> 16];
+    float3 fn = nin;
+    if (alpha > 0.0f && q.rough_nee) {  // secondary ray to a uniformly chosen element (Sec. 2.3.3)
       const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
       word |= (uint32_t)e2 << 24;
-      const uint32_t slot = A.cnt->nee_off[A.k] + append_slot(&A.cnt->nee[A.k]);
-      A.nee.job[slot] = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code)));
-      A.nee.jm[slot] = (uint32_t)m | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16) | ((uint32_t)A.k << 24);
-      A.nee.jpath[slot] = (uint32_t)path;
+      E.job = true;
+      E.job4 = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code) | NEE_ROUGH));
+      E.jm = (uint32_t)m1 | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16) | ((uint32_t)A.k << 24);
+      E.jx = x;
+      E.jw = w;
     }
-    if (rec) *rec = word;
-    // past a scatterer the ray goes on unchanged, so the surface hit found this round is the
-    // next one: it is carried, at its distance from the new origin, unless it lies within the
-    // minimum hit distance (a fresh query would pass over it)
-    float2 carry = make_float2(-1.0f, 0.0f);
-    if (cls == CLS_SCAT) {
-      const float2 ks = A.keep[i];
-      const float t_rem = ks.x - t;
-      if (t_rem > 2.0f * T_MIN) carry = make_float2(t_rem, ks.y);
+    if (alpha > 0.0f) {
+      fn = ggx_sample(nin, alpha, u01(u.z), u01(u.w)).h;
+      if (dot3(w, fn) >= 0.0f) {  // facet met from behind: the path ends here
+        if (rec) {
+          *rec = word;
+          rec[1] = 0u;
+        }
+        return;
+      }
     }
-    const uint32_t o = append_slot(&A.cnt->live[A.k + 1]);
-    A.qout.pa[o] = make_float4(x.x, x.y, x.z, a);
-    A.qout.wt[o] = make_float4(w.x, w.y, w.z, tau_hi);
-    A.qout.meta[o] = make_uint4(meta.x, code, (uint32_t)m | ((uint32_t)(A.k + 1) << 8), __float_as_uint(tau_lo));
-    A.qout.surf[o] = carry;
-    if (A.mis_on) A.qout.mis[o] = mis;
-    ray_key_count(A.rk, o, x, w, carry.x >= 0.0f);
+    const float3 w_in = w;
+    const Iface f = iface(w, fn, med.c[m1], med.c[m2], med.rho[m1], med.rho[m2]);
+    uint32_t choice;
+    if (f.tir) {
+      choice = CH_TIR;
+    } else {
+      const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+      choice = u01(u.x) < pr ? CH_REFLECT : CH_TRANSMIT;
+    }
+    if (choice == CH_TIR) {
+      w = w + fn * (2.0f * f.ci);
+      m = m1;
+    } else if (choice == CH_REFLECT) {
+      const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+      a = a * (f.R / pr);
+      w = w + fn * (2.0f * f.ci);
+      m = m1;
+    } else {
+      const float pr = q.split_mode == 0 ? f.R * f.R : q.split_q;
+      a = a * (f.T / (1.0f - pr));
+      w = w * f.r + fn * (f.r * f.ci - f.ct);
+      m = m2;
+    }
+    word |= choice << 22;
+    if (alpha > 0.0f) {
+      const float on = dot3(w, nin), inn = dot3(w_in, nin);
+      if ((m == m1) != (on > 0.0f)) {  // outgoing direction on the wrong side: the path ends
+        if (rec) {
+          *rec = word;
+          rec[1] = 0u;
+        }
+        return;
+      }
+      a *= -dot3(w_in, fn) * smith_g1(inn, alpha) * smith_g1(on, alpha) / (-inn * dot3(fn, nin));
+      if (A.mis_on) mis = make_float2(rough_bsdf_pdf(q, med, w_in, w, fn, nin, m1, m2, alpha, f, choice == CH_TRANSMIT), 0.0f);
+    } else {
+      mis = make_float2(0.0f, 0.0f);
+    }
+  } else {  // scatterer: secondary ray to a uniformly chosen element; Born pass-through
+    mis.y += t;  // straight on: still the last rough event's direction
+    const int e2 = min(q.ne - 1, (int)floorf(u01(u.y) * (float)q.ne));
+    word |= (uint32_t)e2 << 24;
+    E.job = true;
+    E.job4 = make_float4(a, tau_hi, tau_lo, __uint_as_float(code_id(code)));
+    E.jm = (uint32_t)m | ((uint32_t)e2 << 8) | ((uint32_t)tx << 16) | ((uint32_t)A.k << 24);
+  }
+  if (rec) *rec = word;
+  // past a scatterer the ray goes on unchanged, so the surface hit found this round is the
+  // next one: it is carried, at its distance from the new origin, unless it lies within the
+  // minimum hit distance (a fresh query would pass over it)
+  float2 carry = make_float2(-1.0f, 0.0f);
+  if (cls == CLS_SCAT) {
+    const float2 ks = A.keep[i];
+    const float t_rem = ks.x - t;
+    if (t_rem > 2.0f * T_MIN) carry = make_float2(t_rem, ks.y);
+  }
+  E.ray = true;
+  E.pa = make_float4(x.x, x.y, x.z, a);
+  E.wt = make_float4(w.x, w.y, w.z, tau_hi);
+  E.meta = make_uint4(meta.x, code, (uint32_t)m | ((uint32_t)(A.k + 1) << 8), __float_as_uint(tau_lo));
+  E.surf = carry;
+  E.mis = mis;
+}
+
+constexpr int IA_THREADS = 256, IA_WARPS = IA_THREADS / 32;
+__global__ void __launch_bounds__(IA_THREADS, 3) k_interact(TransportArgs A) {
+  __shared__ uint32_t s_pre[3][IA_WARPS];  // per warp: emissions, then the warp's first offset
+  __shared__ uint32_t s_base[3];           // the block's first slot per counter
+  const uint32_t n = A.cnt->live[A.k];
+  const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
+  for (uint32_t b0 = blockIdx.x * IA_THREADS; b0 < n; b0 += gridDim.x * IA_THREADS) {  // block-uniform
+    const uint32_t i = b0 + threadIdx.x;
+    Emit E;
+    E.ray = E.job = E.arr = false;
+    if (i < n) interact_one(A, i, E);
+    const unsigned mr = __ballot_sync(0xFFFFFFFFu, E.ray);
+    const unsigned mj = __ballot_sync(0xFFFFFFFFu, E.job);
+    const unsigned ma = __ballot_sync(0xFFFFFFFFu, E.arr);
+    if (lane == 0) {
+      s_pre[0][wid] = __popc(mr);
+      s_pre[1][wid] = __popc(mj);
+      s_pre[2][wid] = __popc(ma);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      const int c = threadIdx.x;
+      uint32_t run = 0u;
+      for (int w = 0; w < IA_WARPS; ++w) {
+        const uint32_t v = s_pre[c][w];
+        s_pre[c][w] = run;
+        run += v;
+      }
+      uint32_t* ctr = c == 0 ? &A.cnt->live[A.k + 1] : (c == 1 ? &A.cnt->nee[A.k] : &A.cnt->n_arr);
+      s_base[c] = run ? atomicAdd(ctr, run) : 0u;
+    }
+    __syncthreads();
+    if (E.ray) {
+      const uint32_t o = s_base[0] + s_pre[0][wid] + __popc(mr & below);
+      A.qout.pa[o] = E.pa;
+      A.qout.wt[o] = E.wt;
+      A.qout.meta[o] = E.meta;
+      A.qout.surf[o] = E.surf;
+      if (A.mis_on) A.qout.mis[o] = E.mis;
+      ray_key_count(A.rk, o, xyz(E.pa), xyz(E.wt), E.surf.x >= 0.0f);
+    }
+    if (E.job) {
+      const uint32_t slot = A.cnt->nee_off[A.k] + s_base[1] + s_pre[1][wid] + __popc(mj & below);
+      A.nee.job[slot] = E.job4;
+      A.nee.jm[slot] = E.jm;
+      A.nee.jpath[slot] = E.path;
+      if (__float_as_uint(E.job4.w) & NEE_ROUGH) {
+        A.nee.jx[slot] = make_float4(E.jx.x, E.jx.y, E.jx.z, 0.0f);
+        A.nee.jw[slot] = make_float4(E.jw.x, E.jw.y, E.jw.z, 0.0f);
+      }
+    }
+    if (E.arr) {
+      const uint32_t slot = s_base[2] + s_pre[2][wid] + __popc(ma & below);
+      if (slot < A.arr_cap) A.arr[slot] = E.arr4;
+    }
+    __syncthreads();  // s_pre and s_base are rewritten by the next iteration
   }
 }
 
