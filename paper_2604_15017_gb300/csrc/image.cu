@@ -103,16 +103,24 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das(Acq q, Img im, const float*
     for (int t = 0; t < q.ntx; ++t) utx_s[t * DAS_THREADS + threadIdx.x] = das_split(das_utx(q, g, x, z, t));
     float acc = 0.0f;
     if (valid) {
+      const size_t tstride = (size_t)q.ne * q.ns;  // between one element's rows of two transmits
       for (int e = 0; e < q.ne; ++e) {
         const float2 ur = das_split(das_urx(q, g, x, z, e));
+        const float* row = rf + (size_t)e * q.ns;
         float s = 0.0f;
-        for (int t = 0; t < q.ntx; ++t) {
+#pragma unroll 4
+        for (int t = 0; t < q.ntx; ++t, row += tstride) {
           int i;
           float f;
           das_tap(utx_s[t * DAS_THREADS + threadIdx.x], ur, i, f);
-          const float* row = rf + ((size_t)t * q.ne + e) * q.ns;
-          const float a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
-          const float b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
+          float a, b;
+          if ((unsigned)i < (unsigned)(q.ns - 1)) {  // both samples inside the record
+            a = __ldg(&row[i]);
+            b = __ldg(&row[i + 1]);
+          } else {
+            a = (i >= 0 && i < q.ns) ? __ldg(&row[i]) : 0.0f;
+            b = (i + 1 >= 0 && i + 1 < q.ns) ? __ldg(&row[i + 1]) : 0.0f;
+          }
           s += fmaf(f, b - a, a);
         }
         acc = fmaf(apod_w(q, im, x.hi, z.hi, e), s, acc);
