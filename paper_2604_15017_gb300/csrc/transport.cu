@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
   // lane state
   uint32_t ray = 0xFFFFFFFFu;  // queue slot of the current ray; none when 0xFFFFFFFF
   float3 o = f3(0.0f, 0.0f, 0.0f), w = o;
-  float ix = 0.0f, iy = 0.0f, iz = 0.0f, tnx = 0.0f, tny = 0.0f, tnz = 0.0f, tbest = 0.0f;
+  float ix = 0.0f, iy = 0.0f, iz = 0.0f, tnx = 0.0f, tny = 0.0f, tnz = 0.0f, tbest = 0.0f, t0hit = 0.0f;
   uint32_t prev = 0u, cbest = 0u, code0 = 0u, e = 0u, e_end = 0u;
   int cx = 0, cy = 0, cz = 0, idx = 0, sx = 1, sy = 1, sz = 1, ux = 0, uy = 0, uz = 0;
   // The DDA runs one cell ahead: (cx, cy, cz, idx) is the next cell to enter, at t_ahead, and
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
         o = xyz(pa);
         w = xyz(wt);
         prev = A.qin.meta[ray].y;
-        tbest = hit.x;
+        tbest = t0hit = hit.x;
         cbest = code0 = __float_as_uint(hit.y);
         ix = safe_inv(w.x);
         iy = safe_inv(w.y);
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(MARCH_THREADS) k_march(TransportArgs A) {
     }
     if (!(ahead_ok && t_ahead <= tbest)) {  // no cell left to enter below tbest: done
       if (cbest != code0) {  // a scatterer comes first; its pass-through carries the surface hit on
-        A.keep[ray] = A.hits[ray];
+        A.keep[ray] = make_float2(t0hit, __uint_as_float(code0));  // the hit this ray came with
         A.hits[ray] = make_float2(tbest, __uint_as_float(cbest));
       }
       ray = 0xFFFFFFFFu;
@@ -333,6 +333,7 @@ __device__ __forceinline__ void interact_one(const TransportArgs& A, uint32_t i,
   const uint4 meta = A.qin.meta[i];
   const float4 pa = A.qin.pa[i];  // read with the slot's other words, before the escape test
   const float4 wt = A.qin.wt[i];
+  const float2 ks = A.keep[i];  // used at scatterer events; read with the rest, not after the hit's class
   const long long path = meta.x;
   E.path = meta.x;
   uint32_t* rec = A.record ? &A.record[(size_t)(path - A.path_base) * K1 + A.k] : nullptr;
@@ -456,7 +457,6 @@ __device__ __forceinline__ void interact_one(const TransportArgs& A, uint32_t i,
   // minimum hit distance (a fresh query would pass over it)
   float2 carry = make_float2(-1.0f, 0.0f);
   if (cls == CLS_SCAT) {
-    const float2 ks = A.keep[i];
     const float t_rem = ks.x - t;
     if (t_rem > 2.0f * T_MIN) carry = make_float2(t_rem, ks.y);
   }
