@@ -669,18 +669,24 @@ constexpr int RS_PER = 4;  // rays per thread and chunk: 2048-ray chunks measure
 constexpr int RS_CH = RS_THREADS * RS_PER;
 // One block sorts a chunk of RS_CH rays: shared-memory counts of the chunk's keys (in place
 // then the chunk's first slot per key, 68 KB, so that two blocks fit an SM), then every ray is
-// copied to its slot.  Key and rank travel packed in one word (key < 2^15, rank < 2^13).  The
-// copies go RS_BATCH rays at a time, all loads before the stores, so that each thread keeps
-// several reads in flight.
+// copied to its slot.  The keys the chunk touches are listed as they first occur, so that only
+// they are turned into slots and cleared again (a chunk touches at most RS_CH of the
+// RAY_BUCKETS counters).  Key and rank travel packed in one word (key < 2^15, rank < 2^13).
+// The copies go RS_BATCH rays at a time, all loads before the stores, so that each thread
+// keeps several reads in flight.
 constexpr int RS_BATCH = 2;
 static_assert(RAY_BUCKETS < (1 << 19) && RS_CH <= (1 << 13) && RS_PER % RS_BATCH == 0, "key and rank packing");
+__host__ __device__ constexpr size_t scatter_smem(int buckets) { return sizeof(uint32_t) * ((size_t)buckets + RS_CH); }
 __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, PathQ from, PathQ to, RaySort rs) {
-  extern __shared__ uint32_t sm[];  // [RAY_BUCKETS]
+  extern __shared__ uint32_t sm[];  // [RAY_BUCKETS] counts, then [RS_CH] touched keys
+  uint32_t* touched = sm + RAY_BUCKETS;
+  __shared__ uint32_t n_touched;
   const uint32_t n = A.cnt->live[A.k];
   constexpr uint32_t NONE = 0xFFFFFFFFu;
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) sm[b] = 0;
+  if (threadIdx.x == 0) n_touched = 0;
+  __syncthreads();
   for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
-    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) sm[b] = 0;
-    __syncthreads();
     uint32_t kr[RS_PER];
 #pragma unroll
     for (int j = 0; j < RS_PER; ++j) {
@@ -688,12 +694,17 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, 
       kr[j] = NONE;
       if (i < n) {
         const uint32_t key = rs.key[i];
-        kr[j] = (key << 13) | atomicAdd(&sm[key], 1u);
+        const uint32_t rank = atomicAdd(&sm[key], 1u);
+        if (rank == 0u) touched[atomicAdd(&n_touched, 1u)] = key;
+        kr[j] = (key << 13) | rank;
       }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x)
-      if (sm[b]) sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
+    const uint32_t nt = n_touched;
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
+      const uint32_t b = touched[t];
+      sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
+    }
     __syncthreads();
 #pragma unroll
     for (int j0 = 0; j0 < RS_PER; j0 += RS_BATCH) {
@@ -723,6 +734,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, 
         if (A.mis_on) to.mis[o] = mi[u];
       }
     }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) sm[touched[t]] = 0;
+    if (threadIdx.x == 0) n_touched = 0;
     __syncthreads();
   }
 }
@@ -766,12 +780,15 @@ __global__ void __launch_bounds__(256) k_job_keys(TransportArgs A, NeeQ from, Ra
 constexpr int JOB_BATCH = 4;
 static_assert(RS_PER % JOB_BATCH == 0 && JOB_BUCKETS <= (1 << 19), "job batches, key and rank packing");
 __global__ void __launch_bounds__(RS_THREADS, 2) k_job_scatter(TransportArgs A, NeeQ from, NeeQ to, RaySort rs) {
-  extern __shared__ uint32_t sm[];  // [JOB_BUCKETS]: counts, then the chunk's first slot per key
+  extern __shared__ uint32_t sm[];  // [JOB_BUCKETS] counts, then the chunk's first slot per key; [RS_CH] touched keys
+  uint32_t* touched = sm + JOB_BUCKETS;
+  __shared__ uint32_t n_touched;
   const uint32_t n = A.cnt->nee[A.k], off = A.cnt->nee_off[A.k];
   constexpr uint32_t NONE = 0xFFFFFFFFu;
+  for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x) sm[b] = 0;
+  if (threadIdx.x == 0) n_touched = 0;
+  __syncthreads();
   for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
-    for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x) sm[b] = 0;
-    __syncthreads();
     uint32_t kr[RS_PER];
 #pragma unroll
     for (int j = 0; j < RS_PER; ++j) {
@@ -779,12 +796,17 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_job_scatter(TransportArgs A, 
       kr[j] = NONE;
       if (i < n) {
         const uint32_t key = rs.key[i];
-        kr[j] = (key << 13) | atomicAdd(&sm[key], 1u);
+        const uint32_t rank = atomicAdd(&sm[key], 1u);
+        if (rank == 0u) touched[atomicAdd(&n_touched, 1u)] = key;
+        kr[j] = (key << 13) | rank;
       }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < JOB_BUCKETS; b += blockDim.x)
-      if (sm[b]) sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
+    const uint32_t nt = n_touched;
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
+      const uint32_t b = touched[t];
+      sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
+    }
     __syncthreads();
 #pragma unroll
     for (int j0 = 0; j0 < RS_PER; j0 += JOB_BATCH) {
@@ -814,6 +836,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_job_scatter(TransportArgs A, 
       }
     }
     __syncthreads();
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) sm[touched[t]] = 0;
+    if (threadIdx.x == 0) n_touched = 0;
+    __syncthreads();
   }
 }
 
@@ -822,13 +847,13 @@ void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, c
   cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * JOB_BUCKETS, st);
   k_job_keys<<<grid, 256, sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, rs);
   launch_count_scan(rs.cnt, rs.off, rs.cursor, JOB_BUCKETS, st);
-  k_job_scatter<<<grid, RS_THREADS, sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, to, rs);
+  k_job_scatter<<<grid, RS_THREADS, scatter_smem(JOB_BUCKETS), st>>>(a, from, to, rs);
 }
 
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st) {
   launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
-  k_ray_scatter<<<grid, RS_THREADS, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, from, to, rs);
+  k_ray_scatter<<<grid, RS_THREADS, scatter_smem(RAY_BUCKETS), st>>>(a, from, to, rs);
 }
 
 cudaError_t ray_sort_set_attrs() {
@@ -839,10 +864,10 @@ cudaError_t ray_sort_set_attrs() {
                            (int)(sizeof(uint32_t) * RAY_BUCKETS));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_job_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(uint32_t) * JOB_BUCKETS));
+                           (int)scatter_smem(JOB_BUCKETS));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ray_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(sizeof(uint32_t) * RAY_BUCKETS));
+                              (int)scatter_smem(RAY_BUCKETS));
 }
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {
