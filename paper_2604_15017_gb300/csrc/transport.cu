@@ -665,20 +665,23 @@ __global__ void __launch_bounds__(NEE_THREADS) k_nee(TransportArgs A) {
 
 constexpr int RS_THREADS = 512;
 constexpr int JOB_BUCKETS = 4096;  // <= RAY_BUCKETS (the job sort's scratch is sized as the ray sort's)
-constexpr int RS_PER = 4;  // rays per thread and chunk: 2048-ray chunks measured best (16: +0.2 ms per frame)
-constexpr int RS_CH = RS_THREADS * RS_PER;
-// One block sorts a chunk of RS_CH rays: shared-memory counts of the chunk's keys (in place
+// items per thread and chunk, measured: 1024-ray chunks for the rays (512: +0.25 ms of sort per
+// frame, 2048: +0.12 ms, 8192: +0.5 ms), 2048-job chunks for the jobs
+constexpr int RAY_PER = 2, RS_PER = 4;
+constexpr int RAY_CH = RS_THREADS * RAY_PER, RS_CH = RS_THREADS * RS_PER;
+// One block sorts a chunk of RAY_CH rays: shared-memory counts of the chunk's keys (in place
 // then the chunk's first slot per key, 68 KB, so that two blocks fit an SM), then every ray is
 // copied to its slot.  The keys the chunk touches are listed as they first occur, so that only
-// they are turned into slots and cleared again (a chunk touches at most RS_CH of the
+// they are turned into slots and cleared again (a chunk touches at most RAY_CH of the
 // RAY_BUCKETS counters).  Key and rank travel packed in one word (key < 2^15, rank < 2^13).
 // The copies go RS_BATCH rays at a time, all loads before the stores, so that each thread
 // keeps several reads in flight.
 constexpr int RS_BATCH = 2;
-static_assert(RAY_BUCKETS < (1 << 19) && RS_CH <= (1 << 13) && RS_PER % RS_BATCH == 0, "key and rank packing");
-__host__ __device__ constexpr size_t scatter_smem(int buckets) { return sizeof(uint32_t) * ((size_t)buckets + RS_CH); }
+static_assert(RAY_BUCKETS < (1 << 19) && RAY_CH <= (1 << 13) && RS_CH <= (1 << 13) && RAY_PER % RS_BATCH == 0,
+              "key and rank packing");
+__host__ __device__ constexpr size_t scatter_smem(int buckets, int chunk) { return sizeof(uint32_t) * ((size_t)buckets + chunk); }
 __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, PathQ from, PathQ to, RaySort rs) {
-  extern __shared__ uint32_t sm[];  // [RAY_BUCKETS] counts, then [RS_CH] touched keys
+  extern __shared__ uint32_t sm[];  // [RAY_BUCKETS] counts, then [RAY_CH] touched keys
   uint32_t* touched = sm + RAY_BUCKETS;
   __shared__ uint32_t n_touched;
   const uint32_t n = A.cnt->live[A.k];
@@ -686,10 +689,10 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, 
   for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) sm[b] = 0;
   if (threadIdx.x == 0) n_touched = 0;
   __syncthreads();
-  for (uint32_t c0 = blockIdx.x * RS_CH; c0 < n; c0 += gridDim.x * RS_CH) {
-    uint32_t kr[RS_PER];
+  for (uint32_t c0 = blockIdx.x * RAY_CH; c0 < n; c0 += gridDim.x * RAY_CH) {
+    uint32_t kr[RAY_PER];
 #pragma unroll
-    for (int j = 0; j < RS_PER; ++j) {
+    for (int j = 0; j < RAY_PER; ++j) {
       const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
       kr[j] = NONE;
       if (i < n) {
@@ -707,7 +710,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, 
     }
     __syncthreads();
 #pragma unroll
-    for (int j0 = 0; j0 < RS_PER; j0 += RS_BATCH) {
+    for (int j0 = 0; j0 < RAY_PER; j0 += RS_BATCH) {
       float4 pa[RS_BATCH], wt[RS_BATCH];
       uint4 me[RS_BATCH];
       float2 sf[RS_BATCH], mi[RS_BATCH];
@@ -847,13 +850,13 @@ void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, c
   cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * JOB_BUCKETS, st);
   k_job_keys<<<grid, 256, sizeof(uint32_t) * JOB_BUCKETS, st>>>(a, from, rs);
   launch_count_scan(rs.cnt, rs.off, rs.cursor, JOB_BUCKETS, st);
-  k_job_scatter<<<grid, RS_THREADS, scatter_smem(JOB_BUCKETS), st>>>(a, from, to, rs);
+  k_job_scatter<<<grid, RS_THREADS, scatter_smem(JOB_BUCKETS, RS_CH), st>>>(a, from, to, rs);
 }
 
 void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to, const RaySort& rs, int grid,
                      cudaStream_t st) {
   launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
-  k_ray_scatter<<<grid, RS_THREADS, scatter_smem(RAY_BUCKETS), st>>>(a, from, to, rs);
+  k_ray_scatter<<<grid, RS_THREADS, scatter_smem(RAY_BUCKETS, RAY_CH), st>>>(a, from, to, rs);
 }
 
 cudaError_t ray_sort_set_attrs() {
@@ -864,10 +867,10 @@ cudaError_t ray_sort_set_attrs() {
                            (int)(sizeof(uint32_t) * RAY_BUCKETS));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_job_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)scatter_smem(JOB_BUCKETS));
+                           (int)scatter_smem(JOB_BUCKETS, RS_CH));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_ray_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)scatter_smem(RAY_BUCKETS));
+                              (int)scatter_smem(RAY_BUCKETS, RAY_CH));
 }
 
 void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {
