@@ -506,16 +506,17 @@ int run_transport(us_ctx* ctx, const SceneGPU* sc, const Media& med, const Acq& 
     CKS(ws(ctx, W_JOB_OFF, RAY_BUCKETS + 1, st, &js.off));
     CKS(ws(ctx, W_JOB_CUR, RAY_BUCKETS, st, &js.cursor));
   }
-  // Q.a: rays as generated / as the interaction kernel appends them; Q.b: coherence-sorted
-  A.qout = Q.a;
+  // Q.a: rays as the interaction kernel appends them; Q.b: coherence-sorted (the emission
+  // writes there directly)
+  A.qout = Q.b;
   {
-    StageScope sc_(ctx, US_STAGE_GENERATE, 1, st);
+    StageScope sc_(ctx, US_STAGE_GENERATE, 3, st);
     CK(cudaMemsetAsync(rs.cnt, 0, sizeof(uint32_t) * RAY_BUCKETS, st));
-    launch_generate(A, path0, n, grid_of(ctx, 2), st);
+    launch_generate(A, path0, n, rs, grid_of(ctx, 2), st);
   }
   for (int k = 0; k <= q.kmax; ++k) {
     A.k = k;
-    {
+    if (k > 0) {
       StageScope sc_(ctx, US_STAGE_RAY_SORT, 2, st);
       launch_ray_sort(A, Q.a, Q.b, rs, grid_of(ctx, 2), st);
     }

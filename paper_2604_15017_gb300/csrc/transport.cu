@@ -66,38 +66,36 @@ __device__ __forceinline__ void ray_key_count(const RaySort& rs, uint32_t slot, 
 // face, cosine-weighted direction (f_d / p = pi), weight pi / N_r, steering delay as a time
 // stamp tau_tx = (x_e sin(theta) + W/2 |sin(theta)|) / c_bf.
 // ------------------------------------------------------------------------------------------
-// The emitted rays share few sort keys (all start on the probe face), so the block counts its
-// rays' keys in shared memory and adds the nonzero counts once.
+__device__ __forceinline__ void emit_path(const Acq& q, long long path, float3& o0, float3& w0, float& tau0) {
+  int tx;
+  uint32_t ray;
+  path_tx_ray(q, path, tx, ray);
+  const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, 0u), make_uint2(q.key0, q.key1));
+  const int e = (int)(ray / (uint32_t)q.nr);
+  const float xe = (e - 0.5f * (q.ne - 1)) * q.pitch;
+  const float u0 = u01(u.x), u1 = u01(u.y), u2 = u01(u.z), u3 = u01(u.w);
+  const float r = sqrtf(u2);
+  float sp, cp;
+  sincospif(2.0f * u3, &sp, &cp);
+  const float st = q.sin_tx[tx];
+  tau0 = (xe * st + 0.5f * (q.ne - 1) * q.pitch * fabsf(st)) / q.cbf;
+  o0 = f3(xe + (u0 - 0.5f) * q.pitch, (u1 - 0.5f) * q.hel, 0.0f);
+  w0 = f3(r * cp, r * sp, sqrtf(1.0f - u2));
+}
+// The emitted rays go straight into coherence-sorted order: this pass counts their sort keys
+// (they share few, all starting on the probe face, so the block counts in shared memory and adds
+// the nonzero counts once), k_generate_sorted emits them again, after the scan of the counts,
+// into their slots.  Recomputing an emission costs less than writing a ray and moving it.
 constexpr int GEN_THREADS = 512;
-__global__ void __launch_bounds__(GEN_THREADS) k_generate(TransportArgs A, long long path0, uint32_t n) {
+__global__ void __launch_bounds__(GEN_THREADS) k_generate_count(TransportArgs A, long long path0, uint32_t n) {
   extern __shared__ uint32_t gen_h[];  // [RAY_BUCKETS]
   for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) gen_h[b] = 0u;
   __syncthreads();
-  const Acq& q = A.acq;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const long long path = path0 + i;
-    int tx;
-    uint32_t ray;
-    path_tx_ray(q, path, tx, ray);
-    const uint4 u = philox4x32_10(make_uint4(ray, (uint32_t)tx, q.stream, 0u), make_uint2(q.key0, q.key1));
-    const int e = (int)(ray / (uint32_t)q.nr);
-    const float xe = (e - 0.5f * (q.ne - 1)) * q.pitch;
-    const float u0 = u01(u.x), u1 = u01(u.y), u2 = u01(u.z), u3 = u01(u.w);
-    const float r = sqrtf(u2);
-    float sp, cp;
-    sincospif(2.0f * u3, &sp, &cp);
-    const float wz = sqrtf(1.0f - u2);
-    const float st = q.sin_tx[tx];
-    const float tau0 = (xe * st + 0.5f * (q.ne - 1) * q.pitch * fabsf(st)) / q.cbf;
-    const float3 o0 = f3(xe + (u0 - 0.5f) * q.pitch, (u1 - 0.5f) * q.hel, 0.0f), w0 = f3(r * cp, r * sp, wz);
-    A.qout.pa[i] = make_float4(o0.x, o0.y, o0.z, 3.14159265358979f / q.nr);
-    A.qout.wt[i] = make_float4(w0.x, w0.y, w0.z, tau0);
-    const uint32_t key = ray_key(A.rk, o0, w0, false);
-    A.rk.key[i] = key;
-    atomicAdd(&gen_h[key], 1u);
-    A.qout.meta[i] = make_uint4((uint32_t)path, 0xFFFFFFFFu, 0u, __float_as_uint(0.0f));
-    A.qout.surf[i] = make_float2(-1.0f, 0.0f);
-    if (A.mis_on) A.qout.mis[i] = make_float2(0.0f, 0.0f);
+    float3 o0, w0;
+    float tau0;
+    emit_path(A.acq, path0 + i, o0, w0, tau0);
+    atomicAdd(&gen_h[ray_key(A.rk, o0, w0, false)], 1u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt->live[0] = n;
   __syncthreads();
@@ -744,6 +742,59 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_ray_scatter(TransportArgs A, 
   }
 }
 
+// the second emission pass: chunks of RAY_CH paths, ranked per key as in k_ray_scatter, each
+// ray written once, to its sorted slot of A.qout
+__global__ void __launch_bounds__(RS_THREADS, 2) k_generate_sorted(TransportArgs A, long long path0, uint32_t n,
+                                                                  RaySort rs) {
+  extern __shared__ uint32_t sm[];  // [RAY_BUCKETS] counts, then [RAY_CH] touched keys
+  uint32_t* touched = sm + RAY_BUCKETS;
+  __shared__ uint32_t n_touched;
+  const Acq& q = A.acq;
+  constexpr uint32_t NONE = 0xFFFFFFFFu;
+  for (int b = threadIdx.x; b < RAY_BUCKETS; b += blockDim.x) sm[b] = 0;
+  if (threadIdx.x == 0) n_touched = 0;
+  __syncthreads();
+  for (uint32_t c0 = blockIdx.x * RAY_CH; c0 < n; c0 += gridDim.x * RAY_CH) {
+    uint32_t kr[RAY_PER];
+    float3 o[RAY_PER], w[RAY_PER];
+    float tau[RAY_PER];
+#pragma unroll
+    for (int j = 0; j < RAY_PER; ++j) {
+      const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
+      kr[j] = NONE;
+      if (i < n) {
+        emit_path(q, path0 + i, o[j], w[j], tau[j]);
+        const uint32_t key = ray_key(rs, o[j], w[j], false);
+        const uint32_t rank = atomicAdd(&sm[key], 1u);
+        if (rank == 0u) touched[atomicAdd(&n_touched, 1u)] = key;
+        kr[j] = (key << 13) | rank;
+      }
+    }
+    __syncthreads();
+    const uint32_t nt = n_touched;
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) {
+      const uint32_t b = touched[t];
+      sm[b] = rs.off[b] + atomicAdd(&rs.cursor[b], sm[b]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < RAY_PER; ++j) {
+      const uint32_t v = kr[j];
+      if (v == NONE) continue;
+      const uint32_t i = c0 + j * RS_THREADS + threadIdx.x;
+      const uint32_t slot = sm[v >> 13] + (v & 0x1FFFu);
+      A.qout.pa[slot] = make_float4(o[j].x, o[j].y, o[j].z, 3.14159265358979f / q.nr);
+      A.qout.wt[slot] = make_float4(w[j].x, w[j].y, w[j].z, tau[j]);
+      A.qout.meta[slot] = make_uint4((uint32_t)(path0 + i), 0xFFFFFFFFu, 0u, __float_as_uint(0.0f));
+      if (A.mis_on) A.qout.mis[slot] = make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < nt; t += blockDim.x) sm[touched[t]] = 0;
+    if (threadIdx.x == 0) n_touched = 0;
+    __syncthreads();
+  }
+}
+
 // key of a secondary-ray job: target element and origin cell, 4 in depth x 8 across (jobs aimed
 // at one element from nearby scatterers share a warp); a job the receive directivity cuts off
 // (Eq. cutoff) ends at once: those go to the last bucket so that they do not share warps with
@@ -860,8 +911,11 @@ void launch_ray_sort(const TransportArgs& a, const PathQ& from, const PathQ& to,
 }
 
 cudaError_t ray_sort_set_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(k_generate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_generate_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(uint32_t) * RAY_BUCKETS));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_generate_sorted, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)scatter_smem(RAY_BUCKETS, RAY_CH));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_job_keys, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(uint32_t) * RAY_BUCKETS));
@@ -873,8 +927,11 @@ cudaError_t ray_sort_set_attrs() {
                               (int)scatter_smem(RAY_BUCKETS, RAY_CH));
 }
 
-void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st) {
-  k_generate<<<grid, GEN_THREADS, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, path0, n);
+void launch_generate(const TransportArgs& a, long long path0, uint32_t n, const RaySort& rs, int grid,
+                     cudaStream_t st) {
+  k_generate_count<<<grid, GEN_THREADS, sizeof(uint32_t) * RAY_BUCKETS, st>>>(a, path0, n);
+  launch_count_scan(rs.cnt, rs.off, rs.cursor, RAY_BUCKETS, st);
+  k_generate_sorted<<<grid, RS_THREADS, scatter_smem(RAY_BUCKETS, RAY_CH), st>>>(a, path0, n, rs);
 }
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st) { k_traverse<<<grid, TRAV_THREADS, 0, st>>>(a); }
 void launch_march(const TransportArgs& a, int grid, cudaStream_t st) { k_march<<<grid, MARCH_THREADS, 0, st>>>(a); }

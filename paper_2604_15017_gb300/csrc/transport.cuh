@@ -109,7 +109,10 @@ void launch_job_sort(const TransportArgs& a, const NeeQ& from, const NeeQ& to, c
                      cudaStream_t st);
 cudaError_t ray_sort_set_attrs();
 
-void launch_generate(const TransportArgs& a, long long path0, uint32_t n, int grid, cudaStream_t st);
+// emission of paths [path0, path0 + n) straight into coherence-sorted order in a.qout (its keys
+// counted into rs.cnt, zeroed by the caller, then scanned)
+void launch_generate(const TransportArgs& a, long long path0, uint32_t n, const RaySort& rs, int grid,
+                     cudaStream_t st);
 constexpr int TRAV_THREADS = 128;
 void launch_traverse(const TransportArgs& a, int grid, cudaStream_t st);
 int traverse_blocks_per_sm();  // blocks per SM of the traversal grid
