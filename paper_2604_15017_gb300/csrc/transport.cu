@@ -84,8 +84,9 @@ __device__ __forceinline__ void emit_path(const Acq& q, long long path, float3& 
 }
 // The emitted rays go straight into coherence-sorted order: this pass counts their sort keys
 // (they share few, all starting on the probe face, so the block counts in shared memory and adds
-// the nonzero counts once), k_generate_sorted emits them again, after the scan of the counts,
-// into their slots.  Recomputing an emission costs less than writing a ray and moving it.
+// the nonzero counts once) and keeps each ray's key; k_generate_sorted emits them again, after
+// the scan of the counts, into the slots their kept keys give.  Recomputing an emission costs
+// less than writing a ray and moving it.
 constexpr int GEN_THREADS = 512;
 __global__ void __launch_bounds__(GEN_THREADS) k_generate_count(TransportArgs A, long long path0, uint32_t n) {
   extern __shared__ uint32_t gen_h[];  // [RAY_BUCKETS]
@@ -95,7 +96,9 @@ __global__ void __launch_bounds__(GEN_THREADS) k_generate_count(TransportArgs A,
     float3 o0, w0;
     float tau0;
     emit_path(A.acq, path0 + i, o0, w0, tau0);
-    atomicAdd(&gen_h[ray_key(A.rk, o0, w0, false)], 1u);
+    const uint32_t key = ray_key(A.rk, o0, w0, false);
+    A.rk.key[i] = key;  // the second pass takes the key from here, so that both passes agree
+    atomicAdd(&gen_h[key], 1u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) A.cnt->live[0] = n;
   __syncthreads();
@@ -764,7 +767,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) k_generate_sorted(TransportArgs
       kr[j] = NONE;
       if (i < n) {
         emit_path(q, path0 + i, o[j], w[j], tau[j]);
-        const uint32_t key = ray_key(rs, o[j], w[j], false);
+        const uint32_t key = rs.key[i];  // as counted
         const uint32_t rank = atomicAdd(&sm[key], 1u);
         if (rank == 0u) touched[atomicAdd(&n_touched, 1u)] = key;
         kr[j] = (key << 13) | rank;
