@@ -671,7 +671,8 @@ constexpr int JOB_BUCKETS = 4096;  // <= RAY_BUCKETS (the job sort's scratch is 
 constexpr int RAY_PER = 2, RS_PER = 4;
 constexpr int RAY_CH = RS_THREADS * RAY_PER, RS_CH = RS_THREADS * RS_PER;
 // One block sorts a chunk of RAY_CH rays: shared-memory counts of the chunk's keys (in place
-// then the chunk's first slot per key, 68 KB, so that two blocks fit an SM), then every ray is
+// then the chunk's first slot per key; 72 KB with the touched-key list, so that two blocks fit
+// an SM), then every ray is
 // copied to its slot.  The keys the chunk touches are listed as they first occur, so that only
 // they are turned into slots and cleared again (a chunk touches at most RAY_CH of the
 // RAY_BUCKETS counters).  Key and rank travel packed in one word (key < 2^15, rank < 2^13).
