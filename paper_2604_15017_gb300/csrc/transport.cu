@@ -949,7 +949,7 @@ int traverse_blocks_per_sm() {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_traverse, TRAV_THREADS, 0) != cudaSuccess || b < 1) b = 4;
   return 2 * b;  // two waves of resident blocks: a short tail without a long grid-stride loop
 }
-void launch_interact(const TransportArgs& a, int grid, cudaStream_t st) { k_interact<<<grid, 256, 0, st>>>(a); }
+void launch_interact(const TransportArgs& a, int grid, cudaStream_t st) { k_interact<<<grid, IA_THREADS, 0, st>>>(a); }
 void launch_nee(const TransportArgs& a, int grid, cudaStream_t st) { k_nee<<<grid, NEE_THREADS, 0, st>>>(a); }
 int nee_blocks_per_sm() {
   int b = 0;
