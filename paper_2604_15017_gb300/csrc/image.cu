@@ -537,11 +537,9 @@ __global__ void __launch_bounds__(DJ_THREADS) k_das_adj_tile(Acq q, Img im, cons
       const int2 w = wcur[t];
       if (r < w.y) {
         const long long v = (long long)hi_s[j] * (1ll << DAS_ADJ_LO_BITS) + (long long)lo_s[j];
-        if (v) {
-          atomicAdd(acc + ((size_t)t * q.ne + e) * q.ns + w.x + r, (unsigned long long)v);
-          hi_s[j] = 0;
-          lo_s[j] = 0u;
-        }
+        if (v) atomicAdd(acc + ((size_t)t * q.ne + e) * q.ns + w.x + r, (unsigned long long)v);
+        hi_s[j] = 0;  // both words, also when they cancel (v = 0 with hi = -lo / 2^22)
+        lo_s[j] = 0u;
       }
     }
     __syncthreads();
