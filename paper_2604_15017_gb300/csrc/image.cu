@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(DAS_THREADS) k_das_adj(Acq q, Img im, const fl
 // add to one entry, so neither word can overflow (2^27 and 2^31), and the flush rebuilds
 // hi 2^22 + lo exactly.  The shares and their sums are those of k_das_adj, so the two kernels
 // give the same bits.
-constexpr int DJ_THREADS = 512, DJ_LINES = 16, DJ_DEPTHS = 32, DJ_WIN = 256;
+constexpr int DJ_THREADS = 512, DJ_LINES = 16, DJ_DEPTHS = 32, DJ_WIN = 192;  // 256: +0.07 ms
 constexpr int DJ_SMEM_MAX = 200 * 1024;
 static_assert(DJ_DEPTHS == 32 && DJ_LINES == 16 && DJ_THREADS / 32 == DJ_LINES, "a warp is one line's 32 depths");
 static_assert(DAS_ADJ_V_BITS - DAS_ADJ_LO_BITS + 9 < 31 && DAS_ADJ_LO_BITS + 9 < 32,
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(DJ_THREADS) k_das_adj_tile(Acq q, Img im, cons
     const long long W = gv != 0.0f ? das_adj_fixed64(ldexpf(apod_w(q, im, x.hi, z.hi, e) * gv, kexp)) : 0ll;
     if (W != 0ll) {
       const float2 ur = das_split(das_urx(q, g, x, z, e));
-#pragma unroll 2
+#pragma unroll 4
       for (int t = 0; t < ntx; ++t) {
         int i;
         float f;
